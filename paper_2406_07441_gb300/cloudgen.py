@@ -1,0 +1,403 @@
+"""Seeded synthetic point clouds around a NACA 0012 aerofoil.
+
+This module only builds *inputs*: coordinates, point types (interior, wall,
+outer), wall normals and neighbour lists.  It holds none of the solver's
+arithmetic (no fluxes, no least-squares, no ordering) and is shared by the
+CUDA path, the CPU oracle, the tests and the benchmark.
+
+Geometry (stand-in for the paper's missing NACA 0012 point clouds, Sec. 5):
+
+* NACA 0012 half thickness y_t(x) = 0.6 (0.2969 sqrt x - 0.1260 x - 0.3516 x^2
+  + 0.2843 x^3 - 0.1036 x^4), the closed-trailing-edge variant of the
+  four-digit thickness law, chord 1.
+* Wall point i of n_i: theta_i = 2 pi i / n_i, x = (1 + cos theta) / 2,
+  y = +y_t on the upper surface (0 < theta < pi), -y_t on the lower one;
+  i = 0 is the trailing edge and the wall polygon is counter-clockwise.
+* Far field: a circle of radius 20 about (0.5, 0) at the same theta_i.
+* Layer j lies at blend s_j = (r^j - 1) / (r^(n_j-1) - 1) of the way along
+  the straight line from the wall point to the far-field point,
+  r = 1.1^(63/(n_j-1)) (r = 1.1 for 64 layers; finer clouds refine the same
+  stretching in index space).
+* Point index p = j * n_i + i: the wall points come first, in polygon order,
+  and the outer (far-field) points last.
+
+Stencils are either the 3x3 index block (8 neighbours, 5 on the first and last
+layers) or, for jittered clouds, all points within 2.5 local spacings (nearest
+first, capped at 20, at least 8), with neighbours seen through the aerofoil
+rejected.  Either kind is augmented with further nearby points until every
+split sub-stencil is well posed, so that the least-squares systems of the
+method never degenerate.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+INTERIOR, WALL, OUTER = 0, 1, 2
+BASE_SEED = 20240229
+
+
+@dataclasses.dataclass
+class Cloud:
+    x: np.ndarray        # f64[N]
+    y: np.ndarray        # f64[N]
+    flag: np.ndarray     # u8[N]: 0 interior, 1 wall, 2 outer
+    nx: np.ndarray       # f64[N]: unit wall normal into the fluid (0 elsewhere)
+    ny: np.ndarray
+    nbr_off: np.ndarray  # i32[N+1] CSR row offsets
+    nbr_idx: np.ndarray  # i32[nnz] CSR neighbour indices, no self, no duplicates
+    meta: dict
+
+    @property
+    def n(self) -> int:
+        return int(self.x.shape[0])
+
+    @property
+    def nnz(self) -> int:
+        return int(self.nbr_idx.shape[0])
+
+
+def naca0012_half_thickness(x):
+    x = np.asarray(x, dtype=np.float64)
+    return 0.6 * (0.2969 * np.sqrt(x) - 0.1260 * x - 0.3516 * x**2
+                  + 0.2843 * x**3 - 0.1036 * x**4)
+
+
+def _ogrid(n_i: int, n_j: int):
+    theta = 2.0 * math.pi * np.arange(n_i) / n_i
+    xw = 0.5 * (1.0 + np.cos(theta))
+    yt = naca0012_half_thickness(np.clip(xw, 0.0, 1.0))
+    yw = np.where(theta < math.pi, yt, -yt)
+    yw[0] = 0.0
+    if n_i % 2 == 0:
+        yw[n_i // 2] = 0.0
+    xf = 0.5 + 20.0 * np.cos(theta)
+    yf = 20.0 * np.sin(theta)
+    r = 1.1 ** (63.0 / (n_j - 1))
+    j = np.arange(n_j)
+    s = (r**j - 1.0) / (r ** (n_j - 1) - 1.0)
+    X = xw[None, :] + s[:, None] * (xf - xw)[None, :]
+    Y = yw[None, :] + s[:, None] * (yf - yw)[None, :]
+    return X, Y  # [n_j, n_i]
+
+
+def _wall_normals(xw, yw):
+    """Unit normals into the fluid of the counter-clockwise wall polygon."""
+    tx = np.roll(xw, -1) - np.roll(xw, 1)
+    ty = np.roll(yw, -1) - np.roll(yw, 1)
+    ln = np.hypot(tx, ty)
+    return ty / ln, -tx / ln
+
+
+def _local_spacing(X, Y):
+    """Index-direction half spans h_xi, h_eta and unit directions at every node."""
+    dxi_x = np.roll(X, -1, axis=1) - np.roll(X, 1, axis=1)
+    dxi_y = np.roll(Y, -1, axis=1) - np.roll(Y, 1, axis=1)
+    deta_x = np.empty_like(X)
+    deta_y = np.empty_like(Y)
+    deta_x[1:-1] = X[2:] - X[:-2]
+    deta_y[1:-1] = Y[2:] - Y[:-2]
+    deta_x[0] = 2.0 * (X[1] - X[0])
+    deta_y[0] = 2.0 * (Y[1] - Y[0])
+    deta_x[-1] = 2.0 * (X[-1] - X[-2])
+    deta_y[-1] = 2.0 * (Y[-1] - Y[-2])
+    hxi = 0.5 * np.hypot(dxi_x, dxi_y)
+    heta = 0.5 * np.hypot(deta_x, deta_y)
+    exi = np.stack([dxi_x, dxi_y]) / (2.0 * hxi)
+    eeta = np.stack([deta_x, deta_y]) / (2.0 * heta)
+    return hxi, heta, exi, eeta
+
+
+# ---------------------------------------------------------------------------
+# geometric well-posedness of the split sub-stencils (a property of the input)
+# ---------------------------------------------------------------------------
+
+def _frame(cloud_x, cloud_y, flag, nx, ny, p):
+    if flag[p] == WALL:
+        return (ny[p], -nx[p]), (nx[p], ny[p])
+    return (1.0, 0.0), (0.0, 1.0)
+
+
+def _substencils_ok(dx, dy, is_wall, e1, e2, tol=1e-6):
+    """Each split sub-stencil needs >= 2 points and a well-conditioned 2x2 system."""
+    a = dx * e1[0] + dy * e1[1]
+    b = dx * e2[0] + dy * e2[1]
+    if is_wall:
+        sets = [(a < 0, a, b), (a > 0, a, b), (b > 0, b, a)]
+    else:
+        sets = [(a < 0, a, b), (a > 0, a, b), (b < 0, b, a), (b > 0, b, a)]
+    for m, d, dp in sets:
+        if m.sum() < 2:
+            return False
+        sdd = np.sum(d[m] * d[m])
+        spp = np.sum(dp[m] * dp[m])
+        sdp = np.sum(d[m] * dp[m])
+        det = sdd * spp - sdp * sdp
+        if not det > tol * sdd * spp:
+            return False
+    return True
+
+
+def _full_ok(dx, dy, tol=1e-6):
+    if dx.size < 2:
+        return False
+    sxx = np.sum(dx * dx)
+    syy = np.sum(dy * dy)
+    sxy = np.sum(dx * dy)
+    return (sxx * syy - sxy * sxy) > tol * sxx * syy
+
+
+# ---------------------------------------------------------------------------
+# segment / aerofoil crossing test (rejects neighbours seen through the body)
+# ---------------------------------------------------------------------------
+
+def _crosses_body(px, py, qx, qy, wx, wy, pw, qw):
+    """Boolean per segment: does P->Q pass through the wall polygon's interior?
+
+    pw, qw: wall-vertex index of each end point, or -1.  A proper crossing of an
+    edge not incident to either end point, or a chord between two
+    non-adjacent wall vertices, counts as passing through the body.
+    """
+    nseg = px.shape[0]
+    out = np.zeros(nseg, dtype=bool)
+    if nseg == 0:
+        return out
+    nw = wx.shape[0]
+    ax, ay = wx, wy
+    bx, by = np.roll(wx, -1), np.roll(wy, -1)
+    exmin, exmax = np.minimum(ax, bx), np.maximum(ax, bx)
+    eymin, eymax = np.minimum(ay, by), np.maximum(ay, by)
+    chunk = max(1, 4_000_000 // nw)
+    eidx = np.arange(nw)
+    for s in range(0, nseg, chunk):
+        sl = slice(s, min(nseg, s + chunk))
+        Px, Py, Qx, Qy = px[sl, None], py[sl, None], qx[sl, None], qy[sl, None]
+        bb = ((np.minimum(Px, Qx) <= exmax) & (np.maximum(Px, Qx) >= exmin)
+              & (np.minimum(Py, Qy) <= eymax) & (np.maximum(Py, Qy) >= eymin))
+        if not bb.any():
+            continue
+        d1 = (bx - ax) * (Py - ay) - (by - ay) * (Px - ax)
+        d2 = (bx - ax) * (Qy - ay) - (by - ay) * (Qx - ax)
+        d3 = (Qx - Px) * (ay - Py) - (Qy - Py) * (ax - Px)
+        d4 = (Qx - Px) * (by - Py) - (Qy - Py) * (bx - Px)
+        proper = bb & (d1 * d2 < 0) & (d3 * d4 < 0)
+        incident = ((pw[sl, None] == eidx) | (pw[sl, None] == (eidx + 1) % nw)
+                    | (qw[sl, None] == eidx) | (qw[sl, None] == (eidx + 1) % nw))
+        out[sl] = (proper & ~incident).any(axis=1)
+    both = (pw >= 0) & (qw >= 0)
+    if both.any():
+        dd = np.abs(pw - qw)
+        adj = (dd == 1) | (dd == nw - 1)
+        out |= both & ~adj
+    return out
+
+
+# ---------------------------------------------------------------------------
+# builders
+# ---------------------------------------------------------------------------
+
+def _csr(rows):
+    off = np.zeros(len(rows) + 1, dtype=np.int64)
+    off[1:] = np.cumsum([len(r) for r in rows])
+    idx = np.concatenate([np.asarray(r, dtype=np.int64) for r in rows]) if rows else np.zeros(0, np.int64)
+    return off.astype(np.int32), idx.astype(np.int32)
+
+
+def _fix_stencils(x, y, flag, nx, ny, rows, cand_fn, body=None):
+    """Augment stencils (nearest-first candidates) until every sub-stencil is well posed."""
+    bad = 0
+    for p in range(x.shape[0]):
+        r = rows[p]
+        dx = x[r] - x[p]
+        dy = y[r] - y[p]
+        if flag[p] == OUTER:
+            ok = _full_ok(dx, dy)
+        else:
+            e1, e2 = _frame(x, y, flag, nx, ny, p)
+            ok = _full_ok(dx, dy) and _substencils_ok(dx, dy, flag[p] == WALL, e1, e2)
+        if ok:
+            continue
+        bad += 1
+        have = set(r)
+        for q in cand_fn(p):
+            if q in have or q == p:
+                continue
+            if body is not None:
+                wx, wy, widx = body
+                if _crosses_body(np.array([x[p]]), np.array([y[p]]), np.array([x[q]]), np.array([y[q]]),
+                                 wx, wy, np.array([widx[p]]), np.array([widx[q]]))[0]:
+                    continue
+            r = r + [int(q)]
+            have.add(q)
+            dx = x[r] - x[p]
+            dy = y[r] - y[p]
+            if flag[p] == OUTER:
+                ok = _full_ok(dx, dy)
+            else:
+                e1, e2 = _frame(x, y, flag, nx, ny, p)
+                ok = _full_ok(dx, dy) and _substencils_ok(dx, dy, flag[p] == WALL, e1, e2)
+            if ok:
+                break
+        if not ok:
+            raise RuntimeError(f"could not build a well-posed stencil at point {p}")
+        rows[p] = r
+    return rows, bad
+
+
+def naca0012_block(n_i: int = 160, n_j: int = 64) -> Cloud:
+    """Structured O-grid cloud with 3x3 index-block stencils (8 neighbours)."""
+    X, Y = _ogrid(n_i, n_j)
+    x = X.ravel().copy()
+    y = Y.ravel().copy()
+    n = n_i * n_j
+    flag = np.zeros(n, dtype=np.uint8)
+    flag[:n_i] = WALL
+    flag[-n_i:] = OUTER
+    nx = np.zeros(n)
+    ny = np.zeros(n)
+    nx[:n_i], ny[:n_i] = _wall_normals(x[:n_i], y[:n_i])
+    rows = []
+    for j in range(n_j):
+        for i in range(n_i):
+            r = []
+            for dj in (-1, 0, 1):
+                jj = j + dj
+                if jj < 0 or jj >= n_j:
+                    continue
+                for di in (-1, 0, 1):
+                    if di == 0 and dj == 0:
+                        continue
+                    r.append(jj * n_i + (i + di) % n_i)
+            rows.append(r)
+
+    from scipy.spatial import cKDTree
+    tree = cKDTree(np.stack([x, y], axis=1))
+
+    def cand(p):
+        # nearest points first (the wake line behind the trailing edge needs
+        # more than the 5x5 index block to close its downstream sub-stencil)
+        _, c = tree.query([x[p], y[p]], k=min(n, 64))
+        return np.asarray(c)[1:]
+
+    widx = np.full(n, -1)
+    widx[:n_i] = np.arange(n_i)
+    rows, bad = _fix_stencils(x, y, flag, nx, ny, rows, cand, body=(x[:n_i], y[:n_i], widx))
+    off, idx = _csr(rows)
+    return Cloud(x, y, flag, nx, ny, off, idx,
+                 dict(kind="block", n_i=n_i, n_j=n_j, augmented=bad))
+
+
+def naca0012_jittered(n_i: int = 640, n_j: int = 256, jitter: float = 0.15,
+                      remove_frac: float = 0.10, seed: int = BASE_SEED + 2,
+                      radius_factor: float = 2.5, k_min: int = 8, k_max: int = 20) -> Cloud:
+    """Jittered O-grid cloud with random interior removal and radius/kNN stencils."""
+    from scipy.spatial import cKDTree
+
+    rng = np.random.default_rng(seed)
+    X, Y = _ogrid(n_i, n_j)
+    hxi, heta, exi, eeta = _local_spacing(X, Y)
+    a = rng.uniform(-jitter, jitter, size=X.shape)
+    b = rng.uniform(-jitter, jitter, size=X.shape)
+    Xj = X + a * hxi * exi[0] + b * heta * eeta[0]
+    Yj = Y + a * hxi * exi[1] + b * heta * eeta[1]
+    Xj[0], Yj[0] = X[0], Y[0]
+    Xj[-1], Yj[-1] = X[-1], Y[-1]
+    x = Xj.ravel()
+    y = Yj.ravel()
+    h = np.maximum(hxi, heta).ravel()
+    n0 = n_i * n_j
+    flag = np.zeros(n0, dtype=np.uint8)
+    flag[:n_i] = WALL
+    flag[-n_i:] = OUTER
+    interior = np.flatnonzero(flag == INTERIOR)
+    n_rm = int(math.floor(remove_frac * interior.size))
+    rm = rng.choice(interior, size=n_rm, replace=False)
+    keep = np.ones(n0, dtype=bool)
+    keep[rm] = False
+    x, y, flag, h = x[keep], y[keep], flag[keep], h[keep]
+    n = x.shape[0]
+    nx = np.zeros(n)
+    ny = np.zeros(n)
+    nx[:n_i], ny[:n_i] = _wall_normals(x[:n_i], y[:n_i])
+    widx = np.full(n, -1)
+    widx[:n_i] = np.arange(n_i)
+    wx, wy = x[:n_i].copy(), y[:n_i].copy()
+
+    tree = cKDTree(np.stack([x, y], axis=1))
+    kq = 48
+    dist, nb = tree.query(np.stack([x, y], axis=1), k=kq + 1)
+    dist, nb = dist[:, 1:], nb[:, 1:]
+    # reject neighbours seen through the aerofoil (only segments near the body can)
+    P = np.repeat(np.arange(n), kq)
+    Q = nb.ravel()
+    near = ((np.minimum(x[P], x[Q]) <= 1.02) & (np.maximum(x[P], x[Q]) >= -0.02)
+            & (np.minimum(y[P], y[Q]) <= 0.07) & (np.maximum(y[P], y[Q]) >= -0.07))
+    cross = np.zeros(P.shape[0], dtype=bool)
+    ii = np.flatnonzero(near)
+    cross[ii] = _crosses_body(x[P[ii]], y[P[ii]], x[Q[ii]], y[Q[ii]], wx, wy, widx[P[ii]], widx[Q[ii]])
+    cross = cross.reshape(n, kq)
+    valid = ~cross
+    radius = radius_factor * h
+    rows = []
+    for p in range(n):
+        cand = nb[p][valid[p]]
+        dcand = dist[p][valid[p]]
+        m = int(np.sum(dcand <= radius[p]))
+        m = min(max(m, k_min), k_max, cand.size)
+        rows.append([int(q) for q in cand[:m]])
+    cand_lists = [nb[p][valid[p]] for p in range(n)]
+    rows, bad = _fix_stencils(x, y, flag, nx, ny, rows, lambda p: cand_lists[p])
+    off, idx = _csr(rows)
+    return Cloud(x, y, flag, nx, ny, off, idx,
+                 dict(kind="jittered", n_i=n_i, n_j=n_j, jitter=jitter, remove_frac=remove_frac,
+                      seed=seed, removed=n_rm, augmented=bad))
+
+
+def cartesian_box(n: int = 7, m: int = 7, jitter: float = 0.2, seed: int = BASE_SEED + 7,
+                  wall_bottom: bool = False) -> Cloud:
+    """Small jittered Cartesian patch; the frame is outer (or a flat wall at the bottom).
+
+    Used for tiny oracle checks (dense LU-SGS on ~50 points, mirror symmetry)."""
+    rng = np.random.default_rng(seed)
+    I, J = np.meshgrid(np.arange(n), np.arange(m))
+    X = I.astype(np.float64) / (n - 1)
+    Y = J.astype(np.float64) / (m - 1)
+    inner = (I > 0) & (I < n - 1) & (J > 0) & (J < m - 1)
+    X = X + np.where(inner, rng.uniform(-jitter, jitter, X.shape) / (n - 1), 0.0)
+    Y = Y + np.where(inner, rng.uniform(-jitter, jitter, Y.shape) / (m - 1), 0.0)
+    x, y = X.ravel(), Y.ravel()
+    N = x.shape[0]
+    flag = np.where(inner.ravel(), INTERIOR, OUTER).astype(np.uint8)
+    nx = np.zeros(N)
+    ny = np.zeros(N)
+    if wall_bottom:
+        wb = (J.ravel() == 0) & (I.ravel() > 0) & (I.ravel() < n - 1)
+        flag[wb] = WALL
+        ny[wb] = 1.0
+    from scipy.spatial import cKDTree
+    tree = cKDTree(np.stack([x, y], 1))
+    d, nb = tree.query(np.stack([x, y], 1), k=min(N, 13))
+    rows = [[int(q) for q in nb[p, 1:9]] for p in range(N)]
+    cand = [nb[p, 1:] for p in range(N)]
+    rows, bad = _fix_stencils(x, y, flag, nx, ny, rows, lambda p: cand[p])
+    off, idx = _csr(rows)
+    return Cloud(x, y, flag, nx, ny, off, idx, dict(kind="box", n=n, m=m, seed=seed, augmented=bad))
+
+
+# Workloads of the benchmark and the parity tests (sizes and flow conditions).
+WORKLOADS = {
+    "naca0012_160x64": dict(builder="block", n_i=160, n_j=64, mach=0.63, aoa_deg=2.0, cfl=100.0, iters=300),
+    "naca0012_640x256_jit": dict(builder="jittered", n_i=640, n_j=256, mach=0.85, aoa_deg=1.0, cfl=100.0,
+                                 iters=2000, seed=BASE_SEED + 2),
+    "naca0012_2560x2048_jit": dict(builder="jittered", n_i=2560, n_j=2048, mach=0.8, aoa_deg=1.25, cfl=100.0,
+                                   remove_frac=0.0, seed=BASE_SEED + 3),
+}
+
+
+def build_workload(name: str) -> Cloud:
+    w = WORKLOADS[name]
+    if w["builder"] == "block":
+        return naca0012_block(w["n_i"], w["n_j"])
+    return naca0012_jittered(w["n_i"], w["n_j"], remove_frac=w.get("remove_frac", 0.10), seed=w["seed"])
