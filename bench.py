@@ -1,0 +1,281 @@
+#!/usr/bin/env python
+"""Throughput of the implicit q-LSKUM hot path on GB300, in point-iterations/s.
+
+One step = one pseudo-time iteration (q-derivatives with 3 inner iterations,
+second-order split-flux residual, residual norm, forward and backward LU-SGS
+sweeps with exact-AD Jacobian products, state update) of the plain FP64 solver
+on the jittered NACA 0012 cloud of 640x256 nodes with 10% of the interior
+removed (147,584 points, 8-20 neighbours), M = 0.85, AoA = 1 deg, CFL 100.
+The solve starts with START first-order iterations (untimed set-up, before the
+warm-up); every timed step is a full second-order iteration.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+--impl reference times the FP64 CPU oracle on the host cores instead, on a
+bounded number of iterations of the same workload.  Under torchrun (N > 1)
+every rank runs an independent replica (the single-cloud solve has no
+data-parallel split; see the design notes), value = total point-iterations
+of all ranks / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "naca0012_640x256_jit"
+METRIC = "point-iter/s; wall time to 1e-8 residual drop, plain FP64 vs FP32+warm start"
+UNIT = "point-iter/s"
+L2_BYTES = 129 * 2**20
+# FP64 peak derived from unit counts and clock: 152 SMs x 2 DFMA/clk/SM x 2 flop
+# x 2070 MHz = 1.259 TFLOP/s (a DFMA-chain probe measured 1.196 at ~2.0 GHz).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# FP64 flops (DFMA = 2) the residual kernel executes per neighbour slot that
+# joins a split sub-stencil, counted by ncu on this workload
+# (smsp__sass_thread_inst_executed_op_{dfma,dmul,dadd}_pred_on).
+RES_FLOPS_PER_SLOT = 1150.0
+START = 50  # first-order start-up iterations before warm-up and timing
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.p = None
+        self.gpu_id = gpu_id
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu_id}", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p is not None:
+            time.sleep(0.25)
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                self.out = ""
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _gpu_id(torch, dev):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else f"GPU-{u}"
+    except Exception:
+        return str(dev)
+
+
+def cpu_baseline(cloud, iters, warm=0):
+    """The FP64 oracle, as it stands, on one host core: `iters` iterations."""
+    import oracle as O
+    o = O.Oracle(cloud)
+    U = o.initial_state(0.85, 1.0)
+    r0 = o.run(U, 1 + warm, cfl=100.0, K=3, first_order=1)
+    t0 = time.perf_counter()
+    r = o.run(r0["U"], iters, cfl=100.0, K=3, n0=1 + warm, hist0=r0["hist0"])
+    dt = time.perf_counter() - t0
+    return cloud.n * r["done"] / dt, dt, r["done"]
+
+
+def run_reference(args, rank):
+    from paper_2406_07441_gb300 import cloudgen as cg
+    if rank != 0:
+        return
+    cloud = cg.build_workload(WORKLOAD)
+    steps = max(1, min(args.steps, 10))
+    warm = min(args.warmup, 1)
+    val, dt, done = cpu_baseline(cloud, steps, warm)
+    sample = (f"{done} second-order FP64 oracle iterations on the full {cloud.n}-point cloud after "
+              f"1 first-order start-up and {warm} warm-up iterations")
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": done,
+            "warmup": warm, "ms_per_step": dt * 1e3 / done, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "points": cloud.n, "mach": 0.85, "aoa_deg": 1.0, "cfl": 100.0,
+                       "inner_iters": 3, "jvp": "exact-AD", "order": "second (after start-up)"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_2406_07441_gb300 import cloudgen as cg
+    from paper_2406_07441_gb300 import lskum
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    cloud = cg.build_workload(WORKLOAD)
+    n = cloud.n
+    s = lskum.Solver(cloud, 0.85, 1.0, cfl=100.0, inner_iters=3, jvp=lskum.JVP_EXACT, first_order_iters=START)
+    info = s.info()
+    nslots = int(np.count_nonzero(_memberships(cloud)))
+    # first-order start-up, then warm-up iterations (untimed)
+    assert s.run(START + args.warmup) == START + args.warmup
+    stream = torch.cuda.ExternalStream(s.stream())
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(_gpu_id(torch, local_rank)) as clk:
+        e0.record(stream)
+        s.enqueue(args.steps)
+        e1.record(stream)
+        done = s.wait()
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    if done != args.steps:
+        raise RuntimeError(f"only {done} of {args.steps} iterations ran")
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * n * args.steps / (ms_max / 1e3)
+
+    # live per-phase timing (CUDA events on the library stream) for the roofline
+    phases = s.time_phases(5)
+    res_ms = phases["residual"]
+    achieved = RES_FLOPS_PER_SLOT * nslots / (res_ms / 1e3) / 1e12
+
+    # end to end through the C-ABI with host buffers: state in (H2D), one
+    # iteration, state out (D2H) every step
+    e2e_steps = min(args.steps, 20)
+    U = s.field(lskum.FIELD_U)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        s.set_conserved(U)
+        s.run(1)
+        U = s.field(lskum.FIELD_U)
+    torch.cuda.synchronize()
+    e2e_dt = time.perf_counter() - t0
+    e2e = {"value": n * e2e_steps / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": int(U.nbytes),
+           "d2h_bytes_per_step": int(U.nbytes) + 8}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if world == 1:
+        cv, cdt, cdone = cpu_baseline(cloud, 10)
+        cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{cdone} FP64 oracle iterations on the full {n}-point cloud (single thread)"}
+    ws = _working_set_bytes(cloud)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "points": n, "neighbour_slots": int(cloud.nnz),
+                   "mach": 0.85, "aoa_deg": 1.0, "cfl": 100.0, "inner_iters": 3, "jvp": "exact-AD",
+                   "order": f"second (timed steps follow {START} untimed first-order start-up iterations)",
+                   "colours": info["n_colours"], "parallelism": "replicas" if world > 1 else "single",
+                   "l2": f"inputs larger than L2: device working set {ws / 2**20:.0f} MiB > 129 MiB L2"},
+        "roofline": {"bound": "alu", "kernel": "k_residual", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz",
+                     "launch_ms": res_ms, "phase_ms": phases},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": info["launches_per_iter"] * args.steps,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def _memberships(cloud):
+    """Neighbour slots that join a split sub-stencil of a wall or interior point."""
+    import numpy as np
+    deg = np.diff(cloud.nbr_off)
+    owner = np.repeat(np.arange(cloud.n), deg)
+    dx = cloud.x[cloud.nbr_idx] - cloud.x[owner]
+    dy = cloud.y[cloud.nbr_idx] - cloud.y[owner]
+    wall = cloud.flag[owner] == 1
+    a = np.where(wall, dx * cloud.ny[owner] - dy * cloud.nx[owner], dx)
+    b = np.where(wall, dx * cloud.nx[owner] + dy * cloud.ny[owner], dy)
+    active = cloud.flag[owner] != 2
+    return active & ((a != 0) | ((b > 0) | ((b < 0) & ~wall)))
+
+
+def _working_set_bytes(cloud):
+    n, nnz = cloud.n, cloud.nnz
+    per_slot = 4 + 1 + 6 * 8
+    per_point = 8 * (2 * (4 + 4 + 20) + 4 * 4 + 4 + 1 + 4 + 4 + 13)
+    return nnz * per_slot + n * per_point
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local_rank = _env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        run_reference(args, rank)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

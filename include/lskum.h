@@ -1,0 +1,199 @@
+/*
+ * liblskum: the per-iteration hot path of the implicit q-LSKUM 2D Euler solver
+ * with the modified (exact-AD) LU-SGS scheme, on one GB300 GPU.
+ *
+ * The calls follow the statement of the problem in the paper (Verma, Mamidi,
+ * Nemili, "GPU Accelerated Implicit Kinetic Meshfree Method based on Modified
+ * LU-SGS", 2024): a point cloud with neighbour lists and point types (Sec. 4,
+ * Alg. 1-3: wall, interior and outer points; Alg. 5: connectivity) and the
+ * free-stream Mach number and angle of attack (Sec. 5) go in; the flow state
+ * (Sec. 5), the density-residual history (Sec. 5.1) and the lift and drag
+ * coefficients (Sec. 5.2, Table 5) come out.
+ *
+ * Conventions shared by every call:
+ *  - All pointers are HOST pointers unless a name ends in _dev.
+ *  - Inputs are copied; the caller keeps ownership of its arrays.
+ *  - Point arrays are in the caller's point order; the library's internal
+ *    (colour-sorted) order never leaks out.
+ *  - Every call returns a status; no call aborts the process.  After a
+ *    non-OK status the context stays valid for lskum_get_* (last good state),
+ *    lskum_last_error and lskum_destroy.
+ *  - A context is bound to the CUDA device current at lskum_create and to the
+ *    stream given there (NULL = the legacy default stream).  Calls on one
+ *    context must not overlap in time; different contexts are independent.
+ */
+#ifndef LSKUM_H
+#define LSKUM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lskum_ctx lskum_ctx; /* opaque, owned by the library */
+
+typedef enum {
+    LSKUM_OK = 0,
+    LSKUM_ERR_ARG = -1,         /* bad argument (NULL, size, flag value, option) */
+    LSKUM_ERR_STENCIL = -2,     /* a point's (split) stencil is degenerate */
+    LSKUM_ERR_NONPOSITIVE = -3, /* an update produced rho <= 0, p <= 0 or a non-finite value */
+    LSKUM_ERR_DIVERGED = -4,    /* the residual norm became non-finite */
+    LSKUM_ERR_CUDA = -5,        /* a CUDA runtime call failed */
+    LSKUM_ERR_TIMEOUT = -6,     /* a bounded device wait gave up */
+    LSKUM_ERR_OOM = -7          /* device or host allocation failed */
+} lskum_status;
+
+/* Point types (Alg. 2, 4): */
+enum { LSKUM_INTERIOR = 0, LSKUM_WALL = 1, LSKUM_OUTER = 2 };
+
+/* Jacobian-vector products in the LU-SGS sweeps: */
+enum {
+    LSKUM_JVP_EXACT = 0,    /* forward-mode derivative of the split fluxes (Sec. 3, Listing 3) */
+    LSKUM_JVP_INCREMENT = 1 /* split-flux increments, Eq. 28 */
+};
+
+/* Fields readable with lskum_get_field (caller order; [N][4] row-major unless noted): */
+enum {
+    LSKUM_FIELD_U = 0,   /* conserved state [rho, rho u, rho v, rho e] (Eq. 2) */
+    LSKUM_FIELD_Q = 1,   /* q-variables (Eq. 14) of the current state */
+    LSKUM_FIELD_QX = 2,  /* x-derivatives of q of the last iteration (Eq. 16) */
+    LSKUM_FIELD_QY = 3,  /* y-derivatives of q of the last iteration */
+    LSKUM_FIELD_R = 4,   /* flux residual of the last iteration (Eq. 11-12, 19) */
+    LSKUM_FIELD_D = 5,   /* scalar diagonal D of the last iteration, [N] (Eq. 26, 33-34) */
+    LSKUM_FIELD_DUS = 6, /* forward-sweep increment dU* of the last iteration (Eq. 27) */
+    LSKUM_FIELD_DU = 7   /* backward-sweep increment dU of the last iteration (Eq. 27) */
+};
+
+/*
+ * The point cloud (all host pointers, copied at create):
+ *   n_points  N >= 1
+ *   x, y      f64[N] coordinates
+ *   flag      u8[N]  LSKUM_INTERIOR / LSKUM_WALL / LSKUM_OUTER
+ *   nx, ny    f64[N] unit wall normals pointing into the fluid (read at wall
+ *             points only); must not be NULL when the cloud has wall points
+ *   nbr_off   i32[N+1] CSR offsets, nbr_off[0] = 0, non-decreasing
+ *   nbr_idx   i32[nbr_off[N]] neighbour indices: 0-based, < N, no self, no
+ *             duplicates within a row.  The order within a row is the
+ *             summation order of every neighbour sum.
+ */
+typedef struct {
+    int32_t n_points;
+    const double *x, *y;
+    const uint8_t *flag;
+    const double *nx, *ny;
+    const int32_t *nbr_off, *nbr_idx;
+} lskum_cloud;
+
+/*
+ * Solver options:
+ *   mach, aoa_deg    free stream (rho = 1, p = 1/gamma, gamma = 1.4)
+ *   cfl              local time-step factor (> 0)
+ *   cfl_ramp_iters   if > 0, the CFL of iteration n (1-based) is
+ *                    cfl * min(1, n / cfl_ramp_iters)
+ *   inner_iters      K >= 0 defect-correction inner iterations of the
+ *                    q-derivatives (Eq. 16)
+ *   jvp              LSKUM_JVP_EXACT or LSKUM_JVP_INCREMENT
+ *   precision        0 = FP64 everywhere (the only value accepted so far)
+ *   first_order_iters  iterations n <= first_order_iters (counted since the
+ *                    last set_state / create) use the first-order residual
+ *                    (q~ = q: no defect correction); a start-up aid, >= 0
+ */
+typedef struct {
+    double mach, aoa_deg, cfl, cfl_ramp_iters;
+    int32_t inner_iters, jvp, precision, first_order_iters;
+} lskum_opts;
+
+/*
+ * Validate and copy the cloud, colour it (Alg. 5 on the symmetrised
+ * neighbour graph), order points by colour (the LU-SGS sweep order, Alg. 6-7),
+ * precompute stencil geometry, allocate device memory and set the free-stream
+ * state (normal momentum removed at wall points).
+ *   cloud, opts   host structures (not kept)
+ *   cuda_stream   a cudaStream_t of the current device, or NULL
+ *   out           receives the context; set to NULL on failure
+ * Errors: LSKUM_ERR_ARG (bad input, with the offending point in
+ * lskum_last_error(NULL)), LSKUM_ERR_STENCIL (a degenerate split sub-stencil),
+ * LSKUM_ERR_OOM, LSKUM_ERR_CUDA.
+ */
+lskum_status lskum_create(const lskum_cloud *cloud, const lskum_opts *opts, void *cuda_stream,
+                          lskum_ctx **out);
+
+/* Replace the state by primitive fields (f64[N] each, caller order); the wall
+ * projection is applied and the residual history is cleared.
+ * Errors: LSKUM_ERR_ARG (NULL), LSKUM_ERR_NONPOSITIVE (rho or p <= 0 or not
+ * finite; state unchanged), LSKUM_ERR_CUDA. */
+lskum_status lskum_set_state(lskum_ctx *ctx, const double *rho, const double *u, const double *v,
+                             const double *p);
+
+/* Replace the state by conserved variables U f64[N][4] (caller order), keeping
+ * the residual history (resume from a checkpoint).  Same errors as above. */
+lskum_status lskum_set_conserved(lskum_ctx *ctx, const double *U);
+
+/*
+ * Run up to max_iters pseudo-time iterations of Alg. 1 on the device:
+ * q-derivatives (K inner iterations), flux residual and diagonal, density
+ * residual norm, forward and backward sweeps, state update.  After iteration n
+ * the run stops early if norm_n / norm_1 <= target_drop (norm_1 = the first
+ * norm since the last set_state / create); target_drop <= 0 runs all
+ * iterations.  iters_done (may be NULL) receives the number of iterations run.
+ * Errors: LSKUM_ERR_NONPOSITIVE (an update produced a non-physical state; the
+ * state of the last good iteration is kept), LSKUM_ERR_DIVERGED,
+ * LSKUM_ERR_ARG, LSKUM_ERR_CUDA.
+ */
+lskum_status lskum_run(lskum_ctx *ctx, int32_t max_iters, double target_drop, int32_t *iters_done);
+
+/* The two halves of lskum_run.  lskum_enqueue validates, then enqueues
+ * max_iters iterations (one CUDA graph launch each) on the context's stream
+ * and returns at once; lskum_wait blocks until they finish and reports the
+ * status and the iterations run exactly as lskum_run does.  Between the two,
+ * every other call on the context except lskum_stream returns LSKUM_ERR_ARG. */
+lskum_status lskum_enqueue(lskum_ctx *ctx, int32_t max_iters, double target_drop);
+lskum_status lskum_wait(lskum_ctx *ctx, int32_t *iters_done);
+
+/* The context's internal cudaStream_t (work is enqueued there; the caller's
+ * stream given at create is ordered before and after each call). */
+void *lskum_stream(lskum_ctx *ctx);
+
+/* Primitive state, f64[N] each, caller order. */
+lskum_status lskum_get_state(lskum_ctx *ctx, double *rho, double *u, double *v, double *p);
+
+/* One field (LSKUM_FIELD_*), caller order, into a caller buffer of N*4 (N for D) doubles. */
+lskum_status lskum_get_field(lskum_ctx *ctx, int32_t field, double *out);
+
+/* Density-residual norms of every iteration since the last set_state/create
+ * (absolute, not divided by norm_1).  Copies min(cap, count) entries; *n gets
+ * the count. */
+lskum_status lskum_get_residuals(lskum_ctx *ctx, double *hist, int32_t cap, int32_t *n);
+
+/* Lift and drag coefficients of the current state (wall pressure integrated
+ * over the wall polygon, wall points taken in caller index order). */
+lskum_status lskum_get_forces(lskum_ctx *ctx, double *cl, double *cd);
+
+/* The colouring and sweep order: colour i32[N] (1-based, caller order),
+ * order i32[N] (caller index at each sweep position), n_colours. Any may be NULL. */
+lskum_status lskum_get_order(lskum_ctx *ctx, int32_t *colour, int32_t *order, int32_t *n_colours);
+
+/* Measure: run `reps` iterations with each phase launched directly (not as a
+ * graph) between CUDA events on the context's stream; ms[6] receives the mean
+ * device time per iteration of the phases 0 q-derivatives (all K+1 passes),
+ * 1 residual + diagonal, 2 norm, 3 forward sweep (all levels), 4 backward
+ * sweep, 5 update.  The iterations are real: the state advances by reps
+ * iterations and the history grows.  Errors as lskum_run. */
+lskum_status lskum_time_phases(lskum_ctx *ctx, int32_t reps, double *ms);
+
+/* Number of points, of colours and of kernel launches one iteration makes. */
+lskum_status lskum_get_info(lskum_ctx *ctx, int32_t *n_points, int32_t *n_colours, int32_t *launches_per_iter);
+
+/* Message of the last failure of ctx (or of the last failed create when ctx
+ * is NULL); never NULL; valid until the next call on the same context. */
+const char *lskum_last_error(const lskum_ctx *ctx);
+
+/* Free everything; NULL is allowed. */
+void lskum_destroy(lskum_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSKUM_H */

@@ -67,7 +67,7 @@ def lib():
         L.o_q_from_state.argtypes = [P(_Cloud), vp, vp]
         L.o_cfl_at.argtypes = [d, d, i32]
         L.o_cfl_at.restype = d
-        L.o_run.argtypes = [P(_Cloud), vp, vp, d, d, i32, i32, i32, d, i32,
+        L.o_run.argtypes = [P(_Cloud), vp, vp, d, d, i32, i32, i32, i32, d, i32,
                             vp, vp, vp, vp, vp, vp, vp, vp, vp, P(d), P(i32)]
         L.o_run.restype = i32
         _lib = L
@@ -236,7 +236,7 @@ class Oracle:
         lib().o_forces(C.byref(self.c), _p(U), mach, aoa_deg, C.byref(cl), C.byref(cd))
         return cl.value, cd.value
 
-    def run(self, U, iters, cfl=100.0, K=3, jvp=JVP_EXACT, target=0.0, ramp=0.0, n0=0, hist0=0.0):
+    def run(self, U, iters, cfl=100.0, K=3, jvp=JVP_EXACT, target=0.0, ramp=0.0, n0=0, hist0=0.0, first_order=0):
         """Alg. 1 for up to `iters` iterations.  Returns a dict with the new state,
         the norm history and the last iteration's intermediates."""
         n = self.n
@@ -247,6 +247,6 @@ class Oracle:
         h0 = C.c_double(hist0)
         done = C.c_int32(0)
         st = lib().o_run(C.byref(self.c), _p(self.order), _p(self.rank), float(cfl), float(ramp), int(K), int(jvp),
-                         int(iters), float(target), int(n0), _p(U), _p(w["q"]), _p(w["qx"]), _p(w["qy"]),
+                         int(first_order), int(iters), float(target), int(n0), _p(U), _p(w["q"]), _p(w["qx"]), _p(w["qy"]),
                          _p(w["R"]), _p(D), _p(w["dUs"]), _p(w["dU"]), _p(hist), C.byref(h0), C.byref(done))
         return dict(U=U, hist=hist[:done.value], hist0=h0.value, done=done.value, status=int(st), D=D, **w)

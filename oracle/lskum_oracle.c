@@ -43,6 +43,11 @@
  *   R10 Cl, Cd: pressure integrated over the wall polygon (wall points in
  *       index order), each wall point carrying the sum of its two rotated half
  *       edges as n ds.
+ *   R11 Start-up: the first `first_order` iterations (an option, 0 = none)
+ *       use the first-order residual (q~ = q, no defect correction); the
+ *       impulsive free-stream start otherwise drives the unlimited second-order
+ *       reconstruction out of the Maxwellian range (q~_4 >= 0) at the
+ *       leading edge of jittered clouds.
  */
 #include <math.h>
 #include <stdint.h>
@@ -695,7 +700,8 @@ double o_cfl_at(double cfl, double ramp, int32_t n)
 
 /*
  * Run up to `iters` iterations from the state U (in/out, [4N]).  Iteration n
- * computes q-derivatives, R(U^{n-1}) and its norm hist[n-1], sweeps, and
+ * (counted from n0 + 1) computes q-derivatives, R(U^{n-1}) (first order while
+ * n <= first_order) and its norm hist[n-1], sweeps, and
  * updates to U^n; it stops after iteration n when hist[n-1]/hist0 <= target
  * (hist0 = the first norm of this call unless *hist0 > 0 is passed in).
  * Returns 0, or -(1 + point) on a non-physical update.  *done = iterations run.
@@ -704,24 +710,30 @@ double o_cfl_at(double cfl, double ramp, int32_t n)
  *   q, qx, qy, R, D[N], dUs, dU.
  */
 int32_t o_run(const o_cloud *c, const int32_t *order, const int32_t *rank,
-              double cfl, double ramp, int32_t K, int32_t jvp,
+              double cfl, double ramp, int32_t K, int32_t jvp, int32_t first_order,
               int32_t iters, double target, int32_t n0,
               double *U, double *q, double *qx, double *qy, double *R, double *D,
               double *dUs, double *dU, double *hist, double *hist0, int32_t *done)
 {
     *done = 0;
+    double *zero = calloc(4 * (size_t)c->n, sizeof(double));
     o_q_from_state(c, U, q);
     for (int32_t it = 0; it < iters; it++) {
         int32_t n = n0 + it + 1;
         o_q_gradients(c, q, K, qx, qy);
-        o_residual(c, q, qx, qy, U, o_cfl_at(cfl, ramp, n), R, D);
+        if (n <= first_order) o_residual(c, q, zero, zero, U, o_cfl_at(cfl, ramp, n), R, D);
+        else o_residual(c, q, qx, qy, U, o_cfl_at(cfl, ramp, n), R, D);
         hist[it] = o_residual_norm(c, R);
         if (!(*hist0 > 0.0)) *hist0 = hist[it];
         o_sweeps(c, order, rank, U, R, D, jvp, dUs, dU);
         int32_t bad = o_update(c, U, dU, q);
         *done = it + 1;
-        if (bad >= 0) return -(1 + bad);
+        if (bad >= 0) {
+            free(zero);
+            return -(1 + bad);
+        }
         if (hist[it] / *hist0 <= target) break;
     }
+    free(zero);
     return 0;
 }

@@ -1,0 +1,933 @@
+// Host side of liblskum: input validation, the colouring that fixes the
+// LU-SGS sweep order (Alg. 5), the internal point order and neighbour layout,
+// per-slot least-squares weights, device memory, one CUDA graph per
+// iteration parity, and the C-ABI of include/lskum.h.
+#include "lskum_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/lskum.h"
+
+using namespace lskum;
+
+namespace {
+
+thread_local std::string g_create_error = "no error";
+
+struct Arena {
+    std::vector<void *> ptrs;
+    cudaError_t err = cudaSuccess;
+    template <class T>
+    T *alloc(size_t count)
+    {
+        void *p = nullptr;
+        if (err != cudaSuccess) return nullptr;
+        err = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
+        if (err != cudaSuccess) return nullptr;
+        ptrs.push_back(p);
+        return static_cast<T *>(p);
+    }
+    void release()
+    {
+        for (void *p : ptrs) cudaFree(p);
+        ptrs.clear();
+    }
+};
+
+}  // namespace
+
+struct lskum_ctx {
+    int device = 0;
+    int32_t n = 0, ld = 0;
+    lskum_opts opts{};
+    // host copies (caller order)
+    std::vector<double> x, y, nx, ny;
+    std::vector<uint8_t> flag;
+    // order: internal position -> caller index, and the inverse
+    std::vector<int32_t> perm, inv;
+    std::vector<int32_t> colour;        // caller order, 1-based
+    std::vector<int32_t> canon_order;   // stable colour order of caller indices
+    int32_t n_colours = 0;
+    std::vector<int32_t> lvl_beg, lvl_act_end, lvl_end;
+    // device
+    Arena arena;
+    Dev dev{};
+    Launch launch{};
+    Ctrl *ctrl = nullptr;
+    double *hist = nullptr;
+    int32_t hist_cap = 0;
+    cudaStream_t stream = nullptr;      // internal, capture-capable
+    cudaStream_t user_stream = nullptr;
+    cudaEvent_t ev = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    double *pinned = nullptr;           // 4 * ld doubles of page-locked staging for state copies
+    int launches_per_iter = 0;
+    int cur = 0;                        // state set holding the current state
+    int32_t it_base = 0;                // ctrl->it at the start of the pending enqueue
+    int cur_base = 0;
+    bool pending = false;
+    std::string err = "no error";
+};
+
+namespace {
+
+lskum_status fail(lskum_ctx *c, lskum_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    else g_create_error = buf;
+    return s;
+}
+
+lskum_status cuda_fail(lskum_ctx *c, cudaError_t e, const char *what)
+{
+    return fail(c, e == cudaErrorMemoryAllocation ? LSKUM_ERR_OOM : LSKUM_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+// Greedy colouring of Alg. 5 on the symmetrised neighbour graph: each point's
+// own stencil (given order) followed by the points that list it but are not
+// in its stencil (ascending).  Visiting points in index order, every still
+// uncoloured point (the visited one first, then its neighbours) receives the
+// smallest colour > 0 not used by any of its neighbours.
+int32_t colour_points(int32_t n, const int32_t *off, const int32_t *idx, std::vector<int32_t> &col)
+{
+    std::vector<int32_t> rcnt(n + 1, 0);
+    auto listed_by = [&](int32_t q, int32_t p) {  // is p in stencil(q)?
+        for (int32_t f = off[q]; f < off[q + 1]; f++)
+            if (idx[f] == p) return true;
+        return false;
+    };
+    for (int32_t p = 0; p < n; p++)
+        for (int32_t e = off[p]; e < off[p + 1]; e++)
+            if (!listed_by(idx[e], p)) rcnt[idx[e] + 1]++;
+    for (int32_t p = 0; p < n; p++) rcnt[p + 1] += rcnt[p];
+    std::vector<int32_t> rev(std::max<int32_t>(rcnt[n], 1)), fill(n, 0);
+    for (int32_t p = 0; p < n; p++)
+        for (int32_t e = off[p]; e < off[p + 1]; e++) {
+            const int32_t q = idx[e];
+            if (!listed_by(q, p)) rev[rcnt[q] + fill[q]++] = p;
+        }
+    col.assign(n, 0);
+    std::vector<int32_t> seen;  // seen[colour] == stamp when used by a neighbour
+    int32_t stamp = 0;
+    auto smallest = [&](int32_t p) {
+        stamp++;
+        auto mark = [&](int32_t q) {
+            const int32_t cq = col[q];
+            if (cq >= (int32_t)seen.size()) seen.resize(cq + 1, 0);
+            seen[cq] = stamp;
+        };
+        for (int32_t f = off[p]; f < off[p + 1]; f++) mark(idx[f]);
+        for (int32_t f = rcnt[p]; f < rcnt[p + 1]; f++) mark(rev[f]);
+        int32_t k = 1;
+        while (k < (int32_t)seen.size() && seen[k] == stamp) k++;
+        return k;
+    };
+    if (n > 0) col[0] = 1;
+    for (int32_t i = 0; i < n; i++) {
+        if (col[i] == 0) col[i] = smallest(i);
+        for (int32_t f = off[i]; f < off[i + 1]; f++)
+            if (col[idx[f]] == 0) col[idx[f]] = smallest(idx[f]);
+        for (int32_t f = rcnt[i]; f < rcnt[i + 1]; f++)
+            if (col[rev[f]] == 0) col[rev[f]] = smallest(rev[f]);
+    }
+    int32_t nc = 0;
+    for (int32_t p = 0; p < n; p++) nc = std::max(nc, col[p]);
+    return nc;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lskum_last_error(const lskum_ctx *ctx)
+{
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+// Host-side arrays of the internal layout, built before any device call.
+struct HostPrep {
+    std::vector<int32_t> slice_off, deg, enb;
+    std::vector<uint8_t> emb, fl_i;
+    std::vector<double> edx, edy, ew1, ew2, egx, egy, geo_i, wnx, wny;
+};
+static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &hp);
+static lskum_status upload(lskum_ctx *c, HostPrep &hp);
+
+lskum_status lskum_create(const lskum_cloud *cl, const lskum_opts *opts, void *cuda_stream, lskum_ctx **out)
+{
+    if (!out) return fail(nullptr, LSKUM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!cl || !opts) return fail(nullptr, LSKUM_ERR_ARG, "cloud or opts is NULL");
+    const int32_t n = cl->n_points;
+    if (n < 1) return fail(nullptr, LSKUM_ERR_ARG, "n_points = %d < 1", n);
+    if (!cl->x || !cl->y || !cl->flag || !cl->nbr_off || !cl->nbr_idx)
+        return fail(nullptr, LSKUM_ERR_ARG, "a cloud array is NULL");
+    if (!(opts->cfl > 0.0) || !std::isfinite(opts->cfl) || !std::isfinite(opts->mach) ||
+        !std::isfinite(opts->aoa_deg) || !(opts->cfl_ramp_iters >= 0.0) || opts->inner_iters < 0 ||
+        opts->inner_iters > 64 || (opts->jvp != LSKUM_JVP_EXACT && opts->jvp != LSKUM_JVP_INCREMENT) ||
+        opts->precision != 0 || opts->first_order_iters < 0)
+        return fail(nullptr, LSKUM_ERR_ARG, "invalid option value");
+    const int32_t *off = cl->nbr_off, *idx = cl->nbr_idx;
+    if (off[0] != 0) return fail(nullptr, LSKUM_ERR_ARG, "nbr_off[0] != 0");
+    bool has_wall = false;
+    for (int32_t p = 0; p < n; p++) {
+        if (off[p + 1] < off[p]) return fail(nullptr, LSKUM_ERR_ARG, "nbr_off decreases at point %d", p);
+        if (cl->flag[p] > LSKUM_OUTER) return fail(nullptr, LSKUM_ERR_ARG, "bad flag at point %d", p);
+        if (!std::isfinite(cl->x[p]) || !std::isfinite(cl->y[p]))
+            return fail(nullptr, LSKUM_ERR_ARG, "non-finite coordinate at point %d", p);
+        if (off[p + 1] - off[p] > 255) return fail(nullptr, LSKUM_ERR_ARG, "more than 255 neighbours at point %d", p);
+        has_wall |= cl->flag[p] == LSKUM_WALL;
+    }
+    if (has_wall && (!cl->nx || !cl->ny)) return fail(nullptr, LSKUM_ERR_ARG, "wall points need nx, ny");
+    for (int32_t p = 0; p < n; p++) {
+        for (int32_t e = off[p]; e < off[p + 1]; e++) {
+            const int32_t q = idx[e];
+            if (q < 0 || q >= n || q == p)
+                return fail(nullptr, LSKUM_ERR_ARG, "bad neighbour index %d at point %d", q, p);
+            for (int32_t f = off[p]; f < e; f++)
+                if (idx[f] == q) return fail(nullptr, LSKUM_ERR_ARG, "duplicate neighbour %d at point %d", q, p);
+        }
+        if (cl->flag[p] == LSKUM_WALL) {
+            const double ln = std::hypot(cl->nx[p], cl->ny[p]);
+            if (!(std::fabs(ln - 1.0) < 1e-6)) return fail(nullptr, LSKUM_ERR_ARG, "wall normal not unit at point %d", p);
+        }
+    }
+    lskum_ctx *c = new (std::nothrow) lskum_ctx();
+    if (!c) return fail(nullptr, LSKUM_ERR_OOM, "host allocation failed");
+    c->n = n;
+    c->opts = *opts;
+    c->user_stream = (cudaStream_t)cuda_stream;
+    HostPrep hp;
+    lskum_status s = prepare_host(c, cl, hp);  // no CUDA call before this returns
+    if (s == LSKUM_OK) {
+        cudaError_t e = cudaGetDevice(&c->device);
+        s = e == cudaSuccess ? upload(c, hp) : cuda_fail(c, e, "cudaGetDevice");
+    }
+    if (s != LSKUM_OK) {
+        g_create_error = c->err;
+        lskum_destroy(c);
+        return s;
+    }
+    *out = c;
+    return LSKUM_OK;
+}
+
+static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &hp)
+{
+    const int32_t n = c->n;
+    const int32_t *off = cl->nbr_off, *idx = cl->nbr_idx;
+    c->x.assign(cl->x, cl->x + n);
+    c->y.assign(cl->y, cl->y + n);
+    c->flag.assign(cl->flag, cl->flag + n);
+    c->nx.assign(n, 0.0);
+    c->ny.assign(n, 0.0);
+    for (int32_t p = 0; p < n; p++)
+        if (c->flag[p] == LSKUM_WALL) {
+            c->nx[p] = cl->nx[p];
+            c->ny[p] = cl->ny[p];
+        }
+
+    // ---- per-slot geometry and LS weights (caller order) ----
+    const int64_t nnz = off[n];
+    std::vector<double> sdx(nnz), sdy(nnz), sw1(nnz, 0.0), sw2(nnz, 0.0), swgx(nnz), swgy(nnz);
+    std::vector<uint8_t> smb(nnz, 0);
+    std::vector<double> geo((size_t)G_NFIELDS * n, 0.0);
+    for (int32_t p = 0; p < n; p++) {
+        const bool wall = c->flag[p] == LSKUM_WALL;
+        double e1x = 1.0, e1y = 0.0, e2x = 0.0, e2y = 1.0;
+        if (wall) {
+            e1x = c->ny[p];
+            e1y = -c->nx[p];
+            e2x = c->nx[p];
+            e2y = c->ny[p];
+        }
+        geo[G_E1X * n + p] = e1x;
+        geo[G_E1Y * n + p] = e1y;
+        geo[G_E2X * n + p] = e2x;
+        geo[G_E2Y * n + p] = e2y;
+        double sdd[4] = {0, 0, 0, 0}, spp[4] = {0, 0, 0, 0}, sdp[4] = {0, 0, 0, 0};
+        double s1d[4] = {0, 0, 0, 0}, s1p[4] = {0, 0, 0, 0};
+        int cnt[4] = {0, 0, 0, 0};
+        double sxx = 0, syy = 0, sxy = 0, dmin = INFINITY;
+        for (int32_t e = off[p]; e < off[p + 1]; e++) {
+            const int32_t i = idx[e];
+            const double dx = c->x[i] - c->x[p], dy = c->y[i] - c->y[p];
+            sdx[e] = dx;
+            sdy[e] = dy;
+            sxx += dx * dx;
+            syy += dy * dy;
+            sxy += dx * dy;
+            dmin = std::min(dmin, std::sqrt(dx * dx + dy * dy));
+            const double a = dx * e1x + dy * e1y, b = dx * e2x + dy * e2y;
+            uint8_t mb = 0;
+            if (a < 0.0) mb |= 1;
+            else if (a > 0.0) mb |= 2;
+            if (b < 0.0) { if (!wall) mb |= 4; }
+            else if (b > 0.0) mb |= 8;
+            smb[e] = mb;
+            for (int s = 0; s < 4; s++) {
+                if (!(mb & (1 << s))) continue;
+                const double d = s < 2 ? a : b, dp = s < 2 ? b : a;
+                sdd[s] += d * d;
+                spp[s] += dp * dp;
+                sdp[s] += d * dp;
+                s1d[s] += d;
+                s1p[s] += dp;
+                cnt[s]++;
+            }
+        }
+        const int32_t deg = off[p + 1] - off[p];
+        const double gdet = sxx * syy - sxy * sxy;
+        if (deg < 2 || !(gdet > 1e-12 * sxx * syy))
+            return fail(c, LSKUM_ERR_STENCIL, "degenerate least-squares stencil at point %d", p);
+        for (int32_t e = off[p]; e < off[p + 1]; e++) {
+            swgx[e] = (syy * sdx[e] - sxy * sdy[e]) / gdet;
+            swgy[e] = (sxx * sdy[e] - sxy * sdx[e]) / gdet;
+        }
+        geo[G_DMIN * n + p] = dmin;
+        if (c->flag[p] == LSKUM_OUTER) continue;
+        double det[4];
+        for (int s = 0; s < 4; s++) {
+            if (wall && s == 2) continue;
+            det[s] = sdd[s] * spp[s] - sdp[s] * sdp[s];
+            if (cnt[s] < 2 || !(det[s] > 1e-12 * sdd[s] * spp[s]))
+                return fail(c, LSKUM_ERR_STENCIL, "degenerate split sub-stencil %d at point %d", s, p);
+            geo[(G_LS1_0 + s) * n + p] = (spp[s] * s1d[s] - sdp[s] * s1p[s]) / det[s];
+        }
+        for (int32_t e = off[p]; e < off[p + 1]; e++) {
+            const double a = sdx[e] * e1x + sdy[e] * e1y, b = sdx[e] * e2x + sdy[e] * e2y;
+            for (int s = 0; s < 4; s++) {
+                if (!(smb[e] & (1 << s))) continue;
+                const double d = s < 2 ? a : b, dp = s < 2 ? b : a;
+                const double w = (spp[s] * d - sdp[s] * dp) / det[s];
+                if (s < 2) sw1[e] = w;
+                else sw2[e] = w;
+                geo[(G_ABS_0 + s) * n + p] += std::fabs(w);
+            }
+        }
+    }
+
+    // ---- colouring and orders ----
+    c->n_colours = colour_points(n, off, idx, c->colour);
+    const int32_t nc = c->n_colours;
+    c->canon_order.resize(n);
+    {
+        std::vector<int32_t> cnt(nc + 2, 0);
+        for (int32_t p = 0; p < n; p++) cnt[c->colour[p] + 1]++;
+        for (int32_t k = 1; k <= nc + 1; k++) cnt[k] += cnt[k - 1];
+        std::vector<int32_t> pos(cnt.begin(), cnt.end());
+        for (int32_t p = 0; p < n; p++) c->canon_order[pos[c->colour[p]]++] = p;
+    }
+    // internal order: colour, then wall < interior < outer, then caller index
+    auto trank = [&](int32_t p) { return c->flag[p] == LSKUM_WALL ? 0 : (c->flag[p] == LSKUM_INTERIOR ? 1 : 2); };
+    c->perm.resize(n);
+    std::iota(c->perm.begin(), c->perm.end(), 0);
+    std::stable_sort(c->perm.begin(), c->perm.end(), [&](int32_t a, int32_t b) {
+        if (c->colour[a] != c->colour[b]) return c->colour[a] < c->colour[b];
+        return trank(a) < trank(b);
+    });
+    c->inv.resize(n);
+    for (int32_t k = 0; k < n; k++) c->inv[c->perm[k]] = k;
+    c->lvl_beg.assign(nc, 0);
+    c->lvl_act_end.assign(nc, 0);
+    c->lvl_end.assign(nc, 0);
+    {
+        int32_t k = 0;
+        for (int32_t col = 1; col <= nc; col++) {
+            c->lvl_beg[col - 1] = k;
+            while (k < n && c->colour[c->perm[k]] == col && c->flag[c->perm[k]] != LSKUM_OUTER) k++;
+            c->lvl_act_end[col - 1] = k;
+            while (k < n && c->colour[c->perm[k]] == col) k++;
+            c->lvl_end[col - 1] = k;
+        }
+    }
+
+    // ---- sliced ELL in internal order ----
+    const int32_t ld = (n + 31) / 32 * 32;
+    c->ld = ld;
+    const int32_t nsl = ld / 32;
+    std::vector<int32_t> &slice_off = hp.slice_off, &deg = hp.deg;
+    slice_off.assign(nsl + 1, 0);
+    deg.assign(n, 0);
+    for (int32_t s = 0; s < nsl; s++) {
+        int32_t w = 0;
+        for (int32_t l = 0; l < 32; l++) {
+            const int32_t k = s * 32 + l;
+            if (k < n) {
+                const int32_t p = c->perm[k];
+                w = std::max(w, off[p + 1] - off[p]);
+            }
+        }
+        slice_off[s + 1] = slice_off[s] + 32 * w;
+    }
+    const int64_t ell = slice_off[nsl];
+    const size_t esz = std::max<int64_t>(ell, 1);
+    std::vector<int32_t> &enb = hp.enb;
+    std::vector<uint8_t> &emb = hp.emb;
+    std::vector<double> &edx = hp.edx, &edy = hp.edy, &ew1 = hp.ew1, &ew2 = hp.ew2, &egx = hp.egx, &egy = hp.egy;
+    enb.assign(esz, 0);
+    emb.assign(esz, 0);
+    for (auto *v : {&edx, &edy, &ew1, &ew2, &egx, &egy}) v->assign(esz, 0.0);
+    for (int32_t k = 0; k < n; k++) {
+        const int32_t p = c->perm[k];
+        deg[k] = off[p + 1] - off[p];
+        const int64_t base = slice_off[k / 32] + (k % 32);
+        const int32_t w = (slice_off[k / 32 + 1] - slice_off[k / 32]) / 32;
+        for (int32_t j = 0; j < w; j++) enb[base + 32 * j] = k;  // padding: self, never read
+        for (int32_t j = 0; j < deg[k]; j++) {
+            const int64_t e = off[p] + j, t = base + 32 * j;
+            enb[t] = c->inv[idx[e]];
+            emb[t] = smb[e];
+            edx[t] = sdx[e];
+            edy[t] = sdy[e];
+            ew1[t] = sw1[e];
+            ew2[t] = sw2[e];
+            egx[t] = swgx[e];
+            egy[t] = swgy[e];
+        }
+    }
+    std::vector<double> &geo_i = hp.geo_i, &wnx = hp.wnx, &wny = hp.wny;
+    std::vector<uint8_t> &fl_i = hp.fl_i;
+    geo_i.assign((size_t)G_NFIELDS * ld, 0.0);
+    wnx.assign(ld, 0.0);
+    wny.assign(ld, 0.0);
+    fl_i.assign(ld, LSKUM_OUTER);
+    for (int32_t k = 0; k < n; k++) {
+        const int32_t p = c->perm[k];
+        for (int f = 0; f < G_NFIELDS; f++) geo_i[(size_t)f * ld + k] = geo[(size_t)f * n + p];
+        wnx[k] = c->nx[p];
+        wny[k] = c->ny[p];
+        fl_i[k] = c->flag[p];
+    }
+
+    return LSKUM_OK;
+}
+
+static lskum_status upload(lskum_ctx *c, HostPrep &hp)
+{
+    const int32_t n = c->n, ld = c->ld, nsl = ld / 32, nc = c->n_colours;
+    std::vector<int32_t> &slice_off = hp.slice_off, &deg = hp.deg, &enb = hp.enb;
+    std::vector<uint8_t> &emb = hp.emb, &fl_i = hp.fl_i;
+    std::vector<double> &edx = hp.edx, &edy = hp.edy, &ew1 = hp.ew1, &ew2 = hp.ew2, &egx = hp.egx, &egy = hp.egy;
+    std::vector<double> &geo_i = hp.geo_i, &wnx = hp.wnx, &wny = hp.wny;
+    // ---- device memory ----
+    cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamCreate");
+    e = cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventCreate");
+    Arena &A = c->arena;
+    Dev &d = c->dev;
+    d.n = n;
+    d.ld = ld;
+    d.n_slices = nsl;
+    uint8_t *dfl = A.alloc<uint8_t>(ld);
+    double *dwnx = A.alloc<double>(ld), *dwny = A.alloc<double>(ld);
+    double *dgeo = A.alloc<double>((size_t)G_NFIELDS * ld);
+    int32_t *dso = A.alloc<int32_t>(nsl + 1), *ddeg = A.alloc<int32_t>(n), *dnb = A.alloc<int32_t>(enb.size());
+    uint8_t *dmb = A.alloc<uint8_t>(emb.size());
+    double *ddx = A.alloc<double>(edx.size()), *ddy = A.alloc<double>(edx.size());
+    double *dw1 = A.alloc<double>(edx.size()), *dw2 = A.alloc<double>(edx.size());
+    double *dgx = A.alloc<double>(edx.size()), *dgy = A.alloc<double>(edx.size());
+    for (int s = 0; s < 2; s++) {
+        d.set[s].U = A.alloc<double>(4 * (size_t)ld);
+        d.set[s].q = A.alloc<double>(4 * (size_t)ld);
+        d.set[s].prim = A.alloc<double>((size_t)P_NFIELDS * ld);
+        d.qx[s] = A.alloc<double>(4 * (size_t)ld);
+        d.qy[s] = A.alloc<double>(4 * (size_t)ld);
+    }
+    d.R = A.alloc<double>(4 * (size_t)ld);
+    d.D = A.alloc<double>(ld);
+    d.dUs = A.alloc<double>(4 * (size_t)ld);
+    d.dU = A.alloc<double>(4 * (size_t)ld);
+    // launch shape: enough threads per point to fill the GPU on small clouds
+    c->launch.res_block = 128;
+    c->launch.tpp = n >= 100000 ? 1 : (n >= 50000 ? 2 : (n >= 25000 ? 4 : 8));
+    d.n_blk = residual_blocks(d, c->launch);
+    d.blk = A.alloc<double>(d.n_blk);
+    c->ctrl = A.alloc<Ctrl>(1);
+    c->hist_cap = 4096;
+    c->hist = A.alloc<double>(c->hist_cap);
+    if (A.err != cudaSuccess) return cuda_fail(c, A.err, "cudaMalloc");
+    e = cudaMemset(c->ctrl, 0, sizeof(Ctrl));
+    if (e == cudaSuccess) e = cudaMallocHost(&c->pinned, 4 * (size_t)ld * sizeof(double));
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMallocHost");
+    d.flag = dfl;
+    d.wnx = dwnx;
+    d.wny = dwny;
+    d.geo = dgeo;
+    d.slice_off = dso;
+    d.deg = ddeg;
+    d.nbr = dnb;
+    d.memb = dmb;
+    d.ndx = ddx;
+    d.ndy = ddy;
+    d.w1 = dw1;
+    d.w2 = dw2;
+    d.wgx = dgx;
+    d.wgy = dgy;
+    d.ctrl = c->ctrl;
+    d.cfl = c->opts.cfl;
+    d.ramp = c->opts.cfl_ramp_iters;
+    d.K = c->opts.inner_iters;
+    d.first_order = c->opts.first_order_iters;
+    d.jvp = c->opts.jvp;
+    auto up = [&](void *dst, const void *src, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+    };
+    up(dfl, fl_i.data(), ld);
+    up(dwnx, wnx.data(), ld * sizeof(double));
+    up(dwny, wny.data(), ld * sizeof(double));
+    up(dgeo, geo_i.data(), geo_i.size() * sizeof(double));
+    up(dso, slice_off.data(), slice_off.size() * sizeof(int32_t));
+    up(ddeg, deg.data(), n * sizeof(int32_t));
+    up(dnb, enb.data(), enb.size() * sizeof(int32_t));
+    up(dmb, emb.data(), emb.size());
+    up(ddx, edx.data(), edx.size() * sizeof(double));
+    up(ddy, edy.data(), edy.size() * sizeof(double));
+    up(dw1, ew1.data(), ew1.size() * sizeof(double));
+    up(dw2, ew2.data(), ew2.size() * sizeof(double));
+    up(dgx, egx.data(), egx.size() * sizeof(double));
+    up(dgy, egy.data(), egy.size() * sizeof(double));
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy");
+    // zero intermediates; D = 1 at outer points (never written by the kernels)
+    for (double *p : {d.R, d.dUs, d.dU, d.qx[0], d.qx[1], d.qy[0], d.qy[1]})
+        if (e == cudaSuccess) e = cudaMemset(p, 0, 4 * (size_t)ld * sizeof(double));
+    std::vector<double> ones(ld, 1.0);
+    up(d.D, ones.data(), ld * sizeof(double));
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemset");
+
+    // ---- free-stream start ----
+    const double al = c->opts.aoa_deg * M_PI / 180.0;
+    const double uinf = c->opts.mach * std::cos(al), vinf = c->opts.mach * std::sin(al), pinf = 1.0 / 1.4;
+    std::vector<double> rho(n, 1.0), uu(n, uinf), vv(n, vinf), pp(n, pinf);
+    lskum_status s = lskum_set_state(c, rho.data(), uu.data(), vv.data(), pp.data());
+    if (s != LSKUM_OK) return s;
+
+    // ---- one CUDA graph per state parity ----
+    for (int par = 0; par < 2; par++) {
+        cudaGraph_t g = nullptr;
+        e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamBeginCapture");
+        int launches = 0;
+        cudaError_t le = launch_iteration(d, c->launch, par, nc, c->lvl_beg.data(), c->lvl_act_end.data(),
+                                          c->lvl_end.data(), c->stream, &launches);
+        e = cudaStreamEndCapture(c->stream, &g);
+        if (le != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return cuda_fail(c, le, "kernel launch during capture");
+        }
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&c->graph[par], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+        c->launches_per_iter = launches;
+    }
+    return LSKUM_OK;
+}
+
+void lskum_destroy(lskum_ctx *c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto &g : c->graph)
+        if (g) cudaGraphExecDestroy(g);
+    c->arena.release();
+    if (c->pinned) cudaFreeHost(c->pinned);
+    if (c->ev) cudaEventDestroy(c->ev);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+}  // extern "C"
+
+namespace {
+
+// order the internal stream after the caller's stream
+cudaError_t join_user(lskum_ctx *c)
+{
+    if (!c->user_stream) return cudaSuccess;
+    cudaError_t e = cudaEventRecord(c->ev, c->user_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->ev, 0);
+    return e;
+}
+
+cudaError_t release_user(lskum_ctx *c)
+{
+    if (!c->user_stream) return cudaSuccess;
+    cudaError_t e = cudaEventRecord(c->ev, c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->user_stream, c->ev, 0);
+    return e;
+}
+
+lskum_status read_ctrl(lskum_ctx *c, Ctrl *h)
+{
+    cudaError_t e = cudaMemcpyAsync(h, c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "reading the control block");
+    return LSKUM_OK;
+}
+
+lskum_status ensure_hist(lskum_ctx *c, int32_t need)
+{
+    if (need <= c->hist_cap) return LSKUM_OK;
+    int32_t cap = c->hist_cap;
+    while (cap < need) cap *= 2;
+    double *h = nullptr;
+    cudaError_t e = cudaMalloc(&h, cap * sizeof(double));
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc(history)");
+    e = cudaMemcpyAsync(h, c->hist, c->hist_cap * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cudaFree(h);
+        return cuda_fail(c, e, "copying the history");
+    }
+    for (auto &p : c->arena.ptrs)
+        if (p == c->hist) {
+            cudaFree(p);
+            p = h;
+        }
+    c->hist = h;
+    c->hist_cap = cap;
+    return LSKUM_OK;
+}
+
+lskum_status state_from_conserved(lskum_ctx *c, const std::vector<double> &Ucaller, bool reset_hist)
+{
+    const int32_t n = c->n, ld = c->ld;
+    double *Ui = c->pinned;  // staged in page-locked memory
+    for (int32_t k = 0; k < n; k++) {
+        const int32_t p = c->perm[k];
+        for (int cc = 0; cc < 4; cc++) Ui[(size_t)cc * ld + k] = Ucaller[4 * (size_t)p + cc];
+    }
+    for (int32_t k = n; k < ld; k++) {  // padding: a valid state, never read
+        Ui[k] = 1.0;
+        Ui[(size_t)ld + k] = Ui[2 * (size_t)ld + k] = 0.0;
+        Ui[3 * (size_t)ld + k] = 2.5;
+    }
+    cudaError_t e = join_user(c);
+    const int tgt = c->cur;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->dev.set[tgt].U, Ui, 4 * (size_t)ld * sizeof(double), cudaMemcpyHostToDevice,
+                            c->stream);
+    if (e == cudaSuccess) e = launch_reset_ctrl(c->ctrl, c->stream);
+    if (e == cudaSuccess) e = launch_init_state(c->dev, tgt, c->stream);
+    Ctrl h{};
+    if (e != cudaSuccess) return cuda_fail(c, e, "setting the state");
+    lskum_status s = read_ctrl(c, &h);
+    if (s != LSKUM_OK) return s;
+    if (h.error) return fail(c, LSKUM_ERR_NONPOSITIVE, "non-physical state at point %d", c->perm[h.bad_point]);
+    if (reset_hist) {
+        h.it = 0;
+        h.hist0 = 0.0;
+    }
+    h.hist = c->hist;
+    h.hist_cap = c->hist_cap;
+    h.stop = h.stop_after = h.error = 0;
+    h.bad_point = 0x7fffffff;
+    e = cudaMemcpyAsync(c->ctrl, &h, sizeof(Ctrl), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = release_user(c);
+    if (e != cudaSuccess) return cuda_fail(c, e, "writing the control block");
+    return LSKUM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lskum_status lskum_set_state(lskum_ctx *c, const double *rho, const double *u, const double *v, const double *p)
+{
+    if (!c || !rho || !u || !v || !p) return c ? fail(c, LSKUM_ERR_ARG, "NULL argument") : LSKUM_ERR_ARG;
+    if (c->pending) return fail(c, LSKUM_ERR_ARG, "an enqueued run has not been waited for");
+    std::vector<double> U(4 * (size_t)c->n);
+    for (int32_t k = 0; k < c->n; k++) {
+        if (!(rho[k] > 0.0) || !(p[k] > 0.0) || !std::isfinite(rho[k]) || !std::isfinite(p[k]) ||
+            !std::isfinite(u[k]) || !std::isfinite(v[k]))
+            return fail(c, LSKUM_ERR_NONPOSITIVE, "non-physical input state at point %d", k);
+        U[4 * (size_t)k] = rho[k];
+        U[4 * (size_t)k + 1] = rho[k] * u[k];
+        U[4 * (size_t)k + 2] = rho[k] * v[k];
+        U[4 * (size_t)k + 3] = p[k] / 0.4 + 0.5 * rho[k] * (u[k] * u[k] + v[k] * v[k]);
+    }
+    return state_from_conserved(c, U, true);
+}
+
+lskum_status lskum_set_conserved(lskum_ctx *c, const double *U)
+{
+    if (!c || !U) return c ? fail(c, LSKUM_ERR_ARG, "NULL argument") : LSKUM_ERR_ARG;
+    if (c->pending) return fail(c, LSKUM_ERR_ARG, "an enqueued run has not been waited for");
+    std::vector<double> Uv(U, U + 4 * (size_t)c->n);
+    return state_from_conserved(c, Uv, false);
+}
+
+// Asynchronous part of lskum_run: enqueue max_iters graph launches.
+lskum_status lskum_enqueue(lskum_ctx *c, int32_t max_iters, double target_drop)
+{
+    if (!c || max_iters < 0) return c ? fail(c, LSKUM_ERR_ARG, "bad argument") : LSKUM_ERR_ARG;
+    if (c->pending) return fail(c, LSKUM_ERR_ARG, "an enqueued run has not been waited for");
+    Ctrl h{};
+    lskum_status s = read_ctrl(c, &h);
+    if (s != LSKUM_OK) return s;
+    s = ensure_hist(c, h.it + max_iters);
+    if (s != LSKUM_OK) return s;
+    h.hist = c->hist;
+    h.hist_cap = c->hist_cap;
+    h.stop = h.stop_after = h.error = 0;
+    h.bad_point = 0x7fffffff;
+    h.target = target_drop;
+    cudaError_t e = join_user(c);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->ctrl, &h, sizeof(Ctrl), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    c->it_base = h.it;
+    c->cur_base = c->cur;
+    int par = c->cur;
+    for (int32_t i = 0; i < max_iters && e == cudaSuccess; i++) {
+        e = cudaGraphLaunch(c->graph[par], c->stream);
+        par ^= 1;
+    }
+    if (e == cudaSuccess) e = release_user(c);
+    if (e != cudaSuccess) return cuda_fail(c, e, "enqueueing iterations");
+    c->pending = true;
+    return LSKUM_OK;
+}
+
+lskum_status lskum_wait(lskum_ctx *c, int32_t *iters_done)
+{
+    if (iters_done) *iters_done = 0;
+    if (!c) return LSKUM_ERR_ARG;
+    if (!c->pending) return LSKUM_OK;
+    c->pending = false;
+    Ctrl h{};
+    lskum_status s = read_ctrl(c, &h);
+    if (s != LSKUM_OK) return s;
+    int32_t done = h.it - c->it_base;  // iterations whose norm was recorded
+    if (h.error == LSKUM_ERR_NONPOSITIVE) {
+        // the failed iteration's update was not applied: roll back its norm
+        done -= 1;
+        Ctrl w = h;
+        w.it = h.it - 1;
+        cudaMemcpyAsync(c->ctrl, &w, sizeof(Ctrl), cudaMemcpyHostToDevice, c->stream);
+        cudaStreamSynchronize(c->stream);
+    }
+    c->cur = (c->cur_base + done) & 1;
+    if (iters_done) *iters_done = done;
+    if (h.error == LSKUM_ERR_NONPOSITIVE)
+        return fail(c, LSKUM_ERR_NONPOSITIVE, "non-physical update at point %d in iteration %d",
+                    c->perm[h.bad_point], h.it);
+    if (h.error == LSKUM_ERR_DIVERGED) {
+        c->cur = (c->cur_base + done - 1) & 1;  // that iteration never reached its update
+        if (iters_done) *iters_done = done - 1;
+        return fail(c, LSKUM_ERR_DIVERGED, "residual norm not finite in iteration %d", h.it);
+    }
+    return LSKUM_OK;
+}
+
+lskum_status lskum_run(lskum_ctx *c, int32_t max_iters, double target_drop, int32_t *iters_done)
+{
+    lskum_status s = lskum_enqueue(c, max_iters, target_drop);
+    if (s != LSKUM_OK) {
+        if (iters_done) *iters_done = 0;
+        return s;
+    }
+    return lskum_wait(c, iters_done);
+}
+
+void *lskum_stream(lskum_ctx *c)
+{
+    return c ? (void *)c->stream : nullptr;
+}
+
+static lskum_status download(lskum_ctx *c, const double *src, int comps, std::vector<double> &out)
+{
+    const int32_t n = c->n, ld = c->ld;
+    double *buf = c->pinned;  // page-locked staging, 4 * ld doubles
+    cudaError_t e = cudaMemcpyAsync(buf, src, (size_t)comps * ld * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy D2H");
+    out.assign((size_t)comps * n, 0.0);
+    for (int32_t k = 0; k < n; k++) {
+        const int32_t p = c->perm[k];
+        for (int cc = 0; cc < comps; cc++) out[(size_t)comps * p + cc] = buf[(size_t)cc * ld + k];
+    }
+    return LSKUM_OK;
+}
+
+lskum_status lskum_get_field(lskum_ctx *c, int32_t field, double *out)
+{
+    if (!c || !out) return c ? fail(c, LSKUM_ERR_ARG, "NULL argument") : LSKUM_ERR_ARG;
+    if (c->pending) return fail(c, LSKUM_ERR_ARG, "an enqueued run has not been waited for");
+    const Dev &d = c->dev;
+    const int K = d.K & 1;
+    const double *src = nullptr;
+    int comps = 4;
+    switch (field) {
+    case LSKUM_FIELD_U: src = d.set[c->cur].U; break;
+    case LSKUM_FIELD_Q: src = d.set[c->cur].q; break;
+    case LSKUM_FIELD_QX: src = d.qx[K]; break;
+    case LSKUM_FIELD_QY: src = d.qy[K]; break;
+    case LSKUM_FIELD_R: src = d.R; break;
+    case LSKUM_FIELD_D: src = d.D; comps = 1; break;
+    case LSKUM_FIELD_DUS: src = d.dUs; break;
+    case LSKUM_FIELD_DU: src = d.dU; break;
+    default: return fail(c, LSKUM_ERR_ARG, "unknown field %d", field);
+    }
+    std::vector<double> v;
+    lskum_status s = download(c, src, comps, v);
+    if (s != LSKUM_OK) return s;
+    std::memcpy(out, v.data(), v.size() * sizeof(double));
+    return LSKUM_OK;
+}
+
+lskum_status lskum_get_state(lskum_ctx *c, double *rho, double *u, double *v, double *p)
+{
+    if (!c || !rho || !u || !v || !p) return c ? fail(c, LSKUM_ERR_ARG, "NULL argument") : LSKUM_ERR_ARG;
+    if (c->pending) return fail(c, LSKUM_ERR_ARG, "an enqueued run has not been waited for");
+    std::vector<double> U;
+    lskum_status s = download(c, c->dev.set[c->cur].U, 4, U);
+    if (s != LSKUM_OK) return s;
+    for (int32_t k = 0; k < c->n; k++) {
+        const double r = U[4 * (size_t)k];
+        rho[k] = r;
+        u[k] = U[4 * (size_t)k + 1] / r;
+        v[k] = U[4 * (size_t)k + 2] / r;
+        p[k] = 0.4 * (U[4 * (size_t)k + 3] - 0.5 * r * (u[k] * u[k] + v[k] * v[k]));
+    }
+    return LSKUM_OK;
+}
+
+lskum_status lskum_get_residuals(lskum_ctx *c, double *hist, int32_t cap, int32_t *n)
+{
+    if (!c || !n || cap < 0 || (cap > 0 && !hist)) return c ? fail(c, LSKUM_ERR_ARG, "bad argument") : LSKUM_ERR_ARG;
+    if (c->pending) return fail(c, LSKUM_ERR_ARG, "an enqueued run has not been waited for");
+    Ctrl h{};
+    lskum_status s = read_ctrl(c, &h);
+    if (s != LSKUM_OK) return s;
+    *n = h.it;
+    const int32_t m = std::min(cap, h.it);
+    if (m > 0) {
+        cudaError_t e = cudaMemcpyAsync(hist, c->hist, m * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy history");
+    }
+    return LSKUM_OK;
+}
+
+lskum_status lskum_get_forces(lskum_ctx *c, double *cl, double *cd)
+{
+    if (!c || !cl || !cd) return c ? fail(c, LSKUM_ERR_ARG, "NULL argument") : LSKUM_ERR_ARG;
+    if (c->pending) return fail(c, LSKUM_ERR_ARG, "an enqueued run has not been waited for");
+    std::vector<double> U;
+    lskum_status s = download(c, c->dev.set[c->cur].U, 4, U);
+    if (s != LSKUM_OK) return s;
+    std::vector<int32_t> w;
+    for (int32_t p = 0; p < c->n; p++)
+        if (c->flag[p] == LSKUM_WALL) w.push_back(p);
+    *cl = 0.0;
+    *cd = 0.0;
+    const int32_t nw = (int32_t)w.size();
+    if (nw < 3) return LSKUM_OK;
+    double area2 = 0.0;
+    for (int32_t k = 0; k < nw; k++) {
+        const int32_t a = w[k], b = w[(k + 1) % nw];
+        area2 += c->x[a] * c->y[b] - c->x[b] * c->y[a];
+    }
+    const double orient = area2 > 0.0 ? 1.0 : -1.0;
+    const double pinf = 1.0 / 1.4;
+    double Fx = 0.0, Fy = 0.0;
+    for (int32_t k = 0; k < nw; k++) {
+        const int32_t a = w[(k + nw - 1) % nw], m = w[k], b = w[(k + 1) % nw];
+        const double ex = 0.5 * (c->x[b] - c->x[a]), ey = 0.5 * (c->y[b] - c->y[a]);
+        const double r = U[4 * (size_t)m];
+        const double uu = U[4 * (size_t)m + 1] / r, vv = U[4 * (size_t)m + 2] / r;
+        const double pr = 0.4 * (U[4 * (size_t)m + 3] - 0.5 * r * (uu * uu + vv * vv));
+        Fx -= (pr - pinf) * orient * ey;
+        Fy -= (pr - pinf) * (-orient * ex);
+    }
+    const double al = c->opts.aoa_deg * M_PI / 180.0;
+    const double qinf = 0.5 * c->opts.mach * c->opts.mach;
+    *cl = (Fy * std::cos(al) - Fx * std::sin(al)) / qinf;
+    *cd = (Fx * std::cos(al) + Fy * std::sin(al)) / qinf;
+    return LSKUM_OK;
+}
+
+lskum_status lskum_time_phases(lskum_ctx *c, int32_t reps, double *ms)
+{
+    if (!c || reps < 1 || !ms) return c ? fail(c, LSKUM_ERR_ARG, "bad argument") : LSKUM_ERR_ARG;
+    if (c->pending) return fail(c, LSKUM_ERR_ARG, "an enqueued run has not been waited for");
+    Ctrl h{};
+    lskum_status s = read_ctrl(c, &h);
+    if (s != LSKUM_OK) return s;
+    s = ensure_hist(c, h.it + reps);
+    if (s != LSKUM_OK) return s;
+    h.hist = c->hist;
+    h.hist_cap = c->hist_cap;
+    h.stop = h.stop_after = h.error = 0;
+    h.target = 0.0;
+    cudaError_t e = cudaMemcpyAsync(c->ctrl, &h, sizeof(Ctrl), cudaMemcpyHostToDevice, c->stream);
+    cudaEvent_t ev[7];
+    for (auto &x : ev)
+        if (e == cudaSuccess) e = cudaEventCreate(&x);
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    const Dev &d = c->dev;
+    for (int32_t r = 0; r < reps && e == cudaSuccess; r++) {
+        const int cur = c->cur;
+        for (int ph = 0; ph < 6 && e == cudaSuccess; ph++) {
+            e = cudaEventRecord(ev[ph], c->stream);
+            if (e == cudaSuccess) e = launch_phase(d, c->launch, cur, ph, c->n_colours, c->lvl_beg.data(),
+                                                   c->lvl_act_end.data(), c->lvl_end.data(), c->stream);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(ev[6], c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[6]);
+        for (int ph = 0; ph < 6 && e == cudaSuccess; ph++) {
+            float t = 0.f;
+            e = cudaEventElapsedTime(&t, ev[ph], ev[ph + 1]);
+            acc[ph] += t;
+        }
+        c->cur ^= 1;
+    }
+    for (auto &x : ev) cudaEventDestroy(x);
+    if (e != cudaSuccess) return cuda_fail(c, e, "timing phases");
+    Ctrl h2{};
+    s = read_ctrl(c, &h2);
+    if (s != LSKUM_OK) return s;
+    if (h2.error) {
+        c->cur ^= 1;
+        return fail(c, (lskum_status)h2.error, "iteration failed while timing phases");
+    }
+    for (int ph = 0; ph < 6; ph++) ms[ph] = acc[ph] / reps;
+    return LSKUM_OK;
+}
+
+lskum_status lskum_get_order(lskum_ctx *c, int32_t *colour, int32_t *order, int32_t *n_colours)
+{
+    if (!c) return LSKUM_ERR_ARG;
+    if (colour) std::memcpy(colour, c->colour.data(), c->n * sizeof(int32_t));
+    if (order) std::memcpy(order, c->canon_order.data(), c->n * sizeof(int32_t));
+    if (n_colours) *n_colours = c->n_colours;
+    return LSKUM_OK;
+}
+
+lskum_status lskum_get_info(lskum_ctx *c, int32_t *n_points, int32_t *n_colours, int32_t *launches_per_iter)
+{
+    if (!c) return LSKUM_ERR_ARG;
+    if (n_points) *n_points = c->n;
+    if (n_colours) *n_colours = c->n_colours;
+    if (launches_per_iter) *launches_per_iter = c->launches_per_iter;
+    return LSKUM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,107 @@
+// Device data layout and the launch interface between the host orchestration
+// (lskum_host.cpp) and the kernels (lskum_kernels.cu).
+//
+// Layout in HBM (all in the internal order: points sorted by colour, then by
+// type wall < interior < outer, then by caller index):
+//  - per-point fields are structure-of-arrays with a row stride `ld`
+//    (N rounded up to a multiple of 32): field f of point k at a[f * ld + k];
+//  - neighbour lists are sliced ELLPACK: slice s holds points 32s..32s+31,
+//    neighbour slot j of point k sits at slice_off[k / 32] + 32 j + k % 32, so
+//    the 32 threads of a warp reading slot j of consecutive points touch one
+//    contiguous 128-byte (i32) or 256-byte (f64) span.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lskum {
+
+constexpr int kWall = 1;
+constexpr int kOuter = 2;
+
+// Device-resident control block: lets many iterations be enqueued (CUDA
+// graph launches) without host synchronisation; every kernel of an
+// iteration returns at once when the run has stopped.
+struct Ctrl {
+    int32_t stop;        // 1: skip all further work
+    int32_t stop_after;  // the drop target was reached: finish this iteration, then stop
+    int32_t error;       // lskum_status of a device-detected failure (0 = none)
+    int32_t bad_point;   // smallest internal index of a non-physical update
+    int32_t it;          // iterations whose residual norm has been recorded
+    int32_t hist_cap;    // capacity of hist
+    double hist0;        // first norm (drop reference); <= 0 = not set yet
+    double target;       // drop target of the current run (<= 0: none)
+    double *hist;        // residual-norm history (device)
+};
+
+// Per-point geometry rows (fields of `geo`, stride ld).
+enum GeoField {
+    G_E1X, G_E1Y, G_E2X, G_E2Y,          // frame: (1,0),(0,1) or wall (t, n)
+    G_LS1_0, G_LS1_1, G_LS1_2, G_LS1_3,  // LS_s(1) of the four split sub-stencils
+    G_ABS_0, G_ABS_1, G_ABS_2, G_ABS_3,  // sum_i |w_i| of each split sub-stencil
+    G_DMIN,                              // min_i |r_i - r_0|
+    G_NFIELDS
+};
+
+// Per-point primal quantities of the current state used by the sweeps'
+// Jacobian products (fields of `prim`, stride ld).
+enum PrimField {
+    P_RHO, P_IRHO, P_U, P_V, P_P, P_BETA, P_SB, P_ISB, P_I2P, P_Q2, P_E1, P_E2,
+    P_SX, P_ERFX, P_EXPX, P_BX,   // direction (1,0): S, erf S, exp(-S^2), B
+    P_SY, P_ERFY, P_EXPY, P_BY,   // direction (0,1)
+    P_NFIELDS
+};
+
+struct StateSet {
+    double *U;     // [4][ld] conserved variables
+    double *q;     // [4][ld] q-variables
+    double *prim;  // [P_NFIELDS][ld]
+};
+
+struct Dev {
+    int32_t n, ld, n_slices;
+    // cloud
+    const uint8_t *flag;     // [n]
+    const double *wnx, *wny; // [n] wall normals
+    const double *geo;       // [G_NFIELDS][ld]
+    // sliced ELL neighbour slots
+    const int32_t *slice_off; // [n_slices + 1]
+    const int32_t *deg;       // [n]
+    const int32_t *nbr;       // neighbour (internal index)
+    const uint8_t *memb;      // bits 0/1: e1 sub-stencil +/-, bits 2/3: e2 sub-stencil +/-
+    const double *ndx, *ndy;  // x_i - x_0, y_i - y_0
+    const double *w1, *w2;    // LS weight of the slot in its e1 / e2 split sub-stencil (0 if none)
+    const double *wgx, *wgy;  // full-stencil LS weights of d/dx and d/dy (Eq. 10, 16)
+    // iteration buffers
+    StateSet set[2];
+    double *qx[2], *qy[2];   // double-buffered q-derivatives
+    double *R;               // [4][ld]
+    double *D;               // [ld]
+    double *dUs, *dU;        // [4][ld]
+    double *blk;             // residual-norm partial sums, one per residual block
+    int32_t n_blk;
+    Ctrl *ctrl;
+    // options
+    double cfl, ramp, u_inf[4];
+    int32_t K, jvp;
+    int32_t first_order;  // iterations n <= first_order use q~ = q
+};
+
+// Kernel launch wrappers (lskum_kernels.cu).  `cur` is the state set read by
+// this iteration; the update writes set 1 - cur.
+struct Launch {
+    int tpp;        // threads per point of the gradient and residual kernels
+    int res_block;  // threads per block of the residual kernel
+};
+
+cudaError_t launch_iteration(const Dev &d, const Launch &L, int cur, int n_levels, const int32_t *lvl_beg,
+                             const int32_t *lvl_act_end, const int32_t *lvl_end, cudaStream_t s,
+                             int *launches);
+// One phase of an iteration (0 q-derivatives, 1 residual, 2 norm, 3 forward
+// sweep, 4 backward sweep, 5 update), launched directly on s.
+cudaError_t launch_phase(const Dev &d, const Launch &L, int cur, int phase, int n_levels, const int32_t *lvl_beg,
+                         const int32_t *lvl_act_end, const int32_t *lvl_end, cudaStream_t s);
+cudaError_t launch_init_state(const Dev &d, int cur, cudaStream_t s);
+cudaError_t launch_reset_ctrl(Ctrl *c, cudaStream_t s);
+int residual_blocks(const Dev &d, const Launch &L);
+
+}  // namespace lskum

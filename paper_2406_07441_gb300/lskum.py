@@ -1,0 +1,194 @@
+"""Thin ctypes binding of liblskum (include/lskum.h): argument marshalling only.
+
+Every step of an iteration runs in the library's CUDA kernels.  The binding
+fails loudly when the compiled library is missing; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import LIB
+
+INTERIOR, WALL, OUTER = 0, 1, 2
+JVP_EXACT, JVP_INCREMENT = 0, 1
+FIELD_U, FIELD_Q, FIELD_QX, FIELD_QY, FIELD_R, FIELD_D, FIELD_DUS, FIELD_DU = range(8)
+STATUS = {0: "LSKUM_OK", -1: "LSKUM_ERR_ARG", -2: "LSKUM_ERR_STENCIL", -3: "LSKUM_ERR_NONPOSITIVE",
+          -4: "LSKUM_ERR_DIVERGED", -5: "LSKUM_ERR_CUDA", -6: "LSKUM_ERR_TIMEOUT", -7: "LSKUM_ERR_OOM"}
+
+
+class LskumError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class lskum_cloud(C.Structure):
+    _fields_ = [("n_points", C.c_int32), ("x", C.c_void_p), ("y", C.c_void_p), ("flag", C.c_void_p),
+                ("nx", C.c_void_p), ("ny", C.c_void_p), ("nbr_off", C.c_void_p), ("nbr_idx", C.c_void_p)]
+
+
+class lskum_opts(C.Structure):
+    _fields_ = [("mach", C.c_double), ("aoa_deg", C.c_double), ("cfl", C.c_double), ("cfl_ramp_iters", C.c_double),
+                ("inner_iters", C.c_int32), ("jvp", C.c_int32), ("precision", C.c_int32),
+                ("first_order_iters", C.c_int32)]
+
+
+_lib = None
+
+
+def load():
+    """Load liblskum.so (built by ``python -m paper_2406_07441_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB):
+        raise RuntimeError(f"liblskum is not built ({LIB} missing): run python -m paper_2406_07441_gb300.build")
+    L = C.CDLL(LIB)
+    vp, i32, d, st = C.c_void_p, C.c_int32, C.c_double, C.c_int
+    P = C.POINTER
+    L.lskum_create.argtypes = [P(lskum_cloud), P(lskum_opts), vp, P(vp)]
+    L.lskum_set_state.argtypes = [vp, vp, vp, vp, vp]
+    L.lskum_set_conserved.argtypes = [vp, vp]
+    L.lskum_run.argtypes = [vp, i32, d, P(i32)]
+    L.lskum_enqueue.argtypes = [vp, i32, d]
+    L.lskum_wait.argtypes = [vp, P(i32)]
+    L.lskum_stream.argtypes = [vp]
+    L.lskum_stream.restype = vp
+    L.lskum_get_state.argtypes = [vp, vp, vp, vp, vp]
+    L.lskum_get_field.argtypes = [vp, i32, vp]
+    L.lskum_get_residuals.argtypes = [vp, vp, i32, P(i32)]
+    L.lskum_get_forces.argtypes = [vp, P(d), P(d)]
+    L.lskum_get_order.argtypes = [vp, vp, vp, P(i32)]
+    L.lskum_get_info.argtypes = [vp, P(i32), P(i32), P(i32)]
+    L.lskum_time_phases.argtypes = [vp, i32, vp]
+    L.lskum_last_error.argtypes = [vp]
+    L.lskum_last_error.restype = C.c_char_p
+    L.lskum_destroy.argtypes = [vp]
+    L.lskum_destroy.restype = None
+    for f in ("lskum_create", "lskum_set_state", "lskum_set_conserved", "lskum_run", "lskum_enqueue", "lskum_wait",
+              "lskum_get_state", "lskum_get_field", "lskum_get_residuals", "lskum_get_forces", "lskum_get_order",
+              "lskum_get_info", "lskum_time_phases"):
+        getattr(L, f).restype = st
+    _lib = L
+    return L
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class Solver:
+    """One context of liblskum for one cloud and one flow condition."""
+
+    def __init__(self, cloud, mach, aoa_deg, cfl=100.0, inner_iters=3, jvp=JVP_EXACT, cfl_ramp_iters=0.0,
+                 first_order_iters=0, stream=None):
+        L = load()
+        self.n = int(cloud.n)
+        self._arrays = [np.ascontiguousarray(cloud.x, np.float64), np.ascontiguousarray(cloud.y, np.float64),
+                        np.ascontiguousarray(cloud.flag, np.uint8), np.ascontiguousarray(cloud.nx, np.float64),
+                        np.ascontiguousarray(cloud.ny, np.float64), np.ascontiguousarray(cloud.nbr_off, np.int32),
+                        np.ascontiguousarray(cloud.nbr_idx, np.int32)]
+        cl = lskum_cloud(self.n, *[a.ctypes.data for a in self._arrays])
+        op = lskum_opts(mach, aoa_deg, cfl, cfl_ramp_iters, inner_iters, jvp, 0, first_order_iters)
+        h = C.c_void_p()
+        s = L.lskum_create(C.byref(cl), C.byref(op), C.c_void_p(stream), C.byref(h))
+        self._arrays = None
+        if s != 0:
+            raise LskumError(s, L.lskum_last_error(None).decode())
+        self._h = h
+        self.mach, self.aoa_deg = mach, aoa_deg
+
+    def _check(self, s):
+        if s != 0:
+            raise LskumError(s, load().lskum_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().lskum_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # --- state ---
+    def set_state(self, rho, u, v, p):
+        a = [np.ascontiguousarray(t, np.float64) for t in (rho, u, v, p)]
+        self._check(load().lskum_set_state(self._h, *[_p(t) for t in a]))
+
+    def set_conserved(self, U):
+        U = np.ascontiguousarray(U, np.float64).reshape(self.n, 4)
+        self._check(load().lskum_set_conserved(self._h, _p(U)))
+
+    def get_state(self):
+        out = [np.empty(self.n) for _ in range(4)]
+        self._check(load().lskum_get_state(self._h, *[_p(t) for t in out]))
+        return tuple(out)
+
+    def field(self, which):
+        out = np.empty(self.n if which == FIELD_D else (self.n, 4))
+        self._check(load().lskum_get_field(self._h, int(which), _p(out)))
+        return out
+
+    # --- iterations ---
+    def run(self, max_iters, target_drop=0.0, check=True):
+        done = C.c_int32(0)
+        s = load().lskum_run(self._h, int(max_iters), float(target_drop), C.byref(done))
+        if check:
+            self._check(s)
+        return done.value if check else (s, done.value)
+
+    def enqueue(self, max_iters, target_drop=0.0):
+        self._check(load().lskum_enqueue(self._h, int(max_iters), float(target_drop)))
+
+    def wait(self):
+        done = C.c_int32(0)
+        self._check(load().lskum_wait(self._h, C.byref(done)))
+        return done.value
+
+    def stream(self):
+        return load().lskum_stream(self._h)
+
+    # --- outputs ---
+    def residuals(self):
+        n = C.c_int32(0)
+        self._check(load().lskum_get_residuals(self._h, None, 0, C.byref(n)))
+        h = np.empty(max(n.value, 1))
+        self._check(load().lskum_get_residuals(self._h, _p(h), n.value, C.byref(n)))
+        return h[:n.value]
+
+    def forces(self):
+        cl, cd = C.c_double(), C.c_double()
+        self._check(load().lskum_get_forces(self._h, C.byref(cl), C.byref(cd)))
+        return cl.value, cd.value
+
+    def order(self):
+        col = np.empty(self.n, np.int32)
+        order = np.empty(self.n, np.int32)
+        nc = C.c_int32(0)
+        self._check(load().lskum_get_order(self._h, _p(col), _p(order), C.byref(nc)))
+        return col, order, nc.value
+
+    PHASES = ("grad", "residual", "norm", "sweep_fwd", "sweep_bwd", "update")
+
+    def time_phases(self, reps):
+        """Mean device ms per iteration of each phase (CUDA events, library stream)."""
+        ms = np.zeros(6)
+        self._check(load().lskum_time_phases(self._h, int(reps), _p(ms)))
+        return dict(zip(self.PHASES, ms.tolist()))
+
+    def info(self):
+        a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
+        self._check(load().lskum_get_info(self._h, C.byref(a), C.byref(b), C.byref(c)))
+        return dict(n_points=a.value, n_colours=b.value, launches_per_iter=c.value)

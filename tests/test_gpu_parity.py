@@ -1,0 +1,207 @@
+"""CUDA path (through the C-ABI) against the FP64 CPU oracle, element by element.
+
+Tolerances (derived from the arithmetic): the GPU evaluates the same
+formulas with a different association of the same sums (per-slot LS weights
+instead of the 2x2 solve of Eq. 11), fused multiply-adds, beta^(-5/2) instead
+of exp(-ln(beta)/(gamma-1)) and CUDA's erf/exp/log (<= 2 ulp) instead of
+glibc's.  Each evaluated quantity therefore differs by a few ulp of the terms
+that form it.  A residual is a sum of differences of fluxes of size |G| times
+weights of size 1/h, so its error is measured against max|R| over the cloud
+(normwise), not per entry; the same for the increments.  Per iteration:
+q-derivatives 1e-12, residual / increments / state 1e-10 (normwise),
+diagonal 1e-12 (per entry, a sum of positive terms).  Histories and final
+fields use the benchmark spec's tolerances: 1e-10 relative per history entry and
+1e-9 normwise on the final state.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2406_07441_gb300 import cloudgen as cg
+from tests.conftest import cached_cloud
+
+pytestmark = pytest.mark.gpu
+
+
+def _lskum():
+    from paper_2406_07441_gb300 import lskum
+    return lskum
+
+
+def nrel(a, b):
+    """normwise relative difference max|a - b| / max|b|"""
+    s = np.max(np.abs(b))
+    return float(np.max(np.abs(a - b)) / (s if s > 0 else 1.0))
+
+
+CLOUDS = {
+    "ogrid40x16": lambda: cg.naca0012_block(40, 16),
+    "jit48x20": lambda: cg.naca0012_jittered(48, 20, seed=11),
+    "box9": lambda: cg.cartesian_box(9, 9, seed=2, wall_bottom=True),
+    "naca160x64": lambda: cg.naca0012_block(160, 64),
+}
+COND = dict(mach=0.63, aoa_deg=2.0)
+
+
+def _pair(name, jvp=0, K=3, cfl=100.0, **cond):
+    cond = {**COND, **cond}
+    c = cached_cloud(name, CLOUDS[name])
+    s = _lskum().Solver(c, cond["mach"], cond["aoa_deg"], cfl=cfl, inner_iters=K, jvp=jvp)
+    o = O.Oracle(c)
+    return c, s, o, cond
+
+
+@pytest.mark.parametrize("name", ["ogrid40x16", "jit48x20", "box9", "naca160x64"])
+def test_colouring_and_sweep_order_match_oracle(name):
+    c, s, o, _ = _pair(name)
+    col, order, nc = s.order()
+    assert nc == o.ncolours
+    assert np.array_equal(col, o.colour)
+    assert np.array_equal(order, o.order)
+
+
+@pytest.mark.parametrize("name", ["ogrid40x16", "jit48x20", "box9", "naca160x64"])
+@pytest.mark.parametrize("jvp", [0, 1])
+def test_one_iteration_every_field(name, jvp):
+    lk = _lskum()
+    c, s, o, cond = _pair(name, jvp=jvp)
+    U0 = o.initial_state(cond["mach"], cond["aoa_deg"])
+    assert nrel(s.field(lk.FIELD_U), U0) < 1e-15
+    r = o.run(U0, 1, cfl=100.0, K=3, jvp=jvp)
+    assert r["status"] == 0
+    assert s.run(1) == 1
+    assert nrel(s.field(lk.FIELD_QX), r["qx"]) < 1e-12
+    assert nrel(s.field(lk.FIELD_QY), r["qy"]) < 1e-12
+    assert nrel(s.field(lk.FIELD_R), r["R"]) < 1e-10
+    D = s.field(lk.FIELD_D)
+    assert np.max(np.abs(D - r["D"]) / np.abs(r["D"])) < 1e-12
+    assert nrel(s.field(lk.FIELD_DUS), r["dUs"]) < 1e-10
+    assert nrel(s.field(lk.FIELD_DU), r["dU"]) < 1e-10
+    assert nrel(s.field(lk.FIELD_U), r["U"]) < 1e-12
+    assert nrel(s.field(lk.FIELD_Q), r["q"]) < 1e-12
+    h = s.residuals()
+    assert h.shape == (1,) and abs(h[0] - r["hist"][0]) <= 1e-12 * r["hist"][0]
+
+
+def test_sweeps_from_the_same_residual_are_level_parallel_exact():
+    """Sweep increments depend only on R, D and U: feeding the oracle the GPU's own
+    R and D must reproduce the GPU's increments to rounding (checks the level
+    schedule reproduces the sequential Gauss-Seidel order)."""
+    lk = _lskum()
+    c, s, o, cond = _pair("jit48x20")
+    U0 = o.initial_state(cond["mach"], cond["aoa_deg"])
+    s.run(1)
+    R, D = s.field(lk.FIELD_R), s.field(lk.FIELD_D)
+    dUs, dU = o.sweeps(U0, R, D, 0)
+    assert nrel(s.field(lk.FIELD_DUS), dUs) < 1e-12
+    assert nrel(s.field(lk.FIELD_DU), dU) < 1e-12
+
+
+@pytest.mark.parametrize("jvp,iters", [(0, 300), (1, 100)])
+def test_history_and_final_fields_config1(jvp, iters):
+    """NACA 0012, 160x64 = 10,240 points, M = 0.63, AoA = 2 deg, CFL 100."""
+    lk = _lskum()
+    c, s, o, cond = _pair("naca160x64", jvp=jvp)
+    U0 = o.initial_state(cond["mach"], cond["aoa_deg"])
+    r = o.run(U0, iters, cfl=100.0, K=3, jvp=jvp)
+    assert r["status"] == 0 and r["done"] == iters
+    assert s.run(iters) == iters
+    h = s.residuals()
+    rel = np.abs(h - r["hist"]) / r["hist"]
+    assert rel.max() < 1e-10, (rel.argmax(), rel.max())
+    assert nrel(s.field(lk.FIELD_U), r["U"]) < 1e-9
+    cl, cd = s.forces()
+    cl_o, cd_o = o.forces(r["U"], cond["mach"], cond["aoa_deg"])
+    assert abs(cl - cl_o) < 1e-9 and abs(cd - cd_o) < 1e-9
+
+
+def test_stops_at_the_same_iteration_as_the_oracle():
+    c, s, o, cond = _pair("naca160x64")
+    U0 = o.initial_state(cond["mach"], cond["aoa_deg"])
+    r = o.run(U0, 100, cfl=100.0, K=3, target=0.4)
+    assert r["status"] == 0
+    done = s.run(100, target_drop=0.4)
+    assert done == r["done"] < 100
+    assert s.run(5) == 5  # a stopped run can be continued
+
+
+@pytest.mark.parametrize("name", ["jit48x20", "naca160x64"])
+def test_first_order_start_then_second_order(name):
+    """Iterations n <= first_order_iters use q~ = q; the switch happens at the same
+    iteration on both sides."""
+    lk = _lskum()
+    c = cached_cloud(name, CLOUDS[name])
+    s = lk.Solver(c, 0.8, 1.25, first_order_iters=3)
+    o = O.Oracle(c)
+    r = o.run(o.initial_state(0.8, 1.25), 6, cfl=100.0, K=3, first_order=3)
+    assert r["status"] == 0 and s.run(6) == 6
+    h = s.residuals()
+    assert np.max(np.abs(h - r["hist"]) / r["hist"]) < 1e-10
+    assert nrel(s.field(lk.FIELD_U), r["U"]) < 1e-11
+    assert nrel(s.field(lk.FIELD_R), r["R"]) < 1e-10
+
+
+def test_checkpoint_resume_is_bitwise():
+    lk = _lskum()
+    c = cached_cloud("jit48x20", CLOUDS["jit48x20"])
+    a = lk.Solver(c, 0.8, 1.25)
+    a.run(20)
+    b = lk.Solver(c, 0.8, 1.25)
+    b.run(10)
+    U10 = b.field(lk.FIELD_U)
+    b2 = lk.Solver(c, 0.8, 1.25)
+    b2.run(10)
+    b2.set_conserved(U10)
+    b2.run(10)
+    assert np.array_equal(a.field(lk.FIELD_U), b2.field(lk.FIELD_U))
+    assert np.array_equal(a.residuals(), b2.residuals())
+
+
+def test_enqueue_wait_equals_run():
+    lk = _lskum()
+    c = cached_cloud("ogrid40x16", CLOUDS["ogrid40x16"])
+    a = lk.Solver(c, 0.63, 2.0)
+    a.run(7)
+    b = lk.Solver(c, 0.63, 2.0)
+    b.enqueue(7)
+    assert b.wait() == 7
+    assert np.array_equal(a.field(lk.FIELD_U), b.field(lk.FIELD_U))
+
+
+def test_set_state_round_trip_and_rejects_nonphysical():
+    lk = _lskum()
+    c = cached_cloud("ogrid40x16", CLOUDS["ogrid40x16"])
+    s = lk.Solver(c, 0.5, 0.0)
+    rho, u, v, p = s.get_state()
+    assert np.allclose(rho, 1.0) and np.allclose(p[c.flag != cg.WALL], 1 / 1.4)
+    bad = rho.copy()
+    bad[7] = -1.0
+    with pytest.raises(lk.LskumError) as ei:
+        s.set_state(bad, u, v, p)
+    assert ei.value.status == -3
+    rho2, *_ = s.get_state()
+    assert np.array_equal(rho2, rho)
+
+
+def test_config2_full_size():
+    """Jittered 640x256 cloud, 10% removed: 147,584 points, M = 0.85, AoA = 1 deg,
+    exact JVPs, the bench's launch configuration: one first-order start-up
+    iteration and two second-order ones, every field of the last."""
+    lk = _lskum()
+    c = cached_cloud("jit640x256", lambda: cg.build_workload("naca0012_640x256_jit"))
+    assert c.n == 147584
+    s = lk.Solver(c, 0.85, 1.0, first_order_iters=1)
+    o = O.Oracle(c)
+    U0 = o.initial_state(0.85, 1.0)
+    r = o.run(U0, 3, cfl=100.0, K=3, first_order=1)
+    assert r["status"] == 0
+    assert s.run(3) == 3
+    assert nrel(s.field(lk.FIELD_QX), r["qx"]) < 1e-12
+    assert nrel(s.field(lk.FIELD_R), r["R"]) < 1e-10
+    D = s.field(lk.FIELD_D)
+    assert np.max(np.abs(D - r["D"]) / np.abs(r["D"])) < 1e-12
+    assert nrel(s.field(lk.FIELD_DUS), r["dUs"]) < 1e-10
+    assert nrel(s.field(lk.FIELD_DU), r["dU"]) < 1e-10
+    assert nrel(s.field(lk.FIELD_U), r["U"]) < 1e-12
+    h = s.residuals()
+    assert np.max(np.abs(h - r["hist"]) / r["hist"]) < 1e-10

@@ -1,0 +1,82 @@
+"""CPU-side checks of the C-ABI library: it builds, loads, exports every symbol
+include/lskum.h declares, and rejects bad clouds before touching the GPU."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2406_07441_gb300 import cloudgen as cg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lk():
+    from paper_2406_07441_gb300 import build, lskum
+    build.build()
+    lskum.load()
+    return lskum
+
+
+def test_exports_every_declared_symbol(lk):
+    hdr = open(os.path.join(ROOT, "include", "lskum.h")).read()
+    names = set(re.findall(r"\b(lskum_[a-z_]+)\s*\(", hdr))
+    assert len(names) >= 15
+    L = lk.load()
+    missing = [n for n in sorted(names) if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def _cloud_copy(c):
+    return cg.Cloud(c.x.copy(), c.y.copy(), c.flag.copy(), c.nx.copy(), c.ny.copy(), c.nbr_off.copy(),
+                    c.nbr_idx.copy(), dict(c.meta))
+
+
+@pytest.mark.parametrize("defect", ["self", "range", "dup", "flag", "nan", "offsets", "normal"])
+def test_bad_clouds_are_rejected_on_the_host(lk, defect):
+    c = _cloud_copy(cg.naca0012_block(40, 16))
+    if defect == "self":
+        c.nbr_idx[c.nbr_off[5]] = 5
+    elif defect == "range":
+        c.nbr_idx[3] = c.n
+    elif defect == "dup":
+        c.nbr_idx[c.nbr_off[50] + 1] = c.nbr_idx[c.nbr_off[50]]
+    elif defect == "flag":
+        c.flag[9] = 7
+    elif defect == "nan":
+        c.x[11] = np.nan
+    elif defect == "offsets":
+        c.nbr_off[4] = c.nbr_off[5] + 1
+    elif defect == "normal":
+        c.nx[2] *= 2.0
+    with pytest.raises(lk.LskumError) as ei:
+        lk.Solver(c, 0.5, 1.0)
+    assert ei.value.status == -1
+
+
+def test_degenerate_split_stencil_is_rejected(lk):
+    c = _cloud_copy(cg.cartesian_box(7, 7, seed=1))
+    # an interior point whose neighbours all lie on its left: no x- sub-stencil
+    p = 24
+    x, y = c.x, c.y
+    left = [q for q in range(c.n) if x[q] < x[p] - 1e-9 and q != p]
+    left = sorted(left, key=lambda q: (x[q] - x[p]) ** 2 + (y[q] - y[p]) ** 2)[:6]
+    rows = [list(c.nbr_idx[c.nbr_off[k]:c.nbr_off[k + 1]]) for k in range(c.n)]
+    rows[p] = left
+    off = np.zeros(c.n + 1, np.int32)
+    off[1:] = np.cumsum([len(r) for r in rows])
+    c.nbr_off = off
+    c.nbr_idx = np.concatenate([np.array(r, np.int32) for r in rows])
+    with pytest.raises(lk.LskumError) as ei:
+        lk.Solver(c, 0.5, 1.0)
+    assert ei.value.status == -2
+    assert "point 24" in str(ei.value)
+
+
+def test_bad_options_are_rejected(lk):
+    c = cg.naca0012_block(40, 16)
+    for kw in (dict(cfl=0.0), dict(inner_iters=-1), dict(jvp=5)):
+        with pytest.raises(lk.LskumError) as ei:
+            lk.Solver(c, 0.5, 1.0, **kw)
+        assert ei.value.status == -1
