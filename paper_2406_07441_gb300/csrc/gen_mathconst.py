@@ -1,0 +1,115 @@
+"""Generate lskum_mathconst.h: constants of the kernels' own FP64 exp and erfcx.
+
+Run from the repository root:  python paper_2406_07441_gb300/csrc/gen_mathconst.py
+(needs mpmath; the generated header is committed, so building does not).
+
+exp (table-driven, after P. T. P. Tang, "Table-driven implementation of the
+exponential function in IEEE floating-point arithmetic", ACM TOMS 15(2), 1989):
+  x = (64 m + j) ln2/64 + r, |r| <= ln2/128,  exp(x) = 2^m * 2^(j/64) * e^r,
+  2^(j/64) tabulated (correctly rounded), e^r - 1 by its Taylor polynomial of
+  degree 5 (truncation < 4e-17 relative on |r| <= ln2/128).
+
+erfcx(x) = exp(x^2) erfc(x) for 0 <= x <= 9: on each interval [a, b] the
+Chebyshev interpolant of degree 17 at Chebyshev points of the first kind,
+rewritten as a polynomial in t = (x - c)/h (c, h the interval's centre and
+half width) and evaluated by Horner's rule; every interval reaches a relative
+error of about 2e-16 in double arithmetic.  The kernels use it as
+  A = (1 + s erf S)/2 = 1 - E (s S >= 0)  or  E (s S < 0),
+  E = exp(-S^2) erfcx(|S|) / 2,
+which shares exp(-S^2) with the B term of the split flux and is accurate in
+absolute terms for every S (the kernels clamp |S| to 9, where E < 1e-36).
+"""
+import os
+import struct
+
+import mpmath as mp
+
+mp.mp.dps = 60
+HERE = os.path.dirname(os.path.abspath(__file__))
+OUT = os.path.join(HERE, "lskum_mathconst.h")
+
+INTERVALS = [(0.0, 0.75), (0.75, 1.75), (1.75, 3.25), (3.25, 5.5), (5.5, 9.0)]
+DEGREE = 17
+
+
+def erfcx(x):
+    return mp.exp(x * x) * mp.erfc(x)
+
+
+def cheb_monomial(f, a, b, n):
+    a, b = mp.mpf(a), mp.mpf(b)
+    c, h = (a + b) / 2, (b - a) / 2
+    N = n + 1
+    xs = [mp.cos(mp.pi * (k + mp.mpf(1) / 2) / N) for k in range(N)]
+    fs = [f(c + h * t) for t in xs]
+    ck = [2 * mp.fsum(fs[k] * mp.cos(mp.pi * j * (k + mp.mpf(1) / 2) / N) for k in range(N)) / N
+          for j in range(N)]
+    ck[0] /= 2
+    T = [[mp.mpf(1)], [mp.mpf(0), mp.mpf(1)]]
+    for j in range(2, N):
+        new = [mp.mpf(0)] * (j + 1)
+        for i, v in enumerate(T[j - 1]):
+            new[i + 1] += 2 * v
+        for i, v in enumerate(T[j - 2]):
+            new[i] -= v
+        T.append(new)
+    mono = [mp.mpf(0)] * N
+    for j in range(N):
+        for i, v in enumerate(T[j]):
+            mono[i] += ck[j] * v
+    return mono, c, h
+
+
+def hexd(v):
+    return float(v).hex()
+
+
+def main():
+    lines = [
+        "// Generated by gen_mathconst.py (mpmath, 60 digits); do not edit.",
+        "// Constants of the kernels' own FP64 exp and erfcx; see gen_mathconst.py for the methods.",
+        "#pragma once",
+        "",
+        "namespace lskum {",
+        "",
+        f"constexpr double kExpInvLn2_64 = {hexd(64 / mp.log(2))};  // 64 / ln 2",
+    ]
+    ln2_64 = mp.log(2) / 64
+    # high part: ln2/64 with the low 24 significand bits cleared, so that k * hi
+    # is exact for the |k| < 2^17 that finite results need
+    bits = int.from_bytes(struct.pack(">d", float(ln2_64)), "big") & ~((1 << 24) - 1)
+    fhi = struct.unpack(">d", bits.to_bytes(8, "big"))[0]
+    flo = float(ln2_64 - mp.mpf(fhi))
+    lines += [
+        f"constexpr double kExpLn2_64Hi = {fhi.hex()};  // ln2/64, 29 significant bits",
+        f"constexpr double kExpLn2_64Lo = {flo.hex()};  // ln2/64 - kExpLn2_64Hi",
+        "// 2^(j/64), j = 0..63, correctly rounded",
+        "__constant__ double kExpTable[64] = {",
+    ]
+    for j in range(0, 64, 4):
+        lines.append("    " + ", ".join(hexd(mp.power(2, mp.mpf(k) / 64)) for k in range(j, j + 4)) + ",")
+    lines.append("};")
+    lines.append(f"constexpr int kErfcxDeg = {DEGREE};")
+    lines.append("// interval bounds (upper limits of intervals 0..3), scale 1/h and offset -c/h of t = (x - c)/h")
+    lines.append("constexpr double kErfcxBreak[4] = {" + ", ".join(repr(b) for _, b in INTERVALS[:-1]) + "};")
+    coef_rows, sc, off = [], [], []
+    for a, b in INTERVALS:
+        mono, c, h = cheb_monomial(erfcx, a, b, DEGREE)
+        coef_rows.append([hexd(m / 2) for m in mono])  # E = exp(-S^2) * (erfcx/2)
+        sc.append(hexd(1 / h))
+        off.append(hexd(-c / h))
+    lines.append("__constant__ double kErfcxScale[5] = {" + ", ".join(sc) + "};")
+    lines.append("__constant__ double kErfcxOffset[5] = {" + ", ".join(off) + "};")
+    lines.append(f"// erfcx/2 on each interval as a polynomial in t, coefficients of t^0 .. t^{DEGREE}")
+    lines.append(f"__constant__ double kErfcxHalf[5][{DEGREE + 1}] = {{")
+    for row in coef_rows:
+        lines.append("    {" + ", ".join(row) + "},")
+    lines.append("};")
+    lines += ["", "}  // namespace lskum", ""]
+    with open(OUT, "w") as f:
+        f.write("\n".join(lines))
+    print(OUT)
+
+
+if __name__ == "__main__":
+    main()

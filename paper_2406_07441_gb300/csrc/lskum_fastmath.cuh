@@ -1,0 +1,74 @@
+// FP64 elementary functions of the split fluxes, shaped for GB300's scarce
+// FP64 issue rate (1/64 of FP32): everything that can run on the integer
+// pipes (range-reduction index, exponent scaling, interval selection, sign
+// tests) does, and exp(-S^2) is shared between the two places a split flux
+// needs it.  Constants: lskum_mathconst.h (gen_mathconst.py documents the
+// methods and their accuracy); the tables are staged in shared memory because
+// per-thread indices diverge, which serialises constant-cache reads.
+#pragma once
+#include "lskum_mathconst.h"
+
+namespace lskum {
+
+struct MathTables {
+    double exp2j[64];             // 2^(j/64)
+    double ecx[5][kErfcxDeg + 1]; // erfcx/2 per interval, Horner coefficients
+    double sc[5], off[5];         // t = x * sc + off
+};
+
+// Copy the tables into shared memory (all threads of the block; then sync).
+__device__ __forceinline__ void load_math_tables(MathTables &T)
+{
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) T.exp2j[i] = kExpTable[i];
+    for (int i = threadIdx.x; i < 5 * (kErfcxDeg + 1); i += blockDim.x)
+        T.ecx[i / (kErfcxDeg + 1)][i % (kErfcxDeg + 1)] = kErfcxHalf[i / (kErfcxDeg + 1)][i % (kErfcxDeg + 1)];
+    if (threadIdx.x < 5) {
+        T.sc[threadIdx.x] = kErfcxScale[threadIdx.x];
+        T.off[threadIdx.x] = kErfcxOffset[threadIdx.x];
+    }
+}
+
+// exp(x) for |x| <= 700 (Tang's table-driven method): 10 FP64 instructions.
+__device__ __forceinline__ double exp_t(const MathTables &T, double x)
+{
+    const double big = 0x1.8p52;                            // rounds x*64/ln2 into the low word
+    const double t = fma(x, kExpInvLn2_64, big);
+    const int k = __double2loint(t);                        // round(x * 64 / ln2)
+    const double kd = t - big;
+    double r = fma(kd, -kExpLn2_64Hi, x);
+    r = fma(kd, -kExpLn2_64Lo, r);                          // |r| <= ln2/128
+    double h = fma(r, 1.0 / 120.0, 1.0 / 24.0);
+    h = fma(r, h, 1.0 / 6.0);
+    h = fma(r, h, 0.5);
+    const double p = fma(r * r, h, r);                      // e^r - 1
+    const double e = T.exp2j[k & 63];
+    const double res = fma(e, p, e);                        // 2^(j/64) e^r
+    return __hiloint2double(__double2hiint(res) + ((k >> 6) << 20), __double2loint(res));
+}
+
+// E = exp(-S^2) erfcx(|S|)/2 and eS = exp(-S^2); then (1 + erf S)/2 is 1 - E
+// for S >= 0 and E for S < 0, and (1 - erf S)/2 the other one.  |S| is
+// clamped to 9 (E < 1e-36 there), which also keeps exp's argument in range.
+__device__ __forceinline__ void split_E(const MathTables &T, double S, double &E, double &eS)
+{
+    const double a = fmin(fabs(S), 9.0);
+    const int ha = __double2hiint(a);  // positive doubles order like their high words
+    const int iv = (ha >= 0x3fe80000) + (ha >= 0x3ffc0000) + (ha >= 0x400a0000) + (ha >= 0x40160000);
+    const double t = fma(a, T.sc[iv], T.off[iv]);
+    const double *c = T.ecx[iv];
+    double p = c[kErfcxDeg];
+#pragma unroll
+    for (int j = kErfcxDeg - 1; j >= 0; j--) p = fma(p, t, c[j]);
+    eS = exp_t(T, -a * a);
+    E = eS * p;
+}
+
+// A = (1 + sg erf S)/2 (sg = +-1) and eS = exp(-S^2).
+__device__ __forceinline__ void split_A(const MathTables &T, double S, double sg, double &A, double &eS)
+{
+    double E;
+    split_E(T, S, E, eS);
+    A = ((__double2hiint(S) ^ __double2hiint(sg)) >= 0) ? 1.0 - E : E;
+}
+
+}  // namespace lskum

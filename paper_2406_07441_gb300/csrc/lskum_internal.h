@@ -24,6 +24,7 @@ constexpr int kOuter = 2;
 struct Ctrl {
     int32_t stop;        // 1: skip all further work
     int32_t stop_after;  // the drop target was reached: finish this iteration, then stop
+                         // (the next iteration's first kernel sets stop)
     int32_t error;       // lskum_status of a device-detected failure (0 = none)
     int32_t bad_point;   // smallest internal index of a non-physical update
     int32_t it;          // iterations whose residual norm has been recorded
@@ -46,8 +47,8 @@ enum GeoField {
 // Jacobian products (fields of `prim`, stride ld).
 enum PrimField {
     P_RHO, P_IRHO, P_U, P_V, P_P, P_BETA, P_SB, P_ISB, P_I2P, P_Q2, P_E1, P_E2,
-    P_SX, P_ERFX, P_EXPX, P_BX,   // direction (1,0): S, erf S, exp(-S^2), B
-    P_SY, P_ERFY, P_EXPY, P_BY,   // direction (0,1)
+    P_SX, P_APX, P_AMX, P_EXPX, P_BX,  // direction (1,0): S, A+, A-, exp(-S^2), B
+    P_SY, P_APY, P_AMY, P_EXPY, P_BY,  // direction (0,1)
     P_NFIELDS
 };
 

@@ -15,10 +15,14 @@
 // neighbour slot; the inverse of Eq. 14 uses beta^(-5/2) instead of a log;
 // the sweeps' Jacobian products reuse erf/exp of each point's own state,
 // computed once per iteration by k_update, so an exact product has no
-// transcendental call at all.
+// transcendental call at all; exp and A = (1 + s erf S)/2 are the kernels' own
+// (lskum_fastmath.cuh), which share exp(-S^2) and keep index work off the
+// FP64 pipe.
 #include "lskum_internal.h"
 
 #include <cstdint>
+
+#include "lskum_fastmath.cuh"
 
 namespace lskum {
 
@@ -29,10 +33,13 @@ constexpr double kInv2SqrtPi = 0.28209479177387814347;    // 1 / (2 sqrt(pi))
 constexpr double kInvSqrtPi = 0.56418958354775628695;     // 1 / sqrt(pi)
 constexpr unsigned kFull = 0xffffffffu;
 
+// Every kernel returns at once after a stop or a failure.  k_norm only sets
+// stop_after, so the sweeps and the update of the iteration that reached the
+// drop target still run; k_begin turns it into stop at the start of the next.
 __device__ __forceinline__ bool halted(const Ctrl *c)
 {
     const volatile Ctrl *v = c;
-    return (v->stop | v->stop_after | v->error) != 0;
+    return (v->stop | v->error) != 0;
 }
 
 // Primitive state carried through the residual.
@@ -43,40 +50,53 @@ struct Prim {
 
 // Inverse of Eq. 14: beta = -q4/2, u = q2/(2 beta), v = q3/(2 beta),
 // rho = exp(q1 + beta |u|^2) beta^(-1/(gamma-1)) with 1/(gamma-1) = 5/2,
-// p = rho/(2 beta).  One division, one square root, one exp.
-__device__ __forceinline__ Prim q_to_prim(const double q[4])
+// p = rho/(2 beta).  One reciprocal square root and one exp.
+__device__ __forceinline__ Prim q_to_prim(const MathTables &T, const double q[4])
 {
     Prim P;
     const double beta = -0.5 * q[3];
-    P.sb = sqrt(beta);
-    const double r = 1.0 / (beta * beta * P.sb);  // beta^(-5/2)
-    const double i2b = 0.5 * beta * P.sb * r;     // 1/(2 beta)
-    P.isb = beta * beta * r;                      // beta^(-1/2)
+    P.isb = rsqrt(beta);
+    const double ib = P.isb * P.isb;   // 1/beta
+    const double r = ib * ib * P.isb;  // beta^(-5/2)
+    const double i2b = 0.5 * ib;       // 1/(2 beta)
+    P.sb = beta * P.isb;
     P.u = q[1] * i2b;
     P.v = q[2] * i2b;
     const double q2 = P.u * P.u + P.v * P.v;
-    P.rho = exp(q[0] + beta * q2) * r;
+    P.rho = exp_t(T, fma(beta, q2, q[0])) * r;
     P.p = P.rho * i2b;
     const double k = 0.5 * P.rho * q2;
-    P.e1 = 3.5 * P.p + k;
-    P.e2 = 3.0 * P.p + k;
+    P.e1 = fma(3.5, P.p, k);
+    P.e2 = fma(3.0, P.p, k);
     return P;
 }
 
 // Kinetic split flux G_d^sg (half-range moments of the Maxwellian, sg = +-1)
-// in unit direction (dx, dy).
-__device__ __forceinline__ void split_flux(const Prim &P, double dx, double dy, double sg, double G[4])
+// in unit direction d: DIR 0 is (1,0), DIR 1 is (0,1), DIR 2 is (dx, dy).
+template <int DIR>
+__device__ __forceinline__ void split_flux(const MathTables &T, const Prim &P, double dx, double dy, double sg,
+                                          double G[4])
 {
-    const double ud = P.u * dx + P.v * dy;
+    const double ud = DIR == 0 ? P.u : (DIR == 1 ? P.v : P.u * dx + P.v * dy);
     const double S = ud * P.sb;
-    const double A = 0.5 + 0.5 * sg * erf(S);
-    const double B = exp(-S * S) * kInv2SqrtPi * P.isb;
-    const double M1 = ud * A + sg * B;
+    double A, eS;
+    split_A(T, S, sg, A, eS);
+    const double B = eS * kInv2SqrtPi * P.isb;
+    const double M1 = fma(ud, A, sg * B);
     const double rm = P.rho * M1;
+    const double pA = P.p * A;
     G[0] = rm;
-    G[1] = rm * P.u + P.p * dx * A;
-    G[2] = rm * P.v + P.p * dy * A;
-    G[3] = ud * P.e1 * A + sg * P.e2 * B;
+    if (DIR == 0) {
+        G[1] = fma(rm, P.u, pA);
+        G[2] = rm * P.v;
+    } else if (DIR == 1) {
+        G[1] = rm * P.u;
+        G[2] = fma(rm, P.v, pA);
+    } else {
+        G[1] = fma(rm, P.u, pA * dx);
+        G[2] = fma(rm, P.v, pA * dy);
+    }
+    G[3] = fma(ud * P.e1, A, sg * P.e2 * B);
 }
 
 // Primal quantities of a conserved state for the Jacobian products.
@@ -122,9 +142,9 @@ __device__ __forceinline__ PrimU load_primu(const double *__restrict__ pr, int l
 }
 
 // Exact product A_d^sg(U) dl by forward-mode differentiation of
-// U -> (rho, u, v, p) -> (beta, S, A, B) -> G_d^sg.  S, erf S, exp(-S^2) and
-// B of the state are inputs (precomputed per point for d = x, y).
-__device__ __forceinline__ void jvp_exact(const PrimU &P, double dx, double dy, double sg, double S, double er,
+// U -> (rho, u, v, p) -> (beta, S, A, B) -> G_d^sg.  S, A = (1 + sg erf S)/2,
+// exp(-S^2) and B of the state are inputs (precomputed per point for d = x, y).
+__device__ __forceinline__ void jvp_exact(const PrimU &P, double dx, double dy, double sg, double S, double A,
                                           double eS, double B, const double dl[4], double out[4])
 {
     const double drho = dl[0];
@@ -138,7 +158,6 @@ __device__ __forceinline__ void jvp_exact(const PrimU &P, double dx, double dy, 
     const double dud = du * dx + dv * dy;
     const double dsb = 0.5 * dbeta * P.isb;
     const double dS = dud * P.sb + ud * dsb;
-    const double A = 0.5 + 0.5 * sg * er;
     const double dA = sg * eS * dS * kInvSqrtPi;
     const double dB = -B * (2.0 * S * dS + dsb * P.isb);
     const double M1 = ud * A + sg * B;
@@ -153,19 +172,22 @@ __device__ __forceinline__ void jvp_exact(const PrimU &P, double dx, double dy, 
     out[3] = (dud * P.e1 + ud * de1) * A + ud * P.e1 * dA + sg * (de2 * B + P.e2 * dB);
 }
 
-__device__ __forceinline__ void flux_cons(const double U[4], double dx, double dy, double sg, double G[4])
+__device__ __forceinline__ void flux_cons(const MathTables &T, const double U[4], double dx, double dy, double sg,
+                                          double G[4])
 {
     const PrimU P = prim_from_cons(U);
     const double ud = P.u * dx + P.v * dy;
     const double S = ud * P.sb;
-    const double A = 0.5 + 0.5 * sg * erf(S);
-    const double B = exp(-S * S) * kInv2SqrtPi * P.isb;
-    const double M1 = ud * A + sg * B;
+    double A, eS;
+    split_A(T, S, sg, A, eS);
+    const double B = eS * kInv2SqrtPi * P.isb;
+    const double M1 = fma(ud, A, sg * B);
     const double rm = P.rho * M1;
+    const double pA = P.p * A;
     G[0] = rm;
-    G[1] = rm * P.u + P.p * dx * A;
-    G[2] = rm * P.v + P.p * dy * A;
-    G[3] = ud * P.e1 * A + sg * P.e2 * B;
+    G[1] = fma(rm, P.u, pA * dx);
+    G[2] = fma(rm, P.v, pA * dy);
+    G[3] = fma(ud * P.e1, A, sg * P.e2 * B);
 }
 
 template <int TPP>
@@ -242,7 +264,10 @@ __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const doub
                                                   const double *__restrict__ gy)
 {
     __shared__ double red[32];
+    __shared__ MathTables T;
     if (halted(d.ctrl)) return;
+    load_math_tables(T);
+    __syncthreads();
     const int n1 = ((const volatile Ctrl *)d.ctrl)->it + 1;
     const double cfl = (d.ramp > 0.0 && (double)n1 < d.ramp) ? d.cfl * ((double)n1 / d.ramp) : d.cfl;
     const double hc = n1 <= d.first_order ? 0.0 : 0.5;  // first-order start: q~ = q
@@ -253,6 +278,7 @@ __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const doub
     const int ld = d.ld;
     const int fl = d.flag[kk];
     const bool work = active && fl != kOuter;
+    const bool wall = fl == kWall;
     const double *__restrict__ q = st.q;
     double R[4] = {0.0, 0.0, 0.0, 0.0};
     const double e1x = d.geo[G_E1X * ld + kk], e1y = d.geo[G_E1Y * ld + kk];
@@ -279,25 +305,35 @@ __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const doub
                 qi[c] = q[c * ld + i] - hc * (dx * gx[c * ld + i] + dy * gy[c * ld + i]);
                 q0t[c] = q0[c] - hc * (dx * gx0[c] + dy * gy0[c]);
             }
-            const Prim Pi = q_to_prim(qi);
-            const Prim P0 = q_to_prim(q0t);
+            const Prim Pi = q_to_prim(T, qi);
+            const Prim P0 = q_to_prim(T, q0t);
             if (mb & 3) {
                 const double sg = (mb & 1) ? 1.0 : -1.0;
                 const double w = d.w1[e];
                 double Gi[4], G0[4];
-                split_flux(Pi, e1x, e1y, sg, Gi);
-                split_flux(P0, e1x, e1y, sg, G0);
+                if (wall) {
+                    split_flux<2>(T, Pi, e1x, e1y, sg, Gi);
+                    split_flux<2>(T, P0, e1x, e1y, sg, G0);
+                } else {
+                    split_flux<0>(T, Pi, 1.0, 0.0, sg, Gi);
+                    split_flux<0>(T, P0, 1.0, 0.0, sg, G0);
+                }
 #pragma unroll
-                for (int c = 0; c < 4; c++) R[c] += w * (Gi[c] - G0[c]);
+                for (int c = 0; c < 4; c++) R[c] = fma(w, Gi[c] - G0[c], R[c]);
             }
             if (mb & 12) {
                 const double sg = (mb & 4) ? 1.0 : -1.0;
                 const double w = d.w2[e];
                 double Gi[4], G0[4];
-                split_flux(Pi, e2x, e2y, sg, Gi);
-                split_flux(P0, e2x, e2y, sg, G0);
+                if (wall) {
+                    split_flux<2>(T, Pi, e2x, e2y, sg, Gi);
+                    split_flux<2>(T, P0, e2x, e2y, sg, G0);
+                } else {
+                    split_flux<1>(T, Pi, 0.0, 1.0, sg, Gi);
+                    split_flux<1>(T, P0, 0.0, 1.0, sg, G0);
+                }
 #pragma unroll
-                for (int c = 0; c < 4; c++) R[c] += w * (Gi[c] - G0[c]);
+                for (int c = 0; c < 4; c++) R[c] = fma(w, Gi[c] - G0[c], R[c]);
             }
         }
     }
@@ -386,7 +422,10 @@ __global__ void __launch_bounds__(1024) k_norm(Dev d)
 template <int JVP, bool FWD>
 __global__ void __launch_bounds__(256) k_sweep(Dev d, StateSet st, int lb, int le, int cb_lo, int cb_hi)
 {
+    __shared__ MathTables T;
     if (halted(d.ctrl)) return;
+    load_math_tables(T);
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int k = lb + (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (k >= le) return;  // warp-uniform
@@ -418,21 +457,20 @@ __global__ void __launch_bounds__(256) k_sweep(Dev d, StateSet st, int lb, int l
                 const double sg = (m & 1) ? 1.0 : -1.0;
                 const double w = s == 0 ? d.w1[e] : d.w2[e];
                 const double ddx = s == 0 ? e1x : e2x, ddy = s == 0 ? e1y : e2y;
-                double S, er, eS, B;
+                double S, A, eS, B;
                 if (!wall) {
                     // interior frame: d = (1,0) or (0,1), precomputed per point
                     const int f = s == 0 ? P_SX : P_SY;
                     S = pr[f * ld + i];
-                    er = pr[(f + 1) * ld + i];
-                    eS = pr[(f + 2) * ld + i];
-                    B = pr[(f + 3) * ld + i];
+                    A = pr[(sg > 0.0 ? f + 1 : f + 2) * ld + i];
+                    eS = pr[(f + 3) * ld + i];
+                    B = pr[(f + 4) * ld + i];
                 } else {
                     S = (P.u * ddx + P.v * ddy) * P.sb;
-                    er = erf(S);
-                    eS = exp(-S * S);
+                    split_A(T, S, sg, A, eS);
                     B = eS * kInv2SqrtPi * P.isb;
                 }
-                jvp_exact(P, ddx, ddy, sg, S, er, eS, B, dl, J);
+                jvp_exact(P, ddx, ddy, sg, S, A, eS, B, dl, J);
 #pragma unroll
                 for (int c = 0; c < 4; c++) acc[c] += w * J[c];
             }
@@ -451,8 +489,8 @@ __global__ void __launch_bounds__(256) k_sweep(Dev d, StateSet st, int lb, int l
                 const double w = s == 0 ? d.w1[e] : d.w2[e];
                 const double ddx = s == 0 ? e1x : e2x, ddy = s == 0 ? e1y : e2y;
                 double G1[4], G0[4];
-                flux_cons(Up, ddx, ddy, sg, G1);
-                flux_cons(Ui, ddx, ddy, sg, G0);
+                flux_cons(T, Up, ddx, ddy, sg, G1);
+                flux_cons(T, Ui, ddx, ddy, sg, G0);
 #pragma unroll
                 for (int c = 0; c < 4; c++) acc[c] += w * (G1[c] - G0[c]);
             }
@@ -488,13 +526,18 @@ __global__ void __launch_bounds__(256) k_sweep(Dev d, StateSet st, int lb, int l
 // ---------------------------------------------------------------------------
 // state update (set cur -> set 1-cur) and per-point quantities of the new state
 // ---------------------------------------------------------------------------
+__global__ void k_begin(Ctrl *c)
+{
+    if (c->stop_after) c->stop = 1;
+}
+
 template <bool INC>
 __global__ void __launch_bounds__(256) k_update(Dev d, int cur)
 {
-    if (INC) {
-        const volatile Ctrl *v = d.ctrl;
-        if (v->stop | v->error) return;  // stop_after: this iteration still updates
-    }
+    __shared__ MathTables T;
+    if (INC && halted(d.ctrl)) return;
+    load_math_tables(T);
+    __syncthreads();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= d.n) return;
     const int ld = d.ld;
@@ -542,13 +585,17 @@ __global__ void __launch_bounds__(256) k_update(Dev d, int cur)
     pr[P_E1 * ld + k] = P.e1;
     pr[P_E2 * ld + k] = P.e2;
     const double sx = P.u * P.sb, sy = P.v * P.sb;
-    const double ex = exp(-sx * sx), ey = exp(-sy * sy);
+    double Ex, ex, Ey, ey;
+    split_E(T, sx, Ex, ex);
+    split_E(T, sy, Ey, ey);
     pr[P_SX * ld + k] = sx;
-    pr[P_ERFX * ld + k] = erf(sx);
+    pr[P_APX * ld + k] = sx >= 0.0 ? 1.0 - Ex : Ex;
+    pr[P_AMX * ld + k] = sx >= 0.0 ? Ex : 1.0 - Ex;
     pr[P_EXPX * ld + k] = ex;
     pr[P_BX * ld + k] = ex * kInv2SqrtPi * P.isb;
     pr[P_SY * ld + k] = sy;
-    pr[P_ERFY * ld + k] = erf(sy);
+    pr[P_APY * ld + k] = sy >= 0.0 ? 1.0 - Ey : Ey;
+    pr[P_AMY * ld + k] = sy >= 0.0 ? Ey : 1.0 - Ey;
     pr[P_EXPY * ld + k] = ey;
     pr[P_BY * ld + k] = ey * kInv2SqrtPi * P.isb;
 }
@@ -637,7 +684,10 @@ cudaError_t enqueue_phase(const Dev &d, const Launch &L, int cur, int ph, int n_
                           const int32_t *lvl_act_end, const int32_t *lvl_end, cudaStream_t s, int *launches)
 {
     switch (ph) {
-    case 0: return enqueue_grad_res(d, L, cur, s, launches, true, false);
+    case 0:
+        k_begin<<<1, 1, 0, s>>>(d.ctrl);
+        (*launches)++;
+        return enqueue_grad_res(d, L, cur, s, launches, true, false);
     case 1: return enqueue_grad_res(d, L, cur, s, launches, false, true);
     case 2:
         k_norm<<<1, 1024, 0, s>>>(d);

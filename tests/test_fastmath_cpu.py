@@ -1,0 +1,121 @@
+"""The kernels' own FP64 exp and A = (1 + s erf S)/2, emulated on the CPU
+operation by operation (fused multiply-adds rounded once) with the constants
+of the generated header, against mpmath at 60 digits."""
+import os
+import re
+import struct
+
+import numpy as np
+import pytest
+
+mp = pytest.importorskip("mpmath")
+
+HDR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                   "paper_2406_07441_gb300", "csrc", "lskum_mathconst.h")
+
+
+def _consts():
+    s = open(HDR).read()
+
+    def scalar(name):
+        return float.fromhex(re.search(name + r" = ([-0-9a-fx.p+]+);", s).group(1))
+
+    def array(name):
+        body = re.search(name + r"\[[^=]*\] = \{(.*?)\};", s, re.S).group(1)
+        return [float.fromhex(t) for t in re.findall(r"-?0x[0-9a-f.]+p[-+]?\d+", body)]
+
+    deg = int(re.search(r"kErfcxDeg = (\d+);", s).group(1))
+    ecx = np.array(array("kErfcxHalf")).reshape(5, deg + 1)
+    return dict(inv=scalar("kExpInvLn2_64"), hi=scalar("kExpLn2_64Hi"), lo=scalar("kExpLn2_64Lo"),
+                tab=array("kExpTable"), sc=array("kErfcxScale"), off=array("kErfcxOffset"), ecx=ecx, deg=deg)
+
+
+C = _consts()
+mp.mp.prec = 300
+
+
+def fma(a, b, c):
+    return float(mp.mpf(a) * mp.mpf(b) + mp.mpf(c))
+
+
+def mul(a, b):
+    return float(mp.mpf(a) * mp.mpf(b))
+
+
+def hi_word(x):
+    return struct.unpack(">i", struct.pack(">d", x)[:4])[0]
+
+
+def lo_word(x):
+    return struct.unpack(">i", struct.pack(">d", x)[4:])[0]
+
+
+def from_words(h, l):
+    return struct.unpack(">d", struct.pack(">ii", h, l))[0]
+
+
+def exp_t(x):
+    big = float.fromhex("0x1.8p52")
+    t = fma(x, C["inv"], big)
+    k = lo_word(t)
+    kd = t - big
+    r = fma(kd, -C["hi"], x)
+    r = fma(kd, -C["lo"], r)
+    h = fma(r, 1.0 / 120.0, 1.0 / 24.0)
+    h = fma(r, h, 1.0 / 6.0)
+    h = fma(r, h, 0.5)
+    p = fma(mul(r, r), h, r)
+    e = C["tab"][k & 63]
+    res = fma(e, p, e)
+    return from_words(hi_word(res) + ((k >> 6) << 20), lo_word(res))
+
+
+def split_E(S):
+    a = min(abs(S), 9.0)
+    ha = hi_word(a)
+    iv = int(ha >= 0x3fe80000) + int(ha >= 0x3ffc0000) + int(ha >= 0x400a0000) + int(ha >= 0x40160000)
+    t = fma(a, C["sc"][iv], C["off"][iv])
+    c = C["ecx"][iv]
+    p = float(c[C["deg"]])
+    for j in range(C["deg"] - 1, -1, -1):
+        p = fma(p, t, float(c[j]))
+    eS = exp_t(-mul(a, a))
+    return mul(eS, p), eS
+
+
+def ulp(x):
+    return np.spacing(abs(x))
+
+
+def test_exp_within_one_ulp():
+    rng = np.random.default_rng(3)
+    xs = np.concatenate([np.linspace(-700, 700, 401), rng.uniform(-5, 5, 600), rng.uniform(-1e-3, 1e-3, 50)])
+    worst = 0.0
+    for x in xs:
+        ref = mp.exp(mp.mpf(float(x)))
+        got = exp_t(float(x))
+        worst = max(worst, float(abs(mp.mpf(got) - ref)) / ulp(float(ref)))
+    assert worst <= 1.1, worst
+
+
+def test_split_A_absolute_and_tail_accuracy():
+    rng = np.random.default_rng(4)
+    Ss = np.concatenate([np.linspace(-9.5, 9.5, 381), rng.normal(0, 1.0, 400), [0.0, -0.0, 0.75, 1.75, 3.25, 5.5]])
+    worst_abs = 0.0
+    worst = {3.0: [0.0, 0.0], 9.0: [0.0, 0.0]}  # |S| bound -> [tail rel, exp(-S^2) rel]
+    for S in Ss:
+        S = float(S)
+        E, eS = split_E(S)
+        Ap = 1.0 - E if S >= 0 else E
+        ref_p = (1 + mp.erf(mp.mpf(S))) / 2
+        worst_abs = max(worst_abs, float(abs(mp.mpf(Ap) - ref_p)))
+        tail = min(ref_p, 1 - ref_p)  # the side that equals E
+        ref_e = mp.exp(-mp.mpf(S) ** 2)
+        for bound, w in worst.items():
+            if abs(S) <= bound:
+                w[0] = max(w[0], float(abs(mp.mpf(E) - tail) / tail))
+                w[1] = max(w[1], float(abs(mp.mpf(eS) - ref_e) / ref_e))
+    assert worst_abs <= 2.5e-16, worst_abs
+    # exp(-S^2) inherits the rounding of S^2: |S|^2 * 2^-53 relative
+    assert worst[3.0][0] <= 1.5e-15 and worst[3.0][1] <= 1.5e-15, worst
+    assert worst[9.0][0] <= 1.2e-14 and worst[9.0][1] <= 1.2e-14, worst
