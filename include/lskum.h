@@ -185,6 +185,31 @@ lskum_status lskum_time_phases(lskum_ctx *ctx, int32_t reps, double *ms);
 /* Number of points, of colours and of kernel launches one iteration makes. */
 lskum_status lskum_get_info(lskum_ctx *ctx, int32_t *n_points, int32_t *n_colours, int32_t *launches_per_iter);
 
+/*
+ * Density-residual norm without any device allocation (no counterpart in the
+ * paper: a service for callers that cannot allocate device memory, e.g. hosts
+ * whose device memory all belongs to their own pool allocator, loops that must
+ * not take the synchronisation an allocation or free can cause, or deployments
+ * that forbid runtime allocation).
+ *   r_rho_dev  device pointer to n doubles (density residuals; the order does
+ *              not matter; zeros may be included)
+ *   n          0 <= n <= 134,217,728 (8192 partial sums x 256 threads x 64
+ *              elements per thread); larger n returns LSKUM_ERR_ARG
+ *   norm_dev   device pointer to one double: receives sqrt(sum r^2), the
+ *              quantity lskum_get_residuals reports for the solver's own R
+ *   cuda_stream  stream of the current device (NULL = legacy default); the
+ *              result is ready when that stream reaches it
+ * The scratch is a fixed 64 KiB device array inside the library, held by every
+ * GPU that loads it until the process exits; no cudaMalloc/cudaFree or other
+ * allocating call is made.  The first call on each device performs a one-time
+ * set-up (it looks up that array's device address with that device current),
+ * so make that first call before any stream capture.  All calls share the
+ * array: calls that overlap on the GPU race and must be serialised by the
+ * caller.  Errors: LSKUM_ERR_ARG (NULL pointer, n out of range),
+ * LSKUM_ERR_CUDA (set-up or launch failed).
+ */
+lskum_status lskum_density_norm_noalloc(const double *r_rho_dev, int32_t n, double *norm_dev, void *cuda_stream);
+
 /* Message of the last failure of ctx (or of the last failed create when ctx
  * is NULL); never NULL; valid until the next call on the same context. */
 const char *lskum_last_error(const lskum_ctx *ctx);

@@ -64,13 +64,14 @@ def load():
     L.lskum_get_order.argtypes = [vp, vp, vp, P(i32)]
     L.lskum_get_info.argtypes = [vp, P(i32), P(i32), P(i32)]
     L.lskum_time_phases.argtypes = [vp, i32, vp]
+    L.lskum_density_norm_noalloc.argtypes = [vp, i32, vp, vp]
     L.lskum_last_error.argtypes = [vp]
     L.lskum_last_error.restype = C.c_char_p
     L.lskum_destroy.argtypes = [vp]
     L.lskum_destroy.restype = None
     for f in ("lskum_create", "lskum_set_state", "lskum_set_conserved", "lskum_run", "lskum_enqueue", "lskum_wait",
               "lskum_get_state", "lskum_get_field", "lskum_get_residuals", "lskum_get_forces", "lskum_get_order",
-              "lskum_get_info", "lskum_time_phases"):
+              "lskum_get_info", "lskum_time_phases", "lskum_density_norm_noalloc"):
         getattr(L, f).restype = st
     _lib = L
     return L
