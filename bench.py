@@ -38,8 +38,9 @@ L2_BYTES = 129 * 2**20
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # FP64 flops (DFMA = 2) the residual kernel executes per neighbour slot that
 # joins a split sub-stencil, counted by ncu on this workload
-# (smsp__sass_thread_inst_executed_op_{dfma,dmul,dadd}_pred_on).
-RES_FLOPS_PER_SLOT = 1150.0
+# (2 x smsp__sass_thread_inst_executed_op_dfma_pred_on + dmul + dadd, one
+# launch, divided by the 2,926,611 such slots); see profiles/.
+RES_FLOPS_PER_SLOT = 454.55
 START = 50  # first-order start-up iterations before warm-up and timing
 
 
@@ -157,7 +158,8 @@ def run_ours(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     cloud = cg.build_workload(WORKLOAD)
     n = cloud.n
-    s = lskum.Solver(cloud, 0.85, 1.0, cfl=100.0, inner_iters=3, jvp=lskum.JVP_EXACT, first_order_iters=START)
+    s = lskum.Solver(cloud, 0.85, 1.0, cfl=100.0, inner_iters=3, jvp=lskum.JVP_EXACT, first_order_iters=START,
+                     precision=args.precision)
     info = s.info()
     nslots = int(np.count_nonzero(_memberships(cloud)))
     # first-order start-up, then warm-up iterations (untimed)
@@ -218,8 +220,9 @@ def run_ours(args, rank, world, local_rank):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f64+f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "points": n, "neighbour_slots": int(cloud.nnz),
+                   "precision": "fp64" if args.precision == 0 else "fp32 sweeps, fp64 residual/update",
                    "mach": 0.85, "aoa_deg": 1.0, "cfl": 100.0, "inner_iters": 3, "jvp": "exact-AD",
                    "order": f"second (timed steps follow {START} untimed first-order start-up iterations)",
                    "colours": info["n_colours"], "parallelism": "replicas" if world > 1 else "single",
@@ -265,6 +268,8 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", type=int, choices=[0, 1], default=0,
+                    help="0: plain FP64 (default); 1: FP32 sweeps with FP64 residual and update")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

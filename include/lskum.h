@@ -94,7 +94,9 @@ typedef struct {
  *   inner_iters      K >= 0 defect-correction inner iterations of the
  *                    q-derivatives (Eq. 16)
  *   jvp              LSKUM_JVP_EXACT or LSKUM_JVP_INCREMENT
- *   precision        0 = FP64 everywhere (the only value accepted so far)
+ *   precision        0 = FP64 everywhere; 1 = mixed: the LU-SGS sweeps and
+ *                    their Jacobian products in FP32, the residual (with
+ *                    compensated neighbour sums), norm and update in FP64
  *   first_order_iters  iterations n <= first_order_iters (counted since the
  *                    last set_state / create) use the first-order residual
  *                    (q~ = q: no defect correction); a start-up aid, >= 0

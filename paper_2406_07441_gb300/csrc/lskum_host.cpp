@@ -163,6 +163,11 @@ struct HostPrep {
     std::vector<int32_t> slice_off, deg, enb;
     std::vector<uint8_t> emb, fl_i;
     std::vector<double> edx, edy, ew1, ew2, egx, egy, geo_i, wnx, wny;
+    std::vector<double> exx, exy, eyx, eyy;  // wgx dx, wgx dy, wgy dx, wgy dy per slot
+    // LU-SGS lower / upper slot lists (CSR, internal order) and level orders
+    std::vector<int32_t> lo_off, lo_nbr, up_off, up_nbr, sw_fwd, sw_bwd;
+    std::vector<uint8_t> lo_mb, up_mb;
+    std::vector<double> lo_w1, lo_w2, up_w1, up_w2;
 };
 static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &hp);
 static lskum_status upload(lskum_ctx *c, HostPrep &hp);
@@ -179,7 +184,7 @@ lskum_status lskum_create(const lskum_cloud *cl, const lskum_opts *opts, void *c
     if (!(opts->cfl > 0.0) || !std::isfinite(opts->cfl) || !std::isfinite(opts->mach) ||
         !std::isfinite(opts->aoa_deg) || !(opts->cfl_ramp_iters >= 0.0) || opts->inner_iters < 0 ||
         opts->inner_iters > 64 || (opts->jvp != LSKUM_JVP_EXACT && opts->jvp != LSKUM_JVP_INCREMENT) ||
-        opts->precision != 0 || opts->first_order_iters < 0)
+        (opts->precision != 0 && opts->precision != 1) || opts->first_order_iters < 0)
         return fail(nullptr, LSKUM_ERR_ARG, "invalid option value");
     const int32_t *off = cl->nbr_off, *idx = cl->nbr_idx;
     if (off[0] != 0) return fail(nullptr, LSKUM_ERR_ARG, "nbr_off[0] != 0");
@@ -297,6 +302,10 @@ static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &
         for (int32_t e = off[p]; e < off[p + 1]; e++) {
             swgx[e] = (syy * sdx[e] - sxy * sdy[e]) / gdet;
             swgy[e] = (sxx * sdy[e] - sxy * sdx[e]) / gdet;
+            geo[G_SXX * n + p] += swgx[e] * sdx[e];
+            geo[G_SXY * n + p] += swgx[e] * sdy[e];
+            geo[G_SYX * n + p] += swgy[e] * sdx[e];
+            geo[G_SYY * n + p] += swgy[e] * sdy[e];
         }
         geo[G_DMIN * n + p] = dmin;
         if (c->flag[p] == LSKUM_OUTER) continue;
@@ -381,7 +390,7 @@ static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &
     std::vector<double> &edx = hp.edx, &edy = hp.edy, &ew1 = hp.ew1, &ew2 = hp.ew2, &egx = hp.egx, &egy = hp.egy;
     enb.assign(esz, 0);
     emb.assign(esz, 0);
-    for (auto *v : {&edx, &edy, &ew1, &ew2, &egx, &egy}) v->assign(esz, 0.0);
+    for (auto *v : {&edx, &edy, &ew1, &ew2, &egx, &egy, &hp.exx, &hp.exy, &hp.eyx, &hp.eyy}) v->assign(esz, 0.0);
     for (int32_t k = 0; k < n; k++) {
         const int32_t p = c->perm[k];
         deg[k] = off[p + 1] - off[p];
@@ -398,8 +407,50 @@ static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &
             ew2[t] = sw2[e];
             egx[t] = swgx[e];
             egy[t] = swgy[e];
+            hp.exx[t] = swgx[e] * sdx[e];
+            hp.exy[t] = swgx[e] * sdy[e];
+            hp.eyx[t] = swgy[e] * sdx[e];
+            hp.eyy[t] = swgy[e] * sdy[e];
         }
     }
+    // LU-SGS lists: for each point its slots whose neighbour is earlier (lower)
+    // or later (upper) in the sweep order; outer neighbours (increment 0)
+    // and slots in no split sub-stencil contribute nothing and are left out
+    hp.lo_off.assign(n + 1, 0);
+    hp.up_off.assign(n + 1, 0);
+    for (int32_t k = 0; k < n; k++) {
+        const int32_t p = c->perm[k];
+        if (c->flag[p] != LSKUM_OUTER) {
+            for (int32_t e = off[p]; e < off[p + 1]; e++) {
+                const int32_t q = idx[e];
+                if (c->flag[q] == LSKUM_OUTER || smb[e] == 0) continue;
+                const bool lower = c->colour[q] < c->colour[p];
+                (lower ? hp.lo_nbr : hp.up_nbr).push_back(c->inv[q]);
+                (lower ? hp.lo_mb : hp.up_mb).push_back(smb[e]);
+                (lower ? hp.lo_w1 : hp.up_w1).push_back(sw1[e]);
+                (lower ? hp.lo_w2 : hp.up_w2).push_back(sw2[e]);
+            }
+        }
+        hp.lo_off[k + 1] = (int32_t)hp.lo_nbr.size();
+        hp.up_off[k + 1] = (int32_t)hp.up_nbr.size();
+    }
+    // per level, points by decreasing list length (a warp's groups then share a trip count)
+    hp.sw_fwd.assign(std::max(n, 1), 0);
+    hp.sw_bwd.assign(std::max(n, 1), 0);
+    for (int32_t l = 0; l < nc; l++) {
+        const int32_t b = c->lvl_beg[l], e = c->lvl_act_end[l];
+        for (int32_t k = b; k < e; k++) hp.sw_fwd[k] = hp.sw_bwd[k] = k;
+        auto lo_len = [&](int32_t k) { return hp.lo_off[k + 1] - hp.lo_off[k]; };
+        auto up_len = [&](int32_t k) { return hp.up_off[k + 1] - hp.up_off[k]; };
+        std::stable_sort(hp.sw_fwd.begin() + b, hp.sw_fwd.begin() + e,
+                         [&](int32_t a, int32_t z) { return lo_len(a) > lo_len(z); });
+        std::stable_sort(hp.sw_bwd.begin() + b, hp.sw_bwd.begin() + e,
+                         [&](int32_t a, int32_t z) { return up_len(a) > up_len(z); });
+    }
+    for (auto *v : {&hp.lo_nbr, &hp.up_nbr}) if (v->empty()) v->push_back(0);
+    for (auto *v : {&hp.lo_mb, &hp.up_mb}) if (v->empty()) v->push_back(0);
+    for (auto *v : {&hp.lo_w1, &hp.lo_w2, &hp.up_w1, &hp.up_w2}) if (v->empty()) v->push_back(0.0);
+
     std::vector<double> &geo_i = hp.geo_i, &wnx = hp.wnx, &wny = hp.wny;
     std::vector<uint8_t> &fl_i = hp.fl_i;
     geo_i.assign((size_t)G_NFIELDS * ld, 0.0);
@@ -442,13 +493,41 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
     double *ddx = A.alloc<double>(edx.size()), *ddy = A.alloc<double>(edx.size());
     double *dw1 = A.alloc<double>(edx.size()), *dw2 = A.alloc<double>(edx.size());
     double *dgx = A.alloc<double>(edx.size()), *dgy = A.alloc<double>(edx.size());
+    double *dxx = A.alloc<double>(edx.size()), *dxy = A.alloc<double>(edx.size());
+    double *dyx = A.alloc<double>(edx.size()), *dyy = A.alloc<double>(edx.size());
     for (int s = 0; s < 2; s++) {
         d.set[s].U = A.alloc<double>(4 * (size_t)ld);
         d.set[s].q = A.alloc<double>(4 * (size_t)ld);
-        d.set[s].prim = A.alloc<double>((size_t)P_NFIELDS * ld);
+        d.set[s].prim = A.alloc<double>((size_t)kPrimStride * ld);
         d.qx[s] = A.alloc<double>(4 * (size_t)ld);
         d.qy[s] = A.alloc<double>(4 * (size_t)ld);
     }
+    int32_t *dlo_off = A.alloc<int32_t>(n + 1), *dup_off = A.alloc<int32_t>(n + 1);
+    int32_t *dlo_nbr = A.alloc<int32_t>(hp.lo_nbr.size()), *dup_nbr = A.alloc<int32_t>(hp.up_nbr.size());
+    uint8_t *dlo_mb = A.alloc<uint8_t>(hp.lo_mb.size()), *dup_mb = A.alloc<uint8_t>(hp.up_mb.size());
+    double *dlo_w1 = A.alloc<double>(hp.lo_w1.size()), *dlo_w2 = A.alloc<double>(hp.lo_w2.size());
+    double *dup_w1 = A.alloc<double>(hp.up_w1.size()), *dup_w2 = A.alloc<double>(hp.up_w2.size());
+    int32_t *dsw_fwd = A.alloc<int32_t>(hp.sw_fwd.size()), *dsw_bwd = A.alloc<int32_t>(hp.sw_bwd.size());
+    // mixed precision: FP32 increments, primal records and weights
+    const bool mixed = c->opts.precision == 1;
+    std::vector<float> flo_w1, flo_w2, fup_w1, fup_w2;
+    float *dlo_w1f = nullptr, *dlo_w2f = nullptr, *dup_w1f = nullptr, *dup_w2f = nullptr;
+    d.dUsf = d.dUf = nullptr;
+    for (int s = 0; s < 2; s++) d.set[s].primf = nullptr;
+    if (mixed) {
+        for (auto pr : {std::make_pair(&hp.lo_w1, &flo_w1), std::make_pair(&hp.lo_w2, &flo_w2),
+                        std::make_pair(&hp.up_w1, &fup_w1), std::make_pair(&hp.up_w2, &fup_w2)})
+            pr.second->assign(pr.first->begin(), pr.first->end());
+        dlo_w1f = A.alloc<float>(flo_w1.size());
+        dlo_w2f = A.alloc<float>(flo_w2.size());
+        dup_w1f = A.alloc<float>(fup_w1.size());
+        dup_w2f = A.alloc<float>(fup_w2.size());
+        d.dUsf = A.alloc<float>(4 * (size_t)ld);
+        d.dUf = A.alloc<float>(4 * (size_t)ld);
+        for (int s = 0; s < 2; s++) d.set[s].primf = A.alloc<float>((size_t)kPrimStride * ld);
+    }
+    d.g1x = A.alloc<double>(4 * (size_t)ld);
+    d.g1y = A.alloc<double>(4 * (size_t)ld);
     d.R = A.alloc<double>(4 * (size_t)ld);
     d.D = A.alloc<double>(ld);
     d.dUs = A.alloc<double>(4 * (size_t)ld);
@@ -479,7 +558,28 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
     d.w2 = dw2;
     d.wgx = dgx;
     d.wgy = dgy;
+    d.gxx = dxx;
+    d.gxy = dxy;
+    d.gyx = dyx;
+    d.gyy = dyy;
     d.ctrl = c->ctrl;
+    d.lo_off = dlo_off;
+    d.up_off = dup_off;
+    d.lo_nbr = dlo_nbr;
+    d.up_nbr = dup_nbr;
+    d.lo_mb = dlo_mb;
+    d.up_mb = dup_mb;
+    d.lo_w1 = dlo_w1;
+    d.lo_w2 = dlo_w2;
+    d.up_w1 = dup_w1;
+    d.up_w2 = dup_w2;
+    d.sw_fwd = dsw_fwd;
+    d.sw_bwd = dsw_bwd;
+    d.lo_w1f = dlo_w1f;
+    d.lo_w2f = dlo_w2f;
+    d.up_w1f = dup_w1f;
+    d.up_w2f = dup_w2f;
+    d.precision = c->opts.precision;
     d.cfl = c->opts.cfl;
     d.ramp = c->opts.cfl_ramp_iters;
     d.K = c->opts.inner_iters;
@@ -502,6 +602,30 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
     up(dw2, ew2.data(), ew2.size() * sizeof(double));
     up(dgx, egx.data(), egx.size() * sizeof(double));
     up(dgy, egy.data(), egy.size() * sizeof(double));
+    up(dxx, hp.exx.data(), hp.exx.size() * sizeof(double));
+    up(dxy, hp.exy.data(), hp.exy.size() * sizeof(double));
+    up(dyx, hp.eyx.data(), hp.eyx.size() * sizeof(double));
+    up(dyy, hp.eyy.data(), hp.eyy.size() * sizeof(double));
+    up(dlo_off, hp.lo_off.data(), hp.lo_off.size() * sizeof(int32_t));
+    up(dup_off, hp.up_off.data(), hp.up_off.size() * sizeof(int32_t));
+    up(dlo_nbr, hp.lo_nbr.data(), hp.lo_nbr.size() * sizeof(int32_t));
+    up(dup_nbr, hp.up_nbr.data(), hp.up_nbr.size() * sizeof(int32_t));
+    up(dlo_mb, hp.lo_mb.data(), hp.lo_mb.size());
+    up(dup_mb, hp.up_mb.data(), hp.up_mb.size());
+    up(dlo_w1, hp.lo_w1.data(), hp.lo_w1.size() * sizeof(double));
+    up(dlo_w2, hp.lo_w2.data(), hp.lo_w2.size() * sizeof(double));
+    up(dup_w1, hp.up_w1.data(), hp.up_w1.size() * sizeof(double));
+    up(dup_w2, hp.up_w2.data(), hp.up_w2.size() * sizeof(double));
+    up(dsw_fwd, hp.sw_fwd.data(), hp.sw_fwd.size() * sizeof(int32_t));
+    up(dsw_bwd, hp.sw_bwd.data(), hp.sw_bwd.size() * sizeof(int32_t));
+    if (mixed) {
+        up(dlo_w1f, flo_w1.data(), flo_w1.size() * sizeof(float));
+        up(dlo_w2f, flo_w2.data(), flo_w2.size() * sizeof(float));
+        up(dup_w1f, fup_w1.data(), fup_w1.size() * sizeof(float));
+        up(dup_w2f, fup_w2.data(), fup_w2.size() * sizeof(float));
+        if (e == cudaSuccess) e = cudaMemset(d.dUsf, 0, 4 * (size_t)ld * sizeof(float));
+        if (e == cudaSuccess) e = cudaMemset(d.dUf, 0, 4 * (size_t)ld * sizeof(float));
+    }
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy");
     // zero intermediates; D = 1 at outer points (never written by the kernels)
     for (double *p : {d.R, d.dUs, d.dU, d.qx[0], d.qx[1], d.qy[0], d.qy[1]})
@@ -751,7 +875,9 @@ void *lskum_stream(lskum_ctx *c)
     return c ? (void *)c->stream : nullptr;
 }
 
-static lskum_status download(lskum_ctx *c, const double *src, int comps, std::vector<double> &out)
+// Copy a per-point field to the host in caller order: `comps` rows of stride
+// ld (structure of arrays) or, with aos, `comps` values per point.
+static lskum_status download(lskum_ctx *c, const double *src, int comps, std::vector<double> &out, bool aos = false)
 {
     const int32_t n = c->n, ld = c->ld;
     double *buf = c->pinned;  // page-locked staging, 4 * ld doubles
@@ -761,7 +887,8 @@ static lskum_status download(lskum_ctx *c, const double *src, int comps, std::ve
     out.assign((size_t)comps * n, 0.0);
     for (int32_t k = 0; k < n; k++) {
         const int32_t p = c->perm[k];
-        for (int cc = 0; cc < comps; cc++) out[(size_t)comps * p + cc] = buf[(size_t)cc * ld + k];
+        for (int cc = 0; cc < comps; cc++)
+            out[(size_t)comps * p + cc] = aos ? buf[(size_t)comps * k + cc] : buf[(size_t)cc * ld + k];
     }
     return LSKUM_OK;
 }
@@ -774,6 +901,7 @@ lskum_status lskum_get_field(lskum_ctx *c, int32_t field, double *out)
     const int K = d.K & 1;
     const double *src = nullptr;
     int comps = 4;
+    bool aos = false;
     switch (field) {
     case LSKUM_FIELD_U: src = d.set[c->cur].U; break;
     case LSKUM_FIELD_Q: src = d.set[c->cur].q; break;
@@ -781,12 +909,24 @@ lskum_status lskum_get_field(lskum_ctx *c, int32_t field, double *out)
     case LSKUM_FIELD_QY: src = d.qy[K]; break;
     case LSKUM_FIELD_R: src = d.R; break;
     case LSKUM_FIELD_D: src = d.D; comps = 1; break;
-    case LSKUM_FIELD_DUS: src = d.dUs; break;
-    case LSKUM_FIELD_DU: src = d.dU; break;
+    case LSKUM_FIELD_DUS: src = d.dUs; aos = true; break;
+    case LSKUM_FIELD_DU: src = d.dU; aos = true; break;
     default: return fail(c, LSKUM_ERR_ARG, "unknown field %d", field);
     }
+    if (d.precision && (field == LSKUM_FIELD_DUS || field == LSKUM_FIELD_DU)) {
+        // FP32 increments of the mixed-precision sweeps
+        const float *fsrc = field == LSKUM_FIELD_DUS ? d.dUsf : d.dUf;
+        float *buf = reinterpret_cast<float *>(c->pinned);
+        cudaError_t e = cudaMemcpyAsync(buf, fsrc, 4 * (size_t)c->ld * sizeof(float), cudaMemcpyDeviceToHost,
+                                        c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy D2H");
+        for (int32_t k = 0; k < c->n; k++)
+            for (int cc = 0; cc < 4; cc++) out[4 * (size_t)c->perm[k] + cc] = (double)buf[4 * (size_t)k + cc];
+        return LSKUM_OK;
+    }
     std::vector<double> v;
-    lskum_status s = download(c, src, comps, v);
+    lskum_status s = download(c, src, comps, v, aos);
     if (s != LSKUM_OK) return s;
     std::memcpy(out, v.data(), v.size() * sizeof(double));
     return LSKUM_OK;

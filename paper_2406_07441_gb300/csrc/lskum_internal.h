@@ -40,22 +40,28 @@ enum GeoField {
     G_LS1_0, G_LS1_1, G_LS1_2, G_LS1_3,  // LS_s(1) of the four split sub-stencils
     G_ABS_0, G_ABS_1, G_ABS_2, G_ABS_3,  // sum_i |w_i| of each split sub-stencil
     G_DMIN,                              // min_i |r_i - r_0|
+    G_SXX, G_SXY, G_SYX, G_SYY,          // sums over the stencil of wgx dx, wgx dy, wgy dx, wgy dy
     G_NFIELDS
 };
 
 // Per-point primal quantities of the current state used by the sweeps'
-// Jacobian products (fields of `prim`, stride ld).
+// Jacobian products: array of structures, point k's record at
+// prim[k * kPrimStride + field], so that one neighbour's record is two
+// cache lines instead of one line per field.
 enum PrimField {
     P_RHO, P_IRHO, P_U, P_V, P_P, P_BETA, P_SB, P_ISB, P_I2P, P_Q2, P_E1, P_E2,
     P_SX, P_APX, P_AMX, P_EXPX, P_BX,  // direction (1,0): S, A+, A-, exp(-S^2), B
     P_SY, P_APY, P_AMY, P_EXPY, P_BY,  // direction (0,1)
     P_NFIELDS
 };
+constexpr int kPrimStride = 24;
+static_assert(P_NFIELDS <= kPrimStride, "prim record too small");
 
 struct StateSet {
     double *U;     // [4][ld] conserved variables
     double *q;     // [4][ld] q-variables
-    double *prim;  // [P_NFIELDS][ld]
+    double *prim;  // [ld][kPrimStride]
+    float *primf;  // [ld][kPrimStride] FP32 copy (mixed precision only, else null)
 };
 
 struct Dev {
@@ -72,12 +78,28 @@ struct Dev {
     const double *ndx, *ndy;  // x_i - x_0, y_i - y_0
     const double *w1, *w2;    // LS weight of the slot in its e1 / e2 split sub-stencil (0 if none)
     const double *wgx, *wgy;  // full-stencil LS weights of d/dx and d/dy (Eq. 10, 16)
+    const double *gxx, *gxy, *gyx, *gyy;  // wgx dx, wgx dy, wgy dx, wgy dy (inner iterations)
     // iteration buffers
     StateSet set[2];
     double *qx[2], *qy[2];   // double-buffered q-derivatives
+    double *g1x, *g1y;       // first-order LS derivatives (the fixed part of Eq. 16)
     double *R;               // [4][ld]
     double *D;               // [ld]
-    double *dUs, *dU;        // [4][ld]
+    double *dUs, *dU;        // [ld][4] (array of structures: one 32-byte gather per neighbour)
+    // LU-SGS slot lists (CSR over the internal index): the slots of each point
+    // whose neighbour comes earlier (lo) or later (up) in the sweep order,
+    // outer neighbours and slots in no split sub-stencil left out
+    const int32_t *lo_off, *lo_nbr, *up_off, *up_nbr;
+    const uint8_t *lo_mb, *up_mb;
+    const double *lo_w1, *lo_w2, *up_w1, *up_w2;
+    // mixed precision (precision = 1): FP32 increments ([ld][4]) and weights;
+    // null in FP64 mode
+    float *dUsf, *dUf;
+    const float *lo_w1f, *lo_w2f, *up_w1f, *up_w2f;
+    // per colour level, its non-outer points ordered by decreasing list length
+    // (forward: lower list, backward: upper list), so a warp's groups share a
+    // trip count
+    const int32_t *sw_fwd, *sw_bwd;
     double *blk;             // residual-norm partial sums, one per residual block
     int32_t n_blk;
     Ctrl *ctrl;
@@ -85,6 +107,7 @@ struct Dev {
     double cfl, ramp, u_inf[4];
     int32_t K, jvp;
     int32_t first_order;  // iterations n <= first_order use q~ = q
+    int32_t precision;    // 0 FP64; 1 FP32 sweeps, compensated FP64 residual sums
 };
 
 // Kernel launch wrappers (lskum_kernels.cu).  `cur` is the state set read by

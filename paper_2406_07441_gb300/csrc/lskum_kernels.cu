@@ -99,10 +99,13 @@ __device__ __forceinline__ void split_flux(const MathTables &T, const Prim &P, d
     G[3] = fma(ud * P.e1, A, sg * P.e2 * B);
 }
 
-// Primal quantities of a conserved state for the Jacobian products.
-struct PrimU {
-    double rho, irho, u, v, p, beta, sb, isb, i2p, q2, e1, e2;
+// Primal quantities of a conserved state for the Jacobian products (FP64,
+// or FP32 for the mixed-precision sweeps).
+template <typename T>
+struct PrimT {
+    T rho, irho, u, v, p, beta, sb, isb, i2p, q2, e1, e2;
 };
+using PrimU = PrimT<double>;
 
 __device__ __forceinline__ PrimU prim_from_cons(const double U[4])
 {
@@ -123,49 +126,52 @@ __device__ __forceinline__ PrimU prim_from_cons(const double U[4])
     return P;
 }
 
-__device__ __forceinline__ PrimU load_primu(const double *__restrict__ pr, int ld, int i)
+template <typename T>
+__device__ __forceinline__ PrimT<T> load_prim(const T *__restrict__ pr, int i)
 {
-    PrimU P;
-    P.rho = pr[P_RHO * ld + i];
-    P.irho = pr[P_IRHO * ld + i];
-    P.u = pr[P_U * ld + i];
-    P.v = pr[P_V * ld + i];
-    P.p = pr[P_P * ld + i];
-    P.beta = pr[P_BETA * ld + i];
-    P.sb = pr[P_SB * ld + i];
-    P.isb = pr[P_ISB * ld + i];
-    P.i2p = pr[P_I2P * ld + i];
-    P.q2 = pr[P_Q2 * ld + i];
-    P.e1 = pr[P_E1 * ld + i];
-    P.e2 = pr[P_E2 * ld + i];
+    const T *r = pr + (size_t)i * kPrimStride;
+    PrimT<T> P;
+    P.rho = r[P_RHO];
+    P.irho = r[P_IRHO];
+    P.u = r[P_U];
+    P.v = r[P_V];
+    P.p = r[P_P];
+    P.beta = r[P_BETA];
+    P.sb = r[P_SB];
+    P.isb = r[P_ISB];
+    P.i2p = r[P_I2P];
+    P.q2 = r[P_Q2];
+    P.e1 = r[P_E1];
+    P.e2 = r[P_E2];
     return P;
 }
 
 // Exact product A_d^sg(U) dl by forward-mode differentiation of
 // U -> (rho, u, v, p) -> (beta, S, A, B) -> G_d^sg.  S, A = (1 + sg erf S)/2,
 // exp(-S^2) and B of the state are inputs (precomputed per point for d = x, y).
-__device__ __forceinline__ void jvp_exact(const PrimU &P, double dx, double dy, double sg, double S, double A,
-                                          double eS, double B, const double dl[4], double out[4])
+template <typename T>
+__device__ __forceinline__ void jvp_exact(const PrimT<T> &P, T dx, T dy, T sg, T S, T A, T eS, T B, const T dl[4],
+                                          T out[4])
 {
-    const double drho = dl[0];
-    const double du = (dl[1] - P.u * drho) * P.irho;
-    const double dv = (dl[2] - P.v * drho) * P.irho;
-    const double dq2 = 2.0 * (P.u * du + P.v * dv);
-    const double dk = 0.5 * (drho * P.q2 + P.rho * dq2);  // d(rho |u|^2 / 2)
-    const double dp = kGm1 * (dl[3] - dk);
-    const double dbeta = (drho - 2.0 * P.beta * dp) * P.i2p;
-    const double ud = P.u * dx + P.v * dy;
-    const double dud = du * dx + dv * dy;
-    const double dsb = 0.5 * dbeta * P.isb;
-    const double dS = dud * P.sb + ud * dsb;
-    const double dA = sg * eS * dS * kInvSqrtPi;
-    const double dB = -B * (2.0 * S * dS + dsb * P.isb);
-    const double M1 = ud * A + sg * B;
-    const double dM1 = dud * A + ud * dA + sg * dB;
-    const double de1 = 3.5 * dp + dk;
-    const double de2 = 3.0 * dp + dk;
-    const double drm = drho * M1 + P.rho * dM1;  // d(rho M1)
-    const double rm = P.rho * M1;
+    const T drho = dl[0];
+    const T du = (dl[1] - P.u * drho) * P.irho;
+    const T dv = (dl[2] - P.v * drho) * P.irho;
+    const T dq2 = T(2.0) * (P.u * du + P.v * dv);
+    const T dk = T(0.5) * (drho * P.q2 + P.rho * dq2);  // d(rho |u|^2 / 2)
+    const T dp = T(kGm1) * (dl[3] - dk);
+    const T dbeta = (drho - T(2.0) * P.beta * dp) * P.i2p;
+    const T ud = P.u * dx + P.v * dy;
+    const T dud = du * dx + dv * dy;
+    const T dsb = T(0.5) * dbeta * P.isb;
+    const T dS = dud * P.sb + ud * dsb;
+    const T dA = sg * eS * dS * T(kInvSqrtPi);
+    const T dB = -B * (T(2.0) * S * dS + dsb * P.isb);
+    const T M1 = ud * A + sg * B;
+    const T dM1 = dud * A + ud * dA + sg * dB;
+    const T de1 = T(3.5) * dp + dk;
+    const T de2 = T(3.0) * dp + dk;
+    const T drm = drho * M1 + P.rho * dM1;  // d(rho M1)
+    const T rm = P.rho * M1;
     out[0] = drm;
     out[1] = drm * P.u + rm * du + (dp * A + P.p * dA) * dx;
     out[2] = drm * P.v + rm * dv + (dp * A + P.p * dA) * dy;
@@ -190,8 +196,8 @@ __device__ __forceinline__ void flux_cons(const MathTables &T, const double U[4]
     G[3] = fma(ud * P.e1, A, sg * P.e2 * B);
 }
 
-template <int TPP>
-__device__ __forceinline__ double group_sum(double v)
+template <int TPP, typename T>
+__device__ __forceinline__ T group_sum(T v)
 {
 #pragma unroll
     for (int o = TPP / 2; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
@@ -199,8 +205,14 @@ __device__ __forceinline__ double group_sum(double v)
 }
 
 // ---------------------------------------------------------------------------
-// q-derivatives (Eq. 10; with CORR, one Jacobi inner iteration of Eq. 16)
+// q-derivatives: first order (Eq. 10), then Jacobi inner iterations of Eq. 16
 // ---------------------------------------------------------------------------
+// An inner iteration's right-hand side sum_i w_i (Delta q_i - Delta r_i .
+// (grad q_i - grad q_0)/2) splits into the first-order term g1 = sum_i w_i
+// Delta q_i, fixed across iterations, and
+//   sum_i (w_i dx_i) px_i + (w_i dy_i) py_i - px_0 sum_i w_i dx_i - py_0 sum_i w_i dy_i
+// with per-slot products w dx, w dy precomputed: 4 FMAs per component and
+// slot instead of 7 FP64 instructions.
 template <int TPP, bool CORR>
 __global__ void __launch_bounds__(256) k_grad(Dev d, const double *__restrict__ q, const double *__restrict__ px,
                                               const double *__restrict__ py, double *__restrict__ qx,
@@ -212,14 +224,10 @@ __global__ void __launch_bounds__(256) k_grad(Dev d, const double *__restrict__ 
     const bool active = k < d.n;
     const int kk = active ? k : d.n - 1;
     const int ld = d.ld;
-    double q0[4], px0[4], py0[4], sx[4], sy[4];
+    double q0[4], sx[4], sy[4];
 #pragma unroll
     for (int c = 0; c < 4; c++) {
-        q0[c] = q[c * ld + kk];
-        if (CORR) {
-            px0[c] = px[c * ld + kk];
-            py0[c] = py[c * ld + kk];
-        }
+        if (!CORR) q0[c] = q[c * ld + kk];
         sx[c] = 0.0;
         sy[c] = 0.0;
     }
@@ -228,18 +236,22 @@ __global__ void __launch_bounds__(256) k_grad(Dev d, const double *__restrict__ 
     for (int j = sub; j < deg; j += TPP) {
         const int e = base + 32 * j;
         const int i = d.nbr[e];
-        const double wx = d.wgx[e], wy = d.wgy[e];
-        double dx = 0.0, dy = 0.0;
-        if (CORR) {
-            dx = d.ndx[e];
-            dy = d.ndy[e];
-        }
+        if (!CORR) {
+            const double wx = d.wgx[e], wy = d.wgy[e];
 #pragma unroll
-        for (int c = 0; c < 4; c++) {
-            double dq = q[c * ld + i] - q0[c];
-            if (CORR) dq -= 0.5 * ((px[c * ld + i] - px0[c]) * dx + (py[c * ld + i] - py0[c]) * dy);
-            sx[c] += wx * dq;
-            sy[c] += wy * dq;
+            for (int c = 0; c < 4; c++) {
+                const double dq = q[c * ld + i] - q0[c];
+                sx[c] = fma(wx, dq, sx[c]);
+                sy[c] = fma(wy, dq, sy[c]);
+            }
+        } else {
+            const double axx = d.gxx[e], axy = d.gxy[e], ayx = d.gyx[e], ayy = d.gyy[e];
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                const double a = px[c * ld + i], b = py[c * ld + i];
+                sx[c] = fma(axx, a, fma(axy, b, sx[c]));
+                sy[c] = fma(ayx, a, fma(ayy, b, sy[c]));
+            }
         }
     }
 #pragma unroll
@@ -248,10 +260,23 @@ __global__ void __launch_bounds__(256) k_grad(Dev d, const double *__restrict__ 
         sy[c] = group_sum<TPP>(sy[c]);
     }
     if (active && sub == 0) {
+        if (!CORR) {
 #pragma unroll
-        for (int c = 0; c < 4; c++) {
-            qx[c * ld + k] = sx[c];
-            qy[c * ld + k] = sy[c];
+            for (int c = 0; c < 4; c++) {
+                d.g1x[c * ld + k] = qx[c * ld + k] = sx[c];
+                d.g1y[c * ld + k] = qy[c * ld + k] = sy[c];
+            }
+        } else {
+            const double cxx = d.geo[G_SXX * ld + k], cxy = d.geo[G_SXY * ld + k];
+            const double cyx = d.geo[G_SYX * ld + k], cyy = d.geo[G_SYY * ld + k];
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                const double a0 = px[c * ld + k], b0 = py[c * ld + k];
+                const double rx = sx[c] - fma(cxx, a0, cxy * b0);
+                const double ry = sy[c] - fma(cyx, a0, cyy * b0);
+                qx[c * ld + k] = fma(-0.5, rx, d.g1x[c * ld + k]);
+                qy[c * ld + k] = fma(-0.5, ry, d.g1y[c * ld + k]);
+            }
         }
     }
 }
@@ -259,7 +284,15 @@ __global__ void __launch_bounds__(256) k_grad(Dev d, const double *__restrict__ 
 // ---------------------------------------------------------------------------
 // flux residual, time step, diagonal, norm partials
 // ---------------------------------------------------------------------------
-template <int TPP>
+// R += x with Neumaier's compensated summation (error term in c).
+__device__ __forceinline__ void comp_add(double &R, double &c, double x)
+{
+    const double t = R + x;
+    c += fabs(R) >= fabs(x) ? (R - t) + x : (x - t) + R;
+    R = t;
+}
+
+template <int TPP, bool COMP>
 __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const double *__restrict__ gx,
                                                   const double *__restrict__ gy)
 {
@@ -281,6 +314,7 @@ __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const doub
     const bool wall = fl == kWall;
     const double *__restrict__ q = st.q;
     double R[4] = {0.0, 0.0, 0.0, 0.0};
+    double Rc[4] = {0.0, 0.0, 0.0, 0.0};  // compensation terms (COMP)
     const double e1x = d.geo[G_E1X * ld + kk], e1y = d.geo[G_E1Y * ld + kk];
     const double e2x = d.geo[G_E2X * ld + kk], e2y = d.geo[G_E2Y * ld + kk];
     if (work) {
@@ -319,7 +353,10 @@ __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const doub
                     split_flux<0>(T, P0, 1.0, 0.0, sg, G0);
                 }
 #pragma unroll
-                for (int c = 0; c < 4; c++) R[c] = fma(w, Gi[c] - G0[c], R[c]);
+                for (int c = 0; c < 4; c++) {
+                    if (COMP) comp_add(R[c], Rc[c], w * (Gi[c] - G0[c]));
+                    else R[c] = fma(w, Gi[c] - G0[c], R[c]);
+                }
             }
             if (mb & 12) {
                 const double sg = (mb & 4) ? 1.0 : -1.0;
@@ -333,12 +370,18 @@ __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const doub
                     split_flux<1>(T, P0, 0.0, 1.0, sg, G0);
                 }
 #pragma unroll
-                for (int c = 0; c < 4; c++) R[c] = fma(w, Gi[c] - G0[c], R[c]);
+                for (int c = 0; c < 4; c++) {
+                    if (COMP) comp_add(R[c], Rc[c], w * (Gi[c] - G0[c]));
+                    else R[c] = fma(w, Gi[c] - G0[c], R[c]);
+                }
             }
         }
     }
 #pragma unroll
-    for (int c = 0; c < 4; c++) R[c] = group_sum<TPP>(R[c]);
+    for (int c = 0; c < 4; c++) {
+        if (COMP) R[c] += Rc[c];
+        R[c] = group_sum<TPP>(R[c]);
+    }
     double nrm = 0.0;
     if (work && sub == 0) {
 #pragma unroll
@@ -347,12 +390,10 @@ __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const doub
         // local time step (reading: CFL min_i|dr| / (|u| + a)) and the scalar
         // diagonal of Eq. 26 with the spectral radii of Eq. 34, kept at least
         // sum_s rho_s sum_i |w_i| so that it bounds the off-diagonal blocks
-        const double *pr = st.prim;
-        const double rho = pr[P_RHO * ld + k], u = pr[P_U * ld + k], v = pr[P_V * ld + k];
-        const double p = pr[P_P * ld + k];
-        const double a = sqrt(1.4 * p * pr[P_IRHO * ld + k]);
+        const double *pr = st.prim + (size_t)k * kPrimStride;
+        const double u = pr[P_U], v = pr[P_V];
+        const double a = sqrt(1.4 * pr[P_P] * pr[P_IRHO]);
         const double dt = cfl * d.geo[G_DMIN * ld + k] / (sqrt(u * u + v * v) + a);
-        (void)rho;
         double Dp = 1.0 / dt, Ddom = 0.0;
         const double u1 = u * e1x + v * e1y, u2 = u * e2x + v * e2y;
         const double r0 = fmax(u1 + a, 0.0), r1 = fmax(a - u1, 0.0);
@@ -414,112 +455,152 @@ __global__ void __launch_bounds__(1024) k_norm(Dev d)
 }
 
 // ---------------------------------------------------------------------------
-// LU-SGS sweep, one colour level; one warp per point
+// LU-SGS sweep, one colour level; G lanes per point
 // ---------------------------------------------------------------------------
-// Points [lb, le) of the level (outer points excluded); [cb_lo, cb_hi) is the
-// whole colour block: a neighbour i is "lower" (earlier in the sweep order)
-// iff i < cb_lo and "upper" iff i >= cb_hi.
-template <int JVP, bool FWD>
-__global__ void __launch_bounds__(256) k_sweep(Dev d, StateSet st, int lb, int le, int cb_lo, int cb_hi)
+// Positions [lb, le) of the level's point order (sw_fwd / sw_bwd).  The
+// forward sweep sums over each point's lower list (neighbours earlier in the
+// sweep order, whose dU* this sweep already produced), the backward sweep
+// over its upper list (neighbours later in the order, dU already final).
+// T is the sweep arithmetic: double, or float in the mixed-precision mode
+// (increments, weights, primal records and Jacobian products in FP32; R and
+// D are read in FP64 and rounded once per point).
+template <typename T>
+struct SweepBufs {
+    T *dUs, *dU;
+    const T *lo_w1, *lo_w2, *up_w1, *up_w2, *prim;
+};
+
+template <typename T>
+__device__ __forceinline__ SweepBufs<T> sweep_bufs(const Dev &d, const StateSet &st);
+
+template <>
+__device__ __forceinline__ SweepBufs<double> sweep_bufs<double>(const Dev &d, const StateSet &st)
 {
-    __shared__ MathTables T;
+    return {d.dUs, d.dU, d.lo_w1, d.lo_w2, d.up_w1, d.up_w2, st.prim};
+}
+
+template <>
+__device__ __forceinline__ SweepBufs<float> sweep_bufs<float>(const Dev &d, const StateSet &st)
+{
+    return {d.dUsf, d.dUf, d.lo_w1f, d.lo_w2f, d.up_w1f, d.up_w2f, st.primf};
+}
+
+template <int JVP, bool FWD, int G, typename T>
+__global__ void __launch_bounds__(256) k_sweep(Dev d, StateSet st, int lb, int le)
+{
+    __shared__ MathTables Tb;
     if (halted(d.ctrl)) return;
-    load_math_tables(T);
+    load_math_tables(Tb);
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int k = lb + (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    if (k >= le) return;  // warp-uniform
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    if (lb + (gt & ~31) / G >= le) return;  // the whole warp is past the level
+    const int pos = lb + gt / G, sub = gt % G;
+    const bool active = pos < le;
+    const int k = (FWD ? d.sw_fwd : d.sw_bwd)[active ? pos : le - 1];
+    const SweepBufs<T> sb = sweep_bufs<T>(d, st);
+    const int32_t *__restrict__ off = FWD ? d.lo_off : d.up_off;
+    const int32_t *__restrict__ nbr = FWD ? d.lo_nbr : d.up_nbr;
+    const uint8_t *__restrict__ mbs = FWD ? d.lo_mb : d.up_mb;
+    const T *__restrict__ w1s = FWD ? sb.lo_w1 : sb.up_w1;
+    const T *__restrict__ w2s = FWD ? sb.lo_w2 : sb.up_w2;
+    const T *__restrict__ dW = FWD ? sb.dUs : sb.dU;
+    const T *__restrict__ pr = sb.prim;
     const int ld = d.ld;
-    const double *__restrict__ dW = FWD ? d.dUs : d.dU;
-    const double *__restrict__ pr = st.prim;
     const bool wall = d.flag[k] == kWall;
-    const double e1x = d.geo[G_E1X * ld + k], e1y = d.geo[G_E1Y * ld + k];
-    const double e2x = d.geo[G_E2X * ld + k], e2y = d.geo[G_E2Y * ld + k];
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    const int deg = d.deg[k];
-    const int base = d.slice_off[k >> 5] + (k & 31);
-    for (int j = lane; j < deg; j += 32) {
-        const int e = base + 32 * j;
-        const int i = d.nbr[e];
-        const int mb = d.memb[e];
-        const bool side = FWD ? (i < cb_lo) : (i >= cb_hi);
-        if (!side || !mb) continue;
-        double dl[4];
+    double e1x = 1.0, e1y = 0.0, e2x = 0.0, e2y = 1.0;
+    if (wall) {
+        e1x = d.geo[G_E1X * ld + k];
+        e1y = d.geo[G_E1Y * ld + k];
+        e2x = d.geo[G_E2X * ld + k];
+        e2y = d.geo[G_E2Y * ld + k];
+    }
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+    const int beg = off[k], end = active ? off[k + 1] : beg;
+    for (int e = beg + sub; e < end; e += G) {
+        const int i = nbr[e];
+        const int mb = mbs[e];
+        T dl[4];
 #pragma unroll
-        for (int c = 0; c < 4; c++) dl[c] = dW[c * ld + i];
-        double J[4];
-        if (JVP == 0) {
-            const PrimU P = load_primu(pr, ld, i);
+        for (int c = 0; c < 4; c++) dl[c] = dW[4 * i + c];
+        if (JVP == 0 && !wall) {
+            // interior frame: d = (1,0) or (0,1), S, A, exp(-S^2), B precomputed per point
+            const PrimT<T> P = load_prim(pr, i);
+            const T *rec = pr + (size_t)i * kPrimStride;
 #pragma unroll
             for (int s = 0; s < 2; s++) {
                 const int m = s == 0 ? (mb & 3) : (mb >> 2);
                 if (!m) continue;
-                const double sg = (m & 1) ? 1.0 : -1.0;
-                const double w = s == 0 ? d.w1[e] : d.w2[e];
-                const double ddx = s == 0 ? e1x : e2x, ddy = s == 0 ? e1y : e2y;
-                double S, A, eS, B;
-                if (!wall) {
-                    // interior frame: d = (1,0) or (0,1), precomputed per point
-                    const int f = s == 0 ? P_SX : P_SY;
-                    S = pr[f * ld + i];
-                    A = pr[(sg > 0.0 ? f + 1 : f + 2) * ld + i];
-                    eS = pr[(f + 3) * ld + i];
-                    B = pr[(f + 4) * ld + i];
-                } else {
-                    S = (P.u * ddx + P.v * ddy) * P.sb;
-                    split_A(T, S, sg, A, eS);
-                    B = eS * kInv2SqrtPi * P.isb;
-                }
-                jvp_exact(P, ddx, ddy, sg, S, A, eS, B, dl, J);
+                const T sg = (m & 1) ? T(1) : T(-1);
+                const int f = s == 0 ? P_SX : P_SY;
+                T J[4];
+                jvp_exact(P, s == 0 ? T(1) : T(0), s == 0 ? T(0) : T(1), sg, rec[f], rec[(m & 1) ? f + 1 : f + 2],
+                          rec[f + 3], rec[f + 4], dl, J);
+                const T w = s == 0 ? w1s[e] : w2s[e];
 #pragma unroll
-                for (int c = 0; c < 4; c++) acc[c] += w * J[c];
+                for (int c = 0; c < 4; c++) acc[c] = fma(w, J[c], acc[c]);
             }
         } else {
-            double Ui[4], Up[4];
+            // wall frames (t, n) and the increment form: evaluated in FP64
+            double dld[4];
 #pragma unroll
-            for (int c = 0; c < 4; c++) {
-                Ui[c] = st.U[c * ld + i];
-                Up[c] = Ui[c] + dl[c];
+            for (int c = 0; c < 4; c++) dld[c] = (double)dl[c];
+            double Ui[4], Up[4];
+            PrimU P;
+            if (JVP == 0) {
+                P = load_prim(st.prim, i);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    Ui[c] = st.U[c * ld + i];
+                    Up[c] = Ui[c] + dld[c];
+                }
             }
 #pragma unroll
             for (int s = 0; s < 2; s++) {
                 const int m = s == 0 ? (mb & 3) : (mb >> 2);
                 if (!m) continue;
                 const double sg = (m & 1) ? 1.0 : -1.0;
-                const double w = s == 0 ? d.w1[e] : d.w2[e];
                 const double ddx = s == 0 ? e1x : e2x, ddy = s == 0 ? e1y : e2y;
-                double G1[4], G0[4];
-                flux_cons(T, Up, ddx, ddy, sg, G1);
-                flux_cons(T, Ui, ddx, ddy, sg, G0);
+                double J[4];
+                if (JVP == 0) {
+                    const double S = (P.u * ddx + P.v * ddy) * P.sb;
+                    double A, eS;
+                    split_A(Tb, S, sg, A, eS);
+                    jvp_exact(P, ddx, ddy, sg, S, A, eS, eS * kInv2SqrtPi * P.isb, dld, J);
+                } else {
+                    double G1[4], G0[4];
+                    flux_cons(Tb, Up, ddx, ddy, sg, G1);
+                    flux_cons(Tb, Ui, ddx, ddy, sg, G0);
 #pragma unroll
-                for (int c = 0; c < 4; c++) acc[c] += w * (G1[c] - G0[c]);
+                    for (int c = 0; c < 4; c++) J[c] = G1[c] - G0[c];
+                }
+                const T w = s == 0 ? w1s[e] : w2s[e];
+#pragma unroll
+                for (int c = 0; c < 4; c++) acc[c] = fma(w, (T)J[c], acc[c]);
             }
         }
     }
 #pragma unroll
-    for (int c = 0; c < 4; c++) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(kFull, acc[c], o);
-    }
-    if (lane == 0) {
-        const double Dk = d.D[k];
-        double w[4];
+    for (int c = 0; c < 4; c++) acc[c] = group_sum<G>(acc[c]);
+    if (active && sub == 0) {
+        const T iD = T(1) / (T)d.D[k];
+        T w[4];
         if (FWD) {
 #pragma unroll
-            for (int c = 0; c < 4; c++) w[c] = -(d.R[c * ld + k] + acc[c]) / Dk;
+            for (int c = 0; c < 4; c++) w[c] = -((T)d.R[c * ld + k] + acc[c]) * iD;
         } else {
 #pragma unroll
-            for (int c = 0; c < 4; c++) w[c] = d.dUs[c * ld + k] - acc[c] / Dk;
+            for (int c = 0; c < 4; c++) w[c] = fma(-acc[c], iD, sb.dUs[4 * k + c]);
         }
         if (wall) {
-            const double nx = d.wnx[k], ny = d.wny[k];
-            const double mn = w[1] * nx + w[2] * ny;
+            const T nx = (T)d.wnx[k], ny = (T)d.wny[k];
+            const T mn = w[1] * nx + w[2] * ny;
             w[1] -= mn * nx;
             w[2] -= mn * ny;
         }
-        double *out = FWD ? d.dUs : d.dU;
+        T *out = FWD ? sb.dUs : sb.dU;
 #pragma unroll
-        for (int c = 0; c < 4; c++) out[c * ld + k] = w[c];
+        for (int c = 0; c < 4; c++) out[4 * k + c] = w[c];
     }
 }
 
@@ -549,7 +630,7 @@ __global__ void __launch_bounds__(256) k_update(Dev d, int cur)
     for (int c = 0; c < 4; c++) U[c] = src.U[c * ld + k];
     if (INC && fl != kOuter) {
 #pragma unroll
-        for (int c = 0; c < 4; c++) U[c] += d.dU[c * ld + k];
+        for (int c = 0; c < 4; c++) U[c] += d.dUf ? (double)d.dUf[4 * k + c] : d.dU[4 * k + c];
     }
     if (fl == kWall) {
         const double nx = d.wnx[k], ny = d.wny[k];
@@ -571,33 +652,38 @@ __global__ void __launch_bounds__(256) k_update(Dev d, int cur)
     dst.q[1 * ld + k] = 2.0 * P.beta * P.u;
     dst.q[2 * ld + k] = 2.0 * P.beta * P.v;
     dst.q[3 * ld + k] = -2.0 * P.beta;
-    double *pr = dst.prim;
-    pr[P_RHO * ld + k] = P.rho;
-    pr[P_IRHO * ld + k] = P.irho;
-    pr[P_U * ld + k] = P.u;
-    pr[P_V * ld + k] = P.v;
-    pr[P_P * ld + k] = P.p;
-    pr[P_BETA * ld + k] = P.beta;
-    pr[P_SB * ld + k] = P.sb;
-    pr[P_ISB * ld + k] = P.isb;
-    pr[P_I2P * ld + k] = P.i2p;
-    pr[P_Q2 * ld + k] = P.q2;
-    pr[P_E1 * ld + k] = P.e1;
-    pr[P_E2 * ld + k] = P.e2;
+    double *pr = dst.prim + (size_t)k * kPrimStride;
+    pr[P_RHO] = P.rho;
+    pr[P_IRHO] = P.irho;
+    pr[P_U] = P.u;
+    pr[P_V] = P.v;
+    pr[P_P] = P.p;
+    pr[P_BETA] = P.beta;
+    pr[P_SB] = P.sb;
+    pr[P_ISB] = P.isb;
+    pr[P_I2P] = P.i2p;
+    pr[P_Q2] = P.q2;
+    pr[P_E1] = P.e1;
+    pr[P_E2] = P.e2;
     const double sx = P.u * P.sb, sy = P.v * P.sb;
     double Ex, ex, Ey, ey;
     split_E(T, sx, Ex, ex);
     split_E(T, sy, Ey, ey);
-    pr[P_SX * ld + k] = sx;
-    pr[P_APX * ld + k] = sx >= 0.0 ? 1.0 - Ex : Ex;
-    pr[P_AMX * ld + k] = sx >= 0.0 ? Ex : 1.0 - Ex;
-    pr[P_EXPX * ld + k] = ex;
-    pr[P_BX * ld + k] = ex * kInv2SqrtPi * P.isb;
-    pr[P_SY * ld + k] = sy;
-    pr[P_APY * ld + k] = sy >= 0.0 ? 1.0 - Ey : Ey;
-    pr[P_AMY * ld + k] = sy >= 0.0 ? Ey : 1.0 - Ey;
-    pr[P_EXPY * ld + k] = ey;
-    pr[P_BY * ld + k] = ey * kInv2SqrtPi * P.isb;
+    pr[P_SX] = sx;
+    pr[P_APX] = sx >= 0.0 ? 1.0 - Ex : Ex;
+    pr[P_AMX] = sx >= 0.0 ? Ex : 1.0 - Ex;
+    pr[P_EXPX] = ex;
+    pr[P_BX] = ex * kInv2SqrtPi * P.isb;
+    pr[P_SY] = sy;
+    pr[P_APY] = sy >= 0.0 ? 1.0 - Ey : Ey;
+    pr[P_AMY] = sy >= 0.0 ? Ey : 1.0 - Ey;
+    pr[P_EXPY] = ey;
+    pr[P_BY] = ey * kInv2SqrtPi * P.isb;
+    if (dst.primf) {  // mixed precision: the sweeps' FP32 copy of the record
+        float *pf = dst.primf + (size_t)k * kPrimStride;
+#pragma unroll
+        for (int f = 0; f < P_NFIELDS; f++) pf[f] = (float)pr[f];
+    }
 }
 
 __global__ void k_reset_ctrl(Ctrl *c)
@@ -628,7 +714,8 @@ cudaError_t enqueue_res(const Dev &d, const Launch &L, int cur, cudaStream_t s, 
 {
     const int fin = d.K & 1;
     const int rb = (d.n * TPP + L.res_block - 1) / L.res_block;
-    k_residual<TPP><<<rb, L.res_block, 0, s>>>(d, d.set[cur], d.qx[fin], d.qy[fin]);
+    if (d.precision) k_residual<TPP, true><<<rb, L.res_block, 0, s>>>(d, d.set[cur], d.qx[fin], d.qy[fin]);
+    else k_residual<TPP, false><<<rb, L.res_block, 0, s>>>(d, d.set[cur], d.qx[fin], d.qy[fin]);
     (*launches)++;
     return cudaGetLastError();
 }
@@ -659,23 +746,27 @@ cudaError_t enqueue_grad_res(const Dev &d, const Launch &L, int cur, cudaStream_
     return e;
 }
 
+constexpr int kSweepLanes = 4;  // lanes per point in k_sweep
+
 template <int JVP>
 void enqueue_sweeps(const Dev &d, int cur, int n_levels, const int32_t *lvl_beg, const int32_t *lvl_act_end,
-                    const int32_t *lvl_end, cudaStream_t s, int *launches, bool fwd, bool bwd)
+                    cudaStream_t s, int *launches, bool fwd, bool bwd)
 {
     const StateSet st = d.set[cur];
     for (int l = 0; fwd && l < n_levels; l++) {
         const int np = lvl_act_end[l] - lvl_beg[l];
         if (np <= 0) continue;
-        const int blocks = (np * 32 + 255) / 256;
-        k_sweep<JVP, true><<<blocks, 256, 0, s>>>(d, st, lvl_beg[l], lvl_act_end[l], lvl_beg[l], lvl_end[l]);
+        const int blocks = (np * kSweepLanes + 255) / 256;
+        if (d.precision) k_sweep<JVP, true, kSweepLanes, float><<<blocks, 256, 0, s>>>(d, st, lvl_beg[l], lvl_act_end[l]);
+        else k_sweep<JVP, true, kSweepLanes, double><<<blocks, 256, 0, s>>>(d, st, lvl_beg[l], lvl_act_end[l]);
         (*launches)++;
     }
     for (int l = n_levels - 1; bwd && l >= 0; l--) {
         const int np = lvl_act_end[l] - lvl_beg[l];
         if (np <= 0) continue;
-        const int blocks = (np * 32 + 255) / 256;
-        k_sweep<JVP, false><<<blocks, 256, 0, s>>>(d, st, lvl_beg[l], lvl_act_end[l], lvl_beg[l], lvl_end[l]);
+        const int blocks = (np * kSweepLanes + 255) / 256;
+        if (d.precision) k_sweep<JVP, false, kSweepLanes, float><<<blocks, 256, 0, s>>>(d, st, lvl_beg[l], lvl_act_end[l]);
+        else k_sweep<JVP, false, kSweepLanes, double><<<blocks, 256, 0, s>>>(d, st, lvl_beg[l], lvl_act_end[l]);
         (*launches)++;
     }
 }
@@ -695,8 +786,8 @@ cudaError_t enqueue_phase(const Dev &d, const Launch &L, int cur, int ph, int n_
         return cudaGetLastError();
     case 3:
     case 4:
-        if (d.jvp == 0) enqueue_sweeps<0>(d, cur, n_levels, lvl_beg, lvl_act_end, lvl_end, s, launches, ph == 3, ph == 4);
-        else enqueue_sweeps<1>(d, cur, n_levels, lvl_beg, lvl_act_end, lvl_end, s, launches, ph == 3, ph == 4);
+        if (d.jvp == 0) enqueue_sweeps<0>(d, cur, n_levels, lvl_beg, lvl_act_end, s, launches, ph == 3, ph == 4);
+        else enqueue_sweeps<1>(d, cur, n_levels, lvl_beg, lvl_act_end, s, launches, ph == 3, ph == 4);
         return cudaGetLastError();
     case 5:
         k_update<true><<<(d.n + 255) / 256, 256, 0, s>>>(d, cur);

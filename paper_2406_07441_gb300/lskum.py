@@ -85,7 +85,7 @@ class Solver:
     """One context of liblskum for one cloud and one flow condition."""
 
     def __init__(self, cloud, mach, aoa_deg, cfl=100.0, inner_iters=3, jvp=JVP_EXACT, cfl_ramp_iters=0.0,
-                 first_order_iters=0, stream=None):
+                 first_order_iters=0, precision=0, stream=None):
         L = load()
         self.n = int(cloud.n)
         self._arrays = [np.ascontiguousarray(cloud.x, np.float64), np.ascontiguousarray(cloud.y, np.float64),
@@ -93,7 +93,7 @@ class Solver:
                         np.ascontiguousarray(cloud.ny, np.float64), np.ascontiguousarray(cloud.nbr_off, np.int32),
                         np.ascontiguousarray(cloud.nbr_idx, np.int32)]
         cl = lskum_cloud(self.n, *[a.ctypes.data for a in self._arrays])
-        op = lskum_opts(mach, aoa_deg, cfl, cfl_ramp_iters, inner_iters, jvp, 0, first_order_iters)
+        op = lskum_opts(mach, aoa_deg, cfl, cfl_ramp_iters, inner_iters, jvp, precision, first_order_iters)
         h = C.c_void_p()
         s = L.lskum_create(C.byref(cl), C.byref(op), C.c_void_p(stream), C.byref(h))
         self._arrays = None
