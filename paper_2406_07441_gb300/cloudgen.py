@@ -194,6 +194,45 @@ def _crosses_body(px, py, qx, qy, wx, wy, pw, qw):
     return out
 
 
+def _crosses_body_sectors(px, py, qx, qy, wx, wy, pw, qw, cp, cq, span_max=24):
+    """Same result as _crosses_body for points that lie in the sector of their
+    O-grid column (cp, cq): a segment can only cross the wall edges between
+    its end points' columns, taken the short way round (+-2 for the jitter);
+    segments spanning more than span_max columns use the full test."""
+    nseg = px.shape[0]
+    out = np.zeros(nseg, dtype=bool)
+    if nseg == 0:
+        return out
+    nw = wx.shape[0]
+    d = (cq - cp) % nw
+    fwd = d <= nw // 2
+    lo = np.where(fwd, cp, cq) - 2
+    span = np.where(fwd, d, nw - d) + 4
+    long_ = span > span_max
+    for o in range(span_max + 1):
+        m = (o <= span) & ~long_
+        if not m.any():
+            continue
+        j = (lo + o) % nw
+        ax, ay = wx[j], wy[j]
+        bx, by = wx[(j + 1) % nw], wy[(j + 1) % nw]
+        d1 = (bx - ax) * (py - ay) - (by - ay) * (px - ax)
+        d2 = (bx - ax) * (qy - ay) - (by - ay) * (qx - ax)
+        d3 = (qx - px) * (ay - py) - (qy - py) * (ax - px)
+        d4 = (qx - px) * (by - py) - (qy - py) * (bx - px)
+        incident = (pw == j) | (pw == (j + 1) % nw) | (qw == j) | (qw == (j + 1) % nw)
+        out |= m & (d1 * d2 < 0) & (d3 * d4 < 0) & ~incident
+    if long_.any():
+        ii = np.flatnonzero(long_)
+        out[ii] = _crosses_body(px[ii], py[ii], qx[ii], qy[ii], wx, wy, pw[ii], qw[ii])
+    both = (pw >= 0) & (qw >= 0)
+    if both.any():
+        dd = np.abs(pw - qw)
+        adj = (dd == 1) | (dd == nw - 1)
+        out |= both & ~adj
+    return out
+
+
 # ---------------------------------------------------------------------------
 # builders
 # ---------------------------------------------------------------------------
@@ -205,10 +244,48 @@ def _csr(rows):
     return off.astype(np.int32), idx.astype(np.int32)
 
 
+def _stencils_ok_all(x, y, flag, nx, ny, rows, tol=1e-6):
+    """Vectorised well-posedness of every point's stencil (same tests as the
+    per-point functions above): boolean per point."""
+    n = x.shape[0]
+    deg = np.fromiter((len(r) for r in rows), dtype=np.int64, count=n)
+    owner = np.repeat(np.arange(n), deg)
+    nb = np.fromiter((q for r in rows for q in r), dtype=np.int64, count=int(deg.sum()))
+    dx = x[nb] - x[owner]
+    dy = y[nb] - y[owner]
+    wall = flag == WALL
+
+    def seg(v):
+        return np.bincount(owner, weights=v, minlength=n)
+
+    sxx, syy, sxy = seg(dx * dx), seg(dy * dy), seg(dx * dy)
+    ok = (deg >= 2) & ((sxx * syy - sxy * sxy) > tol * sxx * syy)
+    e1x = np.where(wall, ny, 1.0)[owner]
+    e1y = np.where(wall, -nx, 0.0)[owner]
+    e2x = np.where(wall, nx, 0.0)[owner]
+    e2y = np.where(wall, ny, 1.0)[owner]
+    a = dx * e1x + dy * e1y
+    b = dx * e2x + dy * e2y
+    wo = wall[owner]
+    sets = [(a < 0, a, b), (a > 0, a, b), ((b < 0) & ~wo, b, a), (b > 0, b, a)]
+    for j, (m, d, dp) in enumerate(sets):
+        mf = m.astype(np.float64)
+        cnt = seg(mf)
+        sdd, spp, sdp = seg(mf * d * d), seg(mf * dp * dp), seg(mf * d * dp)
+        good = (cnt >= 2) & ((sdd * spp - sdp * sdp) > tol * sdd * spp)
+        need = flag != OUTER
+        if j == 2:
+            need = need & ~wall
+        ok &= good | ~need
+    return ok
+
+
 def _fix_stencils(x, y, flag, nx, ny, rows, cand_fn, body=None):
     """Augment stencils (nearest-first candidates) until every sub-stencil is well posed."""
     bad = 0
-    for p in range(x.shape[0]):
+    ok_all = _stencils_ok_all(x, y, flag, nx, ny, rows)
+    for p in np.flatnonzero(~ok_all):
+        p = int(p)
         r = rows[p]
         dx = x[r] - x[p]
         dy = y[r] - y[p]
@@ -316,6 +393,7 @@ def naca0012_jittered(n_i: int = 640, n_j: int = 256, jitter: float = 0.15,
     rm = rng.choice(interior, size=n_rm, replace=False)
     keep = np.ones(n0, dtype=bool)
     keep[rm] = False
+    col = np.tile(np.arange(n_i), n_j)[keep]  # O-grid column of every kept point
     x, y, flag, h = x[keep], y[keep], flag[keep], h[keep]
     n = x.shape[0]
     nx = np.zeros(n)
@@ -336,19 +414,23 @@ def naca0012_jittered(n_i: int = 640, n_j: int = 256, jitter: float = 0.15,
             & (np.minimum(y[P], y[Q]) <= 0.07) & (np.maximum(y[P], y[Q]) >= -0.07))
     cross = np.zeros(P.shape[0], dtype=bool)
     ii = np.flatnonzero(near)
-    cross[ii] = _crosses_body(x[P[ii]], y[P[ii]], x[Q[ii]], y[Q[ii]], wx, wy, widx[P[ii]], widx[Q[ii]])
+    cross[ii] = _crosses_body_sectors(x[P[ii]], y[P[ii]], x[Q[ii]], y[Q[ii]], wx, wy, widx[P[ii]], widx[Q[ii]],
+                                      col[P[ii]], col[Q[ii]])
     cross = cross.reshape(n, kq)
     valid = ~cross
     radius = radius_factor * h
-    rows = []
-    for p in range(n):
-        cand = nb[p][valid[p]]
-        dcand = dist[p][valid[p]]
-        m = int(np.sum(dcand <= radius[p]))
-        m = min(max(m, k_min), k_max, cand.size)
-        rows.append([int(q) for q in cand[:m]])
-    cand_lists = [nb[p][valid[p]] for p in range(n)]
-    rows, bad = _fix_stencils(x, y, flag, nx, ny, rows, lambda p: cand_lists[p])
+    # valid candidates first (stable: nearest first), then the count to keep
+    order = np.argsort(~valid, axis=1, kind="stable")
+    nbv = np.take_along_axis(nb, order, axis=1)
+    dv = np.take_along_axis(dist, order, axis=1)
+    nvalid = valid.sum(axis=1)
+    inrad = (dv <= radius[:, None]) & (np.arange(kq)[None, :] < nvalid[:, None])
+    m = np.minimum(np.minimum(np.maximum(inrad.sum(axis=1), k_min), k_max), nvalid)
+    keep = np.arange(kq)[None, :] < m[:, None]
+    flat = nbv[keep]
+    offs = np.concatenate([[0], np.cumsum(m)])
+    rows = [flat[offs[p]:offs[p + 1]].tolist() for p in range(n)]
+    rows, bad = _fix_stencils(x, y, flag, nx, ny, rows, lambda p: nbv[p][:nvalid[p]])
     off, idx = _csr(rows)
     return Cloud(x, y, flag, nx, ny, off, idx,
                  dict(kind="jittered", n_i=n_i, n_j=n_j, jitter=jitter, remove_frac=remove_frac,
