@@ -112,11 +112,11 @@ def _gpu_id(torch, dev):
         return str(dev)
 
 
-def cpu_baseline(cloud, iters, warm=0):
+def cpu_baseline(cloud, iters, warm=0, mach=0.85, aoa=1.0):
     """The FP64 oracle, as it stands, on one host core: `iters` iterations."""
     import oracle as O
     o = O.Oracle(cloud)
-    U = o.initial_state(0.85, 1.0)
+    U = o.initial_state(mach, aoa)
     r0 = o.run(U, 1 + warm, cfl=100.0, K=3, first_order=1)
     t0 = time.perf_counter()
     r = o.run(r0["U"], iters, cfl=100.0, K=3, n0=1 + warm, hist0=r0["hist0"])
@@ -163,7 +163,10 @@ def run_ours(args, rank, world, local_rank):
     info = s.info()
     nslots = int(np.count_nonzero(_memberships(cloud)))
     # first-order start-up, then warm-up iterations (untimed)
-    assert s.run(START + args.warmup) == START + args.warmup
+    assert s.run(START) == START
+    # launch shape chosen by the library's autotuner (real iterations, state restored)
+    tpp, lanes, _ = s.autotune(5)
+    assert s.run(args.warmup) == args.warmup
     stream = torch.cuda.ExternalStream(s.stream())
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -225,8 +228,154 @@ def run_ours(args, rank, world, local_rank):
                    "precision": "fp64" if args.precision == 0 else "fp32 sweeps, fp64 residual/update",
                    "mach": 0.85, "aoa_deg": 1.0, "cfl": 100.0, "inner_iters": 3, "jvp": "exact-AD",
                    "order": f"second (timed steps follow {START} untimed first-order start-up iterations)",
-                   "colours": info["n_colours"], "parallelism": "replicas" if world > 1 else "single",
+                   "colours": info["n_colours"],
+                   "launch_shape": {"threads_per_point": tpp, "sweep_lanes_per_point": lanes, "by": "autotune"},
+                   "parallelism": "replicas" if world > 1 else "single",
                    "l2": f"inputs larger than L2: device working set {ws / 2**20:.0f} MiB > 129 MiB L2"},
+        "roofline": {"bound": "alu", "kernel": "k_residual", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz",
+                     "launch_ms": res_ms, "phase_ms": phases},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": info["launches_per_iter"] * args.steps,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+BATCH_WORKLOAD = "naca0012_batch64"
+
+
+def _shard(cases, rank, world):
+    """Longest-processing-time split of the cases over the ranks (cost = points)."""
+    loads = [0] * world
+    mine = []
+    for k in sorted(range(len(cases)), key=lambda k: -cases[k]["n_i"] * cases[k]["n_j"]):
+        r = loads.index(min(loads))
+        loads[r] += cases[k]["n_i"] * cases[k]["n_j"]
+        if r == rank:
+            mine.append(k)
+    return sorted(mine)
+
+
+def _build_clouds(cases):
+    """Generate the clouds on the host cores (spawned workers, before any CUDA call)."""
+    import multiprocessing as mp
+
+    from paper_2406_07441_gb300 import cloudgen as cg
+    procs = max(1, min(len(cases), os.cpu_count() or 1, 16))
+    if procs == 1:
+        return [cg.build_case(c) for c in cases]
+    with mp.get_context("spawn").Pool(procs) as pool:
+        return pool.map(cg.build_case, cases, chunksize=1)
+
+
+def run_batch(args, rank, world, local_rank):
+    """64 clouds x free-stream conditions solved as one batched context:
+    FP32 sweeps, FP64 residual and update, cases sharded over the ranks."""
+    import numpy as np
+    import torch
+
+    from paper_2406_07441_gb300 import cloudgen as cg
+
+    cases_all = cg.batch_cases()
+    mine = _shard(cases_all, rank, world)
+    cases = [cases_all[k] for k in mine]
+    clouds = _build_clouds(cases)
+    from paper_2406_07441_gb300 import lskum
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    n = sum(c.n for c in clouds)
+    conds = [(c["mach"], c["aoa_deg"]) for c in cases]
+    s = lskum.Solver.batch(clouds, conds, cfl=100.0, inner_iters=3, jvp=lskum.JVP_EXACT, first_order_iters=START,
+                           precision=args.precision)
+    info = s.info()
+    nslots = int(sum(np.count_nonzero(_memberships(c)) for c in clouds))
+    assert s.run(START) == START
+    tpp, lanes, _ = s.autotune(5)
+    assert s.run(args.warmup) == args.warmup
+    it0 = [s.case_info(k)["iters"] for k in range(len(cases))]
+    stream = torch.cuda.ExternalStream(s.stream())
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(_gpu_id(torch, local_rank)) as clk:
+        e0.record(stream)
+        s.enqueue(args.steps)
+        e1.record(stream)
+        done = s.wait()
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    if done != args.steps:
+        raise RuntimeError(f"only {done} of {args.steps} iterations ran")
+    ms = e0.elapsed_time(e1)
+    infos = [s.case_info(k) for k in range(len(cases))]
+    # only the point-iterations of cases still running count: a case that
+    # failed (non-physical update or non-finite norm) is frozen and skipped
+    work = sum(c.n * (inf["iters"] - i0) for c, inf, i0 in zip(clouds, infos, it0))
+    failed = sum(1 for inf in infos if inf["status"] != 0)
+    pts = torch.tensor([float(n), float(work), float(failed)], device="cuda", dtype=torch.float64)
+    t = torch.tensor([ms], device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(pts, op=dist.ReduceOp.SUM)
+    ms_max = float(t.item())
+    n_all, work_all, failed_all = (float(x) for x in pts.tolist())
+    value = work_all / (ms_max / 1e3)
+    drops = [float(h[-1] / h[0]) for k, h in enumerate(s.case_residuals(k) for k in range(len(cases)))
+             if infos[k]["status"] == 0]
+
+    phases = s.time_phases(5)
+    res_ms = phases["residual"]
+    achieved = RES_FLOPS_PER_SLOT * nslots / (res_ms / 1e3) / 1e12
+
+    e2e_steps = min(args.steps, 10)
+    U = s.field(lskum.FIELD_U)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        s.set_conserved(U)
+        s.run(1)
+        U = s.field(lskum.FIELD_U)
+    torch.cuda.synchronize()
+    e2e_dt = time.perf_counter() - t0
+    e2e = {"value": world * work / args.steps * e2e_steps / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": int(U.nbytes),
+           "d2h_bytes_per_step": int(U.nbytes) + 8}
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if world == 1:
+        k0 = int(np.argmin([c.n for c in clouds]))
+        cv, cdt, cdone = cpu_baseline(clouds[k0], 10, mach=cases[k0]["mach"], aoa=cases[k0]["aoa_deg"])
+        cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{cdone} FP64 oracle iterations on the smallest case ({clouds[k0].n} points), one thread"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "strong" if world > 1 else "weak",
+        "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f64+f32", "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD, "cases": len(cases_all), "cases_this_rank": len(cases),
+                   "points": int(n_all), "failed_cases": int(failed_all),
+                   "point_iterations_timed": int(work_all), "precision": "fp64" if args.precision == 0 else
+                   "fp32 sweeps, fp64 residual/update", "cfl": 100.0, "inner_iters": 3, "jvp": "exact-AD",
+                   "order": f"second (timed steps follow {START} untimed first-order start-up iterations)",
+                   "colours": info["n_colours"],
+                   "launch_shape": {"threads_per_point": tpp, "sweep_lanes_per_point": lanes, "by": "autotune"},
+                   "parallelism": f"cases sharded over {world} ranks" if world > 1 else "single",
+                   "residual_drop_min_max": [min(drops), max(drops)] if drops else None,
+                   "l2": "inputs larger than L2"},
         "roofline": {"bound": "alu", "kernel": "k_residual", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
                      "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz",
@@ -268,16 +417,22 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", type=int, choices=[0, 1], default=0,
-                    help="0: plain FP64 (default); 1: FP32 sweeps with FP64 residual and update")
+    ap.add_argument("--precision", type=int, choices=[0, 1], default=None,
+                    help="0: plain FP64 (default for the single cloud); 1: FP32 sweeps with FP64 residual "
+                         "and update (default for the batch)")
+    ap.add_argument("--workload", choices=[WORKLOAD, BATCH_WORKLOAD], default=WORKLOAD)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     rank = _env_int("RANK", 0)
     world = _env_int("WORLD_SIZE", 1)
     local_rank = _env_int("LOCAL_RANK", 0)
+    if args.precision is None:
+        args.precision = 1 if args.workload == BATCH_WORKLOAD else 0
     if args.impl == "reference":
         run_reference(args, rank)
+    elif args.workload == BATCH_WORKLOAD:
+        run_batch(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

@@ -121,6 +121,38 @@ typedef struct {
 lskum_status lskum_create(const lskum_cloud *cloud, const lskum_opts *opts, void *cuda_stream,
                           lskum_ctx **out);
 
+/*
+ * Batched solves (a serving extension; no counterpart in the paper): n_cases
+ * independent flow problems, each with its own cloud and free stream, solved
+ * together.  The context holds the disjoint union of the clouds (caller point
+ * order: case 0's points, then case 1's, ...); one iteration launch covers
+ * every case, colour level by colour level.  Each case keeps its own residual
+ * history and drop test: a case that reaches the target stops updating while
+ * the others continue, and lskum_run returns when all have stopped (or after
+ * max_iters).  A case whose norm is not finite or whose update is
+ * non-physical fails alone: it keeps its last good state, its status
+ * (lskum_get_case_info) says why, and the others go on; lskum_run still
+ * returns LSKUM_OK.  A failed case stays frozen until a new state is set.
+ * opts[b] may differ only in mach and aoa_deg (LSKUM_ERR_ARG otherwise).
+ * The single-case calls act on the whole union (state, fields) or on case 0
+ * (residuals, forces).  Errors as lskum_create.
+ */
+lskum_status lskum_batch_create(const lskum_cloud *clouds, const lskum_opts *opts, int32_t n_cases, void *cuda_stream,
+                                lskum_ctx **out);
+
+/* Case cs (0 <= cs < n_cases): its residual history (as lskum_get_residuals),
+ * its Cl and Cd (with its own Mach and AoA), and its first point in the
+ * caller order of the union, its point count, the norms recorded, whether it
+ * has stopped (target reached or failed) in the last run, its status
+ * (LSKUM_OK, or LSKUM_ERR_DIVERGED / LSKUM_ERR_NONPOSITIVE for a failed case)
+ * and, for LSKUM_ERR_NONPOSITIVE, the offending point (caller order of the
+ * union; else -1).  Pointers other than the context may be NULL in
+ * lskum_get_case_info. */
+lskum_status lskum_get_case_residuals(lskum_ctx *ctx, int32_t cs, double *hist, int32_t cap, int32_t *n);
+lskum_status lskum_get_case_forces(lskum_ctx *ctx, int32_t cs, double *cl, double *cd);
+lskum_status lskum_get_case_info(lskum_ctx *ctx, int32_t cs, int32_t *first_point, int32_t *n_points, int32_t *iters,
+                                 int32_t *stopped, int32_t *status, int32_t *bad_point);
+
 /* Replace the state by primitive fields (f64[N] each, caller order); the wall
  * projection is applied and the residual history is cleared.
  * Errors: LSKUM_ERR_ARG (NULL), LSKUM_ERR_NONPOSITIVE (rho or p <= 0 or not
@@ -164,7 +196,7 @@ lskum_status lskum_get_state(lskum_ctx *ctx, double *rho, double *u, double *v, 
 lskum_status lskum_get_field(lskum_ctx *ctx, int32_t field, double *out);
 
 /* Density-residual norms of every iteration since the last set_state/create
- * (absolute, not divided by norm_1).  Copies min(cap, count) entries; *n gets
+ * (absolute, not divided by norm_1; case 0 of a batch).  Copies min(cap, count) entries; *n gets
  * the count. */
 lskum_status lskum_get_residuals(lskum_ctx *ctx, double *hist, int32_t cap, int32_t *n);
 
@@ -183,6 +215,20 @@ lskum_status lskum_get_order(lskum_ctx *ctx, int32_t *colour, int32_t *order, in
  * sweep, 5 update.  The iterations are real: the state advances by reps
  * iterations and the history grows.  Errors as lskum_run. */
 lskum_status lskum_time_phases(lskum_ctx *ctx, int32_t reps, double *ms);
+
+/* Autotune the launch shape (no counterpart in the paper; the kernels'
+ * results do not depend on it beyond the order of floating-point sums): for
+ * every threads-per-point count {1,2,4,8} of the q-derivative and residual
+ * kernels and lanes-per-point count {2,4,8} of the sweep kernels, re-capture
+ * the iteration graphs, run one warm-up iteration and time `trial_iters`
+ * iterations between CUDA events on the context's stream; keep the fastest
+ * shape.  The state, the per-case counters, stop flags and histories are
+ * saved before and restored after every trial, so the caller sees the
+ * context as before, only faster.  Outputs (each may be NULL): the chosen
+ * threads per point, lanes per point and its mean device time per iteration
+ * in ms.  Errors as lskum_run (the launch shape is then left unchanged). */
+lskum_status lskum_autotune(lskum_ctx *ctx, int32_t trial_iters, int32_t *tpp, int32_t *sweep_lanes,
+                            double *ms_per_iter);
 
 /* Number of points, of colours and of kernel launches one iteration makes. */
 lskum_status lskum_get_info(lskum_ctx *ctx, int32_t *n_points, int32_t *n_colours, int32_t *launches_per_iter);

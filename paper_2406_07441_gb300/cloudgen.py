@@ -478,6 +478,26 @@ WORKLOADS = {
 }
 
 
+def batch_cases(n_cases: int = 64, n_min: int = 20_000, n_max: int = 400_000, seed: int = BASE_SEED + 4):
+    """Cases of the multi-cloud batch: per case N ~ log-uniform[n_min, n_max]
+    points before removal, n_i : n_j = 2.5 : 1 with n_i even, Mach ~ U[0.3,
+    0.85], angle of attack ~ U[-4, 6] degrees, and its own cloud seed.  The
+    clouds are jittered O-grids with 10% of the interior points removed."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n_cases):
+        n = math.exp(rng.uniform(math.log(n_min), math.log(n_max)))
+        n_j = max(8, int(round(math.sqrt(n / 2.5))))
+        n_i = 2 * int(round(1.25 * n_j))
+        out.append(dict(n_i=n_i, n_j=n_j, mach=float(rng.uniform(0.3, 0.85)),
+                        aoa_deg=float(rng.uniform(-4.0, 6.0)), seed=seed + 1000 + k))
+    return out
+
+
+def build_case(case: dict) -> Cloud:
+    return naca0012_jittered(case["n_i"], case["n_j"], remove_frac=0.10, seed=case["seed"])
+
+
 def build_workload(name: str) -> Cloud:
     w = WORKLOADS[name]
     if w["builder"] == "block":

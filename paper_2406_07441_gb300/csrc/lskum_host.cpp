@@ -5,7 +5,9 @@
 #include "lskum_internal.h"
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
+#include <cstdint>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -70,6 +72,15 @@ struct lskum_ctx {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     double *pinned = nullptr;           // 4 * ld doubles of page-locked staging for state copies
     int launches_per_iter = 0;
+    // cases (a batch is the disjoint union of its cases' clouds, caller order
+    // = case 0's points, then case 1's, ...)
+    int32_t n_cases = 1;
+    std::vector<int32_t> case_off;      // [n_cases + 1] caller-order offsets
+    std::vector<double> case_mach, case_aoa;
+    std::vector<int32_t> case_of_caller;
+    int32_t *case_state = nullptr, *case_it = nullptr;  // device, per case
+    int32_t *case_err = nullptr, *case_bad = nullptr;
+    double *case_hist0 = nullptr;
     int cur = 0;                        // state set holding the current state
     int32_t it_base = 0;                // ctrl->it at the start of the pending enqueue
     int cur_base = 0;
@@ -168,26 +179,37 @@ struct HostPrep {
     std::vector<int32_t> lo_off, lo_nbr, up_off, up_nbr, sw_fwd, sw_bwd;
     std::vector<uint8_t> lo_mb, up_mb;
     std::vector<double> lo_w1, lo_w2, up_w1, up_w2;
+    // per-case norm blocks and case of every internal point
+    std::vector<int32_t> blk_pos, blk_case, case_blk, case_of_i;
 };
 static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &hp);
 static lskum_status upload(lskum_ctx *c, HostPrep &hp);
+static lskum_status build_graphs(lskum_ctx *c);
 
-lskum_status lskum_create(const lskum_cloud *cl, const lskum_opts *opts, void *cuda_stream, lskum_ctx **out)
+static bool opts_valid(const lskum_opts *o)
 {
-    if (!out) return fail(nullptr, LSKUM_ERR_ARG, "out is NULL");
-    *out = nullptr;
-    if (!cl || !opts) return fail(nullptr, LSKUM_ERR_ARG, "cloud or opts is NULL");
+    return (o->cfl > 0.0) && std::isfinite(o->cfl) && std::isfinite(o->mach) && std::isfinite(o->aoa_deg) &&
+           (o->cfl_ramp_iters >= 0.0) && o->inner_iters >= 0 && o->inner_iters <= 64 &&
+           (o->jvp == LSKUM_JVP_EXACT || o->jvp == LSKUM_JVP_INCREMENT) && (o->precision == 0 || o->precision == 1) &&
+           o->first_order_iters >= 0;
+}
+
+static bool opts_shared_equal(const lskum_opts *a, const lskum_opts *b)
+{
+    return a->cfl == b->cfl && a->cfl_ramp_iters == b->cfl_ramp_iters && a->inner_iters == b->inner_iters &&
+           a->jvp == b->jvp && a->precision == b->precision && a->first_order_iters == b->first_order_iters;
+}
+
+// Validate one case's cloud (indices local to the case).
+static lskum_status validate_cloud(const lskum_cloud *cl, int32_t cs)
+{
+    if (!cl) return fail(nullptr, LSKUM_ERR_ARG, "case %d: cloud is NULL", cs);
     const int32_t n = cl->n_points;
-    if (n < 1) return fail(nullptr, LSKUM_ERR_ARG, "n_points = %d < 1", n);
+    if (n < 1) return fail(nullptr, LSKUM_ERR_ARG, "case %d: n_points = %d < 1", cs, n);
     if (!cl->x || !cl->y || !cl->flag || !cl->nbr_off || !cl->nbr_idx)
-        return fail(nullptr, LSKUM_ERR_ARG, "a cloud array is NULL");
-    if (!(opts->cfl > 0.0) || !std::isfinite(opts->cfl) || !std::isfinite(opts->mach) ||
-        !std::isfinite(opts->aoa_deg) || !(opts->cfl_ramp_iters >= 0.0) || opts->inner_iters < 0 ||
-        opts->inner_iters > 64 || (opts->jvp != LSKUM_JVP_EXACT && opts->jvp != LSKUM_JVP_INCREMENT) ||
-        (opts->precision != 0 && opts->precision != 1) || opts->first_order_iters < 0)
-        return fail(nullptr, LSKUM_ERR_ARG, "invalid option value");
+        return fail(nullptr, LSKUM_ERR_ARG, "case %d: a cloud array is NULL", cs);
     const int32_t *off = cl->nbr_off, *idx = cl->nbr_idx;
-    if (off[0] != 0) return fail(nullptr, LSKUM_ERR_ARG, "nbr_off[0] != 0");
+    if (off[0] != 0) return fail(nullptr, LSKUM_ERR_ARG, "case %d: nbr_off[0] != 0", cs);
     bool has_wall = false;
     for (int32_t p = 0; p < n; p++) {
         if (off[p + 1] < off[p]) return fail(nullptr, LSKUM_ERR_ARG, "nbr_off decreases at point %d", p);
@@ -197,7 +219,7 @@ lskum_status lskum_create(const lskum_cloud *cl, const lskum_opts *opts, void *c
         if (off[p + 1] - off[p] > 255) return fail(nullptr, LSKUM_ERR_ARG, "more than 255 neighbours at point %d", p);
         has_wall |= cl->flag[p] == LSKUM_WALL;
     }
-    if (has_wall && (!cl->nx || !cl->ny)) return fail(nullptr, LSKUM_ERR_ARG, "wall points need nx, ny");
+    if (has_wall && (!cl->nx || !cl->ny)) return fail(nullptr, LSKUM_ERR_ARG, "case %d: wall points need nx, ny", cs);
     for (int32_t p = 0; p < n; p++) {
         for (int32_t e = off[p]; e < off[p + 1]; e++) {
             const int32_t q = idx[e];
@@ -211,13 +233,64 @@ lskum_status lskum_create(const lskum_cloud *cl, const lskum_opts *opts, void *c
             if (!(std::fabs(ln - 1.0) < 1e-6)) return fail(nullptr, LSKUM_ERR_ARG, "wall normal not unit at point %d", p);
         }
     }
+    return LSKUM_OK;
+}
+
+static lskum_status create_impl(const lskum_cloud *clouds, const lskum_opts *opts, int32_t n_cases,
+                                void *cuda_stream, lskum_ctx **out)
+{
+    if (!out) return fail(nullptr, LSKUM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!clouds || !opts || n_cases < 1) return fail(nullptr, LSKUM_ERR_ARG, "clouds, opts or n_cases invalid");
+    int64_t total = 0, total_nnz = 0;
+    for (int32_t b = 0; b < n_cases; b++) {
+        if (!opts_valid(&opts[b])) return fail(nullptr, LSKUM_ERR_ARG, "invalid option value (case %d)", b);
+        if (!opts_shared_equal(&opts[0], &opts[b]))
+            return fail(nullptr, LSKUM_ERR_ARG, "case %d: options other than mach/aoa differ from case 0", b);
+        lskum_status v = validate_cloud(&clouds[b], b);
+        if (v != LSKUM_OK) return v;
+        total += clouds[b].n_points;
+        total_nnz += clouds[b].nbr_off[clouds[b].n_points];
+    }
+    if (total > INT32_MAX / 2 || total_nnz > INT32_MAX) return fail(nullptr, LSKUM_ERR_ARG, "batch too large");
+    // the disjoint union of the cases' clouds
+    const int32_t n = (int32_t)total;
+    std::vector<double> ux, uy, unx(n, 0.0), uny(n, 0.0);
+    std::vector<uint8_t> ufl;
+    std::vector<int32_t> uoff(1, 0), uidx;
+    ux.reserve(n);
+    uy.reserve(n);
+    ufl.reserve(n);
+    uidx.reserve(total_nnz);
     lskum_ctx *c = new (std::nothrow) lskum_ctx();
     if (!c) return fail(nullptr, LSKUM_ERR_OOM, "host allocation failed");
+    c->n_cases = n_cases;
+    c->case_off.assign(1, 0);
+    for (int32_t b = 0; b < n_cases; b++) {
+        const lskum_cloud &cl = clouds[b];
+        const int32_t base = (int32_t)ux.size();
+        for (int32_t p = 0; p < cl.n_points; p++) {
+            ux.push_back(cl.x[p]);
+            uy.push_back(cl.y[p]);
+            ufl.push_back(cl.flag[p]);
+            if (cl.flag[p] == LSKUM_WALL) {
+                unx[base + p] = cl.nx[p];
+                uny[base + p] = cl.ny[p];
+            }
+            for (int32_t e = cl.nbr_off[p]; e < cl.nbr_off[p + 1]; e++) uidx.push_back(base + cl.nbr_idx[e]);
+            uoff.push_back((int32_t)uidx.size());
+            c->case_of_caller.push_back(b);
+        }
+        c->case_off.push_back((int32_t)ux.size());
+        c->case_mach.push_back(opts[b].mach);
+        c->case_aoa.push_back(opts[b].aoa_deg);
+    }
+    const lskum_cloud u = {n, ux.data(), uy.data(), ufl.data(), unx.data(), uny.data(), uoff.data(), uidx.data()};
     c->n = n;
-    c->opts = *opts;
+    c->opts = opts[0];
     c->user_stream = (cudaStream_t)cuda_stream;
     HostPrep hp;
-    lskum_status s = prepare_host(c, cl, hp);  // no CUDA call before this returns
+    lskum_status s = prepare_host(c, &u, hp);  // no CUDA call before this returns
     if (s == LSKUM_OK) {
         cudaError_t e = cudaGetDevice(&c->device);
         s = e == cudaSuccess ? upload(c, hp) : cuda_fail(c, e, "cudaGetDevice");
@@ -229,6 +302,21 @@ lskum_status lskum_create(const lskum_cloud *cl, const lskum_opts *opts, void *c
     }
     *out = c;
     return LSKUM_OK;
+}
+
+lskum_status lskum_create(const lskum_cloud *cl, const lskum_opts *opts, void *cuda_stream, lskum_ctx **out)
+{
+    if (!cl || !opts) {
+        if (out) *out = nullptr;
+        return fail(nullptr, LSKUM_ERR_ARG, "cloud or opts is NULL");
+    }
+    return create_impl(cl, opts, 1, cuda_stream, out);
+}
+
+lskum_status lskum_batch_create(const lskum_cloud *clouds, const lskum_opts *opts, int32_t n_cases,
+                                void *cuda_stream, lskum_ctx **out)
+{
+    return create_impl(clouds, opts, n_cases, cuda_stream, out);
 }
 
 static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &hp)
@@ -465,6 +553,20 @@ static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &
         fl_i[k] = c->flag[p];
     }
 
+    // per-case norm blocks over caller positions (never straddling two cases)
+    hp.case_blk.assign(1, 0);
+    hp.blk_pos.clear();
+    hp.blk_case.clear();
+    for (int32_t b = 0; b < c->n_cases; b++) {
+        for (int32_t p0 = c->case_off[b]; p0 < c->case_off[b + 1]; p0 += 256) {
+            hp.blk_pos.push_back(p0);
+            hp.blk_case.push_back(b);
+        }
+        hp.case_blk.push_back((int32_t)hp.blk_pos.size());
+    }
+    hp.blk_pos.push_back(n);  // block j ends where block j + 1 (or the next case) starts
+    hp.case_of_i.assign(ld, 0);
+    for (int32_t k = 0; k < n; k++) hp.case_of_i[k] = c->case_of_caller[c->perm[k]];
     return LSKUM_OK;
 }
 
@@ -535,11 +637,21 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
     // launch shape: enough threads per point to fill the GPU on small clouds
     c->launch.res_block = 128;
     c->launch.tpp = n >= 100000 ? 1 : (n >= 50000 ? 2 : (n >= 25000 ? 4 : 8));
-    d.n_blk = residual_blocks(d, c->launch);
+    c->launch.sweep_lanes = 4;
+    d.n_blk = (int32_t)hp.blk_case.size();
+    d.n_cases = c->n_cases;
     d.blk = A.alloc<double>(d.n_blk);
+    int32_t *dblk_pos = A.alloc<int32_t>(hp.blk_pos.size()), *dblk_case = A.alloc<int32_t>(hp.blk_case.size());
+    int32_t *dcase_blk = A.alloc<int32_t>(hp.case_blk.size()), *dinv = A.alloc<int32_t>(n);
+    int32_t *dcase_of = A.alloc<int32_t>(ld);
     c->ctrl = A.alloc<Ctrl>(1);
+    c->case_state = A.alloc<int32_t>(c->n_cases);
+    c->case_it = A.alloc<int32_t>(c->n_cases);
+    c->case_hist0 = A.alloc<double>(c->n_cases);
+    c->case_err = A.alloc<int32_t>(c->n_cases);
+    c->case_bad = A.alloc<int32_t>(c->n_cases);
     c->hist_cap = 4096;
-    c->hist = A.alloc<double>(c->hist_cap);
+    c->hist = A.alloc<double>((size_t)c->n_cases * c->hist_cap);
     if (A.err != cudaSuccess) return cuda_fail(c, A.err, "cudaMalloc");
     e = cudaMemset(c->ctrl, 0, sizeof(Ctrl));
     if (e == cudaSuccess) e = cudaMallocHost(&c->pinned, 4 * (size_t)ld * sizeof(double));
@@ -563,6 +675,12 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
     d.gyx = dyx;
     d.gyy = dyy;
     d.ctrl = c->ctrl;
+    d.case_state = c->case_state;
+    d.blk_pos = dblk_pos;
+    d.blk_case = dblk_case;
+    d.case_blk = dcase_blk;
+    d.inv = dinv;
+    d.case_of = dcase_of;
     d.lo_off = dlo_off;
     d.up_off = dup_off;
     d.lo_nbr = dlo_nbr;
@@ -618,6 +736,16 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
     up(dup_w2, hp.up_w2.data(), hp.up_w2.size() * sizeof(double));
     up(dsw_fwd, hp.sw_fwd.data(), hp.sw_fwd.size() * sizeof(int32_t));
     up(dsw_bwd, hp.sw_bwd.data(), hp.sw_bwd.size() * sizeof(int32_t));
+    up(dblk_pos, hp.blk_pos.data(), hp.blk_pos.size() * sizeof(int32_t));
+    up(dblk_case, hp.blk_case.data(), hp.blk_case.size() * sizeof(int32_t));
+    up(dcase_blk, hp.case_blk.data(), hp.case_blk.size() * sizeof(int32_t));
+    up(dinv, c->inv.data(), n * sizeof(int32_t));
+    up(dcase_of, hp.case_of_i.data(), ld * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemset(c->case_state, 0, c->n_cases * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemset(c->case_it, 0, c->n_cases * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemset(c->case_hist0, 0, c->n_cases * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemset(c->case_err, 0, c->n_cases * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemset(c->case_bad, 0x7f, c->n_cases * sizeof(int32_t));
     if (mixed) {
         up(dlo_w1f, flo_w1.data(), flo_w1.size() * sizeof(float));
         up(dlo_w2f, flo_w2.data(), flo_w2.size() * sizeof(float));
@@ -636,19 +764,36 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
 
     // ---- free-stream start ----
     const double al = c->opts.aoa_deg * M_PI / 180.0;
-    const double uinf = c->opts.mach * std::cos(al), vinf = c->opts.mach * std::sin(al), pinf = 1.0 / 1.4;
-    std::vector<double> rho(n, 1.0), uu(n, uinf), vv(n, vinf), pp(n, pinf);
+    std::vector<double> rho(n, 1.0), uu(n), vv(n), pp(n, 1.0 / 1.4);
+    for (int32_t b = 0; b < c->n_cases; b++) {
+        const double alb = c->case_aoa[b] * M_PI / 180.0;
+        for (int32_t p = c->case_off[b]; p < c->case_off[b + 1]; p++) {
+            uu[p] = c->case_mach[b] * std::cos(alb);
+            vv[p] = c->case_mach[b] * std::sin(alb);
+        }
+    }
+    (void)al;
     lskum_status s = lskum_set_state(c, rho.data(), uu.data(), vv.data(), pp.data());
     if (s != LSKUM_OK) return s;
 
-    // ---- one CUDA graph per state parity ----
+    return build_graphs(c);
+}
+
+// (Re)capture one CUDA graph per state parity with the current launch shape.
+static lskum_status build_graphs(lskum_ctx *c)
+{
+    for (auto &g : c->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
     for (int par = 0; par < 2; par++) {
         cudaGraph_t g = nullptr;
-        e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+        cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamBeginCapture");
         int launches = 0;
-        cudaError_t le = launch_iteration(d, c->launch, par, nc, c->lvl_beg.data(), c->lvl_act_end.data(),
-                                          c->lvl_end.data(), c->stream, &launches);
+        cudaError_t le = launch_iteration(c->dev, c->launch, par, c->n_colours, c->lvl_beg.data(),
+                                          c->lvl_act_end.data(), c->lvl_end.data(), c->stream, &launches);
         e = cudaStreamEndCapture(c->stream, &g);
         if (le != cudaSuccess) {
             if (g) cudaGraphDestroy(g);
@@ -705,15 +850,79 @@ lskum_status read_ctrl(lskum_ctx *c, Ctrl *h)
     return LSKUM_OK;
 }
 
+// Write the host copy of the control block (with the context's per-case
+// pointers filled in) to the device and wait for it.
+lskum_status write_ctrl(lskum_ctx *c, Ctrl &h)
+{
+    h.n_cases = c->n_cases;
+    h.case_state = c->case_state;
+    h.case_it = c->case_it;
+    h.case_hist0 = c->case_hist0;
+    h.case_err = c->case_err;
+    h.case_bad = c->case_bad;
+    h.hist = c->hist;
+    h.hist_cap = c->hist_cap;
+    cudaError_t e = cudaMemcpyAsync(c->ctrl, &h, sizeof(Ctrl), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "writing the control block");
+    return LSKUM_OK;
+}
+
+// Per-case counters.  A new state (`fresh`) clears everything: every case
+// runs again, failures are forgotten and, with `history`, the histories are
+// cleared.  Otherwise stopped cases run again and failed cases stay failed.
+lskum_status reset_cases(lskum_ctx *c, bool history, bool fresh)
+{
+    cudaError_t e = cudaSuccess;
+    if (fresh) {
+        e = cudaMemsetAsync(c->case_state, 0, c->n_cases * sizeof(int32_t), c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->case_err, 0, c->n_cases * sizeof(int32_t), c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->case_bad, 0x7f, c->n_cases * sizeof(int32_t), c->stream);
+    } else {
+        std::vector<int32_t> st(c->n_cases);
+        e = cudaMemcpyAsync(st.data(), c->case_state, c->n_cases * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                            c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        for (auto &x : st) x = (x == kFailed || x == kFailedNow) ? (int32_t)kFailed : (int32_t)kRunning;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c->case_state, st.data(), c->n_cases * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    }
+    if (history && e == cudaSuccess) e = cudaMemsetAsync(c->case_it, 0, c->n_cases * sizeof(int32_t), c->stream);
+    if (history && e == cudaSuccess) e = cudaMemsetAsync(c->case_hist0, 0, c->n_cases * sizeof(double), c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "resetting the cases");
+    return LSKUM_OK;
+}
+
+lskum_status read_case_arrays(lskum_ctx *c, std::vector<int32_t> *state, std::vector<int32_t> *it)
+{
+    cudaError_t e = cudaSuccess;
+    if (state) {
+        state->resize(c->n_cases);
+        e = cudaMemcpyAsync(state->data(), c->case_state, c->n_cases * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                            c->stream);
+    }
+    if (it && e == cudaSuccess) {
+        it->resize(c->n_cases);
+        e = cudaMemcpyAsync(it->data(), c->case_it, c->n_cases * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "reading the case counters");
+    return LSKUM_OK;
+}
+
+// Room for `need` norms per case ([n_cases][cap] rows, copied row by row).
 lskum_status ensure_hist(lskum_ctx *c, int32_t need)
 {
     if (need <= c->hist_cap) return LSKUM_OK;
     int32_t cap = c->hist_cap;
     while (cap < need) cap *= 2;
     double *h = nullptr;
-    cudaError_t e = cudaMalloc(&h, cap * sizeof(double));
+    cudaError_t e = cudaMalloc(&h, (size_t)c->n_cases * cap * sizeof(double));
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc(history)");
-    e = cudaMemcpyAsync(h, c->hist, c->hist_cap * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    e = cudaMemcpy2DAsync(h, cap * sizeof(double), c->hist, c->hist_cap * sizeof(double),
+                          c->hist_cap * sizeof(double), c->n_cases, cudaMemcpyDeviceToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         cudaFree(h);
@@ -754,18 +963,14 @@ lskum_status state_from_conserved(lskum_ctx *c, const std::vector<double> &Ucall
     lskum_status s = read_ctrl(c, &h);
     if (s != LSKUM_OK) return s;
     if (h.error) return fail(c, LSKUM_ERR_NONPOSITIVE, "non-physical state at point %d", c->perm[h.bad_point]);
-    if (reset_hist) {
-        h.it = 0;
-        h.hist0 = 0.0;
-    }
-    h.hist = c->hist;
-    h.hist_cap = c->hist_cap;
-    h.stop = h.stop_after = h.error = 0;
+    if (reset_hist) h.it = 0;
+    h.stop = h.error = 0;
     h.bad_point = 0x7fffffff;
-    e = cudaMemcpyAsync(c->ctrl, &h, sizeof(Ctrl), cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    if (e == cudaSuccess) e = release_user(c);
-    if (e != cudaSuccess) return cuda_fail(c, e, "writing the control block");
+    s = reset_cases(c, reset_hist, true);
+    if (s == LSKUM_OK) s = write_ctrl(c, h);
+    if (s != LSKUM_OK) return s;
+    e = release_user(c);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ordering the caller's stream");
     return LSKUM_OK;
 }
 
@@ -805,17 +1010,20 @@ lskum_status lskum_enqueue(lskum_ctx *c, int32_t max_iters, double target_drop)
     if (c->pending) return fail(c, LSKUM_ERR_ARG, "an enqueued run has not been waited for");
     Ctrl h{};
     lskum_status s = read_ctrl(c, &h);
+    std::vector<int32_t> its;
+    if (s == LSKUM_OK) s = read_case_arrays(c, nullptr, &its);
     if (s != LSKUM_OK) return s;
-    s = ensure_hist(c, h.it + max_iters);
+    const int32_t most = *std::max_element(its.begin(), its.end());
+    s = ensure_hist(c, most + max_iters);
     if (s != LSKUM_OK) return s;
-    h.hist = c->hist;
-    h.hist_cap = c->hist_cap;
-    h.stop = h.stop_after = h.error = 0;
+    h.stop = h.error = 0;
     h.bad_point = 0x7fffffff;
     h.target = target_drop;
     cudaError_t e = join_user(c);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(c->ctrl, &h, sizeof(Ctrl), cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ordering after the caller's stream");
+    s = reset_cases(c, false, false);
+    if (s == LSKUM_OK) s = write_ctrl(c, h);
+    if (s != LSKUM_OK) return s;
     c->it_base = h.it;
     c->cur_base = c->cur;
     int par = c->cur;
@@ -838,25 +1046,17 @@ lskum_status lskum_wait(lskum_ctx *c, int32_t *iters_done)
     Ctrl h{};
     lskum_status s = read_ctrl(c, &h);
     if (s != LSKUM_OK) return s;
-    int32_t done = h.it - c->it_base;  // iterations whose norm was recorded
-    if (h.error == LSKUM_ERR_NONPOSITIVE) {
-        // the failed iteration's update was not applied: roll back its norm
-        done -= 1;
-        Ctrl w = h;
-        w.it = h.it - 1;
-        cudaMemcpyAsync(c->ctrl, &w, sizeof(Ctrl), cudaMemcpyHostToDevice, c->stream);
-        cudaStreamSynchronize(c->stream);
-    }
+    int32_t done = h.it - c->it_base;  // iterations started (k_begin)
+    if (h.error) done -= 1;            // the failed iteration's update was not applied
     c->cur = (c->cur_base + done) & 1;
     if (iters_done) *iters_done = done;
     if (h.error == LSKUM_ERR_NONPOSITIVE)
         return fail(c, LSKUM_ERR_NONPOSITIVE, "non-physical update at point %d in iteration %d",
                     c->perm[h.bad_point], h.it);
-    if (h.error == LSKUM_ERR_DIVERGED) {
-        c->cur = (c->cur_base + done - 1) & 1;  // that iteration never reached its update
-        if (iters_done) *iters_done = done - 1;
-        return fail(c, LSKUM_ERR_DIVERGED, "residual norm not finite in iteration %d", h.it);
-    }
+    if (h.error == LSKUM_ERR_DIVERGED)
+        return fail(c, LSKUM_ERR_DIVERGED, "residual norm of case %d not finite in iteration %d", -1 - h.bad_point,
+                    h.it);
+    if (h.error) return fail(c, LSKUM_ERR_CUDA, "device error %d", h.error);
     return LSKUM_OK;
 }
 
@@ -949,32 +1149,39 @@ lskum_status lskum_get_state(lskum_ctx *c, double *rho, double *u, double *v, do
     return LSKUM_OK;
 }
 
-lskum_status lskum_get_residuals(lskum_ctx *c, double *hist, int32_t cap, int32_t *n)
+lskum_status lskum_get_case_residuals(lskum_ctx *c, int32_t cs, double *hist, int32_t cap, int32_t *n)
 {
-    if (!c || !n || cap < 0 || (cap > 0 && !hist)) return c ? fail(c, LSKUM_ERR_ARG, "bad argument") : LSKUM_ERR_ARG;
+    if (!c || !n || cap < 0 || (cap > 0 && !hist) || cs < 0 || cs >= (c ? c->n_cases : 0))
+        return c ? fail(c, LSKUM_ERR_ARG, "bad argument") : LSKUM_ERR_ARG;
     if (c->pending) return fail(c, LSKUM_ERR_ARG, "an enqueued run has not been waited for");
-    Ctrl h{};
-    lskum_status s = read_ctrl(c, &h);
+    std::vector<int32_t> its;
+    lskum_status s = read_case_arrays(c, nullptr, &its);
     if (s != LSKUM_OK) return s;
-    *n = h.it;
-    const int32_t m = std::min(cap, h.it);
+    *n = std::min(its[cs], c->hist_cap);
+    const int32_t m = std::min(cap, *n);
     if (m > 0) {
-        cudaError_t e = cudaMemcpyAsync(hist, c->hist, m * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        cudaError_t e = cudaMemcpyAsync(hist, c->hist + (size_t)cs * c->hist_cap, m * sizeof(double),
+                                        cudaMemcpyDeviceToHost, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy history");
     }
     return LSKUM_OK;
 }
 
-lskum_status lskum_get_forces(lskum_ctx *c, double *cl, double *cd)
+lskum_status lskum_get_residuals(lskum_ctx *c, double *hist, int32_t cap, int32_t *n)
 {
-    if (!c || !cl || !cd) return c ? fail(c, LSKUM_ERR_ARG, "NULL argument") : LSKUM_ERR_ARG;
+    return lskum_get_case_residuals(c, 0, hist, cap, n);
+}
+
+lskum_status lskum_get_case_forces(lskum_ctx *c, int32_t cs, double *cl, double *cd)
+{
+    if (!c || !cl || !cd || cs < 0 || cs >= c->n_cases) return c ? fail(c, LSKUM_ERR_ARG, "bad argument") : LSKUM_ERR_ARG;
     if (c->pending) return fail(c, LSKUM_ERR_ARG, "an enqueued run has not been waited for");
     std::vector<double> U;
     lskum_status s = download(c, c->dev.set[c->cur].U, 4, U);
     if (s != LSKUM_OK) return s;
     std::vector<int32_t> w;
-    for (int32_t p = 0; p < c->n; p++)
+    for (int32_t p = c->case_off[cs]; p < c->case_off[cs + 1]; p++)
         if (c->flag[p] == LSKUM_WALL) w.push_back(p);
     *cl = 0.0;
     *cd = 0.0;
@@ -997,10 +1204,41 @@ lskum_status lskum_get_forces(lskum_ctx *c, double *cl, double *cd)
         Fx -= (pr - pinf) * orient * ey;
         Fy -= (pr - pinf) * (-orient * ex);
     }
-    const double al = c->opts.aoa_deg * M_PI / 180.0;
-    const double qinf = 0.5 * c->opts.mach * c->opts.mach;
+    const double al = c->case_aoa[cs] * M_PI / 180.0;
+    const double qinf = 0.5 * c->case_mach[cs] * c->case_mach[cs];
     *cl = (Fy * std::cos(al) - Fx * std::sin(al)) / qinf;
     *cd = (Fx * std::cos(al) + Fy * std::sin(al)) / qinf;
+    return LSKUM_OK;
+}
+
+lskum_status lskum_get_forces(lskum_ctx *c, double *cl, double *cd)
+{
+    return lskum_get_case_forces(c, 0, cl, cd);
+}
+
+lskum_status lskum_get_case_info(lskum_ctx *c, int32_t cs, int32_t *first_point, int32_t *n_points,
+                                 int32_t *iters, int32_t *stopped, int32_t *status, int32_t *bad_point)
+{
+    if (!c || cs < 0 || cs >= c->n_cases) return c ? fail(c, LSKUM_ERR_ARG, "bad argument") : LSKUM_ERR_ARG;
+    if (c->pending) return fail(c, LSKUM_ERR_ARG, "an enqueued run has not been waited for");
+    std::vector<int32_t> st, its;
+    lskum_status s = read_case_arrays(c, &st, &its);
+    int32_t err = 0, bad = 0x7fffffff;
+    cudaError_t e = cudaSuccess;
+    if (s == LSKUM_OK) {
+        e = cudaMemcpyAsync(&err, c->case_err + cs, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&bad, c->case_bad + cs, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) s = cuda_fail(c, e, "reading the case status");
+    }
+    if (s != LSKUM_OK) return s;
+    if (first_point) *first_point = c->case_off[cs];
+    if (n_points) *n_points = c->case_off[cs + 1] - c->case_off[cs];
+    if (iters) *iters = its[cs];
+    if (stopped) *stopped = st[cs] != kRunning;
+    if (status) *status = err;
+    if (bad_point) *bad_point = (err == LSKUM_ERR_NONPOSITIVE && bad >= 0 && bad < c->n) ? c->perm[bad] : -1;
     return LSKUM_OK;
 }
 
@@ -1010,14 +1248,17 @@ lskum_status lskum_time_phases(lskum_ctx *c, int32_t reps, double *ms)
     if (c->pending) return fail(c, LSKUM_ERR_ARG, "an enqueued run has not been waited for");
     Ctrl h{};
     lskum_status s = read_ctrl(c, &h);
+    std::vector<int32_t> its;
+    if (s == LSKUM_OK) s = read_case_arrays(c, nullptr, &its);
     if (s != LSKUM_OK) return s;
-    s = ensure_hist(c, h.it + reps);
+    s = ensure_hist(c, *std::max_element(its.begin(), its.end()) + reps);
     if (s != LSKUM_OK) return s;
-    h.hist = c->hist;
-    h.hist_cap = c->hist_cap;
-    h.stop = h.stop_after = h.error = 0;
+    h.stop = h.error = 0;
     h.target = 0.0;
-    cudaError_t e = cudaMemcpyAsync(c->ctrl, &h, sizeof(Ctrl), cudaMemcpyHostToDevice, c->stream);
+    s = reset_cases(c, false, false);
+    if (s == LSKUM_OK) s = write_ctrl(c, h);
+    if (s != LSKUM_OK) return s;
+    cudaError_t e = cudaSuccess;
     cudaEvent_t ev[7];
     for (auto &x : ev)
         if (e == cudaSuccess) e = cudaEventCreate(&x);
@@ -1052,6 +1293,131 @@ lskum_status lskum_time_phases(lskum_ctx *c, int32_t reps, double *ms)
     return LSKUM_OK;
 }
 
+lskum_status lskum_autotune(lskum_ctx *c, int32_t trial_iters, int32_t *tpp, int32_t *sweep_lanes, double *ms_per_iter)
+{
+    if (!c || trial_iters < 1) return c ? fail(c, LSKUM_ERR_ARG, "bad argument") : LSKUM_ERR_ARG;
+    if (c->pending) return fail(c, LSKUM_ERR_ARG, "an enqueued run has not been waited for");
+    // save the state set (device copies, so the restored state is bitwise
+    // the same), the counters and the histories; every trial is restored
+    const size_t ld = c->ld;
+    const size_t bytes_d = (8 * ld + (size_t)kPrimStride * ld) * sizeof(double);
+    const size_t bytes_f = c->dev.set[0].primf ? (size_t)kPrimStride * ld * sizeof(float) : 0;
+    char *save = nullptr;
+    cudaError_t e = cudaMalloc(&save, bytes_d + bytes_f);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc(autotune save)");
+    struct Free {
+        char *p;
+        ~Free() { cudaFree(p); }
+    } free_save{save};
+    auto copy_set = [&](bool to_save) -> cudaError_t {
+        const StateSet &st = c->dev.set[c->cur];
+        char *parts[4] = {(char *)st.U, (char *)st.q, (char *)st.prim, (char *)st.primf};
+        const size_t sz[4] = {4 * ld * sizeof(double), 4 * ld * sizeof(double),
+                              (size_t)kPrimStride * ld * sizeof(double), bytes_f};
+        size_t off = 0;
+        cudaError_t ee = cudaSuccess;
+        for (int i = 0; i < 4 && ee == cudaSuccess; i++) {
+            if (!sz[i]) continue;
+            ee = to_save ? cudaMemcpyAsync(save + off, parts[i], sz[i], cudaMemcpyDeviceToDevice, c->stream)
+                         : cudaMemcpyAsync(parts[i], save + off, sz[i], cudaMemcpyDeviceToDevice, c->stream);
+            off += sz[i];
+        }
+        return ee;
+    };
+    e = copy_set(true);
+    if (e != cudaSuccess) return cuda_fail(c, e, "saving the state");
+    lskum_status s = LSKUM_OK;
+    Ctrl h0{};
+    s = read_ctrl(c, &h0);
+    std::vector<int32_t> st0, it0;
+    if (s == LSKUM_OK) s = read_case_arrays(c, &st0, &it0);
+    if (s == LSKUM_OK) s = ensure_hist(c, *std::max_element(it0.begin(), it0.end()) + trial_iters + 2);
+    if (s != LSKUM_OK) return s;
+    std::vector<double> hist0(c->n_cases), hist((size_t)c->n_cases * c->hist_cap);
+    e = cudaMemcpyAsync(hist0.data(), c->case_hist0, c->n_cases * sizeof(double), cudaMemcpyDeviceToHost,
+                                    c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hist.data(), c->hist, hist.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "saving the state");
+    const int cap0 = c->hist_cap;
+    auto restore = [&]() -> lskum_status {
+        cudaError_t ee = copy_set(false);
+        if (ee == cudaSuccess)
+            ee = cudaMemcpyAsync(c->case_it, it0.data(), c->n_cases * sizeof(int32_t),
+                                         cudaMemcpyHostToDevice, c->stream);
+        if (ee == cudaSuccess)
+            ee = cudaMemcpyAsync(c->case_state, st0.data(), c->n_cases * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                 c->stream);
+        if (ee == cudaSuccess)
+            ee = cudaMemcpyAsync(c->case_hist0, hist0.data(), c->n_cases * sizeof(double), cudaMemcpyHostToDevice,
+                                 c->stream);
+        if (ee == cudaSuccess)
+            ee = cudaMemcpy2DAsync(c->hist, c->hist_cap * sizeof(double), hist.data(), cap0 * sizeof(double),
+                                   cap0 * sizeof(double), c->n_cases, cudaMemcpyHostToDevice, c->stream);
+        if (ee == cudaSuccess) ee = cudaStreamSynchronize(c->stream);
+        if (ee != cudaSuccess) return cuda_fail(c, ee, "restoring the state");
+        Ctrl h = h0;
+        h.stop = h.error = 0;
+        return write_ctrl(c, h);
+    };
+    const Launch orig = c->launch;
+    Launch best = orig;
+    double best_ms = 1e300;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventCreate");
+    for (int tp : {1, 2, 4, 8}) {
+        for (int gl : {2, 4, 8}) {
+            c->launch.tpp = tp;
+            c->launch.sweep_lanes = gl;
+            s = build_graphs(c);
+            int32_t warm = 0;
+            if (s == LSKUM_OK) s = lskum_run(c, 1, 0.0, &warm);  // warm-up
+            if (s == LSKUM_OK) s = lskum_enqueue(c, 0, 0.0);     // sets up the control block
+            if (s == LSKUM_OK) s = lskum_wait(c, nullptr);
+            if (s != LSKUM_OK) break;
+            const int32_t it_start = h0.it + warm;
+            int par = c->cur;
+            e = cudaEventRecord(e0, c->stream);
+            for (int32_t i = 0; i < trial_iters && e == cudaSuccess; i++, par ^= 1)
+                e = cudaGraphLaunch(c->graph[par], c->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                s = cuda_fail(c, e, "timing a launch shape");
+                break;
+            }
+            Ctrl hc{};
+            s = read_ctrl(c, &hc);
+            if (s != LSKUM_OK) break;
+            c->cur = (c->cur + (hc.it - it_start)) & 1;  // trial iterations that ran
+            if (warm == 1 && !hc.error && !hc.stop && hc.it - it_start == trial_iters &&
+                ms / trial_iters < best_ms) {
+                best_ms = ms / trial_iters;
+                best = c->launch;
+            }
+            s = restore();
+            if (s != LSKUM_OK) break;
+        }
+        if (s != LSKUM_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->launch = s == LSKUM_OK ? best : orig;
+    lskum_status s2 = build_graphs(c);
+    if (s == LSKUM_OK) s = restore();
+    if (s != LSKUM_OK) return s;
+    if (s2 != LSKUM_OK) return s2;
+    if (tpp) *tpp = c->launch.tpp;
+    if (sweep_lanes) *sweep_lanes = c->launch.sweep_lanes;
+    if (ms_per_iter) *ms_per_iter = best_ms;
+    return LSKUM_OK;
+}
+
 lskum_status lskum_get_order(lskum_ctx *c, int32_t *colour, int32_t *order, int32_t *n_colours)
 {
     if (!c) return LSKUM_ERR_ARG;
@@ -1064,6 +1430,7 @@ lskum_status lskum_get_order(lskum_ctx *c, int32_t *colour, int32_t *order, int3
 lskum_status lskum_get_info(lskum_ctx *c, int32_t *n_points, int32_t *n_colours, int32_t *launches_per_iter)
 {
     if (!c) return LSKUM_ERR_ARG;
+    if (c->pending) return fail(c, LSKUM_ERR_ARG, "an enqueued run has not been waited for");
     if (n_points) *n_points = c->n;
     if (n_colours) *n_colours = c->n_colours;
     if (launches_per_iter) *launches_per_iter = c->launches_per_iter;

@@ -20,18 +20,30 @@ constexpr int kOuter = 2;
 
 // Device-resident control block: lets many iterations be enqueued (CUDA
 // graph launches) without host synchronisation; every kernel of an
-// iteration returns at once when the run has stopped.
+// iteration returns at once when the run has stopped.  A context holds one
+// or several independent cases (a batch: the disjoint union of their
+// clouds); each case has its own residual history and stopping state.
+// kReachedTarget and kFailedNow finish their iteration (the sweeps and the
+// update run; kFailedNow's update is undone by k_repair) and become
+// kStopped / kFailed at the next k_begin.  Stopped and failed cases are
+// frozen: their points keep their state while the batch's other cases run.
+enum CaseState { kRunning = 0, kReachedTarget = 1, kStopped = 2, kFailedNow = 3, kFailed = 4 };
+
 struct Ctrl {
-    int32_t stop;        // 1: skip all further work
-    int32_t stop_after;  // the drop target was reached: finish this iteration, then stop
-                         // (the next iteration's first kernel sets stop)
+    int32_t stop;        // 1: every case stopped or a failure: skip all further work
     int32_t error;       // lskum_status of a device-detected failure (0 = none)
     int32_t bad_point;   // smallest internal index of a non-physical update
-    int32_t it;          // iterations whose residual norm has been recorded
-    int32_t hist_cap;    // capacity of hist
-    double hist0;        // first norm (drop reference); <= 0 = not set yet
+    int32_t it;          // iterations started since the last reset (k_begin counts)
+    int32_t hist_cap;    // capacity of each case's history
+    int32_t n_cases;
     double target;       // drop target of the current run (<= 0: none)
-    double *hist;        // residual-norm history (device)
+    int32_t *case_state; // [n_cases] CaseState; kReachedTarget finishes the
+                         // iteration, the next k_begin makes it kStopped
+    int32_t *case_it;    // [n_cases] norms recorded
+    double *case_hist0;  // [n_cases] first norm (drop reference); <= 0 = not set
+    double *hist;        // [n_cases][hist_cap] residual-norm histories
+    int32_t *case_err;   // [n_cases] lskum_status of a failed case of a batch (0 = none)
+    int32_t *case_bad;   // [n_cases] smallest internal index of its non-physical update
 };
 
 // Per-point geometry rows (fields of `geo`, stride ld).
@@ -100,9 +112,17 @@ struct Dev {
     // (forward: lower list, backward: upper list), so a warp's groups share a
     // trip count
     const int32_t *sw_fwd, *sw_bwd;
-    double *blk;             // residual-norm partial sums, one per residual block
-    int32_t n_blk;
+    // per-case residual norm: stage 1 sums R_rho^2 over blocks of up to 256
+    // points of one case (caller order), stage 2 adds each case's blocks
+    double *blk;             // [n_blk] partial sums
+    const int32_t *blk_pos;  // [n_blk + 1] caller-order start of each block
+    const int32_t *blk_case; // [n_blk] case of each block
+    const int32_t *case_blk; // [n_cases + 1] first block of each case
+    const int32_t *inv;      // [n] caller index -> internal index
+    const int32_t *case_of;  // [ld] internal index -> case
+    int32_t n_blk, n_cases;
     Ctrl *ctrl;
+    const int32_t *case_state;  // = ctrl->case_state (read per point)
     // options
     double cfl, ramp, u_inf[4];
     int32_t K, jvp;
@@ -113,8 +133,9 @@ struct Dev {
 // Kernel launch wrappers (lskum_kernels.cu).  `cur` is the state set read by
 // this iteration; the update writes set 1 - cur.
 struct Launch {
-    int tpp;        // threads per point of the gradient and residual kernels
-    int res_block;  // threads per block of the residual kernel
+    int tpp;          // threads per point of the gradient and residual kernels (1, 2, 4, 8)
+    int res_block;    // threads per block of the residual kernel
+    int sweep_lanes;  // lanes per point of the sweep kernels (2, 4, 8)
 };
 
 cudaError_t launch_iteration(const Dev &d, const Launch &L, int cur, int n_levels, const int32_t *lvl_beg,
@@ -126,6 +147,5 @@ cudaError_t launch_phase(const Dev &d, const Launch &L, int cur, int phase, int 
                          const int32_t *lvl_act_end, const int32_t *lvl_end, cudaStream_t s);
 cudaError_t launch_init_state(const Dev &d, int cur, cudaStream_t s);
 cudaError_t launch_reset_ctrl(Ctrl *c, cudaStream_t s);
-int residual_blocks(const Dev &d, const Launch &L);
 
 }  // namespace lskum

@@ -2,7 +2,7 @@
 //   k_grad      least-squares q-derivatives, first order + K inner iterations (Eq. 10, 16)
 //   k_residual  defect-corrected kinetic split-flux residual (Eq. 11-15), local time
 //               step and scalar LU-SGS diagonal (Eq. 26, 33-34), density-norm partials
-//   k_norm      residual norm, history and stopping test
+//   k_norm_*    per-case residual norms, histories and stopping tests
 //   k_sweep     one colour level of the forward or backward LU-SGS sweep (Eq. 27) with
 //               exact (forward-mode AD) or increment (Eq. 28) Jacobian-vector products
 //   k_update    U += dU, wall projection, q-variables and the per-point primal
@@ -33,13 +33,29 @@ constexpr double kInv2SqrtPi = 0.28209479177387814347;    // 1 / (2 sqrt(pi))
 constexpr double kInvSqrtPi = 0.56418958354775628695;     // 1 / sqrt(pi)
 constexpr unsigned kFull = 0xffffffffu;
 
-// Every kernel returns at once after a stop or a failure.  k_norm only sets
-// stop_after, so the sweeps and the update of the iteration that reached the
-// drop target still run; k_begin turns it into stop at the start of the next.
+// Every kernel returns at once after a stop or a failure.  When a case
+// reaches its drop target, k_norm marks it kReachedTarget, so the sweeps and
+// the update of that iteration still run; the next k_begin makes it
+// kStopped, after which its points are left alone (a batch keeps iterating
+// its other cases) and, once every case has stopped, sets stop.  In a batch
+// a failure (non-finite norm, non-physical update) fails only its own case,
+// which keeps its last good state; a single case fails the context.
 __device__ __forceinline__ bool halted(const Ctrl *c)
 {
     const volatile Ctrl *v = c;
     return (v->stop | v->error) != 0;
+}
+
+// Is point k's case stopped?  (Only batches have cases that stop while
+// others run; a single case stops the whole context.)
+__device__ __forceinline__ bool frozen_state(int32_t st)
+{
+    return st == kStopped || st == kFailed;
+}
+
+__device__ __forceinline__ bool frozen(const Dev &d, int k)
+{
+    return d.n_cases > 1 && frozen_state(((const volatile int32_t *)d.case_state)[d.case_of[k]]);
 }
 
 // Primitive state carried through the residual.
@@ -296,12 +312,11 @@ template <int TPP, bool COMP>
 __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const double *__restrict__ gx,
                                                   const double *__restrict__ gy)
 {
-    __shared__ double red[32];
     __shared__ MathTables T;
     if (halted(d.ctrl)) return;
     load_math_tables(T);
     __syncthreads();
-    const int n1 = ((const volatile Ctrl *)d.ctrl)->it + 1;
+    const int n1 = ((const volatile Ctrl *)d.ctrl)->it;  // this iteration, counted by k_begin
     const double cfl = (d.ramp > 0.0 && (double)n1 < d.ramp) ? d.cfl * ((double)n1 / d.ramp) : d.cfl;
     const double hc = n1 <= d.first_order ? 0.0 : 0.5;  // first-order start: q~ = q
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
@@ -310,7 +325,7 @@ __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const doub
     const int kk = active ? k : d.n - 1;
     const int ld = d.ld;
     const int fl = d.flag[kk];
-    const bool work = active && fl != kOuter;
+    const bool work = active && fl != kOuter && !frozen(d, kk);
     const bool wall = fl == kWall;
     const double *__restrict__ q = st.q;
     double R[4] = {0.0, 0.0, 0.0, 0.0};
@@ -382,11 +397,9 @@ __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const doub
         if (COMP) R[c] += Rc[c];
         R[c] = group_sum<TPP>(R[c]);
     }
-    double nrm = 0.0;
     if (work && sub == 0) {
 #pragma unroll
         for (int c = 0; c < 4; c++) d.R[c * ld + k] = R[c];
-        nrm = R[0] * R[0];
         // local time step (reading: CFL min_i|dr| / (|u| + a)) and the scalar
         // diagonal of Eq. 26 with the spectral radii of Eq. 34, kept at least
         // sum_s rho_s sum_i |w_i| so that it bounds the off-diagonal blocks
@@ -406,49 +419,72 @@ __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const doub
              + r3 * d.geo[G_ABS_3 * ld + k];
         d.D[k] = Dp > Ddom ? Dp : Ddom;
     }
-    // block partial of sum R_rho^2 (fixed order: warp butterfly, then warp 0)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(kFull, nrm, o);
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) red[wid] = nrm;
-    __syncthreads();
-    if (wid == 0) {
-        double t = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
-        if (lane == 0) d.blk[blockIdx.x] = t;
-    }
 }
 
 // ---------------------------------------------------------------------------
-// residual norm, history, stopping test (one block)
+// per-case residual norms, histories and stopping tests (two stages)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_norm(Dev d)
+// Stage 1: block j sums R_rho^2 over caller positions [blk_pos[j], blk_pos[j+1]),
+// all of one case (outer points hold R = 0).  Fixed order: warp butterfly,
+// then warp 0.
+__global__ void __launch_bounds__(256) k_norm_partials(Dev d)
 {
-    __shared__ double red[32];
+    __shared__ double red[8];
     if (halted(d.ctrl)) return;
+    const int j = blockIdx.x;
+    const int p = d.blk_pos[j] + threadIdx.x;
     double t = 0.0;
-    for (int b = threadIdx.x; b < d.n_blk; b += blockDim.x) t += d.blk[b];
+    if (p < d.blk_pos[j + 1]) {
+        const double r = d.R[d.inv[p]];
+        t = r * r;
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) red[wid] = t;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
     __syncthreads();
-    if (wid == 0) {
-        double s = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+    if (threadIdx.x < 32) {
+        double s = threadIdx.x < 8 ? red[threadIdx.x] : 0.0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
-        if (lane == 0) {
-            Ctrl *c = d.ctrl;
+        if (threadIdx.x == 0) d.blk[j] = s;
+    }
+}
+
+// Stage 2: one block per case adds the case's partials in a fixed order,
+// records the norm and applies the stopping test.
+__global__ void __launch_bounds__(256) k_norm_cases(Dev d)
+{
+    __shared__ double red[8];
+    if (halted(d.ctrl)) return;
+    const int b = blockIdx.x;
+    Ctrl *c = d.ctrl;
+    if (frozen_state(((volatile int32_t *)c->case_state)[b])) return;  // block-uniform
+    double t = 0.0;
+    for (int j = d.case_blk[b] + threadIdx.x; j < d.case_blk[b + 1]; j += blockDim.x) t += d.blk[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double s = threadIdx.x < 8 ? red[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+        if (threadIdx.x == 0) {
             const double nrm = sqrt(s);
-            const int n = c->it;
-            if (n < c->hist_cap) c->hist[n] = nrm;
-            if (!(c->hist0 > 0.0)) c->hist0 = nrm;
-            c->it = n + 1;
+            const int n = c->case_it[b];
+            if (n < c->hist_cap) c->hist[(size_t)b * c->hist_cap + n] = nrm;
+            if (!(c->case_hist0[b] > 0.0)) c->case_hist0[b] = nrm;
+            c->case_it[b] = n + 1;
             if (!isfinite(nrm)) {
-                c->error = -4;  // LSKUM_ERR_DIVERGED
-            } else if (c->target > 0.0 && nrm / c->hist0 <= c->target) {
-                c->stop_after = 1;
+                if (c->n_cases > 1) {  // this case only: frozen from its sweeps on
+                    c->case_state[b] = kFailed;
+                    c->case_err[b] = -4;  // LSKUM_ERR_DIVERGED
+                } else {
+                    atomicExch(&c->error, -4);
+                    atomicMin(&c->bad_point, -1 - b);
+                }
+            } else if (c->target > 0.0 && nrm / c->case_hist0[b] <= c->target) {
+                c->case_state[b] = kReachedTarget;
             }
         }
     }
@@ -497,6 +533,7 @@ __global__ void __launch_bounds__(256) k_sweep(Dev d, StateSet st, int lb, int l
     const int pos = lb + gt / G, sub = gt % G;
     const bool active = pos < le;
     const int k = (FWD ? d.sw_fwd : d.sw_bwd)[active ? pos : le - 1];
+    const bool live = active && !frozen(d, k);
     const SweepBufs<T> sb = sweep_bufs<T>(d, st);
     const int32_t *__restrict__ off = FWD ? d.lo_off : d.up_off;
     const int32_t *__restrict__ nbr = FWD ? d.lo_nbr : d.up_nbr;
@@ -515,7 +552,7 @@ __global__ void __launch_bounds__(256) k_sweep(Dev d, StateSet st, int lb, int l
         e2y = d.geo[G_E2Y * ld + k];
     }
     T acc[4] = {T(0), T(0), T(0), T(0)};
-    const int beg = off[k], end = active ? off[k + 1] : beg;
+    const int beg = off[k], end = live ? off[k + 1] : beg;
     for (int e = beg + sub; e < end; e += G) {
         const int i = nbr[e];
         const int mb = mbs[e];
@@ -582,7 +619,7 @@ __global__ void __launch_bounds__(256) k_sweep(Dev d, StateSet st, int lb, int l
     }
 #pragma unroll
     for (int c = 0; c < 4; c++) acc[c] = group_sum<G>(acc[c]);
-    if (active && sub == 0) {
+    if (live && sub == 0) {
         const T iD = T(1) / (T)d.D[k];
         T w[4];
         if (FWD) {
@@ -609,7 +646,15 @@ __global__ void __launch_bounds__(256) k_sweep(Dev d, StateSet st, int lb, int l
 // ---------------------------------------------------------------------------
 __global__ void k_begin(Ctrl *c)
 {
-    if (c->stop_after) c->stop = 1;
+    if (c->stop | c->error) return;
+    int running = 0;
+    for (int b = 0; b < c->n_cases; b++) {
+        if (c->case_state[b] == kReachedTarget) c->case_state[b] = kStopped;
+        if (c->case_state[b] == kFailedNow) c->case_state[b] = kFailed;
+        running += !frozen_state(c->case_state[b]);
+    }
+    if (running == 0) c->stop = 1;
+    else c->it += 1;
 }
 
 template <bool INC>
@@ -628,11 +673,14 @@ __global__ void __launch_bounds__(256) k_update(Dev d, int cur)
     double U[4];
 #pragma unroll
     for (int c = 0; c < 4; c++) U[c] = src.U[c * ld + k];
-    if (INC && fl != kOuter) {
+    const bool moves = INC && fl != kOuter && !frozen(d, k);
+    if (moves) {
 #pragma unroll
         for (int c = 0; c < 4; c++) U[c] += d.dUf ? (double)d.dUf[4 * k + c] : d.dU[4 * k + c];
     }
-    if (fl == kWall) {
+    // wall projection of a new state only: re-projecting a projected state
+    // could change its last bits, and a stopped case must keep its state
+    if (fl == kWall && (moves || !INC)) {
         const double nx = d.wnx[k], ny = d.wny[k];
         const double mn = U[1] * nx + U[2] * ny;
         U[1] -= mn * nx;
@@ -642,8 +690,15 @@ __global__ void __launch_bounds__(256) k_update(Dev d, int cur)
     const bool ok = P.rho > 0.0 && P.p > 0.0 && isfinite(P.rho) && isfinite(P.p) && isfinite(P.u) &&
                     isfinite(P.v);
     if (!ok) {
-        atomicMin(&d.ctrl->bad_point, k);
-        atomicExch(&d.ctrl->error, -3);  // LSKUM_ERR_NONPOSITIVE
+        if (INC && d.n_cases > 1) {  // fail this case only; k_repair restores its state
+            const int b = d.case_of[k];
+            atomicExch(&d.ctrl->case_state[b], (int32_t)kFailedNow);
+            atomicExch(&d.ctrl->case_err[b], -3);  // LSKUM_ERR_NONPOSITIVE
+            atomicMin(&d.ctrl->case_bad[b], k);
+        } else {
+            atomicMin(&d.ctrl->bad_point, k);
+            atomicExch(&d.ctrl->error, -3);
+        }
         return;
     }
 #pragma unroll
@@ -686,10 +741,31 @@ __global__ void __launch_bounds__(256) k_update(Dev d, int cur)
     }
 }
 
+// Batches: undo this iteration's update of the cases that failed in it (the
+// new state set gets the old set's values), so a failed case keeps its last
+// good state.
+__global__ void __launch_bounds__(256) k_repair(Dev d, int cur)
+{
+    if (halted(d.ctrl)) return;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= d.n) return;
+    if (((const volatile int32_t *)d.case_state)[d.case_of[k]] != kFailedNow) return;
+    const int ld = d.ld;
+    const StateSet src = d.set[cur], dst = d.set[1 - cur];
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        dst.U[c * ld + k] = src.U[c * ld + k];
+        dst.q[c * ld + k] = src.q[c * ld + k];
+    }
+    for (int f = 0; f < kPrimStride; f++) dst.prim[(size_t)k * kPrimStride + f] = src.prim[(size_t)k * kPrimStride + f];
+    if (src.primf)
+        for (int f = 0; f < kPrimStride; f++)
+            dst.primf[(size_t)k * kPrimStride + f] = src.primf[(size_t)k * kPrimStride + f];
+}
+
 __global__ void k_reset_ctrl(Ctrl *c)
 {
     c->stop = 0;
-    c->stop_after = 0;
     c->error = 0;
     c->bad_point = 0x7fffffff;
 }
@@ -746,29 +822,40 @@ cudaError_t enqueue_grad_res(const Dev &d, const Launch &L, int cur, cudaStream_
     return e;
 }
 
-constexpr int kSweepLanes = 4;  // lanes per point in k_sweep
-
-template <int JVP>
-void enqueue_sweeps(const Dev &d, int cur, int n_levels, const int32_t *lvl_beg, const int32_t *lvl_act_end,
-                    cudaStream_t s, int *launches, bool fwd, bool bwd)
+template <int JVP, int G>
+void enqueue_sweeps_g(const Dev &d, int cur, int n_levels, const int32_t *lvl_beg, const int32_t *lvl_act_end,
+                      cudaStream_t s, int *launches, bool fwd, bool bwd)
 {
     const StateSet st = d.set[cur];
     for (int l = 0; fwd && l < n_levels; l++) {
         const int np = lvl_act_end[l] - lvl_beg[l];
         if (np <= 0) continue;
-        const int blocks = (np * kSweepLanes + 255) / 256;
-        if (d.precision) k_sweep<JVP, true, kSweepLanes, float><<<blocks, 256, 0, s>>>(d, st, lvl_beg[l], lvl_act_end[l]);
-        else k_sweep<JVP, true, kSweepLanes, double><<<blocks, 256, 0, s>>>(d, st, lvl_beg[l], lvl_act_end[l]);
+        const int blocks = (np * G + 255) / 256;
+        if (d.precision) k_sweep<JVP, true, G, float><<<blocks, 256, 0, s>>>(d, st, lvl_beg[l], lvl_act_end[l]);
+        else k_sweep<JVP, true, G, double><<<blocks, 256, 0, s>>>(d, st, lvl_beg[l], lvl_act_end[l]);
         (*launches)++;
     }
     for (int l = n_levels - 1; bwd && l >= 0; l--) {
         const int np = lvl_act_end[l] - lvl_beg[l];
         if (np <= 0) continue;
-        const int blocks = (np * kSweepLanes + 255) / 256;
-        if (d.precision) k_sweep<JVP, false, kSweepLanes, float><<<blocks, 256, 0, s>>>(d, st, lvl_beg[l], lvl_act_end[l]);
-        else k_sweep<JVP, false, kSweepLanes, double><<<blocks, 256, 0, s>>>(d, st, lvl_beg[l], lvl_act_end[l]);
+        const int blocks = (np * G + 255) / 256;
+        if (d.precision) k_sweep<JVP, false, G, float><<<blocks, 256, 0, s>>>(d, st, lvl_beg[l], lvl_act_end[l]);
+        else k_sweep<JVP, false, G, double><<<blocks, 256, 0, s>>>(d, st, lvl_beg[l], lvl_act_end[l]);
         (*launches)++;
     }
+}
+
+template <int JVP>
+cudaError_t enqueue_sweeps(const Dev &d, const Launch &L, int cur, int n_levels, const int32_t *lvl_beg,
+                           const int32_t *lvl_act_end, cudaStream_t s, int *launches, bool fwd, bool bwd)
+{
+    switch (L.sweep_lanes) {
+    case 2: enqueue_sweeps_g<JVP, 2>(d, cur, n_levels, lvl_beg, lvl_act_end, s, launches, fwd, bwd); break;
+    case 4: enqueue_sweeps_g<JVP, 4>(d, cur, n_levels, lvl_beg, lvl_act_end, s, launches, fwd, bwd); break;
+    case 8: enqueue_sweeps_g<JVP, 8>(d, cur, n_levels, lvl_beg, lvl_act_end, s, launches, fwd, bwd); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t enqueue_phase(const Dev &d, const Launch &L, int cur, int ph, int n_levels, const int32_t *lvl_beg,
@@ -781,28 +868,27 @@ cudaError_t enqueue_phase(const Dev &d, const Launch &L, int cur, int ph, int n_
         return enqueue_grad_res(d, L, cur, s, launches, true, false);
     case 1: return enqueue_grad_res(d, L, cur, s, launches, false, true);
     case 2:
-        k_norm<<<1, 1024, 0, s>>>(d);
-        (*launches)++;
+        k_norm_partials<<<d.n_blk, 256, 0, s>>>(d);
+        k_norm_cases<<<d.n_cases, 256, 0, s>>>(d);
+        (*launches) += 2;
         return cudaGetLastError();
     case 3:
     case 4:
-        if (d.jvp == 0) enqueue_sweeps<0>(d, cur, n_levels, lvl_beg, lvl_act_end, s, launches, ph == 3, ph == 4);
-        else enqueue_sweeps<1>(d, cur, n_levels, lvl_beg, lvl_act_end, s, launches, ph == 3, ph == 4);
-        return cudaGetLastError();
+        if (d.jvp == 0) return enqueue_sweeps<0>(d, L, cur, n_levels, lvl_beg, lvl_act_end, s, launches, ph == 3, ph == 4);
+        return enqueue_sweeps<1>(d, L, cur, n_levels, lvl_beg, lvl_act_end, s, launches, ph == 3, ph == 4);
     case 5:
         k_update<true><<<(d.n + 255) / 256, 256, 0, s>>>(d, cur);
         (*launches)++;
+        if (d.n_cases > 1) {
+            k_repair<<<(d.n + 255) / 256, 256, 0, s>>>(d, cur);
+            (*launches)++;
+        }
         return cudaGetLastError();
     default: return cudaErrorInvalidValue;
     }
 }
 
 }  // namespace
-
-int residual_blocks(const Dev &d, const Launch &L)
-{
-    return (d.n * L.tpp + L.res_block - 1) / L.res_block;
-}
 
 cudaError_t launch_iteration(const Dev &d, const Launch &L, int cur, int n_levels, const int32_t *lvl_beg,
                              const int32_t *lvl_act_end, const int32_t *lvl_end, cudaStream_t s, int *launches)

@@ -15,6 +15,7 @@ from .build import LIB
 INTERIOR, WALL, OUTER = 0, 1, 2
 JVP_EXACT, JVP_INCREMENT = 0, 1
 FIELD_U, FIELD_Q, FIELD_QX, FIELD_QY, FIELD_R, FIELD_D, FIELD_DUS, FIELD_DU = range(8)
+OK, ERR_ARG, ERR_STENCIL, ERR_NONPOSITIVE, ERR_DIVERGED, ERR_CUDA, ERR_TIMEOUT, ERR_OOM = 0, -1, -2, -3, -4, -5, -6, -7
 STATUS = {0: "LSKUM_OK", -1: "LSKUM_ERR_ARG", -2: "LSKUM_ERR_STENCIL", -3: "LSKUM_ERR_NONPOSITIVE",
           -4: "LSKUM_ERR_DIVERGED", -5: "LSKUM_ERR_CUDA", -6: "LSKUM_ERR_TIMEOUT", -7: "LSKUM_ERR_OOM"}
 
@@ -64,14 +65,20 @@ def load():
     L.lskum_get_order.argtypes = [vp, vp, vp, P(i32)]
     L.lskum_get_info.argtypes = [vp, P(i32), P(i32), P(i32)]
     L.lskum_time_phases.argtypes = [vp, i32, vp]
+    L.lskum_autotune.argtypes = [vp, i32, P(i32), P(i32), P(d)]
     L.lskum_density_norm_noalloc.argtypes = [vp, i32, vp, vp]
+    L.lskum_batch_create.argtypes = [P(lskum_cloud), P(lskum_opts), i32, vp, P(vp)]
+    L.lskum_get_case_residuals.argtypes = [vp, i32, vp, i32, P(i32)]
+    L.lskum_get_case_forces.argtypes = [vp, i32, P(d), P(d)]
+    L.lskum_get_case_info.argtypes = [vp, i32, P(i32), P(i32), P(i32), P(i32), P(i32), P(i32)]
     L.lskum_last_error.argtypes = [vp]
     L.lskum_last_error.restype = C.c_char_p
     L.lskum_destroy.argtypes = [vp]
     L.lskum_destroy.restype = None
     for f in ("lskum_create", "lskum_set_state", "lskum_set_conserved", "lskum_run", "lskum_enqueue", "lskum_wait",
               "lskum_get_state", "lskum_get_field", "lskum_get_residuals", "lskum_get_forces", "lskum_get_order",
-              "lskum_get_info", "lskum_time_phases", "lskum_density_norm_noalloc"):
+              "lskum_get_info", "lskum_time_phases", "lskum_density_norm_noalloc", "lskum_batch_create",
+              "lskum_get_case_residuals", "lskum_get_case_forces", "lskum_get_case_info", "lskum_autotune"):
         getattr(L, f).restype = st
     _lib = L
     return L
@@ -81,26 +88,67 @@ def _p(a):
     return a.ctypes.data_as(C.c_void_p)
 
 
+def _cloud_struct(cloud, keep):
+    arrs = [np.ascontiguousarray(cloud.x, np.float64), np.ascontiguousarray(cloud.y, np.float64),
+            np.ascontiguousarray(cloud.flag, np.uint8), np.ascontiguousarray(cloud.nx, np.float64),
+            np.ascontiguousarray(cloud.ny, np.float64), np.ascontiguousarray(cloud.nbr_off, np.int32),
+            np.ascontiguousarray(cloud.nbr_idx, np.int32)]
+    keep.extend(arrs)
+    return lskum_cloud(int(cloud.n), *[a.ctypes.data for a in arrs])
+
+
 class Solver:
-    """One context of liblskum for one cloud and one flow condition."""
+    """One context of liblskum for one cloud and one flow condition.
+
+    ``Solver.batch(clouds, conditions, ...)`` builds one context that solves
+    several (cloud, (mach, aoa_deg)) cases together."""
 
     def __init__(self, cloud, mach, aoa_deg, cfl=100.0, inner_iters=3, jvp=JVP_EXACT, cfl_ramp_iters=0.0,
-                 first_order_iters=0, precision=0, stream=None):
+                 first_order_iters=0, precision=0, stream=None, _cases=None):
         L = load()
-        self.n = int(cloud.n)
-        self._arrays = [np.ascontiguousarray(cloud.x, np.float64), np.ascontiguousarray(cloud.y, np.float64),
-                        np.ascontiguousarray(cloud.flag, np.uint8), np.ascontiguousarray(cloud.nx, np.float64),
-                        np.ascontiguousarray(cloud.ny, np.float64), np.ascontiguousarray(cloud.nbr_off, np.int32),
-                        np.ascontiguousarray(cloud.nbr_idx, np.int32)]
-        cl = lskum_cloud(self.n, *[a.ctypes.data for a in self._arrays])
-        op = lskum_opts(mach, aoa_deg, cfl, cfl_ramp_iters, inner_iters, jvp, precision, first_order_iters)
+        keep = []
+        clouds = _cases[0] if _cases else [cloud]
+        conds = _cases[1] if _cases else [(mach, aoa_deg)]
+        if len(clouds) != len(conds) or not clouds:
+            raise ValueError("one (mach, aoa_deg) per cloud")
+        cl = (lskum_cloud * len(clouds))(*[_cloud_struct(c, keep) for c in clouds])
+        op = (lskum_opts * len(clouds))(*[lskum_opts(m, a, cfl, cfl_ramp_iters, inner_iters, jvp, precision,
+                                                     first_order_iters) for m, a in conds])
         h = C.c_void_p()
-        s = L.lskum_create(C.byref(cl), C.byref(op), C.c_void_p(stream), C.byref(h))
-        self._arrays = None
+        if _cases:
+            s = L.lskum_batch_create(cl, op, len(clouds), C.c_void_p(stream), C.byref(h))
+        else:
+            s = L.lskum_create(cl, op, C.c_void_p(stream), C.byref(h))
         if s != 0:
             raise LskumError(s, L.lskum_last_error(None).decode())
         self._h = h
-        self.mach, self.aoa_deg = mach, aoa_deg
+        self.n = int(sum(c.n for c in clouds))
+        self.n_cases = len(clouds)
+        self.conditions = list(conds)
+        self.mach, self.aoa_deg = conds[0]
+
+    @classmethod
+    def batch(cls, clouds, conditions, **kw):
+        return cls(None, None, None, _cases=(list(clouds), list(conditions)), **kw)
+
+    def case_residuals(self, cs):
+        n = C.c_int32(0)
+        self._check(load().lskum_get_case_residuals(self._h, int(cs), None, 0, C.byref(n)))
+        h = np.empty(max(n.value, 1))
+        self._check(load().lskum_get_case_residuals(self._h, int(cs), _p(h), n.value, C.byref(n)))
+        return h[:n.value]
+
+    def case_forces(self, cs):
+        cl, cd = C.c_double(), C.c_double()
+        self._check(load().lskum_get_case_forces(self._h, int(cs), C.byref(cl), C.byref(cd)))
+        return cl.value, cd.value
+
+    def case_info(self, cs):
+        a, b, c, d, e, f = (C.c_int32() for _ in range(6))
+        self._check(load().lskum_get_case_info(self._h, int(cs), C.byref(a), C.byref(b), C.byref(c), C.byref(d),
+                                               C.byref(e), C.byref(f)))
+        return dict(first_point=a.value, n_points=b.value, iters=c.value, stopped=bool(d.value), status=e.value,
+                    bad_point=f.value)
 
     def _check(self, s):
         if s != 0:
@@ -188,6 +236,14 @@ class Solver:
         ms = np.zeros(6)
         self._check(load().lskum_time_phases(self._h, int(reps), _p(ms)))
         return dict(zip(self.PHASES, ms.tolist()))
+
+    def autotune(self, trial_iters=5):
+        """Pick the fastest launch shape by timing real iterations; the state
+        and histories are restored.  Returns (threads per point, sweep lanes
+        per point, ms per iteration)."""
+        a, b, t = C.c_int32(), C.c_int32(), C.c_double()
+        self._check(load().lskum_autotune(self._h, int(trial_iters), C.byref(a), C.byref(b), C.byref(t)))
+        return a.value, b.value, t.value
 
     def info(self):
         a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
