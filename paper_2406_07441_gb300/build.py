@@ -18,7 +18,7 @@ LIB = os.path.join(OUT_DIR, "liblskum.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["lskum_kernels.cu", "lskum_host.cpp", "lskum_noalloc.cu"]
+SOURCES = ["lskum_kernels.cu", "lskum_host.cpp", "lskum_noalloc.cu", "lskum_mlp.cu"]
 
 
 def _nvcc():

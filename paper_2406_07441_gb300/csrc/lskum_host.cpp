@@ -3,6 +3,7 @@
 // per-slot least-squares weights, device memory, one CUDA graph per
 // iteration parity, and the C-ABI of include/lskum.h.
 #include "lskum_internal.h"
+#include "lskum_mlp_internal.h"
 
 #include <algorithm>
 #include <climits>
@@ -17,6 +18,7 @@
 #include <vector>
 
 #include "../../include/lskum.h"
+#include "../../include/lskum_mlp.h"
 
 using namespace lskum;
 
@@ -81,6 +83,8 @@ struct lskum_ctx {
     int32_t *case_state = nullptr, *case_it = nullptr;  // device, per case
     int32_t *case_err = nullptr, *case_bad = nullptr;
     double *case_hist0 = nullptr;
+    // geometry the warm-start network reads (built on first use; internal order)
+    float *mx = nullptr, *my = nullptr, *mdw = nullptr, *mcase_mach = nullptr, *mcase_aoa = nullptr;
     int cur = 0;                        // state set holding the current state
     int32_t it_base = 0;                // ctrl->it at the start of the pending enqueue
     int cur_base = 0;
@@ -938,6 +942,8 @@ lskum_status ensure_hist(lskum_ctx *c, int32_t need)
     return LSKUM_OK;
 }
 
+lskum_status finish_state(lskum_ctx *c, bool reset_hist);
+
 lskum_status state_from_conserved(lskum_ctx *c, const std::vector<double> &Ucaller, bool reset_hist)
 {
     const int32_t n = c->n, ld = c->ld;
@@ -956,8 +962,17 @@ lskum_status state_from_conserved(lskum_ctx *c, const std::vector<double> &Ucall
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->dev.set[tgt].U, Ui, 4 * (size_t)ld * sizeof(double), cudaMemcpyHostToDevice,
                             c->stream);
-    if (e == cudaSuccess) e = launch_reset_ctrl(c->ctrl, c->stream);
-    if (e == cudaSuccess) e = launch_init_state(c->dev, tgt, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "setting the state");
+    return finish_state(c, reset_hist);
+}
+
+// The conserved state of the current set was written on the device: derive
+// q and the per-point quantities (with the wall projection), check it, and
+// reset the counters (all of them with reset_hist).
+lskum_status finish_state(lskum_ctx *c, bool reset_hist)
+{
+    cudaError_t e = launch_reset_ctrl(c->ctrl, c->stream);
+    if (e == cudaSuccess) e = launch_init_state(c->dev, c->cur, c->stream);
     Ctrl h{};
     if (e != cudaSuccess) return cuda_fail(c, e, "setting the state");
     lskum_status s = read_ctrl(c, &h);
@@ -1435,6 +1450,169 @@ lskum_status lskum_get_info(lskum_ctx *c, int32_t *n_points, int32_t *n_colours,
     if (n_colours) *n_colours = c->n_colours;
     if (launches_per_iter) *launches_per_iter = c->launches_per_iter;
     return LSKUM_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// what the warm-start network needs from a context (lskum_mlp_internal.h)
+// ---------------------------------------------------------------------------
+namespace lskum {
+
+CtxHost ctx_host(lskum_ctx *c)
+{
+    return CtxHost{c->n, c->n_cases, c->perm.data(), c->inv.data(), c->flag.data(), c->case_of_caller.data()};
+}
+
+lskum_status ctx_fail(lskum_ctx *c, lskum_status s, const char *msg)
+{
+    return fail(c, s, "%s", msg);
+}
+
+lskum_status ctx_case_status(lskum_ctx *c, std::vector<int32_t> &status)
+{
+    status.assign(c->n_cases, 0);
+    cudaError_t e = cudaMemcpyAsync(status.data(), c->case_err, c->n_cases * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                    c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return e == cudaSuccess ? LSKUM_OK : cuda_fail(c, e, "reading the case status");
+}
+
+lskum_status ctx_mlp_view(lskum_ctx *c, MlpView *v)
+{
+    if (c->pending) return fail(c, LSKUM_ERR_ARG, "an enqueued run has not been waited for");
+    const int32_t n = c->n, ld = c->ld;
+    if (!c->mx) {
+        std::vector<float> hx(ld, 0.f), hy(ld, 0.f), cm(c->n_cases), ca(c->n_cases);
+        for (int32_t k = 0; k < n; k++) {
+            hx[k] = (float)c->x[c->perm[k]];
+            hy[k] = (float)c->y[c->perm[k]];
+        }
+        for (int32_t b = 0; b < c->n_cases; b++) {
+            cm[b] = (float)c->case_mach[b];
+            ca[b] = (float)c->case_aoa[b];
+        }
+        // per case: its wall polygon (wall points in caller order, closed)
+        std::vector<float4> seg;
+        std::vector<int32_t> seg_off(c->n_cases + 1, 0);
+        for (int32_t b = 0; b < c->n_cases; b++) {
+            std::vector<int32_t> w;
+            for (int32_t p = c->case_off[b]; p < c->case_off[b + 1]; p++)
+                if (c->flag[p] == LSKUM_WALL) w.push_back(p);
+            for (size_t i = 0; i < w.size(); i++) {
+                const int32_t a = w[i], q = w[(i + 1) % w.size()];
+                seg.push_back(make_float4((float)c->x[a], (float)c->y[a], (float)c->x[q], (float)c->y[q]));
+            }
+            seg_off[b + 1] = (int32_t)seg.size();
+        }
+        Arena &A = c->arena;
+        float *dx = A.alloc<float>(ld), *dy = A.alloc<float>(ld), *dw = A.alloc<float>(ld);
+        float *dm = A.alloc<float>(c->n_cases), *da = A.alloc<float>(c->n_cases);
+        float4 *dseg = A.alloc<float4>(seg.size());
+        int32_t *doff = A.alloc<int32_t>(seg_off.size());
+        if (A.err != cudaSuccess) return cuda_fail(c, A.err, "cudaMalloc(network geometry)");
+        cudaError_t e = cudaMemcpyAsync(dx, hx.data(), ld * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dy, hy.data(), ld * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dm, cm.data(), c->n_cases * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(da, ca.data(), c->n_cases * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess && !seg.empty())
+            e = cudaMemcpyAsync(dseg, seg.data(), seg.size() * sizeof(float4), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(doff, seg_off.data(), seg_off.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(dw, 0, ld * sizeof(float), c->stream);
+        if (e == cudaSuccess) e = launch_wall_distance(dx, dy, c->dev.case_of, n, dseg, doff, dw, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // the host vectors go out of scope
+        if (e != cudaSuccess) return cuda_fail(c, e, "network geometry");
+        c->mx = dx;
+        c->my = dy;
+        c->mdw = dw;
+        c->mcase_mach = dm;
+        c->mcase_aoa = da;
+    }
+    v->n = n;
+    v->ld = ld;
+    v->n_cases = c->n_cases;
+    v->x = c->mx;
+    v->y = c->my;
+    v->dwall = c->mdw;
+    v->flag = c->dev.flag;
+    v->case_of = c->dev.case_of;
+    v->case_mach = c->mcase_mach;
+    v->case_aoa = c->mcase_aoa;
+    v->U = c->dev.set[c->cur].U;
+    v->stream = c->stream;
+    return LSKUM_OK;
+}
+
+lskum_status ctx_state_written(lskum_ctx *c)
+{
+    return finish_state(c, true);
+}
+
+// First residual norm of every case at the current state: one iteration's
+// q-derivatives, residual and norm (no sweeps, no update), then the counters
+// are cleared.  A norm that is not finite comes back as infinity.
+lskum_status ctx_case_norms(lskum_ctx *c, std::vector<double> &norms)
+{
+    Ctrl h{};
+    lskum_status s = read_ctrl(c, &h);
+    if (s == LSKUM_OK) s = reset_cases(c, true, true);
+    if (s != LSKUM_OK) return s;
+    h.it = 0;
+    h.stop = h.error = 0;
+    h.target = 0.0;
+    h.bad_point = 0x7fffffff;
+    s = write_ctrl(c, h);
+    if (s != LSKUM_OK) return s;
+    cudaError_t e = cudaSuccess;
+    for (int ph = 0; ph < 3 && e == cudaSuccess; ph++)
+        e = launch_phase(c->dev, c->launch, c->cur, ph, c->n_colours, c->lvl_beg.data(), c->lvl_act_end.data(),
+                         c->lvl_end.data(), c->stream);
+    norms.assign(c->n_cases, 0.0);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(norms.data(), sizeof(double), c->hist, c->hist_cap * sizeof(double), sizeof(double),
+                              c->n_cases, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "residual norms");
+    for (auto &x : norms)
+        if (!std::isfinite(x)) x = INFINITY;
+    s = read_ctrl(c, &h);
+    if (s == LSKUM_OK) s = reset_cases(c, true, true);
+    if (s != LSKUM_OK) return s;
+    h.it = 0;
+    h.stop = h.error = 0;
+    h.bad_point = 0x7fffffff;
+    return write_ctrl(c, h);
+}
+
+}  // namespace lskum
+
+extern "C" {
+
+lskum_status lskum_get_wall_distance(lskum_ctx *c, double *d)
+{
+    if (!c || !d) return c ? fail(c, LSKUM_ERR_ARG, "NULL argument") : LSKUM_ERR_ARG;
+    MlpView v{};
+    lskum_status s = ctx_mlp_view(c, &v);
+    if (s != LSKUM_OK) return s;
+    std::vector<float> dw(c->ld);
+    cudaError_t e = cudaMemcpyAsync(dw.data(), v.dwall, c->ld * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "reading the wall distance");
+    for (int32_t p = 0; p < c->n; p++) d[p] = dw[c->inv[p]];
+    return LSKUM_OK;
+}
+
+lskum_status lskum_set_start_iters(lskum_ctx *c, int32_t first_order_iters)
+{
+    if (!c || first_order_iters < 0) return c ? fail(c, LSKUM_ERR_ARG, "bad argument") : LSKUM_ERR_ARG;
+    if (c->pending) return fail(c, LSKUM_ERR_ARG, "an enqueued run has not been waited for");
+    c->opts.first_order_iters = first_order_iters;
+    c->dev.first_order = first_order_iters;
+    return build_graphs(c);
 }
 
 }  // extern "C"

@@ -71,6 +71,26 @@ def load():
     L.lskum_get_case_residuals.argtypes = [vp, i32, vp, i32, P(i32)]
     L.lskum_get_case_forces.argtypes = [vp, i32, P(d), P(d)]
     L.lskum_get_case_info.argtypes = [vp, i32, P(i32), P(i32), P(i32), P(i32), P(i32), P(i32)]
+    L.lskum_get_wall_distance.argtypes = [vp, vp]
+    L.lskum_set_start_iters.argtypes = [vp, i32]
+    u64 = C.c_uint64
+    L.lskum_mlp_n_params.argtypes = []
+    L.lskum_mlp_n_params.restype = i32
+    L.lskum_mlp_create.argtypes = [u64, i32, vp, P(vp)]
+    L.lskum_mlp_get_params.argtypes = [vp, vp, vp]
+    L.lskum_mlp_set_params.argtypes = [vp, vp, vp]
+    L.lskum_mlp_features.argtypes = [vp, vp, i32, vp]
+    L.lskum_mlp_forward.argtypes = [vp, vp, i32, vp]
+    L.lskum_mlp_loss_grads.argtypes = [vp, vp, vp, i32, P(C.c_float), vp]
+    L.lskum_mlp_adam.argtypes = [vp, vp, C.c_float]
+    L.lskum_mlp_add_samples.argtypes = [vp, vp, i32, u64]
+    L.lskum_mlp_n_samples.argtypes = [vp, P(i32)]
+    L.lskum_mlp_train.argtypes = [vp, i32, i32, C.c_float, u64, vp]
+    L.lskum_mlp_predict.argtypes = [vp, vp, vp]
+    L.lskum_mlp_last_error.argtypes = [vp]
+    L.lskum_mlp_last_error.restype = C.c_char_p
+    L.lskum_mlp_destroy.argtypes = [vp]
+    L.lskum_mlp_destroy.restype = None
     L.lskum_last_error.argtypes = [vp]
     L.lskum_last_error.restype = C.c_char_p
     L.lskum_destroy.argtypes = [vp]
@@ -78,7 +98,11 @@ def load():
     for f in ("lskum_create", "lskum_set_state", "lskum_set_conserved", "lskum_run", "lskum_enqueue", "lskum_wait",
               "lskum_get_state", "lskum_get_field", "lskum_get_residuals", "lskum_get_forces", "lskum_get_order",
               "lskum_get_info", "lskum_time_phases", "lskum_density_norm_noalloc", "lskum_batch_create",
-              "lskum_get_case_residuals", "lskum_get_case_forces", "lskum_get_case_info", "lskum_autotune"):
+              "lskum_get_case_residuals", "lskum_get_case_forces", "lskum_get_case_info", "lskum_autotune",
+              "lskum_get_wall_distance", "lskum_set_start_iters", "lskum_mlp_create", "lskum_mlp_get_params",
+              "lskum_mlp_set_params", "lskum_mlp_features", "lskum_mlp_forward", "lskum_mlp_loss_grads",
+              "lskum_mlp_adam", "lskum_mlp_add_samples", "lskum_mlp_n_samples", "lskum_mlp_train",
+              "lskum_mlp_predict"):
         getattr(L, f).restype = st
     _lib = L
     return L
@@ -245,7 +269,113 @@ class Solver:
         self._check(load().lskum_autotune(self._h, int(trial_iters), C.byref(a), C.byref(b), C.byref(t)))
         return a.value, b.value, t.value
 
+    def wall_distance(self):
+        """Distance of every point to its case's wall polygon (as the warm-start network sees it)."""
+        d = np.empty(self.n)
+        self._check(load().lskum_get_wall_distance(self._h, _p(d)))
+        return d
+
+    def set_start_iters(self, first_order_iters):
+        self._check(load().lskum_set_start_iters(self._h, int(first_order_iters)))
+
     def info(self):
         a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
         self._check(load().lskum_get_info(self._h, C.byref(a), C.byref(b), C.byref(c)))
         return dict(n_points=a.value, n_colours=b.value, launches_per_iter=c.value)
+
+
+class Mlp:
+    """The warm-start network (include/lskum_mlp.h): BF16 tensor-core
+    training and inference kernels with FP32 accumulation."""
+
+    def __init__(self, seed=0, max_batch=65536, stream=None):
+        L = load()
+        h = C.c_void_p()
+        s = L.lskum_mlp_create(C.c_uint64(seed), int(max_batch), C.c_void_p(stream), C.byref(h))
+        if s != 0:
+            raise LskumError(s, L.lskum_mlp_last_error(None).decode())
+        self._h = h
+        self.n_params = int(L.lskum_mlp_n_params())
+
+    def _check(self, s):
+        if s != 0:
+            raise LskumError(s, load().lskum_mlp_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().lskum_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        p = np.empty(self.n_params, np.float32)
+        B = np.empty(48, np.float32)
+        self._check(load().lskum_mlp_get_params(self._h, _p(p), _p(B)))
+        return p, B.reshape(16, 3)
+
+    def set_params(self, params, fourier=None):
+        p = np.ascontiguousarray(params, np.float32)
+        B = None if fourier is None else np.ascontiguousarray(fourier, np.float32).reshape(48)
+        self._check(load().lskum_mlp_set_params(self._h, _p(p), None if B is None else _p(B)))
+
+    def features(self, in5):
+        a = np.ascontiguousarray(in5, np.float32).reshape(-1, 5)
+        X = np.empty((a.shape[0], 34), np.float32)
+        self._check(load().lskum_mlp_features(self._h, _p(a), a.shape[0], _p(X)))
+        return X
+
+    def forward(self, X):
+        X = np.ascontiguousarray(X, np.float32).reshape(-1, 34)
+        out = np.empty((X.shape[0], 4), np.float32)
+        self._check(load().lskum_mlp_forward(self._h, _p(X), X.shape[0], _p(out)))
+        return out
+
+    def loss_grads(self, X, T):
+        X = np.ascontiguousarray(X, np.float32).reshape(-1, 34)
+        T = np.ascontiguousarray(T, np.float32).reshape(-1, 4)
+        g = np.empty(self.n_params, np.float32)
+        loss = C.c_float()
+        self._check(load().lskum_mlp_loss_grads(self._h, _p(X), _p(T), X.shape[0], C.byref(loss), _p(g)))
+        return loss.value, g
+
+    def adam(self, grads, lr):
+        g = np.ascontiguousarray(grads, np.float32)
+        self._check(load().lskum_mlp_adam(self._h, _p(g), C.c_float(lr)))
+
+    def add_samples(self, solver, per_case, seed=0):
+        self._check(load().lskum_mlp_add_samples(self._h, solver._h, int(per_case), C.c_uint64(seed)))
+
+    def n_samples(self):
+        n = C.c_int32()
+        self._check(load().lskum_mlp_n_samples(self._h, C.byref(n)))
+        return n.value
+
+    def train(self, epochs, batch, lr, seed=0):
+        losses = np.zeros(max(int(epochs), 1), np.float32)
+        self._check(load().lskum_mlp_train(self._h, int(epochs), int(batch), C.c_float(lr), C.c_uint64(seed),
+                                           _p(losses)))
+        return losses[:int(epochs)]
+
+    def predict(self, solver):
+        """Warm-start the solver's state; returns per case whether the prediction was kept."""
+        warm = np.zeros(solver.n_cases, np.int32)
+        self._check(load().lskum_mlp_predict(self._h, solver._h, _p(warm)))
+        return warm.astype(bool)
+
+
+def unflatten_params(p):
+    """Parameter vector -> [(W_l [out, in], b_l [out])] of the 34-128-128-128-128-4 network."""
+    dims = [(34, 128), (128, 128), (128, 128), (128, 128), (128, 4)]
+    out, o = [], 0
+    for fin, fout in dims:
+        W = np.asarray(p[o:o + fin * fout]).reshape(fout, fin)
+        o += fin * fout
+        b = np.asarray(p[o:o + fout])
+        o += fout
+        out.append((W, b))
+    return out

@@ -1,0 +1,146 @@
+"""The warm-start network's tensor-core kernels against the FP64 oracle
+(oracle/mlp.py with BF16 rounding at the kernels' rounding points).
+
+Both sides round the same FP32 inputs, weights, activations and gradients to
+BF16; they differ in the accumulation (FP32 in tensor memory vs FP64), in
+GELU (CUDA's erff/expf vs FP64) and in the FP32 sin/cos of the features.
+An activation whose FP32 and FP64 pre-activations straddle a BF16 rounding
+boundary flips by one BF16 unit (2^-8 relative, ~1e-2 for activations of
+size 3); such flips are rare (a few per thousand outputs here) and the
+layers after it can amplify the change a few times.  Everything else is
+FP32 accumulation (~1e-7 relative).  Bars: outputs with median error
+<= 1e-6, 99th percentile <= 1e-3 and maximum <= 2e-2 (measured: 1e-8,
+-, 5.7e-3); gradients normwise <= 2e-3 per layer (measured <= 1.3e-4);
+features equal except for occasional one-unit flips (measured: 32 of
+102,000 entries, each one unit)."""
+import numpy as np
+import pytest
+
+from oracle import mlp as OM
+from paper_2406_07441_gb300 import cloudgen as cg
+from tests.conftest import cached_cloud
+
+pytestmark = pytest.mark.gpu
+
+
+def _random_params(rng, scale=1.0):
+    p = []
+    for fin, fout in OM.LAYERS:
+        k = 1.0 / np.sqrt(fin)
+        p.append(rng.uniform(-k, k, fout * fin) * scale)
+        p.append(rng.uniform(-k, k, fout))
+    return np.concatenate(p).astype(np.float32)
+
+
+def _net(seed=0):
+    from paper_2406_07441_gb300 import lskum as lk
+    return lk.Mlp(seed=seed, max_batch=4096)
+
+
+def test_features_match_the_oracle():
+    from paper_2406_07441_gb300 import lskum as lk
+    m = _net(1)
+    rng = np.random.default_rng(11)
+    n = 3000
+    in5 = np.stack([rng.uniform(-19, 20, n), rng.uniform(-20, 20, n), rng.uniform(0, 20, n),
+                    rng.uniform(0.3, 0.85, n), rng.uniform(-4, 6, n)], axis=1).astype(np.float32)
+    in5[:300, :2] = rng.uniform(-0.1, 1.1, (300, 2))  # near the aerofoil
+    _, B = m.get_params()
+    X = m.features(in5)
+    Xo = OM.features(in5[:, 0].astype(float), in5[:, 1].astype(float), in5[:, 2].astype(float),
+                     in5[:, 3].astype(float), in5[:, 4].astype(float), B.astype(float), bf16_round=True)[:, :34]
+    diff = np.abs(X - Xo)
+    ulp = np.maximum(np.abs(Xo), 2.0 ** -126) * 2.0 ** -7
+    print("features: max diff", diff.max(), "entries differing", np.count_nonzero(diff), "of", diff.size)
+    assert np.all(diff <= ulp * 1.01 + 1e-6)
+    assert np.count_nonzero(diff) <= 0.01 * diff.size
+
+
+@pytest.mark.parametrize("n", [1, 127, 128, 300, 4096, 5000])
+def test_forward_matches_the_oracle(n):
+    m = _net(2)
+    rng = np.random.default_rng(12 + n)
+    p = _random_params(rng, 2.0)
+    m.set_params(p)
+    X = rng.normal(0, 1, (n, 34)).astype(np.float32)
+    out = m.forward(X)
+    from paper_2406_07441_gb300.lskum import unflatten_params
+    o_ref, _, _ = OM.forward(unflatten_params(p.astype(np.float64)), X.astype(np.float64), bf16_round=True)
+    err = np.abs(out - o_ref)
+    print(f"forward n={n}: max |err| {err.max():.3e} median {np.median(err):.3e} max|o| {np.abs(o_ref).max():.3f}")
+    assert err.max() <= 2e-2 and np.percentile(err, 99) <= 1e-3 and np.median(err) <= 1e-6
+
+
+def test_loss_and_gradients_match_the_oracle():
+    from paper_2406_07441_gb300.lskum import unflatten_params
+    m = _net(3)
+    rng = np.random.default_rng(13)
+    p = _random_params(rng, 2.0)
+    m.set_params(p)
+    n = 1500
+    X = rng.normal(0, 1, (n, 34)).astype(np.float32)
+    T = rng.normal(0, 0.3, (n, 4)).astype(np.float32)
+    loss, g = m.loss_grads(X, T)
+    lo, go = OM.loss_and_grads(unflatten_params(p.astype(np.float64)), X.astype(np.float64), T.astype(np.float64),
+                               bf16_round=True)
+    print("loss", loss, lo)
+    assert abs(loss - lo) <= 1e-3 * lo
+    gg = unflatten_params(g.astype(np.float64))
+    for l, ((gW, gb), (oW, ob)) in enumerate(zip(gg, go)):
+        eW = np.max(np.abs(gW - oW)) / np.max(np.abs(oW))
+        eb = np.max(np.abs(gb - ob)) / np.max(np.abs(ob))
+        print(f"layer {l}: dW normwise {eW:.3e}  db normwise {eb:.3e}")
+        assert eW <= 2e-3 and eb <= 2e-3
+
+
+def test_adam_step_matches_the_oracle():
+    from paper_2406_07441_gb300.lskum import unflatten_params
+    m = _net(4)
+    rng = np.random.default_rng(14)
+    p = _random_params(rng)
+    m.set_params(p)
+    P = unflatten_params(p.astype(np.float64))
+    state = {}
+    for step in range(3):
+        g = (rng.normal(0, 1e-2, p.shape[0]) * (1 + step)).astype(np.float32)
+        m.adam(g, 1e-3)
+        P = OM.adam_step(P, unflatten_params(g.astype(np.float64)), state, 1e-3)
+    got, _ = m.get_params()
+    ref = np.concatenate([np.concatenate([W.ravel(), b]) for W, b in P])
+    print("adam max diff", np.max(np.abs(got - ref)))
+    assert np.max(np.abs(got - ref)) <= 2e-6
+
+
+def test_wall_distance_matches_the_oracle():
+    from paper_2406_07441_gb300 import lskum as lk
+    c = cached_cloud("jit64x32", lambda: cg.naca0012_jittered(64, 32, seed=12))
+    s = lk.Solver(c, 0.6, 1.0)
+    d = s.wall_distance()
+    ref = OM.wall_distance(c.x, c.y, c.flag)
+    assert np.all(d[c.flag == 1] <= 1e-6)
+    assert np.all(np.abs(d - ref) <= 1e-5 * ref + 2e-6)
+
+
+def _solver_batch(conds, K=2):
+    from paper_2406_07441_gb300 import lskum as lk
+    c = cached_cloud("ogrid48x20", lambda: cg.naca0012_block(48, 20))
+    return lk.Solver.batch([c] * len(conds), conds, first_order_iters=20, inner_iters=K), c
+
+
+def test_training_lowers_the_loss_and_predict_is_judged():
+    from paper_2406_07441_gb300 import lskum as lk
+    conds = [(0.4, 0.0), (0.5, 2.0), (0.6, -1.0), (0.45, 3.0)]
+    b, c = _solver_batch(conds)
+    assert b.run(150) == 150
+    m = lk.Mlp(seed=5, max_batch=2048)
+    m.add_samples(b, 4096, seed=1)
+    assert m.n_samples() == 4 * int(np.count_nonzero(c.flag != 2))
+    losses = m.train(60, 512, 2e-3, seed=2)
+    print("epoch losses", losses[[0, 9, 29, 59]])
+    assert losses[-1] < 0.2 * losses[0]
+    t, _ = _solver_batch([(0.55, 1.0)])
+    warm = m.predict(t)
+    r_pred = t.residuals()
+    assert r_pred.size == 0  # history cleared
+    assert t.run(5) == 5     # a valid state either way
+    print("warm kept:", warm)
