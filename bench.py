@@ -164,8 +164,13 @@ def run_ours(args, rank, world, local_rank):
     nslots = int(np.count_nonzero(_memberships(cloud)))
     # first-order start-up, then warm-up iterations (untimed)
     assert s.run(START) == START
-    # launch shape chosen by the library's autotuner (real iterations, state restored)
-    tpp, lanes, _ = s.autotune(5)
+    # launch shape chosen by the library's autotuner (real iterations, state
+    # restored), or given (e.g. for a profiler run with a known launch count)
+    if args.launch_shape:
+        tpp, lanes = (int(t) for t in args.launch_shape.split(","))
+        s.set_launch_shape(tpp, lanes)
+    else:
+        tpp, lanes, _ = s.autotune(5)
     assert s.run(args.warmup) == args.warmup
     stream = torch.cuda.ExternalStream(s.stream())
     e0 = torch.cuda.Event(enable_timing=True)
@@ -229,7 +234,8 @@ def run_ours(args, rank, world, local_rank):
                    "mach": 0.85, "aoa_deg": 1.0, "cfl": 100.0, "inner_iters": 3, "jvp": "exact-AD",
                    "order": f"second (timed steps follow {START} untimed first-order start-up iterations)",
                    "colours": info["n_colours"],
-                   "launch_shape": {"threads_per_point": tpp, "sweep_lanes_per_point": lanes, "by": "autotune"},
+                   "launch_shape": {"threads_per_point": tpp, "sweep_lanes_per_point": lanes,
+                                    "by": "given" if args.launch_shape else "autotune"},
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": f"inputs larger than L2: device working set {ws / 2**20:.0f} MiB > 129 MiB L2"},
         "roofline": {"bound": "alu", "kernel": "k_residual", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
@@ -421,6 +427,8 @@ def main():
                     help="0: plain FP64 (default for the single cloud); 1: FP32 sweeps with FP64 residual "
                          "and update (default for the batch)")
     ap.add_argument("--workload", choices=[WORKLOAD, BATCH_WORKLOAD], default=WORKLOAD)
+    ap.add_argument("--launch-shape", default="",
+                    help="T,L: threads per point and sweep lanes per point instead of autotuning")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -230,6 +230,13 @@ lskum_status lskum_time_phases(lskum_ctx *ctx, int32_t reps, double *ms);
 lskum_status lskum_autotune(lskum_ctx *ctx, int32_t trial_iters, int32_t *tpp, int32_t *sweep_lanes,
                             double *ms_per_iter);
 
+/* Set the launch shape directly (e.g. one found by lskum_autotune for the
+ * same cloud earlier): tpp in {1, 2, 4, 8} threads per point of the
+ * q-derivative and residual kernels, sweep_lanes in {2, 4, 8} lanes per point
+ * of the sweep kernels.  The iteration graphs are re-captured.  Errors:
+ * LSKUM_ERR_ARG (other values, or a run not waited for), LSKUM_ERR_CUDA. */
+lskum_status lskum_set_launch_shape(lskum_ctx *ctx, int32_t tpp, int32_t sweep_lanes);
+
 /* Number of points, of colours and of kernel launches one iteration makes. */
 lskum_status lskum_get_info(lskum_ctx *ctx, int32_t *n_points, int32_t *n_colours, int32_t *launches_per_iter);
 

@@ -1606,6 +1606,17 @@ lskum_status lskum_get_wall_distance(lskum_ctx *c, double *d)
     return LSKUM_OK;
 }
 
+lskum_status lskum_set_launch_shape(lskum_ctx *c, int32_t tpp, int32_t sweep_lanes)
+{
+    if (!c) return LSKUM_ERR_ARG;
+    if ((tpp != 1 && tpp != 2 && tpp != 4 && tpp != 8) || (sweep_lanes != 2 && sweep_lanes != 4 && sweep_lanes != 8))
+        return fail(c, LSKUM_ERR_ARG, "launch shape %d, %d not supported", tpp, sweep_lanes);
+    if (c->pending) return fail(c, LSKUM_ERR_ARG, "an enqueued run has not been waited for");
+    c->launch.tpp = tpp;
+    c->launch.sweep_lanes = sweep_lanes;
+    return build_graphs(c);
+}
+
 lskum_status lskum_set_start_iters(lskum_ctx *c, int32_t first_order_iters)
 {
     if (!c || first_order_iters < 0) return c ? fail(c, LSKUM_ERR_ARG, "bad argument") : LSKUM_ERR_ARG;

@@ -73,6 +73,7 @@ def load():
     L.lskum_get_case_info.argtypes = [vp, i32, P(i32), P(i32), P(i32), P(i32), P(i32), P(i32)]
     L.lskum_get_wall_distance.argtypes = [vp, vp]
     L.lskum_set_start_iters.argtypes = [vp, i32]
+    L.lskum_set_launch_shape.argtypes = [vp, i32, i32]
     u64 = C.c_uint64
     L.lskum_mlp_n_params.argtypes = []
     L.lskum_mlp_n_params.restype = i32
@@ -99,7 +100,7 @@ def load():
               "lskum_get_state", "lskum_get_field", "lskum_get_residuals", "lskum_get_forces", "lskum_get_order",
               "lskum_get_info", "lskum_time_phases", "lskum_density_norm_noalloc", "lskum_batch_create",
               "lskum_get_case_residuals", "lskum_get_case_forces", "lskum_get_case_info", "lskum_autotune",
-              "lskum_get_wall_distance", "lskum_set_start_iters", "lskum_mlp_create", "lskum_mlp_get_params",
+              "lskum_get_wall_distance", "lskum_set_start_iters", "lskum_set_launch_shape", "lskum_mlp_create", "lskum_mlp_get_params",
               "lskum_mlp_set_params", "lskum_mlp_features", "lskum_mlp_forward", "lskum_mlp_loss_grads",
               "lskum_mlp_adam", "lskum_mlp_add_samples", "lskum_mlp_n_samples", "lskum_mlp_train",
               "lskum_mlp_predict"):
@@ -274,6 +275,9 @@ class Solver:
         d = np.empty(self.n)
         self._check(load().lskum_get_wall_distance(self._h, _p(d)))
         return d
+
+    def set_launch_shape(self, tpp, sweep_lanes):
+        self._check(load().lskum_set_launch_shape(self._h, int(tpp), int(sweep_lanes)))
 
     def set_start_iters(self, first_order_iters):
         self._check(load().lskum_set_start_iters(self._h, int(first_order_iters)))
