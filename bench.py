@@ -189,11 +189,8 @@ def run_ours(args, rank, world, local_rank):
     if done != args.steps:
         raise RuntimeError(f"only {done} of {args.steps} iterations ran")
     ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * n * args.steps / (ms_max / 1e3)
+    ms_max, (work_all,) = combine_over_ranks(dist, ms, [float(n) * args.steps], "cuda")
+    value = work_all / (ms_max / 1e3)
 
     # live per-phase timing (CUDA events on the library stream) for the roofline
     phases = s.time_phases(5)
@@ -253,6 +250,18 @@ def run_ours(args, rank, world, local_rank):
 
 
 BATCH_WORKLOAD = "naca0012_batch64"
+
+
+def combine_over_ranks(dist, ms, counts, device):
+    """The job's time is the slowest rank's, its work the sum of the ranks'
+    (dist = torch.distributed or None for one process)."""
+    import torch
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    c = torch.tensor([float(x) for x in counts], device=device, dtype=torch.float64)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), [float(x) for x in c.tolist()]
 
 
 def _shard(cases, rank, world):
@@ -330,13 +339,8 @@ def run_batch(args, rank, world, local_rank):
     # failed (non-physical update or non-finite norm) is frozen and skipped
     work = sum(c.n * (inf["iters"] - i0) for c, inf, i0 in zip(clouds, infos, it0))
     failed = sum(1 for inf in infos if inf["status"] != 0)
-    pts = torch.tensor([float(n), float(work), float(failed)], device="cuda", dtype=torch.float64)
-    t = torch.tensor([ms], device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(pts, op=dist.ReduceOp.SUM)
-    ms_max = float(t.item())
-    n_all, work_all, failed_all = (float(x) for x in pts.tolist())
+    ms_max, (n_all, work_all, failed_all) = combine_over_ranks(dist, ms, [float(n), float(work), float(failed)],
+                                                               "cuda")
     value = work_all / (ms_max / 1e3)
     drops = [float(h[-1] / h[0]) for k, h in enumerate(s.case_residuals(k) for k in range(len(cases)))
              if infos[k]["status"] == 0]
@@ -396,6 +400,103 @@ def run_batch(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+WARM_WORKLOAD = "naca0012_warmstart"
+
+
+def run_warmstart(args, rank, world, local_rank):
+    """Learned warm start on the 147,584-point cloud: train the network on the
+    solver's own solutions at --train-solves random (M, AoA), then for 32
+    unseen (M, AoA) compare the wall time of the plain FP64 solve from the
+    free stream (first-order start-up, then second order) for 300 iterations
+    with the FP32-sweep solve from the prediction (second order from the
+    first iteration) until it reaches the plain solve's final residual norm."""
+    import numpy as np
+    import torch
+
+    from paper_2406_07441_gb300 import cloudgen as cg
+    from paper_2406_07441_gb300 import lskum
+
+    torch.cuda.set_device(local_rank)
+    if rank != 0:
+        return
+    cloud = cg.build_workload(WORKLOAD)
+    rng = np.random.default_rng(cg.BASE_SEED + 5)
+    train = [(float(rng.uniform(0.3, 0.85)), float(rng.uniform(-4, 6))) for _ in range(args.train_solves)]
+    test = [(float(rng.uniform(0.3, 0.85)), float(rng.uniform(-4, 6))) for _ in range(32)]
+    iters = 300
+    # training data: batched FP32-sweep solves, 4,096 points sampled per solve
+    t0 = time.perf_counter()
+    net = lskum.Mlp(seed=cg.BASE_SEED, max_batch=4096)
+    failed_train = 0
+    for g0 in range(0, len(train), 32):
+        conds = train[g0:g0 + 32]
+        b = lskum.Solver.batch([cloud] * len(conds), conds, first_order_iters=START, precision=1)
+        b.run(iters)
+        failed_train += sum(1 for k in range(len(conds)) if b.case_info(k)["status"] != 0)
+        net.add_samples(b, 4096, seed=g0)
+        del b
+    t_data = time.perf_counter() - t0
+    epochs = max(20, int(200 * 64 / max(len(train), 1)))
+    t0 = time.perf_counter()
+    losses = net.train(epochs, 512, 1e-3, seed=1)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+
+    plain_t, warm_t, plain_it, warm_it, kept, dcl, dcd, pred_t = [], [], [], [], [], [], [], []
+    for (m, a) in test:
+        sp = lskum.Solver(cloud, m, a, first_order_iters=START, precision=0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        done = sp.run(iters, check=False)[1]
+        torch.cuda.synchronize()
+        plain_t.append(time.perf_counter() - t0)
+        hp = sp.residuals()
+        target = hp[-1]
+        plain_it.append(done)
+        sw = lskum.Solver(cloud, m, a, first_order_iters=0, precision=1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        kept.append(bool(net.predict(sw)[0]))
+        t1 = time.perf_counter()
+        s1, d1 = sw.run(1, check=False)
+        h0 = sw.residuals()[0]
+        s2, d2 = sw.run(iters - 1, target_drop=target / h0, check=False) if h0 > target else (0, 0)
+        torch.cuda.synchronize()
+        warm_t.append(time.perf_counter() - t0)
+        pred_t.append(t1 - t0)
+        hw = sw.residuals()
+        reached = int(np.argmax(hw <= target)) + 1 if np.any(hw <= target) else -1
+        warm_it.append(reached)
+        clp, cdp = sp.forces()
+        clw, cdw = sw.forces()
+        dcl.append(abs(clw - clp))
+        dcd.append(abs(cdw - cdp))
+        del sp, sw
+    ratio = np.array([w / p if it > 0 else np.inf for w, p, it in zip(warm_t, plain_t, warm_it)])
+    it_ratio = np.array([w / p if w > 0 else np.inf for w, p in zip(warm_it, plain_it)])
+    line = {
+        "metric": "wall time to the plain FP64 solve's 300-iteration residual level, FP32 sweeps + warm start "
+                  "vs plain FP64 from the free stream (ratio, median over 32 unseen conditions)",
+        "value": float(np.median(ratio)), "unit": "ratio", "higher_is_better": False, "n_gpus": 1,
+        "steps": iters, "warmup": 0, "dtype": "f64 (plain) / f64+f32 sweeps + bf16 network (warm)",
+        "data": "synthetic",
+        "config": {"workload": WARM_WORKLOAD, "cloud": WORKLOAD, "points": cloud.n, "train_solves": len(train),
+                   "train_failed": failed_train, "samples": net.n_samples(), "epochs": epochs,
+                   "test_conditions": len(test), "plain": "FP64, 50 first-order start-up iterations, 300 total",
+                   "warm": "FP32 sweeps, prediction judged by the residual, second order from iteration 1"},
+        "warm_start": {
+            "time_ratio_median": float(np.median(ratio)), "time_ratio_worst": float(np.max(ratio)),
+            "iteration_ratio_median": float(np.median(it_ratio)), "iteration_ratio_worst": float(np.max(it_ratio)),
+            "plain_s_median": float(np.median(plain_t)), "warm_s_median": float(np.median(warm_t)),
+            "predict_s_median": float(np.median(pred_t)), "prediction_kept": int(sum(kept)),
+            "not_reached": int(sum(1 for w in warm_it if w < 0)),
+            "cl_diff_median": float(np.median(dcl)), "cd_diff_median": float(np.median(dcd)),
+            "data_s": t_data, "train_s": t_train, "final_loss": float(losses[-1]),
+        },
+    }
+    print(json.dumps(line), flush=True)
+
+
 def _memberships(cloud):
     """Neighbour slots that join a split sub-stencil of a wall or interior point."""
     import numpy as np
@@ -426,7 +527,8 @@ def main():
     ap.add_argument("--precision", type=int, choices=[0, 1], default=None,
                     help="0: plain FP64 (default for the single cloud); 1: FP32 sweeps with FP64 residual "
                          "and update (default for the batch)")
-    ap.add_argument("--workload", choices=[WORKLOAD, BATCH_WORKLOAD], default=WORKLOAD)
+    ap.add_argument("--workload", choices=[WORKLOAD, BATCH_WORKLOAD, WARM_WORKLOAD], default=WORKLOAD)
+    ap.add_argument("--train-solves", type=int, default=128, help="warm-start workload: training solves")
     ap.add_argument("--launch-shape", default="",
                     help="T,L: threads per point and sweep lanes per point instead of autotuning")
     args = ap.parse_args()
@@ -441,6 +543,8 @@ def main():
         run_reference(args, rank)
     elif args.workload == BATCH_WORKLOAD:
         run_batch(args, rank, world, local_rank)
+    elif args.workload == WARM_WORKLOAD:
+        run_warmstart(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 
