@@ -42,6 +42,11 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # launch, divided by the 2,926,611 such slots); see profiles/.
 RES_FLOPS_PER_SLOT = 454.55
 START = 50  # first-order start-up iterations before warm-up and timing
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one residual
+# launch on this workload at 2 threads per point, from one ncu capture of the
+# current kernel (profiles/k_residual_naca0012_640x256_jit.md); reported only
+# when the bench runs that launch shape.
+RES_TRAFFIC = {2: 164.49664e6}
 
 
 def _env_int(k, d):
@@ -236,7 +241,12 @@ def run_ours(args, rank, world, local_rank):
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": f"inputs larger than L2: device working set {ws / 2**20:.0f} MiB > 129 MiB L2"},
         "roofline": {"bound": "alu", "kernel": "k_residual", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     "traffic": RES_TRAFFIC.get(tpp) if args.precision == 0 else None,
+                     "traffic_unit": "bytes per launch (ncu)",
+                     "algorithmic_bytes_per_launch": int(cloud.nnz) * 37 + n * 360,
+                     "algorithmic_bytes_rule": "37 B per neighbour slot (index, membership, dx, dy, 2 weights) "
+                                               "+ 360 B per point (q, grad q, frame, geometry, state, R, D)",
                      "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz",
                      "launch_ms": res_ms, "phase_ms": phases},
         "cpu_baseline": cpu,
@@ -472,6 +482,11 @@ def run_warmstart(args, rank, world, local_rank):
         dcl.append(abs(clw - clp))
         dcd.append(abs(cdw - cdp))
         del sp, sw
+    # the network's forward pass over the whole cloud (tensor-core products)
+    net.time_forward(cloud.n, 3)
+    fwd_ms = net.time_forward(cloud.n, 20)
+    mlp_flops = 2.0 * (34 * 128 + 3 * 128 * 128 + 128 * 4) * cloud.n
+    bf16_peak = 1944.1  # MEASURED_PEAKS.json bf16_tflops (cuBLAS burst)
     ratio = np.array([w / p if it > 0 else np.inf for w, p, it in zip(warm_t, plain_t, warm_it)])
     it_ratio = np.array([w / p if w > 0 else np.inf for w, p in zip(warm_it, plain_it)])
     line = {
@@ -493,6 +508,11 @@ def run_warmstart(args, rank, world, local_rank):
             "cl_diff_median": float(np.median(dcl)), "cd_diff_median": float(np.median(dcd)),
             "data_s": t_data, "train_s": t_train, "final_loss": float(losses[-1]),
         },
+        "roofline": {"bound": "tensor", "kernel": "k_gemm (network forward, all layers)",
+                     "achieved": mlp_flops / (fwd_ms / 1e3) / 1e12, "peak": bf16_peak, "unit": "TFLOP/s",
+                     "frac": mlp_flops / (fwd_ms / 1e3) / 1e12 / bf16_peak, "traffic": None,
+                     "forward_ms": fwd_ms, "flops": mlp_flops,
+                     "peak_source": "measured bf16 dense (cuBLAS burst)"},
     }
     print(json.dumps(line), flush=True)
 

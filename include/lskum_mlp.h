@@ -76,6 +76,12 @@ lskum_status lskum_mlp_loss_grads(lskum_mlp *m, const float *X, const float *T, 
  * given gradient vector (n_params floats) and learning rate. */
 lskum_status lskum_mlp_adam(lskum_mlp *m, const float *grads, float lr);
 
+/* Measure: mean device time (CUDA events on the network's stream) of the
+ * forward pass over n points (in chunks of max_batch), reps repetitions, on
+ * whatever inputs the buffers hold (the products' cost does not depend on
+ * the values).  The network's parameters are unchanged. */
+lskum_status lskum_mlp_time_forward(lskum_mlp *m, int32_t n, int32_t reps, double *ms);
+
 /* Append training samples from the context's current state: per case,
  * per_case points drawn without replacement (seeded; all points of a case if
  * it has fewer) among its wall and interior points, skipping cases whose

@@ -1068,6 +1068,31 @@ lskum_status lskum_mlp_adam(lskum_mlp *m, const float *grads, float lr)
     return e == cudaSuccess ? LSKUM_OK : mcuda(m, e, "Adam step");
 }
 
+lskum_status lskum_mlp_time_forward(lskum_mlp *m, int32_t n, int32_t reps, double *ms)
+{
+    if (!m || n < 1 || reps < 1 || !ms) return m ? mfail(m, LSKUM_ERR_ARG, "bad argument") : LSKUM_ERR_ARG;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, m->stream);
+    for (int r = 0; r < reps && e == cudaSuccess; r++)
+        for (int32_t k0 = 0; k0 < n && e == cudaSuccess; k0 += m->P) {
+            const int nb = std::min(m->P, n - k0);
+            e = forward(m, nb, (nb + 127) / 128 * 128, false);
+        }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, m->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return mcuda(m, e, "timing the forward pass");
+    lskum_status st = check_err(m);
+    if (st != LSKUM_OK) return st;
+    *ms = (double)t / reps;
+    return LSKUM_OK;
+}
+
 lskum_status lskum_mlp_n_samples(lskum_mlp *m, int32_t *n)
 {
     if (!m || !n) return LSKUM_ERR_ARG;

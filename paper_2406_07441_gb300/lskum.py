@@ -85,6 +85,7 @@ def load():
     L.lskum_mlp_loss_grads.argtypes = [vp, vp, vp, i32, P(C.c_float), vp]
     L.lskum_mlp_adam.argtypes = [vp, vp, C.c_float]
     L.lskum_mlp_add_samples.argtypes = [vp, vp, i32, u64]
+    L.lskum_mlp_time_forward.argtypes = [vp, i32, i32, P(d)]
     L.lskum_mlp_n_samples.argtypes = [vp, P(i32)]
     L.lskum_mlp_train.argtypes = [vp, i32, i32, C.c_float, u64, vp]
     L.lskum_mlp_predict.argtypes = [vp, vp, vp]
@@ -102,7 +103,7 @@ def load():
               "lskum_get_case_residuals", "lskum_get_case_forces", "lskum_get_case_info", "lskum_autotune",
               "lskum_get_wall_distance", "lskum_set_start_iters", "lskum_set_launch_shape", "lskum_mlp_create", "lskum_mlp_get_params",
               "lskum_mlp_set_params", "lskum_mlp_features", "lskum_mlp_forward", "lskum_mlp_loss_grads",
-              "lskum_mlp_adam", "lskum_mlp_add_samples", "lskum_mlp_n_samples", "lskum_mlp_train",
+              "lskum_mlp_adam", "lskum_mlp_add_samples", "lskum_mlp_time_forward", "lskum_mlp_n_samples", "lskum_mlp_train",
               "lskum_mlp_predict"):
         getattr(L, f).restype = st
     _lib = L
@@ -350,6 +351,12 @@ class Mlp:
     def adam(self, grads, lr):
         g = np.ascontiguousarray(grads, np.float32)
         self._check(load().lskum_mlp_adam(self._h, _p(g), C.c_float(lr)))
+
+    def time_forward(self, n, reps=10):
+        """Mean device ms of the forward pass over n points."""
+        ms = C.c_double()
+        self._check(load().lskum_mlp_time_forward(self._h, int(n), int(reps), C.byref(ms)))
+        return ms.value
 
     def add_samples(self, solver, per_case, seed=0):
         self._check(load().lskum_mlp_add_samples(self._h, solver._h, int(per_case), C.c_uint64(seed)))
