@@ -13,6 +13,8 @@ diagonal 1e-12 (per entry, a sum of positive terms).  Histories and final
 fields use the benchmark spec's tolerances: 1e-10 relative per history entry and
 1e-9 normwise on the final state.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -206,3 +208,42 @@ def test_config2_full_size():
     assert nrel(s.field(lk.FIELD_U), r["U"]) < 1e-12
     h = s.residuals()
     assert np.max(np.abs(h - r["hist"]) / r["hist"]) < 1e-10
+
+
+@pytest.mark.slow
+@pytest.mark.skipif(os.environ.get("LSKUM_FULL_SIZE") != "1",
+                    reason="5.24M-point cloud: about 5 minutes of host time; set LSKUM_FULL_SIZE=1")
+def test_config3_full_size_fp64_and_mixed():
+    """Jittered 2560x2048 cloud, nothing removed: 5,242,880 points, M = 0.8,
+    AoA = 1.25 deg, exact JVPs: one first-order start-up iteration and one
+    second-order one, plain FP64 and FP32 sweeps, every field of the last
+    against the FP64 oracle."""
+    lk = _lskum()
+    c = cg.build_workload("naca0012_2560x2048_jit")
+    assert c.n == 5242880
+    o = O.Oracle(c)
+    r = o.run(o.initial_state(0.8, 1.25), 2, cfl=100.0, K=3, first_order=1)
+    assert r["status"] == 0
+    for prec in (0, 1):
+        s = lk.Solver(c, 0.8, 1.25, first_order_iters=1, precision=prec)
+        assert s.run(2) == 2
+        e = {k: nrel(s.field(f), r[v]) for k, f, v in (("R", lk.FIELD_R, "R"), ("dUs", lk.FIELD_DUS, "dUs"),
+                                                        ("dU", lk.FIELD_DU, "dU"), ("U", lk.FIELD_U, "U"))}
+        h = s.residuals()
+        e["hist"] = float(np.max(np.abs(h - r["hist"]) / r["hist"]))
+        rho, u, v, p = s.get_state()
+        Uo = r["U"]
+        rho_o = Uo[:, 0]
+        p_o = 0.4 * (Uo[:, 3] - 0.5 * (Uo[:, 1] ** 2 + Uo[:, 2] ** 2) / rho_o)
+        e["rho"] = float(np.max(np.abs(rho - rho_o)))
+        e["p"] = float(np.max(np.abs(p - p_o)))
+        cl, cd = s.forces()
+        clo, cdo = o.forces(Uo, 0.8, 1.25)
+        e["Cl"], e["Cd"] = abs(cl - clo), abs(cd - cdo)
+        print("precision", prec, e)
+        assert e["R"] < 1e-10 and e["hist"] < 1e-10
+        if prec == 0:
+            assert e["dUs"] < 1e-10 and e["dU"] < 1e-10 and e["U"] < 1e-12
+        else:
+            assert e["dUs"] < 1e-5 and e["dU"] < 1e-5 and e["U"] < 1e-6
+        del s
