@@ -16,6 +16,10 @@
 //   kFwdOut     Z + b -> outputs (FP32);
 //   kBwdData    (G W) * GELU'(Z) -> BF16 gradients (row-major and transposed);
 //   kWgrad      split-K partial sums of G^T A for the weight gradients.
+// Inference (forward pass, prediction into a solver state) instead runs
+// k_mlp_fused: persistent CTAs keep all five layers' weights in shared memory
+// and carry each 128-point tile through the five products with the
+// activations staying on the SM (see the comment above that kernel).
 // Operand layouts: activations and gradients are kept both point-major
 // ([points][features], the A operand of forward and backward-data products)
 // and feature-major ([features][points], the operands of weight-gradient
@@ -403,20 +407,6 @@ __global__ void k_features(const float *in5, const int32_t *idx, int n, int rows
     write_features(B, s[0], s[1], s[2], s[3], s[4], X, Xt, i, ldt);
 }
 
-// Points [k0, k0 + n) of a context view, then zeros up to rows.
-__global__ void k_features_view(lskum::MlpView v, int k0, int n, int rows, const float *B, uint16_t *X)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= rows) return;
-    if (i >= n) {
-        zero_features(X, nullptr, i, 0);
-        return;
-    }
-    const int k = k0 + i;
-    const int b = v.case_of[k];
-    write_features(B, v.x[k], v.y[k], v.dwall[k], v.case_mach[b], v.case_aoa[b], X, nullptr, i, 0);
-}
-
 // Given inputs X [n][34] (FP32) -> BF16 X rows and Xt columns, zeros up to rows.
 __global__ void k_inputs_from_f32(const float *Xf, int n, int rows, uint16_t *X, uint16_t *Xt, int ldt)
 {
@@ -528,29 +518,211 @@ __global__ void k_pack(PackArgs a)
     a.Wt[l][(size_t)i * op + o] = h;
 }
 
-// Outputs -> conserved state for points [k0, k0 + n) of a view (outer points
-// get the free stream of their case).
-__global__ void k_outputs_to_state(lskum::MlpView v, int k0, int n, const float *O)
+// ---------------------------------------------------------------------------
+// fused forward pass (inference): all five layers of a 128-point tile in one
+// CTA, weights resident in shared memory, activations never leave the SM
+// ---------------------------------------------------------------------------
+// Shared memory (dynamic): the BF16 weights of the five layers in the
+// core-matrix layout (W1 128x48, W2..W4 128x128, W5 16x128: 112 KB), the
+// input tile (128x48) and the hidden tile (128x128) that each layer's
+// epilogue overwrites with the next layer's input, and the biases.  Persistent
+// CTAs (one per SM, 8 warps) loop over the tiles.  Per layer one thread issues
+// the K/16 products into a 128-column TMEM accumulator; warps w and w + 4 read
+// the same 32 accumulator lanes (rows) and split the columns.
+constexpr int kFusedThreads = 256;
+constexpr int kSmemW1 = 128 * kInPad * 2, kSmemW = 128 * 128 * 2, kSmemW5 = kOutPad * 128 * 2;
+constexpr int kSmemX = 128 * kInPad * 2, kSmemH = 128 * 128 * 2;
+constexpr int kOffW1 = 0, kOffW2 = kOffW1 + kSmemW1, kOffW5 = kOffW2 + 3 * kSmemW, kOffX = kOffW5 + kSmemW5,
+              kOffH = kOffX + kSmemX, kOffBias = kOffH + kSmemH;
+constexpr int kBiasFloats = 4 * kWidth + kOutPad;
+constexpr int kFusedSmem = kOffBias + kBiasFloats * 4;
+
+enum FusedSrc { kSrcBuffer = 0, kSrcView = 1 };
+
+struct FusedArgs {
+    const uint16_t *W[kLayers];  // global BF16 weights [out_pad][in_pad]
+    const float *params;
+    int off[kLayers];
+    int n;                       // rows (points)
+    const uint16_t *X;           // kSrcBuffer: [n][48] BF16 inputs
+    float *O;                    // kSrcBuffer: [n][4] outputs
+    lskum::MlpView v;            // kSrcView: points k0 + i of the view, state written
+    int k0;
+    const float *fourier;
+    int *err;
+};
+
+// Write a row of 16-bit values (8 per 16-byte chunk) into a core-matrix tile.
+__device__ __forceinline__ void store_row_chunk(uint8_t *tile, int kg_stride, int r, int j, const uint16_t *h8)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int k = k0 + i;
-    const int b = v.case_of[k];
-    const double a = (double)v.case_aoa[b] * 0.017453292519943295;
-    const double M = v.case_mach[b];
-    const double uinf = M * cos(a), vinf = M * sin(a);
-    double rho = 1.0, u = uinf, w = vinf, p = 1.0 / 1.4;
-    if (v.flag[k] != LSKUM_OUTER) {
-        rho = exp((double)O[(size_t)i * kOut]);
-        u = uinf + (double)O[(size_t)i * kOut + 1];
-        w = vinf + (double)O[(size_t)i * kOut + 2];
-        p = exp((double)O[(size_t)i * kOut + 3]) / 1.4;
+    *reinterpret_cast<uint4 *>(tile + ((r >> 3) * kg_stride + j) * 128 + (r & 7) * 16) =
+        make_uint4(h8[0] | (uint32_t)h8[1] << 16, h8[2] | (uint32_t)h8[3] << 16, h8[4] | (uint32_t)h8[5] << 16,
+                   h8[6] | (uint32_t)h8[7] << 16);
+}
+
+template <int SRC>
+__global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(FusedArgs a)
+{
+    extern __shared__ __align__(1024) uint8_t sm[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tslot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    float *sbias = reinterpret_cast<float *>(sm + kOffBias);
+    // weights and biases, once per CTA
+    for (int l = 0; l < kLayers; l++) {
+        const int ip = l == 0 ? kInPad : kWidth, op = l == 4 ? kOutPad : kWidth, kg = ip / 8;
+        uint8_t *dst = sm + (l == 0 ? kOffW1 : (l == 4 ? kOffW5 : kOffW2 + (l - 1) * kSmemW));
+        for (int v = tid; v < op * kg; v += kFusedThreads) {
+            const int r = v / kg, j = v - r * kg;
+            *reinterpret_cast<uint4 *>(dst + ((r >> 3) * kg + j) * 128 + (r & 7) * 16) =
+                *reinterpret_cast<const uint4 *>(a.W[l] + (size_t)r * ip + 8 * j);
+        }
     }
-    const int ld = v.ld;
-    v.U[k] = rho;
-    v.U[ld + k] = rho * u;
-    v.U[2 * ld + k] = rho * w;
-    v.U[3 * ld + k] = p / 0.4 + 0.5 * rho * (u * u + w * w);
+    for (int i = tid; i < kBiasFloats; i += kFusedThreads) {
+        const int l = i / kWidth, c = i - l * kWidth;
+        sbias[i] = (l < 4) ? a.params[a.off[l] + kWidth * (l == 0 ? kIn : kWidth) + c]
+                           : (c < kOut ? a.params[a.off[4] + kOut * kWidth + c] : 0.f);
+    }
+    if (warp == 0) tmem_alloc(&tslot, 128);
+    if (tid == 0) mbar_init(&bar, 1);
+    fence_smem_to_async();
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = tslot;
+    const uint32_t sX = smem_u32(sm + kOffX), sH = smem_u32(sm + kOffH);
+    uint32_t parity = 0;
+    int ok = 1;
+    const int n_tiles = (a.n + 127) / 128;
+    const int r_epi = 32 * (warp & 3) + lane;  // accumulator row (lane) this thread reads
+    const int c_half = (warp >> 2) * 64;       // its 64 columns
+    const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+    for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        const int p0 = t * 128;
+        // 1. the input tile
+        if (tid < 128) {
+            const int i = p0 + tid;
+            uint16_t h[kInPad];
+            if (i < a.n) {
+                if (SRC == kSrcBuffer) {
+                    const uint4 *src = reinterpret_cast<const uint4 *>(a.X + (size_t)i * kInPad);
+#pragma unroll
+                    for (int q = 0; q < kInPad / 8; q++) {
+                        const uint4 u = src[q];
+                        h[8 * q] = u.x & 0xFFFF; h[8 * q + 1] = u.x >> 16; h[8 * q + 2] = u.y & 0xFFFF;
+                        h[8 * q + 3] = u.y >> 16; h[8 * q + 4] = u.z & 0xFFFF; h[8 * q + 5] = u.z >> 16;
+                        h[8 * q + 6] = u.w & 0xFFFF; h[8 * q + 7] = u.w >> 16;
+                    }
+                } else {
+                    const int k = a.k0 + i;
+                    const int b = a.v.case_of[k];
+                    const float X0 = a.v.x[k] - 0.5f, y = a.v.y[k], d = a.v.dwall[k];
+                    const float r = sqrtf(X0 * X0 + y * y);
+                    const float z0 = X0 / (1.f + r), z1 = y / (1.f + r), z2 = d / (1.f + d);
+#pragma unroll
+                    for (int f = 0; f < kFreq; f++) {
+                        const float tt = a.fourier[3 * f] * z0 + a.fourier[3 * f + 1] * z1 + a.fourier[3 * f + 2] * z2;
+                        float sn, cs;
+                        sincospif(2.f * tt, &sn, &cs);
+                        h[f] = bf16_bits(sn);
+                        h[kFreq + f] = bf16_bits(cs);
+                    }
+                    h[2 * kFreq] = bf16_bits(a.v.case_mach[b]);
+                    h[2 * kFreq + 1] = bf16_bits(a.v.case_aoa[b] * 0.1f);
+#pragma unroll
+                    for (int f = kIn; f < kInPad; f++) h[f] = 0;
+                }
+            } else {
+#pragma unroll
+                for (int f = 0; f < kInPad; f++) h[f] = 0;
+            }
+#pragma unroll
+            for (int j = 0; j < kInPad / 8; j++) store_row_chunk(sm + kOffX, kInPad / 8, tid, j, h + 8 * j);
+        }
+        fence_smem_to_async();
+        __syncthreads();
+        // 2. the four hidden layers
+        for (int l = 0; l < 4 && ok; l++) {
+            if (tid == 0) {
+                fence_after_sync();
+                const int kg = l == 0 ? kInPad / 8 : kWidth / 8;
+                const uint32_t a0 = l == 0 ? sX : sH;
+                const uint32_t b0 = smem_u32(sm + (l == 0 ? kOffW1 : kOffW2 + (l - 1) * kSmemW));
+                for (int s = 0; s < kg / 2; s++)
+                    mma_bf16(tmem, smem_desc(a0 + 256u * s, 128u, 128u * kg), smem_desc(b0 + 256u * s, 128u, 128u * kg),
+                             idesc_bf16<128>(), s > 0 ? 1u : 0u);
+                mma_commit(&bar);
+            }
+            ok = __syncthreads_and(mbar_wait_bounded(&bar, parity) ? 1 : 0);
+            parity ^= 1u;
+            if (!ok) break;
+            fence_after_sync();
+#pragma unroll 1
+            for (int c0 = c_half; c0 < c_half + 64; c0 += 16) {
+                float v[16];
+                tmem_ld16(taddr + (uint32_t)c0, v);
+                uint16_t h[16];
+#pragma unroll
+                for (int q = 0; q < 16; q++) h[q] = bf16_bits(gelu(v[q] + sbias[l * kWidth + c0 + q]));
+                store_row_chunk(sm + kOffH, kWidth / 8, r_epi, c0 / 8, h);
+                store_row_chunk(sm + kOffH, kWidth / 8, r_epi, c0 / 8 + 1, h + 8);
+            }
+            fence_before_sync();
+            fence_smem_to_async();
+            __syncthreads();
+        }
+        if (!ok) break;
+        // 3. the output layer (N = 16, four used)
+        if (tid == 0) {
+            fence_after_sync();
+            const uint32_t b0 = smem_u32(sm + kOffW5);
+            for (int s = 0; s < kWidth / 16; s++)
+                mma_bf16(tmem, smem_desc(sH + 256u * s, 128u, 128u * (kWidth / 8)),
+                         smem_desc(b0 + 256u * s, 128u, 128u * (kWidth / 8)), idesc_bf16<16>(), s > 0 ? 1u : 0u);
+            mma_commit(&bar);
+        }
+        ok = __syncthreads_and(mbar_wait_bounded(&bar, parity) ? 1 : 0);
+        parity ^= 1u;
+        if (!ok) break;
+        fence_after_sync();
+        if (warp < 4) {
+            float v[16];
+            tmem_ld16(taddr, v);
+            const int i = p0 + r_epi;
+            if (i < a.n) {
+                float o[kOut];
+#pragma unroll
+                for (int q = 0; q < kOut; q++) o[q] = v[q] + sbias[4 * kWidth + q];
+                if (SRC == kSrcBuffer) {
+                    *reinterpret_cast<float4 *>(a.O + (size_t)i * kOut) = make_float4(o[0], o[1], o[2], o[3]);
+                } else {
+                    const int k = a.k0 + i;
+                    const int b = a.v.case_of[k];
+                    const double al = (double)a.v.case_aoa[b] * 0.017453292519943295;
+                    const double M = a.v.case_mach[b];
+                    const double uinf = M * cos(al), vinf = M * sin(al);
+                    double rho = 1.0, u = uinf, w = vinf, p = 1.0 / 1.4;
+                    if (a.v.flag[k] != LSKUM_OUTER) {
+                        rho = exp((double)o[0]);
+                        u = uinf + (double)o[1];
+                        w = vinf + (double)o[2];
+                        p = exp((double)o[3]) / 1.4;
+                    }
+                    const int ld = a.v.ld;
+                    a.v.U[k] = rho;
+                    a.v.U[ld + k] = rho * u;
+                    a.v.U[2 * ld + k] = rho * w;
+                    a.v.U[3 * ld + k] = p / 0.4 + 0.5 * rho * (u * u + w * w);
+                }
+            }
+        }
+        fence_before_sync();
+        __syncthreads();
+    }
+    if (!ok && tid == 0) atomicExch(a.err, 1);
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 128);
 }
 
 // Free stream of each point's case (all points of [0, n)).
@@ -848,6 +1020,44 @@ cudaError_t adam(lskum_mlp *m, float lr)
     return e;
 }
 
+int g_num_sms = 0;
+
+// Fused forward pass over n rows: from the BF16 input buffer X (outputs to O)
+// or from the points [k0, k0 + n) of a context view (state written).
+template <int SRC>
+cudaError_t fused_forward(lskum_mlp *m, int n, const uint16_t *X, float *O, const lskum::MlpView *v, int k0)
+{
+    if (n <= 0) return cudaSuccess;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_mlp_fused<SRC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    if (!g_num_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 1;
+    }
+    FusedArgs a{};
+    for (int l = 0; l < kLayers; l++) {
+        a.W[l] = m->W[l];
+        a.off[l] = m->off[l];
+    }
+    a.params = m->params;
+    a.n = n;
+    a.X = X;
+    a.O = O;
+    if (v) a.v = *v;
+    a.k0 = k0;
+    a.fourier = m->fourier;
+    a.err = m->err;
+    const int tiles = (n + 127) / 128;
+    k_mlp_fused<SRC><<<std::min(tiles, g_num_sms), kFusedThreads, kFusedSmem, m->stream>>>(a);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 extern "C" {
@@ -1024,7 +1234,7 @@ lskum_status lskum_mlp_forward(lskum_mlp *m, const float *X, int32_t n, float *o
             k_inputs_from_f32<<<(rows + 255) / 256, 256, 0, m->stream>>>(m->Xf, nb, rows, m->X, nullptr, 0);
             e = cudaGetLastError();
         }
-        if (e == cudaSuccess) e = forward(m, nb, rows, false);
+        if (e == cudaSuccess) e = fused_forward<kSrcBuffer>(m, nb, m->X, m->O, nullptr, 0);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(out + (size_t)k0 * kOut, m->O, (size_t)nb * kOut * sizeof(float),
                                 cudaMemcpyDeviceToHost, m->stream);
@@ -1078,7 +1288,7 @@ lskum_status lskum_mlp_time_forward(lskum_mlp *m, int32_t n, int32_t reps, doubl
     for (int r = 0; r < reps && e == cudaSuccess; r++)
         for (int32_t k0 = 0; k0 < n && e == cudaSuccess; k0 += m->P) {
             const int nb = std::min(m->P, n - k0);
-            e = forward(m, nb, (nb + 127) / 128 * 128, false);
+            e = fused_forward<kSrcBuffer>(m, nb, m->X, m->O, nullptr, 0);
         }
     if (e == cudaSuccess) e = cudaEventRecord(e1, m->stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -1235,17 +1445,7 @@ lskum_status lskum_mlp_predict(lskum_mlp *m, lskum_ctx *ctx, int32_t *warm)
     st = lskum::ctx_mlp_view(ctx, &v);  // the current state set may have changed
     if (st != LSKUM_OK) return mfail(m, st, "context view");
     e = cudaStreamSynchronize(v.stream);
-    for (int32_t k0 = 0; k0 < v.n && e == cudaSuccess; k0 += m->P) {
-        const int nb = std::min(m->P, v.n - k0);
-        const int rows = (nb + 127) / 128 * 128;
-        k_features_view<<<(rows + 255) / 256, 256, 0, m->stream>>>(v, k0, nb, rows, m->fourier, m->X);
-        e = cudaGetLastError();
-        if (e == cudaSuccess) e = forward(m, nb, rows, false);
-        if (e == cudaSuccess) {
-            k_outputs_to_state<<<(nb + 255) / 256, 256, 0, m->stream>>>(v, k0, nb, m->O);
-            e = cudaGetLastError();
-        }
-    }
+    if (e == cudaSuccess) e = fused_forward<kSrcView>(m, v.n, nullptr, nullptr, &v, 0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
     if (e != cudaSuccess) return mcuda(m, e, "prediction");
     st = check_err(m);
