@@ -241,9 +241,12 @@ def test_config3_full_size_fp64_and_mixed():
         clo, cdo = o.forces(Uo, 0.8, 1.25)
         e["Cl"], e["Cd"] = abs(cl - clo), abs(cd - cdo)
         print("precision", prec, e)
-        assert e["R"] < 1e-10 and e["hist"] < 1e-10
         if prec == 0:
+            assert e["R"] < 1e-10 and e["hist"] < 1e-10
             assert e["dUs"] < 1e-10 and e["dU"] < 1e-10 and e["U"] < 1e-12
         else:
+            # the second residual is evaluated at the state the FP32 sweeps
+            # produced (state error ~3e-8), so it inherits that error
+            assert e["R"] < 1e-6 and e["hist"] < 1e-6
             assert e["dUs"] < 1e-5 and e["dU"] < 1e-5 and e["U"] < 1e-6
         del s
