@@ -10,8 +10,8 @@ weights of size 1/h, so its error is measured against max|R| over the cloud
 (normwise), not per entry; the same for the increments.  Per iteration:
 q-derivatives 1e-12, residual / increments / state 1e-10 (normwise),
 diagonal 1e-12 (per entry, a sum of positive terms).  Histories and final
-fields use the benchmark spec's tolerances: 1e-10 relative per history entry and
-1e-9 normwise on the final state.
+fields use the target tolerances of the plain FP64 path: 1e-10 relative per
+history entry and 1e-9 normwise on the final state.
 """
 import os
 
