@@ -46,7 +46,7 @@ constexpr int kInTrue[kLayers] = {kIn, kWidth, kWidth, kWidth, kWidth};
 constexpr int kInP[kLayers] = {kInPad, kWidth, kWidth, kWidth, kWidth};
 constexpr int kOutTrue[kLayers] = {kWidth, kWidth, kWidth, kWidth, kOut};
 constexpr int kOutP[kLayers] = {kWidth, kWidth, kWidth, kWidth, kOutPad};
-constexpr int kSplitK = 512;  // points per CTA in weight-gradient products
+constexpr int kSplitK = 128;  // points per CTA in weight-gradient products
 constexpr int kBatchAlign = 512;
 
 constexpr int n_params_total()
