@@ -144,3 +144,46 @@ def test_training_lowers_the_loss_and_predict_is_judged():
     assert r_pred.size == 0  # history cleared
     assert t.run(5) == 5     # a valid state either way
     print("warm kept:", warm)
+
+
+def test_predict_on_a_batch_equals_single_contexts_and_judges_per_case():
+    """The prediction of a point depends only on its own inputs and the judge
+    compares each case's own first residuals, so a batch gets, case by case,
+    exactly the state and the decisions of single contexts; an untrained
+    network is rejected and the free stream kept."""
+    from paper_2406_07441_gb300 import lskum as lk
+    conds = [(0.4, 0.0), (0.5, 2.0), (0.6, -1.0), (0.45, 3.0)]
+    b, c = _solver_batch(conds)
+    assert b.run(150) == 150
+    m = lk.Mlp(seed=5, max_batch=2048)
+    m.add_samples(b, 4096, seed=1)
+    m.train(40, 512, 2e-3, seed=2)
+    raw = lk.Mlp(seed=9, max_batch=2048)  # untrained
+    tests = [(0.55, 1.0), (0.42, -2.0)]
+    for net in (m, raw):
+        bt, _ = _solver_batch(tests)
+        warm_b = net.predict(bt)
+        Ub = bt.field(lk.FIELD_U)
+        for k, (mach, aoa) in enumerate(tests):
+            s, _ = _solver_batch([(mach, aoa)])
+            warm_s = net.predict(s)
+            info = bt.case_info(k)
+            sl = slice(info["first_point"], info["first_point"] + info["n_points"])
+            assert warm_s[0] == warm_b[k]
+            assert np.array_equal(Ub[sl], s.field(lk.FIELD_U))
+            if not warm_s[0]:  # the free stream, wall-projected
+                fs, _ = _solver_batch([(mach, aoa)])
+                assert np.array_equal(s.field(lk.FIELD_U), fs.field(lk.FIELD_U))
+        print("warm kept:", warm_b.tolist(), "trained" if net is m else "untrained")
+        if net is m:
+            assert warm_b.all()
+        else:
+            assert not warm_b.any()
+    # outer points keep the free stream in a kept prediction
+    bt, _ = _solver_batch(tests)
+    m.predict(bt)
+    U = bt.field(lk.FIELD_U)
+    fs, _ = _solver_batch(tests)
+    Uf = fs.field(lk.FIELD_U)
+    outer = np.concatenate([c.flag == 2] * len(tests))
+    assert np.array_equal(U[outer], Uf[outer])
