@@ -11,18 +11,18 @@
 namespace lskum {
 
 struct MathTables {
-    double exp2j[64];             // 2^(j/64)
-    double ecx[5][kErfcxDeg + 1]; // erfcx/2 per interval, Horner coefficients
-    double sc[5], off[5];         // t = x * sc + off
+    double exp2j[64];                           // 2^(j/64)
+    double ecx[kErfcxIntervals][kErfcxDeg + 1]; // erfcx/2 per interval, Horner coefficients
+    double sc[kErfcxIntervals], off[kErfcxIntervals];  // t = x * sc + off
 };
 
 // Copy the tables into shared memory (all threads of the block; then sync).
 __device__ __forceinline__ void load_math_tables(MathTables &T)
 {
     for (int i = threadIdx.x; i < 64; i += blockDim.x) T.exp2j[i] = kExpTable[i];
-    for (int i = threadIdx.x; i < 5 * (kErfcxDeg + 1); i += blockDim.x)
+    for (int i = threadIdx.x; i < kErfcxIntervals * (kErfcxDeg + 1); i += blockDim.x)
         T.ecx[i / (kErfcxDeg + 1)][i % (kErfcxDeg + 1)] = kErfcxHalf[i / (kErfcxDeg + 1)][i % (kErfcxDeg + 1)];
-    if (threadIdx.x < 5) {
+    if (threadIdx.x < kErfcxIntervals) {
         T.sc[threadIdx.x] = kErfcxScale[threadIdx.x];
         T.off[threadIdx.x] = kErfcxOffset[threadIdx.x];
     }
@@ -53,7 +53,7 @@ __device__ __forceinline__ void split_E(const MathTables &T, double S, double &E
 {
     const double a = fmin(fabs(S), 9.0);
     const int ha = __double2hiint(a);  // positive doubles order like their high words
-    const int iv = (ha >= 0x3fe80000) + (ha >= 0x3ffc0000) + (ha >= 0x400a0000) + (ha >= 0x40160000);
+    const int iv = erfcx_interval(ha);
     const double t = fma(a, T.sc[iv], T.off[iv]);
     const double *c = T.ecx[iv];
     double p = c[kErfcxDeg];

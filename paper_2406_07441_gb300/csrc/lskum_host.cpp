@@ -85,6 +85,7 @@ struct lskum_ctx {
     double *case_hist0 = nullptr;
     // geometry the warm-start network reads (built on first use; internal order)
     float *mx = nullptr, *my = nullptr, *mdw = nullptr, *mcase_mach = nullptr, *mcase_aoa = nullptr;
+    double *mcase_Uinf = nullptr, *mcase_uv = nullptr;
     int cur = 0;                        // state set holding the current state
     int32_t it_base = 0;                // ctrl->it at the start of the pending enqueue
     int cur_base = 0;
@@ -93,6 +94,24 @@ struct lskum_ctx {
 };
 
 namespace {
+
+// Conserved variables of a primitive state (Eq. 2); the one host formula for
+// every state the library builds from primitives.
+void host_prim_to_cons(double rho, double u, double v, double p, double *U)
+{
+    U[0] = rho;
+    U[1] = rho * u;
+    U[2] = rho * v;
+    U[3] = p / 0.4 + 0.5 * rho * (u * u + v * v);
+}
+
+// Free-stream velocity of case b (the start state and the network's base).
+void host_free_stream(const lskum_ctx *c, int32_t b, double *u, double *v)
+{
+    const double alb = c->case_aoa[b] * M_PI / 180.0;
+    *u = c->case_mach[b] * std::cos(alb);
+    *v = c->case_mach[b] * std::sin(alb);
+}
 
 lskum_status fail(lskum_ctx *c, lskum_status s, const char *fmt, ...)
 {
@@ -767,16 +786,15 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemset");
 
     // ---- free-stream start ----
-    const double al = c->opts.aoa_deg * M_PI / 180.0;
     std::vector<double> rho(n, 1.0), uu(n), vv(n), pp(n, 1.0 / 1.4);
     for (int32_t b = 0; b < c->n_cases; b++) {
-        const double alb = c->case_aoa[b] * M_PI / 180.0;
+        double ub, vb;
+        host_free_stream(c, b, &ub, &vb);
         for (int32_t p = c->case_off[b]; p < c->case_off[b + 1]; p++) {
-            uu[p] = c->case_mach[b] * std::cos(alb);
-            vv[p] = c->case_mach[b] * std::sin(alb);
+            uu[p] = ub;
+            vv[p] = vb;
         }
     }
-    (void)al;
     lskum_status s = lskum_set_state(c, rho.data(), uu.data(), vv.data(), pp.data());
     if (s != LSKUM_OK) return s;
 
@@ -1002,10 +1020,7 @@ lskum_status lskum_set_state(lskum_ctx *c, const double *rho, const double *u, c
         if (!(rho[k] > 0.0) || !(p[k] > 0.0) || !std::isfinite(rho[k]) || !std::isfinite(p[k]) ||
             !std::isfinite(u[k]) || !std::isfinite(v[k]))
             return fail(c, LSKUM_ERR_NONPOSITIVE, "non-physical input state at point %d", k);
-        U[4 * (size_t)k] = rho[k];
-        U[4 * (size_t)k + 1] = rho[k] * u[k];
-        U[4 * (size_t)k + 2] = rho[k] * v[k];
-        U[4 * (size_t)k + 3] = p[k] / 0.4 + 0.5 * rho[k] * (u[k] * u[k] + v[k] * v[k]);
+        host_prim_to_cons(rho[k], u[k], v[k], p[k], &U[4 * (size_t)k]);
     }
     return state_from_conserved(c, U, true);
 }
@@ -1484,6 +1499,11 @@ lskum_status ctx_mlp_view(lskum_ctx *c, MlpView *v)
     const int32_t n = c->n, ld = c->ld;
     if (!c->mx) {
         std::vector<float> hx(ld, 0.f), hy(ld, 0.f), cm(c->n_cases), ca(c->n_cases);
+        std::vector<double> cU(4 * (size_t)c->n_cases), cuv(2 * (size_t)c->n_cases);
+        for (int32_t b = 0; b < c->n_cases; b++) {
+            host_free_stream(c, b, &cuv[2 * b], &cuv[2 * b + 1]);
+            host_prim_to_cons(1.0, cuv[2 * b], cuv[2 * b + 1], 1.0 / 1.4, &cU[4 * b]);
+        }
         for (int32_t k = 0; k < n; k++) {
             hx[k] = (float)c->x[c->perm[k]];
             hy[k] = (float)c->y[c->perm[k]];
@@ -1508,6 +1528,7 @@ lskum_status ctx_mlp_view(lskum_ctx *c, MlpView *v)
         Arena &A = c->arena;
         float *dx = A.alloc<float>(ld), *dy = A.alloc<float>(ld), *dw = A.alloc<float>(ld);
         float *dm = A.alloc<float>(c->n_cases), *da = A.alloc<float>(c->n_cases);
+        double *dU = A.alloc<double>(4 * (size_t)c->n_cases), *duv = A.alloc<double>(2 * (size_t)c->n_cases);
         float4 *dseg = A.alloc<float4>(seg.size());
         int32_t *doff = A.alloc<int32_t>(seg_off.size());
         if (A.err != cudaSuccess) return cuda_fail(c, A.err, "cudaMalloc(network geometry)");
@@ -1517,6 +1538,10 @@ lskum_status ctx_mlp_view(lskum_ctx *c, MlpView *v)
             e = cudaMemcpyAsync(dm, cm.data(), c->n_cases * sizeof(float), cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(da, ca.data(), c->n_cases * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dU, cU.data(), cU.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(duv, cuv.data(), cuv.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess && !seg.empty())
             e = cudaMemcpyAsync(dseg, seg.data(), seg.size() * sizeof(float4), cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess)
@@ -1531,6 +1556,8 @@ lskum_status ctx_mlp_view(lskum_ctx *c, MlpView *v)
         c->mdw = dw;
         c->mcase_mach = dm;
         c->mcase_aoa = da;
+        c->mcase_Uinf = dU;
+        c->mcase_uv = duv;
     }
     v->n = n;
     v->ld = ld;
@@ -1542,6 +1569,8 @@ lskum_status ctx_mlp_view(lskum_ctx *c, MlpView *v)
     v->case_of = c->dev.case_of;
     v->case_mach = c->mcase_mach;
     v->case_aoa = c->mcase_aoa;
+    v->case_Uinf = c->mcase_Uinf;
+    v->case_uv = c->mcase_uv;
     v->U = c->dev.set[c->cur].U;
     v->stream = c->stream;
     return LSKUM_OK;

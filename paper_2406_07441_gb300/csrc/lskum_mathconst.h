@@ -26,18 +26,27 @@ __constant__ double kExpTable[64] = {
     0x1.d5818dcfba487p+0, 0x1.da9e603db3285p+0, 0x1.dfc97337b9b5fp+0, 0x1.e502ee78b3ff6p+0,
     0x1.ea4afa2a490dap+0, 0x1.efa1bee615a27p+0, 0x1.f50765b6e4540p+0, 0x1.fa7c1819e90d8p+0,
 };
-constexpr int kErfcxDeg = 17;
-// interval bounds (upper limits of intervals 0..3), scale 1/h and offset -c/h of t = (x - c)/h
-constexpr double kErfcxBreak[4] = {0.75, 1.75, 3.25, 5.5};
-__constant__ double kErfcxScale[5] = {0x1.5555555555555p+1, 0x1.0000000000000p+1, 0x1.5555555555555p+0, 0x1.c71c71c71c71cp-1, 0x1.2492492492492p-1};
-__constant__ double kErfcxOffset[5] = {-0x1.0000000000000p+0, -0x1.4000000000000p+1, -0x1.aaaaaaaaaaaabp+1, -0x1.f1c71c71c71c7p+1, -0x1.0924924924925p+2};
-// erfcx/2 on each interval as a polynomial in t, coefficients of t^0 .. t^17
-__constant__ double kErfcxHalf[5][18] = {
-    {0x1.5f28ade3ca4acp-2, -0x1.d78a9b6c39906p-4, 0x1.066ec7e9d3637p-5, -0x1.fe7cd332f7cdep-8, 0x1.bee62667c60e7p-10, -0x1.66e2f5701f58ep-12, 0x1.0be20ec8b9b7cp-14, -0x1.7751fff41c288p-17, 0x1.f12d9161ee160p-20, -0x1.392c4dd75f27cp-22, 0x1.78ff0130aa716p-25, -0x1.b35a1d1954186p-28, 0x1.e3e1bec1de83bp-31, -0x1.03882591f1b41p-33, 0x1.0cd8534ccb692p-36, -0x1.0e93032db208bp-39, 0x1.19dd42653c398p-42, -0x1.0b387d9f2e217p-45},
-    {0x1.78a692138767ap-3, -0x1.abaacdbfa8b07p-5, 0x1.b56f45eef7e54p-7, -0x1.9b635ac624ad3p-9, 0x1.68a25a6642604p-11, -0x1.299636d6c5c2cp-13, 0x1.d1b695aa2f084p-16, -0x1.5b8bc94c18337p-18, 0x1.f0fe701071532p-21, -0x1.55c07d51f080fp-23, 0x1.c570150580da3p-26, -0x1.22fc2f897d7a9p-28, 0x1.6a1f9e61f1ef2p-31, -0x1.b5c38e603ea19p-34, 0x1.00a5432e17734p-36, -0x1.265fe133263efp-39, 0x1.66df2b2c822bap-42, -0x1.87225d22d7ebfp-45},
-    {0x1.afbb3f3b7343bp-4, -0x1.c8ca43e8282c8p-6, 0x1.cba83bc9e010bp-8, -0x1.ba746c7f90a7cp-10, 0x1.9940762e167d8p-12, -0x1.6d14f0daa3008p-14, 0x1.3b0d0864add93p-16, -0x1.07ac34bfe02d7p-18, 0x1.acf4e1e2d9e4ep-21, -0x1.53c35ef3c9288p-23, 0x1.0679c8912b6e2p-25, -0x1.8c1a9842f362ap-28, 0x1.245f0d1048559p-30, -0x1.a676f1d32e312p-33, 0x1.28d3a71ea5e37p-35, -0x1.9c996d1cc3ca3p-38, 0x1.4118e5a4fd282p-40, -0x1.ac9aeff844472p-43},
-    {0x1.01afcc22e71b8p-4, -0x1.f974dd6f23b4ep-7, 0x1.e523040980d6ep-9, -0x1.c83e185fa67b3p-11, 0x1.a4df48f2ba79ep-13, -0x1.7d3233c30b1dfp-15, 0x1.5349b8aba65f0p-17, -0x1.28ff334c60491p-19, 0x1.ffba53c69719cp-22, -0x1.b229c2763c53bp-24, 0x1.6af9bd1d12acbp-26, -0x1.2b33815a69a04p-28, 0x1.e6d82a5ae9965p-31, -0x1.86aca3db6bc32p-33, 0x1.315d1493f99f2p-35, -0x1.de45ba75a199ep-38, 0x1.b949f34ad5869p-40, -0x1.501da4dfdabd1p-42},
-    {0x1.3bcc59a28358cp-5, -0x1.2b5da7e32c4a6p-7, 0x1.194c1fd21c328p-9, -0x1.060e8d0d95955p-11, 0x1.e42fa0c62d4d4p-14, -0x1.bba6bffaf74d3p-16, 0x1.9345123121a2ep-18, -0x1.6bb4f625c8088p-20, 0x1.4586359aad2a5p-22, -0x1.212ce5b7061dcp-24, 0x1.fe005be4b3783p-27, -0x1.be85503060b2fp-29, 0x1.8490ae85b5704p-31, -0x1.4f78b8e5e652cp-33, 0x1.19d757a7efc39p-35, -0x1.e070bcc5ebd00p-38, 0x1.fa65a456aa635p-40, -0x1.a8c30a795c542p-42},
+constexpr int kErfcxDeg = 13;
+constexpr int kErfcxIntervals = 10;
+// high words of the interior interval bounds 0.5, 1.0, 1.5, 2.25, 3.0, 4.0, 5.0, 6.0, 7.5; then scale 1/h and offset -c/h of t = (x - c)/h per interval
+__device__ __forceinline__ int erfcx_interval(int ha)  // ha: high word of x >= 0
+{
+    return (ha >= 0x3fe00000) + (ha >= 0x3ff00000) + (ha >= 0x3ff80000) + (ha >= 0x40020000) + (ha >= 0x40080000) + (ha >= 0x40100000) + (ha >= 0x40140000) + (ha >= 0x40180000) + (ha >= 0x401e0000);
+}
+__constant__ double kErfcxScale[10] = {0x1.0000000000000p+2, 0x1.0000000000000p+2, 0x1.0000000000000p+2, 0x1.5555555555555p+1, 0x1.5555555555555p+1, 0x1.0000000000000p+1, 0x1.0000000000000p+1, 0x1.0000000000000p+1, 0x1.5555555555555p+0, 0x1.5555555555555p+0};
+__constant__ double kErfcxOffset[10] = {-0x1.0000000000000p+0, -0x1.8000000000000p+1, -0x1.4000000000000p+2, -0x1.4000000000000p+2, -0x1.c000000000000p+2, -0x1.c000000000000p+2, -0x1.2000000000000p+3, -0x1.6000000000000p+3, -0x1.2000000000000p+3, -0x1.6000000000000p+3};
+// erfcx/2 on each interval as a polynomial in t, coefficients of t^0 .. t^13
+__constant__ double kErfcxHalf[10][14] = {
+    {0x1.8a6adcda2ea92p-2, -0x1.7c857b9b3c191p-4, 0x1.2b497df35f8cfp-6, -0x1.97997ad330318p-9, 0x1.f0ac9d324abd6p-12, -0x1.146985bdac45dp-14, 0x1.1d0c2795710c2p-17, -0x1.132db78cf552ep-20, 0x1.f54d3f56d40bap-24, -0x1.b181df76bf71cp-27, 0x1.658e4ec31edf1p-30, -0x1.1aab1e21ecc3bp-33, 0x1.ba2e44941ccd1p-37, -0x1.4371ff52e055fp-40},
+    {0x1.038d54ea3d834p-2, -0x1.78cdd551ee51ap-5, 0x1.d90093ae108b0p-8, -0x1.09e77d40e0214p-10, 0x1.1192f5bd775ccp-13, -0x1.054d68296477dp-16, 0x1.d43a7c4dbe650p-20, -0x1.8c97dd32ae0e1p-23, 0x1.3f81a9597de0ap-26, -0x1.ec0d1ccb09b6fp-30, 0x1.6b80da7254f0fp-33, -0x1.02a2c5796f3cap-36, 0x1.6be408e744acbp-40, -0x1.e34f70587b39ap-44},
+    {0x1.78a692138767ap-3, -0x1.abaacdbfa8b07p-6, 0x1.b56f45eef7e3fp-9, -0x1.9b635ac624ac6p-12, 0x1.68a25a664836fp-15, -0x1.299636d6c9209p-18, 0x1.d1b69597f0c3dp-22, -0x1.5b8bc9419d840p-25, 0x1.f0fe8a88d3cd7p-29, -0x1.55c08c80d2503p-32, 0x1.c55c924775cc5p-36, -0x1.22f10017ec710p-39, 0x1.71368494f04cfp-43, -0x1.bde45264f2361p-47},
+    {0x1.13e5743b60481p-3, -0x1.6a8c2095f9678p-6, 0x1.bbbcdecac77dcp-9, -0x1.ff44800b6bb0ep-12, 0x1.1770a1387a55bp-14, -0x1.238aaeeff0ef9p-17, 0x1.23addb3a12f79p-20, -0x1.18e8a07eba6efp-23, 0x1.054059cefc55dp-26, -0x1.d682dcf30e74bp-30, 0x1.9af4a1c5406c6p-33, -0x1.5d3b0fd15c227p-36, 0x1.2b78f446ee404p-39, -0x1.e2dd46e69319ep-43},
+    {0x1.9d7738e1f4db7p-4, -0x1.a4ad387d18a36p-7, 0x1.985ce31879abep-10, -0x1.7c27aaae14f17p-13, 0x1.54c5cde0c42dbp-16, -0x1.271fb78890faap-19, 0x1.ef3c4f7e3a39ep-23, -0x1.937ffc5efe7c9p-26, 0x1.3fe3e305e5001p-29, -0x1.ee631de19f54ep-33, 0x1.74d3ca511dc82p-36, -0x1.12edb53981337p-39, 0x1.97bdca17eee26p-43, -0x1.2001ce79d92f7p-46},
+    {0x1.3e0a99a0ee914p-4, -0x1.5285d2eb1ef74p-7, 0x1.5d581133377e1p-10, -0x1.5e5d7e98990adp-13, 0x1.5632136dcfdf2p-16, -0x1.460abd6b5aac9p-19, 0x1.2f839defbf63dp-22, -0x1.146bc3b72634ap-25, 0x1.ed2b25c545409p-29, -0x1.af5dd63878f3cp-32, 0x1.721b31a16be1fp-35, -0x1.381bbf4ef7a2ep-38, 0x1.0c53817265dbep-41, -0x1.b52b88aa6a398p-45},
+    {0x1.f5b2a049cf4c6p-5, -0x1.aa3eb6a946f7ep-8, 0x1.62c12cb5f7555p-11, -0x1.218ed930b239ap-14, 0x1.d00785f2fe34fp-18, -0x1.6d54b133e1dafp-21, 0x1.1ad6a31498c35p-24, -0x1.aef8ea2825beap-28, 0x1.43551f4037b8bp-31, -0x1.de0985254e968p-35, 0x1.5c4a449ee453dp-38, -0x1.f4c4d68de7790p-42, 0x1.6cee7cc8c027ep-45, -0x1.fee5cbcae7c93p-49},
+    {0x1.9d8a8f2284f2cp-5, -0x1.238ca71b93fc3p-8, 0x1.95252b932efdcp-12, -0x1.15976ddda3c9dp-15, 0x1.774f4826df938p-19, -0x1.f4e46d17a1e30p-23, 0x1.4a17e192d447ap-26, -0x1.add7ac91b071bp-30, 0x1.149ce494d441ap-33, -0x1.60002e1ef0109p-37, 0x1.baf6971d5b9c3p-41, -0x1.13ce55f015bd9p-44, 0x1.5ae57d91ad3bfp-48, -0x1.a7111368968b7p-52},
+    {0x1.52b80d463c470p-5, -0x1.26cfae569219ep-8, 0x1.fc0d925cb9bd1p-12, -0x1.b1824073cd015p-15, 0x1.6e66b15c39900p-18, -0x1.32d4007c83afcp-21, 0x1.fd44931e8bec1p-25, -0x1.a2efa7e968f20p-28, 0x1.55aef0217abedp-31, -0x1.14598d251aeaep-34, 0x1.bb2aa06cc5859p-38, -0x1.60ad29029c8e7p-41, 0x1.2010958d391b0p-44, -0x1.c33613da16dbep-48},
+    {0x1.1618fbc75f8a0p-5, -0x1.8ec506eb645fap-9, 0x1.1bedf98ef6527p-12, -0x1.9196f54750860p-16, 0x1.1a1ee1759f40ep-19, -0x1.89ce516e5c4d4p-23, 0x1.1118e35c230b5p-26, -0x1.78668f170f874p-30, 0x1.01cae5867ee54p-33, -0x1.5efb042e31e5ap-37, 0x1.dae5ddbbbf417p-41, -0x1.3f7b094fefbe1p-44, 0x1.b5e7d16dee5dep-48, -0x1.2329273438940p-51},
 };
 
 }  // namespace lskum

@@ -698,21 +698,20 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(FusedArgs a)
                 } else {
                     const int k = a.k0 + i;
                     const int b = a.v.case_of[k];
-                    const double al = (double)a.v.case_aoa[b] * 0.017453292519943295;
-                    const double M = a.v.case_mach[b];
-                    const double uinf = M * cos(al), vinf = M * sin(al);
-                    double rho = 1.0, u = uinf, w = vinf, p = 1.0 / 1.4;
-                    if (a.v.flag[k] != LSKUM_OUTER) {
-                        rho = exp((double)o[0]);
-                        u = uinf + (double)o[1];
-                        w = vinf + (double)o[2];
-                        p = exp((double)o[3]) / 1.4;
-                    }
                     const int ld = a.v.ld;
-                    a.v.U[k] = rho;
-                    a.v.U[ld + k] = rho * u;
-                    a.v.U[2 * ld + k] = rho * w;
-                    a.v.U[3 * ld + k] = p / 0.4 + 0.5 * rho * (u * u + w * w);
+                    if (a.v.flag[k] == LSKUM_OUTER) {  // the context's own free stream, bit for bit
+#pragma unroll
+                        for (int q = 0; q < 4; q++) a.v.U[q * ld + k] = a.v.case_Uinf[4 * b + q];
+                    } else {
+                        const double rho = exp((double)o[0]);
+                        const double u = a.v.case_uv[2 * b] + (double)o[1];
+                        const double w = a.v.case_uv[2 * b + 1] + (double)o[2];
+                        const double p = exp((double)o[3]) / 1.4;
+                        a.v.U[k] = rho;
+                        a.v.U[ld + k] = rho * u;
+                        a.v.U[2 * ld + k] = rho * w;
+                        a.v.U[3 * ld + k] = p / 0.4 + 0.5 * rho * (u * u + w * w);
+                    }
                 }
             }
         }
@@ -732,14 +731,9 @@ __global__ void k_free_stream(lskum::MlpView v, const uint8_t *keep)
     if (k >= v.n) return;
     const int b = v.case_of[k];
     if (keep && keep[b]) return;
-    const double a = (double)v.case_aoa[b] * 0.017453292519943295;
-    const double M = v.case_mach[b];
-    const double u = M * cos(a), w = M * sin(a), p = 1.0 / 1.4;
     const int ld = v.ld;
-    v.U[k] = 1.0;
-    v.U[ld + k] = u;
-    v.U[2 * ld + k] = w;
-    v.U[3 * ld + k] = p / 0.4 + 0.5 * (u * u + w * w);
+#pragma unroll
+    for (int q = 0; q < 4; q++) v.U[q * ld + k] = v.case_Uinf[4 * b + q];
 }
 
 // Training samples from a view's state: inputs (x, y, d, M, AoA) and targets.
@@ -752,16 +746,14 @@ __global__ void k_gather_samples(lskum::MlpView v, const int32_t *pts, int n, fl
     const int ld = v.ld;
     const double rho = v.U[k], u = v.U[ld + k] / rho, w = v.U[2 * ld + k] / rho;
     const double p = 0.4 * (v.U[3 * ld + k] - 0.5 * rho * (u * u + w * w));
-    const double a = (double)v.case_aoa[b] * 0.017453292519943295;
-    const double M = v.case_mach[b];
     in5[(size_t)i * 5] = v.x[k];
     in5[(size_t)i * 5 + 1] = v.y[k];
     in5[(size_t)i * 5 + 2] = v.dwall[k];
     in5[(size_t)i * 5 + 3] = v.case_mach[b];
     in5[(size_t)i * 5 + 4] = v.case_aoa[b];
     tgt[(size_t)i * 4] = (float)log(rho);
-    tgt[(size_t)i * 4 + 1] = (float)(u - M * cos(a));
-    tgt[(size_t)i * 4 + 2] = (float)(w - M * sin(a));
+    tgt[(size_t)i * 4 + 1] = (float)(u - v.case_uv[2 * b]);
+    tgt[(size_t)i * 4 + 2] = (float)(w - v.case_uv[2 * b + 1]);
     tgt[(size_t)i * 4 + 3] = (float)log(p * 1.4);
 }
 

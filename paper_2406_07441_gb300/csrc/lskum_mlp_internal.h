@@ -17,7 +17,9 @@ struct MlpView {
     const float *x, *y, *dwall;    // [ld] coordinates and distance to the case's wall polygon
     const uint8_t *flag;           // [ld]
     const int32_t *case_of;        // [ld]
-    const float *case_mach, *case_aoa;  // [n_cases] (AoA in degrees)
+    const float *case_mach, *case_aoa;  // [n_cases] (AoA in degrees), network inputs
+    const double *case_Uinf;       // [n_cases][4] conserved free stream, bitwise the context's own
+    const double *case_uv;         // [n_cases][2] free-stream velocity (u_inf, v_inf)
     double *U;                     // [4][ld] conserved state of the current state set
     cudaStream_t stream;
 };

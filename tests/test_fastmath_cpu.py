@@ -25,9 +25,14 @@ def _consts():
         return [float.fromhex(t) for t in re.findall(r"-?0x[0-9a-f.]+p[-+]?\d+", body)]
 
     deg = int(re.search(r"kErfcxDeg = (\d+);", s).group(1))
-    ecx = np.array(array("kErfcxHalf")).reshape(5, deg + 1)
+    nI = int(re.search(r"kErfcxIntervals = (\d+);", s).group(1))
+    ecx = np.array(array("kErfcxHalf")).reshape(nI, deg + 1)
+    bounds = [int(t, 16) for t in re.findall(r"ha >= (0x[0-9a-f]{8})",
+                                              re.search(r"int erfcx_interval\(int ha\).*?\}", s, re.S).group(0))]
+    assert len(bounds) == nI - 1
     return dict(inv=scalar("kExpInvLn2_64"), hi=scalar("kExpLn2_64Hi"), lo=scalar("kExpLn2_64Lo"),
-                tab=array("kExpTable"), sc=array("kErfcxScale"), off=array("kErfcxOffset"), ecx=ecx, deg=deg)
+                tab=array("kExpTable"), sc=array("kErfcxScale"), off=array("kErfcxOffset"), ecx=ecx, deg=deg,
+                bounds=bounds)
 
 
 C = _consts()
@@ -73,7 +78,7 @@ def exp_t(x):
 def split_E(S):
     a = min(abs(S), 9.0)
     ha = hi_word(a)
-    iv = int(ha >= 0x3fe80000) + int(ha >= 0x3ffc0000) + int(ha >= 0x400a0000) + int(ha >= 0x40160000)
+    iv = sum(int(ha >= b) for b in C["bounds"])
     t = fma(a, C["sc"][iv], C["off"][iv])
     c = C["ecx"][iv]
     p = float(c[C["deg"]])
