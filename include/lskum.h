@@ -153,6 +153,19 @@ lskum_status lskum_get_case_forces(lskum_ctx *ctx, int32_t cs, double *cl, doubl
 lskum_status lskum_get_case_info(lskum_ctx *ctx, int32_t cs, int32_t *first_point, int32_t *n_points, int32_t *iters,
                                  int32_t *stopped, int32_t *status, int32_t *bad_point);
 
+/* Device-pointer variants (no counterpart in the paper; for callers that keep
+ * the state in device memory, e.g. torch tensors' data_ptr()):
+ *   lskum_get_field_dev: like lskum_get_field into out_dev (device, caller
+ *     order, same shapes), asynchronous: ordered after the work on
+ *     cuda_stream, and cuda_stream is ordered after the copy (NULL = the
+ *     legacy default stream).
+ *   lskum_set_conserved_dev: like lskum_set_conserved from U_dev (device,
+ *     f64[N][4], caller order, read after the work on cuda_stream); returns
+ *     when the state is set, with cuda_stream ordered after it.
+ * Errors as the host versions. */
+lskum_status lskum_get_field_dev(lskum_ctx *ctx, int32_t field, double *out_dev, void *cuda_stream);
+lskum_status lskum_set_conserved_dev(lskum_ctx *ctx, const double *U_dev, void *cuda_stream);
+
 /* Replace the state by primitive fields (f64[N] each, caller order); the wall
  * projection is applied and the residual history is cleared.
  * Errors: LSKUM_ERR_ARG (NULL), LSKUM_ERR_NONPOSITIVE (rho or p <= 0 or not

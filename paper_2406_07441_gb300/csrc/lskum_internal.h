@@ -147,5 +147,9 @@ cudaError_t launch_phase(const Dev &d, const Launch &L, int cur, int phase, int 
                          const int32_t *lvl_act_end, const int32_t *lvl_end, cudaStream_t s);
 cudaError_t launch_init_state(const Dev &d, int cur, cudaStream_t s);
 cudaError_t launch_reset_ctrl(Ctrl *c, cudaStream_t s);
+// Device-side reordering between the internal and the caller's point order.
+cudaError_t launch_to_caller(const double *src, const float *srcf, int comps, bool aos, int ld, int n,
+                             const int32_t *inv, double *out, cudaStream_t s);
+cudaError_t launch_from_caller(const double *in, int ld, int n, const int32_t *inv, double *U, cudaStream_t s);
 
 }  // namespace lskum

@@ -913,6 +913,49 @@ cudaError_t launch_init_state(const Dev &d, int cur, cudaStream_t s)
     return cudaGetLastError();
 }
 
+namespace {
+
+// Internal order (structure of arrays [c][ld], or [ld][4] with aos; FP64 or
+// FP32) -> caller order [p][comps] on the device.
+__global__ void k_to_caller(const double *src, const float *srcf, int comps, bool aos, int ld, int n,
+                            const int32_t *inv, double *out)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int k = inv[p];
+    for (int c = 0; c < comps; c++) {
+        const size_t i = aos ? (size_t)4 * k + c : (size_t)c * ld + k;
+        out[(size_t)comps * p + c] = srcf ? (double)srcf[i] : src[i];
+    }
+}
+
+// Caller order [p][4] -> internal structure of arrays [c][ld].
+__global__ void k_from_caller(const double *in, int ld, int n, const int32_t *inv, double *U)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int k = inv[p];
+#pragma unroll
+    for (int c = 0; c < 4; c++) U[(size_t)c * ld + k] = in[(size_t)4 * p + c];
+}
+
+}  // namespace
+
+cudaError_t launch_to_caller(const double *src, const float *srcf, int comps, bool aos, int ld, int n,
+                             const int32_t *inv, double *out, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_to_caller<<<(n + 255) / 256, 256, 0, s>>>(src, srcf, comps, aos, ld, n, inv, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_from_caller(const double *in, int ld, int n, const int32_t *inv, double *U, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_from_caller<<<(n + 255) / 256, 256, 0, s>>>(in, ld, n, inv, U);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_reset_ctrl(Ctrl *c, cudaStream_t s)
 {
     k_reset_ctrl<<<1, 1, 0, s>>>(c);

@@ -72,6 +72,8 @@ def load():
     L.lskum_get_case_forces.argtypes = [vp, i32, P(d), P(d)]
     L.lskum_get_case_info.argtypes = [vp, i32, P(i32), P(i32), P(i32), P(i32), P(i32), P(i32)]
     L.lskum_get_wall_distance.argtypes = [vp, vp]
+    L.lskum_get_field_dev.argtypes = [vp, i32, vp, vp]
+    L.lskum_set_conserved_dev.argtypes = [vp, vp, vp]
     L.lskum_set_start_iters.argtypes = [vp, i32]
     L.lskum_set_launch_shape.argtypes = [vp, i32, i32]
     u64 = C.c_uint64
@@ -101,7 +103,7 @@ def load():
               "lskum_get_state", "lskum_get_field", "lskum_get_residuals", "lskum_get_forces", "lskum_get_order",
               "lskum_get_info", "lskum_time_phases", "lskum_density_norm_noalloc", "lskum_batch_create",
               "lskum_get_case_residuals", "lskum_get_case_forces", "lskum_get_case_info", "lskum_autotune",
-              "lskum_get_wall_distance", "lskum_set_start_iters", "lskum_set_launch_shape", "lskum_mlp_create", "lskum_mlp_get_params",
+              "lskum_get_wall_distance", "lskum_set_start_iters", "lskum_get_field_dev", "lskum_set_conserved_dev", "lskum_set_launch_shape", "lskum_mlp_create", "lskum_mlp_get_params",
               "lskum_mlp_set_params", "lskum_mlp_features", "lskum_mlp_forward", "lskum_mlp_loss_grads",
               "lskum_mlp_adam", "lskum_mlp_add_samples", "lskum_mlp_time_forward", "lskum_mlp_n_samples", "lskum_mlp_train",
               "lskum_mlp_predict"):
@@ -205,6 +207,14 @@ class Solver:
     def set_conserved(self, U):
         U = np.ascontiguousarray(U, np.float64).reshape(self.n, 4)
         self._check(load().lskum_set_conserved(self._h, _p(U)))
+
+    def field_dev(self, which, out_ptr, stream=None):
+        """Copy a field into device memory at out_ptr (caller order), ordered on `stream`."""
+        self._check(load().lskum_get_field_dev(self._h, int(which), C.c_void_p(out_ptr), C.c_void_p(stream)))
+
+    def set_conserved_dev(self, U_ptr, stream=None):
+        """Set the conserved state from device memory at U_ptr ([N][4], caller order)."""
+        self._check(load().lskum_set_conserved_dev(self._h, C.c_void_p(U_ptr), C.c_void_p(stream)))
 
     def get_state(self):
         out = [np.empty(self.n) for _ in range(4)]

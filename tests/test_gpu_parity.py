@@ -250,3 +250,32 @@ def test_config3_full_size_fp64_and_mixed():
             assert e["R"] < 1e-6 and e["hist"] < 1e-6
             assert e["dUs"] < 1e-5 and e["dU"] < 1e-5 and e["U"] < 1e-6
         del s
+
+
+def test_device_pointer_variants_equal_the_host_ones():
+    """lskum_get_field_dev / lskum_set_conserved_dev on torch CUDA tensors give
+    bit for bit what the host calls give, FP64 and FP32-sweep contexts."""
+    torch = pytest.importorskip("torch")
+    lk = _lskum()
+    c = cached_cloud("jit64x32", lambda: cg.naca0012_jittered(64, 32, seed=12))
+    for prec in (0, 1):
+        s = lk.Solver(c, 0.6, 1.5, first_order_iters=2, precision=prec)
+        assert s.run(4) == 4
+        st = torch.cuda.Stream()
+        for f in range(8):
+            shape = (c.n,) if f == lk.FIELD_D else (c.n, 4)
+            t = torch.full(shape, float("nan"), dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            s.field_dev(f, t.data_ptr(), st.cuda_stream)
+            st.synchronize()
+            assert np.array_equal(t.cpu().numpy(), s.field(f)), f
+        U = s.field(lk.FIELD_U)
+        s2 = lk.Solver(c, 0.6, 1.5, first_order_iters=2, precision=prec)
+        s3 = lk.Solver(c, 0.6, 1.5, first_order_iters=2, precision=prec)
+        s2.set_conserved(U)
+        Ud = torch.from_numpy(U).cuda()
+        torch.cuda.synchronize()
+        s3.set_conserved_dev(Ud.data_ptr(), None)
+        assert np.array_equal(s2.field(lk.FIELD_U), s3.field(lk.FIELD_U))
+        assert s2.run(3) == 3 and s3.run(3) == 3
+        assert np.array_equal(s2.field(lk.FIELD_U), s3.field(lk.FIELD_U))
