@@ -165,32 +165,49 @@ __device__ __forceinline__ PrimT<T> load_prim(const T *__restrict__ pr, int i)
 // Exact product A_d^sg(U) dl by forward-mode differentiation of
 // U -> (rho, u, v, p) -> (beta, S, A, B) -> G_d^sg.  S, A = (1 + sg erf S)/2,
 // exp(-S^2) and B of the state are inputs (precomputed per point for d = x, y).
+// The direction-independent part of the tangent: derivatives of the
+// primitive quantities along dl (shared by a neighbour's x and y split
+// sub-stencils, computed once per neighbour).
 template <typename T>
-__device__ __forceinline__ void jvp_exact(const PrimT<T> &P, T dx, T dy, T sg, T S, T A, T eS, T B, const T dl[4],
-                                          T out[4])
+struct JvpBase {
+    T drho, du, dv, dk, dp, dsb;
+};
+
+template <typename T>
+__device__ __forceinline__ JvpBase<T> jvp_base(const PrimT<T> &P, const T dl[4])
 {
-    const T drho = dl[0];
-    const T du = (dl[1] - P.u * drho) * P.irho;
-    const T dv = (dl[2] - P.v * drho) * P.irho;
-    const T dq2 = T(2.0) * (P.u * du + P.v * dv);
-    const T dk = T(0.5) * (drho * P.q2 + P.rho * dq2);  // d(rho |u|^2 / 2)
-    const T dp = T(kGm1) * (dl[3] - dk);
-    const T dbeta = (drho - T(2.0) * P.beta * dp) * P.i2p;
+    JvpBase<T> b;
+    b.drho = dl[0];
+    b.du = (dl[1] - P.u * b.drho) * P.irho;
+    b.dv = (dl[2] - P.v * b.drho) * P.irho;
+    const T dq2 = T(2.0) * (P.u * b.du + P.v * b.dv);
+    b.dk = T(0.5) * (b.drho * P.q2 + P.rho * dq2);  // d(rho |u|^2 / 2)
+    b.dp = T(kGm1) * (dl[3] - b.dk);
+    const T dbeta = (b.drho - T(2.0) * P.beta * b.dp) * P.i2p;
+    b.dsb = T(0.5) * dbeta * P.isb;
+    return b;
+}
+
+// Tangent of the split flux in direction (dx, dy) with sign sg, given the
+// primal S, A, exp(-S^2), B of that direction.
+template <typename T>
+__device__ __forceinline__ void jvp_dir(const PrimT<T> &P, const JvpBase<T> &b, T dx, T dy, T sg, T S, T A, T eS,
+                                        T B, T out[4])
+{
     const T ud = P.u * dx + P.v * dy;
-    const T dud = du * dx + dv * dy;
-    const T dsb = T(0.5) * dbeta * P.isb;
-    const T dS = dud * P.sb + ud * dsb;
+    const T dud = b.du * dx + b.dv * dy;
+    const T dS = dud * P.sb + ud * b.dsb;
     const T dA = sg * eS * dS * T(kInvSqrtPi);
-    const T dB = -B * (T(2.0) * S * dS + dsb * P.isb);
+    const T dB = -B * (T(2.0) * S * dS + b.dsb * P.isb);
     const T M1 = ud * A + sg * B;
     const T dM1 = dud * A + ud * dA + sg * dB;
-    const T de1 = T(3.5) * dp + dk;
-    const T de2 = T(3.0) * dp + dk;
-    const T drm = drho * M1 + P.rho * dM1;  // d(rho M1)
+    const T de1 = T(3.5) * b.dp + b.dk;
+    const T de2 = T(3.0) * b.dp + b.dk;
+    const T drm = b.drho * M1 + P.rho * dM1;  // d(rho M1)
     const T rm = P.rho * M1;
     out[0] = drm;
-    out[1] = drm * P.u + rm * du + (dp * A + P.p * dA) * dx;
-    out[2] = drm * P.v + rm * dv + (dp * A + P.p * dA) * dy;
+    out[1] = drm * P.u + rm * b.du + (b.dp * A + P.p * dA) * dx;
+    out[2] = drm * P.v + rm * b.dv + (b.dp * A + P.p * dA) * dy;
     out[3] = (dud * P.e1 + ud * de1) * A + ud * P.e1 * dA + sg * (de2 * B + P.e2 * dB);
 }
 
@@ -563,6 +580,7 @@ __global__ void __launch_bounds__(256) k_sweep(Dev d, StateSet st, int lb, int l
             // interior frame: d = (1,0) or (0,1), S, A, exp(-S^2), B precomputed per point
             const PrimT<T> P = load_prim(pr, i);
             const T *rec = pr + (size_t)i * kPrimStride;
+            const JvpBase<T> jb = jvp_base(P, dl);
 #pragma unroll
             for (int s = 0; s < 2; s++) {
                 const int m = s == 0 ? (mb & 3) : (mb >> 2);
@@ -570,8 +588,8 @@ __global__ void __launch_bounds__(256) k_sweep(Dev d, StateSet st, int lb, int l
                 const T sg = (m & 1) ? T(1) : T(-1);
                 const int f = s == 0 ? P_SX : P_SY;
                 T J[4];
-                jvp_exact(P, s == 0 ? T(1) : T(0), s == 0 ? T(0) : T(1), sg, rec[f], rec[(m & 1) ? f + 1 : f + 2],
-                          rec[f + 3], rec[f + 4], dl, J);
+                jvp_dir(P, jb, s == 0 ? T(1) : T(0), s == 0 ? T(0) : T(1), sg, rec[f], rec[(m & 1) ? f + 1 : f + 2],
+                        rec[f + 3], rec[f + 4], J);
                 const T w = s == 0 ? w1s[e] : w2s[e];
 #pragma unroll
                 for (int c = 0; c < 4; c++) acc[c] = fma(w, J[c], acc[c]);
@@ -583,8 +601,10 @@ __global__ void __launch_bounds__(256) k_sweep(Dev d, StateSet st, int lb, int l
             for (int c = 0; c < 4; c++) dld[c] = (double)dl[c];
             double Ui[4], Up[4];
             PrimU P;
+            JvpBase<double> jb{};
             if (JVP == 0) {
                 P = load_prim(st.prim, i);
+                jb = jvp_base(P, dld);
             } else {
 #pragma unroll
                 for (int c = 0; c < 4; c++) {
@@ -603,7 +623,7 @@ __global__ void __launch_bounds__(256) k_sweep(Dev d, StateSet st, int lb, int l
                     const double S = (P.u * ddx + P.v * ddy) * P.sb;
                     double A, eS;
                     split_A(Tb, S, sg, A, eS);
-                    jvp_exact(P, ddx, ddy, sg, S, A, eS, eS * kInv2SqrtPi * P.isb, dld, J);
+                    jvp_dir(P, jb, ddx, ddy, sg, S, A, eS, eS * kInv2SqrtPi * P.isb, J);
                 } else {
                     double G1[4], G0[4];
                     flux_cons(Tb, Up, ddx, ddy, sg, G1);
