@@ -70,6 +70,10 @@ def lib():
         L.o_run.argtypes = [P(_Cloud), vp, vp, d, d, i32, i32, i32, i32, d, i32,
                             vp, vp, vp, vp, vp, vp, vp, vp, vp, P(d), P(i32)]
         L.o_run.restype = i32
+        L.o_explicit_step.argtypes = [P(_Cloud), vp, d, vp, vp, vp]
+        L.o_run_explicit.argtypes = [P(_Cloud), d, d, i32, i32, i32, d, i32, vp, vp, vp, vp, vp, vp, vp, vp,
+                                     P(d), P(i32)]
+        L.o_run_explicit.restype = i32
         _lib = L
     return _lib
 
@@ -235,6 +239,30 @@ class Oracle:
         cl, cd = C.c_double(), C.c_double()
         lib().o_forces(C.byref(self.c), _p(U), mach, aoa_deg, C.byref(cl), C.byref(cd))
         return cl.value, cd.value
+
+    def explicit_step(self, U, R, cfl):
+        """The explicit (forward Euler) increment of the residual R at state U."""
+        U = _f64(U, (self.n, 4))
+        R = _f64(R, (self.n, 4))
+        D = np.zeros(self.n)
+        dU = np.zeros((self.n, 4))
+        lib().o_explicit_step(C.byref(self.c), _p(U), float(cfl), _p(R), _p(D), _p(dU))
+        return dU, D
+
+    def run_explicit(self, U, iters, cfl=0.5, K=3, target=0.0, ramp=0.0, n0=0, hist0=0.0, first_order=0):
+        """Explicit solver: as run() with the forward Euler step in place of the sweeps."""
+        n = self.n
+        U = _f64(U, (n, 4)).copy()
+        w = {k: np.zeros((n, 4)) for k in ("q", "qx", "qy", "R", "dU")}
+        D = np.zeros(n)
+        hist = np.zeros(max(1, iters))
+        h0 = C.c_double(hist0)
+        done = C.c_int32(0)
+        st = lib().o_run_explicit(C.byref(self.c), float(cfl), float(ramp), int(K), int(first_order), int(iters),
+                                  float(target), int(n0), _p(U), _p(w["q"]), _p(w["qx"]), _p(w["qy"]), _p(w["R"]),
+                                  _p(D), _p(w["dU"]), _p(hist), C.byref(h0), C.byref(done))
+        return dict(U=U, hist=hist[:done.value], hist0=h0.value, done=done.value, status=int(st), D=D,
+                    dUs=np.zeros((n, 4)), **w)
 
     def run(self, U, iters, cfl=100.0, K=3, jvp=JVP_EXACT, target=0.0, ramp=0.0, n0=0, hist0=0.0, first_order=0):
         """Alg. 1 for up to `iters` iterations.  Returns a dict with the new state,

@@ -699,6 +699,42 @@ double o_cfl_at(double cfl, double ramp, int32_t n)
 }
 
 /*
+ * Explicit q-LSKUM step (the paper's solver (e), Sec. 5: the same residual,
+ * no implicit operator): forward Euler in pseudo-time with the local time
+ * step of the implicit scheme, dt_0 = CFL min_i |r_i - r_0| / (|u_0| + a_0):
+ * dU_0 = -dt_0 R_0 at wall and interior points, with the normal momentum
+ * removed at wall points (reading R4, as for the implicit increments); outer
+ * points keep dU = 0.  D[p] receives 1/dt_0 (1 at outer points).
+ */
+void o_explicit_step(const o_cloud *c, const double *U, double cfl, const double *R, double *D, double *dU)
+{
+    for (int32_t p = 0; p < c->n; p++) {
+        for (int k = 0; k < 4; k++) dU[4 * p + k] = 0.0;
+        if (c->flag[p] == PT_OUTER) {
+            D[p] = 1.0;
+            continue;
+        }
+        double dmin = INFINITY;
+        for (int32_t e = c->off[p]; e < c->off[p + 1]; e++) {
+            int32_t i = c->idx[e];
+            double dx = c->x[i] - c->x[p], dy = c->y[i] - c->y[p];
+            double dist = sqrt(dx * dx + dy * dy);
+            if (dist < dmin) dmin = dist;
+        }
+        double rho, u, v, pr;
+        o_cons_to_prim(&U[4 * p], &rho, &u, &v, &pr);
+        double dt = cfl * dmin / (sqrt(u * u + v * v) + sqrt(GAMMA * pr / rho));
+        D[p] = 1.0 / dt;
+        for (int k = 0; k < 4; k++) dU[4 * p + k] = -dt * R[4 * p + k];
+        if (c->flag[p] == PT_WALL) {
+            double mn = dU[4 * p + 1] * c->nx[p] + dU[4 * p + 2] * c->ny[p];
+            dU[4 * p + 1] -= mn * c->nx[p];
+            dU[4 * p + 2] -= mn * c->ny[p];
+        }
+    }
+}
+
+/*
  * Run up to `iters` iterations from the state U (in/out, [4N]).  Iteration n
  * (counted from n0 + 1) computes q-derivatives, R(U^{n-1}) (first order while
  * n <= first_order) and its norm hist[n-1], sweeps, and
@@ -726,6 +762,36 @@ int32_t o_run(const o_cloud *c, const int32_t *order, const int32_t *rank,
         hist[it] = o_residual_norm(c, R);
         if (!(*hist0 > 0.0)) *hist0 = hist[it];
         o_sweeps(c, order, rank, U, R, D, jvp, dUs, dU);
+        int32_t bad = o_update(c, U, dU, q);
+        *done = it + 1;
+        if (bad >= 0) {
+            free(zero);
+            return -(1 + bad);
+        }
+        if (hist[it] / *hist0 <= target) break;
+    }
+    free(zero);
+    return 0;
+}
+
+/* As o_run with the explicit step in place of the LU-SGS sweeps (dUs stays 0). */
+int32_t o_run_explicit(const o_cloud *c, double cfl, double ramp, int32_t K, int32_t first_order,
+                       int32_t iters, double target, int32_t n0,
+                       double *U, double *q, double *qx, double *qy, double *R, double *D,
+                       double *dU, double *hist, double *hist0, int32_t *done)
+{
+    *done = 0;
+    double *zero = calloc(4 * (size_t)c->n, sizeof(double));
+    o_q_from_state(c, U, q);
+    for (int32_t it = 0; it < iters; it++) {
+        int32_t n = n0 + it + 1;
+        double cfl_n = o_cfl_at(cfl, ramp, n);
+        o_q_gradients(c, q, K, qx, qy);
+        if (n <= first_order) o_residual(c, q, zero, zero, U, cfl_n, R, D);
+        else o_residual(c, q, qx, qy, U, cfl_n, R, D);
+        hist[it] = o_residual_norm(c, R);
+        if (!(*hist0 > 0.0)) *hist0 = hist[it];
+        o_explicit_step(c, U, cfl_n, R, D, dU);
         int32_t bad = o_update(c, U, dU, q);
         *done = it + 1;
         if (bad >= 0) {

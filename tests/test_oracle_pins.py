@@ -511,3 +511,58 @@ def test_symmetric_aerofoil_symmetric_state_has_no_lift():
         U[p] = O.prim_to_cons(r, u, v, pp)
     cl, cd = o.forces(U, 0.5, 0.0)
     assert abs(cl) < 1e-14
+
+
+def _perturbed_state(o, c, mach=0.5, aoa=1.0, amp=0.02):
+    U = o.initial_state(mach, aoa)
+    rng = np.random.default_rng(17)
+    act = c.flag != 2
+    U[act, 0] *= 1 + amp * rng.uniform(-1, 1, act.sum())
+    U[act, 3] *= 1 + amp * rng.uniform(-1, 1, act.sum())
+    return U
+
+
+def test_implicit_increment_tends_to_the_explicit_step_as_cfl_vanishes():
+    """As the pseudo-time step shrinks, the LU-SGS system's diagonal 1/dt
+    dominates and its increment tends to the forward Euler step -dt R: their
+    difference is O(dt^2), so relative to dt R it halves with the CFL."""
+    c = cg.naca0012_block(24, 10)
+    o = O.Oracle(c)
+    U = _perturbed_state(o, c)
+    q = o.q_from_state(U)
+    z = np.zeros((c.n, 4))
+    errs = []
+    for cfl in (2e-3, 1e-3, 5e-4):
+        R, D = o.residual(q, z, z, U, cfl)
+        _, dU = o.sweeps(U, R, D)
+        dE, _ = o.explicit_step(U, R, cfl)
+        errs.append(np.max(np.abs(dU - dE)) / np.max(np.abs(dE)))
+    assert errs[0] < 1e-2
+    for a, b in zip(errs, errs[1:]):
+        assert 1.7 < a / b < 2.3, errs
+
+
+def test_explicit_solver_is_forward_euler():
+    """Two explicit steps at CFL c/2 and one at CFL c differ by O(dt^2)
+    (first-order residual, so every step is U - dt R(U)): the difference
+    quarters when the CFL halves; and the increment is -dt R with the
+    normal momentum removed at wall points."""
+    c = cg.naca0012_block(24, 10)
+    o = O.Oracle(c)
+    U = _perturbed_state(o, c)
+    diffs = []
+    for cfl in (0.02, 0.01, 0.005):
+        one = o.run_explicit(U, 1, cfl=cfl, K=0, first_order=10)["U"]
+        two = o.run_explicit(U, 2, cfl=cfl / 2, K=0, first_order=10)["U"]
+        diffs.append(np.max(np.abs(one - two)))
+    for a, b in zip(diffs, diffs[1:]):
+        assert 3.4 < a / b < 4.6, diffs
+    q = o.q_from_state(U)
+    z = np.zeros((c.n, 4))
+    R, _ = o.residual(q, z, z, U, 0.3)
+    dE, D = o.explicit_step(U, R, 0.3)
+    wall = c.flag == 1
+    assert np.max(np.abs(dE[wall, 1] * c.nx[wall] + dE[wall, 2] * c.ny[wall])) < 1e-15
+    inner = c.flag == 0
+    assert np.allclose(dE[inner], -R[inner] / D[inner, None], rtol=0, atol=1e-15)
+    assert np.all(dE[c.flag == 2] == 0.0)
