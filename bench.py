@@ -163,8 +163,10 @@ def run_ours(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     cloud = cg.build_workload(WORKLOAD)
     n = cloud.n
-    s = lskum.Solver(cloud, 0.85, 1.0, cfl=100.0, inner_iters=3, jvp=lskum.JVP_EXACT, first_order_iters=START,
-                     precision=args.precision)
+    explicit = args.scheme == "explicit"
+    cfl = 0.3 if explicit else 100.0
+    s = lskum.Solver(cloud, 0.85, 1.0, cfl=cfl, inner_iters=3, jvp=lskum.JVP_EXACT, first_order_iters=START,
+                     precision=args.precision, scheme=lskum.SCHEME_EXPLICIT if explicit else lskum.SCHEME_LUSGS)
     info = s.info()
     nslots = int(np.count_nonzero(_memberships(cloud)))
     # first-order start-up, then warm-up iterations (untimed)
@@ -233,7 +235,9 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f64+f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "points": n, "neighbour_slots": int(cloud.nnz),
                    "precision": "fp64" if args.precision == 0 else "fp32 sweeps, fp64 residual/update",
-                   "mach": 0.85, "aoa_deg": 1.0, "cfl": 100.0, "inner_iters": 3, "jvp": "exact-AD",
+                   "mach": 0.85, "aoa_deg": 1.0, "cfl": cfl, "inner_iters": 3,
+                   "scheme": "explicit (forward Euler, no sweeps)" if explicit else "implicit LU-SGS",
+                   "jvp": "exact-AD",
                    "order": f"second (timed steps follow {START} untimed first-order start-up iterations)",
                    "colours": info["n_colours"],
                    "launch_shape": {"threads_per_point": tpp, "sweep_lanes_per_point": lanes,
@@ -581,6 +585,8 @@ def main():
     ap.add_argument("--workload", choices=[WORKLOAD, BATCH_WORKLOAD, WARM_WORKLOAD], default=WORKLOAD)
     ap.add_argument("--train-solves", type=int, default=512, help="warm-start workload: training solves")
     ap.add_argument("--test-conditions", type=int, default=16, help="warm-start workload: unseen conditions")
+    ap.add_argument("--scheme", choices=["lusgs", "explicit"], default="lusgs",
+                    help="default workload: the implicit LU-SGS solver or the paper's explicit solver")
     ap.add_argument("--launch-shape", default="",
                     help="T,L: threads per point and sweep lanes per point instead of autotuning")
     args = ap.parse_args()

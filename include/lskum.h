@@ -100,10 +100,15 @@ typedef struct {
  *   first_order_iters  iterations n <= first_order_iters (counted since the
  *                    last set_state / create) use the first-order residual
  *                    (q~ = q: no defect correction); a start-up aid, >= 0
+ *   scheme           LSKUM_SCHEME_LUSGS (0, the implicit solver) or
+ *                    LSKUM_SCHEME_EXPLICIT (1, the paper's explicit solver:
+ *                    forward Euler with the same local time step, no sweeps;
+ *                    stable for cfl <= ~0.3; precision must be 0)
  */
+enum { LSKUM_SCHEME_LUSGS = 0, LSKUM_SCHEME_EXPLICIT = 1 };
 typedef struct {
     double mach, aoa_deg, cfl, cfl_ramp_iters;
-    int32_t inner_iters, jvp, precision, first_order_iters;
+    int32_t inner_iters, jvp, precision, first_order_iters, scheme;
 } lskum_opts;
 
 /*

@@ -214,13 +214,15 @@ static bool opts_valid(const lskum_opts *o)
     return (o->cfl > 0.0) && std::isfinite(o->cfl) && std::isfinite(o->mach) && std::isfinite(o->aoa_deg) &&
            (o->cfl_ramp_iters >= 0.0) && o->inner_iters >= 0 && o->inner_iters <= 64 &&
            (o->jvp == LSKUM_JVP_EXACT || o->jvp == LSKUM_JVP_INCREMENT) && (o->precision == 0 || o->precision == 1) &&
-           o->first_order_iters >= 0;
+           o->first_order_iters >= 0 &&
+           (o->scheme == LSKUM_SCHEME_LUSGS || (o->scheme == LSKUM_SCHEME_EXPLICIT && o->precision == 0));
 }
 
 static bool opts_shared_equal(const lskum_opts *a, const lskum_opts *b)
 {
     return a->cfl == b->cfl && a->cfl_ramp_iters == b->cfl_ramp_iters && a->inner_iters == b->inner_iters &&
-           a->jvp == b->jvp && a->precision == b->precision && a->first_order_iters == b->first_order_iters;
+           a->jvp == b->jvp && a->precision == b->precision && a->first_order_iters == b->first_order_iters &&
+           a->scheme == b->scheme;
 }
 
 // Validate one case's cloud (indices local to the case).
@@ -726,6 +728,7 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
     d.K = c->opts.inner_iters;
     d.first_order = c->opts.first_order_iters;
     d.jvp = c->opts.jvp;
+    d.scheme = c->opts.scheme;
     auto up = [&](void *dst, const void *src, size_t bytes) {
         if (e == cudaSuccess) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
     };

@@ -424,6 +424,10 @@ __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const doub
         const double u = pr[P_U], v = pr[P_V];
         const double a = sqrt(1.4 * pr[P_P] * pr[P_IRHO]);
         const double dt = cfl * d.geo[G_DMIN * ld + k] / (sqrt(u * u + v * v) + a);
+        if (d.scheme == 1) {  // explicit: D = 1/dt, the step is -R/D
+            d.D[k] = 1.0 / dt;
+            return;
+        }
         double Dp = 1.0 / dt, Ddom = 0.0;
         const double u1 = u * e1x + v * e1y, u2 = u * e2x + v * e2y;
         const double r0 = fmax(u1 + a, 0.0), r1 = fmax(a - u1, 0.0);
@@ -761,6 +765,31 @@ __global__ void __launch_bounds__(256) k_update(Dev d, int cur)
     }
 }
 
+// Explicit scheme (the paper's solver (e)): dU = -dt R = -R / D at wall and
+// interior points, normal momentum removed at wall points; outer points 0.
+__global__ void __launch_bounds__(256) k_explicit(Dev d)
+{
+    if (halted(d.ctrl)) return;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= d.n) return;
+    const int ld = d.ld;
+    double w[4] = {0.0, 0.0, 0.0, 0.0};
+    const int fl = d.flag[k];
+    if (fl != kOuter && !frozen(d, k)) {
+        const double dt = 1.0 / d.D[k];
+#pragma unroll
+        for (int c = 0; c < 4; c++) w[c] = -dt * d.R[c * ld + k];
+        if (fl == kWall) {
+            const double nx = d.wnx[k], ny = d.wny[k];
+            const double mn = w[1] * nx + w[2] * ny;
+            w[1] -= mn * nx;
+            w[2] -= mn * ny;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; c++) d.dU[4 * k + c] = w[c];
+}
+
 // Batches: undo this iteration's update of the cases that failed in it (the
 // new state set gets the old set's values), so a failed case keeps its last
 // good state.
@@ -894,6 +923,13 @@ cudaError_t enqueue_phase(const Dev &d, const Launch &L, int cur, int ph, int n_
         return cudaGetLastError();
     case 3:
     case 4:
+        if (d.scheme == 1) {  // explicit: one step kernel instead of the two sweeps
+            if (ph == 3) {
+                k_explicit<<<(d.n + 255) / 256, 256, 0, s>>>(d);
+                (*launches)++;
+            }
+            return cudaGetLastError();
+        }
         if (d.jvp == 0) return enqueue_sweeps<0>(d, L, cur, n_levels, lvl_beg, lvl_act_end, s, launches, ph == 3, ph == 4);
         return enqueue_sweeps<1>(d, L, cur, n_levels, lvl_beg, lvl_act_end, s, launches, ph == 3, ph == 4);
     case 5:

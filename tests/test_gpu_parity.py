@@ -279,3 +279,28 @@ def test_device_pointer_variants_equal_the_host_ones():
         assert np.array_equal(s2.field(lk.FIELD_U), s3.field(lk.FIELD_U))
         assert s2.run(3) == 3 and s3.run(3) == 3
         assert np.array_equal(s2.field(lk.FIELD_U), s3.field(lk.FIELD_U))
+
+
+@pytest.mark.parametrize("name", ["ogrid40x16", "jit64x32"])
+def test_explicit_scheme_matches_oracle(name):
+    """The explicit solver (forward Euler, the implicit scheme's local time
+    step, no sweeps): one iteration's fields and a 40-iteration history."""
+    lk = _lskum()
+    c = cached_cloud(name, CLOUDS[name])
+    o = O.Oracle(c)
+    U0 = o.initial_state(0.5, 1.0)
+    s = lk.Solver(c, 0.5, 1.0, cfl=0.3, inner_iters=2, first_order_iters=10, scheme=lk.SCHEME_EXPLICIT)
+    r = o.run_explicit(U0, 1, cfl=0.3, K=2, first_order=10)
+    assert s.run(1) == 1
+    assert nrel(s.field(lk.FIELD_R), r["R"]) < 1e-10
+    D = s.field(lk.FIELD_D)
+    assert np.max(np.abs(D - r["D"]) / np.abs(r["D"])) < 1e-12
+    assert nrel(s.field(lk.FIELD_DU), r["dU"]) < 1e-10
+    assert nrel(s.field(lk.FIELD_U), r["U"]) < 1e-12
+    s2 = lk.Solver(c, 0.5, 1.0, cfl=0.3, inner_iters=2, first_order_iters=10, scheme=lk.SCHEME_EXPLICIT)
+    r2 = o.run_explicit(U0, 40, cfl=0.3, K=2, first_order=10)
+    assert r2["status"] == 0 and s2.run(40) == 40
+    h = s2.residuals()
+    assert np.max(np.abs(h - r2["hist"]) / r2["hist"]) < 1e-10
+    assert nrel(s2.field(lk.FIELD_U), r2["U"]) < 1e-9
+    assert s2.info()["launches_per_iter"] < lk.Solver(c, 0.5, 1.0).info()["launches_per_iter"]

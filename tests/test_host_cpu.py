@@ -77,7 +77,7 @@ def test_degenerate_split_stencil_is_rejected(lk):
 
 def test_bad_options_are_rejected(lk):
     c = cg.naca0012_block(40, 16)
-    for kw in (dict(cfl=0.0), dict(inner_iters=-1), dict(jvp=5)):
+    for kw in (dict(cfl=0.0), dict(inner_iters=-1), dict(jvp=5), dict(scheme=2), dict(scheme=1, precision=1)):
         with pytest.raises(lk.LskumError) as ei:
             lk.Solver(c, 0.5, 1.0, **kw)
         assert ei.value.status == -1
