@@ -104,11 +104,25 @@ typedef struct {
  *                    LSKUM_SCHEME_EXPLICIT (1, the paper's explicit solver:
  *                    forward Euler with the same local time step, no sweeps;
  *                    stable for cfl <= ~0.3; precision must be 0)
+ *   lusgs            implicit solver's LU-SGS form (Sec. 3):
+ *                    LSKUM_LUSGS_ANANDH (0): the scalar diagonal of the
+ *                    split-flux spectral radii (Eq. 34), with the dominance
+ *                    bound sum_s rho_s sum_i |w_i|;
+ *                    LSKUM_LUSGS_MANISH (1): the revised form of Manish et
+ *                    al.: Jameson's splitting gives D = 1/dt + sum_s
+ *                    (|u_d| + a)|LS_s(1)|/2, and the term S_0 = -1/2 sum_s
+ *                    LS_s(1) A_d(U_0) dU_0 of the previous iteration's
+ *                    increment (exact unsplit Jacobian products) joins the
+ *                    right-hand side as -R - S (the sign the algebra of the
+ *                    split diagonal gives); converges faster at cfl ~ 2-3,
+ *                    diverges at cfl >= ~7.  The lag restarts from dU = 0
+ *                    after every new state.
  */
 enum { LSKUM_SCHEME_LUSGS = 0, LSKUM_SCHEME_EXPLICIT = 1 };
+enum { LSKUM_LUSGS_ANANDH = 0, LSKUM_LUSGS_MANISH = 1 };
 typedef struct {
     double mach, aoa_deg, cfl, cfl_ramp_iters;
-    int32_t inner_iters, jvp, precision, first_order_iters, scheme;
+    int32_t inner_iters, jvp, precision, first_order_iters, scheme, lusgs;
 } lskum_opts;
 
 /*

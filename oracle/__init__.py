@@ -71,6 +71,10 @@ def lib():
                             vp, vp, vp, vp, vp, vp, vp, vp, vp, P(d), P(i32)]
         L.o_run.restype = i32
         L.o_explicit_step.argtypes = [P(_Cloud), vp, d, vp, vp, vp]
+        L.o_manish_terms.argtypes = [P(_Cloud), vp, d, vp, vp, vp]
+        L.o_run_manish.argtypes = [P(_Cloud), vp, vp, d, d, i32, i32, i32, i32, i32, d, i32,
+                                   vp, vp, vp, vp, vp, vp, vp, vp, vp, P(d), P(i32)]
+        L.o_run_manish.restype = i32
         L.o_run_explicit.argtypes = [P(_Cloud), d, d, i32, i32, i32, d, i32, vp, vp, vp, vp, vp, vp, vp, vp,
                                      P(d), P(i32)]
         L.o_run_explicit.restype = i32
@@ -248,6 +252,31 @@ class Oracle:
         dU = np.zeros((self.n, 4))
         lib().o_explicit_step(C.byref(self.c), _p(U), float(cfl), _p(R), _p(D), _p(dU))
         return dU, D
+
+    def manish_terms(self, U, cfl, dU_prev=None):
+        """Diagonal D and lagged term S of the revised LU-SGS of Manish et al."""
+        U = _f64(U, (self.n, 4))
+        D = np.zeros(self.n)
+        S = np.zeros((self.n, 4))
+        prev = None if dU_prev is None else _f64(dU_prev, (self.n, 4))
+        lib().o_manish_terms(C.byref(self.c), _p(U), float(cfl), None if prev is None else _p(prev), _p(D), _p(S))
+        return D, S
+
+    def run_manish(self, U, iters, cfl=100.0, K=3, jvp=JVP_EXACT, sigma=-1, target=0.0, ramp=0.0, n0=0,
+                   hist0=0.0, first_order=0):
+        """The revised LU-SGS of Manish et al.; as run() otherwise."""
+        n = self.n
+        U = _f64(U, (n, 4)).copy()
+        w = {k: np.zeros((n, 4)) for k in ("q", "qx", "qy", "R", "dUs", "dU")}
+        D = np.zeros(n)
+        hist = np.zeros(max(1, iters))
+        h0 = C.c_double(hist0)
+        done = C.c_int32(0)
+        st = lib().o_run_manish(C.byref(self.c), _p(self.order), _p(self.rank), float(cfl), float(ramp), int(K),
+                                int(jvp), int(first_order), int(sigma), int(iters), float(target), int(n0), _p(U),
+                                _p(w["q"]), _p(w["qx"]), _p(w["qy"]), _p(w["R"]), _p(D), _p(w["dUs"]), _p(w["dU"]),
+                                _p(hist), C.byref(h0), C.byref(done))
+        return dict(U=U, hist=hist[:done.value], hist0=h0.value, done=done.value, status=int(st), D=D, **w)
 
     def run_explicit(self, U, iters, cfl=0.5, K=3, target=0.0, ramp=0.0, n0=0, hist0=0.0, first_order=0):
         """Explicit solver: as run() with the forward Euler step in place of the sweeps."""

@@ -699,6 +699,75 @@ double o_cfl_at(double cfl, double ramp, int32_t n)
 }
 
 /*
+ * The revised LU-SGS of Manish et al. (Sec. 3, "+AD" form): Jameson's
+ * splitting A_d(+-) = (A_d +- rho(A_d) I)/2 with rho(A_d) = |u_d| + a turns
+ * the block diagonal into the scalar
+ *   D_0 = 1/dt + sum_s rho(A_dir(s)) |LS_s(1)| / 2
+ * plus the term S_0 = -1/2 sum_s LS_s(1) A_dir(s)(U_0) dU_0, which is
+ * evaluated with the previous iteration's increment (exact unsplit Jacobian
+ * products, here the sum of the exact split ones: G = G+ + G-) and moved to
+ * the right-hand side.  Sub-stencils s and frames as in o_residual (wall:
+ * t+, t-, n-).  With Sprev = NULL, S is not computed.
+ */
+void o_manish_terms(const o_cloud *c, const double *U, double cfl, const double *dUprev, double *D, double *S)
+{
+    for (int32_t p = 0; p < c->n; p++) {
+        for (int k = 0; k < 4; k++) S[4 * p + k] = 0.0;
+        if (c->flag[p] == PT_OUTER) {
+            D[p] = 1.0;
+            continue;
+        }
+        int is_wall = c->flag[p] == PT_WALL;
+        double e1x, e1y, e2x, e2y;
+        frame(c, p, &e1x, &e1y, &e2x, &e2y);
+        double sdd[4] = { 0 }, spp[4] = { 0 }, sdp[4] = { 0 }, sd1[4] = { 0 }, sp1[4] = { 0 };
+        double dmin = INFINITY;
+        for (int32_t e = c->off[p]; e < c->off[p + 1]; e++) {
+            int32_t i = c->idx[e];
+            double dx = c->x[i] - c->x[p], dy = c->y[i] - c->y[p];
+            double dist = sqrt(dx * dx + dy * dy);
+            if (dist < dmin) dmin = dist;
+            double a = dx * e1x + dy * e1y, b = dx * e2x + dy * e2y;
+            int sub[2];
+            int m = members(is_wall, a, b, sub);
+            for (int j = 0; j < m; j++) {
+                double d, dp;
+                sub_offsets(sub[j], a, b, &d, &dp);
+                sdd[sub[j]] += d * d;
+                spp[sub[j]] += dp * dp;
+                sdp[sub[j]] += d * dp;
+                sd1[sub[j]] += d;
+                sp1[sub[j]] += dp;
+            }
+        }
+        double rho, u, v, pr;
+        o_cons_to_prim(&U[4 * p], &rho, &u, &v, &pr);
+        double snd = sqrt(GAMMA * pr / rho);
+        double dt = cfl * dmin / (sqrt(u * u + v * v) + snd);
+        double Dp = 1.0 / dt;
+        double A1[4] = { 0 }, A2[4] = { 0 };
+        if (dUprev) {
+            double jp[4], jm[4];
+            o_split_jvp_exact(&U[4 * p], &dUprev[4 * p], e1x, e1y, +1, jp);
+            o_split_jvp_exact(&U[4 * p], &dUprev[4 * p], e1x, e1y, -1, jm);
+            for (int k = 0; k < 4; k++) A1[k] = jp[k] + jm[k];
+            o_split_jvp_exact(&U[4 * p], &dUprev[4 * p], e2x, e2y, +1, jp);
+            o_split_jvp_exact(&U[4 * p], &dUprev[4 * p], e2x, e2y, -1, jm);
+            for (int k = 0; k < 4; k++) A2[k] = jp[k] + jm[k];
+        }
+        for (int ss = 0; ss < 4; ss++) {
+            if (is_wall && ss == 2) continue;
+            double det = sdd[ss] * spp[ss] - sdp[ss] * sdp[ss];
+            double ls1 = (spp[ss] * sd1[ss] - sdp[ss] * sp1[ss]) / det;
+            double ud = ss < 2 ? u * e1x + v * e1y : u * e2x + v * e2y;
+            Dp += 0.5 * (fabs(ud) + snd) * fabs(ls1);
+            for (int k = 0; k < 4; k++) S[4 * p + k] -= 0.5 * ls1 * (ss < 2 ? A1[k] : A2[k]);
+        }
+        D[p] = Dp;
+    }
+}
+
+/*
  * Explicit q-LSKUM step (the paper's solver (e), Sec. 5: the same residual,
  * no implicit operator): forward Euler in pseudo-time with the local time
  * step of the implicit scheme, dt_0 = CFL min_i |r_i - r_0| / (|u_0| + a_0):
@@ -772,6 +841,54 @@ int32_t o_run(const o_cloud *c, const int32_t *order, const int32_t *rank,
     }
     free(zero);
     return 0;
+}
+
+/*
+ * As o_run with the revised LU-SGS of Manish et al.: D from o_manish_terms
+ * and the right-hand side -R + sigma S(dU of the previous iteration of this
+ * call; zero at its first), sigma = +1 as the paper prints the sweeps, -1 as
+ * the algebra of the split diagonal gives.  Both leave the fixed point R = 0
+ * unchanged.  The history holds the norms of R.
+ */
+int32_t o_run_manish(const o_cloud *c, const int32_t *order, const int32_t *rank,
+                     double cfl, double ramp, int32_t K, int32_t jvp, int32_t first_order, int32_t sigma,
+                     int32_t iters, double target, int32_t n0,
+                     double *U, double *q, double *qx, double *qy, double *R, double *D,
+                     double *dUs, double *dU, double *hist, double *hist0, int32_t *done)
+{
+    *done = 0;
+    size_t n4 = 4 * (size_t)c->n;
+    double *zero = calloc(n4, sizeof(double));
+    double *S = calloc(n4, sizeof(double));
+    double *Reff = calloc(n4, sizeof(double));
+    double *prev = calloc(n4, sizeof(double));
+    o_q_from_state(c, U, q);
+    int32_t status = 0;
+    for (int32_t it = 0; it < iters; it++) {
+        int32_t n = n0 + it + 1;
+        double cfl_n = o_cfl_at(cfl, ramp, n);
+        o_q_gradients(c, q, K, qx, qy);
+        if (n <= first_order) o_residual(c, q, zero, zero, U, cfl_n, R, D);
+        else o_residual(c, q, qx, qy, U, cfl_n, R, D);
+        hist[it] = o_residual_norm(c, R);
+        if (!(*hist0 > 0.0)) *hist0 = hist[it];
+        o_manish_terms(c, U, cfl_n, prev, D, S);
+        for (size_t k = 0; k < n4; k++) Reff[k] = R[k] - (double)sigma * S[k];
+        o_sweeps(c, order, rank, U, Reff, D, jvp, dUs, dU);
+        for (size_t k = 0; k < n4; k++) prev[k] = dU[k];
+        int32_t bad = o_update(c, U, dU, q);
+        *done = it + 1;
+        if (bad >= 0) {
+            status = -(1 + bad);
+            break;
+        }
+        if (hist[it] / *hist0 <= target) break;
+    }
+    free(zero);
+    free(S);
+    free(Reff);
+    free(prev);
+    return status;
 }
 
 /* As o_run with the explicit step in place of the LU-SGS sweeps (dUs stays 0). */

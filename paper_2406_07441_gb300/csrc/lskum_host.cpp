@@ -215,14 +215,15 @@ static bool opts_valid(const lskum_opts *o)
            (o->cfl_ramp_iters >= 0.0) && o->inner_iters >= 0 && o->inner_iters <= 64 &&
            (o->jvp == LSKUM_JVP_EXACT || o->jvp == LSKUM_JVP_INCREMENT) && (o->precision == 0 || o->precision == 1) &&
            o->first_order_iters >= 0 &&
-           (o->scheme == LSKUM_SCHEME_LUSGS || (o->scheme == LSKUM_SCHEME_EXPLICIT && o->precision == 0));
+           (o->scheme == LSKUM_SCHEME_LUSGS || (o->scheme == LSKUM_SCHEME_EXPLICIT && o->precision == 0)) &&
+           (o->lusgs == LSKUM_LUSGS_ANANDH || o->lusgs == LSKUM_LUSGS_MANISH);
 }
 
 static bool opts_shared_equal(const lskum_opts *a, const lskum_opts *b)
 {
     return a->cfl == b->cfl && a->cfl_ramp_iters == b->cfl_ramp_iters && a->inner_iters == b->inner_iters &&
            a->jvp == b->jvp && a->precision == b->precision && a->first_order_iters == b->first_order_iters &&
-           a->scheme == b->scheme;
+           a->scheme == b->scheme && a->lusgs == b->lusgs;
 }
 
 // Validate one case's cloud (indices local to the case).
@@ -729,6 +730,7 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
     d.first_order = c->opts.first_order_iters;
     d.jvp = c->opts.jvp;
     d.scheme = c->opts.scheme;
+    d.lusgs = c->opts.lusgs;
     auto up = [&](void *dst, const void *src, size_t bytes) {
         if (e == cudaSuccess) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
     };
@@ -992,7 +994,12 @@ lskum_status state_from_conserved(lskum_ctx *c, const std::vector<double> &Ucall
 // reset the counters (all of them with reset_hist).
 lskum_status finish_state(lskum_ctx *c, bool reset_hist)
 {
-    cudaError_t e = launch_reset_ctrl(c->ctrl, c->stream);
+    // a new state: the increments restart from zero (the revised LU-SGS
+    // lags its S term on the previous increment)
+    cudaError_t e = cudaMemsetAsync(c->dev.dU, 0, 4 * (size_t)c->ld * sizeof(double), c->stream);
+    if (e == cudaSuccess && c->dev.dUf)
+        e = cudaMemsetAsync(c->dev.dUf, 0, 4 * (size_t)c->ld * sizeof(float), c->stream);
+    if (e == cudaSuccess) e = launch_reset_ctrl(c->ctrl, c->stream);
     if (e == cudaSuccess) e = launch_init_state(c->dev, c->cur, c->stream);
     Ctrl h{};
     if (e != cudaSuccess) return cuda_fail(c, e, "setting the state");
@@ -1385,8 +1392,9 @@ lskum_status lskum_autotune(lskum_ctx *c, int32_t trial_iters, int32_t *tpp, int
     const size_t ld = c->ld;
     const size_t bytes_d = (8 * ld + (size_t)kPrimStride * ld) * sizeof(double);
     const size_t bytes_f = c->dev.set[0].primf ? (size_t)kPrimStride * ld * sizeof(float) : 0;
+    const size_t bytes_inc = 4 * ld * sizeof(double) + (c->dev.dUf ? 4 * ld * sizeof(float) : 0);
     char *save = nullptr;
-    cudaError_t e = cudaMalloc(&save, bytes_d + bytes_f);
+    cudaError_t e = cudaMalloc(&save, bytes_d + bytes_f + bytes_inc);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc(autotune save)");
     struct Free {
         char *p;
@@ -1394,12 +1402,15 @@ lskum_status lskum_autotune(lskum_ctx *c, int32_t trial_iters, int32_t *tpp, int
     } free_save{save};
     auto copy_set = [&](bool to_save) -> cudaError_t {
         const StateSet &st = c->dev.set[c->cur];
-        char *parts[4] = {(char *)st.U, (char *)st.q, (char *)st.prim, (char *)st.primf};
-        const size_t sz[4] = {4 * ld * sizeof(double), 4 * ld * sizeof(double),
-                              (size_t)kPrimStride * ld * sizeof(double), bytes_f};
+        // the state set and the last increments (the revised LU-SGS lags on them)
+        char *parts[6] = {(char *)st.U, (char *)st.q, (char *)st.prim, (char *)st.primf, (char *)c->dev.dU,
+                          (char *)c->dev.dUf};
+        const size_t sz[6] = {4 * ld * sizeof(double), 4 * ld * sizeof(double),
+                              (size_t)kPrimStride * ld * sizeof(double), bytes_f, 4 * ld * sizeof(double),
+                              c->dev.dUf ? 4 * ld * sizeof(float) : 0};
         size_t off = 0;
         cudaError_t ee = cudaSuccess;
-        for (int i = 0; i < 4 && ee == cudaSuccess; i++) {
+        for (int i = 0; i < 6 && ee == cudaSuccess; i++) {
             if (!sz[i]) continue;
             ee = to_save ? cudaMemcpyAsync(save + off, parts[i], sz[i], cudaMemcpyDeviceToDevice, c->stream)
                          : cudaMemcpyAsync(parts[i], save + off, sz[i], cudaMemcpyDeviceToDevice, c->stream);

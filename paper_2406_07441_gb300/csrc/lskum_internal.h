@@ -129,6 +129,7 @@ struct Dev {
     int32_t first_order;  // iterations n <= first_order use q~ = q
     int32_t precision;    // 0 FP64; 1 FP32 sweeps, compensated FP64 residual sums
     int32_t scheme;       // 0 implicit LU-SGS; 1 explicit (forward Euler, no sweeps)
+    int32_t lusgs;        // 0 Anandhanarayanan's diagonal; 1 the revised form of Manish et al.
 };
 
 // Kernel launch wrappers (lskum_kernels.cu).  `cur` is the state set read by

@@ -211,6 +211,25 @@ __device__ __forceinline__ void jvp_dir(const PrimT<T> &P, const JvpBase<T> &b, 
     out[3] = (dud * P.e1 + ud * de1) * A + ud * P.e1 * dA + sg * (de2 * B + P.e2 * dB);
 }
 
+// Unsplit Euler-flux Jacobian product A_d(U) dU in direction d = (dx, dy)
+// (the tangent of G_d = (rho u_d, rho u u_d + p dx, rho v u_d + p dy,
+// (E + p) u_d) along dU; the revised LU-SGS's S term).
+__device__ __forceinline__ void euler_jvp(double rho, double u, double v, double p, const double dU[4], double dx,
+                                          double dy, double out[4])
+{
+    const double irho = 1.0 / rho;
+    const double ud = u * dx + v * dy;
+    const double du = (dU[1] - u * dU[0]) * irho, dv = (dU[2] - v * dU[0]) * irho;
+    const double dud = du * dx + dv * dy;
+    const double dk = u * dU[1] + v * dU[2] - 0.5 * (u * u + v * v) * dU[0];  // d(rho |u|^2 / 2)
+    const double dp = kGm1 * (dU[3] - dk);
+    const double E = p / kGm1 + 0.5 * rho * (u * u + v * v);
+    out[0] = dU[1] * dx + dU[2] * dy;
+    out[1] = dU[1] * ud + rho * u * dud + dp * dx;
+    out[2] = dU[2] * ud + rho * v * dud + dp * dy;
+    out[3] = (dU[3] + dp) * ud + (E + p) * dud;
+}
+
 __device__ __forceinline__ void flux_cons(const MathTables &T, const double U[4], double dx, double dy, double sg,
                                           double G[4])
 {
@@ -426,6 +445,13 @@ __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const doub
         const double dt = cfl * d.geo[G_DMIN * ld + k] / (sqrt(u * u + v * v) + a);
         if (d.scheme == 1) {  // explicit: D = 1/dt, the step is -R/D
             d.D[k] = 1.0 / dt;
+            return;
+        }
+        if (d.lusgs == 1) {  // revised LU-SGS: Jameson's splitting, rho(A_d) = |u_d| + a
+            const double u1 = fabs(u * e1x + v * e1y) + a, u2 = fabs(u * e2x + v * e2y) + a;
+            d.D[k] = 1.0 / dt +
+                     0.5 * (u1 * (fabs(d.geo[G_LS1_0 * ld + k]) + fabs(d.geo[G_LS1_1 * ld + k])) +
+                            u2 * (fabs(d.geo[G_LS1_2 * ld + k]) + fabs(d.geo[G_LS1_3 * ld + k])));
             return;
         }
         double Dp = 1.0 / dt, Ddom = 0.0;
@@ -647,8 +673,27 @@ __global__ void __launch_bounds__(256) k_sweep(Dev d, StateSet st, int lb, int l
         const T iD = T(1) / (T)d.D[k];
         T w[4];
         if (FWD) {
+            double rhs[4];
 #pragma unroll
-            for (int c = 0; c < 4; c++) w[c] = -((T)d.R[c * ld + k] + acc[c]) * iD;
+            for (int c = 0; c < 4; c++) rhs[c] = d.R[c * ld + k];
+            if (d.lusgs == 1) {
+                // revised LU-SGS: -R - S with S_0 = -1/2 sum_s LS_s(1) A_d(U_0) dU_0 of
+                // the previous iteration's increment (still in dU: the backward
+                // sweep of this iteration has not run)
+                double dp[4];
+#pragma unroll
+                for (int c = 0; c < 4; c++) dp[c] = d.dUf ? (double)d.dUf[4 * k + c] : d.dU[4 * k + c];
+                const double *pk = st.prim + (size_t)k * kPrimStride;
+                double J1[4], J2[4];
+                euler_jvp(pk[P_RHO], pk[P_U], pk[P_V], pk[P_P], dp, e1x, e1y, J1);
+                euler_jvp(pk[P_RHO], pk[P_U], pk[P_V], pk[P_P], dp, e2x, e2y, J2);
+                const double l1 = d.geo[G_LS1_0 * ld + k] + d.geo[G_LS1_1 * ld + k];
+                const double l2 = d.geo[G_LS1_2 * ld + k] + d.geo[G_LS1_3 * ld + k];
+#pragma unroll
+                for (int c = 0; c < 4; c++) rhs[c] -= 0.5 * (l1 * J1[c] + l2 * J2[c]);  // R + S
+            }
+#pragma unroll
+            for (int c = 0; c < 4; c++) w[c] = -((T)rhs[c] + acc[c]) * iD;
         } else {
 #pragma unroll
             for (int c = 0; c < 4; c++) w[c] = fma(-acc[c], iD, sb.dUs[4 * k + c]);

@@ -566,3 +566,46 @@ def test_explicit_solver_is_forward_euler():
     inner = c.flag == 0
     assert np.allclose(dE[inner], -R[inner] / D[inner, None], rtol=0, atol=1e-15)
     assert np.all(dE[c.flag == 2] == 0.0)
+
+
+def test_revised_lusgs_diagonal_and_lag_term_closed_forms():
+    """Manish et al.'s diagonal on the regular 3x3 stencil of spacing h is
+    1/dt + (|u| + a)/h + (|v| + a)/h (each split sub-stencil has LS(1) = -+1/h),
+    and the lagged term S vanishes there (mirror sub-stencils: LS+(1) =
+    -LS-(1)); S is zero for a zero increment and linear in it."""
+    n = 9
+    c = cg.cartesian_box(n, n, jitter=0.0, seed=3)
+    o = O.Oracle(c)
+    h = 1.0 / (n - 1)
+    rng = np.random.default_rng(5)
+    U = np.array([O.prim_to_cons(1.1, 0.3, -0.2, 0.8)] * c.n)
+    centre = int(np.argmin((c.x - 0.5) ** 2 + (c.y - 0.5) ** 2))
+    cfl = 3.0
+    a = math.sqrt(1.4 * 0.8 / 1.1)
+    dU = rng.normal(0, 1e-3, (c.n, 4))
+    D, S = o.manish_terms(U, cfl, dU)
+    dt = cfl * h / (math.hypot(0.3, 0.2) + a)
+    assert abs(D[centre] - (1 / dt + (0.3 + a) / h + (0.2 + a) / h)) < 1e-12 * D[centre]
+    assert np.max(np.abs(S[centre])) < 1e-15
+    cj = cg.cartesian_box(n, n, jitter=0.25, seed=3)  # skewed stencils: S != 0
+    oj = O.Oracle(cj)
+    Uj = np.array([O.prim_to_cons(1.1, 0.3, -0.2, 0.8)] * cj.n)
+    dUj = rng.normal(0, 1e-3, (cj.n, 4))
+    _, Sj = oj.manish_terms(Uj, cfl, dUj)
+    assert np.max(np.abs(Sj)) > 1e-4
+    _, S0 = oj.manish_terms(Uj, cfl, np.zeros((cj.n, 4)))
+    assert np.all(S0 == 0.0)
+    _, S2 = oj.manish_terms(Uj, cfl, 2 * dUj)
+    assert np.max(np.abs(S2 - 2 * Sj)) < 1e-12 * np.max(np.abs(Sj))
+
+
+def test_revised_lusgs_keeps_the_fixed_point():
+    """At a converged state (R ~ 0, dU ~ 0) the revised sweeps' increment
+    vanishes too: the lagged term only changes the path."""
+    c = cg.naca0012_block(40, 16)
+    o = O.Oracle(c)
+    r = o.run(o.initial_state(0.63, 2.0), 6000, cfl=100.0, K=2, first_order=50, target=1e-10)
+    assert r["status"] == 0 and r["hist"][-1] / r["hist0"] <= 1e-10
+    m = o.run_manish(r["U"], 3, cfl=3.0, K=2, n0=100, sigma=-1)
+    assert m["status"] == 0
+    assert np.max(np.abs(m["U"] - r["U"])) < 1e-9 * np.max(np.abs(r["U"]))
