@@ -304,3 +304,26 @@ def test_explicit_scheme_matches_oracle(name):
     assert np.max(np.abs(h - r2["hist"]) / r2["hist"]) < 1e-10
     assert nrel(s2.field(lk.FIELD_U), r2["U"]) < 1e-9
     assert s2.info()["launches_per_iter"] < lk.Solver(c, 0.5, 1.0).info()["launches_per_iter"]
+
+
+@pytest.mark.parametrize("name", ["ogrid40x16", "jit64x32"])
+def test_revised_lusgs_matches_oracle(name):
+    """The revised LU-SGS of Manish et al. (Jameson diagonal, lagged S term):
+    fields of the first iteration (S = 0) and of the fifth (S from the fourth
+    iteration's increment), and the history."""
+    lk = _lskum()
+    c = cached_cloud(name, CLOUDS[name])
+    o = O.Oracle(c)
+    U0 = o.initial_state(0.63, 2.0)
+    for iters in (1, 5):
+        s = lk.Solver(c, 0.63, 2.0, cfl=3.0, inner_iters=2, first_order_iters=2, lusgs=lk.LUSGS_MANISH)
+        r = o.run_manish(U0, iters, cfl=3.0, K=2, first_order=2, sigma=-1)
+        assert r["status"] == 0 and s.run(iters) == iters
+        D = s.field(lk.FIELD_D)
+        assert np.max(np.abs(D - r["D"]) / np.abs(r["D"])) < 1e-12
+        assert nrel(s.field(lk.FIELD_R), r["R"]) < 1e-10
+        assert nrel(s.field(lk.FIELD_DUS), r["dUs"]) < 1e-10
+        assert nrel(s.field(lk.FIELD_DU), r["dU"]) < 1e-10
+        assert nrel(s.field(lk.FIELD_U), r["U"]) < 1e-12
+        h = s.residuals()
+        assert np.max(np.abs(h - r["hist"]) / r["hist"]) < 1e-10
