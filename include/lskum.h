@@ -117,12 +117,18 @@ typedef struct {
  *                    split diagonal gives); converges faster at cfl ~ 2-3,
  *                    diverges at cfl >= ~7.  The lag restarts from dU = 0
  *                    after every new state.
+ *   ordering         the LU-SGS sweep order: LSKUM_ORDER_COLOUR (0; all
+ *                    points of a colour together, Alg. 6) or
+ *                    LSKUM_ORDER_WALL_FIRST (1; the wall points colour by
+ *                    colour, then the interior points colour by colour,
+ *                    Alg. 4; the backward sweep is the exact reverse)
  */
 enum { LSKUM_SCHEME_LUSGS = 0, LSKUM_SCHEME_EXPLICIT = 1 };
 enum { LSKUM_LUSGS_ANANDH = 0, LSKUM_LUSGS_MANISH = 1 };
+enum { LSKUM_ORDER_COLOUR = 0, LSKUM_ORDER_WALL_FIRST = 1 };
 typedef struct {
     double mach, aoa_deg, cfl, cfl_ramp_iters;
-    int32_t inner_iters, jvp, precision, first_order_iters, scheme, lusgs;
+    int32_t inner_iters, jvp, precision, first_order_iters, scheme, lusgs, ordering;
 } lskum_opts;
 
 /*
@@ -237,7 +243,8 @@ lskum_status lskum_get_residuals(lskum_ctx *ctx, double *hist, int32_t cap, int3
 lskum_status lskum_get_forces(lskum_ctx *ctx, double *cl, double *cd);
 
 /* The colouring and sweep order: colour i32[N] (1-based, caller order),
- * order i32[N] (caller index at each sweep position), n_colours. Any may be NULL. */
+ * order i32[N] (caller index at each sweep position, as opts.ordering
+ * defines it), n_colours. Any may be NULL. */
 lskum_status lskum_get_order(lskum_ctx *ctx, int32_t *colour, int32_t *order, int32_t *n_colours);
 
 /* Measure: run `reps` iterations with each phase launched directly (not as a

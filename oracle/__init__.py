@@ -166,7 +166,10 @@ def freestream(mach, aoa_deg):
 class Oracle:
     """One cloud, the canonical sweep order, and the steps of Alg. 1 on it."""
 
-    def __init__(self, cloud):
+    def __init__(self, cloud, ordering=0):
+        """ordering 0: the sweep order of Alg. 6 (points stably sorted by
+        colour); 1: Alg. 4 (wall points by colour, then interior points by
+        colour, then outer points)."""
         self.cloud = cloud
         self.n = cloud.n
         self._keep = [np.ascontiguousarray(cloud.x, np.float64), np.ascontiguousarray(cloud.y, np.float64),
@@ -180,6 +183,11 @@ class Oracle:
         self.rank = np.zeros(self.n, np.int32)
         self.ncolours = lib().o_color_order(self.n, _p(k[5]), _p(k[6]), _p(self.colour), _p(self.order),
                                             _p(self.rank))
+        if ordering == 1:
+            group = np.where(cloud.flag == 1, 0, np.where(cloud.flag == 0, 1, 2))
+            key = group.astype(np.int64) * (self.ncolours + 1) + self.colour
+            self.order[:] = np.argsort(key, kind="stable").astype(np.int32)
+            self.rank[self.order] = np.arange(self.n, dtype=np.int32)
 
     def initial_state(self, mach, aoa_deg):
         U = np.zeros((self.n, 4))

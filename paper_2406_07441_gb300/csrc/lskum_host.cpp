@@ -60,6 +60,7 @@ struct lskum_ctx {
     std::vector<int32_t> colour;        // caller order, 1-based
     std::vector<int32_t> canon_order;   // stable colour order of caller indices
     int32_t n_colours = 0;
+    int32_t n_levels = 0;               // sweep levels (colours, or (wall|interior, colour) pairs)
     std::vector<int32_t> lvl_beg, lvl_act_end, lvl_end;
     // device
     Arena arena;
@@ -216,14 +217,15 @@ static bool opts_valid(const lskum_opts *o)
            (o->jvp == LSKUM_JVP_EXACT || o->jvp == LSKUM_JVP_INCREMENT) && (o->precision == 0 || o->precision == 1) &&
            o->first_order_iters >= 0 &&
            (o->scheme == LSKUM_SCHEME_LUSGS || (o->scheme == LSKUM_SCHEME_EXPLICIT && o->precision == 0)) &&
-           (o->lusgs == LSKUM_LUSGS_ANANDH || o->lusgs == LSKUM_LUSGS_MANISH);
+           (o->lusgs == LSKUM_LUSGS_ANANDH || o->lusgs == LSKUM_LUSGS_MANISH) &&
+           (o->ordering == LSKUM_ORDER_COLOUR || o->ordering == LSKUM_ORDER_WALL_FIRST);
 }
 
 static bool opts_shared_equal(const lskum_opts *a, const lskum_opts *b)
 {
     return a->cfl == b->cfl && a->cfl_ramp_iters == b->cfl_ramp_iters && a->inner_iters == b->inner_iters &&
            a->jvp == b->jvp && a->precision == b->precision && a->first_order_iters == b->first_order_iters &&
-           a->scheme == b->scheme && a->lusgs == b->lusgs;
+           a->scheme == b->scheme && a->lusgs == b->lusgs && a->ordering == b->ordering;
 }
 
 // Validate one case's cloud (indices local to the case).
@@ -447,37 +449,51 @@ static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &
     // ---- colouring and orders ----
     c->n_colours = colour_points(n, off, idx, c->colour);
     const int32_t nc = c->n_colours;
-    c->canon_order.resize(n);
-    {
-        std::vector<int32_t> cnt(nc + 2, 0);
-        for (int32_t p = 0; p < n; p++) cnt[c->colour[p] + 1]++;
-        for (int32_t k = 1; k <= nc + 1; k++) cnt[k] += cnt[k - 1];
-        std::vector<int32_t> pos(cnt.begin(), cnt.end());
-        for (int32_t p = 0; p < n; p++) c->canon_order[pos[c->colour[p]]++] = p;
-    }
-    // internal order: colour, then wall < interior < outer, then caller index
+    // sweep order (caller indices): colour by colour (Alg. 6), or wall points
+    // colour by colour, then interior, then outer points (Alg. 4); ties by
+    // caller index.  `skey` is the level a point belongs to; a neighbour is
+    // "lower" when its key is smaller.
     auto trank = [&](int32_t p) { return c->flag[p] == LSKUM_WALL ? 0 : (c->flag[p] == LSKUM_INTERIOR ? 1 : 2); };
+    const bool wall_first = c->opts.ordering == LSKUM_ORDER_WALL_FIRST;
+    auto skey = [&](int32_t p) -> int64_t {
+        return wall_first ? (int64_t)trank(p) * (nc + 1) + c->colour[p] : (int64_t)c->colour[p];
+    };
+    c->canon_order.resize(n);
+    std::iota(c->canon_order.begin(), c->canon_order.end(), 0);
+    std::stable_sort(c->canon_order.begin(), c->canon_order.end(),
+                     [&](int32_t a, int32_t b) { return skey(a) < skey(b); });
+    // internal order: level, then wall < interior < outer, then caller index
     c->perm.resize(n);
     std::iota(c->perm.begin(), c->perm.end(), 0);
     std::stable_sort(c->perm.begin(), c->perm.end(), [&](int32_t a, int32_t b) {
-        if (c->colour[a] != c->colour[b]) return c->colour[a] < c->colour[b];
+        if (skey(a) != skey(b)) return skey(a) < skey(b);
         return trank(a) < trank(b);
     });
     c->inv.resize(n);
     for (int32_t k = 0; k < n; k++) c->inv[c->perm[k]] = k;
-    c->lvl_beg.assign(nc, 0);
-    c->lvl_act_end.assign(nc, 0);
-    c->lvl_end.assign(nc, 0);
+    // levels: runs of equal key holding wall or interior points; outer points
+    // (never swept) close their level's range (or, wall-first, the last level)
+    c->lvl_beg.clear();
+    c->lvl_act_end.clear();
+    c->lvl_end.clear();
     {
         int32_t k = 0;
-        for (int32_t col = 1; col <= nc; col++) {
-            c->lvl_beg[col - 1] = k;
-            while (k < n && c->colour[c->perm[k]] == col && c->flag[c->perm[k]] != LSKUM_OUTER) k++;
-            c->lvl_act_end[col - 1] = k;
-            while (k < n && c->colour[c->perm[k]] == col) k++;
-            c->lvl_end[col - 1] = k;
+        while (k < n) {
+            const int64_t key = skey(c->perm[k]);
+            const int32_t b = k;
+            while (k < n && skey(c->perm[k]) == key && c->flag[c->perm[k]] != LSKUM_OUTER) k++;
+            const int32_t ae = k;
+            while (k < n && skey(c->perm[k]) == key) k++;
+            if (ae > b) {
+                c->lvl_beg.push_back(b);
+                c->lvl_act_end.push_back(ae);
+                c->lvl_end.push_back(k);
+            } else if (!c->lvl_end.empty()) {
+                c->lvl_end.back() = k;  // an all-outer run
+            }
         }
     }
+    c->n_levels = (int32_t)c->lvl_beg.size();
 
     // ---- sliced ELL in internal order ----
     const int32_t ld = (n + 31) / 32 * 32;
@@ -538,7 +554,7 @@ static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &
             for (int32_t e = off[p]; e < off[p + 1]; e++) {
                 const int32_t q = idx[e];
                 if (c->flag[q] == LSKUM_OUTER || smb[e] == 0) continue;
-                const bool lower = c->colour[q] < c->colour[p];
+                const bool lower = skey(q) < skey(p);
                 (lower ? hp.lo_nbr : hp.up_nbr).push_back(c->inv[q]);
                 (lower ? hp.lo_mb : hp.up_mb).push_back(smb[e]);
                 (lower ? hp.lo_w1 : hp.up_w1).push_back(sw1[e]);
@@ -551,7 +567,7 @@ static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &
     // per level, points by decreasing list length (a warp's groups then share a trip count)
     hp.sw_fwd.assign(std::max(n, 1), 0);
     hp.sw_bwd.assign(std::max(n, 1), 0);
-    for (int32_t l = 0; l < nc; l++) {
+    for (int32_t l = 0; l < c->n_levels; l++) {
         const int32_t b = c->lvl_beg[l], e = c->lvl_act_end[l];
         for (int32_t k = b; k < e; k++) hp.sw_fwd[k] = hp.sw_bwd[k] = k;
         auto lo_len = [&](int32_t k) { return hp.lo_off[k + 1] - hp.lo_off[k]; };
@@ -598,7 +614,7 @@ static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &
 
 static lskum_status upload(lskum_ctx *c, HostPrep &hp)
 {
-    const int32_t n = c->n, ld = c->ld, nsl = ld / 32, nc = c->n_colours;
+    const int32_t n = c->n, ld = c->ld, nsl = ld / 32;
     std::vector<int32_t> &slice_off = hp.slice_off, &deg = hp.deg, &enb = hp.enb;
     std::vector<uint8_t> &emb = hp.emb, &fl_i = hp.fl_i;
     std::vector<double> &edx = hp.edx, &edy = hp.edy, &ew1 = hp.ew1, &ew2 = hp.ew2, &egx = hp.egx, &egy = hp.egy;
@@ -819,7 +835,7 @@ static lskum_status build_graphs(lskum_ctx *c)
         cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamBeginCapture");
         int launches = 0;
-        cudaError_t le = launch_iteration(c->dev, c->launch, par, c->n_colours, c->lvl_beg.data(),
+        cudaError_t le = launch_iteration(c->dev, c->launch, par, c->n_levels, c->lvl_beg.data(),
                                           c->lvl_act_end.data(), c->lvl_end.data(), c->stream, &launches);
         e = cudaStreamEndCapture(c->stream, &g);
         if (le != cudaSuccess) {
@@ -1358,7 +1374,7 @@ lskum_status lskum_time_phases(lskum_ctx *c, int32_t reps, double *ms)
         const int cur = c->cur;
         for (int ph = 0; ph < 6 && e == cudaSuccess; ph++) {
             e = cudaEventRecord(ev[ph], c->stream);
-            if (e == cudaSuccess) e = launch_phase(d, c->launch, cur, ph, c->n_colours, c->lvl_beg.data(),
+            if (e == cudaSuccess) e = launch_phase(d, c->launch, cur, ph, c->n_levels, c->lvl_beg.data(),
                                                    c->lvl_act_end.data(), c->lvl_end.data(), c->stream);
         }
         if (e == cudaSuccess) e = cudaEventRecord(ev[6], c->stream);
@@ -1662,7 +1678,7 @@ lskum_status ctx_case_norms(lskum_ctx *c, std::vector<double> &norms)
     if (s != LSKUM_OK) return s;
     cudaError_t e = cudaSuccess;
     for (int ph = 0; ph < 3 && e == cudaSuccess; ph++)
-        e = launch_phase(c->dev, c->launch, c->cur, ph, c->n_colours, c->lvl_beg.data(), c->lvl_act_end.data(),
+        e = launch_phase(c->dev, c->launch, c->cur, ph, c->n_levels, c->lvl_beg.data(), c->lvl_act_end.data(),
                          c->lvl_end.data(), c->stream);
     norms.assign(c->n_cases, 0.0);
     if (e == cudaSuccess)

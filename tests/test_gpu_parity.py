@@ -327,3 +327,27 @@ def test_revised_lusgs_matches_oracle(name):
         assert nrel(s.field(lk.FIELD_U), r["U"]) < 1e-12
         h = s.residuals()
         assert np.max(np.abs(h - r["hist"]) / r["hist"]) < 1e-10
+
+
+@pytest.mark.parametrize("name", ["ogrid40x16", "jit64x32"])
+def test_wall_first_ordering_matches_oracle(name):
+    """Alg. 4's order (wall points colour by colour, then interior points):
+    the library's sweep order equals the oracle's, and an iteration's fields
+    and a 20-iteration history match."""
+    lk = _lskum()
+    c = cached_cloud(name, CLOUDS[name])
+    o = O.Oracle(c, ordering=1)
+    s = lk.Solver(c, 0.63, 2.0, inner_iters=2, first_order_iters=3, ordering=lk.ORDER_WALL_FIRST)
+    col, order, nc = s.order()
+    assert nc == o.ncolours and np.array_equal(col, o.colour) and np.array_equal(order, o.order)
+    r = o.run(o.initial_state(0.63, 2.0), 1, cfl=100.0, K=2, first_order=3)
+    assert s.run(1) == 1
+    assert nrel(s.field(lk.FIELD_DUS), r["dUs"]) < 1e-10
+    assert nrel(s.field(lk.FIELD_DU), r["dU"]) < 1e-10
+    assert nrel(s.field(lk.FIELD_U), r["U"]) < 1e-12
+    s2 = lk.Solver(c, 0.63, 2.0, inner_iters=2, first_order_iters=3, ordering=lk.ORDER_WALL_FIRST)
+    r2 = o.run(o.initial_state(0.63, 2.0), 20, cfl=100.0, K=2, first_order=3)
+    assert s2.run(20) == 20
+    h = s2.residuals()
+    assert np.max(np.abs(h - r2["hist"]) / r2["hist"]) < 1e-10
+    assert s2.info()["launches_per_iter"] >= lk.Solver(c, 0.63, 2.0, inner_iters=2).info()["launches_per_iter"]
