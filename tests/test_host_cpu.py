@@ -81,3 +81,19 @@ def test_bad_options_are_rejected(lk):
         with pytest.raises(lk.LskumError) as ei:
             lk.Solver(c, 0.5, 1.0, **kw)
         assert ei.value.status == -1
+
+
+def test_empty_and_isolated_clouds_are_rejected(lk):
+    """No points: LSKUM_ERR_ARG; one interior point without neighbours: its
+    least-squares stencil is degenerate, LSKUM_ERR_STENCIL; both before any
+    device call."""
+    empty = cg.Cloud(np.zeros(0), np.zeros(0), np.zeros(0, np.uint8), np.zeros(0), np.zeros(0),
+                     np.zeros(1, np.int32), np.zeros(0, np.int32), {})
+    with pytest.raises(lk.LskumError) as ei:
+        lk.Solver(empty, 0.5, 1.0)
+    assert ei.value.status == -1
+    one = cg.Cloud(np.zeros(1), np.zeros(1), np.zeros(1, np.uint8), np.zeros(1), np.zeros(1),
+                   np.zeros(2, np.int32), np.zeros(0, np.int32), {})
+    with pytest.raises(lk.LskumError) as ei:
+        lk.Solver(one, 0.5, 1.0)
+    assert ei.value.status == -2
