@@ -147,6 +147,21 @@ lskum_status lskum_create(const lskum_cloud *cloud, const lskum_opts *opts, void
                           lskum_ctx **out);
 
 /*
+ * Dry run (no counterpart in the paper): validate the clouds and options
+ * exactly as lskum_batch_create does (n_cases = 1: as lskum_create), build
+ * the host layout (colouring, sweep order and levels, slot lists) and check
+ * its invariants: the sweep order is a permutation, every wall or interior
+ * point lies in one sweep level and outer points in none, each level's sweep
+ * orders are permutations of it, no two coupled points share a level, and
+ * the lower / upper slot lists hold exactly the coupling slots of earlier /
+ * later levels.  No device call is made.  n_colours, n_levels (may be NULL)
+ * receive the counts.  Errors as lskum_create (LSKUM_ERR_ARG also for a
+ * failed invariant, with the reason in lskum_last_error(NULL)).
+ */
+lskum_status lskum_validate(const lskum_cloud *clouds, const lskum_opts *opts, int32_t n_cases, int32_t *n_colours,
+                            int32_t *n_levels);
+
+/*
  * Batched solves (a serving extension; no counterpart in the paper): n_cases
  * independent flow problems, each with its own cloud and free stream, solved
  * together.  The context holds the disjoint union of the clouds (caller point

@@ -205,6 +205,7 @@ struct HostPrep {
     std::vector<double> lo_w1, lo_w2, up_w1, up_w2;
     // per-case norm blocks and case of every internal point
     std::vector<int32_t> blk_pos, blk_case, case_blk, case_of_i;
+    std::vector<uint8_t> smb_caller;  // sub-stencil membership per caller-order slot
 };
 static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &hp);
 static lskum_status upload(lskum_ctx *c, HostPrep &hp);
@@ -264,8 +265,68 @@ static lskum_status validate_cloud(const lskum_cloud *cl, int32_t cs)
     return LSKUM_OK;
 }
 
+// Invariants of the host layout that the kernels rely on: the internal order
+// is a permutation, every wall or interior point lies in exactly one sweep
+// level and outer points in none, each level's two sweep orders are
+// permutations of the level, no two points of a level are coupled, and
+// every lower (upper) slot list entry lies in an earlier (later) level, the
+// two lists together holding every coupling slot.
+static lskum_status verify_layout(lskum_ctx *c, const lskum_cloud *cl, const HostPrep &hp)
+{
+    const int32_t n = c->n;
+    std::vector<int32_t> seen(n, 0);
+    for (int32_t k = 0; k < n; k++) {
+        const int32_t p = c->perm[k];
+        if (p < 0 || p >= n || seen[p]++ || c->inv[p] != k) return fail(c, LSKUM_ERR_ARG, "layout: order");
+    }
+    std::vector<int32_t> level(n, -1);
+    int32_t prev_end = 0;
+    for (int32_t l = 0; l < c->n_levels; l++) {
+        const int32_t b = c->lvl_beg[l], ae = c->lvl_act_end[l], e = c->lvl_end[l];
+        if (!(b >= prev_end && b < ae && ae <= e && e <= n)) return fail(c, LSKUM_ERR_ARG, "layout: level %d", l);
+        prev_end = e;
+        std::vector<int32_t> f(hp.sw_fwd.begin() + b, hp.sw_fwd.begin() + ae),
+            g(hp.sw_bwd.begin() + b, hp.sw_bwd.begin() + ae);
+        std::sort(f.begin(), f.end());
+        std::sort(g.begin(), g.end());
+        for (int32_t k = b; k < ae; k++) {
+            if (f[k - b] != k || g[k - b] != k) return fail(c, LSKUM_ERR_ARG, "layout: sweep order of level %d", l);
+            if (c->flag[c->perm[k]] == LSKUM_OUTER) return fail(c, LSKUM_ERR_ARG, "layout: outer point swept");
+            level[k] = l;
+        }
+    }
+    for (int32_t k = 0; k < n; k++)
+        if ((level[k] < 0) != (c->flag[c->perm[k]] == LSKUM_OUTER))
+            return fail(c, LSKUM_ERR_ARG, "layout: point %d not in a level", c->perm[k]);
+    for (int32_t k = 0; k < n; k++) {
+        if (level[k] < 0) continue;
+        int32_t coupled = 0;
+        const int32_t p = c->perm[k];
+        for (int32_t e = cl->nbr_off[p]; e < cl->nbr_off[p + 1]; e++) {
+            const int32_t q = c->inv[cl->nbr_idx[e]];
+            if (level[q] < 0) continue;
+            if (level[q] == level[k]) return fail(c, LSKUM_ERR_ARG, "layout: coupled points %d, %d in one level", p,
+                                                  cl->nbr_idx[e]);
+        }
+        for (int32_t j = hp.lo_off[k]; j < hp.lo_off[k + 1]; j++, coupled++)
+            if (hp.lo_nbr[j] < 0 || hp.lo_nbr[j] >= n || !(level[hp.lo_nbr[j]] >= 0 && level[hp.lo_nbr[j]] < level[k]))
+                return fail(c, LSKUM_ERR_ARG, "layout: lower list of point %d", p);
+        for (int32_t j = hp.up_off[k]; j < hp.up_off[k + 1]; j++, coupled++)
+            if (hp.up_nbr[j] < 0 || hp.up_nbr[j] >= n || !(level[hp.up_nbr[j]] > level[k]))
+                return fail(c, LSKUM_ERR_ARG, "layout: upper list of point %d", p);
+        int32_t expect = 0;
+        for (int32_t e = cl->nbr_off[p]; e < cl->nbr_off[p + 1]; e++)
+            expect += level[c->inv[cl->nbr_idx[e]]] >= 0 && hp.smb_caller[e] != 0;
+        if (coupled != expect) return fail(c, LSKUM_ERR_ARG, "layout: slot lists of point %d", p);
+    }
+    for (int64_t t = 0; t < (int64_t)hp.enb.size(); t++)
+        if (hp.enb[t] < 0 || hp.enb[t] >= n) return fail(c, LSKUM_ERR_ARG, "layout: neighbour slot");
+    return LSKUM_OK;
+}
+
 static lskum_status create_impl(const lskum_cloud *clouds, const lskum_opts *opts, int32_t n_cases,
-                                void *cuda_stream, lskum_ctx **out)
+                                void *cuda_stream, lskum_ctx **out, bool host_only = false,
+                                int32_t *n_colours = nullptr, int32_t *n_levels = nullptr)
 {
     if (!out) return fail(nullptr, LSKUM_ERR_ARG, "out is NULL");
     *out = nullptr;
@@ -319,6 +380,17 @@ static lskum_status create_impl(const lskum_cloud *clouds, const lskum_opts *opt
     c->user_stream = (cudaStream_t)cuda_stream;
     HostPrep hp;
     lskum_status s = prepare_host(c, &u, hp);  // no CUDA call before this returns
+    if (host_only) {
+        if (s == LSKUM_OK) s = verify_layout(c, &u, hp);
+        if (s == LSKUM_OK) {
+            if (n_colours) *n_colours = c->n_colours;
+            if (n_levels) *n_levels = c->n_levels;
+        } else {
+            g_create_error = c->err;
+        }
+        lskum_destroy(c);
+        return s;
+    }
     if (s == LSKUM_OK) {
         cudaError_t e = cudaGetDevice(&c->device);
         s = e == cudaSuccess ? upload(c, hp) : cuda_fail(c, e, "cudaGetDevice");
@@ -330,6 +402,13 @@ static lskum_status create_impl(const lskum_cloud *clouds, const lskum_opts *opt
     }
     *out = c;
     return LSKUM_OK;
+}
+
+lskum_status lskum_validate(const lskum_cloud *clouds, const lskum_opts *opts, int32_t n_cases, int32_t *n_colours,
+                            int32_t *n_levels)
+{
+    lskum_ctx *dummy = nullptr;
+    return create_impl(clouds, opts, n_cases, nullptr, &dummy, true, n_colours, n_levels);
 }
 
 lskum_status lskum_create(const lskum_cloud *cl, const lskum_opts *opts, void *cuda_stream, lskum_ctx **out)
@@ -365,7 +444,8 @@ static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &
     // ---- per-slot geometry and LS weights (caller order) ----
     const int64_t nnz = off[n];
     std::vector<double> sdx(nnz), sdy(nnz), sw1(nnz, 0.0), sw2(nnz, 0.0), swgx(nnz), swgy(nnz);
-    std::vector<uint8_t> smb(nnz, 0);
+    std::vector<uint8_t> &smb = hp.smb_caller;
+    smb.assign(nnz, 0);
     std::vector<double> geo((size_t)G_NFIELDS * n, 0.0);
     for (int32_t p = 0; p < n; p++) {
         const bool wall = c->flag[p] == LSKUM_WALL;

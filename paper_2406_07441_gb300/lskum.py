@@ -76,6 +76,7 @@ def load():
     L.lskum_get_case_forces.argtypes = [vp, i32, P(d), P(d)]
     L.lskum_get_case_info.argtypes = [vp, i32, P(i32), P(i32), P(i32), P(i32), P(i32), P(i32)]
     L.lskum_get_wall_distance.argtypes = [vp, vp]
+    L.lskum_validate.argtypes = [P(lskum_cloud), P(lskum_opts), i32, P(i32), P(i32)]
     L.lskum_get_field_dev.argtypes = [vp, i32, vp, vp]
     L.lskum_set_conserved_dev.argtypes = [vp, vp, vp]
     L.lskum_set_start_iters.argtypes = [vp, i32]
@@ -107,7 +108,7 @@ def load():
               "lskum_get_state", "lskum_get_field", "lskum_get_residuals", "lskum_get_forces", "lskum_get_order",
               "lskum_get_info", "lskum_time_phases", "lskum_density_norm_noalloc", "lskum_batch_create",
               "lskum_get_case_residuals", "lskum_get_case_forces", "lskum_get_case_info", "lskum_autotune",
-              "lskum_get_wall_distance", "lskum_set_start_iters", "lskum_get_field_dev", "lskum_set_conserved_dev", "lskum_set_launch_shape", "lskum_mlp_create", "lskum_mlp_get_params",
+              "lskum_get_wall_distance", "lskum_validate", "lskum_set_start_iters", "lskum_get_field_dev", "lskum_set_conserved_dev", "lskum_set_launch_shape", "lskum_mlp_create", "lskum_mlp_get_params",
               "lskum_mlp_set_params", "lskum_mlp_features", "lskum_mlp_forward", "lskum_mlp_loss_grads",
               "lskum_mlp_adam", "lskum_mlp_add_samples", "lskum_mlp_time_forward", "lskum_mlp_n_samples", "lskum_mlp_train",
               "lskum_mlp_predict"):
@@ -127,6 +128,25 @@ def _cloud_struct(cloud, keep):
             np.ascontiguousarray(cloud.nbr_idx, np.int32)]
     keep.extend(arrs)
     return lskum_cloud(int(cloud.n), *[a.ctypes.data for a in arrs])
+
+
+def validate(clouds, conditions, **kw):
+    """Host-only dry run of create (see lskum_validate): returns (n_colours,
+    n_levels) or raises LskumError; no GPU is needed."""
+    L = load()
+    keep = []
+    cl = (lskum_cloud * len(clouds))(*[_cloud_struct(c, keep) for c in clouds])
+    o = dict(cfl=100.0, cfl_ramp_iters=0.0, inner_iters=3, jvp=JVP_EXACT, precision=0, first_order_iters=0,
+             scheme=SCHEME_LUSGS, lusgs=LUSGS_ANANDH, ordering=ORDER_COLOUR)
+    o.update(kw)
+    op = (lskum_opts * len(clouds))(*[lskum_opts(m, a, o["cfl"], o["cfl_ramp_iters"], o["inner_iters"], o["jvp"],
+                                                 o["precision"], o["first_order_iters"], o["scheme"], o["lusgs"],
+                                                 o["ordering"]) for m, a in conditions])
+    nc, nl = C.c_int32(), C.c_int32()
+    s = L.lskum_validate(cl, op, len(clouds), C.byref(nc), C.byref(nl))
+    if s != 0:
+        raise LskumError(s, L.lskum_last_error(None).decode())
+    return nc.value, nl.value
 
 
 class Solver:

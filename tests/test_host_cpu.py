@@ -97,3 +97,31 @@ def test_empty_and_isolated_clouds_are_rejected(lk):
     with pytest.raises(lk.LskumError) as ei:
         lk.Solver(one, 0.5, 1.0)
     assert ei.value.status == -2
+
+
+@pytest.mark.parametrize("ordering", [0, 1])
+def test_host_layout_invariants_hold(lk, ordering):
+    """lskum_validate builds the host layout without a device and checks its
+    invariants (sweep levels independent, slot lists exactly the couplings
+    of earlier / later levels, sweep orders permutations); the colour count
+    equals the oracle's Alg. 5."""
+    import oracle as O
+    clouds = [cg.naca0012_block(40, 16), cg.naca0012_jittered(64, 32, seed=12),
+              cg.cartesian_box(7, 7, seed=2, wall_bottom=True), cg.naca0012_jittered(200, 80, seed=5)]
+    for c in clouds:
+        nc, nl = lk.validate([c], [(0.5, 1.0)], ordering=ordering)
+        assert nc == O.Oracle(c).ncolours
+        assert nl >= nc if ordering else nl <= nc
+    nc, nl = lk.validate(clouds[:2], [(0.5, 1.0), (0.7, -2.0)], ordering=ordering)
+    assert nc == max(O.Oracle(c).ncolours for c in clouds[:2])
+
+
+def test_validate_rejects_what_create_rejects(lk):
+    c = _cloud_copy(cg.naca0012_block(40, 16))
+    c.nbr_idx[3] = c.n
+    with pytest.raises(lk.LskumError) as ei:
+        lk.validate([c], [(0.5, 1.0)])
+    assert ei.value.status == -1
+    with pytest.raises(lk.LskumError) as ei:
+        lk.validate([cg.naca0012_block(40, 16)], [(0.5, 1.0)], scheme=1, precision=1)
+    assert ei.value.status == -1
