@@ -152,3 +152,23 @@ def test_failed_case_keeps_its_last_good_state_and_others_go_on():
     assert b.run(2) == 2
     assert b.case_info(2)["iters"] == 4 and b.case_info(0)["iters"] == 10
     assert np.array_equal(b.field(lk.FIELD_U)[b.case_info(2)["first_point"]:], singles[2][1])
+
+
+@pytest.mark.parametrize("opts", [dict(precision=1), dict(lusgs=1, cfl=3.0), dict(ordering=1),
+                                  dict(scheme=1, cfl=0.3), dict(precision=1, ordering=1, jvp=1)])
+def test_batch_equals_single_solves_for_every_option(opts):
+    """Every solver option keeps the batch property: each case of a batch is
+    bit for bit its own single-case solve (same launch shape)."""
+    from paper_2406_07441_gb300 import lskum as lk
+    clouds, conds = _clouds()
+    kw = dict(first_order_iters=3, inner_iters=2, **opts)
+    b = lk.Solver.batch(clouds, conds, **kw)
+    assert b.run(6) == 6
+    Ub = b.field(lk.FIELD_U)
+    for cs, (c, (m, a)) in enumerate(zip(clouds, conds)):
+        s = lk.Solver(c, m, a, **kw)
+        assert s.run(6) == 6
+        info = b.case_info(cs)
+        sl = slice(info["first_point"], info["first_point"] + info["n_points"])
+        assert np.array_equal(Ub[sl], s.field(lk.FIELD_U)), (opts, cs)
+        assert np.array_equal(b.case_residuals(cs), s.residuals())
