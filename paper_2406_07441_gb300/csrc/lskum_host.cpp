@@ -74,6 +74,7 @@ struct lskum_ctx {
     cudaEvent_t ev = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     double *pinned = nullptr;           // 4 * ld doubles of page-locked staging for state copies
+    double *dscratch = nullptr;         // 4 * ld doubles on the device: caller-order staging
     int launches_per_iter = 0;
     // cases (a batch is the disjoint union of its cases' clouds, caller order
     // = case 0's points, then case 1's, ...)
@@ -774,6 +775,7 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
     c->case_bad = A.alloc<int32_t>(c->n_cases);
     c->hist_cap = 4096;
     c->hist = A.alloc<double>((size_t)c->n_cases * c->hist_cap);
+    c->dscratch = A.alloc<double>(4 * (size_t)ld);
     if (A.err != cudaSuccess) return cuda_fail(c, A.err, "cudaMalloc");
     e = cudaMemset(c->ctrl, 0, sizeof(Ctrl));
     if (e == cudaSuccess) e = cudaMallocHost(&c->pinned, 4 * (size_t)ld * sizeof(double));
@@ -1063,24 +1065,17 @@ lskum_status ensure_hist(lskum_ctx *c, int32_t need)
 
 lskum_status finish_state(lskum_ctx *c, bool reset_hist);
 
-lskum_status state_from_conserved(lskum_ctx *c, const std::vector<double> &Ucaller, bool reset_hist)
+lskum_status state_from_conserved(lskum_ctx *c, const double *Ucaller, bool reset_hist)
 {
-    const int32_t n = c->n, ld = c->ld;
-    double *Ui = c->pinned;  // staged in page-locked memory
-    for (int32_t k = 0; k < n; k++) {
-        const int32_t p = c->perm[k];
-        for (int cc = 0; cc < 4; cc++) Ui[(size_t)cc * ld + k] = Ucaller[4 * (size_t)p + cc];
-    }
-    for (int32_t k = n; k < ld; k++) {  // padding: a valid state, never read
-        Ui[k] = 1.0;
-        Ui[(size_t)ld + k] = Ui[2 * (size_t)ld + k] = 0.0;
-        Ui[3 * (size_t)ld + k] = 2.5;
-    }
+    // caller order, contiguous: one copy into page-locked memory, then the
+    // reordering into the internal structure of arrays on the device
+    const int32_t n = c->n;
+    std::memcpy(c->pinned, Ucaller, 4 * (size_t)n * sizeof(double));
     cudaError_t e = join_user(c);
-    const int tgt = c->cur;
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(c->dev.set[tgt].U, Ui, 4 * (size_t)ld * sizeof(double), cudaMemcpyHostToDevice,
+        e = cudaMemcpyAsync(c->dscratch, c->pinned, 4 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice,
                             c->stream);
+    if (e == cudaSuccess) e = launch_from_caller(c->dscratch, c->ld, n, c->dev.inv, c->dev.set[c->cur].U, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "setting the state");
     return finish_state(c, reset_hist);
 }
@@ -1128,15 +1123,14 @@ lskum_status lskum_set_state(lskum_ctx *c, const double *rho, const double *u, c
             return fail(c, LSKUM_ERR_NONPOSITIVE, "non-physical input state at point %d", k);
         host_prim_to_cons(rho[k], u[k], v[k], p[k], &U[4 * (size_t)k]);
     }
-    return state_from_conserved(c, U, true);
+    return state_from_conserved(c, U.data(), true);
 }
 
 lskum_status lskum_set_conserved(lskum_ctx *c, const double *U)
 {
     if (!c || !U) return c ? fail(c, LSKUM_ERR_ARG, "NULL argument") : LSKUM_ERR_ARG;
     if (c->pending) return fail(c, LSKUM_ERR_ARG, "an enqueued run has not been waited for");
-    std::vector<double> Uv(U, U + 4 * (size_t)c->n);
-    return state_from_conserved(c, Uv, false);
+    return state_from_conserved(c, U, false);
 }
 
 // Asynchronous part of lskum_run: enqueue max_iters graph launches.
@@ -1211,22 +1205,25 @@ void *lskum_stream(lskum_ctx *c)
     return c ? (void *)c->stream : nullptr;
 }
 
-// Copy a per-point field to the host in caller order: `comps` rows of stride
-// ld (structure of arrays) or, with aos, `comps` values per point.
-static lskum_status download(lskum_ctx *c, const double *src, int comps, std::vector<double> &out, bool aos = false)
+// Copy a per-point field to the host in caller order: reordered on the
+// device (from `comps` rows of stride ld, or `comps` values per point with
+// aos; FP32 when srcf is given), then one contiguous copy.
+static lskum_status download_to(lskum_ctx *c, const double *src, const float *srcf, int comps, bool aos,
+                                double *out)
 {
-    const int32_t n = c->n, ld = c->ld;
-    double *buf = c->pinned;  // page-locked staging, 4 * ld doubles
-    cudaError_t e = cudaMemcpyAsync(buf, src, (size_t)comps * ld * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    const size_t bytes = (size_t)comps * c->n * sizeof(double);
+    cudaError_t e = launch_to_caller(src, srcf, comps, aos, c->ld, c->n, c->dev.inv, c->dscratch, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->pinned, c->dscratch, bytes, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy D2H");
-    out.assign((size_t)comps * n, 0.0);
-    for (int32_t k = 0; k < n; k++) {
-        const int32_t p = c->perm[k];
-        for (int cc = 0; cc < comps; cc++)
-            out[(size_t)comps * p + cc] = aos ? buf[(size_t)comps * k + cc] : buf[(size_t)cc * ld + k];
-    }
+    std::memcpy(out, c->pinned, bytes);
     return LSKUM_OK;
+}
+
+static lskum_status download(lskum_ctx *c, const double *src, int comps, std::vector<double> &out, bool aos = false)
+{
+    out.resize((size_t)comps * c->n);
+    return download_to(c, src, nullptr, comps, aos, out.data());
 }
 
 lskum_status lskum_get_field(lskum_ctx *c, int32_t field, double *out)
@@ -1249,73 +1246,10 @@ lskum_status lskum_get_field(lskum_ctx *c, int32_t field, double *out)
     case LSKUM_FIELD_DU: src = d.dU; aos = true; break;
     default: return fail(c, LSKUM_ERR_ARG, "unknown field %d", field);
     }
-    if (d.precision && (field == LSKUM_FIELD_DUS || field == LSKUM_FIELD_DU)) {
-        // FP32 increments of the mixed-precision sweeps
-        const float *fsrc = field == LSKUM_FIELD_DUS ? d.dUsf : d.dUf;
-        float *buf = reinterpret_cast<float *>(c->pinned);
-        cudaError_t e = cudaMemcpyAsync(buf, fsrc, 4 * (size_t)c->ld * sizeof(float), cudaMemcpyDeviceToHost,
-                                        c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy D2H");
-        for (int32_t k = 0; k < c->n; k++)
-            for (int cc = 0; cc < 4; cc++) out[4 * (size_t)c->perm[k] + cc] = (double)buf[4 * (size_t)k + cc];
-        return LSKUM_OK;
-    }
-    std::vector<double> v;
-    lskum_status s = download(c, src, comps, v, aos);
-    if (s != LSKUM_OK) return s;
-    std::memcpy(out, v.data(), v.size() * sizeof(double));
-    return LSKUM_OK;
-}
-
-// Order stream `waiter` after the work already enqueued on `waited`.
-static cudaError_t order_after(lskum_ctx *c, cudaStream_t waiter, cudaStream_t waited)
-{
-    cudaError_t e = cudaEventRecord(c->ev, waited);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(waiter, c->ev, 0);
-    return e;
-}
-
-lskum_status lskum_get_field_dev(lskum_ctx *c, int32_t field, double *out_dev, void *cuda_stream)
-{
-    if (!c || !out_dev) return c ? fail(c, LSKUM_ERR_ARG, "NULL argument") : LSKUM_ERR_ARG;
-    if (c->pending) return fail(c, LSKUM_ERR_ARG, "an enqueued run has not been waited for");
-    const Dev &d = c->dev;
-    const int K = d.K & 1;
-    const double *src = nullptr;
     const float *srcf = nullptr;
-    int comps = 4;
-    bool aos = false;
-    switch (field) {
-    case LSKUM_FIELD_U: src = d.set[c->cur].U; break;
-    case LSKUM_FIELD_Q: src = d.set[c->cur].q; break;
-    case LSKUM_FIELD_QX: src = d.qx[K]; break;
-    case LSKUM_FIELD_QY: src = d.qy[K]; break;
-    case LSKUM_FIELD_R: src = d.R; break;
-    case LSKUM_FIELD_D: src = d.D; comps = 1; break;
-    case LSKUM_FIELD_DUS: src = d.dUs; srcf = d.precision ? d.dUsf : nullptr; aos = true; break;
-    case LSKUM_FIELD_DU: src = d.dU; srcf = d.precision ? d.dUf : nullptr; aos = true; break;
-    default: return fail(c, LSKUM_ERR_ARG, "unknown field %d", field);
-    }
-    cudaStream_t us = (cudaStream_t)cuda_stream;
-    cudaError_t e = order_after(c, c->stream, us);
-    if (e == cudaSuccess) e = launch_to_caller(src, srcf, comps, aos, c->ld, c->n, d.inv, out_dev, c->stream);
-    if (e == cudaSuccess) e = order_after(c, us, c->stream);
-    return e == cudaSuccess ? LSKUM_OK : cuda_fail(c, e, "field to device memory");
-}
-
-lskum_status lskum_set_conserved_dev(lskum_ctx *c, const double *U_dev, void *cuda_stream)
-{
-    if (!c || !U_dev) return c ? fail(c, LSKUM_ERR_ARG, "NULL argument") : LSKUM_ERR_ARG;
-    if (c->pending) return fail(c, LSKUM_ERR_ARG, "an enqueued run has not been waited for");
-    cudaStream_t us = (cudaStream_t)cuda_stream;
-    cudaError_t e = order_after(c, c->stream, us);
-    if (e == cudaSuccess) e = launch_from_caller(U_dev, c->ld, c->n, c->dev.inv, c->dev.set[c->cur].U, c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "state from device memory");
-    lskum_status s = finish_state(c, false);
-    if (s != LSKUM_OK) return s;
-    e = order_after(c, us, c->stream);
-    return e == cudaSuccess ? LSKUM_OK : cuda_fail(c, e, "ordering the caller's stream");
+    if (d.precision && (field == LSKUM_FIELD_DUS || field == LSKUM_FIELD_DU))
+        srcf = field == LSKUM_FIELD_DUS ? d.dUsf : d.dUf;  // FP32 increments of the mixed-precision sweeps
+    return download_to(c, src, srcf, comps, aos, out);
 }
 
 lskum_status lskum_get_state(lskum_ctx *c, double *rho, double *u, double *v, double *p)
