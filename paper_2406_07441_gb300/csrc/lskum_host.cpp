@@ -1252,6 +1252,56 @@ lskum_status lskum_get_field(lskum_ctx *c, int32_t field, double *out)
     return download_to(c, src, srcf, comps, aos, out);
 }
 
+// Order stream `waiter` after the work already enqueued on `waited`.
+static cudaError_t order_after(lskum_ctx *c, cudaStream_t waiter, cudaStream_t waited)
+{
+    cudaError_t e = cudaEventRecord(c->ev, waited);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(waiter, c->ev, 0);
+    return e;
+}
+
+lskum_status lskum_get_field_dev(lskum_ctx *c, int32_t field, double *out_dev, void *cuda_stream)
+{
+    if (!c || !out_dev) return c ? fail(c, LSKUM_ERR_ARG, "NULL argument") : LSKUM_ERR_ARG;
+    if (c->pending) return fail(c, LSKUM_ERR_ARG, "an enqueued run has not been waited for");
+    const Dev &d = c->dev;
+    const int K = d.K & 1;
+    const double *src = nullptr;
+    const float *srcf = nullptr;
+    int comps = 4;
+    bool aos = false;
+    switch (field) {
+    case LSKUM_FIELD_U: src = d.set[c->cur].U; break;
+    case LSKUM_FIELD_Q: src = d.set[c->cur].q; break;
+    case LSKUM_FIELD_QX: src = d.qx[K]; break;
+    case LSKUM_FIELD_QY: src = d.qy[K]; break;
+    case LSKUM_FIELD_R: src = d.R; break;
+    case LSKUM_FIELD_D: src = d.D; comps = 1; break;
+    case LSKUM_FIELD_DUS: src = d.dUs; srcf = d.precision ? d.dUsf : nullptr; aos = true; break;
+    case LSKUM_FIELD_DU: src = d.dU; srcf = d.precision ? d.dUf : nullptr; aos = true; break;
+    default: return fail(c, LSKUM_ERR_ARG, "unknown field %d", field);
+    }
+    cudaStream_t us = (cudaStream_t)cuda_stream;
+    cudaError_t e = order_after(c, c->stream, us);
+    if (e == cudaSuccess) e = launch_to_caller(src, srcf, comps, aos, c->ld, c->n, d.inv, out_dev, c->stream);
+    if (e == cudaSuccess) e = order_after(c, us, c->stream);
+    return e == cudaSuccess ? LSKUM_OK : cuda_fail(c, e, "field to device memory");
+}
+
+lskum_status lskum_set_conserved_dev(lskum_ctx *c, const double *U_dev, void *cuda_stream)
+{
+    if (!c || !U_dev) return c ? fail(c, LSKUM_ERR_ARG, "NULL argument") : LSKUM_ERR_ARG;
+    if (c->pending) return fail(c, LSKUM_ERR_ARG, "an enqueued run has not been waited for");
+    cudaStream_t us = (cudaStream_t)cuda_stream;
+    cudaError_t e = order_after(c, c->stream, us);
+    if (e == cudaSuccess) e = launch_from_caller(U_dev, c->ld, c->n, c->dev.inv, c->dev.set[c->cur].U, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "state from device memory");
+    lskum_status s = finish_state(c, false);
+    if (s != LSKUM_OK) return s;
+    e = order_after(c, us, c->stream);
+    return e == cudaSuccess ? LSKUM_OK : cuda_fail(c, e, "ordering the caller's stream");
+}
+
 lskum_status lskum_get_state(lskum_ctx *c, double *rho, double *u, double *v, double *p)
 {
     if (!c || !rho || !u || !v || !p) return c ? fail(c, LSKUM_ERR_ARG, "NULL argument") : LSKUM_ERR_ARG;
