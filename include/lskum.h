@@ -189,6 +189,10 @@ lskum_status lskum_batch_create(const lskum_cloud *clouds, const lskum_opts *opt
  * union; else -1).  Pointers other than the context may be NULL in
  * lskum_get_case_info. */
 lskum_status lskum_get_case_residuals(lskum_ctx *ctx, int32_t cs, double *hist, int32_t cap, int32_t *n);
+/* As lskum_get_case_residuals for the norms of all four residual components
+ * (mass, x and y momentum, energy): hist4 f64[cap][4], n receives the count;
+ * column 0 is the density history the drop test uses. */
+lskum_status lskum_get_case_residuals4(lskum_ctx *ctx, int32_t cs, double *hist4, int32_t cap, int32_t *n);
 lskum_status lskum_get_case_forces(lskum_ctx *ctx, int32_t cs, double *cl, double *cd);
 lskum_status lskum_get_case_info(lskum_ctx *ctx, int32_t cs, int32_t *first_point, int32_t *n_points, int32_t *iters,
                                  int32_t *stopped, int32_t *status, int32_t *bad_point);

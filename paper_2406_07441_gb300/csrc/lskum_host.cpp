@@ -67,7 +67,7 @@ struct lskum_ctx {
     Dev dev{};
     Launch launch{};
     Ctrl *ctrl = nullptr;
-    double *hist = nullptr;
+    double *hist = nullptr, *hist4 = nullptr;
     int32_t hist_cap = 0;
     cudaStream_t stream = nullptr;      // internal, capture-capable
     cudaStream_t user_stream = nullptr;
@@ -763,7 +763,7 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
     c->launch.sweep_lanes = 4;
     d.n_blk = (int32_t)hp.blk_case.size();
     d.n_cases = c->n_cases;
-    d.blk = A.alloc<double>(d.n_blk);
+    d.blk = A.alloc<double>(4 * (size_t)d.n_blk);
     int32_t *dblk_pos = A.alloc<int32_t>(hp.blk_pos.size()), *dblk_case = A.alloc<int32_t>(hp.blk_case.size());
     int32_t *dcase_blk = A.alloc<int32_t>(hp.case_blk.size()), *dinv = A.alloc<int32_t>(n);
     int32_t *dcase_of = A.alloc<int32_t>(ld);
@@ -775,6 +775,7 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
     c->case_bad = A.alloc<int32_t>(c->n_cases);
     c->hist_cap = 4096;
     c->hist = A.alloc<double>((size_t)c->n_cases * c->hist_cap);
+    c->hist4 = A.alloc<double>((size_t)c->n_cases * c->hist_cap * 4);
     c->dscratch = A.alloc<double>(4 * (size_t)ld);
     if (A.err != cudaSuccess) return cuda_fail(c, A.err, "cudaMalloc");
     e = cudaMemset(c->ctrl, 0, sizeof(Ctrl));
@@ -986,6 +987,7 @@ lskum_status write_ctrl(lskum_ctx *c, Ctrl &h)
     h.case_err = c->case_err;
     h.case_bad = c->case_bad;
     h.hist = c->hist;
+    h.hist4 = c->hist4;
     h.hist_cap = c->hist_cap;
     cudaError_t e = cudaMemcpyAsync(c->ctrl, &h, sizeof(Ctrl), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -1043,22 +1045,35 @@ lskum_status ensure_hist(lskum_ctx *c, int32_t need)
     if (need <= c->hist_cap) return LSKUM_OK;
     int32_t cap = c->hist_cap;
     while (cap < need) cap *= 2;
-    double *h = nullptr;
+    double *h = nullptr, *h4 = nullptr;
     cudaError_t e = cudaMalloc(&h, (size_t)c->n_cases * cap * sizeof(double));
-    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc(history)");
+    if (e == cudaSuccess) e = cudaMalloc(&h4, (size_t)c->n_cases * cap * 4 * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaFree(h);
+        return cuda_fail(c, e, "cudaMalloc(history)");
+    }
     e = cudaMemcpy2DAsync(h, cap * sizeof(double), c->hist, c->hist_cap * sizeof(double),
                           c->hist_cap * sizeof(double), c->n_cases, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(h4, 4 * cap * sizeof(double), c->hist4, 4 * c->hist_cap * sizeof(double),
+                              4 * c->hist_cap * sizeof(double), c->n_cases, cudaMemcpyDeviceToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         cudaFree(h);
+        cudaFree(h4);
         return cuda_fail(c, e, "copying the history");
     }
-    for (auto &p : c->arena.ptrs)
+    for (auto &p : c->arena.ptrs) {
         if (p == c->hist) {
             cudaFree(p);
             p = h;
+        } else if (p == c->hist4) {
+            cudaFree(p);
+            p = h4;
         }
+    }
     c->hist = h;
+    c->hist4 = h4;
     c->hist_cap = cap;
     return LSKUM_OK;
 }
@@ -1067,13 +1082,12 @@ lskum_status finish_state(lskum_ctx *c, bool reset_hist);
 
 lskum_status state_from_conserved(lskum_ctx *c, const double *Ucaller, bool reset_hist)
 {
-    // caller order, contiguous: one copy into page-locked memory, then the
-    // reordering into the internal structure of arrays on the device
+    // caller order, contiguous: one copy straight from the caller's memory,
+    // then the reordering into the internal structure of arrays on the device
     const int32_t n = c->n;
-    std::memcpy(c->pinned, Ucaller, 4 * (size_t)n * sizeof(double));
     cudaError_t e = join_user(c);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(c->dscratch, c->pinned, 4 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice,
+        e = cudaMemcpyAsync(c->dscratch, Ucaller, 4 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice,
                             c->stream);
     if (e == cudaSuccess) e = launch_from_caller(c->dscratch, c->ld, n, c->dev.inv, c->dev.set[c->cur].U, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "setting the state");
@@ -1213,10 +1227,9 @@ static lskum_status download_to(lskum_ctx *c, const double *src, const float *sr
 {
     const size_t bytes = (size_t)comps * c->n * sizeof(double);
     cudaError_t e = launch_to_caller(src, srcf, comps, aos, c->ld, c->n, c->dev.inv, c->dscratch, c->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(c->pinned, c->dscratch, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, c->dscratch, bytes, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy D2H");
-    std::memcpy(out, c->pinned, bytes);
     return LSKUM_OK;
 }
 
@@ -1334,6 +1347,25 @@ lskum_status lskum_get_case_residuals(lskum_ctx *c, int32_t cs, double *hist, in
                                         cudaMemcpyDeviceToHost, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy history");
+    }
+    return LSKUM_OK;
+}
+
+lskum_status lskum_get_case_residuals4(lskum_ctx *c, int32_t cs, double *hist4, int32_t cap, int32_t *n)
+{
+    if (!c || !n || cap < 0 || (cap > 0 && !hist4) || cs < 0 || cs >= (c ? c->n_cases : 0))
+        return c ? fail(c, LSKUM_ERR_ARG, "bad argument") : LSKUM_ERR_ARG;
+    if (c->pending) return fail(c, LSKUM_ERR_ARG, "an enqueued run has not been waited for");
+    std::vector<int32_t> its;
+    lskum_status s = read_case_arrays(c, nullptr, &its);
+    if (s != LSKUM_OK) return s;
+    *n = std::min(its[cs], c->hist_cap);
+    const int32_t m = std::min(*n, cap);
+    if (m > 0) {
+        cudaError_t e = cudaMemcpyAsync(hist4, c->hist4 + (size_t)cs * c->hist_cap * 4, 4 * (size_t)m * sizeof(double),
+                                        cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "reading the residual history");
     }
     return LSKUM_OK;
 }

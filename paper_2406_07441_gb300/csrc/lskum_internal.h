@@ -41,7 +41,8 @@ struct Ctrl {
                          // iteration, the next k_begin makes it kStopped
     int32_t *case_it;    // [n_cases] norms recorded
     double *case_hist0;  // [n_cases] first norm (drop reference); <= 0 = not set
-    double *hist;        // [n_cases][hist_cap] residual-norm histories
+    double *hist;        // [n_cases][hist_cap] residual-norm histories (density)
+    double *hist4;       // [n_cases][hist_cap][4] norms of the four residual components
     int32_t *case_err;   // [n_cases] lskum_status of a failed case of a batch (0 = none)
     int32_t *case_bad;   // [n_cases] smallest internal index of its non-physical update
 };
@@ -114,7 +115,7 @@ struct Dev {
     const int32_t *sw_fwd, *sw_bwd;
     // per-case residual norm: stage 1 sums R_rho^2 over blocks of up to 256
     // points of one case (caller order), stage 2 adds each case's blocks
-    double *blk;             // [n_blk] partial sums
+    double *blk;             // [n_blk][4] partial sums of the four components
     const int32_t *blk_pos;  // [n_blk + 1] caller-order start of each block
     const int32_t *blk_case; // [n_blk] case of each block
     const int32_t *case_blk; // [n_cases + 1] first block of each case

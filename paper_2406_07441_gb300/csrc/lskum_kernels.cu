@@ -476,24 +476,34 @@ __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const doub
 // then warp 0.
 __global__ void __launch_bounds__(256) k_norm_partials(Dev d)
 {
-    __shared__ double red[8];
+    __shared__ double red[4][8];
     if (halted(d.ctrl)) return;
     const int j = blockIdx.x;
     const int p = d.blk_pos[j] + threadIdx.x;
-    double t = 0.0;
+    double t[4] = {0.0, 0.0, 0.0, 0.0};
     if (p < d.blk_pos[j + 1]) {
-        const double r = d.R[d.inv[p]];
-        t = r * r;
+        const int k = d.inv[p];
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            const double r = d.R[c * d.ld + k];
+            t[c] = r * r;
+        }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+    for (int c = 0; c < 4; c++) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t[c] += __shfl_xor_sync(kFull, t[c], o);
+        if ((threadIdx.x & 31) == 0) red[c][threadIdx.x >> 5] = t[c];
+    }
     __syncthreads();
     if (threadIdx.x < 32) {
-        double s = threadIdx.x < 8 ? red[threadIdx.x] : 0.0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
-        if (threadIdx.x == 0) d.blk[j] = s;
+        for (int c = 0; c < 4; c++) {
+            double s = threadIdx.x < 8 ? red[c][threadIdx.x] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+            if (threadIdx.x == 0) d.blk[4 * j + c] = s;
+        }
     }
 }
 
@@ -501,22 +511,36 @@ __global__ void __launch_bounds__(256) k_norm_partials(Dev d)
 // records the norm and applies the stopping test.
 __global__ void __launch_bounds__(256) k_norm_cases(Dev d)
 {
-    __shared__ double red[8];
+    __shared__ double red[4][8];
     if (halted(d.ctrl)) return;
     const int b = blockIdx.x;
     Ctrl *c = d.ctrl;
     if (frozen_state(((volatile int32_t *)c->case_state)[b])) return;  // block-uniform
-    double t = 0.0;
-    for (int j = d.case_blk[b] + threadIdx.x; j < d.case_blk[b + 1]; j += blockDim.x) t += d.blk[j];
+    double t[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int j = d.case_blk[b] + threadIdx.x; j < d.case_blk[b + 1]; j += blockDim.x)
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+        for (int q = 0; q < 4; q++) t[q] += d.blk[4 * j + q];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t[q] += __shfl_xor_sync(kFull, t[q], o);
+        if ((threadIdx.x & 31) == 0) red[q][threadIdx.x >> 5] = t[q];
+    }
     __syncthreads();
     if (threadIdx.x < 32) {
-        double s = threadIdx.x < 8 ? red[threadIdx.x] : 0.0;
+        double sq[4];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+        for (int q = 0; q < 4; q++) {
+            sq[q] = threadIdx.x < 8 ? red[q][threadIdx.x] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sq[q] += __shfl_xor_sync(kFull, sq[q], o);
+        }
+        const double s = sq[0];
         if (threadIdx.x == 0) {
+            const int n0 = c->case_it[b];
+            if (n0 < c->hist_cap)
+#pragma unroll
+                for (int q = 0; q < 4; q++) c->hist4[((size_t)b * c->hist_cap + n0) * 4 + q] = sqrt(sq[q]);
             const double nrm = sqrt(s);
             const int n = c->case_it[b];
             if (n < c->hist_cap) c->hist[(size_t)b * c->hist_cap + n] = nrm;

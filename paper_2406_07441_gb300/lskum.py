@@ -73,6 +73,7 @@ def load():
     L.lskum_density_norm_noalloc.argtypes = [vp, i32, vp, vp]
     L.lskum_batch_create.argtypes = [P(lskum_cloud), P(lskum_opts), i32, vp, P(vp)]
     L.lskum_get_case_residuals.argtypes = [vp, i32, vp, i32, P(i32)]
+    L.lskum_get_case_residuals4.argtypes = [vp, i32, vp, i32, P(i32)]
     L.lskum_get_case_forces.argtypes = [vp, i32, P(d), P(d)]
     L.lskum_get_case_info.argtypes = [vp, i32, P(i32), P(i32), P(i32), P(i32), P(i32), P(i32)]
     L.lskum_get_wall_distance.argtypes = [vp, vp]
@@ -107,7 +108,7 @@ def load():
     for f in ("lskum_create", "lskum_set_state", "lskum_set_conserved", "lskum_run", "lskum_enqueue", "lskum_wait",
               "lskum_get_state", "lskum_get_field", "lskum_get_residuals", "lskum_get_forces", "lskum_get_order",
               "lskum_get_info", "lskum_time_phases", "lskum_density_norm_noalloc", "lskum_batch_create",
-              "lskum_get_case_residuals", "lskum_get_case_forces", "lskum_get_case_info", "lskum_autotune",
+              "lskum_get_case_residuals", "lskum_get_case_residuals4", "lskum_get_case_forces", "lskum_get_case_info", "lskum_autotune",
               "lskum_get_wall_distance", "lskum_validate", "lskum_set_start_iters", "lskum_get_field_dev", "lskum_set_conserved_dev", "lskum_set_launch_shape", "lskum_mlp_create", "lskum_mlp_get_params",
               "lskum_mlp_set_params", "lskum_mlp_features", "lskum_mlp_forward", "lskum_mlp_loss_grads",
               "lskum_mlp_adam", "lskum_mlp_add_samples", "lskum_mlp_time_forward", "lskum_mlp_n_samples", "lskum_mlp_train",
@@ -191,6 +192,17 @@ class Solver:
         h = np.empty(max(n.value, 1))
         self._check(load().lskum_get_case_residuals(self._h, int(cs), _p(h), n.value, C.byref(n)))
         return h[:n.value]
+
+    def case_residuals4(self, cs):
+        """[n][4] norms of the four residual components per iteration (column 0: density)."""
+        n = C.c_int32(0)
+        self._check(load().lskum_get_case_residuals4(self._h, int(cs), None, 0, C.byref(n)))
+        h = np.empty((max(n.value, 1), 4))
+        self._check(load().lskum_get_case_residuals4(self._h, int(cs), _p(h), n.value, C.byref(n)))
+        return h[:n.value]
+
+    def residuals4(self):
+        return self.case_residuals4(0)
 
     def case_forces(self, cs):
         cl, cd = C.c_double(), C.c_double()

@@ -351,3 +351,21 @@ def test_wall_first_ordering_matches_oracle(name):
     h = s2.residuals()
     assert np.max(np.abs(h - r2["hist"]) / r2["hist"]) < 1e-10
     assert s2.info()["launches_per_iter"] >= lk.Solver(c, 0.63, 2.0, inner_iters=2).info()["launches_per_iter"]
+
+
+def test_four_component_residual_history():
+    """Column 0 of the four-component history is the density history bit for
+    bit; the last row holds the norms of the oracle's last residual (wall and
+    interior points) for all four components."""
+    lk = _lskum()
+    c = cached_cloud("jit64x32", CLOUDS["jit64x32"])
+    o = O.Oracle(c)
+    s = lk.Solver(c, 0.63, 2.0, first_order_iters=2)
+    r = o.run(o.initial_state(0.63, 2.0), 6, cfl=100.0, K=3, first_order=2)
+    assert s.run(6) == 6
+    h4 = s.residuals4()
+    assert h4.shape == (6, 4)
+    assert np.array_equal(h4[:, 0], s.residuals())
+    act = c.flag != 2
+    ref = np.sqrt(np.sum(r["R"][act] ** 2, axis=0))
+    assert np.max(np.abs(h4[-1] - ref) / ref) < 1e-10
