@@ -89,7 +89,7 @@ struct lskum_ctx {
     float *mx = nullptr, *my = nullptr, *mdw = nullptr, *mcase_mach = nullptr, *mcase_aoa = nullptr;
     double *mcase_Uinf = nullptr, *mcase_uv = nullptr;
     int cur = 0;                        // state set holding the current state
-    int32_t it_base = 0;                // ctrl->it at the start of the pending enqueue
+    int64_t hist_bound = 0;             // upper bound of every case's recorded norms
     int cur_base = 0;
     bool pending = false;
     std::string err = "no error";
@@ -1075,7 +1075,10 @@ lskum_status ensure_hist(lskum_ctx *c, int32_t need)
     c->hist = h;
     c->hist4 = h4;
     c->hist_cap = cap;
-    return LSKUM_OK;
+    Ctrl hc{};
+    lskum_status s = read_ctrl(c, &hc);  // the device copy points at the new arrays
+    if (s == LSKUM_OK) s = write_ctrl(c, hc);
+    return s;
 }
 
 lskum_status finish_state(lskum_ctx *c, bool reset_hist);
@@ -1111,7 +1114,10 @@ lskum_status finish_state(lskum_ctx *c, bool reset_hist)
     lskum_status s = read_ctrl(c, &h);
     if (s != LSKUM_OK) return s;
     if (h.error) return fail(c, LSKUM_ERR_NONPOSITIVE, "non-physical state at point %d", c->perm[h.bad_point]);
-    if (reset_hist) h.it = 0;
+    if (reset_hist) {
+        h.it = 0;
+        c->hist_bound = 0;
+    }
     h.stop = h.error = 0;
     h.bad_point = 0x7fffffff;
     s = reset_cases(c, reset_hist, true);
@@ -1152,23 +1158,15 @@ lskum_status lskum_enqueue(lskum_ctx *c, int32_t max_iters, double target_drop)
 {
     if (!c || max_iters < 0) return c ? fail(c, LSKUM_ERR_ARG, "bad argument") : LSKUM_ERR_ARG;
     if (c->pending) return fail(c, LSKUM_ERR_ARG, "an enqueued run has not been waited for");
-    Ctrl h{};
-    lskum_status s = read_ctrl(c, &h);
-    std::vector<int32_t> its;
-    if (s == LSKUM_OK) s = read_case_arrays(c, nullptr, &its);
+    // no host round trip: the history bound is kept on the host and the
+    // control block is prepared by a kernel ahead of the graph launches
+    if (c->hist_bound + max_iters > INT32_MAX / 8) return fail(c, LSKUM_ERR_ARG, "history too long");
+    lskum_status s = ensure_hist(c, (int32_t)(c->hist_bound + max_iters));
     if (s != LSKUM_OK) return s;
-    const int32_t most = *std::max_element(its.begin(), its.end());
-    s = ensure_hist(c, most + max_iters);
-    if (s != LSKUM_OK) return s;
-    h.stop = h.error = 0;
-    h.bad_point = 0x7fffffff;
-    h.target = target_drop;
+    c->hist_bound += max_iters;
     cudaError_t e = join_user(c);
-    if (e != cudaSuccess) return cuda_fail(c, e, "ordering after the caller's stream");
-    s = reset_cases(c, false, false);
-    if (s == LSKUM_OK) s = write_ctrl(c, h);
-    if (s != LSKUM_OK) return s;
-    c->it_base = h.it;
+    if (e == cudaSuccess) e = launch_prep_run(c->ctrl, target_drop, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "preparing the run");
     c->cur_base = c->cur;
     int par = c->cur;
     for (int32_t i = 0; i < max_iters && e == cudaSuccess; i++) {
@@ -1190,7 +1188,7 @@ lskum_status lskum_wait(lskum_ctx *c, int32_t *iters_done)
     Ctrl h{};
     lskum_status s = read_ctrl(c, &h);
     if (s != LSKUM_OK) return s;
-    int32_t done = h.it - c->it_base;  // iterations started (k_begin)
+    int32_t done = h.it - h.it_start;  // iterations started (k_begin)
     if (h.error) done -= 1;            // the failed iteration's update was not applied
     c->cur = (c->cur_base + done) & 1;
     if (iters_done) *iters_done = done;
@@ -1455,6 +1453,7 @@ lskum_status lskum_time_phases(lskum_ctx *c, int32_t reps, double *ms)
     if (s != LSKUM_OK) return s;
     s = ensure_hist(c, *std::max_element(its.begin(), its.end()) + reps);
     if (s != LSKUM_OK) return s;
+    c->hist_bound += reps;
     h.stop = h.error = 0;
     h.target = 0.0;
     s = reset_cases(c, false, false);

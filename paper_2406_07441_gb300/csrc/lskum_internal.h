@@ -34,6 +34,7 @@ struct Ctrl {
     int32_t error;       // lskum_status of a device-detected failure (0 = none)
     int32_t bad_point;   // smallest internal index of a non-physical update
     int32_t it;          // iterations started since the last reset (k_begin counts)
+    int32_t it_start;    // it when the current run was enqueued
     int32_t hist_cap;    // capacity of each case's history
     int32_t n_cases;
     double target;       // drop target of the current run (<= 0: none)
@@ -150,6 +151,9 @@ cudaError_t launch_phase(const Dev &d, const Launch &L, int cur, int phase, int 
                          const int32_t *lvl_act_end, const int32_t *lvl_end, cudaStream_t s);
 cudaError_t launch_init_state(const Dev &d, int cur, cudaStream_t s);
 cudaError_t launch_reset_ctrl(Ctrl *c, cudaStream_t s);
+// Prepare the control block for a run, on the device: flags cleared, drop
+// target set, it_start = it, stopped cases running again (failed ones stay).
+cudaError_t launch_prep_run(Ctrl *c, double target, cudaStream_t s);
 // Device-side reordering between the internal and the caller's point order.
 cudaError_t launch_to_caller(const double *src, const float *srcf, int comps, bool aos, int ld, int n,
                              const int32_t *inv, double *out, cudaStream_t s);

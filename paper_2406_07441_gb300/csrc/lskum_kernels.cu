@@ -888,6 +888,17 @@ __global__ void k_reset_ctrl(Ctrl *c)
     c->bad_point = 0x7fffffff;
 }
 
+__global__ void k_prep_run(Ctrl *c, double target)
+{
+    c->stop = 0;
+    c->error = 0;
+    c->bad_point = 0x7fffffff;
+    c->target = target;
+    c->it_start = c->it;
+    for (int b = 0; b < c->n_cases; b++)
+        c->case_state[b] = (c->case_state[b] == kFailed || c->case_state[b] == kFailedNow) ? kFailed : kRunning;
+}
+
 template <int TPP>
 cudaError_t enqueue_grad(const Dev &d, int cur, cudaStream_t s, int *launches)
 {
@@ -1078,6 +1089,12 @@ cudaError_t launch_from_caller(const double *in, int ld, int n, const int32_t *i
 {
     if (n <= 0) return cudaSuccess;
     k_from_caller<<<(n + 255) / 256, 256, 0, s>>>(in, ld, n, inv, U);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep_run(Ctrl *c, double target, cudaStream_t s)
+{
+    k_prep_run<<<1, 1, 0, s>>>(c, target);
     return cudaGetLastError();
 }
 
