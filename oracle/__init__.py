@@ -18,6 +18,7 @@ SRC = os.path.join(HERE, "lskum_oracle.c")
 LIB = os.path.join(HERE, "liblskum_oracle.so")
 
 JVP_EXACT, JVP_INCREMENT = 0, 1
+FARFIELD_FREESTREAM, FARFIELD_KINETIC = 0, 1
 _lib = None
 
 
@@ -32,7 +33,8 @@ def build(force: bool = False) -> str:
 
 class _Cloud(C.Structure):
     _fields_ = [("n", C.c_int32), ("x", C.c_void_p), ("y", C.c_void_p), ("flag", C.c_void_p),
-                ("nx", C.c_void_p), ("ny", C.c_void_p), ("off", C.c_void_p), ("idx", C.c_void_p)]
+                ("nx", C.c_void_p), ("ny", C.c_void_p), ("off", C.c_void_p), ("idx", C.c_void_p),
+                ("farfield", C.c_int32), ("uinf", C.c_double * 4)]
 
 
 def lib():
@@ -166,10 +168,12 @@ def freestream(mach, aoa_deg):
 class Oracle:
     """One cloud, the canonical sweep order, and the steps of Alg. 1 on it."""
 
-    def __init__(self, cloud, ordering=0):
+    def __init__(self, cloud, ordering=0, farfield=FARFIELD_FREESTREAM, mach=0.0, aoa_deg=0.0):
         """ordering 0: the sweep order of Alg. 6 (points stably sorted by
         colour); 1: Alg. 4 (wall points by colour, then interior points by
-        colour, then outer points)."""
+        colour, then outer points).  farfield 0: outer points frozen at the
+        free stream; 1: the kinetic far field with the free stream of
+        (mach, aoa_deg) and the cloud's outward normals at outer points."""
         self.cloud = cloud
         self.n = cloud.n
         self._keep = [np.ascontiguousarray(cloud.x, np.float64), np.ascontiguousarray(cloud.y, np.float64),
@@ -178,6 +182,11 @@ class Oracle:
                       np.ascontiguousarray(cloud.nbr_idx, np.int32)]
         k = self._keep
         self.c = _Cloud(self.n, *[a.ctypes.data for a in k])
+        self.farfield = int(farfield)
+        self.c.farfield = self.farfield
+        if self.farfield == FARFIELD_KINETIC:
+            for j, v in enumerate(freestream(mach, aoa_deg)):
+                self.c.uinf[j] = v
         self.colour = np.zeros(self.n, np.int32)
         self.order = np.zeros(self.n, np.int32)
         self.rank = np.zeros(self.n, np.int32)

@@ -48,6 +48,21 @@
  *       impulsive free-stream start otherwise drives the unlimited second-order
  *       reconstruction out of the Maxwellian range (q~_4 >= 0) at the
  *       leading edge of jittered clouds.
+ *   R12 Kinetic far field (an option; the paper's sweeps visit outer points,
+ *       Alg. 2 and 4, but it states no outer-boundary formula).  Outer points
+ *       are then unknowns like the others, in the local frame (t, n), n the
+ *       unit normal out of the domain and t = (n_y, -n_x).  Their residual is
+ *       the sum of the t+, t- and n+ split derivatives over their (inside)
+ *       neighbours, plus the n- derivative against ghost points that hold
+ *       the free stream at the mirror images of the n+ neighbours across the
+ *       tangent line: molecules entering the domain carry the free-stream
+ *       Maxwellian.  Mirroring negates the n-derivative weights, so that term
+ *       is LS_3(1) (G_n^-(U_inf) - G_n^-(U_0)) with LS_3(1) = -LS_2(1) and
+ *       sum |w| equal to that of the n+ stencil; it is first order (the
+ *       point's own conserved state, no defect correction).  On a 1D stencil
+ *       it is the upwind difference against a free-stream ghost cell.  The
+ *       sweeps, the update (no projection) and the norm then include outer
+ *       points.
  */
 #include <math.h>
 #include <stdint.h>
@@ -204,18 +219,38 @@ void o_split_jvp_increment(const double *U, const double *dUin, double dx, doubl
 /* Cloud, split stencils and frames                                           */
 /* ------------------------------------------------------------------------- */
 
+/* farfield: 0 = outer points frozen at the free stream (R8); 1 = the kinetic
+ * far field (R12), with uinf the free-stream conserved state and (nx, ny) the
+ * outward unit normals at outer points. */
 typedef struct {
     int32_t n;
     const double *x, *y;
     const uint8_t *flag;
     const double *nx, *ny;
     const int32_t *off, *idx;
+    int32_t farfield;
+    double uinf[4];
 } o_cloud;
 
-/* Frame of point p: e1 = (1,0), e2 = (0,1) in the interior; (t, n) at the wall. */
+/* Is point p an unknown of the iteration?  (Outer points only with R12.) */
+static int is_active(const o_cloud *c, int p)
+{
+    return c->flag[p] != PT_OUTER || c->farfield == 1;
+}
+
+/* Stencil kind: 0 interior, 1 wall, 2 outer under the kinetic far field. */
+static int kind_of(const o_cloud *c, int p)
+{
+    if (c->flag[p] == PT_WALL) return 1;
+    if (c->flag[p] == PT_OUTER && c->farfield == 1) return 2;
+    return 0;
+}
+
+/* Frame of point p: e1 = (1,0), e2 = (0,1) in the interior; (t, n) at the
+ * wall (n into the fluid) and at kinetic outer points (n out of the domain). */
 static void frame(const o_cloud *c, int p, double *e1x, double *e1y, double *e2x, double *e2y)
 {
-    if (c->flag[p] == PT_WALL) {
+    if (kind_of(c, p) != 0) {
         *e1x = c->ny[p]; *e1y = -c->nx[p];
         *e2x = c->nx[p]; *e2y = c->ny[p];
     } else {
@@ -228,17 +263,24 @@ static void frame(const o_cloud *c, int p, double *e1x, double *e1y, double *e2x
  * Split sub-stencils of a point, in a fixed order:
  *   interior: 0 = e1+ (a<0), 1 = e1- (a>0), 2 = e2+ (b<0), 3 = e2- (b>0)
  *   wall:     0 = t+  (a<0), 1 = t-  (a>0),                 3 = n-  (b>0)
+ *   outer:    0 = t+  (a<0), 1 = t-  (a>0), 2 = n+  (b<0)   (3: the ghosts, R12)
  * a = Delta r . e1, b = Delta r . e2.  member() returns, for neighbour
  * offsets (a, b), the sub-stencils it joins (at most one per direction).
  */
-static int members(int is_wall, double a, double b, int *s)
+static int members(int kind, double a, double b, int *s)
 {
     int m = 0;
     if (a < 0.0) s[m++] = 0;
     else if (a > 0.0) s[m++] = 1;
-    if (b < 0.0) { if (!is_wall) s[m++] = 2; }
-    else if (b > 0.0) s[m++] = 3;
+    if (b < 0.0) { if (kind != 1) s[m++] = 2; }
+    else if (b > 0.0) { if (kind != 2) s[m++] = 3; }
     return m;
+}
+
+/* Is sub-stencil s formed from the point's neighbours? */
+static int real_sub(int kind, int s)
+{
+    return !((kind == 1 && s == 2) || (kind == 2 && s == 3));
 }
 
 static const int SUB_SIGN[4] = { +1, -1, +1, -1 };
@@ -396,18 +438,19 @@ void o_q_gradients(const o_cloud *c, const double *q, int K, double *qx, double 
  *   split flux G_s evaluated at the modified q-variables of Eq. 15,
  *   Delta G_i = G_s(q~_i) - G_s(q~_0), q~ defined per neighbour pair;
  *   D_0 = 1/dt_0 - sum_s sign_s rho_s LS_s(1)  (Eq. 26 with Eq. 33-34).
- * Outer points get R = 0, D = 1.  R: [4N], D: [N].
+ * Under the kinetic far field outer points add the ghost term of R12 as
+ * sub-stencil 3; otherwise they get R = 0, D = 1.  R: [4N], D: [N].
  */
 void o_residual(const o_cloud *c, const double *q, const double *qx, const double *qy,
                 const double *U, double cfl, double *R, double *D)
 {
     for (int32_t p = 0; p < c->n; p++) {
-        if (c->flag[p] == PT_OUTER) {
+        if (!is_active(c, p)) {
             for (int k = 0; k < 4; k++) R[4 * p + k] = 0.0;
             D[p] = 1.0;
             continue;
         }
-        int is_wall = c->flag[p] == PT_WALL;
+        int kind = kind_of(c, p);
         double e1x, e1y, e2x, e2y;
         frame(c, p, &e1x, &e1y, &e2x, &e2y);
         double sdd[4] = { 0 }, spp[4] = { 0 }, sdp[4] = { 0 }, sd1[4] = { 0 }, sp1[4] = { 0 };
@@ -422,7 +465,7 @@ void o_residual(const o_cloud *c, const double *q, const double *qx, const doubl
             double a = dx * e1x + dy * e1y;
             double b = dx * e2x + dy * e2y;
             int s[2];
-            int m = members(is_wall, a, b, s);
+            int m = members(kind, a, b, s);
             if (m == 0) continue;
             double qti[4], qt0[4];
             for (int k = 0; k < 4; k++) {
@@ -461,7 +504,7 @@ void o_residual(const o_cloud *c, const double *q, const double *qx, const doubl
             double a = dx * e1x + dy * e1y;
             double b = dx * e2x + dy * e2y;
             int s[2];
-            int m = members(is_wall, a, b, s);
+            int m = members(kind, a, b, s);
             for (int j = 0; j < m; j++) {
                 int ss = s[j];
                 double d, dp;
@@ -470,6 +513,7 @@ void o_residual(const o_cloud *c, const double *q, const double *qx, const doubl
                 sabsw[ss] += fabs((spp[ss] * d - sdp[ss] * dp) / det);
             }
         }
+        if (kind == 2) sabsw[3] = sabsw[2]; /* the mirrored ghosts (R12) */
         double rho, u, v, pr;
         o_cons_to_prim(&U[4 * p], &rho, &u, &v, &pr);
         double snd = sqrt(GAMMA * pr / rho);
@@ -477,12 +521,24 @@ void o_residual(const o_cloud *c, const double *q, const double *qx, const doubl
         double Dp = 1.0 / dt;
         double Ddom = 0.0;
         double Rp[4] = { 0, 0, 0, 0 };
+        double ls1_2 = 0.0;
         for (int ss = 0; ss < 4; ss++) {
-            if (is_wall && ss == 2) continue;
-            double det = sdd[ss] * spp[ss] - sdp[ss] * sdp[ss];
-            for (int k = 0; k < 4; k++)
-                Rp[k] += (spp[ss] * sdG[ss][k] - sdp[ss] * spG[ss][k]) / det;
-            double ls1 = (spp[ss] * sd1[ss] - sdp[ss] * sp1[ss]) / det;
+            if (kind == 1 && ss == 2) continue;
+            double ls1;
+            if (real_sub(kind, ss)) {
+                double det = sdd[ss] * spp[ss] - sdp[ss] * sdp[ss];
+                for (int k = 0; k < 4; k++)
+                    Rp[k] += (spp[ss] * sdG[ss][k] - sdp[ss] * spG[ss][k]) / det;
+                ls1 = (spp[ss] * sd1[ss] - sdp[ss] * sp1[ss]) / det;
+                if (ss == 2) ls1_2 = ls1;
+            } else {
+                /* R12: LS_3(1) (G_n^-(U_inf) - G_n^-(U_0)), LS_3(1) = -LS_2(1) */
+                ls1 = -ls1_2;
+                double Gi[4], G0[4];
+                o_split_flux_cons(c->uinf, e2x, e2y, -1, Gi);
+                o_split_flux_cons(&U[4 * p], e2x, e2y, -1, G0);
+                for (int k = 0; k < 4; k++) Rp[k] += ls1 * (Gi[k] - G0[k]);
+            }
             double ddx = ss < 2 ? e1x : e2x, ddy = ss < 2 ? e1y : e2y;
             double ud = u * ddx + v * ddy;
             double rs;
@@ -520,7 +576,7 @@ static void wall_project(const o_cloud *c, int p, double *w)
 static void offdiag(const o_cloud *c, int p, const int32_t *rank, int lower,
                     const double *U, const double *dW, int jvp, double *out)
 {
-    int is_wall = c->flag[p] == PT_WALL;
+    int kind = kind_of(c, p);
     double e1x, e1y, e2x, e2y;
     frame(c, p, &e1x, &e1y, &e2x, &e2y);
     double sdd[4] = { 0 }, spp[4] = { 0 }, sdp[4] = { 0 };
@@ -532,7 +588,7 @@ static void offdiag(const o_cloud *c, int p, const int32_t *rank, int lower,
         double a = dx * e1x + dy * e1y;
         double b = dx * e2x + dy * e2y;
         int s[2];
-        int m = members(is_wall, a, b, s);
+        int m = members(kind, a, b, s);
         int side = lower ? (rank[i] < rank[p]) : (rank[i] > rank[p]);
         for (int j = 0; j < m; j++) {
             int ss = s[j];
@@ -554,7 +610,7 @@ static void offdiag(const o_cloud *c, int p, const int32_t *rank, int lower,
     }
     for (int k = 0; k < 4; k++) out[k] = 0.0;
     for (int ss = 0; ss < 4; ss++) {
-        if (is_wall && ss == 2) continue;
+        if (!real_sub(kind, ss)) continue;
         double det = sdd[ss] * spp[ss] - sdp[ss] * sdp[ss];
         for (int k = 0; k < 4; k++)
             out[k] += (spp[ss] * sdJ[ss][k] - sdp[ss] * spJ[ss][k]) / det;
@@ -563,7 +619,7 @@ static void offdiag(const o_cloud *c, int p, const int32_t *rank, int lower,
 
 /* Forward: dU*_0 = -(R_0 + L dU*)/D_0 over the order; backward, in reverse:
  * dU_0 = dU*_0 - (U dU)/D_0.  Wall increments are projected (reading R4).
- * dUs, dU: [4N] outputs (outer points 0). */
+ * dUs, dU: [4N] outputs (outer points 0 unless R12). */
 void o_sweeps(const o_cloud *c, const int32_t *order, const int32_t *rank, const double *U,
               const double *R, const double *D, int jvp, double *dUs, double *dU)
 {
@@ -571,7 +627,7 @@ void o_sweeps(const o_cloud *c, const int32_t *order, const int32_t *rank, const
     for (int64_t k = 0; k < 4 * (int64_t)n; k++) { dUs[k] = 0.0; dU[k] = 0.0; }
     for (int32_t pos = 0; pos < n; pos++) {
         int32_t p = order[pos];
-        if (c->flag[p] == PT_OUTER) continue;
+        if (!is_active(c, p)) continue;
         double L[4];
         offdiag(c, p, rank, 1, U, dUs, jvp, L);
         double w[4];
@@ -581,7 +637,7 @@ void o_sweeps(const o_cloud *c, const int32_t *order, const int32_t *rank, const
     }
     for (int32_t pos = n - 1; pos >= 0; pos--) {
         int32_t p = order[pos];
-        if (c->flag[p] == PT_OUTER) continue;
+        if (!is_active(c, p)) continue;
         double Uc[4];
         offdiag(c, p, rank, 0, U, dU, jvp, Uc);
         double w[4];
@@ -600,7 +656,7 @@ int32_t o_update(const o_cloud *c, double *U, const double *dU, double *q)
 {
     int32_t bad = -1;
     for (int32_t p = 0; p < c->n; p++) {
-        if (c->flag[p] != PT_OUTER) {
+        if (is_active(c, p)) {
             for (int k = 0; k < 4; k++) U[4 * p + k] += dU[4 * p + k];
             if (c->flag[p] == PT_WALL) wall_project(c, p, &U[4 * p]);
         }
@@ -615,11 +671,12 @@ int32_t o_update(const o_cloud *c, double *U, const double *dU, double *q)
     return bad;
 }
 
+/* Over the points the iteration updates (R9; with R12 the outer points too). */
 double o_residual_norm(const o_cloud *c, const double *R)
 {
     double s = 0.0;
     for (int32_t p = 0; p < c->n; p++)
-        if (c->flag[p] != PT_OUTER) s += R[4 * p] * R[4 * p];
+        if (is_active(c, p)) s += R[4 * p] * R[4 * p];
     return sqrt(s);
 }
 
@@ -707,17 +764,18 @@ double o_cfl_at(double cfl, double ramp, int32_t n)
  * evaluated with the previous iteration's increment (exact unsplit Jacobian
  * products, here the sum of the exact split ones: G = G+ + G-) and moved to
  * the right-hand side.  Sub-stencils s and frames as in o_residual (wall:
- * t+, t-, n-).  With Sprev = NULL, S is not computed.
+ * t+, t-, n-; kinetic outer: t+, t-, n+ and the ghosts of R12 with
+ * LS_3(1) = -LS_2(1)).  With dUprev = NULL, S is not computed.
  */
 void o_manish_terms(const o_cloud *c, const double *U, double cfl, const double *dUprev, double *D, double *S)
 {
     for (int32_t p = 0; p < c->n; p++) {
         for (int k = 0; k < 4; k++) S[4 * p + k] = 0.0;
-        if (c->flag[p] == PT_OUTER) {
+        if (!is_active(c, p)) {
             D[p] = 1.0;
             continue;
         }
-        int is_wall = c->flag[p] == PT_WALL;
+        int kind = kind_of(c, p);
         double e1x, e1y, e2x, e2y;
         frame(c, p, &e1x, &e1y, &e2x, &e2y);
         double sdd[4] = { 0 }, spp[4] = { 0 }, sdp[4] = { 0 }, sd1[4] = { 0 }, sp1[4] = { 0 };
@@ -729,7 +787,7 @@ void o_manish_terms(const o_cloud *c, const double *U, double cfl, const double 
             if (dist < dmin) dmin = dist;
             double a = dx * e1x + dy * e1y, b = dx * e2x + dy * e2y;
             int sub[2];
-            int m = members(is_wall, a, b, sub);
+            int m = members(kind, a, b, sub);
             for (int j = 0; j < m; j++) {
                 double d, dp;
                 sub_offsets(sub[j], a, b, &d, &dp);
@@ -755,10 +813,17 @@ void o_manish_terms(const o_cloud *c, const double *U, double cfl, const double 
             o_split_jvp_exact(&U[4 * p], &dUprev[4 * p], e2x, e2y, -1, jm);
             for (int k = 0; k < 4; k++) A2[k] = jp[k] + jm[k];
         }
+        double ls1_2 = 0.0;
         for (int ss = 0; ss < 4; ss++) {
-            if (is_wall && ss == 2) continue;
-            double det = sdd[ss] * spp[ss] - sdp[ss] * sdp[ss];
-            double ls1 = (spp[ss] * sd1[ss] - sdp[ss] * sp1[ss]) / det;
+            if (kind == 1 && ss == 2) continue;
+            double ls1;
+            if (real_sub(kind, ss)) {
+                double det = sdd[ss] * spp[ss] - sdp[ss] * sdp[ss];
+                ls1 = (spp[ss] * sd1[ss] - sdp[ss] * sp1[ss]) / det;
+                if (ss == 2) ls1_2 = ls1;
+            } else {
+                ls1 = -ls1_2; /* the ghosts of R12 */
+            }
             double ud = ss < 2 ? u * e1x + v * e1y : u * e2x + v * e2y;
             Dp += 0.5 * (fabs(ud) + snd) * fabs(ls1);
             for (int k = 0; k < 4; k++) S[4 * p + k] -= 0.5 * ls1 * (ss < 2 ? A1[k] : A2[k]);
@@ -773,13 +838,13 @@ void o_manish_terms(const o_cloud *c, const double *U, double cfl, const double 
  * step of the implicit scheme, dt_0 = CFL min_i |r_i - r_0| / (|u_0| + a_0):
  * dU_0 = -dt_0 R_0 at wall and interior points, with the normal momentum
  * removed at wall points (reading R4, as for the implicit increments); outer
- * points keep dU = 0.  D[p] receives 1/dt_0 (1 at outer points).
+ * points keep dU = 0 unless R12.  D[p] receives 1/dt_0 (1 at frozen points).
  */
 void o_explicit_step(const o_cloud *c, const double *U, double cfl, const double *R, double *D, double *dU)
 {
     for (int32_t p = 0; p < c->n; p++) {
         for (int k = 0; k < 4; k++) dU[4 * p + k] = 0.0;
-        if (c->flag[p] == PT_OUTER) {
+        if (!is_active(c, p)) {
             D[p] = 1.0;
             continue;
         }

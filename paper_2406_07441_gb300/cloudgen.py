@@ -27,6 +27,12 @@ first, capped at 20, at least 8), with neighbours seen through the aerofoil
 rejected.  Either kind is augmented with further nearby points until every
 split sub-stencil is well posed, so that the least-squares systems of the
 method never degenerate.
+
+Outer points carry their unit normal out of the domain (radial from (0.5, 0)
+on the O-grids, the side's normal or the corner's diagonal on the boxes).
+With ``kinetic_outer=True`` their t+, t- and n+ split sub-stencils in the
+frame (t, n), t = (n_y, -n_x), are made well posed too, as the kinetic far
+field needs.
 """
 from __future__ import annotations
 
@@ -44,7 +50,8 @@ class Cloud:
     x: np.ndarray        # f64[N]
     y: np.ndarray        # f64[N]
     flag: np.ndarray     # u8[N]: 0 interior, 1 wall, 2 outer
-    nx: np.ndarray       # f64[N]: unit wall normal into the fluid (0 elsewhere)
+    nx: np.ndarray       # f64[N]: unit normal, into the fluid at wall points and
+                         # out of the domain at outer points (0 elsewhere)
     ny: np.ndarray
     nbr_off: np.ndarray  # i32[N+1] CSR row offsets
     nbr_idx: np.ndarray  # i32[nnz] CSR neighbour indices, no self, no duplicates
@@ -114,18 +121,30 @@ def _local_spacing(X, Y):
 # geometric well-posedness of the split sub-stencils (a property of the input)
 # ---------------------------------------------------------------------------
 
-def _frame(cloud_x, cloud_y, flag, nx, ny, p):
+def _kind(flag, p, kinetic_outer):
+    """Stencil kind: 0 interior, 1 wall, 2 outer under the kinetic far field, -1 frozen outer."""
     if flag[p] == WALL:
+        return 1
+    if flag[p] == OUTER:
+        return 2 if kinetic_outer else -1
+    return 0
+
+
+def _frame(cloud_x, cloud_y, flag, nx, ny, p, kinetic_outer=False):
+    if _kind(flag, p, kinetic_outer) > 0:
         return (ny[p], -nx[p]), (nx[p], ny[p])
     return (1.0, 0.0), (0.0, 1.0)
 
 
-def _substencils_ok(dx, dy, is_wall, e1, e2, tol=1e-6):
-    """Each split sub-stencil needs >= 2 points and a well-conditioned 2x2 system."""
+def _substencils_ok(dx, dy, kind, e1, e2, tol=1e-6):
+    """Each split sub-stencil needs >= 2 points and a well-conditioned 2x2 system
+    (kind 1, wall: t+, t-, n-; kind 2, kinetic outer: t+, t-, n+)."""
     a = dx * e1[0] + dy * e1[1]
     b = dx * e2[0] + dy * e2[1]
-    if is_wall:
+    if kind == 1:
         sets = [(a < 0, a, b), (a > 0, a, b), (b > 0, b, a)]
+    elif kind == 2:
+        sets = [(a < 0, a, b), (a > 0, a, b), (b < 0, b, a)]
     else:
         sets = [(a < 0, a, b), (a > 0, a, b), (b < 0, b, a), (b > 0, b, a)]
     for m, d, dp in sets:
@@ -244,7 +263,7 @@ def _csr(rows):
     return off.astype(np.int32), idx.astype(np.int32)
 
 
-def _stencils_ok_all(x, y, flag, nx, ny, rows, tol=1e-6):
+def _stencils_ok_all(x, y, flag, nx, ny, rows, tol=1e-6, kinetic_outer=False):
     """Vectorised well-posedness of every point's stencil (same tests as the
     per-point functions above): boolean per point."""
     n = x.shape[0]
@@ -254,46 +273,52 @@ def _stencils_ok_all(x, y, flag, nx, ny, rows, tol=1e-6):
     dx = x[nb] - x[owner]
     dy = y[nb] - y[owner]
     wall = flag == WALL
+    framed = wall | ((flag == OUTER) if kinetic_outer else np.zeros(n, dtype=bool))
+    outer_k = framed & ~wall
 
     def seg(v):
         return np.bincount(owner, weights=v, minlength=n)
 
     sxx, syy, sxy = seg(dx * dx), seg(dy * dy), seg(dx * dy)
     ok = (deg >= 2) & ((sxx * syy - sxy * sxy) > tol * sxx * syy)
-    e1x = np.where(wall, ny, 1.0)[owner]
-    e1y = np.where(wall, -nx, 0.0)[owner]
-    e2x = np.where(wall, nx, 0.0)[owner]
-    e2y = np.where(wall, ny, 1.0)[owner]
+    e1x = np.where(framed, ny, 1.0)[owner]
+    e1y = np.where(framed, -nx, 0.0)[owner]
+    e2x = np.where(framed, nx, 0.0)[owner]
+    e2y = np.where(framed, ny, 1.0)[owner]
     a = dx * e1x + dy * e1y
     b = dx * e2x + dy * e2y
     wo = wall[owner]
-    sets = [(a < 0, a, b), (a > 0, a, b), ((b < 0) & ~wo, b, a), (b > 0, b, a)]
+    ko = outer_k[owner]
+    sets = [(a < 0, a, b), (a > 0, a, b), ((b < 0) & ~wo, b, a), ((b > 0) & ~ko, b, a)]
     for j, (m, d, dp) in enumerate(sets):
         mf = m.astype(np.float64)
         cnt = seg(mf)
         sdd, spp, sdp = seg(mf * d * d), seg(mf * dp * dp), seg(mf * d * dp)
         good = (cnt >= 2) & ((sdd * spp - sdp * sdp) > tol * sdd * spp)
-        need = flag != OUTER
+        need = (flag != OUTER) | outer_k
         if j == 2:
             need = need & ~wall
+        if j == 3:
+            need = need & ~outer_k
         ok &= good | ~need
     return ok
 
 
-def _fix_stencils(x, y, flag, nx, ny, rows, cand_fn, body=None):
+def _fix_stencils(x, y, flag, nx, ny, rows, cand_fn, body=None, kinetic_outer=False):
     """Augment stencils (nearest-first candidates) until every sub-stencil is well posed."""
     bad = 0
-    ok_all = _stencils_ok_all(x, y, flag, nx, ny, rows)
+    ok_all = _stencils_ok_all(x, y, flag, nx, ny, rows, kinetic_outer=kinetic_outer)
     for p in np.flatnonzero(~ok_all):
         p = int(p)
         r = rows[p]
         dx = x[r] - x[p]
         dy = y[r] - y[p]
-        if flag[p] == OUTER:
+        kind = _kind(flag, p, kinetic_outer)
+        if kind < 0:
             ok = _full_ok(dx, dy)
         else:
-            e1, e2 = _frame(x, y, flag, nx, ny, p)
-            ok = _full_ok(dx, dy) and _substencils_ok(dx, dy, flag[p] == WALL, e1, e2)
+            e1, e2 = _frame(x, y, flag, nx, ny, p, kinetic_outer)
+            ok = _full_ok(dx, dy) and _substencils_ok(dx, dy, kind, e1, e2)
         if ok:
             continue
         bad += 1
@@ -310,11 +335,11 @@ def _fix_stencils(x, y, flag, nx, ny, rows, cand_fn, body=None):
             have.add(q)
             dx = x[r] - x[p]
             dy = y[r] - y[p]
-            if flag[p] == OUTER:
+            if kind < 0:
                 ok = _full_ok(dx, dy)
             else:
-                e1, e2 = _frame(x, y, flag, nx, ny, p)
-                ok = _full_ok(dx, dy) and _substencils_ok(dx, dy, flag[p] == WALL, e1, e2)
+                e1, e2 = _frame(x, y, flag, nx, ny, p, kinetic_outer)
+                ok = _full_ok(dx, dy) and _substencils_ok(dx, dy, kind, e1, e2)
             if ok:
                 break
         if not ok:
@@ -323,7 +348,13 @@ def _fix_stencils(x, y, flag, nx, ny, rows, cand_fn, body=None):
     return rows, bad
 
 
-def naca0012_block(n_i: int = 160, n_j: int = 64) -> Cloud:
+def _outer_normals(x, y):
+    """Unit normals of the far-field circle about (0.5, 0), out of the domain."""
+    r = np.hypot(x - 0.5, y)
+    return (x - 0.5) / r, y / r
+
+
+def naca0012_block(n_i: int = 160, n_j: int = 64, kinetic_outer: bool = False) -> Cloud:
     """Structured O-grid cloud with 3x3 index-block stencils (8 neighbours)."""
     X, Y = _ogrid(n_i, n_j)
     x = X.ravel().copy()
@@ -335,6 +366,7 @@ def naca0012_block(n_i: int = 160, n_j: int = 64) -> Cloud:
     nx = np.zeros(n)
     ny = np.zeros(n)
     nx[:n_i], ny[:n_i] = _wall_normals(x[:n_i], y[:n_i])
+    nx[-n_i:], ny[-n_i:] = _outer_normals(x[-n_i:], y[-n_i:])
     rows = []
     for j in range(n_j):
         for i in range(n_i):
@@ -360,15 +392,17 @@ def naca0012_block(n_i: int = 160, n_j: int = 64) -> Cloud:
 
     widx = np.full(n, -1)
     widx[:n_i] = np.arange(n_i)
-    rows, bad = _fix_stencils(x, y, flag, nx, ny, rows, cand, body=(x[:n_i], y[:n_i], widx))
+    rows, bad = _fix_stencils(x, y, flag, nx, ny, rows, cand, body=(x[:n_i], y[:n_i], widx),
+                              kinetic_outer=kinetic_outer)
     off, idx = _csr(rows)
     return Cloud(x, y, flag, nx, ny, off, idx,
-                 dict(kind="block", n_i=n_i, n_j=n_j, augmented=bad))
+                 dict(kind="block", n_i=n_i, n_j=n_j, augmented=bad, kinetic_outer=kinetic_outer))
 
 
 def naca0012_jittered(n_i: int = 640, n_j: int = 256, jitter: float = 0.15,
                       remove_frac: float = 0.10, seed: int = BASE_SEED + 2,
-                      radius_factor: float = 2.5, k_min: int = 8, k_max: int = 20) -> Cloud:
+                      radius_factor: float = 2.5, k_min: int = 8, k_max: int = 20,
+                      kinetic_outer: bool = False) -> Cloud:
     """Jittered O-grid cloud with random interior removal and radius/kNN stencils."""
     from scipy.spatial import cKDTree
 
@@ -399,6 +433,7 @@ def naca0012_jittered(n_i: int = 640, n_j: int = 256, jitter: float = 0.15,
     nx = np.zeros(n)
     ny = np.zeros(n)
     nx[:n_i], ny[:n_i] = _wall_normals(x[:n_i], y[:n_i])
+    nx[-n_i:], ny[-n_i:] = _outer_normals(x[-n_i:], y[-n_i:])
     widx = np.full(n, -1)
     widx[:n_i] = np.arange(n_i)
     wx, wy = x[:n_i].copy(), y[:n_i].copy()
@@ -430,15 +465,15 @@ def naca0012_jittered(n_i: int = 640, n_j: int = 256, jitter: float = 0.15,
     flat = nbv[keep]
     offs = np.concatenate([[0], np.cumsum(m)])
     rows = [flat[offs[p]:offs[p + 1]].tolist() for p in range(n)]
-    rows, bad = _fix_stencils(x, y, flag, nx, ny, rows, lambda p: nbv[p][:nvalid[p]])
+    rows, bad = _fix_stencils(x, y, flag, nx, ny, rows, lambda p: nbv[p][:nvalid[p]], kinetic_outer=kinetic_outer)
     off, idx = _csr(rows)
     return Cloud(x, y, flag, nx, ny, off, idx,
                  dict(kind="jittered", n_i=n_i, n_j=n_j, jitter=jitter, remove_frac=remove_frac,
-                      seed=seed, removed=n_rm, augmented=bad))
+                      seed=seed, removed=n_rm, augmented=bad, kinetic_outer=kinetic_outer))
 
 
 def cartesian_box(n: int = 7, m: int = 7, jitter: float = 0.2, seed: int = BASE_SEED + 7,
-                  wall_bottom: bool = False) -> Cloud:
+                  wall_bottom: bool = False, kinetic_outer: bool = False) -> Cloud:
     """Small jittered Cartesian patch; the frame is outer (or a flat wall at the bottom).
 
     Used for tiny oracle checks (dense LU-SGS on ~50 points, mirror symmetry)."""
@@ -452,20 +487,27 @@ def cartesian_box(n: int = 7, m: int = 7, jitter: float = 0.2, seed: int = BASE_
     x, y = X.ravel(), Y.ravel()
     N = x.shape[0]
     flag = np.where(inner.ravel(), INTERIOR, OUTER).astype(np.uint8)
-    nx = np.zeros(N)
-    ny = np.zeros(N)
+    Ii, Jj = I.ravel(), J.ravel()
+    ox = np.where(Ii == 0, -1.0, np.where(Ii == n - 1, 1.0, 0.0))
+    oy = np.where(Jj == 0, -1.0, np.where(Jj == m - 1, 1.0, 0.0))
+    ol = np.hypot(ox, oy)
+    outer = flag == OUTER
+    nx = np.where(outer, ox / np.where(ol > 0, ol, 1.0), 0.0)
+    ny = np.where(outer, oy / np.where(ol > 0, ol, 1.0), 0.0)
     if wall_bottom:
         wb = (J.ravel() == 0) & (I.ravel() > 0) & (I.ravel() < n - 1)
         flag[wb] = WALL
+        nx[wb] = 0.0
         ny[wb] = 1.0
     from scipy.spatial import cKDTree
     tree = cKDTree(np.stack([x, y], 1))
     d, nb = tree.query(np.stack([x, y], 1), k=min(N, 13))
     rows = [[int(q) for q in nb[p, 1:9]] for p in range(N)]
     cand = [nb[p, 1:] for p in range(N)]
-    rows, bad = _fix_stencils(x, y, flag, nx, ny, rows, lambda p: cand[p])
+    rows, bad = _fix_stencils(x, y, flag, nx, ny, rows, lambda p: cand[p], kinetic_outer=kinetic_outer)
     off, idx = _csr(rows)
-    return Cloud(x, y, flag, nx, ny, off, idx, dict(kind="box", n=n, m=m, seed=seed, augmented=bad))
+    return Cloud(x, y, flag, nx, ny, off, idx,
+                 dict(kind="box", n=n, m=m, seed=seed, augmented=bad, kinetic_outer=kinetic_outer))
 
 
 # Workloads of the benchmark and the parity tests (sizes and flow conditions).

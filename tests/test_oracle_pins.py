@@ -340,9 +340,9 @@ def test_residual_converges_to_euler_divergence_second_order():
 # O8: sweeps equal the dense LU-SGS solve of Eq. 26-27 (brute force)
 # ---------------------------------------------------------------------------
 
-def _dense_lusgs(c, o, U, R, D):
+def _dense_lusgs(c, o, U, R, D, kinetic=False):
     n = c.n
-    act = np.flatnonzero(c.flag != cg.OUTER)
+    act = np.flatnonzero((c.flag != cg.OUTER) | kinetic)
     pos = {p: k for k, p in enumerate(act)}
     m = len(act)
     L = np.zeros((4 * m, 4 * m))
@@ -353,25 +353,29 @@ def _dense_lusgs(c, o, U, R, D):
         dx = c.x[r] - c.x[p]
         dy = c.y[r] - c.y[p]
         wall = c.flag[p] == cg.WALL
-        if wall:
+        outer = c.flag[p] == cg.OUTER
+        if wall or outer:
             e1 = (c.ny[p], -c.nx[p])
             e2 = (c.nx[p], c.ny[p])
+        else:
+            e1, e2 = (1.0, 0.0), (0.0, 1.0)
+        if wall:
             nn = np.array([c.nx[p], c.ny[p]])
             k = pos[p]
             P[4 * k + 1:4 * k + 3, 4 * k + 1:4 * k + 3] = np.eye(2) - np.outer(nn, nn)
-        else:
-            e1, e2 = (1.0, 0.0), (0.0, 1.0)
         a = dx * e1[0] + dy * e1[1]
         b = dx * e2[0] + dy * e2[1]
-        subs = [(a < 0, a, b, e1, +1), (a > 0, a, b, e1, -1), (b > 0, b, a, e2, -1)]
+        subs = [(a < 0, a, b, e1, +1), (a > 0, a, b, e1, -1)]
         if not wall:
-            subs.insert(2, (b < 0, b, a, e2, +1))
+            subs.append((b < 0, b, a, e2, +1))
+        if not outer:  # a kinetic outer point's n- side holds the constant free-stream ghosts
+            subs.append((b > 0, b, a, e2, -1))
         for msk, dd, dp, e, sg in subs:
             sdd, spp, sdp = np.sum(dd[msk] ** 2), np.sum(dp[msk] ** 2), np.sum(dd[msk] * dp[msk])
             det = sdd * spp - sdp * sdp
             for i, di, pi in zip(r[msk], dd[msk], dp[msk]):
                 w = (spp * di - sdp * pi) / det
-                if c.flag[i] == cg.OUTER:
+                if c.flag[i] == cg.OUTER and not kinetic:
                     continue
                 J = np.stack([O.split_jvp(U[i], np.eye(4)[k], e[0], e[1], sg) for k in range(4)], 1)
                 tgt = L if o.rank[i] < o.rank[p] else Uu
@@ -412,6 +416,112 @@ def test_sweeps_equal_dense_lusgs(wall, ordering):
     assert scale > 1e-6
     assert np.allclose(dUs, ds_ref, rtol=0, atol=1e-12 * np.abs(ds_ref).max())
     assert np.allclose(dU, d_ref, rtol=0, atol=1e-12 * scale)
+
+
+# ---------------------------------------------------------------------------
+# Kinetic far field (outer points updated; ghosts hold the free stream)
+# ---------------------------------------------------------------------------
+
+def _kinetic_smooth_state(c, Uinf, amp=0.05):
+    x, y = c.x, c.y
+    rho = 1 + amp * np.sin(3 * x + 1) * np.cos(2 * y)
+    u = Uinf[1] + amp * np.cos(2 * x - 3 * y)
+    v = Uinf[2] + amp * np.sin(x + 2 * y)
+    p = 1 / GAMMA + amp * np.cos(3 * x) * np.sin(2 * y + 0.3)
+    return np.stack([rho, rho * u, rho * v, p / 0.4 + 0.5 * rho * (u * u + v * v)], 1)
+
+
+@pytest.mark.parametrize("which", ["box", "ogrid"])
+def test_kinetic_far_field_preserves_the_free_stream_bitwise(which):
+    c = cg.cartesian_box(9, 9, kinetic_outer=True) if which == "box" else cg.naca0012_block(40, 16, kinetic_outer=True)
+    o = O.Oracle(c, farfield=O.FARFIELD_KINETIC, mach=1.2, aoa_deg=3.0)
+    U = np.tile(O.freestream(1.2, 3.0), (c.n, 1))  # uniform, walls included (as above)
+    q = o.q_from_state(U)
+    qx, qy = o.q_gradients(q, 3)
+    R, D = o.residual(q, qx, qy, U, 100.0)
+    assert np.all(R == 0.0)
+    assert np.all(D > 0) and np.all(D[c.flag == cg.OUTER] != 1.0)
+    dUs, dU = o.sweeps(U, R, D)
+    assert np.all(dU == 0.0)
+
+
+def test_kinetic_ghost_term_is_the_mirrored_free_stream_stencil():
+    """The far-field term equals an n-derivative over ghost points that carry
+    the free stream at the mirror images of the point's inside (n+)
+    neighbours: the difference of the residuals for two free streams A and B
+    is, at an outer point, sum_g w_g (G_n^-(A) - G_n^-(B)) with w_g the
+    least-squares n-derivative weights of the ghost set (solved here with
+    numpy, from the coordinates), and exactly 0 at every other point."""
+    c = cg.cartesian_box(9, 8, seed=11, kinetic_outer=True)
+    A, B = (0.5, 10.0), (1.5, -20.0)
+    Ua, Ub = O.freestream(*A), O.freestream(*B)
+    U = _kinetic_smooth_state(c, Ua)
+    out = []
+    for m, al in (A, B):
+        o = O.Oracle(c, farfield=O.FARFIELD_KINETIC, mach=m, aoa_deg=al)
+        q = o.q_from_state(U)
+        qx, qy = o.q_gradients(q, 3)
+        out.append(o.residual(q, qx, qy, U, 10.0)[0])
+    dR = out[0] - out[1]
+    inner = c.flag != cg.OUTER
+    assert np.all(dR[inner] == 0.0)
+    checked = 0
+    for p in np.flatnonzero(~inner):
+        r = c.nbr_idx[c.nbr_off[p]:c.nbr_off[p + 1]]
+        t = np.array([c.ny[p], -c.nx[p]])
+        nn = np.array([c.nx[p], c.ny[p]])
+        d = np.stack([c.x[r] - c.x[p], c.y[r] - c.y[p]], 1)
+        inside = d @ nn < 0
+        g = d[inside] - 2.0 * np.outer(d[inside] @ nn, nn)  # mirror images across the tangent line
+        Xg = np.stack([g @ t, g @ nn], 1)
+        W = np.linalg.solve(Xg.T @ Xg, Xg.T)  # rows: t- and n-derivative weights
+        wn = W[1]
+        expect = wn.sum() * (O.split_flux_cons(Ua, nn[0], nn[1], -1) - O.split_flux_cons(Ub, nn[0], nn[1], -1))
+        assert np.allclose(dR[p], expect, rtol=1e-11, atol=1e-13 * np.abs(expect).max()), p
+        assert wn.sum() > 0
+        checked += 1
+    assert checked == int((~inner).sum())
+
+
+@pytest.mark.parametrize("wall", [False, True])
+def test_kinetic_sweeps_equal_dense_lusgs(wall):
+    """With the kinetic far field the outer points are unknowns of the dense
+    system too; the sequential sweeps still equal its solve."""
+    c = cg.cartesian_box(7, 7, seed=21, wall_bottom=wall, kinetic_outer=True)
+    o = O.Oracle(c, farfield=O.FARFIELD_KINETIC, mach=0.8, aoa_deg=5.0)
+    U = _kinetic_smooth_state(c, O.freestream(0.8, 5.0), amp=0.08)
+    if wall:
+        U[c.flag == cg.WALL, 2] = 0.0
+    q = o.q_from_state(U)
+    qx, qy = o.q_gradients(q, 3)
+    R, D = o.residual(q, qx, qy, U, 5.0)
+    dUs, dU = o.sweeps(U, R, D, O.JVP_EXACT)
+    ds_ref, d_ref = _dense_lusgs(c, o, U, R, D, kinetic=True)
+    scale = np.abs(d_ref).max()
+    assert np.abs(dU[c.flag == cg.OUTER]).max() > 1e-3 * scale
+    assert np.allclose(dUs, ds_ref, rtol=0, atol=1e-12 * np.abs(ds_ref).max())
+    assert np.allclose(dU, d_ref, rtol=0, atol=1e-12 * scale)
+
+
+@pytest.mark.parametrize("mach,aoa", [(2.0, 10.0), (0.5, 10.0)])
+@pytest.mark.parametrize("scheme", ["lusgs", "manish", "explicit"])
+def test_kinetic_far_field_returns_to_the_free_stream(mach, aoa, scheme):
+    """Without a body the free stream is the steady state: from a perturbed
+    start (outer points included) every scheme drives the whole cloud back to
+    it, through incoming (free-stream ghosts) and outgoing boundaries alike."""
+    c = cg.cartesian_box(9, 9, seed=3, kinetic_outer=True)
+    o = O.Oracle(c, farfield=O.FARFIELD_KINETIC, mach=mach, aoa_deg=aoa)
+    Uinf = O.freestream(mach, aoa)
+    U = _kinetic_smooth_state(c, Uinf)
+    if scheme == "lusgs":
+        r = o.run(U, 400, cfl=5.0, K=3)
+    elif scheme == "manish":
+        r = o.run_manish(U, 400, cfl=2.0, K=3)
+    else:
+        r = o.run_explicit(U, 3000, cfl=0.3, K=3)
+    assert r["status"] == 0
+    assert r["hist"][-1] < 1e-6 * r["hist"][0]
+    assert np.abs(r["U"] - Uinf).max() < 1e-6
 
 
 # ---------------------------------------------------------------------------
