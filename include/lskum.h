@@ -70,8 +70,10 @@ enum {
  *   n_points  N >= 1
  *   x, y      f64[N] coordinates
  *   flag      u8[N]  LSKUM_INTERIOR / LSKUM_WALL / LSKUM_OUTER
- *   nx, ny    f64[N] unit wall normals pointing into the fluid (read at wall
- *             points only); must not be NULL when the cloud has wall points
+ *   nx, ny    f64[N] unit normals: at wall points into the fluid; at outer
+ *             points out of the domain (read there only under
+ *             LSKUM_FARFIELD_KINETIC); read nowhere else; must not be NULL
+ *             when some point needs them
  *   nbr_off   i32[N+1] CSR offsets, nbr_off[0] = 0, non-decreasing
  *   nbr_idx   i32[nbr_off[N]] neighbour indices: 0-based, < N, no self, no
  *             duplicates within a row.  The order within a row is the
@@ -122,13 +124,29 @@ typedef struct {
  *                    LSKUM_ORDER_WALL_FIRST (1; the wall points colour by
  *                    colour, then the interior points colour by colour,
  *                    Alg. 4; the backward sweep is the exact reverse)
+ *   farfield         the outer (far-field) points: LSKUM_FARFIELD_FREESTREAM
+ *                    (0) holds them at the free stream (Dirichlet; they are
+ *                    not swept); LSKUM_FARFIELD_KINETIC (1) makes them
+ *                    unknowns like the others (the paper's sweeps visit them,
+ *                    Alg. 2 and 4; it states no formula): in the frame (t, n),
+ *                    n the outward normal, their residual is the t+, t- and
+ *                    n+ split derivatives over their neighbours plus the
+ *                    n- derivative against free-stream ghost points at the
+ *                    mirror images of the n+ neighbours, LS_3(1)
+ *                    (G_n^-(U_inf) - G_n^-(U_0)) with LS_3(1) = -LS_2(1):
+ *                    molecules entering the domain carry the free-stream
+ *                    Maxwellian (supersonic inflow and outflow alike).  They
+ *                    are swept (last among equal colours, or after the
+ *                    interior points in LSKUM_ORDER_WALL_FIRST), updated and
+ *                    counted in the residual norms.
  */
 enum { LSKUM_SCHEME_LUSGS = 0, LSKUM_SCHEME_EXPLICIT = 1 };
 enum { LSKUM_LUSGS_ANANDH = 0, LSKUM_LUSGS_MANISH = 1 };
 enum { LSKUM_ORDER_COLOUR = 0, LSKUM_ORDER_WALL_FIRST = 1 };
+enum { LSKUM_FARFIELD_FREESTREAM = 0, LSKUM_FARFIELD_KINETIC = 1 };
 typedef struct {
     double mach, aoa_deg, cfl, cfl_ramp_iters;
-    int32_t inner_iters, jvp, precision, first_order_iters, scheme, lusgs, ordering;
+    int32_t inner_iters, jvp, precision, first_order_iters, scheme, lusgs, ordering, farfield;
 } lskum_opts;
 
 /*
@@ -151,7 +169,8 @@ lskum_status lskum_create(const lskum_cloud *cloud, const lskum_opts *opts, void
  * exactly as lskum_batch_create does (n_cases = 1: as lskum_create), build
  * the host layout (colouring, sweep order and levels, slot lists) and check
  * its invariants: the sweep order is a permutation, every wall or interior
- * point lies in one sweep level and outer points in none, each level's sweep
+ * point (and every outer point under LSKUM_FARFIELD_KINETIC) lies in one
+ * sweep level and frozen outer points in none, each level's sweep
  * orders are permutations of it, no two coupled points share a level, and
  * the lower / upper slot lists hold exactly the coupling slots of earlier /
  * later levels.  No device call is made.  n_colours, n_levels (may be NULL)

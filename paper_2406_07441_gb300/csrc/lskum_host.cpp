@@ -209,6 +209,13 @@ struct HostPrep {
     std::vector<uint8_t> smb_caller;  // sub-stencil membership per caller-order slot
 };
 static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &hp);
+
+// Is point p (caller order of the union) an unknown of the iteration?  Outer
+// points are only under the kinetic far field.
+static bool swept(const lskum_ctx *c, int32_t p)
+{
+    return c->flag[p] != LSKUM_OUTER || c->opts.farfield == LSKUM_FARFIELD_KINETIC;
+}
 static lskum_status upload(lskum_ctx *c, HostPrep &hp);
 static lskum_status build_graphs(lskum_ctx *c);
 
@@ -220,18 +227,20 @@ static bool opts_valid(const lskum_opts *o)
            o->first_order_iters >= 0 &&
            (o->scheme == LSKUM_SCHEME_LUSGS || (o->scheme == LSKUM_SCHEME_EXPLICIT && o->precision == 0)) &&
            (o->lusgs == LSKUM_LUSGS_ANANDH || o->lusgs == LSKUM_LUSGS_MANISH) &&
-           (o->ordering == LSKUM_ORDER_COLOUR || o->ordering == LSKUM_ORDER_WALL_FIRST);
+           (o->ordering == LSKUM_ORDER_COLOUR || o->ordering == LSKUM_ORDER_WALL_FIRST) &&
+           (o->farfield == LSKUM_FARFIELD_FREESTREAM || o->farfield == LSKUM_FARFIELD_KINETIC);
 }
 
 static bool opts_shared_equal(const lskum_opts *a, const lskum_opts *b)
 {
     return a->cfl == b->cfl && a->cfl_ramp_iters == b->cfl_ramp_iters && a->inner_iters == b->inner_iters &&
            a->jvp == b->jvp && a->precision == b->precision && a->first_order_iters == b->first_order_iters &&
-           a->scheme == b->scheme && a->lusgs == b->lusgs && a->ordering == b->ordering;
+           a->scheme == b->scheme && a->lusgs == b->lusgs && a->ordering == b->ordering && a->farfield == b->farfield;
 }
 
-// Validate one case's cloud (indices local to the case).
-static lskum_status validate_cloud(const lskum_cloud *cl, int32_t cs)
+// Validate one case's cloud (indices local to the case); `kinetic`: outer
+// points need outward unit normals (the kinetic far field).
+static lskum_status validate_cloud(const lskum_cloud *cl, int32_t cs, bool kinetic)
 {
     if (!cl) return fail(nullptr, LSKUM_ERR_ARG, "case %d: cloud is NULL", cs);
     const int32_t n = cl->n_points;
@@ -240,7 +249,7 @@ static lskum_status validate_cloud(const lskum_cloud *cl, int32_t cs)
         return fail(nullptr, LSKUM_ERR_ARG, "case %d: a cloud array is NULL", cs);
     const int32_t *off = cl->nbr_off, *idx = cl->nbr_idx;
     if (off[0] != 0) return fail(nullptr, LSKUM_ERR_ARG, "case %d: nbr_off[0] != 0", cs);
-    bool has_wall = false;
+    bool has_wall = false, has_outer = false;
     for (int32_t p = 0; p < n; p++) {
         if (off[p + 1] < off[p]) return fail(nullptr, LSKUM_ERR_ARG, "nbr_off decreases at point %d", p);
         if (cl->flag[p] > LSKUM_OUTER) return fail(nullptr, LSKUM_ERR_ARG, "bad flag at point %d", p);
@@ -248,8 +257,11 @@ static lskum_status validate_cloud(const lskum_cloud *cl, int32_t cs)
             return fail(nullptr, LSKUM_ERR_ARG, "non-finite coordinate at point %d", p);
         if (off[p + 1] - off[p] > 255) return fail(nullptr, LSKUM_ERR_ARG, "more than 255 neighbours at point %d", p);
         has_wall |= cl->flag[p] == LSKUM_WALL;
+        has_outer |= cl->flag[p] == LSKUM_OUTER;
     }
     if (has_wall && (!cl->nx || !cl->ny)) return fail(nullptr, LSKUM_ERR_ARG, "case %d: wall points need nx, ny", cs);
+    if (kinetic && has_outer && (!cl->nx || !cl->ny))
+        return fail(nullptr, LSKUM_ERR_ARG, "case %d: the kinetic far field needs nx, ny at outer points", cs);
     for (int32_t p = 0; p < n; p++) {
         for (int32_t e = off[p]; e < off[p + 1]; e++) {
             const int32_t q = idx[e];
@@ -258,17 +270,20 @@ static lskum_status validate_cloud(const lskum_cloud *cl, int32_t cs)
             for (int32_t f = off[p]; f < e; f++)
                 if (idx[f] == q) return fail(nullptr, LSKUM_ERR_ARG, "duplicate neighbour %d at point %d", q, p);
         }
-        if (cl->flag[p] == LSKUM_WALL) {
+        if (cl->flag[p] == LSKUM_WALL || (kinetic && cl->flag[p] == LSKUM_OUTER)) {
             const double ln = std::hypot(cl->nx[p], cl->ny[p]);
-            if (!(std::fabs(ln - 1.0) < 1e-6)) return fail(nullptr, LSKUM_ERR_ARG, "wall normal not unit at point %d", p);
+            if (!(std::fabs(ln - 1.0) < 1e-6))
+                return fail(nullptr, LSKUM_ERR_ARG, "%s normal not unit at point %d",
+                            cl->flag[p] == LSKUM_WALL ? "wall" : "outer", p);
         }
     }
     return LSKUM_OK;
 }
 
 // Invariants of the host layout that the kernels rely on: the internal order
-// is a permutation, every wall or interior point lies in exactly one sweep
-// level and outer points in none, each level's two sweep orders are
+// is a permutation, every wall or interior point (and, under the kinetic far
+// field, every outer point) lies in exactly one sweep level and frozen outer
+// points in none, each level's two sweep orders are
 // permutations of the level, no two points of a level are coupled, and
 // every lower (upper) slot list entry lies in an earlier (later) level, the
 // two lists together holding every coupling slot.
@@ -292,12 +307,12 @@ static lskum_status verify_layout(lskum_ctx *c, const lskum_cloud *cl, const Hos
         std::sort(g.begin(), g.end());
         for (int32_t k = b; k < ae; k++) {
             if (f[k - b] != k || g[k - b] != k) return fail(c, LSKUM_ERR_ARG, "layout: sweep order of level %d", l);
-            if (c->flag[c->perm[k]] == LSKUM_OUTER) return fail(c, LSKUM_ERR_ARG, "layout: outer point swept");
+            if (!swept(c, c->perm[k])) return fail(c, LSKUM_ERR_ARG, "layout: frozen outer point swept");
             level[k] = l;
         }
     }
     for (int32_t k = 0; k < n; k++)
-        if ((level[k] < 0) != (c->flag[c->perm[k]] == LSKUM_OUTER))
+        if ((level[k] < 0) == swept(c, c->perm[k]))
             return fail(c, LSKUM_ERR_ARG, "layout: point %d not in a level", c->perm[k]);
     for (int32_t k = 0; k < n; k++) {
         if (level[k] < 0) continue;
@@ -337,7 +352,7 @@ static lskum_status create_impl(const lskum_cloud *clouds, const lskum_opts *opt
         if (!opts_valid(&opts[b])) return fail(nullptr, LSKUM_ERR_ARG, "invalid option value (case %d)", b);
         if (!opts_shared_equal(&opts[0], &opts[b]))
             return fail(nullptr, LSKUM_ERR_ARG, "case %d: options other than mach/aoa differ from case 0", b);
-        lskum_status v = validate_cloud(&clouds[b], b);
+        lskum_status v = validate_cloud(&clouds[b], b, opts[0].farfield == LSKUM_FARFIELD_KINETIC);
         if (v != LSKUM_OK) return v;
         total += clouds[b].n_points;
         total_nnz += clouds[b].nbr_off[clouds[b].n_points];
@@ -363,7 +378,7 @@ static lskum_status create_impl(const lskum_cloud *clouds, const lskum_opts *opt
             ux.push_back(cl.x[p]);
             uy.push_back(cl.y[p]);
             ufl.push_back(cl.flag[p]);
-            if (cl.flag[p] == LSKUM_WALL) {
+            if (cl.flag[p] == LSKUM_WALL || (opts[0].farfield == LSKUM_FARFIELD_KINETIC && cl.flag[p] == LSKUM_OUTER)) {
                 unx[base + p] = cl.nx[p];
                 uny[base + p] = cl.ny[p];
             }
@@ -436,8 +451,9 @@ static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &
     c->flag.assign(cl->flag, cl->flag + n);
     c->nx.assign(n, 0.0);
     c->ny.assign(n, 0.0);
+    const bool kinetic = c->opts.farfield == LSKUM_FARFIELD_KINETIC;
     for (int32_t p = 0; p < n; p++)
-        if (c->flag[p] == LSKUM_WALL) {
+        if (c->flag[p] == LSKUM_WALL || (kinetic && c->flag[p] == LSKUM_OUTER)) {
             c->nx[p] = cl->nx[p];
             c->ny[p] = cl->ny[p];
         }
@@ -449,9 +465,13 @@ static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &
     smb.assign(nnz, 0);
     std::vector<double> geo((size_t)G_NFIELDS * n, 0.0);
     for (int32_t p = 0; p < n; p++) {
+        // frames: (t, n) at wall points (n into the fluid) and at outer points
+        // of the kinetic far field (n out of the domain; their n- side is the
+        // free-stream ghosts, sub-stencil 3 with LS_3(1) = -LS_2(1))
         const bool wall = c->flag[p] == LSKUM_WALL;
+        const bool kouter = kinetic && c->flag[p] == LSKUM_OUTER;
         double e1x = 1.0, e1y = 0.0, e2x = 0.0, e2y = 1.0;
-        if (wall) {
+        if (wall || kouter) {
             e1x = c->ny[p];
             e1y = -c->nx[p];
             e2x = c->nx[p];
@@ -479,7 +499,7 @@ static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &
             if (a < 0.0) mb |= 1;
             else if (a > 0.0) mb |= 2;
             if (b < 0.0) { if (!wall) mb |= 4; }
-            else if (b > 0.0) mb |= 8;
+            else if (b > 0.0) { if (!kouter) mb |= 8; }
             smb[e] = mb;
             for (int s = 0; s < 4; s++) {
                 if (!(mb & (1 << s))) continue;
@@ -505,10 +525,10 @@ static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &
             geo[G_SYY * n + p] += swgy[e] * sdy[e];
         }
         geo[G_DMIN * n + p] = dmin;
-        if (c->flag[p] == LSKUM_OUTER) continue;
+        if (!swept(c, p)) continue;
         double det[4];
         for (int s = 0; s < 4; s++) {
-            if (wall && s == 2) continue;
+            if ((wall && s == 2) || (kouter && s == 3)) continue;
             det[s] = sdd[s] * spp[s] - sdp[s] * sdp[s];
             if (cnt[s] < 2 || !(det[s] > 1e-12 * sdd[s] * spp[s]))
                 return fail(c, LSKUM_ERR_STENCIL, "degenerate split sub-stencil %d at point %d", s, p);
@@ -524,6 +544,10 @@ static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &
                 else sw2[e] = w;
                 geo[(G_ABS_0 + s) * n + p] += std::fabs(w);
             }
+        }
+        if (kouter) {  // the mirrored free-stream ghosts
+            geo[G_LS1_3 * n + p] = -geo[G_LS1_2 * n + p];
+            geo[G_ABS_3 * n + p] = geo[G_ABS_2 * n + p];
         }
     }
 
@@ -552,8 +576,8 @@ static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &
     });
     c->inv.resize(n);
     for (int32_t k = 0; k < n; k++) c->inv[c->perm[k]] = k;
-    // levels: runs of equal key holding wall or interior points; outer points
-    // (never swept) close their level's range (or, wall-first, the last level)
+    // levels: runs of equal key holding swept points; frozen outer points
+    // close their level's range (or, wall-first, the last level)
     c->lvl_beg.clear();
     c->lvl_act_end.clear();
     c->lvl_end.clear();
@@ -562,7 +586,7 @@ static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &
         while (k < n) {
             const int64_t key = skey(c->perm[k]);
             const int32_t b = k;
-            while (k < n && skey(c->perm[k]) == key && c->flag[c->perm[k]] != LSKUM_OUTER) k++;
+            while (k < n && skey(c->perm[k]) == key && swept(c, c->perm[k])) k++;
             const int32_t ae = k;
             while (k < n && skey(c->perm[k]) == key) k++;
             if (ae > b) {
@@ -625,16 +649,16 @@ static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &
         }
     }
     // LU-SGS lists: for each point its slots whose neighbour is earlier (lower)
-    // or later (upper) in the sweep order; outer neighbours (increment 0)
+    // or later (upper) in the sweep order; frozen neighbours (increment 0)
     // and slots in no split sub-stencil contribute nothing and are left out
     hp.lo_off.assign(n + 1, 0);
     hp.up_off.assign(n + 1, 0);
     for (int32_t k = 0; k < n; k++) {
         const int32_t p = c->perm[k];
-        if (c->flag[p] != LSKUM_OUTER) {
+        if (swept(c, p)) {
             for (int32_t e = off[p]; e < off[p + 1]; e++) {
                 const int32_t q = idx[e];
-                if (c->flag[q] == LSKUM_OUTER || smb[e] == 0) continue;
+                if (!swept(c, q) || smb[e] == 0) continue;
                 const bool lower = skey(q) < skey(p);
                 (lower ? hp.lo_nbr : hp.up_nbr).push_back(c->inv[q]);
                 (lower ? hp.lo_mb : hp.up_mb).push_back(smb[e]);
@@ -830,6 +854,16 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
     d.jvp = c->opts.jvp;
     d.scheme = c->opts.scheme;
     d.lusgs = c->opts.lusgs;
+    d.farfield = c->opts.farfield;
+    double *dcase_uinf = A.alloc<double>(4 * (size_t)c->n_cases);
+    if (A.err != cudaSuccess) return cuda_fail(c, A.err, "cudaMalloc");
+    d.case_uinf = dcase_uinf;
+    std::vector<double> cuinf(4 * (size_t)c->n_cases);
+    for (int32_t b = 0; b < c->n_cases; b++) {
+        double ub, vb;
+        host_free_stream(c, b, &ub, &vb);
+        host_prim_to_cons(1.0, ub, vb, 1.0 / 1.4, &cuinf[4 * b]);  // as the start state below
+    }
     auto up = [&](void *dst, const void *src, size_t bytes) {
         if (e == cudaSuccess) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
     };
@@ -868,6 +902,7 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
     up(dcase_blk, hp.case_blk.data(), hp.case_blk.size() * sizeof(int32_t));
     up(dinv, c->inv.data(), n * sizeof(int32_t));
     up(dcase_of, hp.case_of_i.data(), ld * sizeof(int32_t));
+    up(dcase_uinf, cuinf.data(), cuinf.size() * sizeof(double));
     if (e == cudaSuccess) e = cudaMemset(c->case_state, 0, c->n_cases * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemset(c->case_it, 0, c->n_cases * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemset(c->case_hist0, 0, c->n_cases * sizeof(double));

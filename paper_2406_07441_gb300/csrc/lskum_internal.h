@@ -15,6 +15,7 @@
 
 namespace lskum {
 
+constexpr int kInterior = 0;
 constexpr int kWall = 1;
 constexpr int kOuter = 2;
 
@@ -50,8 +51,9 @@ struct Ctrl {
 
 // Per-point geometry rows (fields of `geo`, stride ld).
 enum GeoField {
-    G_E1X, G_E1Y, G_E2X, G_E2Y,          // frame: (1,0),(0,1) or wall (t, n)
-    G_LS1_0, G_LS1_1, G_LS1_2, G_LS1_3,  // LS_s(1) of the four split sub-stencils
+    G_E1X, G_E1Y, G_E2X, G_E2Y,          // frame: (1,0),(0,1), or (t, n) at wall and kinetic outer points
+    G_LS1_0, G_LS1_1, G_LS1_2, G_LS1_3,  // LS_s(1) of the four split sub-stencils (kinetic
+                                         // outer points: LS_3(1) = -LS_2(1), the ghosts)
     G_ABS_0, G_ABS_1, G_ABS_2, G_ABS_3,  // sum_i |w_i| of each split sub-stencil
     G_DMIN,                              // min_i |r_i - r_0|
     G_SXX, G_SXY, G_SYX, G_SYY,          // sums over the stencil of wgx dx, wgx dy, wgy dx, wgy dy
@@ -82,7 +84,7 @@ struct Dev {
     int32_t n, ld, n_slices;
     // cloud
     const uint8_t *flag;     // [n]
-    const double *wnx, *wny; // [n] wall normals
+    const double *wnx, *wny; // [n] wall normals (and outer normals under the kinetic far field)
     const double *geo;       // [G_NFIELDS][ld]
     // sliced ELL neighbour slots
     const int32_t *slice_off; // [n_slices + 1]
@@ -132,6 +134,8 @@ struct Dev {
     int32_t precision;    // 0 FP64; 1 FP32 sweeps, compensated FP64 residual sums
     int32_t scheme;       // 0 implicit LU-SGS; 1 explicit (forward Euler, no sweeps)
     int32_t lusgs;        // 0 Anandhanarayanan's diagonal; 1 the revised form of Manish et al.
+    int32_t farfield;     // 0 outer points frozen at the free stream; 1 the kinetic far field
+    const double *case_uinf;  // [n_cases][4] free-stream conserved state of each case
 };
 
 // Kernel launch wrappers (lskum_kernels.cu).  `cur` is the state set read by

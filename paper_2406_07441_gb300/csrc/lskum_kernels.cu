@@ -361,8 +361,8 @@ __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const doub
     const int kk = active ? k : d.n - 1;
     const int ld = d.ld;
     const int fl = d.flag[kk];
-    const bool work = active && fl != kOuter && !frozen(d, kk);
-    const bool wall = fl == kWall;
+    const bool work = active && (fl != kOuter || d.farfield == 1) && !frozen(d, kk);
+    const bool framed = fl != kInterior;  // (t, n) frame: wall and kinetic outer points
     const double *__restrict__ q = st.q;
     double R[4] = {0.0, 0.0, 0.0, 0.0};
     double Rc[4] = {0.0, 0.0, 0.0, 0.0};  // compensation terms (COMP)
@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const doub
                 const double sg = (mb & 1) ? 1.0 : -1.0;
                 const double w = d.w1[e];
                 double Gi[4], G0[4];
-                if (wall) {
+                if (framed) {
                     split_flux<2>(T, Pi, e1x, e1y, sg, Gi);
                     split_flux<2>(T, P0, e1x, e1y, sg, G0);
                 } else {
@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const doub
                 const double sg = (mb & 4) ? 1.0 : -1.0;
                 const double w = d.w2[e];
                 double Gi[4], G0[4];
-                if (wall) {
+                if (framed) {
                     split_flux<2>(T, Pi, e2x, e2y, sg, Gi);
                     split_flux<2>(T, P0, e2x, e2y, sg, G0);
                 } else {
@@ -434,6 +434,28 @@ __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const doub
         R[c] = group_sum<TPP>(R[c]);
     }
     if (work && sub == 0) {
+        if (fl == kOuter) {
+            // kinetic far field: the n- side is free-stream ghosts at the mirror
+            // images of the inside neighbours, LS_3(1) (G_n^-(U_inf) - G_n^-(U_0))
+            // with LS_3(1) = -LS_2(1); first order (the point's own state)
+            const double *ui = d.case_uinf + 4 * d.case_of[k];
+            double U0[4], Ui[4];
+            bool same = true;
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                U0[c] = st.U[c * ld + k];
+                Ui[c] = ui[c];
+                same = same && U0[c] == Ui[c];
+            }
+            if (!same) {  // (equal states give exactly 0)
+                double Gi[4], G0[4];
+                flux_cons(T, Ui, e2x, e2y, -1.0, Gi);
+                flux_cons(T, U0, e2x, e2y, -1.0, G0);
+                const double l3 = d.geo[G_LS1_3 * ld + k];
+#pragma unroll
+                for (int c = 0; c < 4; c++) R[c] = fma(l3, Gi[c] - G0[c], R[c]);
+            }
+        }
 #pragma unroll
         for (int c = 0; c < 4; c++) d.R[c * ld + k] = R[c];
         // local time step (reading: CFL min_i|dr| / (|u| + a)) and the scalar
@@ -472,7 +494,7 @@ __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const doub
 // per-case residual norms, histories and stopping tests (two stages)
 // ---------------------------------------------------------------------------
 // Stage 1: block j sums R_rho^2 over caller positions [blk_pos[j], blk_pos[j+1]),
-// all of one case (outer points hold R = 0).  Fixed order: warp butterfly,
+// all of one case (frozen outer points hold R = 0).  Fixed order: warp butterfly,
 // then warp 0.
 __global__ void __launch_bounds__(256) k_norm_partials(Dev d)
 {
@@ -614,9 +636,10 @@ __global__ void __launch_bounds__(256) k_sweep(Dev d, StateSet st, int lb, int l
     const T *__restrict__ dW = FWD ? sb.dUs : sb.dU;
     const T *__restrict__ pr = sb.prim;
     const int ld = d.ld;
-    const bool wall = d.flag[k] == kWall;
+    const int fk = d.flag[k];
+    const bool wall = fk == kWall, framed = fk != kInterior;  // (t, n): wall and kinetic outer points
     double e1x = 1.0, e1y = 0.0, e2x = 0.0, e2y = 1.0;
-    if (wall) {
+    if (framed) {
         e1x = d.geo[G_E1X * ld + k];
         e1y = d.geo[G_E1Y * ld + k];
         e2x = d.geo[G_E2X * ld + k];
@@ -630,7 +653,7 @@ __global__ void __launch_bounds__(256) k_sweep(Dev d, StateSet st, int lb, int l
         T dl[4];
 #pragma unroll
         for (int c = 0; c < 4; c++) dl[c] = dW[4 * i + c];
-        if (JVP == 0 && !wall) {
+        if (JVP == 0 && !framed) {
             // interior frame: d = (1,0) or (0,1), S, A, exp(-S^2), B precomputed per point
             const PrimT<T> P = load_prim(pr, i);
             const T *rec = pr + (size_t)i * kPrimStride;
@@ -649,7 +672,7 @@ __global__ void __launch_bounds__(256) k_sweep(Dev d, StateSet st, int lb, int l
                 for (int c = 0; c < 4; c++) acc[c] = fma(w, J[c], acc[c]);
             }
         } else {
-            // wall frames (t, n) and the increment form: evaluated in FP64
+            // (t, n) frames and the increment form: evaluated in FP64
             double dld[4];
 #pragma unroll
             for (int c = 0; c < 4; c++) dld[c] = (double)dl[c];
@@ -766,7 +789,7 @@ __global__ void __launch_bounds__(256) k_update(Dev d, int cur)
     double U[4];
 #pragma unroll
     for (int c = 0; c < 4; c++) U[c] = src.U[c * ld + k];
-    const bool moves = INC && fl != kOuter && !frozen(d, k);
+    const bool moves = INC && (fl != kOuter || d.farfield == 1) && !frozen(d, k);
     if (moves) {
 #pragma unroll
         for (int c = 0; c < 4; c++) U[c] += d.dUf ? (double)d.dUf[4 * k + c] : d.dU[4 * k + c];
@@ -835,7 +858,8 @@ __global__ void __launch_bounds__(256) k_update(Dev d, int cur)
 }
 
 // Explicit scheme (the paper's solver (e)): dU = -dt R = -R / D at wall and
-// interior points, normal momentum removed at wall points; outer points 0.
+// interior points (and outer points under the kinetic far field), normal
+// momentum removed at wall points; frozen outer points 0.
 __global__ void __launch_bounds__(256) k_explicit(Dev d)
 {
     if (halted(d.ctrl)) return;
@@ -844,7 +868,7 @@ __global__ void __launch_bounds__(256) k_explicit(Dev d)
     const int ld = d.ld;
     double w[4] = {0.0, 0.0, 0.0, 0.0};
     const int fl = d.flag[k];
-    if (fl != kOuter && !frozen(d, k)) {
+    if ((fl != kOuter || d.farfield == 1) && !frozen(d, k)) {
         const double dt = 1.0 / d.D[k];
 #pragma unroll
         for (int c = 0; c < 4; c++) w[c] = -dt * d.R[c * ld + k];

@@ -17,6 +17,7 @@ JVP_EXACT, JVP_INCREMENT = 0, 1
 SCHEME_LUSGS, SCHEME_EXPLICIT = 0, 1
 LUSGS_ANANDH, LUSGS_MANISH = 0, 1
 ORDER_COLOUR, ORDER_WALL_FIRST = 0, 1
+FARFIELD_FREESTREAM, FARFIELD_KINETIC = 0, 1
 FIELD_U, FIELD_Q, FIELD_QX, FIELD_QY, FIELD_R, FIELD_D, FIELD_DUS, FIELD_DU = range(8)
 OK, ERR_ARG, ERR_STENCIL, ERR_NONPOSITIVE, ERR_DIVERGED, ERR_CUDA, ERR_TIMEOUT, ERR_OOM = 0, -1, -2, -3, -4, -5, -6, -7
 STATUS = {0: "LSKUM_OK", -1: "LSKUM_ERR_ARG", -2: "LSKUM_ERR_STENCIL", -3: "LSKUM_ERR_NONPOSITIVE",
@@ -38,7 +39,7 @@ class lskum_opts(C.Structure):
     _fields_ = [("mach", C.c_double), ("aoa_deg", C.c_double), ("cfl", C.c_double), ("cfl_ramp_iters", C.c_double),
                 ("inner_iters", C.c_int32), ("jvp", C.c_int32), ("precision", C.c_int32),
                 ("first_order_iters", C.c_int32), ("scheme", C.c_int32), ("lusgs", C.c_int32),
-                ("ordering", C.c_int32)]
+                ("ordering", C.c_int32), ("farfield", C.c_int32)]
 
 
 _lib = None
@@ -138,11 +139,11 @@ def validate(clouds, conditions, **kw):
     keep = []
     cl = (lskum_cloud * len(clouds))(*[_cloud_struct(c, keep) for c in clouds])
     o = dict(cfl=100.0, cfl_ramp_iters=0.0, inner_iters=3, jvp=JVP_EXACT, precision=0, first_order_iters=0,
-             scheme=SCHEME_LUSGS, lusgs=LUSGS_ANANDH, ordering=ORDER_COLOUR)
+             scheme=SCHEME_LUSGS, lusgs=LUSGS_ANANDH, ordering=ORDER_COLOUR, farfield=FARFIELD_FREESTREAM)
     o.update(kw)
     op = (lskum_opts * len(clouds))(*[lskum_opts(m, a, o["cfl"], o["cfl_ramp_iters"], o["inner_iters"], o["jvp"],
                                                  o["precision"], o["first_order_iters"], o["scheme"], o["lusgs"],
-                                                 o["ordering"]) for m, a in conditions])
+                                                 o["ordering"], o["farfield"]) for m, a in conditions])
     nc, nl = C.c_int32(), C.c_int32()
     s = L.lskum_validate(cl, op, len(clouds), C.byref(nc), C.byref(nl))
     if s != 0:
@@ -158,7 +159,7 @@ class Solver:
 
     def __init__(self, cloud, mach, aoa_deg, cfl=100.0, inner_iters=3, jvp=JVP_EXACT, cfl_ramp_iters=0.0,
                  first_order_iters=0, precision=0, scheme=SCHEME_LUSGS, lusgs=LUSGS_ANANDH,
-                 ordering=ORDER_COLOUR, stream=None, _cases=None):
+                 ordering=ORDER_COLOUR, farfield=FARFIELD_FREESTREAM, stream=None, _cases=None):
         L = load()
         keep = []
         clouds = _cases[0] if _cases else [cloud]
@@ -167,7 +168,7 @@ class Solver:
             raise ValueError("one (mach, aoa_deg) per cloud")
         cl = (lskum_cloud * len(clouds))(*[_cloud_struct(c, keep) for c in clouds])
         op = (lskum_opts * len(clouds))(*[lskum_opts(m, a, cfl, cfl_ramp_iters, inner_iters, jvp, precision,
-                                                     first_order_iters, scheme, lusgs, ordering)
+                                                     first_order_iters, scheme, lusgs, ordering, farfield)
                                           for m, a in conds])
         h = C.c_void_p()
         if _cases:

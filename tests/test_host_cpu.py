@@ -77,7 +77,8 @@ def test_degenerate_split_stencil_is_rejected(lk):
 
 def test_bad_options_are_rejected(lk):
     c = cg.naca0012_block(40, 16)
-    for kw in (dict(cfl=0.0), dict(inner_iters=-1), dict(jvp=5), dict(scheme=2), dict(scheme=1, precision=1)):
+    for kw in (dict(cfl=0.0), dict(inner_iters=-1), dict(jvp=5), dict(scheme=2), dict(scheme=1, precision=1),
+               dict(farfield=2)):
         with pytest.raises(lk.LskumError) as ei:
             lk.Solver(c, 0.5, 1.0, **kw)
         assert ei.value.status == -1
@@ -125,3 +126,47 @@ def test_validate_rejects_what_create_rejects(lk):
     with pytest.raises(lk.LskumError) as ei:
         lk.validate([cg.naca0012_block(40, 16)], [(0.5, 1.0)], scheme=1, precision=1)
     assert ei.value.status == -1
+
+
+@pytest.mark.parametrize("ordering", [0, 1])
+def test_kinetic_far_field_layout(lk, ordering):
+    """Under the kinetic far field every outer point is swept: in the colour
+    order each colour is one level holding all its points; the invariants
+    (checked by lskum_validate) hold with the outer points in the lists."""
+    import oracle as O
+    for c in (cg.naca0012_block(40, 16, kinetic_outer=True), cg.naca0012_jittered(64, 32, seed=12, kinetic_outer=True),
+              cg.cartesian_box(7, 7, seed=2, wall_bottom=True, kinetic_outer=True)):
+        nc, nl = lk.validate([c], [(1.2, 0.0)], ordering=ordering, farfield=lk.FARFIELD_KINETIC)
+        assert nc == O.Oracle(c).ncolours
+        assert nl == nc if ordering == 0 else nl >= nc
+        nc0, nl0 = lk.validate([c], [(1.2, 0.0)], ordering=ordering)
+        assert nc0 == nc and nl0 <= nl
+
+
+def test_kinetic_far_field_checks_outer_normals_and_stencils(lk):
+    """Outer normals are read (and must be unit) only under the kinetic far
+    field, and only then must the outer points' t+, t- and n+ sub-stencils be
+    well posed (LSKUM_ERR_STENCIL otherwise)."""
+    c = _cloud_copy(cg.naca0012_block(40, 16, kinetic_outer=True))
+    c.nx[-1] *= 2.0
+    lk.validate([c], [(1.2, 0.0)])
+    with pytest.raises(lk.LskumError) as ei:
+        lk.validate([c], [(1.2, 0.0)], farfield=lk.FARFIELD_KINETIC)
+    assert ei.value.status == -1 and "outer normal" in str(ei.value)
+    # bottom-edge outer point of a box (normal (0, -1), t = (-1, 0)): keep its
+    # neighbours on the left (t- side) and just one on the right, so its t+
+    # sub-stencil has a single point
+    b = cg.cartesian_box(7, 7, seed=2, kinetic_outer=True)
+    p = 3
+    assert b.flag[p] == cg.OUTER and b.nx[p] == 0.0 and b.ny[p] == -1.0
+    rows = [list(b.nbr_idx[b.nbr_off[q]:b.nbr_off[q + 1]]) for q in range(b.n)]
+    left = [q for q in rows[p] if b.x[q] <= b.x[p]]
+    right = sorted((q for q in rows[p] if b.x[q] > b.x[p]), key=lambda q: abs(b.x[q] - b.x[p]) + abs(b.y[q] - b.y[p]))
+    rows[p] = left + right[:1]
+    off = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32)
+    idx = np.concatenate(rows).astype(np.int32)
+    bad = cg.Cloud(b.x, b.y, b.flag, b.nx, b.ny, off, idx, {})
+    lk.validate([bad], [(1.2, 0.0)])
+    with pytest.raises(lk.LskumError) as ei:
+        lk.validate([bad], [(1.2, 0.0)], farfield=lk.FARFIELD_KINETIC)
+    assert ei.value.status == -2
