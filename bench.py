@@ -11,6 +11,10 @@ warm-up); every timed step is a full second-order iteration.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
+--workload naca0012_640x256_jit_m1.2 runs the paper's supersonic case (M 1.2,
+AoA 0, K = 2) on the same cloud with the kinetic far field, and also times a
+whole solve to a 1e-8 residual drop (--solve-iters caps it).
+
 --impl reference times the FP64 CPU oracle on the host cores instead, on a
 bounded number of iterations of the same workload.  Under torchrun (N > 1)
 every rank runs an independent replica (the single-cloud solve has no
@@ -30,6 +34,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "naca0012_640x256_jit"
+# the supersonic case with the kinetic far field (K = 2: with 3 inner
+# iterations the unlimited reconstruction fails in the coarse far field)
+SUPER_WORKLOAD = "naca0012_640x256_jit_m1.2"
+CASES = {WORKLOAD: dict(mach=0.85, aoa=1.0, K=3, farfield=0),
+         SUPER_WORKLOAD: dict(mach=1.2, aoa=0.0, K=2, farfield=1)}
 METRIC = "point-iter/s; wall time to 1e-8 residual drop, plain FP64 vs FP32+warm start"
 UNIT = "point-iter/s"
 L2_BYTES = 129 * 2**20
@@ -117,14 +126,14 @@ def _gpu_id(torch, dev):
         return str(dev)
 
 
-def cpu_baseline(cloud, iters, warm=0, mach=0.85, aoa=1.0):
+def cpu_baseline(cloud, iters, warm=0, mach=0.85, aoa=1.0, K=3, farfield=0):
     """The FP64 oracle, as it stands, on one host core: `iters` iterations."""
     import oracle as O
-    o = O.Oracle(cloud)
+    o = O.Oracle(cloud, farfield=farfield, mach=mach, aoa_deg=aoa)
     U = o.initial_state(mach, aoa)
-    r0 = o.run(U, 1 + warm, cfl=100.0, K=3, first_order=1)
+    r0 = o.run(U, 1 + warm, cfl=100.0, K=K, first_order=1)
     t0 = time.perf_counter()
-    r = o.run(r0["U"], iters, cfl=100.0, K=3, n0=1 + warm, hist0=r0["hist0"])
+    r = o.run(r0["U"], iters, cfl=100.0, K=K, n0=1 + warm, hist0=r0["hist0"])
     dt = time.perf_counter() - t0
     return cloud.n * r["done"] / dt, dt, r["done"]
 
@@ -133,17 +142,20 @@ def run_reference(args, rank):
     from paper_2406_07441_gb300 import cloudgen as cg
     if rank != 0:
         return
-    cloud = cg.build_workload(WORKLOAD)
+    wl = args.workload if args.workload in CASES else WORKLOAD
+    case = CASES[wl]
+    cloud = cg.build_workload(wl)
     steps = max(1, min(args.steps, 10))
     warm = min(args.warmup, 1)
-    val, dt, done = cpu_baseline(cloud, steps, warm)
+    val, dt, done = cpu_baseline(cloud, steps, warm, mach=case["mach"], aoa=case["aoa"], K=case["K"],
+                                 farfield=case["farfield"])
     sample = (f"{done} second-order FP64 oracle iterations on the full {cloud.n}-point cloud after "
               f"1 first-order start-up and {warm} warm-up iterations")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": done,
             "warmup": warm, "ms_per_step": dt * 1e3 / done, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "points": cloud.n, "mach": 0.85, "aoa_deg": 1.0, "cfl": 100.0,
-                       "inner_iters": 3, "jvp": "exact-AD", "order": "second (after start-up)"},
+            "config": {"workload": wl, "points": cloud.n, "mach": case["mach"], "aoa_deg": case["aoa"], "cfl": 100.0,
+                       "inner_iters": case["K"], "jvp": "exact-AD", "order": "second (after start-up)"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -161,14 +173,18 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    cloud = cg.build_workload(WORKLOAD)
+    wl = args.workload
+    case = CASES[wl]
+    mach, aoa, K, kinetic = case["mach"], case["aoa"], case["K"], case["farfield"] == 1
+    cloud = cg.build_workload(wl)
     n = cloud.n
     explicit = args.scheme == "explicit"
     cfl = 0.3 if explicit else 100.0
-    s = lskum.Solver(cloud, 0.85, 1.0, cfl=cfl, inner_iters=3, jvp=lskum.JVP_EXACT, first_order_iters=START,
-                     precision=args.precision, scheme=lskum.SCHEME_EXPLICIT if explicit else lskum.SCHEME_LUSGS)
+    kw = dict(cfl=cfl, inner_iters=K, jvp=lskum.JVP_EXACT, first_order_iters=START, precision=args.precision,
+              scheme=lskum.SCHEME_EXPLICIT if explicit else lskum.SCHEME_LUSGS, farfield=case["farfield"])
+    s = lskum.Solver(cloud, mach, aoa, **kw)
     info = s.info()
-    nslots = int(np.count_nonzero(_memberships(cloud)))
+    nslots = int(np.count_nonzero(_memberships(cloud, kinetic)))
     # first-order start-up, then warm-up iterations (untimed)
     assert s.run(START) == START
     # launch shape chosen by the library's autotuner (real iterations, state
@@ -219,13 +235,29 @@ def run_ours(args, rank, world, local_rank):
     e2e = {"value": n * e2e_steps / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": int(U.nbytes),
            "d2h_bytes_per_step": int(U.nbytes) + 8}
 
+    solve = None
+    if args.solve_iters > 0:
+        # wall time of a whole solve from the free stream to the drop target
+        # (host clock around the C-ABI call; the launch shape of the timed steps)
+        s2 = lskum.Solver(cloud, mach, aoa, **kw)
+        s2.set_launch_shape(tpp, lanes)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        it = s2.run(args.solve_iters, target_drop=1e-8)
+        sec = time.perf_counter() - t0
+        h = s2.residuals()
+        cl, cd = s2.forces()
+        solve = {"target_drop": 1e-8, "iterations": int(it), "seconds": sec, "reached": bool(h[-1] / h[0] <= 1e-8),
+                 "final_drop": float(h[-1] / h[0]), "cl": cl, "cd": cd, "max_iters": args.solve_iters}
+        s2.close()
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
     cpu = None
     if world == 1:
-        cv, cdt, cdone = cpu_baseline(cloud, 10)
+        cv, cdt, cdone = cpu_baseline(cloud, 10, mach=mach, aoa=aoa, K=K, farfield=case["farfield"])
         cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{cdone} FP64 oracle iterations on the full {n}-point cloud (single thread)"}
     ws = _working_set_bytes(cloud)
@@ -233,9 +265,11 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f64+f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "points": n, "neighbour_slots": int(cloud.nnz),
+        "config": {"workload": wl, "points": n, "neighbour_slots": int(cloud.nnz),
                    "precision": "fp64" if args.precision == 0 else "fp32 sweeps, fp64 residual/update",
-                   "mach": 0.85, "aoa_deg": 1.0, "cfl": cfl, "inner_iters": 3,
+                   "mach": mach, "aoa_deg": aoa, "cfl": cfl, "inner_iters": K,
+                   "far_field": "kinetic (outer points updated, free-stream ghosts)" if kinetic
+                   else "free stream held at the outer points",
                    "scheme": "explicit (forward Euler, no sweeps)" if explicit else "implicit LU-SGS",
                    "jvp": "exact-AD",
                    "order": f"second (timed steps follow {START} untimed first-order start-up iterations)",
@@ -246,7 +280,7 @@ def run_ours(args, rank, world, local_rank):
                    "l2": f"inputs larger than L2: device working set {ws / 2**20:.0f} MiB > 129 MiB L2"},
         "roofline": {"bound": "alu", "kernel": "k_residual", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                     "traffic": RES_TRAFFIC.get(tpp) if args.precision == 0 else None,
+                     "traffic": RES_TRAFFIC.get(tpp) if args.precision == 0 and wl == WORKLOAD else None,
                      "traffic_unit": "bytes per launch (ncu)",
                      "algorithmic_bytes_per_launch": int(cloud.nnz) * 37 + n * 360,
                      "algorithmic_bytes_rule": "37 B per neighbour slot (index, membership, dx, dy, 2 weights) "
@@ -258,6 +292,8 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": info["launches_per_iter"] * args.steps,
         "clocks": clk.summary(),
     }
+    if solve is not None:
+        line["solve"] = solve
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -552,18 +588,21 @@ def run_warmstart(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
-def _memberships(cloud):
-    """Neighbour slots that join a split sub-stencil of a wall or interior point."""
+def _memberships(cloud, kinetic=False):
+    """Neighbour slots that join a split sub-stencil of a swept point (wall,
+    interior and, under the kinetic far field, outer points)."""
     import numpy as np
     deg = np.diff(cloud.nbr_off)
     owner = np.repeat(np.arange(cloud.n), deg)
     dx = cloud.x[cloud.nbr_idx] - cloud.x[owner]
     dy = cloud.y[cloud.nbr_idx] - cloud.y[owner]
     wall = cloud.flag[owner] == 1
-    a = np.where(wall, dx * cloud.ny[owner] - dy * cloud.nx[owner], dx)
-    b = np.where(wall, dx * cloud.nx[owner] + dy * cloud.ny[owner], dy)
-    active = cloud.flag[owner] != 2
-    return active & ((a != 0) | ((b > 0) | ((b < 0) & ~wall)))
+    outer = cloud.flag[owner] == 2
+    framed = wall | (outer & kinetic)
+    a = np.where(framed, dx * cloud.ny[owner] - dy * cloud.nx[owner], dx)
+    b = np.where(framed, dx * cloud.nx[owner] + dy * cloud.ny[owner], dy)
+    active = ~outer | kinetic
+    return active & ((a != 0) | ((b > 0) & ~outer) | ((b < 0) & ~wall))
 
 
 def _working_set_bytes(cloud):
@@ -582,7 +621,10 @@ def main():
     ap.add_argument("--precision", type=int, choices=[0, 1], default=None,
                     help="0: plain FP64 (default for the single cloud); 1: FP32 sweeps with FP64 residual "
                          "and update (default for the batch)")
-    ap.add_argument("--workload", choices=[WORKLOAD, BATCH_WORKLOAD, WARM_WORKLOAD], default=WORKLOAD)
+    ap.add_argument("--workload", choices=[WORKLOAD, SUPER_WORKLOAD, BATCH_WORKLOAD, WARM_WORKLOAD], default=WORKLOAD)
+    ap.add_argument("--solve-iters", type=int, default=-1,
+                    help="single-cloud workloads: also time a whole solve to a 1e-8 drop, at most this many "
+                         "iterations (default: 0 for the transonic cloud, 30000 for the supersonic one)")
     ap.add_argument("--train-solves", type=int, default=512, help="warm-start workload: training solves")
     ap.add_argument("--test-conditions", type=int, default=16, help="warm-start workload: unseen conditions")
     ap.add_argument("--scheme", choices=["lusgs", "explicit"], default="lusgs",
@@ -597,6 +639,8 @@ def main():
     local_rank = _env_int("LOCAL_RANK", 0)
     if args.precision is None:
         args.precision = 1 if args.workload == BATCH_WORKLOAD else 0
+    if args.solve_iters < 0:
+        args.solve_iters = 30000 if args.workload == SUPER_WORKLOAD else 0
     if args.impl == "reference":
         run_reference(args, rank)
     elif args.workload == BATCH_WORKLOAD:

@@ -517,6 +517,10 @@ WORKLOADS = {
                                  iters=2000, seed=BASE_SEED + 2),
     "naca0012_2560x2048_jit": dict(builder="jittered", n_i=2560, n_j=2048, mach=0.8, aoa_deg=1.25, cfl=100.0,
                                    remove_frac=0.0, seed=BASE_SEED + 3),
+    # the supersonic case (Sec. 5.3: M 1.2, AoA 0) on the 147,584-point cloud,
+    # with the outer stencils the kinetic far field needs
+    "naca0012_640x256_jit_m1.2": dict(builder="jittered", n_i=640, n_j=256, mach=1.2, aoa_deg=0.0, cfl=100.0,
+                                      seed=BASE_SEED + 2, kinetic_outer=True),
 }
 
 
@@ -542,6 +546,8 @@ def build_case(case: dict) -> Cloud:
 
 def build_workload(name: str) -> Cloud:
     w = WORKLOADS[name]
+    ko = w.get("kinetic_outer", False)
     if w["builder"] == "block":
-        return naca0012_block(w["n_i"], w["n_j"])
-    return naca0012_jittered(w["n_i"], w["n_j"], remove_frac=w.get("remove_frac", 0.10), seed=w["seed"])
+        return naca0012_block(w["n_i"], w["n_j"], kinetic_outer=ko)
+    return naca0012_jittered(w["n_i"], w["n_j"], remove_frac=w.get("remove_frac", 0.10), seed=w["seed"],
+                             kinetic_outer=ko)
