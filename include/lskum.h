@@ -296,7 +296,10 @@ lskum_status lskum_time_phases(lskum_ctx *ctx, int32_t reps, double *ms);
 /* Autotune the launch shape (no counterpart in the paper; the kernels'
  * results do not depend on it beyond the order of floating-point sums): for
  * every threads-per-point count {1,2,4,8} of the q-derivative and residual
- * kernels and lanes-per-point count {2,4,8} of the sweep kernels, re-capture
+ * kernels and lanes-per-point count {2,4,8} of the sweep kernels, plus the
+ * packed sweep form (sweep_lanes = 32: one lane per list slot, whole points
+ * packed into warps; available when no point has more than 32 lower or
+ * upper neighbours), re-capture
  * the iteration graphs, run one warm-up iteration and time `trial_iters`
  * iterations between CUDA events on the context's stream; keep the fastest
  * shape.  The state, the per-case counters, stop flags and histories are
@@ -310,8 +313,9 @@ lskum_status lskum_autotune(lskum_ctx *ctx, int32_t trial_iters, int32_t *tpp, i
 /* Set the launch shape directly (e.g. one found by lskum_autotune for the
  * same cloud earlier): tpp in {1, 2, 4, 8} threads per point of the
  * q-derivative and residual kernels, sweep_lanes in {2, 4, 8} lanes per point
- * of the sweep kernels.  The iteration graphs are re-captured.  Errors:
- * LSKUM_ERR_ARG (other values, or a run not waited for), LSKUM_ERR_CUDA. */
+ * of the sweep kernels or 32 for the packed form.  The iteration graphs are
+ * re-captured.  Errors: LSKUM_ERR_ARG (other values, the packed form where
+ * it is not available, or a run not waited for), LSKUM_ERR_CUDA. */
 lskum_status lskum_set_launch_shape(lskum_ctx *ctx, int32_t tpp, int32_t sweep_lanes);
 
 /* Number of points, of colours and of kernel launches one iteration makes. */

@@ -62,6 +62,8 @@ struct lskum_ctx {
     int32_t n_colours = 0;
     int32_t n_levels = 0;               // sweep levels (colours, or (wall|interior, colour) pairs)
     std::vector<int32_t> lvl_beg, lvl_act_end, lvl_end;
+    std::vector<int32_t> pk_lw[2];      // packed sweeps: first warp of each level (+ total), per direction
+    bool pk_ok = false;                 // packed sweeps available (every list <= 32 slots)
     // device
     Arena arena;
     Dev dev{};
@@ -207,6 +209,10 @@ struct HostPrep {
     // per-case norm blocks and case of every internal point
     std::vector<int32_t> blk_pos, blk_case, case_blk, case_of_i;
     std::vector<uint8_t> smb_caller;  // sub-stencil membership per caller-order slot
+    // packed sweep form per direction (0 forward / lower lists, 1 backward / upper lists)
+    std::vector<int32_t> pk_pt[2], pk_nbr[2];
+    std::vector<uint8_t> pk_mb[2];
+    std::vector<double> pk_w1[2], pk_w2[2];
 };
 static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &hp);
 
@@ -337,6 +343,36 @@ static lskum_status verify_layout(lskum_ctx *c, const lskum_cloud *cl, const Hos
     }
     for (int64_t t = 0; t < (int64_t)hp.enb.size(); t++)
         if (hp.enb[t] < 0 || hp.enb[t] >= n) return fail(c, LSKUM_ERR_ARG, "layout: neighbour slot");
+    // packed sweep form: each level's warps hold exactly its points, each
+    // point's list (or one empty slot) in consecutive lanes of one warp
+    for (int dir = 0; dir < 2 && c->pk_ok; dir++) {
+        const std::vector<int32_t> &lw = c->pk_lw[dir], &pt = hp.pk_pt[dir], &nb = hp.pk_nbr[dir];
+        const std::vector<int32_t> &so = dir == 0 ? hp.sw_fwd : hp.sw_bwd;
+        const std::vector<int32_t> &loff = dir == 0 ? hp.lo_off : hp.up_off;
+        const std::vector<int32_t> &lnbr = dir == 0 ? hp.lo_nbr : hp.up_nbr;
+        if ((int32_t)lw.size() != c->n_levels + 1 || (size_t)lw.back() * 32 != pt.size() || nb.size() != pt.size())
+            return fail(c, LSKUM_ERR_ARG, "layout: packed sweep size");
+        std::vector<int32_t> seen_pos(n, 0);
+        for (int32_t l = 0; l < c->n_levels; l++) {
+            for (int64_t t = (int64_t)lw[l] * 32; t < (int64_t)lw[l + 1] * 32; t++) {
+                const int32_t pos = pt[t];
+                if (pos < 0) continue;
+                if (pos < c->lvl_beg[l] || pos >= c->lvl_act_end[l] || nb[t] < 0 || nb[t] >= n)
+                    return fail(c, LSKUM_ERR_ARG, "layout: packed slot %lld", (long long)t);
+                if (t % 32 != 0 && pt[t - 1] == pos) continue;  // not the point's first slot
+                if (seen_pos[pos]++) return fail(c, LSKUM_ERR_ARG, "layout: packed point split");
+                const int32_t k = so[pos], len = loff[k + 1] - loff[k];
+                if (t % 32 + std::max(1, len) > 32) return fail(c, LSKUM_ERR_ARG, "layout: packed point crosses a warp");
+                for (int32_t j = 0; j < std::max(1, len); j++)
+                    if (pt[t + j] != pos || (len > 0 && nb[t + j] != lnbr[loff[k] + j]))
+                        return fail(c, LSKUM_ERR_ARG, "layout: packed list of position %d", pos);
+                if (t % 32 + std::max(1, len) < 32 && pt[t + std::max(1, len)] == pos)
+                    return fail(c, LSKUM_ERR_ARG, "layout: packed list of position %d too long", pos);
+            }
+            for (int32_t pos = c->lvl_beg[l]; pos < c->lvl_act_end[l]; pos++)
+                if (seen_pos[pos] != 1) return fail(c, LSKUM_ERR_ARG, "layout: position %d not packed", pos);
+        }
+    }
     return LSKUM_OK;
 }
 
@@ -682,6 +718,75 @@ static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &
         std::stable_sort(hp.sw_bwd.begin() + b, hp.sw_bwd.begin() + e,
                          [&](int32_t a, int32_t z) { return up_len(a) > up_len(z); });
     }
+    // packed sweep form: per level, its points' slots packed into warps of 32
+    // lanes by best fit (longest lists first; a point with an empty list
+    // takes one slot with membership 0); a point never straddles two warps
+    c->pk_ok = true;
+    for (int32_t k = 0; k < n; k++)
+        if (hp.lo_off[k + 1] - hp.lo_off[k] > 32 || hp.up_off[k + 1] - hp.up_off[k] > 32) c->pk_ok = false;
+    for (int dir = 0; dir < 2 && c->pk_ok; dir++) {
+        const std::vector<int32_t> &so = dir == 0 ? hp.sw_fwd : hp.sw_bwd;
+        const std::vector<int32_t> &loff = dir == 0 ? hp.lo_off : hp.up_off;
+        const std::vector<int32_t> &lnbr = dir == 0 ? hp.lo_nbr : hp.up_nbr;
+        const std::vector<uint8_t> &lmb = dir == 0 ? hp.lo_mb : hp.up_mb;
+        const std::vector<double> &lw1 = dir == 0 ? hp.lo_w1 : hp.up_w1, &lw2 = dir == 0 ? hp.lo_w2 : hp.up_w2;
+        std::vector<int32_t> &lw = c->pk_lw[dir];
+        lw.assign(1, 0);
+        int32_t nw = 0;
+        for (int32_t l = 0; l < c->n_levels; l++) {
+            // best fit: warps by free lanes (bucket r holds warps with r free)
+            std::vector<std::vector<int32_t>> bucket(33);
+            std::vector<std::vector<int32_t>> members;  // positions per warp of this level
+            for (int32_t pos = c->lvl_beg[l]; pos < c->lvl_act_end[l]; pos++) {
+                const int32_t k = so[pos];
+                const int32_t len = std::max(1, loff[k + 1] - loff[k]);
+                int32_t w = -1;
+                for (int32_t r = len; r <= 32 && w < 0; r++)
+                    if (!bucket[r].empty()) {
+                        w = bucket[r].back();
+                        bucket[r].pop_back();
+                        bucket[r - len].push_back(w);
+                    }
+                if (w < 0) {
+                    w = (int32_t)members.size();
+                    members.emplace_back();
+                    bucket[32 - len].push_back(w);
+                }
+                members[w].push_back(pos);
+            }
+            for (const auto &mw : members) {
+                int32_t lane = 0;
+                for (int32_t pos : mw) {
+                    const int32_t k = so[pos];
+                    const int32_t b = loff[k], e = loff[k + 1];
+                    if (e == b) {
+                        hp.pk_pt[dir].push_back(pos);
+                        hp.pk_nbr[dir].push_back(k);
+                        hp.pk_mb[dir].push_back(0);
+                        hp.pk_w1[dir].push_back(0.0);
+                        hp.pk_w2[dir].push_back(0.0);
+                        lane++;
+                    }
+                    for (int32_t j = b; j < e; j++, lane++) {
+                        hp.pk_pt[dir].push_back(pos);
+                        hp.pk_nbr[dir].push_back(lnbr[j]);
+                        hp.pk_mb[dir].push_back(lmb[j]);
+                        hp.pk_w1[dir].push_back(lw1[j]);
+                        hp.pk_w2[dir].push_back(lw2[j]);
+                    }
+                }
+                for (; lane < 32; lane++) {  // padding
+                    hp.pk_pt[dir].push_back(-1);
+                    hp.pk_nbr[dir].push_back(0);
+                    hp.pk_mb[dir].push_back(0);
+                    hp.pk_w1[dir].push_back(0.0);
+                    hp.pk_w2[dir].push_back(0.0);
+                }
+            }
+            nw += (int32_t)members.size();
+            lw.push_back(nw);
+        }
+    }
     for (auto *v : {&hp.lo_nbr, &hp.up_nbr}) if (v->empty()) v->push_back(0);
     for (auto *v : {&hp.lo_mb, &hp.up_mb}) if (v->empty()) v->push_back(0);
     for (auto *v : {&hp.lo_w1, &hp.lo_w2, &hp.up_w1, &hp.up_w2}) if (v->empty()) v->push_back(0.0);
@@ -775,6 +880,29 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
         d.dUf = A.alloc<float>(4 * (size_t)ld);
         for (int s = 0; s < 2; s++) d.set[s].primf = A.alloc<float>((size_t)kPrimStride * ld);
     }
+    // packed sweep form
+    std::vector<float> pkf[2][2];
+    for (int dir = 0; dir < 2; dir++) {
+        d.pk_pt[dir] = d.pk_nbr[dir] = nullptr;
+        d.pk_mb[dir] = nullptr;
+        d.pk_w1[dir] = d.pk_w2[dir] = nullptr;
+        d.pk_w1f[dir] = d.pk_w2f[dir] = nullptr;
+        if (!c->pk_ok || hp.pk_pt[dir].empty()) continue;
+        const size_t m = hp.pk_pt[dir].size();
+        d.pk_pt[dir] = A.alloc<int32_t>(m);
+        d.pk_nbr[dir] = A.alloc<int32_t>(m);
+        d.pk_mb[dir] = A.alloc<uint8_t>(m);
+        d.pk_w1[dir] = A.alloc<double>(m);
+        d.pk_w2[dir] = A.alloc<double>(m);
+        if (mixed) {
+            pkf[dir][0].assign(hp.pk_w1[dir].begin(), hp.pk_w1[dir].end());
+            pkf[dir][1].assign(hp.pk_w2[dir].begin(), hp.pk_w2[dir].end());
+            d.pk_w1f[dir] = A.alloc<float>(m);
+            d.pk_w2f[dir] = A.alloc<float>(m);
+        }
+    }
+    c->launch.pk_lw[0] = c->pk_ok ? c->pk_lw[0].data() : nullptr;
+    c->launch.pk_lw[1] = c->pk_ok ? c->pk_lw[1].data() : nullptr;
     d.g1x = A.alloc<double>(4 * (size_t)ld);
     d.g1y = A.alloc<double>(4 * (size_t)ld);
     d.R = A.alloc<double>(4 * (size_t)ld);
@@ -903,6 +1031,19 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
     up(dinv, c->inv.data(), n * sizeof(int32_t));
     up(dcase_of, hp.case_of_i.data(), ld * sizeof(int32_t));
     up(dcase_uinf, cuinf.data(), cuinf.size() * sizeof(double));
+    for (int dir = 0; dir < 2; dir++) {
+        if (!d.pk_pt[dir]) continue;
+        const size_t m = hp.pk_pt[dir].size();
+        up((void *)d.pk_pt[dir], hp.pk_pt[dir].data(), m * sizeof(int32_t));
+        up((void *)d.pk_nbr[dir], hp.pk_nbr[dir].data(), m * sizeof(int32_t));
+        up((void *)d.pk_mb[dir], hp.pk_mb[dir].data(), m);
+        up((void *)d.pk_w1[dir], hp.pk_w1[dir].data(), m * sizeof(double));
+        up((void *)d.pk_w2[dir], hp.pk_w2[dir].data(), m * sizeof(double));
+        if (d.pk_w1f[dir]) {
+            up((void *)d.pk_w1f[dir], pkf[dir][0].data(), m * sizeof(float));
+            up((void *)d.pk_w2f[dir], pkf[dir][1].data(), m * sizeof(float));
+        }
+    }
     if (e == cudaSuccess) e = cudaMemset(c->case_state, 0, c->n_cases * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemset(c->case_it, 0, c->n_cases * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemset(c->case_hist0, 0, c->n_cases * sizeof(double));
@@ -1609,7 +1750,8 @@ lskum_status lskum_autotune(lskum_ctx *c, int32_t trial_iters, int32_t *tpp, int
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventCreate");
     for (int tp : {1, 2, 4, 8}) {
-        for (int gl : {2, 4, 8}) {
+        for (int gl : {2, 4, 8, 32}) {
+            if (gl == 32 && !c->pk_ok) continue;
             c->launch.tpp = tp;
             c->launch.sweep_lanes = gl;
             s = build_graphs(c);
@@ -1848,7 +1990,8 @@ lskum_status lskum_get_wall_distance(lskum_ctx *c, double *d)
 lskum_status lskum_set_launch_shape(lskum_ctx *c, int32_t tpp, int32_t sweep_lanes)
 {
     if (!c) return LSKUM_ERR_ARG;
-    if ((tpp != 1 && tpp != 2 && tpp != 4 && tpp != 8) || (sweep_lanes != 2 && sweep_lanes != 4 && sweep_lanes != 8))
+    if ((tpp != 1 && tpp != 2 && tpp != 4 && tpp != 8) ||
+        (sweep_lanes != 2 && sweep_lanes != 4 && sweep_lanes != 8 && !(sweep_lanes == 32 && c->pk_ok)))
         return fail(c, LSKUM_ERR_ARG, "launch shape %d, %d not supported", tpp, sweep_lanes);
     if (c->pending) return fail(c, LSKUM_ERR_ARG, "an enqueued run has not been waited for");
     c->launch.tpp = tpp;

@@ -112,10 +112,19 @@ struct Dev {
     // null in FP64 mode
     float *dUsf, *dUf;
     const float *lo_w1f, *lo_w2f, *up_w1f, *up_w2f;
-    // per colour level, its non-outer points ordered by decreasing list length
+    // per colour level, its swept points ordered by decreasing list length
     // (forward: lower list, backward: upper list), so a warp's groups share a
     // trip count
     const int32_t *sw_fwd, *sw_bwd;
+    // packed sweep form, [0] forward (lower lists), [1] backward (upper
+    // lists): warp w's 32 lanes hold slots 32w .. 32w+31, each with the sweep
+    // position of its point (-1: padding), neighbour, membership and weights;
+    // a point's slots are consecutive lanes of one warp (null when a list is
+    // longer than 32)
+    const int32_t *pk_pt[2], *pk_nbr[2];
+    const uint8_t *pk_mb[2];
+    const double *pk_w1[2], *pk_w2[2];
+    const float *pk_w1f[2], *pk_w2f[2];
     // per-case residual norm: stage 1 sums R_rho^2 over blocks of up to 256
     // points of one case (caller order), stage 2 adds each case's blocks
     double *blk;             // [n_blk][4] partial sums of the four components
@@ -143,7 +152,8 @@ struct Dev {
 struct Launch {
     int tpp;          // threads per point of the gradient and residual kernels (1, 2, 4, 8)
     int res_block;    // threads per block of the residual kernel
-    int sweep_lanes;  // lanes per point of the sweep kernels (2, 4, 8)
+    int sweep_lanes;  // lanes per point of the sweep kernels (2, 4, 8), or 32: the packed form
+    const int32_t *pk_lw[2];  // packed form: host arrays [n_levels + 1], first warp of each level
 };
 
 cudaError_t launch_iteration(const Dev &d, const Launch &L, int cur, int n_levels, const int32_t *lvl_beg,

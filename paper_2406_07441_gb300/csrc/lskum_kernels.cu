@@ -614,6 +614,143 @@ __device__ __forceinline__ SweepBufs<float> sweep_bufs<float>(const Dev &d, cons
     return {d.dUsf, d.dUf, d.lo_w1f, d.lo_w2f, d.up_w1f, d.up_w2f, st.primf};
 }
 
+// One slot of a point's lower / upper list: acc += w_s J_s(U_i) dW_i over the
+// split sub-stencils s the slot joins (exact AD or increment products).
+template <int JVP, typename T>
+__device__ __forceinline__ void sweep_slot(const Dev &d, const StateSet &st, const MathTables &Tb,
+                                           const T *__restrict__ dW, const T *__restrict__ pr, bool framed,
+                                           double e1x, double e1y, double e2x, double e2y, int i, int mb, T w1,
+                                           T w2, T acc[4])
+{
+    T dl[4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) dl[c] = dW[4 * i + c];
+    if (JVP == 0 && !framed) {
+        // interior frame: d = (1,0) or (0,1), S, A, exp(-S^2), B precomputed per point
+        const PrimT<T> P = load_prim(pr, i);
+        const T *rec = pr + (size_t)i * kPrimStride;
+        const JvpBase<T> jb = jvp_base(P, dl);
+#pragma unroll
+        for (int s = 0; s < 2; s++) {
+            const int m = s == 0 ? (mb & 3) : (mb >> 2);
+            if (!m) continue;
+            const T sg = (m & 1) ? T(1) : T(-1);
+            const int f = s == 0 ? P_SX : P_SY;
+            T J[4];
+            jvp_dir(P, jb, s == 0 ? T(1) : T(0), s == 0 ? T(0) : T(1), sg, rec[f], rec[(m & 1) ? f + 1 : f + 2],
+                    rec[f + 3], rec[f + 4], J);
+            const T w = s == 0 ? w1 : w2;
+#pragma unroll
+            for (int c = 0; c < 4; c++) acc[c] = fma(w, J[c], acc[c]);
+        }
+    } else {
+        // (t, n) frames and the increment form: evaluated in FP64
+        double dld[4];
+#pragma unroll
+        for (int c = 0; c < 4; c++) dld[c] = (double)dl[c];
+        const int ld = d.ld;
+        double Ui[4], Up[4];
+        PrimU P;
+        JvpBase<double> jb{};
+        if (JVP == 0) {
+            P = load_prim(st.prim, i);
+            jb = jvp_base(P, dld);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                Ui[c] = st.U[c * ld + i];
+                Up[c] = Ui[c] + dld[c];
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < 2; s++) {
+            const int m = s == 0 ? (mb & 3) : (mb >> 2);
+            if (!m) continue;
+            const double sg = (m & 1) ? 1.0 : -1.0;
+            const double ddx = s == 0 ? e1x : e2x, ddy = s == 0 ? e1y : e2y;
+            double J[4];
+            if (JVP == 0) {
+                const double S = (P.u * ddx + P.v * ddy) * P.sb;
+                double A, eS;
+                split_A(Tb, S, sg, A, eS);
+                jvp_dir(P, jb, ddx, ddy, sg, S, A, eS, eS * kInv2SqrtPi * P.isb, J);
+            } else {
+                double G1[4], G0[4];
+                flux_cons(Tb, Up, ddx, ddy, sg, G1);
+                flux_cons(Tb, Ui, ddx, ddy, sg, G0);
+#pragma unroll
+                for (int c = 0; c < 4; c++) J[c] = G1[c] - G0[c];
+            }
+            const T w = s == 0 ? w1 : w2;
+#pragma unroll
+            for (int c = 0; c < 4; c++) acc[c] = fma(w, (T)J[c], acc[c]);
+        }
+    }
+}
+
+// Point k's new increment from its list sum acc: forward dU*_k = -(R_k (+ S_k)
+// + acc) / D_k, backward dU_k = dU*_k - acc / D_k; normal momentum removed at
+// wall points.
+template <bool FWD, typename T>
+__device__ __forceinline__ void sweep_point(const Dev &d, const StateSet &st, const SweepBufs<T> &sb, int k,
+                                            bool wall, double e1x, double e1y, double e2x, double e2y,
+                                            const T acc[4])
+{
+    const int ld = d.ld;
+    const T iD = T(1) / (T)d.D[k];
+    T w[4];
+    if (FWD) {
+        double rhs[4];
+#pragma unroll
+        for (int c = 0; c < 4; c++) rhs[c] = d.R[c * ld + k];
+        if (d.lusgs == 1) {
+            // revised LU-SGS: -R - S with S_0 = -1/2 sum_s LS_s(1) A_d(U_0) dU_0 of
+            // the previous iteration's increment (still in dU: the backward
+            // sweep of this iteration has not run)
+            double dp[4];
+#pragma unroll
+            for (int c = 0; c < 4; c++) dp[c] = d.dUf ? (double)d.dUf[4 * k + c] : d.dU[4 * k + c];
+            const double *pk = st.prim + (size_t)k * kPrimStride;
+            double J1[4], J2[4];
+            euler_jvp(pk[P_RHO], pk[P_U], pk[P_V], pk[P_P], dp, e1x, e1y, J1);
+            euler_jvp(pk[P_RHO], pk[P_U], pk[P_V], pk[P_P], dp, e2x, e2y, J2);
+            const double l1 = d.geo[G_LS1_0 * ld + k] + d.geo[G_LS1_1 * ld + k];
+            const double l2 = d.geo[G_LS1_2 * ld + k] + d.geo[G_LS1_3 * ld + k];
+#pragma unroll
+            for (int c = 0; c < 4; c++) rhs[c] -= 0.5 * (l1 * J1[c] + l2 * J2[c]);  // R + S
+        }
+#pragma unroll
+        for (int c = 0; c < 4; c++) w[c] = -((T)rhs[c] + acc[c]) * iD;
+    } else {
+#pragma unroll
+        for (int c = 0; c < 4; c++) w[c] = fma(-acc[c], iD, sb.dUs[4 * k + c]);
+    }
+    if (wall) {
+        const T nx = (T)d.wnx[k], ny = (T)d.wny[k];
+        const T mn = w[1] * nx + w[2] * ny;
+        w[1] -= mn * nx;
+        w[2] -= mn * ny;
+    }
+    T *out = FWD ? sb.dUs : sb.dU;
+#pragma unroll
+    for (int c = 0; c < 4; c++) out[4 * k + c] = w[c];
+}
+
+// The frame of point k: (1,0), (0,1), or (t, n) at wall and kinetic outer points.
+__device__ __forceinline__ void point_frame(const Dev &d, int k, bool framed, double &e1x, double &e1y, double &e2x,
+                                            double &e2y)
+{
+    e1x = 1.0, e1y = 0.0, e2x = 0.0, e2y = 1.0;
+    if (framed) {
+        const int ld = d.ld;
+        e1x = d.geo[G_E1X * ld + k];
+        e1y = d.geo[G_E1Y * ld + k];
+        e2x = d.geo[G_E2X * ld + k];
+        e2y = d.geo[G_E2Y * ld + k];
+    }
+}
+
+// G lanes per point over the point's list, butterfly reduction.
 template <int JVP, bool FWD, int G, typename T>
 __global__ void __launch_bounds__(256) k_sweep(Dev d, StateSet st, int lb, int le)
 {
@@ -634,127 +771,67 @@ __global__ void __launch_bounds__(256) k_sweep(Dev d, StateSet st, int lb, int l
     const T *__restrict__ w1s = FWD ? sb.lo_w1 : sb.up_w1;
     const T *__restrict__ w2s = FWD ? sb.lo_w2 : sb.up_w2;
     const T *__restrict__ dW = FWD ? sb.dUs : sb.dU;
-    const T *__restrict__ pr = sb.prim;
-    const int ld = d.ld;
     const int fk = d.flag[k];
-    const bool wall = fk == kWall, framed = fk != kInterior;  // (t, n): wall and kinetic outer points
-    double e1x = 1.0, e1y = 0.0, e2x = 0.0, e2y = 1.0;
-    if (framed) {
-        e1x = d.geo[G_E1X * ld + k];
-        e1y = d.geo[G_E1Y * ld + k];
-        e2x = d.geo[G_E2X * ld + k];
-        e2y = d.geo[G_E2Y * ld + k];
-    }
+    const bool wall = fk == kWall, framed = fk != kInterior;
+    double e1x, e1y, e2x, e2y;
+    point_frame(d, k, framed, e1x, e1y, e2x, e2y);
     T acc[4] = {T(0), T(0), T(0), T(0)};
     const int beg = off[k], end = live ? off[k + 1] : beg;
-    for (int e = beg + sub; e < end; e += G) {
-        const int i = nbr[e];
-        const int mb = mbs[e];
-        T dl[4];
-#pragma unroll
-        for (int c = 0; c < 4; c++) dl[c] = dW[4 * i + c];
-        if (JVP == 0 && !framed) {
-            // interior frame: d = (1,0) or (0,1), S, A, exp(-S^2), B precomputed per point
-            const PrimT<T> P = load_prim(pr, i);
-            const T *rec = pr + (size_t)i * kPrimStride;
-            const JvpBase<T> jb = jvp_base(P, dl);
-#pragma unroll
-            for (int s = 0; s < 2; s++) {
-                const int m = s == 0 ? (mb & 3) : (mb >> 2);
-                if (!m) continue;
-                const T sg = (m & 1) ? T(1) : T(-1);
-                const int f = s == 0 ? P_SX : P_SY;
-                T J[4];
-                jvp_dir(P, jb, s == 0 ? T(1) : T(0), s == 0 ? T(0) : T(1), sg, rec[f], rec[(m & 1) ? f + 1 : f + 2],
-                        rec[f + 3], rec[f + 4], J);
-                const T w = s == 0 ? w1s[e] : w2s[e];
-#pragma unroll
-                for (int c = 0; c < 4; c++) acc[c] = fma(w, J[c], acc[c]);
-            }
-        } else {
-            // (t, n) frames and the increment form: evaluated in FP64
-            double dld[4];
-#pragma unroll
-            for (int c = 0; c < 4; c++) dld[c] = (double)dl[c];
-            double Ui[4], Up[4];
-            PrimU P;
-            JvpBase<double> jb{};
-            if (JVP == 0) {
-                P = load_prim(st.prim, i);
-                jb = jvp_base(P, dld);
-            } else {
-#pragma unroll
-                for (int c = 0; c < 4; c++) {
-                    Ui[c] = st.U[c * ld + i];
-                    Up[c] = Ui[c] + dld[c];
-                }
-            }
-#pragma unroll
-            for (int s = 0; s < 2; s++) {
-                const int m = s == 0 ? (mb & 3) : (mb >> 2);
-                if (!m) continue;
-                const double sg = (m & 1) ? 1.0 : -1.0;
-                const double ddx = s == 0 ? e1x : e2x, ddy = s == 0 ? e1y : e2y;
-                double J[4];
-                if (JVP == 0) {
-                    const double S = (P.u * ddx + P.v * ddy) * P.sb;
-                    double A, eS;
-                    split_A(Tb, S, sg, A, eS);
-                    jvp_dir(P, jb, ddx, ddy, sg, S, A, eS, eS * kInv2SqrtPi * P.isb, J);
-                } else {
-                    double G1[4], G0[4];
-                    flux_cons(Tb, Up, ddx, ddy, sg, G1);
-                    flux_cons(Tb, Ui, ddx, ddy, sg, G0);
-#pragma unroll
-                    for (int c = 0; c < 4; c++) J[c] = G1[c] - G0[c];
-                }
-                const T w = s == 0 ? w1s[e] : w2s[e];
-#pragma unroll
-                for (int c = 0; c < 4; c++) acc[c] = fma(w, (T)J[c], acc[c]);
-            }
-        }
-    }
+    for (int e = beg + sub; e < end; e += G)
+        sweep_slot<JVP, T>(d, st, Tb, dW, sb.prim, framed, e1x, e1y, e2x, e2y, nbr[e], mbs[e], w1s[e], w2s[e], acc);
 #pragma unroll
     for (int c = 0; c < 4; c++) acc[c] = group_sum<G>(acc[c]);
-    if (live && sub == 0) {
-        const T iD = T(1) / (T)d.D[k];
-        T w[4];
-        if (FWD) {
-            double rhs[4];
-#pragma unroll
-            for (int c = 0; c < 4; c++) rhs[c] = d.R[c * ld + k];
-            if (d.lusgs == 1) {
-                // revised LU-SGS: -R - S with S_0 = -1/2 sum_s LS_s(1) A_d(U_0) dU_0 of
-                // the previous iteration's increment (still in dU: the backward
-                // sweep of this iteration has not run)
-                double dp[4];
-#pragma unroll
-                for (int c = 0; c < 4; c++) dp[c] = d.dUf ? (double)d.dUf[4 * k + c] : d.dU[4 * k + c];
-                const double *pk = st.prim + (size_t)k * kPrimStride;
-                double J1[4], J2[4];
-                euler_jvp(pk[P_RHO], pk[P_U], pk[P_V], pk[P_P], dp, e1x, e1y, J1);
-                euler_jvp(pk[P_RHO], pk[P_U], pk[P_V], pk[P_P], dp, e2x, e2y, J2);
-                const double l1 = d.geo[G_LS1_0 * ld + k] + d.geo[G_LS1_1 * ld + k];
-                const double l2 = d.geo[G_LS1_2 * ld + k] + d.geo[G_LS1_3 * ld + k];
-#pragma unroll
-                for (int c = 0; c < 4; c++) rhs[c] -= 0.5 * (l1 * J1[c] + l2 * J2[c]);  // R + S
-            }
-#pragma unroll
-            for (int c = 0; c < 4; c++) w[c] = -((T)rhs[c] + acc[c]) * iD;
-        } else {
-#pragma unroll
-            for (int c = 0; c < 4; c++) w[c] = fma(-acc[c], iD, sb.dUs[4 * k + c]);
-        }
-        if (wall) {
-            const T nx = (T)d.wnx[k], ny = (T)d.wny[k];
-            const T mn = w[1] * nx + w[2] * ny;
-            w[1] -= mn * nx;
-            w[2] -= mn * ny;
-        }
-        T *out = FWD ? sb.dUs : sb.dU;
-#pragma unroll
-        for (int c = 0; c < 4; c++) out[4 * k + c] = w[c];
+    if (live && sub == 0) sweep_point<FWD, T>(d, st, sb, k, wall, e1x, e1y, e2x, e2y, acc);
+}
+
+// Packed form: one lane per list slot.  At create the level's points (in
+// sweep order) are packed whole into warps of up to 32 slots (a point with
+// an empty list takes one idle slot), so lanes are not left idle by lists
+// shorter than a lane group; a segmented suffix sum over the lanes of each
+// point (fixed tree order, no atomics) leaves the point's sum in its first
+// lane, which finishes the point.  Warps [wb, we) are the level's.
+template <int JVP, bool FWD, typename T>
+__global__ void __launch_bounds__(256) k_sweep_packed(Dev d, StateSet st, int wb, int we)
+{
+    __shared__ MathTables Tb;
+    if (halted(d.ctrl)) return;
+    load_math_tables(Tb);
+    __syncthreads();
+    const int gw = wb + (blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    if (gw >= we) return;  // whole warps only (blocks are whole warps)
+    const int lane = threadIdx.x & 31;
+    const int dir = FWD ? 0 : 1;
+    const size_t e = (size_t)gw * 32 + lane;
+    const int pos = d.pk_pt[dir][e];  // sweep position of the slot's point, -1: padding
+    const int k = pos >= 0 ? (FWD ? d.sw_fwd : d.sw_bwd)[pos] : 0;
+    const bool live = pos >= 0 && !frozen(d, k);
+    const SweepBufs<T> sb = sweep_bufs<T>(d, st);
+    const T *__restrict__ dW = FWD ? sb.dUs : sb.dU;
+    const int fk = d.flag[k];
+    const bool wall = fk == kWall, framed = fk != kInterior;
+    double e1x, e1y, e2x, e2y;
+    point_frame(d, k, framed, e1x, e1y, e2x, e2y);
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+    const int mb = d.pk_mb[dir][e];
+    if (live && mb) {
+        const T w1 = sizeof(T) == 4 ? (T)d.pk_w1f[dir][e] : (T)d.pk_w1[dir][e];
+        const T w2 = sizeof(T) == 4 ? (T)d.pk_w2f[dir][e] : (T)d.pk_w2[dir][e];
+        sweep_slot<JVP, T>(d, st, Tb, dW, sb.prim, framed, e1x, e1y, e2x, e2y, d.pk_nbr[dir][e], mb, w1, w2, acc);
     }
+    // segmented suffix sum: lane l adds lane l + o when both hold the same point
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int p2 = __shfl_down_sync(kFull, pos, o);
+        T v[4];
+#pragma unroll
+        for (int c = 0; c < 4; c++) v[c] = __shfl_down_sync(kFull, acc[c], o);
+        if (lane + o < 32 && p2 == pos) {
+#pragma unroll
+            for (int c = 0; c < 4; c++) acc[c] += v[c];
+        }
+    }
+    const int prev = __shfl_up_sync(kFull, pos, 1);
+    if (live && (lane == 0 || prev != pos)) sweep_point<FWD, T>(d, st, sb, k, wall, e1x, e1y, e2x, e2y, acc);
 }
 
 // ---------------------------------------------------------------------------
@@ -999,6 +1076,29 @@ void enqueue_sweeps_g(const Dev &d, int cur, int n_levels, const int32_t *lvl_be
 }
 
 template <int JVP>
+void enqueue_sweeps_packed(const Dev &d, const Launch &L, int cur, int n_levels, cudaStream_t s, int *launches,
+                           bool fwd, bool bwd)
+{
+    const StateSet st = d.set[cur];
+    for (int l = 0; fwd && l < n_levels; l++) {
+        const int wb = L.pk_lw[0][l], we = L.pk_lw[0][l + 1];
+        if (we <= wb) continue;
+        const int blocks = ((we - wb) * 32 + 255) / 256;
+        if (d.precision) k_sweep_packed<JVP, true, float><<<blocks, 256, 0, s>>>(d, st, wb, we);
+        else k_sweep_packed<JVP, true, double><<<blocks, 256, 0, s>>>(d, st, wb, we);
+        (*launches)++;
+    }
+    for (int l = n_levels - 1; bwd && l >= 0; l--) {
+        const int wb = L.pk_lw[1][l], we = L.pk_lw[1][l + 1];
+        if (we <= wb) continue;
+        const int blocks = ((we - wb) * 32 + 255) / 256;
+        if (d.precision) k_sweep_packed<JVP, false, float><<<blocks, 256, 0, s>>>(d, st, wb, we);
+        else k_sweep_packed<JVP, false, double><<<blocks, 256, 0, s>>>(d, st, wb, we);
+        (*launches)++;
+    }
+}
+
+template <int JVP>
 cudaError_t enqueue_sweeps(const Dev &d, const Launch &L, int cur, int n_levels, const int32_t *lvl_beg,
                            const int32_t *lvl_act_end, cudaStream_t s, int *launches, bool fwd, bool bwd)
 {
@@ -1006,6 +1106,10 @@ cudaError_t enqueue_sweeps(const Dev &d, const Launch &L, int cur, int n_levels,
     case 2: enqueue_sweeps_g<JVP, 2>(d, cur, n_levels, lvl_beg, lvl_act_end, s, launches, fwd, bwd); break;
     case 4: enqueue_sweeps_g<JVP, 4>(d, cur, n_levels, lvl_beg, lvl_act_end, s, launches, fwd, bwd); break;
     case 8: enqueue_sweeps_g<JVP, 8>(d, cur, n_levels, lvl_beg, lvl_act_end, s, launches, fwd, bwd); break;
+    case 32:
+        if (!d.pk_pt[0] || !L.pk_lw[0]) return cudaErrorInvalidValue;
+        enqueue_sweeps_packed<JVP>(d, L, cur, n_levels, s, launches, fwd, bwd);
+        break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

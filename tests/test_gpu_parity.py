@@ -369,3 +369,58 @@ def test_four_component_residual_history():
     act = c.flag != 2
     ref = np.sqrt(np.sum(r["R"][act] ** 2, axis=0))
     assert np.max(np.abs(h4[-1] - ref) / ref) < 1e-10
+
+
+@pytest.mark.parametrize("jvp", [0, 1])
+def test_packed_sweeps_match_oracle(jvp):
+    """The packed sweep form (sweep_lanes = 32: one lane per list slot, whole
+    points packed into warps, segmented sums): one iteration's increments and
+    a 30-iteration history against the oracle, FP64 and mixed precision."""
+    lk = _lskum()
+    c = cached_cloud("jit64x32", CLOUDS["jit64x32"])
+    o = O.Oracle(c)
+    U0 = o.initial_state(0.63, 2.0)
+    r = o.run(U0, 1, cfl=100.0, K=3, jvp=jvp, first_order=3)
+    s = lk.Solver(c, 0.63, 2.0, jvp=jvp, first_order_iters=3)
+    s.set_launch_shape(2, 32)
+    assert s.run(1) == 1
+    assert nrel(s.field(lk.FIELD_DUS), r["dUs"]) < 1e-10
+    assert nrel(s.field(lk.FIELD_DU), r["dU"]) < 1e-10
+    assert nrel(s.field(lk.FIELD_U), r["U"]) < 1e-12
+    r2 = o.run(U0, 30, cfl=100.0, K=3, jvp=jvp, first_order=3)
+    for precision, bar in ((0, 1e-10), (1, 1e-4)):
+        s2 = lk.Solver(c, 0.63, 2.0, jvp=jvp, first_order_iters=3, precision=precision)
+        s2.set_launch_shape(4, 32)
+        assert s2.run(30) == 30
+        h = s2.residuals()
+        assert np.max(np.abs(h - r2["hist"]) / r2["hist"]) < bar
+    # the same launch count as the lanes-per-point form
+    assert s2.info()["launches_per_iter"] == lk.Solver(c, 0.63, 2.0).info()["launches_per_iter"]
+
+
+def test_packed_sweeps_kinetic_and_batch():
+    """Packed sweeps with the kinetic far field (outer points in the lists)
+    and in a batch (frozen cases skip their points): equal to the
+    lanes-per-point form to rounding and to single solves bit for bit."""
+    lk = _lskum()
+    c1 = cg.naca0012_block(40, 16, kinetic_outer=True)
+    c2 = cg.naca0012_jittered(48, 20, seed=11, kinetic_outer=True)
+    kw = dict(inner_iters=2, first_order_iters=3, farfield=lk.FARFIELD_KINETIC)
+    a = lk.Solver(c1, 1.2, 0.0, **kw)
+    b = lk.Solver(c1, 1.2, 0.0, **kw)
+    a.set_launch_shape(2, 8)
+    b.set_launch_shape(2, 32)
+    assert a.run(10) == 10 and b.run(10) == 10
+    assert nrel(b.field(lk.FIELD_U), a.field(lk.FIELD_U)) < 1e-12
+    assert np.max(np.abs(b.residuals() - a.residuals()) / a.residuals()) < 1e-11
+    conds = [(1.2, 0.0), (0.63, 2.0)]
+    bt = lk.Solver.batch([c1, c2], conds, **kw)
+    bt.set_launch_shape(2, 32)
+    assert bt.run(6) == 6
+    U = bt.field(lk.FIELD_U)
+    for cs, (c, (m, al)) in enumerate(zip([c1, c2], conds)):
+        s = lk.Solver(c, m, al, **kw)
+        s.set_launch_shape(2, 32)
+        assert s.run(6) == 6
+        info = bt.case_info(cs)
+        assert np.array_equal(U[info["first_point"]:info["first_point"] + c.n], s.field(lk.FIELD_U))
