@@ -63,12 +63,12 @@ __device__ __forceinline__ void split_E(const MathTables &T, double S, double &E
     E = eS * p;
 }
 
-// A = (1 + sg erf S)/2 (sg = +-1) and eS = exp(-S^2).
-__device__ __forceinline__ void split_A(const MathTables &T, double S, double sg, double &A, double &eS)
+// A = (1 + sg erf S)/2 (sg = +1 if pos, else -1) and eS = exp(-S^2).
+__device__ __forceinline__ void split_A(const MathTables &T, double S, bool pos, double &A, double &eS)
 {
     double E;
     split_E(T, S, E, eS);
-    A = ((__double2hiint(S) ^ __double2hiint(sg)) >= 0) ? 1.0 - E : E;
+    A = ((__double2hiint(S) >= 0) == pos) ? 1.0 - E : E;
 }
 
 }  // namespace lskum

@@ -66,8 +66,8 @@ enum GeoField {
 // cache lines instead of one line per field.
 enum PrimField {
     P_RHO, P_IRHO, P_U, P_V, P_P, P_BETA, P_SB, P_ISB, P_I2P, P_Q2, P_E1, P_E2,
-    P_SX, P_APX, P_AMX, P_EXPX, P_BX,  // direction (1,0): S, A+, A-, exp(-S^2), B
-    P_SY, P_APY, P_AMY, P_EXPY, P_BY,  // direction (0,1)
+    P_BSX, P_APX, P_AMX, P_EKX, P_BX,  // direction (1,0): 2 B S, A+, A-, exp(-S^2)/sqrt(pi), B
+    P_BSY, P_APY, P_AMY, P_EKY, P_BY,  // direction (0,1)
     P_NFIELDS
 };
 constexpr int kPrimStride = 24;

@@ -87,18 +87,20 @@ __device__ __forceinline__ Prim q_to_prim(const MathTables &T, const double q[4]
     return P;
 }
 
-// Kinetic split flux G_d^sg (half-range moments of the Maxwellian, sg = +-1)
-// in unit direction d: DIR 0 is (1,0), DIR 1 is (0,1), DIR 2 is (dx, dy).
+// Kinetic split flux G_d^sg (half-range moments of the Maxwellian; sg = +1
+// if pos, else -1, applied by negation) in unit direction d: DIR 0 is (1,0),
+// DIR 1 is (0,1), DIR 2 is (dx, dy).
 template <int DIR>
-__device__ __forceinline__ void split_flux(const MathTables &T, const Prim &P, double dx, double dy, double sg,
+__device__ __forceinline__ void split_flux(const MathTables &T, const Prim &P, double dx, double dy, bool pos,
                                           double G[4])
 {
     const double ud = DIR == 0 ? P.u : (DIR == 1 ? P.v : P.u * dx + P.v * dy);
     const double S = ud * P.sb;
     double A, eS;
-    split_A(T, S, sg, A, eS);
+    split_A(T, S, pos, A, eS);
     const double B = eS * kInv2SqrtPi * P.isb;
-    const double M1 = fma(ud, A, sg * B);
+    const double sB = pos ? B : -B;
+    const double M1 = fma(ud, A, sB);
     const double rm = P.rho * M1;
     const double pA = P.p * A;
     G[0] = rm;
@@ -112,7 +114,7 @@ __device__ __forceinline__ void split_flux(const MathTables &T, const Prim &P, d
         G[1] = fma(rm, P.u, pA * dx);
         G[2] = fma(rm, P.v, pA * dy);
     }
-    G[3] = fma(ud * P.e1, A, sg * P.e2 * B);
+    G[3] = fma(ud * P.e1, A, P.e2 * sB);
 }
 
 // Primal quantities of a conserved state for the Jacobian products (FP64,
@@ -171,6 +173,7 @@ __device__ __forceinline__ PrimT<T> load_prim(const T *__restrict__ pr, int i)
 template <typename T>
 struct JvpBase {
     T drho, du, dv, dk, dp, dsb;
+    T dsbi, de1, de2;  // dsb / sqrt(beta), d(3.5 p + k), d(3 p + k)
 };
 
 template <typename T>
@@ -185,6 +188,9 @@ __device__ __forceinline__ JvpBase<T> jvp_base(const PrimT<T> &P, const T dl[4])
     b.dp = T(kGm1) * (dl[3] - b.dk);
     const T dbeta = (b.drho - T(2.0) * P.beta * b.dp) * P.i2p;
     b.dsb = T(0.5) * dbeta * P.isb;
+    b.dsbi = b.dsb * P.isb;
+    b.de1 = T(3.5) * b.dp + b.dk;
+    b.de2 = T(3.0) * b.dp + b.dk;
     return b;
 }
 
@@ -198,17 +204,50 @@ __device__ __forceinline__ void jvp_dir(const PrimT<T> &P, const JvpBase<T> &b, 
     const T dud = b.du * dx + b.dv * dy;
     const T dS = dud * P.sb + ud * b.dsb;
     const T dA = sg * eS * dS * T(kInvSqrtPi);
-    const T dB = -B * (T(2.0) * S * dS + b.dsb * P.isb);
+    const T dB = -B * (T(2.0) * S * dS + b.dsbi);
     const T M1 = ud * A + sg * B;
     const T dM1 = dud * A + ud * dA + sg * dB;
-    const T de1 = T(3.5) * b.dp + b.dk;
-    const T de2 = T(3.0) * b.dp + b.dk;
+    const T de1 = b.de1;
+    const T de2 = b.de2;
     const T drm = b.drho * M1 + P.rho * dM1;  // d(rho M1)
     const T rm = P.rho * M1;
     out[0] = drm;
     out[1] = drm * P.u + rm * b.du + (b.dp * A + P.p * dA) * dx;
     out[2] = drm * P.v + rm * b.dv + (b.dp * A + P.p * dA) * dy;
     out[3] = (dud * P.e1 + ud * de1) * A + ud * P.e1 * dA + sg * (de2 * B + P.e2 * dB);
+}
+
+// The same product along an axis (DIR 0: d = (1,0), DIR 1: (0,1)) from the
+// point's record: A, exp(-S^2)/sqrt(pi) (ek), B and 2 B S precomputed per
+// point, the direction-free tangents in the base, signs applied by
+// negation (no multiplication by 0, 1 or +-1 is left to the FP64 pipe).
+template <int DIR, typename T>
+__device__ __forceinline__ void jvp_axis(const PrimT<T> &P, const JvpBase<T> &b, bool pos, T A, T ek, T B, T B2S,
+                                         T out[4])
+{
+    const T ud = DIR == 0 ? P.u : P.v;
+    const T dud = DIR == 0 ? b.du : b.dv;
+    const T dS = fma(dud, P.sb, ud * b.dsb);
+    const T dA0 = ek * dS;
+    const T dA = pos ? dA0 : -dA0;
+    const T dB0 = -fma(B2S, dS, B * b.dsbi);  // tangent of B
+    const T sB = pos ? B : -B, sdB = pos ? dB0 : -dB0;
+    const T M1 = fma(ud, A, sB);
+    const T dM1 = fma(dud, A, fma(ud, dA, sdB));
+    const T rm = P.rho * M1;
+    const T drm = fma(b.drho, M1, P.rho * dM1);
+    const T pA = fma(b.dp, A, P.p * dA);  // tangent of p A
+    out[0] = drm;
+    if (DIR == 0) {
+        out[1] = fma(drm, P.u, fma(rm, b.du, pA));
+        out[2] = fma(drm, P.v, rm * b.dv);
+    } else {
+        out[1] = fma(drm, P.u, rm * b.du);
+        out[2] = fma(drm, P.v, fma(rm, b.dv, pA));
+    }
+    const T t1 = fma(dud, P.e1, ud * b.de1);
+    const T t3 = fma(b.de2, sB, P.e2 * sdB);
+    out[3] = fma(t1, A, fma(ud * P.e1, dA, t3));
 }
 
 // Unsplit Euler-flux Jacobian product A_d(U) dU in direction d = (dx, dy)
@@ -230,22 +269,23 @@ __device__ __forceinline__ void euler_jvp(double rho, double u, double v, double
     out[3] = (dU[3] + dp) * ud + (E + p) * dud;
 }
 
-__device__ __forceinline__ void flux_cons(const MathTables &T, const double U[4], double dx, double dy, double sg,
+__device__ __forceinline__ void flux_cons(const MathTables &T, const double U[4], double dx, double dy, bool pos,
                                           double G[4])
 {
     const PrimU P = prim_from_cons(U);
     const double ud = P.u * dx + P.v * dy;
     const double S = ud * P.sb;
     double A, eS;
-    split_A(T, S, sg, A, eS);
+    split_A(T, S, pos, A, eS);
     const double B = eS * kInv2SqrtPi * P.isb;
-    const double M1 = fma(ud, A, sg * B);
+    const double sB = pos ? B : -B;
+    const double M1 = fma(ud, A, sB);
     const double rm = P.rho * M1;
     const double pA = P.p * A;
     G[0] = rm;
     G[1] = fma(rm, P.u, pA * dx);
     G[2] = fma(rm, P.v, pA * dy);
-    G[3] = fma(ud * P.e1, A, sg * P.e2 * B);
+    G[3] = fma(ud * P.e1, A, P.e2 * sB);
 }
 
 template <int TPP, typename T>
@@ -393,15 +433,15 @@ __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const doub
             const Prim Pi = q_to_prim(T, qi);
             const Prim P0 = q_to_prim(T, q0t);
             if (mb & 3) {
-                const double sg = (mb & 1) ? 1.0 : -1.0;
+                const bool pos = mb & 1;
                 const double w = d.w1[e];
                 double Gi[4], G0[4];
                 if (framed) {
-                    split_flux<2>(T, Pi, e1x, e1y, sg, Gi);
-                    split_flux<2>(T, P0, e1x, e1y, sg, G0);
+                    split_flux<2>(T, Pi, e1x, e1y, pos, Gi);
+                    split_flux<2>(T, P0, e1x, e1y, pos, G0);
                 } else {
-                    split_flux<0>(T, Pi, 1.0, 0.0, sg, Gi);
-                    split_flux<0>(T, P0, 1.0, 0.0, sg, G0);
+                    split_flux<0>(T, Pi, 1.0, 0.0, pos, Gi);
+                    split_flux<0>(T, P0, 1.0, 0.0, pos, G0);
                 }
 #pragma unroll
                 for (int c = 0; c < 4; c++) {
@@ -410,15 +450,15 @@ __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const doub
                 }
             }
             if (mb & 12) {
-                const double sg = (mb & 4) ? 1.0 : -1.0;
+                const bool pos = mb & 4;
                 const double w = d.w2[e];
                 double Gi[4], G0[4];
                 if (framed) {
-                    split_flux<2>(T, Pi, e2x, e2y, sg, Gi);
-                    split_flux<2>(T, P0, e2x, e2y, sg, G0);
+                    split_flux<2>(T, Pi, e2x, e2y, pos, Gi);
+                    split_flux<2>(T, P0, e2x, e2y, pos, G0);
                 } else {
-                    split_flux<1>(T, Pi, 0.0, 1.0, sg, Gi);
-                    split_flux<1>(T, P0, 0.0, 1.0, sg, G0);
+                    split_flux<1>(T, Pi, 0.0, 1.0, pos, Gi);
+                    split_flux<1>(T, P0, 0.0, 1.0, pos, G0);
                 }
 #pragma unroll
                 for (int c = 0; c < 4; c++) {
@@ -449,8 +489,8 @@ __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const doub
             }
             if (!same) {  // (equal states give exactly 0)
                 double Gi[4], G0[4];
-                flux_cons(T, Ui, e2x, e2y, -1.0, Gi);
-                flux_cons(T, U0, e2x, e2y, -1.0, G0);
+                flux_cons(T, Ui, e2x, e2y, false, Gi);
+                flux_cons(T, U0, e2x, e2y, false, G0);
                 const double l3 = d.geo[G_LS1_3 * ld + k];
 #pragma unroll
                 for (int c = 0; c < 4; c++) R[c] = fma(l3, Gi[c] - G0[c], R[c]);
@@ -626,7 +666,8 @@ __device__ __forceinline__ void sweep_slot(const Dev &d, const StateSet &st, con
 #pragma unroll
     for (int c = 0; c < 4; c++) dl[c] = dW[4 * i + c];
     if (JVP == 0 && !framed) {
-        // interior frame: d = (1,0) or (0,1), S, A, exp(-S^2), B precomputed per point
+        // interior frame: d = (1,0) or (0,1); A+-, exp(-S^2)/sqrt(pi), B and
+        // 2 B S precomputed per point
         const PrimT<T> P = load_prim(pr, i);
         const T *rec = pr + (size_t)i * kPrimStride;
         const JvpBase<T> jb = jvp_base(P, dl);
@@ -634,11 +675,12 @@ __device__ __forceinline__ void sweep_slot(const Dev &d, const StateSet &st, con
         for (int s = 0; s < 2; s++) {
             const int m = s == 0 ? (mb & 3) : (mb >> 2);
             if (!m) continue;
-            const T sg = (m & 1) ? T(1) : T(-1);
-            const int f = s == 0 ? P_SX : P_SY;
+            const bool pos = m & 1;
             T J[4];
-            jvp_dir(P, jb, s == 0 ? T(1) : T(0), s == 0 ? T(0) : T(1), sg, rec[f], rec[(m & 1) ? f + 1 : f + 2],
-                    rec[f + 3], rec[f + 4], J);
+            if (s == 0)
+                jvp_axis<0, T>(P, jb, pos, rec[pos ? P_APX : P_AMX], rec[P_EKX], rec[P_BX], rec[P_BSX], J);
+            else
+                jvp_axis<1, T>(P, jb, pos, rec[pos ? P_APY : P_AMY], rec[P_EKY], rec[P_BY], rec[P_BSY], J);
             const T w = s == 0 ? w1 : w2;
 #pragma unroll
             for (int c = 0; c < 4; c++) acc[c] = fma(w, J[c], acc[c]);
@@ -666,18 +708,19 @@ __device__ __forceinline__ void sweep_slot(const Dev &d, const StateSet &st, con
         for (int s = 0; s < 2; s++) {
             const int m = s == 0 ? (mb & 3) : (mb >> 2);
             if (!m) continue;
-            const double sg = (m & 1) ? 1.0 : -1.0;
+            const bool pos = m & 1;
+            const double sg = pos ? 1.0 : -1.0;
             const double ddx = s == 0 ? e1x : e2x, ddy = s == 0 ? e1y : e2y;
             double J[4];
             if (JVP == 0) {
                 const double S = (P.u * ddx + P.v * ddy) * P.sb;
                 double A, eS;
-                split_A(Tb, S, sg, A, eS);
+                split_A(Tb, S, pos, A, eS);
                 jvp_dir(P, jb, ddx, ddy, sg, S, A, eS, eS * kInv2SqrtPi * P.isb, J);
             } else {
                 double G1[4], G0[4];
-                flux_cons(Tb, Up, ddx, ddy, sg, G1);
-                flux_cons(Tb, Ui, ddx, ddy, sg, G0);
+                flux_cons(Tb, Up, ddx, ddy, pos, G1);
+                flux_cons(Tb, Ui, ddx, ddy, pos, G0);
 #pragma unroll
                 for (int c = 0; c < 4; c++) J[c] = G1[c] - G0[c];
             }
@@ -917,16 +960,17 @@ __global__ void __launch_bounds__(256) k_update(Dev d, int cur)
     double Ex, ex, Ey, ey;
     split_E(T, sx, Ex, ex);
     split_E(T, sy, Ey, ey);
-    pr[P_SX] = sx;
+    const double bx = ex * kInv2SqrtPi * P.isb, by = ey * kInv2SqrtPi * P.isb;
+    pr[P_BSX] = 2.0 * bx * sx;
     pr[P_APX] = sx >= 0.0 ? 1.0 - Ex : Ex;
     pr[P_AMX] = sx >= 0.0 ? Ex : 1.0 - Ex;
-    pr[P_EXPX] = ex;
-    pr[P_BX] = ex * kInv2SqrtPi * P.isb;
-    pr[P_SY] = sy;
+    pr[P_EKX] = ex * kInvSqrtPi;
+    pr[P_BX] = bx;
+    pr[P_BSY] = 2.0 * by * sy;
     pr[P_APY] = sy >= 0.0 ? 1.0 - Ey : Ey;
     pr[P_AMY] = sy >= 0.0 ? Ey : 1.0 - Ey;
-    pr[P_EXPY] = ey;
-    pr[P_BY] = ey * kInv2SqrtPi * P.isb;
+    pr[P_EKY] = ey * kInvSqrtPi;
+    pr[P_BY] = by;
     if (dst.primf) {  // mixed precision: the sweeps' FP32 copy of the record
         float *pf = dst.primf + (size_t)k * kPrimStride;
 #pragma unroll
