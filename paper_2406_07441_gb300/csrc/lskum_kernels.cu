@@ -58,6 +58,17 @@ __device__ __forceinline__ bool frozen(const Dev &d, int k)
     return d.n_cases > 1 && frozen_state(((const volatile int32_t *)d.case_state)[d.case_of[k]]);
 }
 
+// x with its sign flipped unless pos: an integer XOR of the sign bit, so a
+// selected sign costs no FP64 (or FP32) instruction.
+__device__ __forceinline__ double signed_by(double x, bool pos)
+{
+    return __hiloint2double(__double2hiint(x) ^ (pos ? 0 : (int)0x80000000), __double2loint(x));
+}
+__device__ __forceinline__ float signed_by(float x, bool pos)
+{
+    return __int_as_float(__float_as_int(x) ^ (pos ? 0 : (int)0x80000000));
+}
+
 // Primitive state carried through the residual.
 struct Prim {
     double rho, u, v, p, sb, isb, e1, e2;  // sb = sqrt(beta), isb = 1/sb,
@@ -99,7 +110,7 @@ __device__ __forceinline__ void split_flux(const MathTables &T, const Prim &P, d
     double A, eS;
     split_A(T, S, pos, A, eS);
     const double B = eS * kInv2SqrtPi * P.isb;
-    const double sB = pos ? B : -B;
+    const double sB = signed_by(B, pos);
     const double M1 = fma(ud, A, sB);
     const double rm = P.rho * M1;
     const double pA = P.p * A;
@@ -228,10 +239,9 @@ __device__ __forceinline__ void jvp_axis(const PrimT<T> &P, const JvpBase<T> &b,
     const T ud = DIR == 0 ? P.u : P.v;
     const T dud = DIR == 0 ? b.du : b.dv;
     const T dS = fma(dud, P.sb, ud * b.dsb);
-    const T dA0 = ek * dS;
-    const T dA = pos ? dA0 : -dA0;
-    const T dB0 = -fma(B2S, dS, B * b.dsbi);  // tangent of B
-    const T sB = pos ? B : -B, sdB = pos ? dB0 : -dB0;
+    const T dA = signed_by(ek * dS, pos);
+    const T sB = signed_by(B, pos);
+    const T sdB = signed_by(fma(B2S, dS, B * b.dsbi), !pos);  // sg times the tangent of B
     const T M1 = fma(ud, A, sB);
     const T dM1 = fma(dud, A, fma(ud, dA, sdB));
     const T rm = P.rho * M1;
@@ -278,7 +288,7 @@ __device__ __forceinline__ void flux_cons(const MathTables &T, const double U[4]
     double A, eS;
     split_A(T, S, pos, A, eS);
     const double B = eS * kInv2SqrtPi * P.isb;
-    const double sB = pos ? B : -B;
+    const double sB = signed_by(B, pos);
     const double M1 = fma(ud, A, sB);
     const double rm = P.rho * M1;
     const double pA = P.p * A;
