@@ -853,8 +853,7 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
         d.set[s].U = A.alloc<double>(4 * (size_t)ld);
         d.set[s].q = A.alloc<double>(4 * (size_t)ld);
         d.set[s].prim = A.alloc<double>((size_t)kPrimStride * ld);
-        d.qx[s] = A.alloc<double>(4 * (size_t)ld);
-        d.qy[s] = A.alloc<double>(4 * (size_t)ld);
+        d.gq[s] = A.alloc<double>(8 * (size_t)ld);
     }
     int32_t *dlo_off = A.alloc<int32_t>(n + 1), *dup_off = A.alloc<int32_t>(n + 1);
     int32_t *dlo_nbr = A.alloc<int32_t>(hp.lo_nbr.size()), *dup_nbr = A.alloc<int32_t>(hp.up_nbr.size());
@@ -1059,7 +1058,7 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy");
     // zero intermediates; D = 1 at outer points (never written by the kernels)
-    for (double *p : {d.R, d.dUs, d.dU, d.qx[0], d.qx[1], d.qy[0], d.qy[1]})
+    for (double *p : {d.R, d.dUs, d.dU, d.gq[0], d.gq[0] + 4 * (size_t)ld, d.gq[1], d.gq[1] + 4 * (size_t)ld})
         if (e == cudaSuccess) e = cudaMemset(p, 0, 4 * (size_t)ld * sizeof(double));
     std::vector<double> ones(ld, 1.0);
     up(d.D, ones.data(), ld * sizeof(double));
@@ -1394,23 +1393,24 @@ void *lskum_stream(lskum_ctx *c)
 }
 
 // Copy a per-point field to the host in caller order: reordered on the
-// device (from `comps` rows of stride ld, or `comps` values per point with
-// aos; FP32 when srcf is given), then one contiguous copy.
-static lskum_status download_to(lskum_ctx *c, const double *src, const float *srcf, int comps, bool aos,
+// device (from `comps` rows of stride ld when stride is 0, else `comps`
+// values of point k at stride * k; FP32 when srcf is given), then one
+// contiguous copy.
+static lskum_status download_to(lskum_ctx *c, const double *src, const float *srcf, int comps, int stride,
                                 double *out)
 {
     const size_t bytes = (size_t)comps * c->n * sizeof(double);
-    cudaError_t e = launch_to_caller(src, srcf, comps, aos, c->ld, c->n, c->dev.inv, c->dscratch, c->stream);
+    cudaError_t e = launch_to_caller(src, srcf, comps, stride, c->ld, c->n, c->dev.inv, c->dscratch, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, c->dscratch, bytes, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy D2H");
     return LSKUM_OK;
 }
 
-static lskum_status download(lskum_ctx *c, const double *src, int comps, std::vector<double> &out, bool aos = false)
+static lskum_status download(lskum_ctx *c, const double *src, int comps, std::vector<double> &out, int stride = 0)
 {
     out.resize((size_t)comps * c->n);
-    return download_to(c, src, nullptr, comps, aos, out.data());
+    return download_to(c, src, nullptr, comps, stride, out.data());
 }
 
 lskum_status lskum_get_field(lskum_ctx *c, int32_t field, double *out)
@@ -1420,23 +1420,22 @@ lskum_status lskum_get_field(lskum_ctx *c, int32_t field, double *out)
     const Dev &d = c->dev;
     const int K = d.K & 1;
     const double *src = nullptr;
-    int comps = 4;
-    bool aos = false;
+    int comps = 4, stride = 0;
     switch (field) {
     case LSKUM_FIELD_U: src = d.set[c->cur].U; break;
     case LSKUM_FIELD_Q: src = d.set[c->cur].q; break;
-    case LSKUM_FIELD_QX: src = d.qx[K]; break;
-    case LSKUM_FIELD_QY: src = d.qy[K]; break;
+    case LSKUM_FIELD_QX: src = d.gq[K]; stride = 8; break;
+    case LSKUM_FIELD_QY: src = d.gq[K] + 4; stride = 8; break;
     case LSKUM_FIELD_R: src = d.R; break;
     case LSKUM_FIELD_D: src = d.D; comps = 1; break;
-    case LSKUM_FIELD_DUS: src = d.dUs; aos = true; break;
-    case LSKUM_FIELD_DU: src = d.dU; aos = true; break;
+    case LSKUM_FIELD_DUS: src = d.dUs; stride = 4; break;
+    case LSKUM_FIELD_DU: src = d.dU; stride = 4; break;
     default: return fail(c, LSKUM_ERR_ARG, "unknown field %d", field);
     }
     const float *srcf = nullptr;
     if (d.precision && (field == LSKUM_FIELD_DUS || field == LSKUM_FIELD_DU))
         srcf = field == LSKUM_FIELD_DUS ? d.dUsf : d.dUf;  // FP32 increments of the mixed-precision sweeps
-    return download_to(c, src, srcf, comps, aos, out);
+    return download_to(c, src, srcf, comps, stride, out);
 }
 
 // Order stream `waiter` after the work already enqueued on `waited`.
@@ -1455,22 +1454,21 @@ lskum_status lskum_get_field_dev(lskum_ctx *c, int32_t field, double *out_dev, v
     const int K = d.K & 1;
     const double *src = nullptr;
     const float *srcf = nullptr;
-    int comps = 4;
-    bool aos = false;
+    int comps = 4, stride = 0;
     switch (field) {
     case LSKUM_FIELD_U: src = d.set[c->cur].U; break;
     case LSKUM_FIELD_Q: src = d.set[c->cur].q; break;
-    case LSKUM_FIELD_QX: src = d.qx[K]; break;
-    case LSKUM_FIELD_QY: src = d.qy[K]; break;
+    case LSKUM_FIELD_QX: src = d.gq[K]; stride = 8; break;
+    case LSKUM_FIELD_QY: src = d.gq[K] + 4; stride = 8; break;
     case LSKUM_FIELD_R: src = d.R; break;
     case LSKUM_FIELD_D: src = d.D; comps = 1; break;
-    case LSKUM_FIELD_DUS: src = d.dUs; srcf = d.precision ? d.dUsf : nullptr; aos = true; break;
-    case LSKUM_FIELD_DU: src = d.dU; srcf = d.precision ? d.dUf : nullptr; aos = true; break;
+    case LSKUM_FIELD_DUS: src = d.dUs; srcf = d.precision ? d.dUsf : nullptr; stride = 4; break;
+    case LSKUM_FIELD_DU: src = d.dU; srcf = d.precision ? d.dUf : nullptr; stride = 4; break;
     default: return fail(c, LSKUM_ERR_ARG, "unknown field %d", field);
     }
     cudaStream_t us = (cudaStream_t)cuda_stream;
     cudaError_t e = order_after(c, c->stream, us);
-    if (e == cudaSuccess) e = launch_to_caller(src, srcf, comps, aos, c->ld, c->n, d.inv, out_dev, c->stream);
+    if (e == cudaSuccess) e = launch_to_caller(src, srcf, comps, stride, c->ld, c->n, d.inv, out_dev, c->stream);
     if (e == cudaSuccess) e = order_after(c, us, c->stream);
     return e == cudaSuccess ? LSKUM_OK : cuda_fail(c, e, "field to device memory");
 }

@@ -97,7 +97,8 @@ struct Dev {
     const double *gxx, *gxy, *gyx, *gyy;  // wgx dx, wgx dy, wgy dx, wgy dy (inner iterations)
     // iteration buffers
     StateSet set[2];
-    double *qx[2], *qy[2];   // double-buffered q-derivatives
+    double *gq[2];           // double-buffered q-derivatives, [ld][8]: point k's
+                             // (dq/dx 0..3, dq/dy 0..3) at 8k, one 64-byte record
     double *g1x, *g1y;       // first-order LS derivatives (the fixed part of Eq. 16)
     double *R;               // [4][ld]
     double *D;               // [ld]
@@ -168,8 +169,9 @@ cudaError_t launch_reset_ctrl(Ctrl *c, cudaStream_t s);
 // Prepare the control block for a run, on the device: flags cleared, drop
 // target set, it_start = it, stopped cases running again (failed ones stay).
 cudaError_t launch_prep_run(Ctrl *c, double target, cudaStream_t s);
-// Device-side reordering between the internal and the caller's point order.
-cudaError_t launch_to_caller(const double *src, const float *srcf, int comps, bool aos, int ld, int n,
+// Device-side reordering between the internal and the caller's point order
+// (source layout [c][ld] for stride 0, else point k's values at stride * k).
+cudaError_t launch_to_caller(const double *src, const float *srcf, int comps, int stride, int ld, int n,
                              const int32_t *inv, double *out, cudaStream_t s);
 cudaError_t launch_from_caller(const double *in, int ld, int n, const int32_t *inv, double *U, cudaStream_t s);
 

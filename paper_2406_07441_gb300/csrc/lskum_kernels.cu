@@ -315,10 +315,11 @@ __device__ __forceinline__ T group_sum(T v)
 //   sum_i (w_i dx_i) px_i + (w_i dy_i) py_i - px_0 sum_i w_i dx_i - py_0 sum_i w_i dy_i
 // with per-slot products w dx, w dy precomputed: 4 FMAs per component and
 // slot instead of 7 FP64 instructions.
+// The q-derivatives live in 64-byte records ([ld][8]), so a neighbour's
+// previous iterate is two 32-byte sectors instead of eight scattered ones.
 template <int TPP, bool CORR>
-__global__ void __launch_bounds__(256) k_grad(Dev d, const double *__restrict__ q, const double *__restrict__ px,
-                                              const double *__restrict__ py, double *__restrict__ qx,
-                                              double *__restrict__ qy)
+__global__ void __launch_bounds__(256) k_grad(Dev d, const double *__restrict__ q, const double *__restrict__ pg,
+                                              double *__restrict__ g)
 {
     if (halted(d.ctrl)) return;
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
@@ -348,11 +349,13 @@ __global__ void __launch_bounds__(256) k_grad(Dev d, const double *__restrict__ 
             }
         } else {
             const double axx = d.gxx[e], axy = d.gxy[e], ayx = d.gyx[e], ayy = d.gyy[e];
+            const double2 *r = reinterpret_cast<const double2 *>(pg + 8 * (size_t)i);
+            const double2 a01 = r[0], a23 = r[1], b01 = r[2], b23 = r[3];
+            const double a[4] = {a01.x, a01.y, a23.x, a23.y}, b[4] = {b01.x, b01.y, b23.x, b23.y};
 #pragma unroll
             for (int c = 0; c < 4; c++) {
-                const double a = px[c * ld + i], b = py[c * ld + i];
-                sx[c] = fma(axx, a, fma(axy, b, sx[c]));
-                sy[c] = fma(ayx, a, fma(ayy, b, sy[c]));
+                sx[c] = fma(axx, a[c], fma(axy, b[c], sx[c]));
+                sy[c] = fma(ayx, a[c], fma(ayy, b[c], sy[c]));
             }
         }
     }
@@ -365,19 +368,19 @@ __global__ void __launch_bounds__(256) k_grad(Dev d, const double *__restrict__ 
         if (!CORR) {
 #pragma unroll
             for (int c = 0; c < 4; c++) {
-                d.g1x[c * ld + k] = qx[c * ld + k] = sx[c];
-                d.g1y[c * ld + k] = qy[c * ld + k] = sy[c];
+                d.g1x[c * ld + k] = g[8 * (size_t)k + c] = sx[c];
+                d.g1y[c * ld + k] = g[8 * (size_t)k + 4 + c] = sy[c];
             }
         } else {
             const double cxx = d.geo[G_SXX * ld + k], cxy = d.geo[G_SXY * ld + k];
             const double cyx = d.geo[G_SYX * ld + k], cyy = d.geo[G_SYY * ld + k];
 #pragma unroll
             for (int c = 0; c < 4; c++) {
-                const double a0 = px[c * ld + k], b0 = py[c * ld + k];
+                const double a0 = pg[8 * (size_t)k + c], b0 = pg[8 * (size_t)k + 4 + c];
                 const double rx = sx[c] - fma(cxx, a0, cxy * b0);
                 const double ry = sy[c] - fma(cyx, a0, cyy * b0);
-                qx[c * ld + k] = fma(-0.5, rx, d.g1x[c * ld + k]);
-                qy[c * ld + k] = fma(-0.5, ry, d.g1y[c * ld + k]);
+                g[8 * (size_t)k + c] = fma(-0.5, rx, d.g1x[c * ld + k]);
+                g[8 * (size_t)k + 4 + c] = fma(-0.5, ry, d.g1y[c * ld + k]);
             }
         }
     }
@@ -395,8 +398,7 @@ __device__ __forceinline__ void comp_add(double &R, double &c, double x)
 }
 
 template <int TPP, bool COMP>
-__global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const double *__restrict__ gx,
-                                                  const double *__restrict__ gy)
+__global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const double *__restrict__ g)
 {
     __shared__ MathTables T;
     if (halted(d.ctrl)) return;
@@ -423,8 +425,8 @@ __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const doub
 #pragma unroll
         for (int c = 0; c < 4; c++) {
             q0[c] = q[c * ld + kk];
-            gx0[c] = gx[c * ld + kk];
-            gy0[c] = gy[c * ld + kk];
+            gx0[c] = g[8 * (size_t)kk + c];
+            gy0[c] = g[8 * (size_t)kk + 4 + c];
         }
         const int deg = d.deg[kk];
         const int base = d.slice_off[kk >> 5] + (kk & 31);
@@ -435,9 +437,12 @@ __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const doub
             const int i = d.nbr[e];
             const double dx = d.ndx[e], dy = d.ndy[e];
             double qi[4], q0t[4];
+            const double2 *gr = reinterpret_cast<const double2 *>(g + 8 * (size_t)i);
+            const double2 x01 = gr[0], x23 = gr[1], y01 = gr[2], y23 = gr[3];
+            const double gxi[4] = {x01.x, x01.y, x23.x, x23.y}, gyi[4] = {y01.x, y01.y, y23.x, y23.y};
 #pragma unroll
             for (int c = 0; c < 4; c++) {
-                qi[c] = q[c * ld + i] - hc * (dx * gx[c * ld + i] + dy * gy[c * ld + i]);
+                qi[c] = q[c * ld + i] - hc * (dx * gxi[c] + dy * gyi[c]);
                 q0t[c] = q0[c] - hc * (dx * gx0[c] + dy * gy0[c]);
             }
             const Prim Pi = q_to_prim(T, qi);
@@ -1059,11 +1064,11 @@ cudaError_t enqueue_grad(const Dev &d, int cur, cudaStream_t s, int *launches)
 {
     const int gb = (d.n * TPP + 255) / 256;
     const StateSet st = d.set[cur];
-    k_grad<TPP, false><<<gb, 256, 0, s>>>(d, st.q, nullptr, nullptr, d.qx[0], d.qy[0]);
+    k_grad<TPP, false><<<gb, 256, 0, s>>>(d, st.q, nullptr, d.gq[0]);
     (*launches)++;
     for (int it = 1; it <= d.K; it++) {
         const int a = (it - 1) & 1, b = it & 1;
-        k_grad<TPP, true><<<gb, 256, 0, s>>>(d, st.q, d.qx[a], d.qy[a], d.qx[b], d.qy[b]);
+        k_grad<TPP, true><<<gb, 256, 0, s>>>(d, st.q, d.gq[a], d.gq[b]);
         (*launches)++;
     }
     return cudaGetLastError();
@@ -1074,8 +1079,8 @@ cudaError_t enqueue_res(const Dev &d, const Launch &L, int cur, cudaStream_t s, 
 {
     const int fin = d.K & 1;
     const int rb = (d.n * TPP + L.res_block - 1) / L.res_block;
-    if (d.precision) k_residual<TPP, true><<<rb, L.res_block, 0, s>>>(d, d.set[cur], d.qx[fin], d.qy[fin]);
-    else k_residual<TPP, false><<<rb, L.res_block, 0, s>>>(d, d.set[cur], d.qx[fin], d.qy[fin]);
+    if (d.precision) k_residual<TPP, true><<<rb, L.res_block, 0, s>>>(d, d.set[cur], d.gq[fin]);
+    else k_residual<TPP, false><<<rb, L.res_block, 0, s>>>(d, d.set[cur], d.gq[fin]);
     (*launches)++;
     return cudaGetLastError();
 }
@@ -1233,16 +1238,16 @@ cudaError_t launch_init_state(const Dev &d, int cur, cudaStream_t s)
 
 namespace {
 
-// Internal order (structure of arrays [c][ld], or [ld][4] with aos; FP64 or
-// FP32) -> caller order [p][comps] on the device.
-__global__ void k_to_caller(const double *src, const float *srcf, int comps, bool aos, int ld, int n,
+// Internal order (structure of arrays [c][ld] for stride 0, else point k's
+// values at stride * k; FP64 or FP32) -> caller order [p][comps] on the device.
+__global__ void k_to_caller(const double *src, const float *srcf, int comps, int stride, int ld, int n,
                             const int32_t *inv, double *out)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const int k = inv[p];
     for (int c = 0; c < comps; c++) {
-        const size_t i = aos ? (size_t)4 * k + c : (size_t)c * ld + k;
+        const size_t i = stride ? (size_t)stride * k + c : (size_t)c * ld + k;
         out[(size_t)comps * p + c] = srcf ? (double)srcf[i] : src[i];
     }
 }
@@ -1259,11 +1264,11 @@ __global__ void k_from_caller(const double *in, int ld, int n, const int32_t *in
 
 }  // namespace
 
-cudaError_t launch_to_caller(const double *src, const float *srcf, int comps, bool aos, int ld, int n,
+cudaError_t launch_to_caller(const double *src, const float *srcf, int comps, int stride, int ld, int n,
                              const int32_t *inv, double *out, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    k_to_caller<<<(n + 255) / 256, 256, 0, s>>>(src, srcf, comps, aos, ld, n, inv, out);
+    k_to_caller<<<(n + 255) / 256, 256, 0, s>>>(src, srcf, comps, stride, ld, n, inv, out);
     return cudaGetLastError();
 }
 
