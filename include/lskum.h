@@ -72,8 +72,14 @@ enum {
  *   flag      u8[N]  LSKUM_INTERIOR / LSKUM_WALL / LSKUM_OUTER
  *   nx, ny    f64[N] unit normals: at wall points into the fluid; at outer
  *             points out of the domain (read there only under
- *             LSKUM_FARFIELD_KINETIC); read nowhere else; must not be NULL
- *             when some point needs them
+ *             LSKUM_FARFIELD_KINETIC); read nowhere else.  Both NULL: the
+ *             library computes them from the closed polygon of the wall
+ *             points (and of the outer points) in caller order -- the
+ *             central-difference tangent (next minus previous point)
+ *             rotated to its right for a counter-clockwise polygon (to its
+ *             left for a clockwise one): into the fluid at the wall, out of
+ *             the domain at the far field (LSKUM_ERR_ARG for fewer than 3
+ *             such points or a zero tangent)
  *   nbr_off   i32[N+1] CSR offsets, nbr_off[0] = 0, non-decreasing
  *   nbr_idx   i32[nbr_off[N]] neighbour indices: 0-based, < N, no self, no
  *             duplicates within a row.  The order within a row is the

@@ -265,9 +265,7 @@ static lskum_status validate_cloud(const lskum_cloud *cl, int32_t cs, bool kinet
         has_wall |= cl->flag[p] == LSKUM_WALL;
         has_outer |= cl->flag[p] == LSKUM_OUTER;
     }
-    if (has_wall && (!cl->nx || !cl->ny)) return fail(nullptr, LSKUM_ERR_ARG, "case %d: wall points need nx, ny", cs);
-    if (kinetic && has_outer && (!cl->nx || !cl->ny))
-        return fail(nullptr, LSKUM_ERR_ARG, "case %d: the kinetic far field needs nx, ny at outer points", cs);
+    if (!cl->nx != !cl->ny) return fail(nullptr, LSKUM_ERR_ARG, "case %d: nx and ny must both be given or both NULL", cs);
     for (int32_t p = 0; p < n; p++) {
         for (int32_t e = off[p]; e < off[p + 1]; e++) {
             const int32_t q = idx[e];
@@ -276,12 +274,44 @@ static lskum_status validate_cloud(const lskum_cloud *cl, int32_t cs, bool kinet
             for (int32_t f = off[p]; f < e; f++)
                 if (idx[f] == q) return fail(nullptr, LSKUM_ERR_ARG, "duplicate neighbour %d at point %d", q, p);
         }
-        if (cl->flag[p] == LSKUM_WALL || (kinetic && cl->flag[p] == LSKUM_OUTER)) {
+        if (cl->nx && (cl->flag[p] == LSKUM_WALL || (kinetic && cl->flag[p] == LSKUM_OUTER))) {
             const double ln = std::hypot(cl->nx[p], cl->ny[p]);
             if (!(std::fabs(ln - 1.0) < 1e-6))
                 return fail(nullptr, LSKUM_ERR_ARG, "%s normal not unit at point %d",
                             cl->flag[p] == LSKUM_WALL ? "wall" : "outer", p);
         }
+    }
+    return LSKUM_OK;
+}
+
+// Unit normals of the closed polygon of a case's points of type `type`, in
+// caller order: the central-difference tangent (next - previous) rotated to
+// its right, turned so that it points away from the region the polygon
+// encloses when that region is the body (wall) and out of the domain for the
+// outer boundary -- both the right-hand normal of a counter-clockwise polygon.
+// Errors: fewer than 3 such points, or a zero tangent.
+static lskum_status polygon_normals(const lskum_cloud *cl, int32_t cs, uint8_t type, double *nx, double *ny)
+{
+    std::vector<int32_t> v;
+    for (int32_t p = 0; p < cl->n_points; p++)
+        if (cl->flag[p] == type) v.push_back(p);
+    if (v.empty()) return LSKUM_OK;
+    const size_t m = v.size();
+    if (m < 3) return fail(nullptr, LSKUM_ERR_ARG, "case %d: fewer than 3 %s points to form a polygon", cs,
+                           type == LSKUM_WALL ? "wall" : "outer");
+    double area2 = 0.0;
+    for (size_t k = 0; k < m; k++) {
+        const int32_t a = v[k], b = v[(k + 1) % m];
+        area2 += cl->x[a] * cl->y[b] - cl->x[b] * cl->y[a];
+    }
+    const double orient = area2 > 0.0 ? 1.0 : -1.0;
+    for (size_t k = 0; k < m; k++) {
+        const int32_t a = v[(k + m - 1) % m], p = v[k], b = v[(k + 1) % m];
+        const double tx = cl->x[b] - cl->x[a], ty = cl->y[b] - cl->y[a];
+        const double ln = std::hypot(tx, ty);
+        if (!(ln > 0.0)) return fail(nullptr, LSKUM_ERR_ARG, "case %d: zero polygon tangent at point %d", cs, p);
+        nx[p] = orient * ty / ln;
+        ny[p] = -orient * tx / ln;
     }
     return LSKUM_OK;
 }
@@ -407,16 +437,30 @@ static lskum_status create_impl(const lskum_cloud *clouds, const lskum_opts *opt
     if (!c) return fail(nullptr, LSKUM_ERR_OOM, "host allocation failed");
     c->n_cases = n_cases;
     c->case_off.assign(1, 0);
+    const bool kinetic = opts[0].farfield == LSKUM_FARFIELD_KINETIC;
     for (int32_t b = 0; b < n_cases; b++) {
         const lskum_cloud &cl = clouds[b];
         const int32_t base = (int32_t)ux.size();
+        // normals not given: from the wall polygon (and the outer polygon)
+        std::vector<double> cnx, cny;
+        if (!cl.nx) {
+            cnx.assign(cl.n_points, 0.0);
+            cny.assign(cl.n_points, 0.0);
+            lskum_status ps = polygon_normals(&cl, b, LSKUM_WALL, cnx.data(), cny.data());
+            if (ps == LSKUM_OK && kinetic) ps = polygon_normals(&cl, b, LSKUM_OUTER, cnx.data(), cny.data());
+            if (ps != LSKUM_OK) {
+                delete c;
+                return ps;
+            }
+        }
+        const double *cnxp = cl.nx ? cl.nx : cnx.data(), *cnyp = cl.ny ? cl.ny : cny.data();
         for (int32_t p = 0; p < cl.n_points; p++) {
             ux.push_back(cl.x[p]);
             uy.push_back(cl.y[p]);
             ufl.push_back(cl.flag[p]);
-            if (cl.flag[p] == LSKUM_WALL || (opts[0].farfield == LSKUM_FARFIELD_KINETIC && cl.flag[p] == LSKUM_OUTER)) {
-                unx[base + p] = cl.nx[p];
-                uny[base + p] = cl.ny[p];
+            if (cl.flag[p] == LSKUM_WALL || (kinetic && cl.flag[p] == LSKUM_OUTER)) {
+                unx[base + p] = cnxp[p];
+                uny[base + p] = cnyp[p];
             }
             for (int32_t e = cl.nbr_off[p]; e < cl.nbr_off[p + 1]; e++) uidx.push_back(base + cl.nbr_idx[e]);
             uoff.push_back((int32_t)uidx.size());

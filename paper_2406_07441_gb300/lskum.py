@@ -124,12 +124,15 @@ def _p(a):
 
 
 def _cloud_struct(cloud, keep):
+    """The C view of a cloud; nx / ny may be None (the library then computes
+    the normals from the wall and outer polygons)."""
     arrs = [np.ascontiguousarray(cloud.x, np.float64), np.ascontiguousarray(cloud.y, np.float64),
-            np.ascontiguousarray(cloud.flag, np.uint8), np.ascontiguousarray(cloud.nx, np.float64),
-            np.ascontiguousarray(cloud.ny, np.float64), np.ascontiguousarray(cloud.nbr_off, np.int32),
-            np.ascontiguousarray(cloud.nbr_idx, np.int32)]
-    keep.extend(arrs)
-    return lskum_cloud(int(cloud.n), *[a.ctypes.data for a in arrs])
+            np.ascontiguousarray(cloud.flag, np.uint8),
+            None if cloud.nx is None else np.ascontiguousarray(cloud.nx, np.float64),
+            None if cloud.ny is None else np.ascontiguousarray(cloud.ny, np.float64),
+            np.ascontiguousarray(cloud.nbr_off, np.int32), np.ascontiguousarray(cloud.nbr_idx, np.int32)]
+    keep.extend(a for a in arrs if a is not None)
+    return lskum_cloud(int(len(cloud.x)), *[None if a is None else a.ctypes.data for a in arrs])
 
 
 def validate(clouds, conditions, **kw):

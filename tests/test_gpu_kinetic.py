@@ -164,3 +164,23 @@ def test_kinetic_supersonic_naca0012_160x64():
     clo, cdo = o.forces(r["U"], 1.2, 0.0)
     print("M 1.2 kinetic far field, 300 iterations: history max rel", rel.max(), "Cl", cl, clo, "Cd", cd, cdo)
     assert abs(cd - cdo) < 1e-8 and abs(cl) < 1e-4
+
+
+def test_normals_computed_by_the_library():
+    """With nx = ny = NULL the library computes the wall normals as the
+    generator does (central-difference tangent of the wall polygon, rotated
+    into the fluid): the same solve bit for bit; the outer ring's polygon
+    normals equal the generator's radial ones to rounding, so the kinetic
+    far-field solve agrees to rounding."""
+    lk = _lk()
+    c = cached_cloud("ogrid40x16k", CLOUDS["ogrid40x16k"])
+    bare = cg.Cloud(c.x, c.y, c.flag, None, None, c.nbr_off, c.nbr_idx, {})
+    a = lk.Solver(c, 0.63, 2.0, inner_iters=2, first_order_iters=3)
+    b = lk.Solver(bare, 0.63, 2.0, inner_iters=2, first_order_iters=3)
+    assert a.run(10) == 10 and b.run(10) == 10
+    assert np.array_equal(a.field(lk.FIELD_U), b.field(lk.FIELD_U))
+    kw = dict(inner_iters=2, first_order_iters=3, farfield=lk.FARFIELD_KINETIC)
+    a = lk.Solver(c, 1.2, 0.0, **kw)
+    b = lk.Solver(bare, 1.2, 0.0, **kw)
+    assert a.run(10) == 10 and b.run(10) == 10
+    assert nrel(b.field(lk.FIELD_U), a.field(lk.FIELD_U)) < 1e-12

@@ -170,3 +170,24 @@ def test_kinetic_far_field_checks_outer_normals_and_stencils(lk):
     with pytest.raises(lk.LskumError) as ei:
         lk.validate([bad], [(1.2, 0.0)], farfield=lk.FARFIELD_KINETIC)
     assert ei.value.status == -2
+
+
+def test_normals_may_be_computed_from_the_polygons(lk):
+    """nx = ny = NULL: the library takes the normals from the closed wall
+    (and outer) polygons in caller order; the layout is the same as with
+    the generator's normals, and a polygon of fewer than 3 points or a
+    mismatched pair of normal arrays is rejected."""
+    c = cg.naca0012_block(40, 16, kinetic_outer=True)
+    bare = cg.Cloud(c.x, c.y, c.flag, None, None, c.nbr_off, c.nbr_idx, {})
+    for kw in (dict(), dict(farfield=lk.FARFIELD_KINETIC), dict(ordering=1)):
+        assert lk.validate([bare], [(0.8, 1.0)], **kw) == lk.validate([c], [(0.8, 1.0)], **kw)
+    half = cg.Cloud(c.x, c.y, c.flag, c.nx, None, c.nbr_off, c.nbr_idx, {})
+    with pytest.raises(lk.LskumError) as ei:
+        lk.validate([half], [(0.8, 1.0)])
+    assert ei.value.status == -1
+    b = cg.cartesian_box(7, 7, seed=2, wall_bottom=True)
+    two = b.flag.copy()
+    two[np.flatnonzero(two == cg.WALL)[2:]] = cg.INTERIOR  # only two wall points left
+    with pytest.raises(lk.LskumError) as ei:
+        lk.validate([cg.Cloud(b.x, b.y, two, None, None, b.nbr_off, b.nbr_idx, {})], [(0.5, 0.0)])
+    assert ei.value.status == -1 and "polygon" in str(ei.value)
