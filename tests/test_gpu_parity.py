@@ -425,3 +425,25 @@ def test_packed_sweeps_kinetic_and_batch():
         assert s.run(6) == 6
         info = bt.case_info(cs)
         assert np.array_equal(U[info["first_point"]:info["first_point"] + c.n], s.field(lk.FIELD_U))
+
+
+def test_packed_sweeps_wall_first_and_manish():
+    """The packed form under the wall-first order (levels split by point
+    type) and with the revised LU-SGS (its lagged term in the first lane of
+    each point): increments against the oracle."""
+    lk = _lskum()
+    c = cached_cloud("ogrid40x16", CLOUDS["ogrid40x16"])
+    o1 = O.Oracle(c, ordering=1)
+    r = o1.run(o1.initial_state(0.63, 2.0), 4, cfl=100.0, K=2, first_order=2)
+    s = lk.Solver(c, 0.63, 2.0, inner_iters=2, first_order_iters=2, ordering=lk.ORDER_WALL_FIRST)
+    s.set_launch_shape(2, 32)
+    assert s.run(4) == 4
+    assert nrel(s.field(lk.FIELD_DUS), r["dUs"]) < 1e-10 and nrel(s.field(lk.FIELD_DU), r["dU"]) < 1e-10
+    o = O.Oracle(c)
+    r = o.run_manish(o.initial_state(0.63, 2.0), 5, cfl=3.0, K=2, first_order=2, sigma=-1)
+    s = lk.Solver(c, 0.63, 2.0, cfl=3.0, inner_iters=2, first_order_iters=2, lusgs=lk.LUSGS_MANISH)
+    s.set_launch_shape(2, 32)
+    assert s.run(5) == 5
+    assert nrel(s.field(lk.FIELD_DUS), r["dUs"]) < 1e-10 and nrel(s.field(lk.FIELD_DU), r["dU"]) < 1e-10
+    h = s.residuals()
+    assert np.max(np.abs(h - r["hist"]) / r["hist"]) < 1e-10
