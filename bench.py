@@ -56,6 +56,10 @@ START = 50  # first-order start-up iterations before warm-up and timing
 # current kernel (profiles/k_residual_naca0012_640x256_jit.md); reported only
 # when the bench runs that launch shape.
 RES_TRAFFIC = {2: 164.335104e6}
+# sm__pipe_fp64_cycles_active of that launch (fraction of peak sustained): the
+# residual's binding unit; the counted-flop fraction is lower because
+# additions, multiplications and comparisons occupy the pipe like an FMA
+RES_FP64_PIPE_ACTIVE = 0.894
 
 
 def _env_int(k, d):
@@ -286,6 +290,7 @@ def run_ours(args, rank, world, local_rank):
                      "algorithmic_bytes_rule": "37 B per neighbour slot (index, membership, dx, dy, 2 weights) "
                                                "+ 360 B per point (q, grad q, frame, geometry, state, R, D)",
                      "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz",
+                     "fp64_pipe_active_ncu": RES_FP64_PIPE_ACTIVE if args.precision == 0 and wl == WORKLOAD else None,
                      "launch_ms": res_ms, "phase_ms": phases},
         "cpu_baseline": cpu,
         "e2e": e2e,
