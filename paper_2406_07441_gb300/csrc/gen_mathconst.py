@@ -5,9 +5,10 @@ Run from the repository root:  python paper_2406_07441_gb300/csrc/gen_mathconst.
 
 exp (table-driven, after P. T. P. Tang, "Table-driven implementation of the
 exponential function in IEEE floating-point arithmetic", ACM TOMS 15(2), 1989):
-  x = (64 m + j) ln2/64 + r, |r| <= ln2/128,  exp(x) = 2^m * 2^(j/64) * e^r,
-  2^(j/64) tabulated (correctly rounded), e^r - 1 by its Taylor polynomial of
-  degree 5 (truncation < 4e-17 relative on |r| <= ln2/128).
+  x = (N m + j) ln2/N + r, |r| <= ln2/(2N), N = 512,
+  exp(x) = 2^m * 2^(j/N) * e^r, 2^(j/N) tabulated (correctly rounded),
+  e^r - 1 by its Taylor polynomial of degree 4 (truncation < 2e-18 relative
+  on |r| <= ln2/1024; the larger table buys one FP64 instruction per exp).
 
 erfcx(x) = exp(x^2) erfc(x) for 0 <= x <= 9: on each of ten intervals [a, b]
 the Chebyshev interpolant of degree 13 at Chebyshev points of the first kind,
@@ -34,6 +35,7 @@ OUT = os.path.join(HERE, "lskum_mathconst.h")
 BOUNDS = [0.0, 0.5, 1.0, 1.5, 2.25, 3.0, 4.0, 5.0, 6.0, 7.5, 9.0]
 INTERVALS = list(zip(BOUNDS[:-1], BOUNDS[1:]))
 DEGREE = 13
+EXP_N = 512
 
 
 def erfcx(x):
@@ -76,22 +78,24 @@ def main():
         "",
         "namespace lskum {",
         "",
-        f"constexpr double kExpInvLn2_64 = {hexd(64 / mp.log(2))};  // 64 / ln 2",
+        f"constexpr int kExpN = {EXP_N};  // table size N (a power of two)",
+        f"constexpr int kExpShift = {EXP_N.bit_length() - 1};  // log2 N",
+        f"constexpr double kExpInvLn2N = {hexd(EXP_N / mp.log(2))};  // N / ln 2",
     ]
-    ln2_64 = mp.log(2) / 64
-    # high part: ln2/64 with the low 24 significand bits cleared, so that k * hi
-    # is exact for the |k| < 2^17 that finite results need
-    bits = int.from_bytes(struct.pack(">d", float(ln2_64)), "big") & ~((1 << 24) - 1)
+    ln2_n = mp.log(2) / EXP_N
+    # high part: ln2/N with the low 24 significand bits cleared, so that k * hi
+    # is exact for the |k| < 2^20 that finite results need
+    bits = int.from_bytes(struct.pack(">d", float(ln2_n)), "big") & ~((1 << 24) - 1)
     fhi = struct.unpack(">d", bits.to_bytes(8, "big"))[0]
-    flo = float(ln2_64 - mp.mpf(fhi))
+    flo = float(ln2_n - mp.mpf(fhi))
     lines += [
-        f"constexpr double kExpLn2_64Hi = {fhi.hex()};  // ln2/64, 29 significant bits",
-        f"constexpr double kExpLn2_64Lo = {flo.hex()};  // ln2/64 - kExpLn2_64Hi",
-        "// 2^(j/64), j = 0..63, correctly rounded",
-        "__constant__ double kExpTable[64] = {",
+        f"constexpr double kExpLn2NHi = {fhi.hex()};  // ln2/N, 29 significant bits",
+        f"constexpr double kExpLn2NLo = {flo.hex()};  // ln2/N - kExpLn2NHi",
+        f"// 2^(j/N), j = 0..N-1, correctly rounded",
+        f"__constant__ double kExpTable[{EXP_N}] = {{",
     ]
-    for j in range(0, 64, 4):
-        lines.append("    " + ", ".join(hexd(mp.power(2, mp.mpf(k) / 64)) for k in range(j, j + 4)) + ",")
+    for j in range(0, EXP_N, 4):
+        lines.append("    " + ", ".join(hexd(mp.power(2, mp.mpf(k) / EXP_N)) for k in range(j, j + 4)) + ",")
     lines.append("};")
     nI = len(INTERVALS)
     lines.append(f"constexpr int kErfcxDeg = {DEGREE};")

@@ -11,7 +11,7 @@
 namespace lskum {
 
 struct MathTables {
-    double exp2j[64];                           // 2^(j/64)
+    double exp2j[kExpN];                        // 2^(j/N)
     double ecx[kErfcxIntervals][kErfcxDeg + 1]; // erfcx/2 per interval, Horner coefficients
     double sc[kErfcxIntervals], off[kErfcxIntervals];  // t = x * sc + off
 };
@@ -19,7 +19,7 @@ struct MathTables {
 // Copy the tables into shared memory (all threads of the block; then sync).
 __device__ __forceinline__ void load_math_tables(MathTables &T)
 {
-    for (int i = threadIdx.x; i < 64; i += blockDim.x) T.exp2j[i] = kExpTable[i];
+    for (int i = threadIdx.x; i < kExpN; i += blockDim.x) T.exp2j[i] = kExpTable[i];
     for (int i = threadIdx.x; i < kErfcxIntervals * (kErfcxDeg + 1); i += blockDim.x)
         T.ecx[i / (kErfcxDeg + 1)][i % (kErfcxDeg + 1)] = kErfcxHalf[i / (kErfcxDeg + 1)][i % (kErfcxDeg + 1)];
     if (threadIdx.x < kErfcxIntervals) {
@@ -28,22 +28,22 @@ __device__ __forceinline__ void load_math_tables(MathTables &T)
     }
 }
 
-// exp(x) for |x| <= 700 (Tang's table-driven method): 10 FP64 instructions.
+// exp(x) for |x| <= 700 (Tang's table-driven method, N = 512 table entries):
+// 9 FP64 instructions.
 __device__ __forceinline__ double exp_t(const MathTables &T, double x)
 {
-    const double big = 0x1.8p52;                            // rounds x*64/ln2 into the low word
-    const double t = fma(x, kExpInvLn2_64, big);
-    const int k = __double2loint(t);                        // round(x * 64 / ln2)
+    const double big = 0x1.8p52;                            // rounds x*N/ln2 into the low word
+    const double t = fma(x, kExpInvLn2N, big);
+    const int k = __double2loint(t);                        // round(x * N / ln2)
     const double kd = t - big;
-    double r = fma(kd, -kExpLn2_64Hi, x);
-    r = fma(kd, -kExpLn2_64Lo, r);                          // |r| <= ln2/128
-    double h = fma(r, 1.0 / 120.0, 1.0 / 24.0);
-    h = fma(r, h, 1.0 / 6.0);
+    double r = fma(kd, -kExpLn2NHi, x);
+    r = fma(kd, -kExpLn2NLo, r);                            // |r| <= ln2/(2N)
+    double h = fma(r, 1.0 / 24.0, 1.0 / 6.0);
     h = fma(r, h, 0.5);
     const double p = fma(r * r, h, r);                      // e^r - 1
-    const double e = T.exp2j[k & 63];
-    const double res = fma(e, p, e);                        // 2^(j/64) e^r
-    return __hiloint2double(__double2hiint(res) + ((k >> 6) << 20), __double2loint(res));
+    const double e = T.exp2j[k & (kExpN - 1)];
+    const double res = fma(e, p, e);                        // 2^(j/N) e^r
+    return __hiloint2double(__double2hiint(res) + ((k >> kExpShift) << 20), __double2loint(res));
 }
 
 // E = exp(-S^2) erfcx(|S|)/2 and eS = exp(-S^2); then (1 + erf S)/2 is 1 - E

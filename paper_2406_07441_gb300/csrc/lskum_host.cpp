@@ -1108,6 +1108,10 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
     up(d.D, ones.data(), ld * sizeof(double));
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemset");
 
+    // the function tables the sweeps read from global memory
+    e = launch_init_math(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "initialising the function tables");
+
     // ---- free-stream start ----
     std::vector<double> rho(n, 1.0), uu(n), vv(n), pp(n, 1.0 / 1.4);
     for (int32_t b = 0; b < c->n_cases; b++) {

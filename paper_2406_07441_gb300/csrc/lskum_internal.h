@@ -165,6 +165,8 @@ cudaError_t launch_iteration(const Dev &d, const Launch &L, int cur, int n_level
 cudaError_t launch_phase(const Dev &d, const Launch &L, int cur, int phase, int n_levels, const int32_t *lvl_beg,
                          const int32_t *lvl_act_end, const int32_t *lvl_end, cudaStream_t s);
 cudaError_t launch_init_state(const Dev &d, int cur, cudaStream_t s);
+// Fill the global copy of the function tables the sweeps read (idempotent).
+cudaError_t launch_init_math(cudaStream_t s);
 cudaError_t launch_reset_ctrl(Ctrl *c, cudaStream_t s);
 // Prepare the control block for a run, on the device: flags cleared, drop
 // target set, it_start = it, stopped cases running again (failed ones stay).

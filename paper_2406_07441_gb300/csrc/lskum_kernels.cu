@@ -58,6 +58,16 @@ __device__ __forceinline__ bool frozen(const Dev &d, int k)
     return d.n_cases > 1 && frozen_state(((const volatile int32_t *)d.case_state)[d.case_of[k]]);
 }
 
+// One copy of the function tables in global memory, for kernels that need
+// them only at a few points (the sweeps: wall and outer points); kernels that
+// evaluate them at every point stage them in shared memory instead.
+__device__ MathTables g_math;
+
+__global__ void k_init_math()
+{
+    load_math_tables(g_math);
+}
+
 // x with its sign flipped unless pos: an integer XOR of the sign bit, so a
 // selected sign costs no FP64 (or FP32) instruction.
 __device__ __forceinline__ double signed_by(double x, bool pos)
@@ -73,6 +83,7 @@ __device__ __forceinline__ float signed_by(float x, bool pos)
 struct Prim {
     double rho, u, v, p, sb, isb, e1, e2;  // sb = sqrt(beta), isb = 1/sb,
                                            // e1 = 3.5 p + rho|u|^2/2, e2 = 3 p + rho|u|^2/2
+    double bk;                             // 1 / (2 sqrt(pi beta)): B = exp(-S^2) bk
 };
 
 // Inverse of Eq. 14: beta = -q4/2, u = q2/(2 beta), v = q3/(2 beta),
@@ -95,6 +106,7 @@ __device__ __forceinline__ Prim q_to_prim(const MathTables &T, const double q[4]
     const double k = 0.5 * P.rho * q2;
     P.e1 = fma(3.5, P.p, k);
     P.e2 = fma(3.0, P.p, k);
+    P.bk = kInv2SqrtPi * P.isb;
     return P;
 }
 
@@ -109,7 +121,7 @@ __device__ __forceinline__ void split_flux(const MathTables &T, const Prim &P, d
     const double S = ud * P.sb;
     double A, eS;
     split_A(T, S, pos, A, eS);
-    const double B = eS * kInv2SqrtPi * P.isb;
+    const double B = eS * P.bk;
     const double sB = signed_by(B, pos);
     const double M1 = fma(ud, A, sB);
     const double rm = P.rho * M1;
@@ -440,10 +452,11 @@ __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const doub
             const double2 *gr = reinterpret_cast<const double2 *>(g + 8 * (size_t)i);
             const double2 x01 = gr[0], x23 = gr[1], y01 = gr[2], y23 = gr[3];
             const double gxi[4] = {x01.x, x01.y, x23.x, x23.y}, gyi[4] = {y01.x, y01.y, y23.x, y23.y};
+            const double hdx = hc * dx, hdy = hc * dy;  // exact: hc is 0 or 1/2
 #pragma unroll
             for (int c = 0; c < 4; c++) {
-                qi[c] = q[c * ld + i] - hc * (dx * gxi[c] + dy * gyi[c]);
-                q0t[c] = q0[c] - hc * (dx * gx0[c] + dy * gy0[c]);
+                qi[c] = fma(-hdx, gxi[c], fma(-hdy, gyi[c], q[c * ld + i]));
+                q0t[c] = fma(-hdx, gx0[c], fma(-hdy, gy0[c], q0[c]));
             }
             const Prim Pi = q_to_prim(T, qi);
             const Prim P0 = q_to_prim(T, q0t);
@@ -812,10 +825,8 @@ __device__ __forceinline__ void point_frame(const Dev &d, int k, bool framed, do
 template <int JVP, bool FWD, int G, typename T>
 __global__ void __launch_bounds__(256) k_sweep(Dev d, StateSet st, int lb, int le)
 {
-    __shared__ MathTables Tb;
+    const MathTables &Tb = g_math;  // wall and outer points only: no per-block copy
     if (halted(d.ctrl)) return;
-    load_math_tables(Tb);
-    __syncthreads();
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     if (lb + (gt & ~31) / G >= le) return;  // the whole warp is past the level
     const int pos = lb + gt / G, sub = gt % G;
@@ -851,10 +862,8 @@ __global__ void __launch_bounds__(256) k_sweep(Dev d, StateSet st, int lb, int l
 template <int JVP, bool FWD, typename T>
 __global__ void __launch_bounds__(256) k_sweep_packed(Dev d, StateSet st, int wb, int we)
 {
-    __shared__ MathTables Tb;
+    const MathTables &Tb = g_math;  // wall and outer points only: no per-block copy
     if (halted(d.ctrl)) return;
-    load_math_tables(Tb);
-    __syncthreads();
     const int gw = wb + (blockIdx.x * blockDim.x + threadIdx.x) / 32;
     if (gw >= we) return;  // whole warps only (blocks are whole warps)
     const int lane = threadIdx.x & 31;
@@ -1276,6 +1285,12 @@ cudaError_t launch_from_caller(const double *in, int ld, int n, const int32_t *i
 {
     if (n <= 0) return cudaSuccess;
     k_from_caller<<<(n + 255) / 256, 256, 0, s>>>(in, ld, n, inv, U);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_math(cudaStream_t s)
+{
+    k_init_math<<<1, 256, 0, s>>>();
     return cudaGetLastError();
 }
 

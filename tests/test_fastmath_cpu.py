@@ -30,7 +30,9 @@ def _consts():
     bounds = [int(t, 16) for t in re.findall(r"ha >= (0x[0-9a-f]{8})",
                                               re.search(r"int erfcx_interval\(int ha\).*?\}", s, re.S).group(0))]
     assert len(bounds) == nI - 1
-    return dict(inv=scalar("kExpInvLn2_64"), hi=scalar("kExpLn2_64Hi"), lo=scalar("kExpLn2_64Lo"),
+    n = int(re.search(r"kExpN = (\d+);", s).group(1))
+    shift = int(re.search(r"kExpShift = (\d+);", s).group(1))
+    return dict(inv=scalar("kExpInvLn2N"), hi=scalar("kExpLn2NHi"), lo=scalar("kExpLn2NLo"), n=n, shift=shift,
                 tab=array("kExpTable"), sc=array("kErfcxScale"), off=array("kErfcxOffset"), ecx=ecx, deg=deg,
                 bounds=bounds)
 
@@ -66,13 +68,12 @@ def exp_t(x):
     kd = t - big
     r = fma(kd, -C["hi"], x)
     r = fma(kd, -C["lo"], r)
-    h = fma(r, 1.0 / 120.0, 1.0 / 24.0)
-    h = fma(r, h, 1.0 / 6.0)
+    h = fma(r, 1.0 / 24.0, 1.0 / 6.0)
     h = fma(r, h, 0.5)
     p = fma(mul(r, r), h, r)
-    e = C["tab"][k & 63]
+    e = C["tab"][k & (C["n"] - 1)]
     res = fma(e, p, e)
-    return from_words(hi_word(res) + ((k >> 6) << 20), lo_word(res))
+    return from_words(hi_word(res) + ((k >> C["shift"]) << 20), lo_word(res))
 
 
 def split_E(S):
