@@ -10,12 +10,17 @@ exponential function in IEEE floating-point arithmetic", ACM TOMS 15(2), 1989):
   e^r - 1 by its Taylor polynomial of degree 4 (truncation < 2e-18 relative
   on |r| <= ln2/1024; the larger table buys one FP64 instruction per exp).
 
-erfcx(x) = exp(x^2) erfc(x) for 0 <= x <= 9: on each of ten intervals [a, b]
-the Chebyshev interpolant of degree 13 at Chebyshev points of the first kind,
-rewritten as a polynomial in t = (x - c)/h (c, h the interval's centre and
-half width) and evaluated by Horner's rule; the interpolants are within
-4e-17 relative of erfcx in exact arithmetic (checked at 200 points per
-interval with mpmath), so the evaluation's rounding dominates.  The kernels use it as
+erfcx(x) = exp(x^2) erfc(x) for 0 <= x <= 9: the intervals are [0, 2^-5)
+and, above it, sixteen per binade, [2^e (1 + m/16), 2^e (1 + (m+1)/16)) for
+e = -5 .. 3 (132 in all, the last one [9, 9.5) holding only the clamp value
+9): the interval of x is the high word of x shifted right by 16 (its
+exponent and top four significand bits) minus that of 2^-5, plus one,
+floored at 0 -- two integer instructions.  On each interval the Chebyshev
+interpolant of degree 9 at Chebyshev points of the first kind, rewritten as
+a polynomial in t = (x - c)/h (c, h the interval's centre and half width)
+and evaluated by Horner's rule; the interpolants are within 4e-17 relative
+of erfcx in exact arithmetic (checked at 200 points per interval with
+mpmath), so the evaluation's rounding dominates.  The kernels use it as
   A = (1 + s erf S)/2 = 1 - E (s S >= 0)  or  E (s S < 0),
   E = exp(-S^2) erfcx(|S|) / 2,
 which shares exp(-S^2) with the B term of the split flux and is accurate in
@@ -30,11 +35,26 @@ mp.mp.dps = 60
 HERE = os.path.dirname(os.path.abspath(__file__))
 OUT = os.path.join(HERE, "lskum_mathconst.h")
 
-# Interval bounds are doubles whose low 32 bits are zero, so that the kernels
-# pick the interval by integer comparisons of the high word.
-BOUNDS = [0.0, 0.5, 1.0, 1.5, 2.25, 3.0, 4.0, 5.0, 6.0, 7.5, 9.0]
-INTERVALS = list(zip(BOUNDS[:-1], BOUNDS[1:]))
-DEGREE = 13
+# Interval bounds: 0, then 2^e (1 + m/16) for e = -5 .. 3, m = 0 .. 15, up to
+# the interval that holds 9 (the kernels' clamp of |S|).
+LOW_EXP, MBITS = -5, 4
+
+
+def _intervals():
+    out = [(0.0, 2.0 ** LOW_EXP)]
+    e = LOW_EXP
+    while True:
+        for m in range(2 ** MBITS):
+            a = 2.0 ** e * (1 + m / 2 ** MBITS)
+            b = 2.0 ** e * (1 + (m + 1) / 2 ** MBITS)
+            out.append((a, b))
+            if b > 9.0:
+                return out
+        e += 1
+
+
+INTERVALS = _intervals()
+DEGREE = 9
 EXP_N = 512
 
 
@@ -92,32 +112,47 @@ def main():
         f"constexpr double kExpLn2NHi = {fhi.hex()};  // ln2/N, 29 significant bits",
         f"constexpr double kExpLn2NLo = {flo.hex()};  // ln2/N - kExpLn2NHi",
         f"// 2^(j/N), j = 0..N-1, correctly rounded",
-        f"__constant__ double kExpTable[{EXP_N}] = {{",
+        f"__device__ double kExpTable[{EXP_N}] = {{",
     ]
     for j in range(0, EXP_N, 4):
         lines.append("    " + ", ".join(hexd(mp.power(2, mp.mpf(k) / EXP_N)) for k in range(j, j + 4)) + ",")
     lines.append("};")
     nI = len(INTERVALS)
+    key0 = (int.from_bytes(struct.pack(">d", 2.0 ** LOW_EXP), "big") >> 32) >> (20 - MBITS)
+    # the index function reproduces the table's intervals
+    for k, (a, b) in enumerate(INTERVALS):
+        for x in (a, (a + b) / 2, b * (1 - 2 ** -52)):
+            ha = int.from_bytes(struct.pack(">d", x), "big") >> 32
+            assert max(0, (ha >> (20 - MBITS)) - key0 + 1) == k or x == 0.0 and k == 0, (k, x)
     lines.append(f"constexpr int kErfcxDeg = {DEGREE};")
     lines.append(f"constexpr int kErfcxIntervals = {nI};")
-    hi = [int.from_bytes(struct.pack(">d", b), "big") >> 32 for _, b in INTERVALS[:-1]]
-    assert all((int.from_bytes(struct.pack(">d", b), "big") & 0xFFFFFFFF) == 0 for _, b in INTERVALS)
-    lines.append("// high words of the interior interval bounds " + ", ".join(repr(b) for _, b in INTERVALS[:-1]) +
-                 "; then scale 1/h and offset -c/h of t = (x - c)/h per interval")
+    lines.append(f"constexpr int kErfcxShift = {20 - MBITS};  // high word >> shift: exponent and top {MBITS} bits")
+    lines.append(f"constexpr int kErfcxKey0 = 0x{key0:x};  // that key of 2^{LOW_EXP}")
+    lines.append("// interval of x in [0, 9.5): [0, 2^" + str(LOW_EXP) + f") is 0, then {2 ** MBITS} per binade")
     lines.append("__device__ __forceinline__ int erfcx_interval(int ha)  // ha: high word of x >= 0")
     lines.append("{")
-    lines.append("    return " + " + ".join(f"(ha >= 0x{h:08x})" for h in hi) + ";")
+    lines.append("    return max(0, (ha >> kErfcxShift) - kErfcxKey0 + 1);")
     lines.append("}")
+    lines.append("// then scale 1/h and offset -c/h of t = (x - c)/h per interval")
     coef_rows, sc, off = [], [], []
     for a, b in INTERVALS:
         mono, c, h = cheb_monomial(erfcx, a, b, DEGREE)
+        # the interpolant in exact arithmetic, at 200 points of the interval
+        for k in range(200):
+            x = mp.mpf(a) + (mp.mpf(b) - a) * k / 199
+            t = (x - c) / h
+            p = mp.mpf(0)
+            for m in reversed(mono):
+                p = p * t + m
+            assert abs(p / erfcx(x) - 1) < 4e-17, (a, b, x)
         coef_rows.append([hexd(m / 2) for m in mono])  # E = exp(-S^2) * (erfcx/2)
         sc.append(hexd(1 / h))
         off.append(hexd(-c / h))
-    lines.append(f"__constant__ double kErfcxScale[{nI}] = {{" + ", ".join(sc) + "};")
-    lines.append(f"__constant__ double kErfcxOffset[{nI}] = {{" + ", ".join(off) + "};")
+    # global (not constant) memory: blocks copy the tables with coalesced loads
+    lines.append(f"__device__ double kErfcxScale[{nI}] = {{" + ", ".join(sc) + "};")
+    lines.append(f"__device__ double kErfcxOffset[{nI}] = {{" + ", ".join(off) + "};")
     lines.append(f"// erfcx/2 on each interval as a polynomial in t, coefficients of t^0 .. t^{DEGREE}")
-    lines.append(f"__constant__ double kErfcxHalf[{nI}][{DEGREE + 1}] = {{")
+    lines.append(f"__device__ double kErfcxHalf[{nI}][{DEGREE + 1}] = {{")
     for row in coef_rows:
         lines.append("    {" + ", ".join(row) + "},")
     lines.append("};")

@@ -48,12 +48,16 @@ __device__ __forceinline__ double exp_t(const MathTables &T, double x)
 
 // E = exp(-S^2) erfcx(|S|)/2 and eS = exp(-S^2); then (1 + erf S)/2 is 1 - E
 // for S >= 0 and E for S < 0, and (1 - erf S)/2 the other one.  |S| is
-// clamped to 9 (E < 1e-36 there), which also keeps exp's argument in range.
+// clamped to 9 (E < 1e-36 there), which also keeps exp's argument in range;
+// the absolute value, the clamp and the interval come from the high word on
+// the integer pipe (positive doubles order like their high words).
 __device__ __forceinline__ void split_E(const MathTables &T, double S, double &E, double &eS)
 {
-    const double a = fmin(fabs(S), 9.0);
-    const int ha = __double2hiint(a);  // positive doubles order like their high words
-    const int iv = erfcx_interval(ha);
+    constexpr int kNineHi = 0x40220000;  // high word of 9.0 (low word 0)
+    const int hs = __double2hiint(S) & 0x7fffffff;
+    const bool clamp = hs >= kNineHi;
+    const double a = clamp ? 9.0 : __hiloint2double(hs, __double2loint(S));
+    const int iv = erfcx_interval(clamp ? kNineHi : hs);
     const double t = fma(a, T.sc[iv], T.off[iv]);
     const double *c = T.ecx[iv];
     double p = c[kErfcxDeg];

@@ -27,14 +27,13 @@ def _consts():
     deg = int(re.search(r"kErfcxDeg = (\d+);", s).group(1))
     nI = int(re.search(r"kErfcxIntervals = (\d+);", s).group(1))
     ecx = np.array(array("kErfcxHalf")).reshape(nI, deg + 1)
-    bounds = [int(t, 16) for t in re.findall(r"ha >= (0x[0-9a-f]{8})",
-                                              re.search(r"int erfcx_interval\(int ha\).*?\}", s, re.S).group(0))]
-    assert len(bounds) == nI - 1
+    eshift = int(re.search(r"kErfcxShift = (\d+);", s).group(1))
+    key0 = int(re.search(r"kErfcxKey0 = (0x[0-9a-f]+);", s).group(1), 16)
     n = int(re.search(r"kExpN = (\d+);", s).group(1))
     shift = int(re.search(r"kExpShift = (\d+);", s).group(1))
     return dict(inv=scalar("kExpInvLn2N"), hi=scalar("kExpLn2NHi"), lo=scalar("kExpLn2NLo"), n=n, shift=shift,
                 tab=array("kExpTable"), sc=array("kErfcxScale"), off=array("kErfcxOffset"), ecx=ecx, deg=deg,
-                bounds=bounds)
+                eshift=eshift, key0=key0)
 
 
 C = _consts()
@@ -79,7 +78,8 @@ def exp_t(x):
 def split_E(S):
     a = min(abs(S), 9.0)
     ha = hi_word(a)
-    iv = sum(int(ha >= b) for b in C["bounds"])
+    iv = max(0, (ha >> C["eshift"]) - C["key0"] + 1)
+    assert 0 <= iv < len(C["sc"])
     t = fma(a, C["sc"][iv], C["off"][iv])
     c = C["ecx"][iv]
     p = float(c[C["deg"]])
