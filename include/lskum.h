@@ -235,6 +235,20 @@ lskum_status lskum_get_case_info(lskum_ctx *ctx, int32_t cs, int32_t *first_poin
 lskum_status lskum_get_field_dev(lskum_ctx *ctx, int32_t field, double *out_dev, void *cuda_stream);
 lskum_status lskum_set_conserved_dev(lskum_ctx *ctx, const double *U_dev, void *cuda_stream);
 
+/* Host-array transfers (no counterpart in the paper).  Where the device can
+ * read and write pageable host memory directly (cudaDevAttrPageableMemoryAccess,
+ * as on a GPU attached to a Grace CPU), the calls that take or fill host
+ * arrays (lskum_set_state, lskum_set_conserved, lskum_get_field,
+ * lskum_get_state) reorder between the caller's array and the device layout
+ * in one kernel, with no staging copy; otherwise one copy each way goes
+ * through a device buffer.  Both give the same bits.  lskum_set_host_io
+ * chooses: direct = 1 (LSKUM_ERR_ARG where it is not supported) or 0 (the
+ * copies); a context starts with 1 where supported.  lskum_get_host_io
+ * reports the mode in use and whether direct access is supported (either
+ * pointer may be NULL). */
+lskum_status lskum_set_host_io(lskum_ctx *ctx, int32_t direct);
+lskum_status lskum_get_host_io(lskum_ctx *ctx, int32_t *direct, int32_t *supported);
+
 /* Replace the state by primitive fields (f64[N] each, caller order); the wall
  * projection is applied and the residual history is cleared.
  * Errors: LSKUM_ERR_ARG (NULL), LSKUM_ERR_NONPOSITIVE (rho or p <= 0 or not

@@ -77,6 +77,8 @@ struct lskum_ctx {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     double *pinned = nullptr;           // 4 * ld doubles of page-locked staging for state copies
     double *dscratch = nullptr;         // 4 * ld doubles on the device: caller-order staging
+    bool host_direct_ok = false;        // the device reads and writes pageable host memory
+    bool host_direct = false;           // host arrays go straight to / from the reorder kernels
     int launches_per_iter = 0;
     // cases (a batch is the disjoint union of its cases' clouds, caller order
     // = case 0's points, then case 1's, ...)
@@ -1108,6 +1110,12 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
     up(d.D, ones.data(), ld * sizeof(double));
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemset");
 
+    // host arrays straight to and from the reorder kernels where the device
+    // reads and writes pageable host memory
+    int pageable = 0;
+    if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, c->device) != cudaSuccess) pageable = 0;
+    c->host_direct_ok = c->host_direct = pageable == 1;
+
     // the function tables the sweeps read from global memory
     e = launch_init_math(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "initialising the function tables");
@@ -1310,12 +1318,19 @@ lskum_status state_from_conserved(lskum_ctx *c, const double *Ucaller, bool rese
 {
     // caller order, contiguous: one copy straight from the caller's memory,
     // then the reordering into the internal structure of arrays on the device
+    // (or, where the device reads pageable host memory, the reordering kernel
+    // reads the caller's array itself; finish_state synchronises before the
+    // call returns, so the caller may reuse the array)
     const int32_t n = c->n;
     cudaError_t e = join_user(c);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(c->dscratch, Ucaller, 4 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice,
-                            c->stream);
-    if (e == cudaSuccess) e = launch_from_caller(c->dscratch, c->ld, n, c->dev.inv, c->dev.set[c->cur].U, c->stream);
+    const double *src = Ucaller;
+    if (!c->host_direct) {
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c->dscratch, Ucaller, 4 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice,
+                                c->stream);
+        src = c->dscratch;
+    }
+    if (e == cudaSuccess) e = launch_from_caller(src, c->ld, n, c->dev.inv, c->dev.set[c->cur].U, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "setting the state");
     return finish_state(c, reset_hist);
 }
@@ -1448,8 +1463,10 @@ static lskum_status download_to(lskum_ctx *c, const double *src, const float *sr
                                 double *out)
 {
     const size_t bytes = (size_t)comps * c->n * sizeof(double);
-    cudaError_t e = launch_to_caller(src, srcf, comps, stride, c->ld, c->n, c->dev.inv, c->dscratch, c->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(out, c->dscratch, bytes, cudaMemcpyDeviceToHost, c->stream);
+    cudaError_t e = launch_to_caller(src, srcf, comps, stride, c->ld, c->n, c->dev.inv,
+                                     c->host_direct ? out : c->dscratch, c->stream);
+    if (e == cudaSuccess && !c->host_direct)
+        e = cudaMemcpyAsync(out, c->dscratch, bytes, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy D2H");
     return LSKUM_OK;
@@ -1852,6 +1869,24 @@ lskum_status lskum_get_order(lskum_ctx *c, int32_t *colour, int32_t *order, int3
     if (colour) std::memcpy(colour, c->colour.data(), c->n * sizeof(int32_t));
     if (order) std::memcpy(order, c->canon_order.data(), c->n * sizeof(int32_t));
     if (n_colours) *n_colours = c->n_colours;
+    return LSKUM_OK;
+}
+
+lskum_status lskum_set_host_io(lskum_ctx *c, int32_t direct)
+{
+    if (!c || (direct != 0 && direct != 1)) return c ? fail(c, LSKUM_ERR_ARG, "bad argument") : LSKUM_ERR_ARG;
+    if (c->pending) return fail(c, LSKUM_ERR_ARG, "an enqueued run has not been waited for");
+    if (direct && !c->host_direct_ok)
+        return fail(c, LSKUM_ERR_ARG, "the device cannot access pageable host memory directly");
+    c->host_direct = direct == 1;
+    return LSKUM_OK;
+}
+
+lskum_status lskum_get_host_io(lskum_ctx *c, int32_t *direct, int32_t *supported)
+{
+    if (!c) return LSKUM_ERR_ARG;
+    if (direct) *direct = c->host_direct ? 1 : 0;
+    if (supported) *supported = c->host_direct_ok ? 1 : 0;
     return LSKUM_OK;
 }
 

@@ -81,6 +81,8 @@ def load():
     L.lskum_validate.argtypes = [P(lskum_cloud), P(lskum_opts), i32, P(i32), P(i32)]
     L.lskum_get_field_dev.argtypes = [vp, i32, vp, vp]
     L.lskum_set_conserved_dev.argtypes = [vp, vp, vp]
+    L.lskum_set_host_io.argtypes = [vp, i32]
+    L.lskum_get_host_io.argtypes = [vp, vp, vp]
     L.lskum_set_start_iters.argtypes = [vp, i32]
     L.lskum_set_launch_shape.argtypes = [vp, i32, i32]
     u64 = C.c_uint64
@@ -110,7 +112,8 @@ def load():
               "lskum_get_state", "lskum_get_field", "lskum_get_residuals", "lskum_get_forces", "lskum_get_order",
               "lskum_get_info", "lskum_time_phases", "lskum_density_norm_noalloc", "lskum_batch_create",
               "lskum_get_case_residuals", "lskum_get_case_residuals4", "lskum_get_case_forces", "lskum_get_case_info", "lskum_autotune",
-              "lskum_get_wall_distance", "lskum_validate", "lskum_set_start_iters", "lskum_get_field_dev", "lskum_set_conserved_dev", "lskum_set_launch_shape", "lskum_mlp_create", "lskum_mlp_get_params",
+              "lskum_get_wall_distance", "lskum_validate", "lskum_set_start_iters", "lskum_get_field_dev", "lskum_set_conserved_dev", "lskum_set_launch_shape",
+              "lskum_set_host_io", "lskum_get_host_io", "lskum_mlp_create", "lskum_mlp_get_params",
               "lskum_mlp_set_params", "lskum_mlp_features", "lskum_mlp_forward", "lskum_mlp_loss_grads",
               "lskum_mlp_adam", "lskum_mlp_add_samples", "lskum_mlp_time_forward", "lskum_mlp_n_samples", "lskum_mlp_train",
               "lskum_mlp_predict"):
@@ -331,6 +334,17 @@ class Solver:
 
     def set_launch_shape(self, tpp, sweep_lanes):
         self._check(load().lskum_set_launch_shape(self._h, int(tpp), int(sweep_lanes)))
+
+    def set_host_io(self, direct):
+        """1: host arrays straight to / from the device's reorder kernels
+        (where the device reads pageable host memory); 0: staging copies."""
+        self._check(load().lskum_set_host_io(self._h, int(direct)))
+
+    def host_io(self):
+        """(direct in use, direct supported)."""
+        a, b = C.c_int32(), C.c_int32()
+        self._check(load().lskum_get_host_io(self._h, C.byref(a), C.byref(b)))
+        return a.value, b.value
 
     def set_start_iters(self, first_order_iters):
         self._check(load().lskum_set_start_iters(self._h, int(first_order_iters)))

@@ -65,3 +65,30 @@ def test_full_and_ragged_slices_match_the_oracle(n, m, wall):
         got, ref = s.field(f), r[k]
         scale = max(np.max(np.abs(ref)), 1e-300)
         assert np.max(np.abs(got - ref)) / scale < 1e-10, k
+
+
+def test_host_io_modes_give_the_same_bits():
+    """Host arrays through the staging copies and, where the device reads and
+    writes pageable host memory, straight through the reorder kernels: the
+    same state, fields and history, bit for bit; a mode the device does not
+    support is refused."""
+    from paper_2406_07441_gb300 import cloudgen as cg
+    from paper_2406_07441_gb300 import lskum as lk
+    c = cg.naca0012_jittered(48, 20, seed=11)
+    direct, supported = lk.Solver(c, 0.63, 2.0).host_io()
+    assert direct == supported
+    out = []
+    for mode in ((0, 1) if supported else (0,)):
+        s = lk.Solver(c, 0.63, 2.0, first_order_iters=3)
+        s.set_host_io(mode)
+        assert s.host_io() == (mode, supported)
+        assert s.run(5) == 5
+        U = s.field(lk.FIELD_U)
+        s.set_conserved(U * 1.0)
+        assert s.run(2) == 2
+        out.append((s.field(lk.FIELD_U), s.field(lk.FIELD_QX), s.field(lk.FIELD_DU), s.get_state()[3], s.residuals()))
+    for a, b in zip(out[0], out[-1]):
+        assert np.array_equal(a, b)
+    if not supported:
+        with pytest.raises(lk.LskumError):
+            lk.Solver(c, 0.63, 2.0).set_host_io(1)
