@@ -243,9 +243,11 @@ lskum_status lskum_set_conserved_dev(lskum_ctx *ctx, const double *U_dev, void *
  * in one kernel, with no staging copy; otherwise one copy each way goes
  * through a device buffer.  Both give the same bits.  lskum_set_host_io
  * chooses: direct = 1 (LSKUM_ERR_ARG where it is not supported) or 0 (the
- * copies); a context starts with 1 where supported.  lskum_get_host_io
- * reports the mode in use and whether direct access is supported (either
- * pointer may be NULL). */
+ * copies); a context starts with 0: on GB300 with a Grace host the direct
+ * kernels read 4.7 MB in 0.12 ms (the copy path 0.13 ms) but write a fresh
+ * array in 0.13 ms (0.05 ms), the device's first touches of new host pages
+ * being faults.  lskum_get_host_io reports the mode in use and whether
+ * direct access is supported (either pointer may be NULL). */
 lskum_status lskum_set_host_io(lskum_ctx *ctx, int32_t direct);
 lskum_status lskum_get_host_io(lskum_ctx *ctx, int32_t *direct, int32_t *supported);
 

@@ -1110,11 +1110,13 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
     up(d.D, ones.data(), ld * sizeof(double));
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemset");
 
-    // host arrays straight to and from the reorder kernels where the device
-    // reads and writes pageable host memory
+    // host arrays may go straight to and from the reorder kernels where the
+    // device reads and writes pageable host memory (off by default: not
+    // faster on GB300, see lskum_set_host_io)
     int pageable = 0;
     if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, c->device) != cudaSuccess) pageable = 0;
-    c->host_direct_ok = c->host_direct = pageable == 1;
+    c->host_direct_ok = pageable == 1;
+    c->host_direct = false;
 
     // the function tables the sweeps read from global memory
     e = launch_init_math(c->stream);
