@@ -401,11 +401,15 @@ __global__ void __launch_bounds__(256) k_grad(Dev d, const double *__restrict__ 
 // ---------------------------------------------------------------------------
 // flux residual, time step, diagonal, norm partials
 // ---------------------------------------------------------------------------
-// R += x with Neumaier's compensated summation (error term in c).
-__device__ __forceinline__ void comp_add(double &R, double &c, double x)
+// R += w dG with Kahan's compensated summation (W. Kahan, "Further remarks on
+// reducing truncation errors", CACM 8(1), 1965): c carries the negated
+// rounding error of the running sum into the next term; the product is folded
+// into that correction by one FMA.  The final sum is R - c.
+__device__ __forceinline__ void comp_add(double &R, double &c, double w, double dG)
 {
-    const double t = R + x;
-    c += fabs(R) >= fabs(x) ? (R - t) + x : (x - t) + R;
+    const double y = fma(w, dG, -c);  // the term w dG less the carried error, rounded once
+    const double t = R + y;
+    c = (t - R) - y;  // what the addition lost (negated)
     R = t;
 }
 
@@ -473,7 +477,7 @@ __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const doub
                 }
 #pragma unroll
                 for (int c = 0; c < 4; c++) {
-                    if (COMP) comp_add(R[c], Rc[c], w * (Gi[c] - G0[c]));
+                    if (COMP) comp_add(R[c], Rc[c], w, Gi[c] - G0[c]);
                     else R[c] = fma(w, Gi[c] - G0[c], R[c]);
                 }
             }
@@ -490,7 +494,7 @@ __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const doub
                 }
 #pragma unroll
                 for (int c = 0; c < 4; c++) {
-                    if (COMP) comp_add(R[c], Rc[c], w * (Gi[c] - G0[c]));
+                    if (COMP) comp_add(R[c], Rc[c], w, Gi[c] - G0[c]);
                     else R[c] = fma(w, Gi[c] - G0[c], R[c]);
                 }
             }
@@ -498,7 +502,7 @@ __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const doub
     }
 #pragma unroll
     for (int c = 0; c < 4; c++) {
-        if (COMP) R[c] += Rc[c];
+        if (COMP) R[c] -= Rc[c];
         R[c] = group_sum<TPP>(R[c]);
     }
     if (work && sub == 0) {
