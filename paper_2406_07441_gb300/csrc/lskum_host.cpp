@@ -952,6 +952,7 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
     d.g1y = A.alloc<double>(4 * (size_t)ld);
     d.R = A.alloc<double>(4 * (size_t)ld);
     d.D = A.alloc<double>(ld);
+    d.iD = A.alloc<double>(ld);
     d.dUs = A.alloc<double>(4 * (size_t)ld);
     d.dU = A.alloc<double>(4 * (size_t)ld);
     // launch shape: enough threads per point to fill the GPU on small clouds
@@ -1108,6 +1109,7 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
         if (e == cudaSuccess) e = cudaMemset(p, 0, 4 * (size_t)ld * sizeof(double));
     std::vector<double> ones(ld, 1.0);
     up(d.D, ones.data(), ld * sizeof(double));
+    up(d.iD, ones.data(), ld * sizeof(double));
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemset");
 
     // host arrays may go straight to and from the reorder kernels where the

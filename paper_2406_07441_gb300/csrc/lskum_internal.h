@@ -102,6 +102,7 @@ struct Dev {
     double *g1x, *g1y;       // first-order LS derivatives (the fixed part of Eq. 16)
     double *R;               // [4][ld]
     double *D;               // [ld]
+    double *iD;              // [ld] 1/D (explicit scheme: the local time step)
     double *dUs, *dU;        // [ld][4] (array of structures: one 32-byte gather per neighbour)
     // LU-SGS slot lists (CSR over the internal index): the slots of each point
     // whose neighbour comes earlier (lo) or later (up) in the sweep order,

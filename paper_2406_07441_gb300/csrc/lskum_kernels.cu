@@ -537,15 +537,20 @@ __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const doub
         const double u = pr[P_U], v = pr[P_V];
         const double a = sqrt(1.4 * pr[P_P] * pr[P_IRHO]);
         const double dt = cfl * d.geo[G_DMIN * ld + k] / (sqrt(u * u + v * v) + a);
-        if (d.scheme == 1) {  // explicit: D = 1/dt, the step is -R/D
+        // D and 1/D: the sweeps multiply by 1/D (one division per point here
+        // instead of one per point in each sweep)
+        if (d.scheme == 1) {  // explicit: D = 1/dt, the step is -dt R
             d.D[k] = 1.0 / dt;
+            d.iD[k] = dt;
             return;
         }
         if (d.lusgs == 1) {  // revised LU-SGS: Jameson's splitting, rho(A_d) = |u_d| + a
             const double u1 = fabs(u * e1x + v * e1y) + a, u2 = fabs(u * e2x + v * e2y) + a;
-            d.D[k] = 1.0 / dt +
-                     0.5 * (u1 * (fabs(d.geo[G_LS1_0 * ld + k]) + fabs(d.geo[G_LS1_1 * ld + k])) +
-                            u2 * (fabs(d.geo[G_LS1_2 * ld + k]) + fabs(d.geo[G_LS1_3 * ld + k])));
+            const double Dm = 1.0 / dt +
+                              0.5 * (u1 * (fabs(d.geo[G_LS1_0 * ld + k]) + fabs(d.geo[G_LS1_1 * ld + k])) +
+                                     u2 * (fabs(d.geo[G_LS1_2 * ld + k]) + fabs(d.geo[G_LS1_3 * ld + k])));
+            d.D[k] = Dm;
+            d.iD[k] = 1.0 / Dm;
             return;
         }
         double Dp = 1.0 / dt, Ddom = 0.0;
@@ -558,7 +563,9 @@ __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const doub
         Dp += r3 * d.geo[G_LS1_3 * ld + k];
         Ddom = r0 * d.geo[G_ABS_0 * ld + k] + r1 * d.geo[G_ABS_1 * ld + k] + r2 * d.geo[G_ABS_2 * ld + k]
              + r3 * d.geo[G_ABS_3 * ld + k];
-        d.D[k] = Dp > Ddom ? Dp : Ddom;
+        const double Da = Dp > Ddom ? Dp : Ddom;
+        d.D[k] = Da;
+        d.iD[k] = 1.0 / Da;
     }
 }
 
@@ -772,7 +779,7 @@ __device__ __forceinline__ void sweep_point(const Dev &d, const StateSet &st, co
                                             const T acc[4])
 {
     const int ld = d.ld;
-    const T iD = T(1) / (T)d.D[k];
+    const T iD = (T)d.iD[k];
     T w[4];
     if (FWD) {
         double rhs[4];
@@ -1018,7 +1025,7 @@ __global__ void __launch_bounds__(256) k_explicit(Dev d)
     double w[4] = {0.0, 0.0, 0.0, 0.0};
     const int fl = d.flag[k];
     if ((fl != kOuter || d.farfield == 1) && !frozen(d, k)) {
-        const double dt = 1.0 / d.D[k];
+        const double dt = d.iD[k];
 #pragma unroll
         for (int c = 0; c < 4; c++) w[c] = -dt * d.R[c * ld + k];
         if (fl == kWall) {
