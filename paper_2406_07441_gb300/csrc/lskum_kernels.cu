@@ -33,21 +33,6 @@ constexpr double kInv2SqrtPi = 0.28209479177387814347;    // 1 / (2 sqrt(pi))
 constexpr double kInvSqrtPi = 0.56418958354775628695;     // 1 / sqrt(pi)
 constexpr unsigned kFull = 0xffffffffu;
 
-// Programmatic dependent launch: the kernels of an iteration are launched so
-// that the next one may start while this one finishes.  Each signals at once
-// that its dependents may be scheduled (they run only once every block of
-// this grid has started) and waits for its predecessor grid, with its
-// memory visible, before its first read of anything the predecessor writes;
-// both are no-ops for an ordinary launch.
-__device__ __forceinline__ void pdl_trigger()
-{
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-__device__ __forceinline__ void pdl_wait()
-{
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-}
-
 // Every kernel returns at once after a stop or a failure.  When a case
 // reaches its drop target, k_norm marks it kReachedTarget, so the sweeps and
 // the update of that iteration still run; the next k_begin makes it
@@ -348,8 +333,6 @@ template <int TPP, bool CORR>
 __global__ void __launch_bounds__(256) k_grad(Dev d, const double *__restrict__ q, const double *__restrict__ pg,
                                               double *__restrict__ g)
 {
-    pdl_trigger();
-    pdl_wait();
     if (halted(d.ctrl)) return;
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     const int k = gt / TPP, sub = gt % TPP;
@@ -434,11 +417,9 @@ template <int TPP, bool COMP>
 __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const double *__restrict__ g)
 {
     __shared__ MathTables T;
-    pdl_trigger();
-    load_math_tables(T);  // constant tables: before the wait, overlapping the predecessor
-    pdl_wait();
-    __syncthreads();
     if (halted(d.ctrl)) return;
+    load_math_tables(T);
+    __syncthreads();
     const int n1 = ((const volatile Ctrl *)d.ctrl)->it;  // this iteration, counted by k_begin
     const double cfl = (d.ramp > 0.0 && (double)n1 < d.ramp) ? d.cfl * ((double)n1 / d.ramp) : d.cfl;
     const double hc = n1 <= d.first_order ? 0.0 : 0.5;  // first-order start: q~ = q
@@ -597,8 +578,6 @@ __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const doub
 __global__ void __launch_bounds__(256) k_norm_partials(Dev d)
 {
     __shared__ double red[4][8];
-    pdl_trigger();
-    pdl_wait();
     if (halted(d.ctrl)) return;
     const int j = blockIdx.x;
     const int p = d.blk_pos[j] + threadIdx.x;
@@ -634,8 +613,6 @@ __global__ void __launch_bounds__(256) k_norm_partials(Dev d)
 __global__ void __launch_bounds__(256) k_norm_cases(Dev d)
 {
     __shared__ double red[4][8];
-    pdl_trigger();
-    pdl_wait();
     if (halted(d.ctrl)) return;
     const int b = blockIdx.x;
     Ctrl *c = d.ctrl;
@@ -860,8 +837,6 @@ template <int JVP, bool FWD, int G, typename T>
 __global__ void __launch_bounds__(256) k_sweep(Dev d, StateSet st, int lb, int le)
 {
     const MathTables &Tb = g_math;  // wall and outer points only: no per-block copy
-    pdl_trigger();
-    pdl_wait();
     if (halted(d.ctrl)) return;
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     if (lb + (gt & ~31) / G >= le) return;  // the whole warp is past the level
@@ -899,8 +874,6 @@ template <int JVP, bool FWD, typename T>
 __global__ void __launch_bounds__(256) k_sweep_packed(Dev d, StateSet st, int wb, int we)
 {
     const MathTables &Tb = g_math;  // wall and outer points only: no per-block copy
-    pdl_trigger();
-    pdl_wait();
     if (halted(d.ctrl)) return;
     const int gw = wb + (blockIdx.x * blockDim.x + threadIdx.x) / 32;
     if (gw >= we) return;  // whole warps only (blocks are whole warps)
@@ -944,8 +917,6 @@ __global__ void __launch_bounds__(256) k_sweep_packed(Dev d, StateSet st, int wb
 // ---------------------------------------------------------------------------
 __global__ void k_begin(Ctrl *c)
 {
-    pdl_trigger();
-    pdl_wait();
     if (c->stop | c->error) return;
     int running = 0;
     for (int b = 0; b < c->n_cases; b++) {
@@ -961,11 +932,9 @@ template <bool INC>
 __global__ void __launch_bounds__(256) k_update(Dev d, int cur)
 {
     __shared__ MathTables T;
-    pdl_trigger();
-    load_math_tables(T);  // constant tables: before the wait, overlapping the predecessor
-    pdl_wait();
-    __syncthreads();
     if (INC && halted(d.ctrl)) return;
+    load_math_tables(T);
+    __syncthreads();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= d.n) return;
     const int ld = d.ld;
@@ -1049,8 +1018,6 @@ __global__ void __launch_bounds__(256) k_update(Dev d, int cur)
 // momentum removed at wall points; frozen outer points 0.
 __global__ void __launch_bounds__(256) k_explicit(Dev d)
 {
-    pdl_trigger();
-    pdl_wait();
     if (halted(d.ctrl)) return;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= d.n) return;
@@ -1077,8 +1044,6 @@ __global__ void __launch_bounds__(256) k_explicit(Dev d)
 // good state.
 __global__ void __launch_bounds__(256) k_repair(Dev d, int cur)
 {
-    pdl_trigger();
-    pdl_wait();
     if (halted(d.ctrl)) return;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= d.n) return;
@@ -1114,34 +1079,16 @@ __global__ void k_prep_run(Ctrl *c, double target)
         c->case_state[b] = (c->case_state[b] == kFailed || c->case_state[b] == kFailedNow) ? kFailed : kRunning;
 }
 
-// Launch with programmatic stream serialisation (see pdl_wait): within a
-// captured iteration the next kernel may be scheduled before this one ends.
-template <typename... KArgs, typename... Args>
-void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args... args)
-{
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kern, args...);
-}
-
 template <int TPP>
 cudaError_t enqueue_grad(const Dev &d, int cur, cudaStream_t s, int *launches)
 {
     const int gb = (d.n * TPP + 255) / 256;
     const StateSet st = d.set[cur];
-    launch_pdl(k_grad<TPP, false>, gb, 256, s, d, st.q, (const double *)nullptr, d.gq[0]);
+    k_grad<TPP, false><<<gb, 256, 0, s>>>(d, st.q, nullptr, d.gq[0]);
     (*launches)++;
     for (int it = 1; it <= d.K; it++) {
         const int a = (it - 1) & 1, b = it & 1;
-        launch_pdl(k_grad<TPP, true>, gb, 256, s, d, st.q, (const double *)d.gq[a], d.gq[b]);
+        k_grad<TPP, true><<<gb, 256, 0, s>>>(d, st.q, d.gq[a], d.gq[b]);
         (*launches)++;
     }
     return cudaGetLastError();
@@ -1152,8 +1099,8 @@ cudaError_t enqueue_res(const Dev &d, const Launch &L, int cur, cudaStream_t s, 
 {
     const int fin = d.K & 1;
     const int rb = (d.n * TPP + L.res_block - 1) / L.res_block;
-    if (d.precision) launch_pdl(k_residual<TPP, true>, rb, L.res_block, s, d, d.set[cur], (const double *)d.gq[fin]);
-    else launch_pdl(k_residual<TPP, false>, rb, L.res_block, s, d, d.set[cur], (const double *)d.gq[fin]);
+    if (d.precision) k_residual<TPP, true><<<rb, L.res_block, 0, s>>>(d, d.set[cur], d.gq[fin]);
+    else k_residual<TPP, false><<<rb, L.res_block, 0, s>>>(d, d.set[cur], d.gq[fin]);
     (*launches)++;
     return cudaGetLastError();
 }
@@ -1193,16 +1140,16 @@ void enqueue_sweeps_g(const Dev &d, int cur, int n_levels, const int32_t *lvl_be
         const int np = lvl_act_end[l] - lvl_beg[l];
         if (np <= 0) continue;
         const int blocks = (np * G + 255) / 256;
-        if (d.precision) launch_pdl(k_sweep<JVP, true, G, float>, blocks, 256, s, d, st, (int)lvl_beg[l], (int)lvl_act_end[l]);
-        else launch_pdl(k_sweep<JVP, true, G, double>, blocks, 256, s, d, st, (int)lvl_beg[l], (int)lvl_act_end[l]);
+        if (d.precision) k_sweep<JVP, true, G, float><<<blocks, 256, 0, s>>>(d, st, lvl_beg[l], lvl_act_end[l]);
+        else k_sweep<JVP, true, G, double><<<blocks, 256, 0, s>>>(d, st, lvl_beg[l], lvl_act_end[l]);
         (*launches)++;
     }
     for (int l = n_levels - 1; bwd && l >= 0; l--) {
         const int np = lvl_act_end[l] - lvl_beg[l];
         if (np <= 0) continue;
         const int blocks = (np * G + 255) / 256;
-        if (d.precision) launch_pdl(k_sweep<JVP, false, G, float>, blocks, 256, s, d, st, (int)lvl_beg[l], (int)lvl_act_end[l]);
-        else launch_pdl(k_sweep<JVP, false, G, double>, blocks, 256, s, d, st, (int)lvl_beg[l], (int)lvl_act_end[l]);
+        if (d.precision) k_sweep<JVP, false, G, float><<<blocks, 256, 0, s>>>(d, st, lvl_beg[l], lvl_act_end[l]);
+        else k_sweep<JVP, false, G, double><<<blocks, 256, 0, s>>>(d, st, lvl_beg[l], lvl_act_end[l]);
         (*launches)++;
     }
 }
@@ -1216,16 +1163,16 @@ void enqueue_sweeps_packed(const Dev &d, const Launch &L, int cur, int n_levels,
         const int wb = L.pk_lw[0][l], we = L.pk_lw[0][l + 1];
         if (we <= wb) continue;
         const int blocks = ((we - wb) * 32 + 255) / 256;
-        if (d.precision) launch_pdl(k_sweep_packed<JVP, true, float>, blocks, 256, s, d, st, wb, we);
-        else launch_pdl(k_sweep_packed<JVP, true, double>, blocks, 256, s, d, st, wb, we);
+        if (d.precision) k_sweep_packed<JVP, true, float><<<blocks, 256, 0, s>>>(d, st, wb, we);
+        else k_sweep_packed<JVP, true, double><<<blocks, 256, 0, s>>>(d, st, wb, we);
         (*launches)++;
     }
     for (int l = n_levels - 1; bwd && l >= 0; l--) {
         const int wb = L.pk_lw[1][l], we = L.pk_lw[1][l + 1];
         if (we <= wb) continue;
         const int blocks = ((we - wb) * 32 + 255) / 256;
-        if (d.precision) launch_pdl(k_sweep_packed<JVP, false, float>, blocks, 256, s, d, st, wb, we);
-        else launch_pdl(k_sweep_packed<JVP, false, double>, blocks, 256, s, d, st, wb, we);
+        if (d.precision) k_sweep_packed<JVP, false, float><<<blocks, 256, 0, s>>>(d, st, wb, we);
+        else k_sweep_packed<JVP, false, double><<<blocks, 256, 0, s>>>(d, st, wb, we);
         (*launches)++;
     }
 }
@@ -1252,20 +1199,20 @@ cudaError_t enqueue_phase(const Dev &d, const Launch &L, int cur, int ph, int n_
 {
     switch (ph) {
     case 0:
-        launch_pdl(k_begin, 1, 1, s, d.ctrl);
+        k_begin<<<1, 1, 0, s>>>(d.ctrl);
         (*launches)++;
         return enqueue_grad_res(d, L, cur, s, launches, true, false);
     case 1: return enqueue_grad_res(d, L, cur, s, launches, false, true);
     case 2:
-        launch_pdl(k_norm_partials, d.n_blk, 256, s, d);
-        launch_pdl(k_norm_cases, d.n_cases, 256, s, d);
+        k_norm_partials<<<d.n_blk, 256, 0, s>>>(d);
+        k_norm_cases<<<d.n_cases, 256, 0, s>>>(d);
         (*launches) += 2;
         return cudaGetLastError();
     case 3:
     case 4:
         if (d.scheme == 1) {  // explicit: one step kernel instead of the two sweeps
             if (ph == 3) {
-                launch_pdl(k_explicit, (d.n + 255) / 256, 256, s, d);
+                k_explicit<<<(d.n + 255) / 256, 256, 0, s>>>(d);
                 (*launches)++;
             }
             return cudaGetLastError();
@@ -1273,10 +1220,10 @@ cudaError_t enqueue_phase(const Dev &d, const Launch &L, int cur, int ph, int n_
         if (d.jvp == 0) return enqueue_sweeps<0>(d, L, cur, n_levels, lvl_beg, lvl_act_end, s, launches, ph == 3, ph == 4);
         return enqueue_sweeps<1>(d, L, cur, n_levels, lvl_beg, lvl_act_end, s, launches, ph == 3, ph == 4);
     case 5:
-        launch_pdl(k_update<true>, (d.n + 255) / 256, 256, s, d, cur);
+        k_update<true><<<(d.n + 255) / 256, 256, 0, s>>>(d, cur);
         (*launches)++;
         if (d.n_cases > 1) {
-            launch_pdl(k_repair, (d.n + 255) / 256, 256, s, d, cur);
+            k_repair<<<(d.n + 255) / 256, 256, 0, s>>>(d, cur);
             (*launches)++;
         }
         return cudaGetLastError();
