@@ -974,7 +974,8 @@ __global__ void __launch_bounds__(256) k_update(Dev d, int cur)
     }
 #pragma unroll
     for (int c = 0; c < 4; c++) dst.U[c * ld + k] = U[c];
-    dst.q[0 * ld + k] = log(P.rho) + 2.5 * log(P.beta) - P.beta * P.q2;
+    // q1 = ln rho + 2.5 ln beta - beta |u|^2 with one logarithm: ln(rho beta^2 sqrt(beta))
+    dst.q[0 * ld + k] = log(P.rho * (P.beta * P.beta) * P.sb) - P.beta * P.q2;
     dst.q[1 * ld + k] = 2.0 * P.beta * P.u;
     dst.q[2 * ld + k] = 2.0 * P.beta * P.v;
     dst.q[3 * ld + k] = -2.0 * P.beta;
