@@ -75,7 +75,6 @@ struct lskum_ctx {
     cudaStream_t user_stream = nullptr;
     cudaEvent_t ev = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
-    double *pinned = nullptr;           // 4 * ld doubles of page-locked staging for state copies
     double *dscratch = nullptr;         // 4 * ld doubles on the device: caller-order staging
     bool host_direct_ok = false;        // the device reads and writes pageable host memory
     bool host_direct = false;           // host arrays go straight to / from the reorder kernels
@@ -977,8 +976,7 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
     c->dscratch = A.alloc<double>(4 * (size_t)ld);
     if (A.err != cudaSuccess) return cuda_fail(c, A.err, "cudaMalloc");
     e = cudaMemset(c->ctrl, 0, sizeof(Ctrl));
-    if (e == cudaSuccess) e = cudaMallocHost(&c->pinned, 4 * (size_t)ld * sizeof(double));
-    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMallocHost");
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemset");
     d.flag = dfl;
     d.wnx = dwnx;
     d.wny = dwny;
@@ -1176,7 +1174,6 @@ void lskum_destroy(lskum_ctx *c)
     for (auto &g : c->graph)
         if (g) cudaGraphExecDestroy(g);
     c->arena.release();
-    if (c->pinned) cudaFreeHost(c->pinned);
     if (c->ev) cudaEventDestroy(c->ev);
     if (c->stream) cudaStreamDestroy(c->stream);
     delete c;
