@@ -212,7 +212,7 @@ struct HostPrep {
     std::vector<uint8_t> smb_caller;  // sub-stencil membership per caller-order slot
     // packed sweep form per direction (0 forward / lower lists, 1 backward / upper lists)
     std::vector<int32_t> pk_pt[2], pk_nbr[2];
-    std::vector<uint8_t> pk_mb[2];
+    std::vector<uint8_t> pk_mb[2], pk_steps[2];
     std::vector<double> pk_w1[2], pk_w2[2];
 };
 static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &hp);
@@ -381,8 +381,17 @@ static lskum_status verify_layout(lskum_ctx *c, const lskum_cloud *cl, const Hos
         const std::vector<int32_t> &so = dir == 0 ? hp.sw_fwd : hp.sw_bwd;
         const std::vector<int32_t> &loff = dir == 0 ? hp.lo_off : hp.up_off;
         const std::vector<int32_t> &lnbr = dir == 0 ? hp.lo_nbr : hp.up_nbr;
-        if ((int32_t)lw.size() != c->n_levels + 1 || (size_t)lw.back() * 32 != pt.size() || nb.size() != pt.size())
+        if ((int32_t)lw.size() != c->n_levels + 1 || (size_t)lw.back() * 32 != pt.size() || nb.size() != pt.size() ||
+            hp.pk_steps[dir].size() != (size_t)lw.back())
             return fail(c, LSKUM_ERR_ARG, "layout: packed sweep size");
+        for (int64_t w = 0; w < lw.back(); w++) {  // each segment fits the warp's sum steps
+            int32_t run = 0;
+            for (int64_t t = w * 32; t < w * 32 + 32; t++) {
+                run = (t > w * 32 && pt[t] == pt[t - 1] && pt[t] >= 0) ? run + 1 : 1;
+                if (pt[t] >= 0 && run > (1 << hp.pk_steps[dir][w]))
+                    return fail(c, LSKUM_ERR_ARG, "layout: packed sum steps of warp %lld", (long long)w);
+            }
+        }
         std::vector<int32_t> seen_pos(n, 0);
         for (int32_t l = 0; l < c->n_levels; l++) {
             for (int64_t t = (int64_t)lw[l] * 32; t < (int64_t)lw[l + 1] * 32; t++) {
@@ -800,7 +809,11 @@ static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &
                 members[w].push_back(pos);
             }
             for (const auto &mw : members) {
-                int32_t lane = 0;
+                int32_t lane = 0, longest = 1;
+                for (int32_t pos : mw) longest = std::max(longest, loff[so[pos] + 1] - loff[so[pos]]);
+                uint8_t steps = 0;
+                while ((1 << steps) < longest) steps++;
+                hp.pk_steps[dir].push_back(steps);
                 for (int32_t pos : mw) {
                     const int32_t k = so[pos];
                     const int32_t b = loff[k], e = loff[k + 1];
@@ -928,7 +941,7 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
     std::vector<float> pkf[2][2];
     for (int dir = 0; dir < 2; dir++) {
         d.pk_pt[dir] = d.pk_nbr[dir] = nullptr;
-        d.pk_mb[dir] = nullptr;
+        d.pk_mb[dir] = d.pk_steps[dir] = nullptr;
         d.pk_w1[dir] = d.pk_w2[dir] = nullptr;
         d.pk_w1f[dir] = d.pk_w2f[dir] = nullptr;
         if (!c->pk_ok || hp.pk_pt[dir].empty()) continue;
@@ -936,6 +949,7 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
         d.pk_pt[dir] = A.alloc<int32_t>(m);
         d.pk_nbr[dir] = A.alloc<int32_t>(m);
         d.pk_mb[dir] = A.alloc<uint8_t>(m);
+        d.pk_steps[dir] = A.alloc<uint8_t>(hp.pk_steps[dir].size());
         d.pk_w1[dir] = A.alloc<double>(m);
         d.pk_w2[dir] = A.alloc<double>(m);
         if (mixed) {
@@ -1081,6 +1095,7 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
         up((void *)d.pk_pt[dir], hp.pk_pt[dir].data(), m * sizeof(int32_t));
         up((void *)d.pk_nbr[dir], hp.pk_nbr[dir].data(), m * sizeof(int32_t));
         up((void *)d.pk_mb[dir], hp.pk_mb[dir].data(), m);
+        up((void *)d.pk_steps[dir], hp.pk_steps[dir].data(), hp.pk_steps[dir].size());
         up((void *)d.pk_w1[dir], hp.pk_w1[dir].data(), m * sizeof(double));
         up((void *)d.pk_w2[dir], hp.pk_w2[dir].data(), m * sizeof(double));
         if (d.pk_w1f[dir]) {

@@ -125,6 +125,7 @@ struct Dev {
     // longer than 32)
     const int32_t *pk_pt[2], *pk_nbr[2];
     const uint8_t *pk_mb[2];
+    const uint8_t *pk_steps[2];  // per warp: steps of its segmented sum, ceil(log2(longest list))
     const double *pk_w1[2], *pk_w2[2];
     const float *pk_w1f[2], *pk_w2f[2];
     // per-case residual norm: stage 1 sums R_rho^2 over blocks of up to 256

@@ -896,9 +896,12 @@ __global__ void __launch_bounds__(256) k_sweep_packed(Dev d, StateSet st, int wb
         const T w2 = sizeof(T) == 4 ? (T)d.pk_w2f[dir][e] : (T)d.pk_w2[dir][e];
         sweep_slot<JVP, T>(d, st, Tb, dW, sb.prim, framed, e1x, e1y, e2x, e2y, d.pk_nbr[dir][e], mb, w1, w2, acc);
     }
-    // segmented suffix sum: lane l adds lane l + o when both hold the same point
+    // segmented suffix sum: lane l adds lane l + o when both hold the same
+    // point; the warp's longest list bounds the steps (warp-uniform)
+    const int steps = d.pk_steps[dir][gw];
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
+        if (o >= (1 << steps)) break;
         const int p2 = __shfl_down_sync(kFull, pos, o);
         T v[4];
 #pragma unroll
