@@ -259,7 +259,11 @@ lskum_status lskum_set_state(lskum_ctx *ctx, const double *rho, const double *u,
                              const double *p);
 
 /* Replace the state by conserved variables U f64[N][4] (caller order), keeping
- * the residual history (resume from a checkpoint).  Same errors as above. */
+ * the residual history (resume from a checkpoint).  U is taken as given, with
+ * no wall projection, so a state read with lskum_get_field(LSKUM_FIELD_U)
+ * resumes bit for bit (re-projecting a projected state can move its last
+ * bit); every update projects the wall points it moves.  Same errors as
+ * above. */
 lskum_status lskum_set_conserved(lskum_ctx *ctx, const double *U);
 
 /*

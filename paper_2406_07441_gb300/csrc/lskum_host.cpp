@@ -1328,9 +1328,9 @@ lskum_status ensure_hist(lskum_ctx *c, int32_t need)
     return s;
 }
 
-lskum_status finish_state(lskum_ctx *c, bool reset_hist);
+lskum_status finish_state(lskum_ctx *c, bool reset_hist, bool project);
 
-lskum_status state_from_conserved(lskum_ctx *c, const double *Ucaller, bool reset_hist)
+lskum_status state_from_conserved(lskum_ctx *c, const double *Ucaller, bool reset_hist, bool project)
 {
     // caller order, contiguous: one copy straight from the caller's memory,
     // then the reordering into the internal structure of arrays on the device
@@ -1348,13 +1348,15 @@ lskum_status state_from_conserved(lskum_ctx *c, const double *Ucaller, bool rese
     }
     if (e == cudaSuccess) e = launch_from_caller(src, c->ld, n, c->dev.inv, c->dev.set[c->cur].U, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "setting the state");
-    return finish_state(c, reset_hist);
+    return finish_state(c, reset_hist, project);
 }
 
 // The conserved state of the current set was written on the device: derive
-// q and the per-point quantities (with the wall projection), check it, and
-// reset the counters (all of them with reset_hist).
-lskum_status finish_state(lskum_ctx *c, bool reset_hist)
+// q and the per-point quantities (with the wall projection when `project`:
+// a state built from primitives or predicted; a conserved checkpoint is
+// taken as given, since re-projecting a projected state can move its last
+// bit), check it, and reset the counters (all of them with reset_hist).
+lskum_status finish_state(lskum_ctx *c, bool reset_hist, bool project)
 {
     // a new state: the increments restart from zero (the revised LU-SGS
     // lags its S term on the previous increment)
@@ -1362,7 +1364,7 @@ lskum_status finish_state(lskum_ctx *c, bool reset_hist)
     if (e == cudaSuccess && c->dev.dUf)
         e = cudaMemsetAsync(c->dev.dUf, 0, 4 * (size_t)c->ld * sizeof(float), c->stream);
     if (e == cudaSuccess) e = launch_reset_ctrl(c->ctrl, c->stream);
-    if (e == cudaSuccess) e = launch_init_state(c->dev, c->cur, c->stream);
+    if (e == cudaSuccess) e = launch_init_state(c->dev, c->cur, project, c->stream);
     Ctrl h{};
     if (e != cudaSuccess) return cuda_fail(c, e, "setting the state");
     lskum_status s = read_ctrl(c, &h);
@@ -1397,14 +1399,14 @@ lskum_status lskum_set_state(lskum_ctx *c, const double *rho, const double *u, c
             return fail(c, LSKUM_ERR_NONPOSITIVE, "non-physical input state at point %d", k);
         host_prim_to_cons(rho[k], u[k], v[k], p[k], &U[4 * (size_t)k]);
     }
-    return state_from_conserved(c, U.data(), true);
+    return state_from_conserved(c, U.data(), true, true);
 }
 
 lskum_status lskum_set_conserved(lskum_ctx *c, const double *U)
 {
     if (!c || !U) return c ? fail(c, LSKUM_ERR_ARG, "NULL argument") : LSKUM_ERR_ARG;
     if (c->pending) return fail(c, LSKUM_ERR_ARG, "an enqueued run has not been waited for");
-    return state_from_conserved(c, U, false);
+    return state_from_conserved(c, U, false, false);
 }
 
 // Asynchronous part of lskum_run: enqueue max_iters graph launches.
@@ -1562,7 +1564,7 @@ lskum_status lskum_set_conserved_dev(lskum_ctx *c, const double *U_dev, void *cu
     cudaError_t e = order_after(c, c->stream, us);
     if (e == cudaSuccess) e = launch_from_caller(U_dev, c->ld, c->n, c->dev.inv, c->dev.set[c->cur].U, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "state from device memory");
-    lskum_status s = finish_state(c, false);
+    lskum_status s = finish_state(c, false, false);
     if (s != LSKUM_OK) return s;
     e = order_after(c, us, c->stream);
     return e == cudaSuccess ? LSKUM_OK : cuda_fail(c, e, "ordering the caller's stream");
@@ -2027,7 +2029,7 @@ lskum_status ctx_mlp_view(lskum_ctx *c, MlpView *v)
 
 lskum_status ctx_state_written(lskum_ctx *c)
 {
-    return finish_state(c, true);
+    return finish_state(c, true, true);
 }
 
 // First residual norm of every case at the current state: one iteration's

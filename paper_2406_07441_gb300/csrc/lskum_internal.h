@@ -166,7 +166,9 @@ cudaError_t launch_iteration(const Dev &d, const Launch &L, int cur, int n_level
 // sweep, 4 backward sweep, 5 update), launched directly on s.
 cudaError_t launch_phase(const Dev &d, const Launch &L, int cur, int phase, int n_levels, const int32_t *lvl_beg,
                          const int32_t *lvl_act_end, const int32_t *lvl_end, cudaStream_t s);
-cudaError_t launch_init_state(const Dev &d, int cur, cudaStream_t s);
+// Derive q and the per-point records of a new state in set cur (with the
+// wall projection of the state when project).
+cudaError_t launch_init_state(const Dev &d, int cur, bool project, cudaStream_t s);
 // Fill the global copy of the function tables the sweeps read (idempotent).
 cudaError_t launch_init_math(cudaStream_t s);
 cudaError_t launch_reset_ctrl(Ctrl *c, cudaStream_t s);

@@ -932,7 +932,7 @@ __global__ void k_begin(Ctrl *c)
 }
 
 template <bool INC>
-__global__ void __launch_bounds__(256) k_update(Dev d, int cur)
+__global__ void __launch_bounds__(256) k_update(Dev d, int cur, bool project = true)
 {
     __shared__ MathTables T;
     if (INC && halted(d.ctrl)) return;
@@ -952,9 +952,10 @@ __global__ void __launch_bounds__(256) k_update(Dev d, int cur)
 #pragma unroll
         for (int c = 0; c < 4; c++) U[c] += d.dUf ? (double)d.dUf[4 * k + c] : d.dU[4 * k + c];
     }
-    // wall projection of a new state only: re-projecting a projected state
+    // wall projection of a moved point, or of a new state built from
+    // primitives or predicted (project): re-projecting a projected state
     // could change its last bits, and a stopped case must keep its state
-    if (fl == kWall && (moves || !INC)) {
+    if (fl == kWall && (moves || (!INC && project))) {
         const double nx = d.wnx[k], ny = d.wny[k];
         const double mn = U[1] * nx + U[2] * ny;
         U[1] -= mn * nx;
@@ -1254,9 +1255,9 @@ cudaError_t launch_phase(const Dev &d, const Launch &L, int cur, int phase, int 
     return enqueue_phase(d, L, cur, phase, n_levels, lvl_beg, lvl_act_end, lvl_end, s, &launches);
 }
 
-cudaError_t launch_init_state(const Dev &d, int cur, cudaStream_t s)
+cudaError_t launch_init_state(const Dev &d, int cur, bool project, cudaStream_t s)
 {
-    k_update<false><<<(d.n + 255) / 256, 256, 0, s>>>(d, cur);
+    k_update<false><<<(d.n + 255) / 256, 256, 0, s>>>(d, cur, project);
     return cudaGetLastError();
 }
 
