@@ -931,23 +931,26 @@ __global__ void k_begin(Ctrl *c)
     else c->it += 1;
 }
 
-template <bool INC>
-__global__ void __launch_bounds__(256) k_update(Dev d, int cur, bool project = true)
+// One kernel for both uses (inc: after an iteration, set cur -> 1 - cur; not
+// inc: a new state in set cur), so that q and the per-point records of a
+// given U come from the same instructions either way: a resumed checkpoint
+// continues bit for bit.
+__global__ void __launch_bounds__(256) k_update(Dev d, int cur, bool inc, bool project)
 {
     __shared__ MathTables T;
-    if (INC && halted(d.ctrl)) return;
+    if (inc && halted(d.ctrl)) return;
     load_math_tables(T);
     __syncthreads();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= d.n) return;
     const int ld = d.ld;
     const StateSet src = d.set[cur];
-    const StateSet dst = d.set[INC ? 1 - cur : cur];
+    const StateSet dst = d.set[inc ? 1 - cur : cur];
     const int fl = d.flag[k];
     double U[4];
 #pragma unroll
     for (int c = 0; c < 4; c++) U[c] = src.U[c * ld + k];
-    const bool moves = INC && (fl != kOuter || d.farfield == 1) && !frozen(d, k);
+    const bool moves = inc && (fl != kOuter || d.farfield == 1) && !frozen(d, k);
     if (moves) {
 #pragma unroll
         for (int c = 0; c < 4; c++) U[c] += d.dUf ? (double)d.dUf[4 * k + c] : d.dU[4 * k + c];
@@ -955,7 +958,7 @@ __global__ void __launch_bounds__(256) k_update(Dev d, int cur, bool project = t
     // wall projection of a moved point, or of a new state built from
     // primitives or predicted (project): re-projecting a projected state
     // could change its last bits, and a stopped case must keep its state
-    if (fl == kWall && (moves || (!INC && project))) {
+    if (fl == kWall && (moves || (!inc && project))) {
         const double nx = d.wnx[k], ny = d.wny[k];
         const double mn = U[1] * nx + U[2] * ny;
         U[1] -= mn * nx;
@@ -965,7 +968,7 @@ __global__ void __launch_bounds__(256) k_update(Dev d, int cur, bool project = t
     const bool ok = P.rho > 0.0 && P.p > 0.0 && isfinite(P.rho) && isfinite(P.p) && isfinite(P.u) &&
                     isfinite(P.v);
     if (!ok) {
-        if (INC && d.n_cases > 1) {  // fail this case only; k_repair restores its state
+        if (inc && d.n_cases > 1) {  // fail this case only; k_repair restores its state
             const int b = d.case_of[k];
             atomicExch(&d.ctrl->case_state[b], (int32_t)kFailedNow);
             atomicExch(&d.ctrl->case_err[b], -3);  // LSKUM_ERR_NONPOSITIVE
@@ -1225,7 +1228,7 @@ cudaError_t enqueue_phase(const Dev &d, const Launch &L, int cur, int ph, int n_
         if (d.jvp == 0) return enqueue_sweeps<0>(d, L, cur, n_levels, lvl_beg, lvl_act_end, s, launches, ph == 3, ph == 4);
         return enqueue_sweeps<1>(d, L, cur, n_levels, lvl_beg, lvl_act_end, s, launches, ph == 3, ph == 4);
     case 5:
-        k_update<true><<<(d.n + 255) / 256, 256, 0, s>>>(d, cur);
+        k_update<<<(d.n + 255) / 256, 256, 0, s>>>(d, cur, true, true);
         (*launches)++;
         if (d.n_cases > 1) {
             k_repair<<<(d.n + 255) / 256, 256, 0, s>>>(d, cur);
@@ -1257,7 +1260,7 @@ cudaError_t launch_phase(const Dev &d, const Launch &L, int cur, int phase, int 
 
 cudaError_t launch_init_state(const Dev &d, int cur, bool project, cudaStream_t s)
 {
-    k_update<false><<<(d.n + 255) / 256, 256, 0, s>>>(d, cur, project);
+    k_update<<<(d.n + 255) / 256, 256, 0, s>>>(d, cur, false, project);
     return cudaGetLastError();
 }
 
