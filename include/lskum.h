@@ -129,7 +129,14 @@ typedef struct {
  *                    points of a colour together, Alg. 6) or
  *                    LSKUM_ORDER_WALL_FIRST (1; the wall points colour by
  *                    colour, then the interior points colour by colour,
- *                    Alg. 4; the backward sweep is the exact reverse)
+ *                    Alg. 4; the backward sweep is the exact reverse) or
+ *                    LSKUM_ORDER_SERIAL (2; the serial sweeps of Alg. 2:
+ *                    wall, interior and outer points, each in caller order,
+ *                    no colouring; executed level by level over the
+ *                    dependency graph this order induces -- a point's level
+ *                    is one more than the highest among its earlier
+ *                    neighbours -- which reproduces the sequential sweeps
+ *                    exactly; as many levels as the longest dependency chain)
  *   farfield         the outer (far-field) points: LSKUM_FARFIELD_FREESTREAM
  *                    (0) holds them at the free stream (Dirichlet; they are
  *                    not swept); LSKUM_FARFIELD_KINETIC (1) makes them
@@ -148,7 +155,7 @@ typedef struct {
  */
 enum { LSKUM_SCHEME_LUSGS = 0, LSKUM_SCHEME_EXPLICIT = 1 };
 enum { LSKUM_LUSGS_ANANDH = 0, LSKUM_LUSGS_MANISH = 1 };
-enum { LSKUM_ORDER_COLOUR = 0, LSKUM_ORDER_WALL_FIRST = 1 };
+enum { LSKUM_ORDER_COLOUR = 0, LSKUM_ORDER_WALL_FIRST = 1, LSKUM_ORDER_SERIAL = 2 };
 enum { LSKUM_FARFIELD_FREESTREAM = 0, LSKUM_FARFIELD_KINETIC = 1 };
 typedef struct {
     double mach, aoa_deg, cfl, cfl_ramp_iters;

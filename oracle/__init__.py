@@ -171,7 +171,8 @@ class Oracle:
     def __init__(self, cloud, ordering=0, farfield=FARFIELD_FREESTREAM, mach=0.0, aoa_deg=0.0):
         """ordering 0: the sweep order of Alg. 6 (points stably sorted by
         colour); 1: Alg. 4 (wall points by colour, then interior points by
-        colour, then outer points).  farfield 0: outer points frozen at the
+        colour, then outer points); 2: Alg. 2 (wall, interior and outer
+        points, each in index order; no colours).  farfield 0: outer points frozen at the
         free stream; 1: the kinetic far field with the free stream of
         (mach, aoa_deg) and the cloud's outward normals at outer points."""
         self.cloud = cloud
@@ -192,10 +193,13 @@ class Oracle:
         self.rank = np.zeros(self.n, np.int32)
         self.ncolours = lib().o_color_order(self.n, _p(k[5]), _p(k[6]), _p(self.colour), _p(self.order),
                                             _p(self.rank))
+        group = np.where(cloud.flag == 1, 0, np.where(cloud.flag == 0, 1, 2))
         if ordering == 1:
-            group = np.where(cloud.flag == 1, 0, np.where(cloud.flag == 0, 1, 2))
             key = group.astype(np.int64) * (self.ncolours + 1) + self.colour
             self.order[:] = np.argsort(key, kind="stable").astype(np.int32)
+            self.rank[self.order] = np.arange(self.n, dtype=np.int32)
+        elif ordering == 2:
+            self.order[:] = np.argsort(group, kind="stable").astype(np.int32)
             self.rank[self.order] = np.arange(self.n, dtype=np.int32)
 
     def initial_state(self, mach, aoa_deg):

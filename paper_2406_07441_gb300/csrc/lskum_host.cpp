@@ -141,9 +141,12 @@ lskum_status cuda_fail(lskum_ctx *c, cudaError_t e, const char *what)
 // in its stencil (ascending).  Visiting points in index order, every still
 // uncoloured point (the visited one first, then its neighbours) receives the
 // smallest colour > 0 not used by any of its neighbours.
-int32_t colour_points(int32_t n, const int32_t *off, const int32_t *idx, std::vector<int32_t> &col)
+// The other half of the symmetrised neighbour graph: for each point, the
+// points that list it but are not in its own stencil, ascending (CSR).
+void reverse_lists(int32_t n, const int32_t *off, const int32_t *idx, std::vector<int32_t> &rcnt,
+                   std::vector<int32_t> &rev)
 {
-    std::vector<int32_t> rcnt(n + 1, 0);
+    rcnt.assign(n + 1, 0);
     auto listed_by = [&](int32_t q, int32_t p) {  // is p in stencil(q)?
         for (int32_t f = off[q]; f < off[q + 1]; f++)
             if (idx[f] == p) return true;
@@ -153,12 +156,19 @@ int32_t colour_points(int32_t n, const int32_t *off, const int32_t *idx, std::ve
         for (int32_t e = off[p]; e < off[p + 1]; e++)
             if (!listed_by(idx[e], p)) rcnt[idx[e] + 1]++;
     for (int32_t p = 0; p < n; p++) rcnt[p + 1] += rcnt[p];
-    std::vector<int32_t> rev(std::max<int32_t>(rcnt[n], 1)), fill(n, 0);
+    rev.assign(std::max<int32_t>(rcnt[n], 1), 0);
+    std::vector<int32_t> fill(n, 0);
     for (int32_t p = 0; p < n; p++)
         for (int32_t e = off[p]; e < off[p + 1]; e++) {
             const int32_t q = idx[e];
             if (!listed_by(q, p)) rev[rcnt[q] + fill[q]++] = p;
         }
+}
+
+int32_t colour_points(int32_t n, const int32_t *off, const int32_t *idx, std::vector<int32_t> &col)
+{
+    std::vector<int32_t> rcnt, rev;
+    reverse_lists(n, off, idx, rcnt, rev);
     col.assign(n, 0);
     std::vector<int32_t> seen;  // seen[colour] == stamp when used by a neighbour
     int32_t stamp = 0;
@@ -234,7 +244,8 @@ static bool opts_valid(const lskum_opts *o)
            o->first_order_iters >= 0 &&
            (o->scheme == LSKUM_SCHEME_LUSGS || (o->scheme == LSKUM_SCHEME_EXPLICIT && o->precision == 0)) &&
            (o->lusgs == LSKUM_LUSGS_ANANDH || o->lusgs == LSKUM_LUSGS_MANISH) &&
-           (o->ordering == LSKUM_ORDER_COLOUR || o->ordering == LSKUM_ORDER_WALL_FIRST) &&
+           (o->ordering == LSKUM_ORDER_COLOUR || o->ordering == LSKUM_ORDER_WALL_FIRST ||
+            o->ordering == LSKUM_ORDER_SERIAL) &&
            (o->farfield == LSKUM_FARFIELD_FREESTREAM || o->farfield == LSKUM_FARFIELD_KINETIC);
 }
 
@@ -647,16 +658,45 @@ static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &
     // sweep order (caller indices): colour by colour (Alg. 6), or wall points
     // colour by colour, then interior, then outer points (Alg. 4); ties by
     // caller index.  `skey` is the level a point belongs to; a neighbour is
-    // "lower" when its key is smaller.
+    // "lower" when its key is smaller.  The serial order of Alg. 2 (wall,
+    // interior, outer points, each in caller order) has no colours: its
+    // levels are those of its dependency graph, a point's level one more
+    // than the highest level of its earlier neighbours in the symmetrised
+    // graph, so that coupled points never share a level, every earlier
+    // neighbour lies in a lower level and every later one in a higher level,
+    // and the level-parallel sweeps reproduce the sequential ones exactly.
     auto trank = [&](int32_t p) { return c->flag[p] == LSKUM_WALL ? 0 : (c->flag[p] == LSKUM_INTERIOR ? 1 : 2); };
     const bool wall_first = c->opts.ordering == LSKUM_ORDER_WALL_FIRST;
-    auto skey = [&](int32_t p) -> int64_t {
-        return wall_first ? (int64_t)trank(p) * (nc + 1) + c->colour[p] : (int64_t)c->colour[p];
-    };
+    const bool serial = c->opts.ordering == LSKUM_ORDER_SERIAL;
+    std::vector<int64_t> depth;
     c->canon_order.resize(n);
     std::iota(c->canon_order.begin(), c->canon_order.end(), 0);
-    std::stable_sort(c->canon_order.begin(), c->canon_order.end(),
-                     [&](int32_t a, int32_t b) { return skey(a) < skey(b); });
+    if (serial) {
+        std::stable_sort(c->canon_order.begin(), c->canon_order.end(),
+                         [&](int32_t a, int32_t b) { return trank(a) < trank(b); });
+        std::vector<int32_t> rank(n), rcnt, rev;
+        for (int32_t k = 0; k < n; k++) rank[c->canon_order[k]] = k;
+        reverse_lists(n, off, idx, rcnt, rev);
+        depth.assign(n, 0);
+        for (int32_t k = 0; k < n; k++) {
+            const int32_t p = c->canon_order[k];
+            if (!swept(c, p)) continue;
+            int64_t dmax = 0;
+            auto see = [&](int32_t q) {
+                if (swept(c, q) && rank[q] < k) dmax = std::max(dmax, depth[q] + 1);
+            };
+            for (int32_t e = off[p]; e < off[p + 1]; e++) see(idx[e]);
+            for (int32_t f = rcnt[p]; f < rcnt[p + 1]; f++) see(rev[f]);
+            depth[p] = dmax;
+        }
+    }
+    auto skey = [&](int32_t p) -> int64_t {
+        if (serial) return depth[p];
+        return wall_first ? (int64_t)trank(p) * (nc + 1) + c->colour[p] : (int64_t)c->colour[p];
+    };
+    if (!serial)
+        std::stable_sort(c->canon_order.begin(), c->canon_order.end(),
+                         [&](int32_t a, int32_t b) { return skey(a) < skey(b); });
     // internal order: level, then wall < interior < outer, then caller index
     c->perm.resize(n);
     std::iota(c->perm.begin(), c->perm.end(), 0);

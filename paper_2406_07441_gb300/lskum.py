@@ -16,7 +16,7 @@ INTERIOR, WALL, OUTER = 0, 1, 2
 JVP_EXACT, JVP_INCREMENT = 0, 1
 SCHEME_LUSGS, SCHEME_EXPLICIT = 0, 1
 LUSGS_ANANDH, LUSGS_MANISH = 0, 1
-ORDER_COLOUR, ORDER_WALL_FIRST = 0, 1
+ORDER_COLOUR, ORDER_WALL_FIRST, ORDER_SERIAL = 0, 1, 2
 FARFIELD_FREESTREAM, FARFIELD_KINETIC = 0, 1
 FIELD_U, FIELD_Q, FIELD_QX, FIELD_QY, FIELD_R, FIELD_D, FIELD_DUS, FIELD_DU = range(8)
 OK, ERR_ARG, ERR_STENCIL, ERR_NONPOSITIVE, ERR_DIVERGED, ERR_CUDA, ERR_TIMEOUT, ERR_OOM = 0, -1, -2, -3, -4, -5, -6, -7

@@ -447,3 +447,29 @@ def test_packed_sweeps_wall_first_and_manish():
     assert nrel(s.field(lk.FIELD_DUS), r["dUs"]) < 1e-10 and nrel(s.field(lk.FIELD_DU), r["dU"]) < 1e-10
     h = s.residuals()
     assert np.max(np.abs(h - r["hist"]) / r["hist"]) < 1e-10
+
+
+@pytest.mark.parametrize("name", ["ogrid40x16", "box9"])
+def test_serial_order_matches_oracle(name):
+    """The serial sweeps of Alg. 2 (wall, interior, outer points in index
+    order), run level by level over their dependency graph: the same order as
+    the oracle's sequential sweeps, one iteration's increments and a
+    20-iteration history."""
+    lk = _lskum()
+    c = cached_cloud(name, CLOUDS[name])
+    o = O.Oracle(c, ordering=2)
+    s = lk.Solver(c, 0.63, 2.0, inner_iters=2, first_order_iters=3, ordering=lk.ORDER_SERIAL)
+    col, order, nc = s.order()
+    assert np.array_equal(order, o.order)
+    U0 = o.initial_state(0.63, 2.0)
+    r = o.run(U0, 1, cfl=100.0, K=2, first_order=3)
+    assert s.run(1) == 1
+    assert nrel(s.field(lk.FIELD_DUS), r["dUs"]) < 1e-10
+    assert nrel(s.field(lk.FIELD_DU), r["dU"]) < 1e-10
+    assert nrel(s.field(lk.FIELD_U), r["U"]) < 1e-12
+    s.set_launch_shape(2, 32)
+    r2 = o.run(r["U"], 19, cfl=100.0, K=2, first_order=3, n0=1, hist0=r["hist0"])
+    assert r2["status"] == 0 and s.run(19) == 19
+    h = s.residuals()
+    ref = np.concatenate([r["hist"], r2["hist"]])
+    assert np.max(np.abs(h - ref) / ref) < 1e-10

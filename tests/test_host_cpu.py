@@ -191,3 +191,39 @@ def test_normals_may_be_computed_from_the_polygons(lk):
     with pytest.raises(lk.LskumError) as ei:
         lk.validate([cg.Cloud(b.x, b.y, two, None, None, b.nbr_off, b.nbr_idx, {})], [(0.5, 0.0)])
     assert ei.value.status == -1 and "polygon" in str(ei.value)
+
+
+def _serial_depth(c, kinetic=False):
+    """Dependency levels of the serial order (Alg. 2) computed here: wall,
+    interior, outer points in index order; a point's level is one more than
+    the highest level among its earlier neighbours (either direction)."""
+    swept = (c.flag != cg.OUTER) | kinetic
+    group = np.where(c.flag == cg.WALL, 0, np.where(c.flag == cg.INTERIOR, 1, 2))
+    order = np.argsort(group, kind="stable")
+    rank = np.empty(c.n, int)
+    rank[order] = np.arange(c.n)
+    nbrs = [set() for _ in range(c.n)]
+    for p in range(c.n):
+        for q in c.nbr_idx[c.nbr_off[p]:c.nbr_off[p + 1]]:
+            nbrs[p].add(int(q))
+            nbrs[int(q)].add(p)
+    depth = np.zeros(c.n, int)
+    for p in order:
+        if swept[p]:
+            earlier = [depth[q] + 1 for q in nbrs[p] if swept[q] and rank[q] < rank[p]]
+            depth[p] = max(earlier, default=0)
+    return depth[swept]
+
+
+@pytest.mark.parametrize("kinetic", [False, True])
+def test_serial_order_levels(lk, kinetic):
+    """The serial order (Alg. 2) runs by levels of its dependency graph: the
+    level count equals the longest dependency chain computed independently
+    here, and the layout invariants hold (checked by lskum_validate)."""
+    kw = dict(ordering=lk.ORDER_SERIAL)
+    if kinetic:
+        kw["farfield"] = lk.FARFIELD_KINETIC
+    for c in (cg.cartesian_box(7, 7, seed=2, wall_bottom=True, kinetic_outer=True),
+              cg.naca0012_block(40, 16, kinetic_outer=True), cg.naca0012_jittered(48, 20, seed=11, kinetic_outer=True)):
+        nc, nl = lk.validate([c], [(0.63, 2.0)], **kw)
+        assert nl == _serial_depth(c, kinetic).max() + 1

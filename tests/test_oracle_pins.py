@@ -392,16 +392,20 @@ def _dense_lusgs(c, o, U, R, D, kinetic=False):
     return out_s, out
 
 
-@pytest.mark.parametrize("wall,ordering", [(False, 0), (True, 0), (True, 1)])
+@pytest.mark.parametrize("wall,ordering", [(False, 0), (True, 0), (True, 1), (True, 2)])
 def test_sweeps_equal_dense_lusgs(wall, ordering):
-    """Sequential sweeps in the order of Alg. 6 (colours) or of Alg. 4 (wall
-    points first) equal the dense solve with L and U split by that order."""
+    """Sequential sweeps in the order of Alg. 6 (colours), of Alg. 4 (wall
+    points first, by colour) or of Alg. 2 (wall, interior, outer points in
+    index order) equal the dense solve with L and U split by that order."""
     c = cg.cartesian_box(7, 7, seed=21, wall_bottom=wall)
     assert c.n == 49
     o = O.Oracle(c, ordering=ordering)
-    if ordering == 1:  # wall points lead the order, each group by colour
+    if ordering >= 1:  # wall points lead the order, then interior, then outer
         f = c.flag[o.order]
         assert np.all(np.diff(np.where(f == cg.WALL, 0, np.where(f == cg.INTERIOR, 1, 2))) >= 0)
+    if ordering == 2:  # each group in index order
+        for g in (cg.WALL, cg.INTERIOR, cg.OUTER):
+            assert np.all(np.diff(o.order[c.flag[o.order] == g]) > 0)
     rho, u, v, p = _smooth_state(c.x * 3, c.y * 3, amp=0.08)
     U = np.stack([rho, rho * u, rho * v, p / 0.4 + 0.5 * rho * (u * u + v * v)], 1)
     if wall:
