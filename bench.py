@@ -48,18 +48,18 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # FP64 flops (DFMA = 2) the residual kernel executes per neighbour slot that
 # joins a split sub-stencil, counted by ncu on this workload
 # (2 x smsp__sass_thread_inst_executed_op_dfma_pred_on + dmul + dadd, one
-# launch: 1.0655e9, divided by the 2,926,611 such slots); see profiles/.
-RES_FLOPS_PER_SLOT = 364.07
+# launch: 1.0421e9, divided by the 2,926,611 such slots); see profiles/.
+RES_FLOPS_PER_SLOT = 356.07
 START = 50  # first-order start-up iterations before warm-up and timing
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one residual
 # launch on this workload at 2 threads per point, from one ncu capture of the
 # current kernel (profiles/k_residual_naca0012_640x256_jit.md); reported only
 # when the bench runs that launch shape.
-RES_TRAFFIC = {2: 164.982528e6}
+RES_TRAFFIC = {2: 164.885504e6}
 # sm__pipe_fp64_cycles_active of that launch (fraction of peak sustained): the
 # residual's binding unit; the counted-flop fraction is lower because
 # additions, multiplications and comparisons occupy the pipe like an FMA
-RES_FP64_PIPE_ACTIVE = 0.891
+RES_FP64_PIPE_ACTIVE = 0.894
 
 
 def _env_int(k, d):

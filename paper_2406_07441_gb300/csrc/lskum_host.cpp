@@ -224,6 +224,9 @@ struct HostPrep {
     std::vector<int32_t> pk_pt[2], pk_nbr[2];
     std::vector<uint8_t> pk_mb[2], pk_steps[2];
     std::vector<double> pk_w1[2], pk_w2[2];
+    // the points of each warp (internal index, in lane order of their first
+    // slots), warp w's at pk_hk[pk_wp[w]] .. pk_hk[pk_wp[w + 1] - 1]
+    std::vector<int32_t> pk_wp[2], pk_hk[2];
 };
 static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &hp);
 
@@ -422,6 +425,20 @@ static lskum_status verify_layout(lskum_ctx *c, const lskum_cloud *cl, const Hos
             }
             for (int32_t pos = c->lvl_beg[l]; pos < c->lvl_act_end[l]; pos++)
                 if (seen_pos[pos] != 1) return fail(c, LSKUM_ERR_ARG, "layout: position %d not packed", pos);
+        }
+        // each warp's point list: exactly its points, in lane order
+        const std::vector<int32_t> &wp = hp.pk_wp[dir], &hk = hp.pk_hk[dir];
+        if ((int64_t)wp.size() != (int64_t)lw.back() + 1 || wp[0] != 0 || (size_t)wp.back() != hk.size())
+            return fail(c, LSKUM_ERR_ARG, "layout: packed point lists size");
+        for (int64_t w = 0; w < lw.back(); w++) {
+            int32_t j = wp[w];
+            for (int64_t t = w * 32; t < w * 32 + 32; t++) {
+                if (pt[t] < 0 || (t % 32 != 0 && pt[t - 1] == pt[t])) continue;  // not a first slot
+                if (j >= wp[w + 1] || hk[j] != so[pt[t]] || hk[j] < 0 || hk[j] >= n)
+                    return fail(c, LSKUM_ERR_ARG, "layout: point list of warp %lld", (long long)w);
+                j++;
+            }
+            if (j != wp[w + 1]) return fail(c, LSKUM_ERR_ARG, "layout: point list of warp %lld", (long long)w);
         }
     }
     return LSKUM_OK;
@@ -766,8 +783,8 @@ static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &
             const int64_t e = off[p] + j, t = base + 32 * j;
             enb[t] = c->inv[idx[e]];
             emb[t] = smb[e];
-            edx[t] = sdx[e];
-            edy[t] = sdy[e];
+            edx[t] = 0.5 * sdx[e];  // half offsets (exact): the residual's reconstruction
+            edy[t] = 0.5 * sdy[e];  // steps q - (dx, dy)/2 . grad q
             ew1[t] = sw1[e];
             ew2[t] = sw2[e];
             egx[t] = swgx[e];
@@ -814,7 +831,10 @@ static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &
     }
     // packed sweep form: per level, its points' slots packed into warps of 32
     // lanes by best fit (longest lists first; a point with an empty list
-    // takes one slot with membership 0); a point never straddles two warps
+    // takes one slot with membership 0); a point never straddles two warps.
+    // Points in a (t, n) frame (wall points, and outer points under the
+    // kinetic far field) are packed into warps of their own: their products
+    // are evaluated per slot, the other points' are gathered.
     c->pk_ok = true;
     for (int32_t k = 0; k < n; k++)
         if (hp.lo_off[k + 1] - hp.lo_off[k] > 32 || hp.up_off[k + 1] - hp.up_off[k] > 32) c->pk_ok = false;
@@ -826,29 +846,36 @@ static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &
         const std::vector<double> &lw1 = dir == 0 ? hp.lo_w1 : hp.up_w1, &lw2 = dir == 0 ? hp.lo_w2 : hp.up_w2;
         std::vector<int32_t> &lw = c->pk_lw[dir];
         lw.assign(1, 0);
+        hp.pk_wp[dir].assign(1, 0);
         int32_t nw = 0;
         for (int32_t l = 0; l < c->n_levels; l++) {
-            // best fit: warps by free lanes (bucket r holds warps with r free)
-            std::vector<std::vector<int32_t>> bucket(33);
+            // best fit: warps by free lanes (bucket r holds warps with r free),
+            // framed points first, in warps of their own
             std::vector<std::vector<int32_t>> members;  // positions per warp of this level
-            for (int32_t pos = c->lvl_beg[l]; pos < c->lvl_act_end[l]; pos++) {
-                const int32_t k = so[pos];
-                const int32_t len = std::max(1, loff[k + 1] - loff[k]);
-                int32_t w = -1;
-                for (int32_t r = len; r <= 32 && w < 0; r++)
-                    if (!bucket[r].empty()) {
-                        w = bucket[r].back();
-                        bucket[r].pop_back();
-                        bucket[r - len].push_back(w);
+            for (int pass = 0; pass < 2; pass++) {
+                std::vector<std::vector<int32_t>> bucket(33);
+                for (int32_t pos = c->lvl_beg[l]; pos < c->lvl_act_end[l]; pos++) {
+                    const int32_t k = so[pos];
+                    if ((c->flag[c->perm[k]] != LSKUM_INTERIOR) != (pass == 0)) continue;
+                    const int32_t len = std::max(1, loff[k + 1] - loff[k]);
+                    int32_t w = -1;
+                    for (int32_t r = len; r <= 32 && w < 0; r++)
+                        if (!bucket[r].empty()) {
+                            w = bucket[r].back();
+                            bucket[r].pop_back();
+                            bucket[r - len].push_back(w);
+                        }
+                    if (w < 0) {
+                        w = (int32_t)members.size();
+                        members.emplace_back();
+                        bucket[32 - len].push_back(w);
                     }
-                if (w < 0) {
-                    w = (int32_t)members.size();
-                    members.emplace_back();
-                    bucket[32 - len].push_back(w);
+                    members[w].push_back(pos);
                 }
-                members[w].push_back(pos);
             }
             for (const auto &mw : members) {
+                for (int32_t pos : mw) hp.pk_hk[dir].push_back(so[pos]);
+                hp.pk_wp[dir].push_back((int32_t)hp.pk_hk[dir].size());
                 int32_t lane = 0, longest = 1;
                 for (int32_t pos : mw) longest = std::max(longest, loff[so[pos] + 1] - loff[so[pos]]);
                 uint8_t steps = 0;
@@ -984,8 +1011,11 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
         d.pk_mb[dir] = d.pk_steps[dir] = nullptr;
         d.pk_w1[dir] = d.pk_w2[dir] = nullptr;
         d.pk_w1f[dir] = d.pk_w2f[dir] = nullptr;
+        d.pk_wp[dir] = d.pk_hk[dir] = nullptr;
         if (!c->pk_ok || hp.pk_pt[dir].empty()) continue;
         const size_t m = hp.pk_pt[dir].size();
+        d.pk_wp[dir] = A.alloc<int32_t>(hp.pk_wp[dir].size());
+        d.pk_hk[dir] = A.alloc<int32_t>(std::max<size_t>(hp.pk_hk[dir].size(), 1));
         d.pk_pt[dir] = A.alloc<int32_t>(m);
         d.pk_nbr[dir] = A.alloc<int32_t>(m);
         d.pk_mb[dir] = A.alloc<uint8_t>(m);
@@ -998,6 +1028,13 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
             d.pk_w1f[dir] = A.alloc<float>(m);
             d.pk_w2f[dir] = A.alloc<float>(m);
         }
+    }
+    // per-point axis Jacobian products of the packed form (x+, x-, y+, y-)
+    d.jc = nullptr;
+    d.jcf = nullptr;
+    if (c->pk_ok) {
+        if (mixed) d.jcf = A.alloc<float>(16 * (size_t)ld);
+        else d.jc = A.alloc<double>(16 * (size_t)ld);
     }
     c->launch.pk_lw[0] = c->pk_ok ? c->pk_lw[0].data() : nullptr;
     c->launch.pk_lw[1] = c->pk_ok ? c->pk_lw[1].data() : nullptr;
@@ -1039,8 +1076,8 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
     d.deg = ddeg;
     d.nbr = dnb;
     d.memb = dmb;
-    d.ndx = ddx;
-    d.ndy = ddy;
+    d.nhx = ddx;
+    d.nhy = ddy;
     d.w1 = dw1;
     d.w2 = dw2;
     d.wgx = dgx;
@@ -1138,11 +1175,16 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
         up((void *)d.pk_steps[dir], hp.pk_steps[dir].data(), hp.pk_steps[dir].size());
         up((void *)d.pk_w1[dir], hp.pk_w1[dir].data(), m * sizeof(double));
         up((void *)d.pk_w2[dir], hp.pk_w2[dir].data(), m * sizeof(double));
+        up((void *)d.pk_wp[dir], hp.pk_wp[dir].data(), hp.pk_wp[dir].size() * sizeof(int32_t));
+        if (!hp.pk_hk[dir].empty())
+            up((void *)d.pk_hk[dir], hp.pk_hk[dir].data(), hp.pk_hk[dir].size() * sizeof(int32_t));
         if (d.pk_w1f[dir]) {
             up((void *)d.pk_w1f[dir], pkf[dir][0].data(), m * sizeof(float));
             up((void *)d.pk_w2f[dir], pkf[dir][1].data(), m * sizeof(float));
         }
     }
+    if (e == cudaSuccess && d.jc) e = cudaMemset(d.jc, 0, 16 * (size_t)ld * sizeof(double));
+    if (e == cudaSuccess && d.jcf) e = cudaMemset(d.jcf, 0, 16 * (size_t)ld * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(c->case_state, 0, c->n_cases * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemset(c->case_it, 0, c->n_cases * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemset(c->case_hist0, 0, c->n_cases * sizeof(double));

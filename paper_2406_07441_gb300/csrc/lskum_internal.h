@@ -68,6 +68,7 @@ enum PrimField {
     P_RHO, P_IRHO, P_U, P_V, P_P, P_BETA, P_SB, P_ISB, P_I2P, P_Q2, P_E1, P_E2,
     P_BSX, P_APX, P_AMX, P_EKX, P_BX,  // direction (1,0): 2 B S, A+, A-, exp(-S^2)/sqrt(pi), B
     P_BSY, P_APY, P_AMY, P_EKY, P_BY,  // direction (0,1)
+    P_UE1, P_VE1,                      // u e1, v e1
     P_NFIELDS
 };
 constexpr int kPrimStride = 24;
@@ -91,7 +92,7 @@ struct Dev {
     const int32_t *deg;       // [n]
     const int32_t *nbr;       // neighbour (internal index)
     const uint8_t *memb;      // bits 0/1: e1 sub-stencil +/-, bits 2/3: e2 sub-stencil +/-
-    const double *ndx, *ndy;  // x_i - x_0, y_i - y_0
+    const double *nhx, *nhy;  // (x_i - x_0)/2, (y_i - y_0)/2
     const double *w1, *w2;    // LS weight of the slot in its e1 / e2 split sub-stencil (0 if none)
     const double *wgx, *wgy;  // full-stencil LS weights of d/dx and d/dy (Eq. 10, 16)
     const double *gxx, *gxy, *gyx, *gyy;  // wgx dx, wgx dy, wgy dx, wgy dy (inner iterations)
@@ -128,6 +129,15 @@ struct Dev {
     const uint8_t *pk_steps[2];  // per warp: steps of its segmented sum, ceil(log2(longest list))
     const double *pk_w1[2], *pk_w2[2];
     const float *pk_w1f[2], *pk_w2f[2];
+    // the points of warp w (internal index, lane order of their first slots):
+    // pk_hk[pk_wp[w]] .. pk_hk[pk_wp[w + 1] - 1]
+    const int32_t *pk_wp[2], *pk_hk[2];
+    // packed form: per point, the axis split-flux Jacobian products of its
+    // latest increment, [ld][4 products: x+, x-, y+, y-][4]: written by the
+    // point's own level, gathered by the later levels' interior points
+    // (FP64, or FP32 for the mixed-precision sweeps; the other is null)
+    double *jc;
+    float *jcf;
     // per-case residual norm: stage 1 sums R_rho^2 over blocks of up to 256
     // points of one case (caller order), stage 2 adds each case's blocks
     double *blk;             // [n_blk][4] partial sums of the four components

@@ -79,6 +79,28 @@ __device__ __forceinline__ float signed_by(float x, bool pos)
     return __int_as_float(__float_as_int(x) ^ (pos ? 0 : (int)0x80000000));
 }
 
+// x / 2 and 2 x as a step of the exponent field on the integer pipe: the same
+// bits as the FP64 multiplication whenever both x and the result are normal
+// (a multiplication by a power of two is exact there).  Zeros and
+// non-finite values come back unchanged, which is again the exact result;
+// only magnitudes below 2^-1021 (halving) or above 2^1023 (doubling) would
+// differ, far outside what any quantity of the solver reaches.  FP32 keeps
+// its multiplication (its pipe is not the bottleneck).
+__device__ __forceinline__ double half_of(double x)
+{
+    const int hi = __double2hiint(x);
+    const unsigned ex = ((unsigned)hi >> 20) & 0x7ffu;
+    return __hiloint2double(ex - 2u < 0x7fdu ? hi - 0x00100000 : hi, __double2loint(x));
+}
+__device__ __forceinline__ double twice(double x)
+{
+    const int hi = __double2hiint(x);
+    const unsigned ex = ((unsigned)hi >> 20) & 0x7ffu;
+    return __hiloint2double(ex - 1u < 0x7fdu ? hi + 0x00100000 : hi, __double2loint(x));
+}
+__device__ __forceinline__ float half_of(float x) { return 0.5f * x; }
+__device__ __forceinline__ float twice(float x) { return 2.0f * x; }
+
 // Primitive state carried through the residual.
 struct Prim {
     double rho, u, v, p, sb, isb, e1, e2;  // sb = sqrt(beta), isb = 1/sb,
@@ -92,18 +114,18 @@ struct Prim {
 __device__ __forceinline__ Prim q_to_prim(const MathTables &T, const double q[4])
 {
     Prim P;
-    const double beta = -0.5 * q[3];
+    const double beta = signed_by(half_of(q[3]), false);  // -q4/2, the sign by XOR
     P.isb = rsqrt(beta);
     const double ib = P.isb * P.isb;   // 1/beta
     const double r = ib * ib * P.isb;  // beta^(-5/2)
-    const double i2b = 0.5 * ib;       // 1/(2 beta)
+    const double i2b = half_of(ib);    // 1/(2 beta)
     P.sb = beta * P.isb;
     P.u = q[1] * i2b;
     P.v = q[2] * i2b;
     const double q2 = P.u * P.u + P.v * P.v;
     P.rho = exp_t(T, fma(beta, q2, q[0])) * r;
     P.p = P.rho * i2b;
-    const double k = 0.5 * P.rho * q2;
+    const double k = half_of(P.rho * q2);
     P.e1 = fma(3.5, P.p, k);
     P.e2 = fma(3.0, P.p, k);
     P.bk = kInv2SqrtPi * P.isb;
@@ -206,11 +228,11 @@ __device__ __forceinline__ JvpBase<T> jvp_base(const PrimT<T> &P, const T dl[4])
     b.drho = dl[0];
     b.du = (dl[1] - P.u * b.drho) * P.irho;
     b.dv = (dl[2] - P.v * b.drho) * P.irho;
-    const T dq2 = T(2.0) * (P.u * b.du + P.v * b.dv);
-    b.dk = T(0.5) * (b.drho * P.q2 + P.rho * dq2);  // d(rho |u|^2 / 2)
+    const T dq2 = twice(P.u * b.du + P.v * b.dv);
+    b.dk = half_of(b.drho * P.q2 + P.rho * dq2);  // d(rho |u|^2 / 2)
     b.dp = T(kGm1) * (dl[3] - b.dk);
-    const T dbeta = (b.drho - T(2.0) * P.beta * b.dp) * P.i2p;
-    b.dsb = T(0.5) * dbeta * P.isb;
+    const T dbeta = (b.drho - twice(P.beta) * b.dp) * P.i2p;
+    b.dsb = half_of(dbeta) * P.isb;
     b.dsbi = b.dsb * P.isb;
     b.de1 = T(3.5) * b.dp + b.dk;
     b.de2 = T(3.0) * b.dp + b.dk;
@@ -241,12 +263,12 @@ __device__ __forceinline__ void jvp_dir(const PrimT<T> &P, const JvpBase<T> &b, 
 }
 
 // The same product along an axis (DIR 0: d = (1,0), DIR 1: (0,1)) from the
-// point's record: A, exp(-S^2)/sqrt(pi) (ek), B and 2 B S precomputed per
-// point, the direction-free tangents in the base, signs applied by
+// point's record: A, exp(-S^2)/sqrt(pi) (ek), B, 2 B S and u_d e1 precomputed
+// per point, the direction-free tangents in the base, signs applied by
 // negation (no multiplication by 0, 1 or +-1 is left to the FP64 pipe).
 template <int DIR, typename T>
 __device__ __forceinline__ void jvp_axis(const PrimT<T> &P, const JvpBase<T> &b, bool pos, T A, T ek, T B, T B2S,
-                                         T out[4])
+                                         T ude1, T out[4])
 {
     const T ud = DIR == 0 ? P.u : P.v;
     const T dud = DIR == 0 ? b.du : b.dv;
@@ -269,7 +291,7 @@ __device__ __forceinline__ void jvp_axis(const PrimT<T> &P, const JvpBase<T> &b,
     }
     const T t1 = fma(dud, P.e1, ud * b.de1);
     const T t3 = fma(b.de2, sB, P.e2 * sdB);
-    out[3] = fma(t1, A, fma(ud * P.e1, dA, t3));
+    out[3] = fma(t1, A, fma(ude1, dA, t3));  // ude1 = u_d e1, from the record
 }
 
 // Unsplit Euler-flux Jacobian product A_d(U) dU in direction d = (dx, dy)
@@ -401,16 +423,25 @@ __global__ void __launch_bounds__(256) k_grad(Dev d, const double *__restrict__ 
 // ---------------------------------------------------------------------------
 // flux residual, time step, diagonal, norm partials
 // ---------------------------------------------------------------------------
-// R += w dG with Kahan's compensated summation (W. Kahan, "Further remarks on
-// reducing truncation errors", CACM 8(1), 1965): c carries the negated
-// rounding error of the running sum into the next term; the product is folded
-// into that correction by one FMA.  The final sum is R - c.
-__device__ __forceinline__ void comp_add(double &R, double &c, double w, double dG)
+// R += w1 dG1 + w2 dG2 (a slot's two split sub-stencils; a weight and its
+// difference are 0 where the slot is in one only) with Kahan's compensated
+// summation (W. Kahan, "Further remarks on reducing truncation errors", CACM
+// 8(1), 1965): c carries the negated rounding error of the running sum into
+// the next term; the products are folded into that correction by two FMAs,
+// so one compensated addition serves both sub-stencils.  The final sum is
+// R - c.
+__device__ __forceinline__ void comp_add2(double &R, double &c, double w1, double dG1, double w2, double dG2)
 {
-    const double y = fma(w, dG, -c);  // the term w dG less the carried error, rounded once
+    const double y = fma(w1, dG1, fma(w2, dG2, -c));  // the slot's term less the carried error
     const double t = R + y;
     c = (t - R) - y;  // what the addition lost (negated)
     R = t;
+}
+
+// The sign of x with magnitude 0 (what 0 * x gives), on the integer pipe.
+__device__ __forceinline__ double zero_like(double x)
+{
+    return __hiloint2double(__double2hiint(x) & (int)0x80000000, 0);
 }
 
 template <int TPP, bool COMP>
@@ -422,7 +453,7 @@ __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const doub
     __syncthreads();
     const int n1 = ((const volatile Ctrl *)d.ctrl)->it;  // this iteration, counted by k_begin
     const double cfl = (d.ramp > 0.0 && (double)n1 < d.ramp) ? d.cfl * ((double)n1 / d.ramp) : d.cfl;
-    const double hc = n1 <= d.first_order ? 0.0 : 0.5;  // first-order start: q~ = q
+    const bool second = n1 > d.first_order;  // first-order start: q~ = q
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     const int k = gt / TPP, sub = gt % TPP;
     const bool active = k < d.n;
@@ -451,12 +482,12 @@ __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const doub
             const int mb = d.memb[e];
             if (!mb) continue;
             const int i = d.nbr[e];
-            const double dx = d.ndx[e], dy = d.ndy[e];
+            const double hx = d.nhx[e], hy = d.nhy[e];  // half offsets
             double qi[4], q0t[4];
             const double2 *gr = reinterpret_cast<const double2 *>(g + 8 * (size_t)i);
             const double2 x01 = gr[0], x23 = gr[1], y01 = gr[2], y23 = gr[3];
             const double gxi[4] = {x01.x, x01.y, x23.x, x23.y}, gyi[4] = {y01.x, y01.y, y23.x, y23.y};
-            const double hdx = hc * dx, hdy = hc * dy;  // exact: hc is 0 or 1/2
+            const double hdx = second ? hx : zero_like(hx), hdy = second ? hy : zero_like(hy);
 #pragma unroll
             for (int c = 0; c < 4; c++) {
                 qi[c] = fma(-hdx, gxi[c], fma(-hdy, gyi[c], q[c * ld + i]));
@@ -464,6 +495,7 @@ __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const doub
             }
             const Prim Pi = q_to_prim(T, qi);
             const Prim P0 = q_to_prim(T, q0t);
+            double w1 = 0.0, dG1[4] = {0.0, 0.0, 0.0, 0.0};  // (COMP) the first sub-stencil's term
             if (mb & 3) {
                 const bool pos = mb & 1;
                 const double w = d.w1[e];
@@ -477,10 +509,12 @@ __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const doub
                 }
 #pragma unroll
                 for (int c = 0; c < 4; c++) {
-                    if (COMP) comp_add(R[c], Rc[c], w, Gi[c] - G0[c]);
+                    if (COMP) dG1[c] = Gi[c] - G0[c];
                     else R[c] = fma(w, Gi[c] - G0[c], R[c]);
                 }
+                w1 = w;
             }
+            double w2 = 0.0, dG2[4] = {0.0, 0.0, 0.0, 0.0};
             if (mb & 12) {
                 const bool pos = mb & 4;
                 const double w = d.w2[e];
@@ -494,9 +528,14 @@ __global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const doub
                 }
 #pragma unroll
                 for (int c = 0; c < 4; c++) {
-                    if (COMP) comp_add(R[c], Rc[c], w, Gi[c] - G0[c]);
+                    if (COMP) dG2[c] = Gi[c] - G0[c];
                     else R[c] = fma(w, Gi[c] - G0[c], R[c]);
                 }
+                w2 = w;
+            }
+            if (COMP) {
+#pragma unroll
+                for (int c = 0; c < 4; c++) comp_add2(R[c], Rc[c], w1, dG1[c], w2, dG2[c]);
             }
         }
     }
@@ -676,6 +715,7 @@ template <typename T>
 struct SweepBufs {
     T *dUs, *dU;
     const T *lo_w1, *lo_w2, *up_w1, *up_w2, *prim;
+    T *jc;  // packed form's per-point axis products
 };
 
 template <typename T>
@@ -684,13 +724,13 @@ __device__ __forceinline__ SweepBufs<T> sweep_bufs(const Dev &d, const StateSet 
 template <>
 __device__ __forceinline__ SweepBufs<double> sweep_bufs<double>(const Dev &d, const StateSet &st)
 {
-    return {d.dUs, d.dU, d.lo_w1, d.lo_w2, d.up_w1, d.up_w2, st.prim};
+    return {d.dUs, d.dU, d.lo_w1, d.lo_w2, d.up_w1, d.up_w2, st.prim, d.jc};
 }
 
 template <>
 __device__ __forceinline__ SweepBufs<float> sweep_bufs<float>(const Dev &d, const StateSet &st)
 {
-    return {d.dUsf, d.dUf, d.lo_w1f, d.lo_w2f, d.up_w1f, d.up_w2f, st.primf};
+    return {d.dUsf, d.dUf, d.lo_w1f, d.lo_w2f, d.up_w1f, d.up_w2f, st.primf, d.jcf};
 }
 
 // One slot of a point's lower / upper list: acc += w_s J_s(U_i) dW_i over the
@@ -705,8 +745,8 @@ __device__ __forceinline__ void sweep_slot(const Dev &d, const StateSet &st, con
 #pragma unroll
     for (int c = 0; c < 4; c++) dl[c] = dW[4 * i + c];
     if (JVP == 0 && !framed) {
-        // interior frame: d = (1,0) or (0,1); A+-, exp(-S^2)/sqrt(pi), B and
-        // 2 B S precomputed per point
+        // interior frame: d = (1,0) or (0,1); A+-, exp(-S^2)/sqrt(pi), B,
+        // 2 B S and u_d e1 precomputed per point
         const PrimT<T> P = load_prim(pr, i);
         const T *rec = pr + (size_t)i * kPrimStride;
         const JvpBase<T> jb = jvp_base(P, dl);
@@ -717,9 +757,11 @@ __device__ __forceinline__ void sweep_slot(const Dev &d, const StateSet &st, con
             const bool pos = m & 1;
             T J[4];
             if (s == 0)
-                jvp_axis<0, T>(P, jb, pos, rec[pos ? P_APX : P_AMX], rec[P_EKX], rec[P_BX], rec[P_BSX], J);
+                jvp_axis<0, T>(P, jb, pos, rec[pos ? P_APX : P_AMX], rec[P_EKX], rec[P_BX], rec[P_BSX], rec[P_UE1],
+                               J);
             else
-                jvp_axis<1, T>(P, jb, pos, rec[pos ? P_APY : P_AMY], rec[P_EKY], rec[P_BY], rec[P_BSY], J);
+                jvp_axis<1, T>(P, jb, pos, rec[pos ? P_APY : P_AMY], rec[P_EKY], rec[P_BY], rec[P_BSY], rec[P_VE1],
+                               J);
             const T w = s == 0 ? w1 : w2;
 #pragma unroll
             for (int c = 0; c < 4; c++) acc[c] = fma(w, J[c], acc[c]);
@@ -864,55 +906,149 @@ __global__ void __launch_bounds__(256) k_sweep(Dev d, StateSet st, int lb, int l
     if (live && sub == 0) sweep_point<FWD, T>(d, st, sb, k, wall, e1x, e1y, e2x, e2y, acc);
 }
 
+// Four consecutive values from 16-byte-aligned storage (one point's product).
+__device__ __forceinline__ void load4(const double *__restrict__ p, double v[4])
+{
+    const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+    v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+}
+__device__ __forceinline__ void load4(const float *__restrict__ p, float v[4])
+{
+    const float4 a = *reinterpret_cast<const float4 *>(p);
+    v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
+}
+
+// Axis product cb (0: x+, 1: x-, 2: y+, 3: y-) of point k's new increment
+// (in inc), the value every interior point whose list holds k would form
+// for that sub-stencil (the same function, arguments and precision), stored
+// for the later levels.
+template <int JVP, typename T>
+__device__ __forceinline__ void store_axis_product(const Dev &d, const StateSet &st, const MathTables &Tb,
+                                                   const SweepBufs<T> &sb, const T *inc, int k, int cb)
+{
+    const bool pos = !(cb & 1);
+    T dl[4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) dl[c] = __ldcg(inc + 4 * k + c);  // written by this block
+    T J[4];
+    if (JVP == 0) {
+        const PrimT<T> P = load_prim(sb.prim, k);
+        const T *rec = sb.prim + (size_t)k * kPrimStride;
+        const JvpBase<T> jb = jvp_base(P, dl);
+        if (cb < 2)
+            jvp_axis<0, T>(P, jb, pos, rec[pos ? P_APX : P_AMX], rec[P_EKX], rec[P_BX], rec[P_BSX], rec[P_UE1], J);
+        else
+            jvp_axis<1, T>(P, jb, pos, rec[pos ? P_APY : P_AMY], rec[P_EKY], rec[P_BY], rec[P_BSY], rec[P_VE1], J);
+    } else {  // increment form, in FP64
+        const int ld = d.ld;
+        double Ui[4], Up[4], G1[4], G0[4];
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            Ui[c] = st.U[c * ld + k];
+            Up[c] = Ui[c] + (double)dl[c];
+        }
+        const double ddx = cb < 2 ? 1.0 : 0.0, ddy = cb < 2 ? 0.0 : 1.0;
+        flux_cons(Tb, Up, ddx, ddy, pos, G1);
+        flux_cons(Tb, Ui, ddx, ddy, pos, G0);
+#pragma unroll
+        for (int c = 0; c < 4; c++) J[c] = (T)(G1[c] - G0[c]);
+    }
+    T *out = sb.jc + 16 * (size_t)k + 4 * cb;
+#pragma unroll
+    for (int c = 0; c < 4; c++) out[c] = J[c];
+}
+
 // Packed form: one lane per list slot.  At create the level's points (in
 // sweep order) are packed whole into warps of up to 32 slots (a point with
 // an empty list takes one idle slot), so lanes are not left idle by lists
 // shorter than a lane group; a segmented suffix sum over the lanes of each
 // point (fixed tree order, no atomics) leaves the point's sum in its first
 // lane, which finishes the point.  Warps [wb, we) are the level's.
+// A neighbour's Jacobian product along an axis depends only on the
+// neighbour, the axis and the sub-stencil's sign, so each block ends by
+// forming the four axis products of its points' new increments, once per
+// point; interior points gather them (8 FMAs per slot instead of ~70 FP64
+// instructions), in the order the per-slot form adds them, so the sums are
+// the same bits.  Points in a (t, n) frame form their products per slot.
 template <int JVP, bool FWD, typename T>
 __global__ void __launch_bounds__(256) k_sweep_packed(Dev d, StateSet st, int wb, int we)
 {
     const MathTables &Tb = g_math;  // wall and outer points only: no per-block copy
-    if (halted(d.ctrl)) return;
+    __shared__ int halt;
+    if (threadIdx.x == 0) halt = halted(d.ctrl);
+    __syncthreads();
+    if (halt) return;  // the whole block: every thread reaches the barrier below
     const int gw = wb + (blockIdx.x * blockDim.x + threadIdx.x) / 32;
-    if (gw >= we) return;  // whole warps only (blocks are whole warps)
-    const int lane = threadIdx.x & 31;
     const int dir = FWD ? 0 : 1;
-    const size_t e = (size_t)gw * 32 + lane;
-    const int pos = d.pk_pt[dir][e];  // sweep position of the slot's point, -1: padding
-    const int k = pos >= 0 ? (FWD ? d.sw_fwd : d.sw_bwd)[pos] : 0;
-    const bool live = pos >= 0 && !frozen(d, k);
     const SweepBufs<T> sb = sweep_bufs<T>(d, st);
-    const T *__restrict__ dW = FWD ? sb.dUs : sb.dU;
-    const int fk = d.flag[k];
-    const bool wall = fk == kWall, framed = fk != kInterior;
-    double e1x, e1y, e2x, e2y;
-    point_frame(d, k, framed, e1x, e1y, e2x, e2y);
-    T acc[4] = {T(0), T(0), T(0), T(0)};
-    const int mb = d.pk_mb[dir][e];
-    if (live && mb) {
-        const T w1 = sizeof(T) == 4 ? (T)d.pk_w1f[dir][e] : (T)d.pk_w1[dir][e];
-        const T w2 = sizeof(T) == 4 ? (T)d.pk_w2f[dir][e] : (T)d.pk_w2[dir][e];
-        sweep_slot<JVP, T>(d, st, Tb, dW, sb.prim, framed, e1x, e1y, e2x, e2y, d.pk_nbr[dir][e], mb, w1, w2, acc);
+    T *const inc = FWD ? sb.dUs : sb.dU;  // this sweep's increments
+    if (gw < we) {  // whole warps (blocks are whole warps)
+        const int lane = threadIdx.x & 31;
+        const size_t e = (size_t)gw * 32 + lane;
+        const int pos = d.pk_pt[dir][e];  // sweep position of the slot's point, -1: padding
+        const int k = pos >= 0 ? (FWD ? d.sw_fwd : d.sw_bwd)[pos] : 0;
+        const bool live = pos >= 0 && !frozen(d, k);
+        const T *__restrict__ dW = inc;  // earlier levels' increments
+        const T *__restrict__ jn = sb.jc;  // earlier levels' products
+        const int fk = d.flag[k];
+        const bool wall = fk == kWall, framed = fk != kInterior;
+        double e1x, e1y, e2x, e2y;
+        point_frame(d, k, framed, e1x, e1y, e2x, e2y);
+        T acc[4] = {T(0), T(0), T(0), T(0)};
+        const int mb = d.pk_mb[dir][e];
+        if (live && mb) {
+            const T w1 = sizeof(T) == 4 ? (T)d.pk_w1f[dir][e] : (T)d.pk_w1[dir][e];
+            const T w2 = sizeof(T) == 4 ? (T)d.pk_w2f[dir][e] : (T)d.pk_w2[dir][e];
+            const int i = d.pk_nbr[dir][e];
+            if (framed) {
+                sweep_slot<JVP, T>(d, st, Tb, dW, sb.prim, framed, e1x, e1y, e2x, e2y, i, mb, w1, w2, acc);
+            } else {
+                T J[4];
+                if (mb & 3) {
+                    load4(jn + 16 * (size_t)i + ((mb & 1) ? 0 : 4), J);
+#pragma unroll
+                    for (int c = 0; c < 4; c++) acc[c] = fma(w1, J[c], acc[c]);
+                }
+                if (mb & 12) {
+                    load4(jn + 16 * (size_t)i + ((mb & 4) ? 8 : 12), J);
+#pragma unroll
+                    for (int c = 0; c < 4; c++) acc[c] = fma(w2, J[c], acc[c]);
+                }
+            }
+        }
+        // segmented suffix sum: lane l adds lane l + o when both hold the same
+        // point; the warp's longest list bounds the steps (warp-uniform)
+        const int steps = d.pk_steps[dir][gw];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            if (o >= (1 << steps)) break;
+            const int p2 = __shfl_down_sync(kFull, pos, o);
+            T v[4];
+#pragma unroll
+            for (int c = 0; c < 4; c++) v[c] = __shfl_down_sync(kFull, acc[c], o);
+            if (lane + o < 32 && p2 == pos) {
+#pragma unroll
+                for (int c = 0; c < 4; c++) acc[c] += v[c];
+            }
+        }
+        const int prev = __shfl_up_sync(kFull, pos, 1);
+        if (live && (lane == 0 || prev != pos)) sweep_point<FWD, T>(d, st, sb, k, wall, e1x, e1y, e2x, e2y, acc);
     }
-    // segmented suffix sum: lane l adds lane l + o when both hold the same
-    // point; the warp's longest list bounds the steps (warp-uniform)
-    const int steps = d.pk_steps[dir][gw];
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        if (o >= (1 << steps)) break;
-        const int p2 = __shfl_down_sync(kFull, pos, o);
-        T v[4];
-#pragma unroll
-        for (int c = 0; c < 4; c++) v[c] = __shfl_down_sync(kFull, acc[c], o);
-        if (lane + o < 32 && p2 == pos) {
-#pragma unroll
-            for (int c = 0; c < 4; c++) acc[c] += v[c];
+    __syncthreads();  // the block's new increments are written
+    // the block's points' axis products, one thread per (point, product):
+    // first every point's x products, then the y products, so that a warp
+    // takes one axis (the sign costs no branch)
+    const int wpb = blockDim.x / 32;
+    const int gw0 = wb + blockIdx.x * wpb, gw1 = min(gw0 + wpb, we);
+    if (gw0 < we) {
+        const int p0 = d.pk_wp[dir][gw0], np = d.pk_wp[dir][gw1] - p0;
+        for (int t = threadIdx.x; t < 4 * np; t += blockDim.x) {
+            const int y = t >= 2 * np;
+            const int r = y ? t - 2 * np : t;
+            const int k = d.pk_hk[dir][p0 + (r >> 1)];
+            if (!frozen(d, k)) store_axis_product<JVP, T>(d, st, Tb, sb, inc, k, 2 * y + (r & 1));
         }
     }
-    const int prev = __shfl_up_sync(kFull, pos, 1);
-    if (live && (lane == 0 || prev != pos)) sweep_point<FWD, T>(d, st, sb, k, wall, e1x, e1y, e2x, e2y, acc);
 }
 
 // ---------------------------------------------------------------------------
@@ -1014,6 +1150,8 @@ __global__ void __launch_bounds__(256) k_update(Dev d, int cur, bool inc, bool p
     pr[P_AMY] = sy >= 0.0 ? Ey : 1.0 - Ey;
     pr[P_EKY] = ey * kInvSqrtPi;
     pr[P_BY] = by;
+    pr[P_UE1] = P.u * P.e1;
+    pr[P_VE1] = P.v * P.e1;
     if (dst.primf) {  // mixed precision: the sweeps' FP32 copy of the record
         float *pf = dst.primf + (size_t)k * kPrimStride;
 #pragma unroll

@@ -147,8 +147,8 @@ def test_training_lowers_the_loss_and_predict_is_judged():
 
 
 def test_predict_on_a_batch_equals_single_contexts_and_judges_per_case():
-    """The prediction of a point depends only on its own inputs and the judge
-    compares each case's own first residuals, so a batch gets, case by case,
+    """The prediction of a point depends only on its own inputs and the
+    residual check compares each case's own first residuals, so a batch gets, case by case,
     exactly the state and the decisions of single contexts; an untrained
     network is rejected and the free stream kept."""
     from paper_2406_07441_gb300 import lskum as lk
