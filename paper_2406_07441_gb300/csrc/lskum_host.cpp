@@ -62,7 +62,8 @@ struct lskum_ctx {
     int32_t n_colours = 0;
     int32_t n_levels = 0;               // sweep levels (colours, or (wall|interior, colour) pairs)
     std::vector<int32_t> lvl_beg, lvl_act_end, lvl_end;
-    std::vector<int32_t> pk_lw[2];      // packed sweeps: first warp of each level (+ total), per direction
+    std::vector<int32_t> pk_lw[2];      // packed sweeps: first framed-point warp of each level (+ total), per direction
+    std::vector<int32_t> lp_lg[2];      // packed sweeps: first interior group of each level (+ total), per direction
     bool pk_ok = false;                 // packed sweeps available (every list <= 32 slots)
     // device
     Arena arena;
@@ -224,9 +225,12 @@ struct HostPrep {
     std::vector<int32_t> pk_pt[2], pk_nbr[2];
     std::vector<uint8_t> pk_mb[2], pk_steps[2];
     std::vector<double> pk_w1[2], pk_w2[2];
-    // the points of each warp (internal index, in lane order of their first
-    // slots), warp w's at pk_hk[pk_wp[w]] .. pk_hk[pk_wp[w + 1] - 1]
-    std::vector<int32_t> pk_wp[2], pk_hk[2];
+    // interior points in lane-per-point groups of 32 (thread t of group g:
+    // point lp_k[32 g + t], -1 for none, with lp_len[32 g + t] slots at
+    // lp_goff[g] + 32 j + t)
+    std::vector<int32_t> lp_k[2], lp_len[2], lp_goff[2], lp_nbr[2];
+    std::vector<uint8_t> lp_mb[2];
+    std::vector<double> lp_w1[2], lp_w2[2];
 };
 static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &hp);
 
@@ -406,6 +410,18 @@ static lskum_status verify_layout(lskum_ctx *c, const lskum_cloud *cl, const Hos
                     return fail(c, LSKUM_ERR_ARG, "layout: packed sum steps of warp %lld", (long long)w);
             }
         }
+        // interior groups: sizes, and every lane's list inside its group's slots
+        const std::vector<int32_t> &lg = c->lp_lg[dir], &lk = hp.lp_k[dir], &ll = hp.lp_len[dir];
+        const std::vector<int32_t> &go = hp.lp_goff[dir], &lnb = hp.lp_nbr[dir];
+        if ((int32_t)lg.size() != c->n_levels + 1 || lg[0] != 0 || (size_t)lg.back() * 32 != lk.size() ||
+            ll.size() != lk.size() || go.size() != (size_t)lg.back() + 1 || go[0] != 0 ||
+            (size_t)go.back() != lnb.size() || hp.lp_mb[dir].size() != lnb.size() ||
+            hp.lp_w1[dir].size() != lnb.size() || hp.lp_w2[dir].size() != lnb.size())
+            return fail(c, LSKUM_ERR_ARG, "layout: interior groups size");
+        std::vector<int32_t> pos_of(n, -1);  // sweep position of each swept point
+        for (int32_t l = 0; l < c->n_levels; l++)
+            for (int32_t pos = c->lvl_beg[l]; pos < c->lvl_act_end[l]; pos++)
+                if (so[pos] >= 0 && so[pos] < n) pos_of[so[pos]] = pos;
         std::vector<int32_t> seen_pos(n, 0);
         for (int32_t l = 0; l < c->n_levels; l++) {
             for (int64_t t = (int64_t)lw[l] * 32; t < (int64_t)lw[l + 1] * 32; t++) {
@@ -423,22 +439,30 @@ static lskum_status verify_layout(lskum_ctx *c, const lskum_cloud *cl, const Hos
                 if (t % 32 + std::max(1, len) < 32 && pt[t + std::max(1, len)] == pos)
                     return fail(c, LSKUM_ERR_ARG, "layout: packed list of position %d too long", pos);
             }
+            if (lg[l + 1] < lg[l]) return fail(c, LSKUM_ERR_ARG, "layout: interior groups of level %d", l);
+            for (int64_t g = lg[l]; g < lg[l + 1]; g++) {
+                if (go[g + 1] < go[g] || (go[g + 1] - go[g]) % 32 != 0)
+                    return fail(c, LSKUM_ERR_ARG, "layout: interior group %lld", (long long)g);
+                const int32_t width = (go[g + 1] - go[g]) / 32;
+                for (int32_t t = 0; t < 32; t++) {
+                    const int32_t k = lk[32 * g + t];
+                    if (k < 0) continue;
+                    if (k >= n || c->flag[c->perm[k]] != LSKUM_INTERIOR)
+                        return fail(c, LSKUM_ERR_ARG, "layout: interior group %lld", (long long)g);
+                    const int32_t pos = pos_of[k], len = loff[k + 1] - loff[k];
+                    if (pos < c->lvl_beg[l] || pos >= c->lvl_act_end[l] || seen_pos[pos]++)
+                        return fail(c, LSKUM_ERR_ARG, "layout: interior point %d", k);
+                    if (ll[32 * g + t] != len || len > width)
+                        return fail(c, LSKUM_ERR_ARG, "layout: interior list of point %d", k);
+                    for (int32_t j = 0; j < len; j++) {
+                        const int64_t e = go[g] + 32 * (int64_t)j + t;
+                        if (lnb[e] != lnbr[loff[k] + j] || lnb[e] < 0 || lnb[e] >= n)
+                            return fail(c, LSKUM_ERR_ARG, "layout: interior list of point %d", k);
+                    }
+                }
+            }
             for (int32_t pos = c->lvl_beg[l]; pos < c->lvl_act_end[l]; pos++)
                 if (seen_pos[pos] != 1) return fail(c, LSKUM_ERR_ARG, "layout: position %d not packed", pos);
-        }
-        // each warp's point list: exactly its points, in lane order
-        const std::vector<int32_t> &wp = hp.pk_wp[dir], &hk = hp.pk_hk[dir];
-        if ((int64_t)wp.size() != (int64_t)lw.back() + 1 || wp[0] != 0 || (size_t)wp.back() != hk.size())
-            return fail(c, LSKUM_ERR_ARG, "layout: packed point lists size");
-        for (int64_t w = 0; w < lw.back(); w++) {
-            int32_t j = wp[w];
-            for (int64_t t = w * 32; t < w * 32 + 32; t++) {
-                if (pt[t] < 0 || (t % 32 != 0 && pt[t - 1] == pt[t])) continue;  // not a first slot
-                if (j >= wp[w + 1] || hk[j] != so[pt[t]] || hk[j] < 0 || hk[j] >= n)
-                    return fail(c, LSKUM_ERR_ARG, "layout: point list of warp %lld", (long long)w);
-                j++;
-            }
-            if (j != wp[w + 1]) return fail(c, LSKUM_ERR_ARG, "layout: point list of warp %lld", (long long)w);
         }
     }
     return LSKUM_OK;
@@ -829,12 +853,16 @@ static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &
         std::stable_sort(hp.sw_bwd.begin() + b, hp.sw_bwd.begin() + e,
                          [&](int32_t a, int32_t z) { return up_len(a) > up_len(z); });
     }
-    // packed sweep form: per level, its points' slots packed into warps of 32
-    // lanes by best fit (longest lists first; a point with an empty list
-    // takes one slot with membership 0); a point never straddles two warps.
-    // Points in a (t, n) frame (wall points, and outer points under the
-    // kinetic far field) are packed into warps of their own: their products
-    // are evaluated per slot, the other points' are gathered.
+    // packed sweep form, per level:
+    // - points in a (t, n) frame (wall points, and outer points under the
+    //   kinetic far field), which form their Jacobian products per slot: their
+    //   slots packed into warps of 32 lanes by best fit (longest lists first; a
+    //   point with an empty list takes one slot with membership 0), a point
+    //   never straddling two warps;
+    // - interior points, which gather their neighbours' stored axis products:
+    //   one lane per point, in groups of 32 in sweep order (decreasing list
+    //   length), each group's lists in ELL layout (slot j of lane t at
+    //   lp_goff[g] + 32 j + t).
     c->pk_ok = true;
     for (int32_t k = 0; k < n; k++)
         if (hp.lo_off[k + 1] - hp.lo_off[k] > 32 || hp.up_off[k + 1] - hp.up_off[k] > 32) c->pk_ok = false;
@@ -844,38 +872,38 @@ static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &
         const std::vector<int32_t> &lnbr = dir == 0 ? hp.lo_nbr : hp.up_nbr;
         const std::vector<uint8_t> &lmb = dir == 0 ? hp.lo_mb : hp.up_mb;
         const std::vector<double> &lw1 = dir == 0 ? hp.lo_w1 : hp.up_w1, &lw2 = dir == 0 ? hp.lo_w2 : hp.up_w2;
-        std::vector<int32_t> &lw = c->pk_lw[dir];
+        std::vector<int32_t> &lw = c->pk_lw[dir], &lg = c->lp_lg[dir];
         lw.assign(1, 0);
-        hp.pk_wp[dir].assign(1, 0);
-        int32_t nw = 0;
+        lg.assign(1, 0);
+        hp.lp_goff[dir].assign(1, 0);
+        int32_t nw = 0, ng = 0;
         for (int32_t l = 0; l < c->n_levels; l++) {
-            // best fit: warps by free lanes (bucket r holds warps with r free),
-            // framed points first, in warps of their own
+            // framed points: best fit, warps by free lanes (bucket r holds warps with r free)
             std::vector<std::vector<int32_t>> members;  // positions per warp of this level
-            for (int pass = 0; pass < 2; pass++) {
-                std::vector<std::vector<int32_t>> bucket(33);
-                for (int32_t pos = c->lvl_beg[l]; pos < c->lvl_act_end[l]; pos++) {
-                    const int32_t k = so[pos];
-                    if ((c->flag[c->perm[k]] != LSKUM_INTERIOR) != (pass == 0)) continue;
-                    const int32_t len = std::max(1, loff[k + 1] - loff[k]);
-                    int32_t w = -1;
-                    for (int32_t r = len; r <= 32 && w < 0; r++)
-                        if (!bucket[r].empty()) {
-                            w = bucket[r].back();
-                            bucket[r].pop_back();
-                            bucket[r - len].push_back(w);
-                        }
-                    if (w < 0) {
-                        w = (int32_t)members.size();
-                        members.emplace_back();
-                        bucket[32 - len].push_back(w);
-                    }
-                    members[w].push_back(pos);
+            std::vector<int32_t> inner;                 // interior points (internal index), sweep order
+            std::vector<std::vector<int32_t>> bucket(33);
+            for (int32_t pos = c->lvl_beg[l]; pos < c->lvl_act_end[l]; pos++) {
+                const int32_t k = so[pos];
+                if (c->flag[c->perm[k]] == LSKUM_INTERIOR) {
+                    inner.push_back(k);
+                    continue;
                 }
+                const int32_t len = std::max(1, loff[k + 1] - loff[k]);
+                int32_t w = -1;
+                for (int32_t r = len; r <= 32 && w < 0; r++)
+                    if (!bucket[r].empty()) {
+                        w = bucket[r].back();
+                        bucket[r].pop_back();
+                        bucket[r - len].push_back(w);
+                    }
+                if (w < 0) {
+                    w = (int32_t)members.size();
+                    members.emplace_back();
+                    bucket[32 - len].push_back(w);
+                }
+                members[w].push_back(pos);
             }
             for (const auto &mw : members) {
-                for (int32_t pos : mw) hp.pk_hk[dir].push_back(so[pos]);
-                hp.pk_wp[dir].push_back((int32_t)hp.pk_hk[dir].size());
                 int32_t lane = 0, longest = 1;
                 for (int32_t pos : mw) longest = std::max(longest, loff[so[pos] + 1] - loff[so[pos]]);
                 uint8_t steps = 0;
@@ -910,6 +938,35 @@ static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &
             }
             nw += (int32_t)members.size();
             lw.push_back(nw);
+            // interior points: groups of 32 lanes, ELL lists
+            for (size_t g0 = 0; g0 < inner.size(); g0 += 32) {
+                int32_t width = 0;
+                for (size_t t = 0; t < 32; t++) {
+                    const int32_t k = g0 + t < inner.size() ? inner[g0 + t] : -1;
+                    const int32_t len = k >= 0 ? loff[k + 1] - loff[k] : 0;
+                    hp.lp_k[dir].push_back(k);
+                    hp.lp_len[dir].push_back(len);
+                    width = std::max(width, len);
+                }
+                const int32_t base = hp.lp_goff[dir].back();
+                hp.lp_goff[dir].push_back(base + 32 * width);
+                hp.lp_nbr[dir].resize((size_t)base + 32 * width, 0);
+                hp.lp_mb[dir].resize((size_t)base + 32 * width, 0);
+                hp.lp_w1[dir].resize((size_t)base + 32 * width, 0.0);
+                hp.lp_w2[dir].resize((size_t)base + 32 * width, 0.0);
+                for (size_t t = 0; t < 32 && g0 + t < inner.size(); t++) {
+                    const int32_t k = inner[g0 + t];
+                    for (int32_t j = 0; j < loff[k + 1] - loff[k]; j++) {
+                        const size_t e = (size_t)base + 32 * (size_t)j + t;
+                        hp.lp_nbr[dir][e] = lnbr[loff[k] + j];
+                        hp.lp_mb[dir][e] = lmb[loff[k] + j];
+                        hp.lp_w1[dir][e] = lw1[loff[k] + j];
+                        hp.lp_w2[dir][e] = lw2[loff[k] + j];
+                    }
+                }
+                ng++;
+            }
+            lg.push_back(ng);
         }
     }
     for (auto *v : {&hp.lo_nbr, &hp.up_nbr}) if (v->empty()) v->push_back(0);
@@ -1004,29 +1061,43 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
         d.dUf = A.alloc<float>(4 * (size_t)ld);
         for (int s = 0; s < 2; s++) d.set[s].primf = A.alloc<float>((size_t)kPrimStride * ld);
     }
-    // packed sweep form
-    std::vector<float> pkf[2][2];
+    // packed sweep form (arrays of at least one element, so that a level set
+    // without framed points, or without interior points, still has them)
+    std::vector<float> pkf[2][2], lpf[2][2];
     for (int dir = 0; dir < 2; dir++) {
         d.pk_pt[dir] = d.pk_nbr[dir] = nullptr;
         d.pk_mb[dir] = d.pk_steps[dir] = nullptr;
         d.pk_w1[dir] = d.pk_w2[dir] = nullptr;
         d.pk_w1f[dir] = d.pk_w2f[dir] = nullptr;
-        d.pk_wp[dir] = d.pk_hk[dir] = nullptr;
-        if (!c->pk_ok || hp.pk_pt[dir].empty()) continue;
-        const size_t m = hp.pk_pt[dir].size();
-        d.pk_wp[dir] = A.alloc<int32_t>(hp.pk_wp[dir].size());
-        d.pk_hk[dir] = A.alloc<int32_t>(std::max<size_t>(hp.pk_hk[dir].size(), 1));
+        d.lp_k[dir] = d.lp_len[dir] = d.lp_goff[dir] = d.lp_nbr[dir] = nullptr;
+        d.lp_mb[dir] = nullptr;
+        d.lp_w1[dir] = d.lp_w2[dir] = nullptr;
+        d.lp_w1f[dir] = d.lp_w2f[dir] = nullptr;
+        if (!c->pk_ok) continue;
+        const size_t m = std::max<size_t>(hp.pk_pt[dir].size(), 1);
         d.pk_pt[dir] = A.alloc<int32_t>(m);
         d.pk_nbr[dir] = A.alloc<int32_t>(m);
         d.pk_mb[dir] = A.alloc<uint8_t>(m);
-        d.pk_steps[dir] = A.alloc<uint8_t>(hp.pk_steps[dir].size());
+        d.pk_steps[dir] = A.alloc<uint8_t>(std::max<size_t>(hp.pk_steps[dir].size(), 1));
         d.pk_w1[dir] = A.alloc<double>(m);
         d.pk_w2[dir] = A.alloc<double>(m);
+        const size_t nk = std::max<size_t>(hp.lp_k[dir].size(), 1), ne = std::max<size_t>(hp.lp_nbr[dir].size(), 1);
+        d.lp_k[dir] = A.alloc<int32_t>(nk);
+        d.lp_len[dir] = A.alloc<int32_t>(nk);
+        d.lp_goff[dir] = A.alloc<int32_t>(hp.lp_goff[dir].size());
+        d.lp_nbr[dir] = A.alloc<int32_t>(ne);
+        d.lp_mb[dir] = A.alloc<uint8_t>(ne);
+        d.lp_w1[dir] = A.alloc<double>(ne);
+        d.lp_w2[dir] = A.alloc<double>(ne);
         if (mixed) {
             pkf[dir][0].assign(hp.pk_w1[dir].begin(), hp.pk_w1[dir].end());
             pkf[dir][1].assign(hp.pk_w2[dir].begin(), hp.pk_w2[dir].end());
             d.pk_w1f[dir] = A.alloc<float>(m);
             d.pk_w2f[dir] = A.alloc<float>(m);
+            lpf[dir][0].assign(hp.lp_w1[dir].begin(), hp.lp_w1[dir].end());
+            lpf[dir][1].assign(hp.lp_w2[dir].begin(), hp.lp_w2[dir].end());
+            d.lp_w1f[dir] = A.alloc<float>(ne);
+            d.lp_w2f[dir] = A.alloc<float>(ne);
         }
     }
     // per-point axis Jacobian products of the packed form (x+, x-, y+, y-)
@@ -1038,6 +1109,8 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
     }
     c->launch.pk_lw[0] = c->pk_ok ? c->pk_lw[0].data() : nullptr;
     c->launch.pk_lw[1] = c->pk_ok ? c->pk_lw[1].data() : nullptr;
+    c->launch.lp_lg[0] = c->pk_ok ? c->lp_lg[0].data() : nullptr;
+    c->launch.lp_lg[1] = c->pk_ok ? c->lp_lg[1].data() : nullptr;
     d.g1x = A.alloc<double>(4 * (size_t)ld);
     d.g1y = A.alloc<double>(4 * (size_t)ld);
     d.R = A.alloc<double>(4 * (size_t)ld);
@@ -1128,7 +1201,7 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
         host_prim_to_cons(1.0, ub, vb, 1.0 / 1.4, &cuinf[4 * b]);  // as the start state below
     }
     auto up = [&](void *dst, const void *src, size_t bytes) {
-        if (e == cudaSuccess) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && bytes) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
     };
     up(dfl, fl_i.data(), ld);
     up(dwnx, wnx.data(), ld * sizeof(double));
@@ -1168,19 +1241,25 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
     up(dcase_uinf, cuinf.data(), cuinf.size() * sizeof(double));
     for (int dir = 0; dir < 2; dir++) {
         if (!d.pk_pt[dir]) continue;
-        const size_t m = hp.pk_pt[dir].size();
+        const size_t m = hp.pk_pt[dir].size(), nk = hp.lp_k[dir].size(), ne = hp.lp_nbr[dir].size();
         up((void *)d.pk_pt[dir], hp.pk_pt[dir].data(), m * sizeof(int32_t));
         up((void *)d.pk_nbr[dir], hp.pk_nbr[dir].data(), m * sizeof(int32_t));
         up((void *)d.pk_mb[dir], hp.pk_mb[dir].data(), m);
         up((void *)d.pk_steps[dir], hp.pk_steps[dir].data(), hp.pk_steps[dir].size());
         up((void *)d.pk_w1[dir], hp.pk_w1[dir].data(), m * sizeof(double));
         up((void *)d.pk_w2[dir], hp.pk_w2[dir].data(), m * sizeof(double));
-        up((void *)d.pk_wp[dir], hp.pk_wp[dir].data(), hp.pk_wp[dir].size() * sizeof(int32_t));
-        if (!hp.pk_hk[dir].empty())
-            up((void *)d.pk_hk[dir], hp.pk_hk[dir].data(), hp.pk_hk[dir].size() * sizeof(int32_t));
+        up((void *)d.lp_k[dir], hp.lp_k[dir].data(), nk * sizeof(int32_t));
+        up((void *)d.lp_len[dir], hp.lp_len[dir].data(), nk * sizeof(int32_t));
+        up((void *)d.lp_goff[dir], hp.lp_goff[dir].data(), hp.lp_goff[dir].size() * sizeof(int32_t));
+        up((void *)d.lp_nbr[dir], hp.lp_nbr[dir].data(), ne * sizeof(int32_t));
+        up((void *)d.lp_mb[dir], hp.lp_mb[dir].data(), ne);
+        up((void *)d.lp_w1[dir], hp.lp_w1[dir].data(), ne * sizeof(double));
+        up((void *)d.lp_w2[dir], hp.lp_w2[dir].data(), ne * sizeof(double));
         if (d.pk_w1f[dir]) {
             up((void *)d.pk_w1f[dir], pkf[dir][0].data(), m * sizeof(float));
             up((void *)d.pk_w2f[dir], pkf[dir][1].data(), m * sizeof(float));
+            up((void *)d.lp_w1f[dir], lpf[dir][0].data(), ne * sizeof(float));
+            up((void *)d.lp_w2f[dir], lpf[dir][1].data(), ne * sizeof(float));
         }
     }
     if (e == cudaSuccess && d.jc) e = cudaMemset(d.jc, 0, 16 * (size_t)ld * sizeof(double));

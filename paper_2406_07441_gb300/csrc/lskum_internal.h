@@ -120,22 +120,26 @@ struct Dev {
     // trip count
     const int32_t *sw_fwd, *sw_bwd;
     // packed sweep form, [0] forward (lower lists), [1] backward (upper
-    // lists): warp w's 32 lanes hold slots 32w .. 32w+31, each with the sweep
-    // position of its point (-1: padding), neighbour, membership and weights;
-    // a point's slots are consecutive lanes of one warp (null when a list is
-    // longer than 32)
+    // lists), for the points in a (t, n) frame: warp w's 32 lanes hold slots
+    // 32w .. 32w+31, each with the sweep position of its point (-1: padding),
+    // neighbour, membership and weights; a point's slots are consecutive
+    // lanes of one warp (null when a list is longer than 32)
     const int32_t *pk_pt[2], *pk_nbr[2];
     const uint8_t *pk_mb[2];
     const uint8_t *pk_steps[2];  // per warp: steps of its segmented sum, ceil(log2(longest list))
     const double *pk_w1[2], *pk_w2[2];
     const float *pk_w1f[2], *pk_w2f[2];
-    // the points of warp w (internal index, lane order of their first slots):
-    // pk_hk[pk_wp[w]] .. pk_hk[pk_wp[w + 1] - 1]
-    const int32_t *pk_wp[2], *pk_hk[2];
+    // and for the interior points: one lane per point in groups of 32 (by
+    // decreasing list length): lane t of group g is point lp_k[32 g + t] (-1:
+    // none), whose lp_len[32 g + t] slots are at lp_goff[g] + 32 j + t
+    const int32_t *lp_k[2], *lp_len[2], *lp_goff[2], *lp_nbr[2];
+    const uint8_t *lp_mb[2];
+    const double *lp_w1[2], *lp_w2[2];
+    const float *lp_w1f[2], *lp_w2f[2];
     // packed form: per point, the axis split-flux Jacobian products of its
-    // latest increment, [ld][4 products: x+, x-, y+, y-][4]: written by the
-    // point's own level, gathered by the later levels' interior points
-    // (FP64, or FP32 for the mixed-precision sweeps; the other is null)
+    // latest increment, [ld][4 products: x+, x-, y+, y-][4]: written when the
+    // point's increment is formed, gathered by the later levels' interior
+    // points (FP64, or FP32 for the mixed-precision sweeps; the other is null)
     double *jc;
     float *jcf;
     // per-case residual norm: stage 1 sums R_rho^2 over blocks of up to 256
@@ -166,7 +170,8 @@ struct Launch {
     int tpp;          // threads per point of the gradient and residual kernels (1, 2, 4, 8)
     int res_block;    // threads per block of the residual kernel
     int sweep_lanes;  // lanes per point of the sweep kernels (2, 4, 8), or 32: the packed form
-    const int32_t *pk_lw[2];  // packed form: host arrays [n_levels + 1], first warp of each level
+    const int32_t *pk_lw[2];  // packed form: host arrays [n_levels + 1], first framed-point warp of each level
+    const int32_t *lp_lg[2];  // packed form: host arrays [n_levels + 1], first interior group of each level
 };
 
 cudaError_t launch_iteration(const Dev &d, const Launch &L, int cur, int n_levels, const int32_t *lvl_beg,

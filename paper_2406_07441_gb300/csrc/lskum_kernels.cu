@@ -814,15 +814,14 @@ __device__ __forceinline__ void sweep_slot(const Dev &d, const StateSet &st, con
 
 // Point k's new increment from its list sum acc: forward dU*_k = -(R_k (+ S_k)
 // + acc) / D_k, backward dU_k = dU*_k - acc / D_k; normal momentum removed at
-// wall points.
+// wall points.  Stored, and returned in w.
 template <bool FWD, typename T>
 __device__ __forceinline__ void sweep_point(const Dev &d, const StateSet &st, const SweepBufs<T> &sb, int k,
                                             bool wall, double e1x, double e1y, double e2x, double e2y,
-                                            const T acc[4])
+                                            const T acc[4], T w[4])
 {
     const int ld = d.ld;
     const T iD = (T)d.iD[k];
-    T w[4];
     if (FWD) {
         double rhs[4];
 #pragma unroll
@@ -903,7 +902,8 @@ __global__ void __launch_bounds__(256) k_sweep(Dev d, StateSet st, int lb, int l
         sweep_slot<JVP, T>(d, st, Tb, dW, sb.prim, framed, e1x, e1y, e2x, e2y, nbr[e], mbs[e], w1s[e], w2s[e], acc);
 #pragma unroll
     for (int c = 0; c < 4; c++) acc[c] = group_sum<G>(acc[c]);
-    if (live && sub == 0) sweep_point<FWD, T>(d, st, sb, k, wall, e1x, e1y, e2x, e2y, acc);
+    T w[4];
+    if (live && sub == 0) sweep_point<FWD, T>(d, st, sb, k, wall, e1x, e1y, e2x, e2y, acc, w);
 }
 
 // Four consecutive values from 16-byte-aligned storage (one point's product).
@@ -918,107 +918,109 @@ __device__ __forceinline__ void load4(const float *__restrict__ p, float v[4])
     v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
 }
 
-// Axis product cb (0: x+, 1: x-, 2: y+, 3: y-) of point k's new increment
-// (in inc), the value every interior point whose list holds k would form
-// for that sub-stencil (the same function, arguments and precision), stored
-// for the later levels.
-template <int JVP, typename T>
-__device__ __forceinline__ void store_axis_product(const Dev &d, const StateSet &st, const MathTables &Tb,
-                                                   const SweepBufs<T> &sb, const T *inc, int k, int cb)
+__device__ __forceinline__ void store4(double *p, const double v[4])
 {
-    const bool pos = !(cb & 1);
-    T dl[4];
-#pragma unroll
-    for (int c = 0; c < 4; c++) dl[c] = __ldcg(inc + 4 * k + c);  // written by this block
-    T J[4];
+    reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+}
+__device__ __forceinline__ void store4(float *p, const float v[4])
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+// The four axis products (x+, x-, y+, y-) of point k's new increment w: the
+// values an interior point whose list holds k would form for those
+// sub-stencils (the same functions, arguments and precision), stored once
+// for every later level to gather.
+template <int JVP, typename T>
+__device__ __forceinline__ void store_axis_products(const Dev &d, const StateSet &st, const MathTables &Tb,
+                                                    const SweepBufs<T> &sb, const T w[4], int k)
+{
+    T *out = sb.jc + 16 * (size_t)k;
     if (JVP == 0) {
         const PrimT<T> P = load_prim(sb.prim, k);
         const T *rec = sb.prim + (size_t)k * kPrimStride;
-        const JvpBase<T> jb = jvp_base(P, dl);
-        if (cb < 2)
-            jvp_axis<0, T>(P, jb, pos, rec[pos ? P_APX : P_AMX], rec[P_EKX], rec[P_BX], rec[P_BSX], rec[P_UE1], J);
-        else
-            jvp_axis<1, T>(P, jb, pos, rec[pos ? P_APY : P_AMY], rec[P_EKY], rec[P_BY], rec[P_BSY], rec[P_VE1], J);
+        const JvpBase<T> jb = jvp_base(P, w);
+#pragma unroll
+        for (int cb = 0; cb < 4; cb++) {
+            const bool pos = !(cb & 1);
+            T J[4];
+            if (cb < 2)
+                jvp_axis<0, T>(P, jb, pos, rec[pos ? P_APX : P_AMX], rec[P_EKX], rec[P_BX], rec[P_BSX], rec[P_UE1], J);
+            else
+                jvp_axis<1, T>(P, jb, pos, rec[pos ? P_APY : P_AMY], rec[P_EKY], rec[P_BY], rec[P_BSY], rec[P_VE1], J);
+            store4(out + 4 * cb, J);
+        }
     } else {  // increment form, in FP64
         const int ld = d.ld;
-        double Ui[4], Up[4], G1[4], G0[4];
+        double Ui[4], Up[4];
 #pragma unroll
         for (int c = 0; c < 4; c++) {
             Ui[c] = st.U[c * ld + k];
-            Up[c] = Ui[c] + (double)dl[c];
+            Up[c] = Ui[c] + (double)w[c];
         }
-        const double ddx = cb < 2 ? 1.0 : 0.0, ddy = cb < 2 ? 0.0 : 1.0;
-        flux_cons(Tb, Up, ddx, ddy, pos, G1);
-        flux_cons(Tb, Ui, ddx, ddy, pos, G0);
+#pragma unroll 1
+        for (int cb = 0; cb < 4; cb++) {
+            const bool pos = !(cb & 1);
+            const double ddx = cb < 2 ? 1.0 : 0.0, ddy = cb < 2 ? 0.0 : 1.0;
+            double G1[4], G0[4];
+            T J[4];
+            flux_cons(Tb, Up, ddx, ddy, pos, G1);
+            flux_cons(Tb, Ui, ddx, ddy, pos, G0);
 #pragma unroll
-        for (int c = 0; c < 4; c++) J[c] = (T)(G1[c] - G0[c]);
+            for (int c = 0; c < 4; c++) J[c] = (T)(G1[c] - G0[c]);
+            store4(out + 4 * cb, J);
+        }
     }
-    T *out = sb.jc + 16 * (size_t)k + 4 * cb;
-#pragma unroll
-    for (int c = 0; c < 4; c++) out[c] = J[c];
 }
 
-// Packed form: one lane per list slot.  At create the level's points (in
-// sweep order) are packed whole into warps of up to 32 slots (a point with
-// an empty list takes one idle slot), so lanes are not left idle by lists
-// shorter than a lane group; a segmented suffix sum over the lanes of each
-// point (fixed tree order, no atomics) leaves the point's sum in its first
-// lane, which finishes the point.  Warps [wb, we) are the level's.
-// A neighbour's Jacobian product along an axis depends only on the
-// neighbour, the axis and the sub-stencil's sign, so each block ends by
-// forming the four axis products of its points' new increments, once per
-// point; interior points gather them (8 FMAs per slot instead of ~70 FP64
-// instructions), in the order the per-slot form adds them, so the sums are
-// the same bits.  Points in a (t, n) frame form their products per slot.
+// Packed form of a level.  A neighbour's Jacobian product along an axis
+// depends only on the neighbour, the axis and the sub-stencil's sign, so a
+// point forms the four axis products of its new increment once, and
+// interior points gather them: 8 FMAs per slot instead of ~70 FP64
+// instructions, in the order the per-slot form adds them.
+// - Warps [0, wf): the points in a (t, n) frame (products per slot in their
+//   own frame), their slots packed whole into warps (at create, by best
+//   fit; a point with an empty list takes one idle slot), one lane per slot;
+//   a segmented suffix sum over the lanes of each point (fixed tree order,
+//   no atomics) leaves the point's sum in its first lane, which finishes
+//   the point.  Packed warps [wb, wb + wf) are the level's.
+// - Warps [wf, wf + ng): the interior points, one lane per point, in groups
+//   of 32 of similar list length (groups [g0, g0 + ng) are the level's),
+//   each lane summing its list in order.
 template <int JVP, bool FWD, typename T>
-__global__ void __launch_bounds__(256) k_sweep_packed(Dev d, StateSet st, int wb, int we)
+__global__ void __launch_bounds__(256) k_sweep_packed(Dev d, StateSet st, int wb, int wf, int g0, int ng)
 {
-    const MathTables &Tb = g_math;  // wall and outer points only: no per-block copy
-    __shared__ int halt;
-    if (threadIdx.x == 0) halt = halted(d.ctrl);
-    __syncthreads();
-    if (halt) return;  // the whole block: every thread reaches the barrier below
-    const int gw = wb + (blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const MathTables &Tb = g_math;  // framed points only: no per-block copy
+    if (halted(d.ctrl)) return;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    if (gw >= wf + ng) return;  // whole warps (blocks are whole warps)
+    const int lane = threadIdx.x & 31;
     const int dir = FWD ? 0 : 1;
     const SweepBufs<T> sb = sweep_bufs<T>(d, st);
-    T *const inc = FWD ? sb.dUs : sb.dU;  // this sweep's increments
-    if (gw < we) {  // whole warps (blocks are whole warps)
-        const int lane = threadIdx.x & 31;
-        const size_t e = (size_t)gw * 32 + lane;
+    const T *__restrict__ dW = FWD ? sb.dUs : sb.dU;  // earlier levels' increments
+    const T *__restrict__ jn = sb.jc;                 // earlier levels' axis products
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+    T w[4];
+    if (gw < wf) {
+        const size_t e = (size_t)(wb + gw) * 32 + lane;
         const int pos = d.pk_pt[dir][e];  // sweep position of the slot's point, -1: padding
         const int k = pos >= 0 ? (FWD ? d.sw_fwd : d.sw_bwd)[pos] : 0;
         const bool live = pos >= 0 && !frozen(d, k);
-        const T *__restrict__ dW = inc;  // earlier levels' increments
-        const T *__restrict__ jn = sb.jc;  // earlier levels' products
         const int fk = d.flag[k];
         const bool wall = fk == kWall, framed = fk != kInterior;
         double e1x, e1y, e2x, e2y;
         point_frame(d, k, framed, e1x, e1y, e2x, e2y);
-        T acc[4] = {T(0), T(0), T(0), T(0)};
         const int mb = d.pk_mb[dir][e];
         if (live && mb) {
             const T w1 = sizeof(T) == 4 ? (T)d.pk_w1f[dir][e] : (T)d.pk_w1[dir][e];
             const T w2 = sizeof(T) == 4 ? (T)d.pk_w2f[dir][e] : (T)d.pk_w2[dir][e];
-            const int i = d.pk_nbr[dir][e];
-            if (framed) {
-                sweep_slot<JVP, T>(d, st, Tb, dW, sb.prim, framed, e1x, e1y, e2x, e2y, i, mb, w1, w2, acc);
-            } else {
-                T J[4];
-                if (mb & 3) {
-                    load4(jn + 16 * (size_t)i + ((mb & 1) ? 0 : 4), J);
-#pragma unroll
-                    for (int c = 0; c < 4; c++) acc[c] = fma(w1, J[c], acc[c]);
-                }
-                if (mb & 12) {
-                    load4(jn + 16 * (size_t)i + ((mb & 4) ? 8 : 12), J);
-#pragma unroll
-                    for (int c = 0; c < 4; c++) acc[c] = fma(w2, J[c], acc[c]);
-                }
-            }
+            sweep_slot<JVP, T>(d, st, Tb, dW, sb.prim, framed, e1x, e1y, e2x, e2y, d.pk_nbr[dir][e], mb, w1, w2,
+                               acc);
         }
         // segmented suffix sum: lane l adds lane l + o when both hold the same
         // point; the warp's longest list bounds the steps (warp-uniform)
-        const int steps = d.pk_steps[dir][gw];
+        const int steps = d.pk_steps[dir][wb + gw];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             if (o >= (1 << steps)) break;
@@ -1032,23 +1034,37 @@ __global__ void __launch_bounds__(256) k_sweep_packed(Dev d, StateSet st, int wb
             }
         }
         const int prev = __shfl_up_sync(kFull, pos, 1);
-        if (live && (lane == 0 || prev != pos)) sweep_point<FWD, T>(d, st, sb, k, wall, e1x, e1y, e2x, e2y, acc);
+        if (live && (lane == 0 || prev != pos)) {
+            sweep_point<FWD, T>(d, st, sb, k, wall, e1x, e1y, e2x, e2y, acc, w);
+            store_axis_products<JVP, T>(d, st, Tb, sb, w, k);
+        }
+        return;
     }
-    __syncthreads();  // the block's new increments are written
-    // the block's points' axis products, one thread per (point, product):
-    // first every point's x products, then the y products, so that a warp
-    // takes one axis (the sign costs no branch)
-    const int wpb = blockDim.x / 32;
-    const int gw0 = wb + blockIdx.x * wpb, gw1 = min(gw0 + wpb, we);
-    if (gw0 < we) {
-        const int p0 = d.pk_wp[dir][gw0], np = d.pk_wp[dir][gw1] - p0;
-        for (int t = threadIdx.x; t < 4 * np; t += blockDim.x) {
-            const int y = t >= 2 * np;
-            const int r = y ? t - 2 * np : t;
-            const int k = d.pk_hk[dir][p0 + (r >> 1)];
-            if (!frozen(d, k)) store_axis_product<JVP, T>(d, st, Tb, sb, inc, k, 2 * y + (r & 1));
+    const int g = g0 + gw - wf;
+    const int k = d.lp_k[dir][32 * g + lane];
+    if (k < 0 || frozen(d, k)) return;
+    const int len = d.lp_len[dir][32 * g + lane];
+    const size_t base = (size_t)d.lp_goff[dir][g] + lane;
+#pragma unroll 4
+    for (int j = 0; j < len; j++) {
+        const size_t e = base + 32 * (size_t)j;
+        const int i = d.lp_nbr[dir][e], mb = d.lp_mb[dir][e];
+        T J[4];
+        if (mb & 3) {
+            const T w1 = sizeof(T) == 4 ? (T)d.lp_w1f[dir][e] : (T)d.lp_w1[dir][e];
+            load4(jn + 16 * (size_t)i + ((mb & 1) ? 0 : 4), J);
+#pragma unroll
+            for (int c = 0; c < 4; c++) acc[c] = fma(w1, J[c], acc[c]);
+        }
+        if (mb & 12) {
+            const T w2 = sizeof(T) == 4 ? (T)d.lp_w2f[dir][e] : (T)d.lp_w2[dir][e];
+            load4(jn + 16 * (size_t)i + ((mb & 4) ? 8 : 12), J);
+#pragma unroll
+            for (int c = 0; c < 4; c++) acc[c] = fma(w2, J[c], acc[c]);
         }
     }
+    sweep_point<FWD, T>(d, st, sb, k, false, 1.0, 0.0, 0.0, 1.0, acc, w);
+    store_axis_products<JVP, T>(d, st, Tb, sb, w, k);
 }
 
 // ---------------------------------------------------------------------------
@@ -1306,19 +1322,21 @@ void enqueue_sweeps_packed(const Dev &d, const Launch &L, int cur, int n_levels,
 {
     const StateSet st = d.set[cur];
     for (int l = 0; fwd && l < n_levels; l++) {
-        const int wb = L.pk_lw[0][l], we = L.pk_lw[0][l + 1];
-        if (we <= wb) continue;
-        const int blocks = ((we - wb) * 32 + 255) / 256;
-        if (d.precision) k_sweep_packed<JVP, true, float><<<blocks, 256, 0, s>>>(d, st, wb, we);
-        else k_sweep_packed<JVP, true, double><<<blocks, 256, 0, s>>>(d, st, wb, we);
+        const int wb = L.pk_lw[0][l], wf = L.pk_lw[0][l + 1] - wb;
+        const int g0 = L.lp_lg[0][l], ng = L.lp_lg[0][l + 1] - g0;
+        if (wf + ng <= 0) continue;
+        const int blocks = ((wf + ng) * 32 + 255) / 256;
+        if (d.precision) k_sweep_packed<JVP, true, float><<<blocks, 256, 0, s>>>(d, st, wb, wf, g0, ng);
+        else k_sweep_packed<JVP, true, double><<<blocks, 256, 0, s>>>(d, st, wb, wf, g0, ng);
         (*launches)++;
     }
     for (int l = n_levels - 1; bwd && l >= 0; l--) {
-        const int wb = L.pk_lw[1][l], we = L.pk_lw[1][l + 1];
-        if (we <= wb) continue;
-        const int blocks = ((we - wb) * 32 + 255) / 256;
-        if (d.precision) k_sweep_packed<JVP, false, float><<<blocks, 256, 0, s>>>(d, st, wb, we);
-        else k_sweep_packed<JVP, false, double><<<blocks, 256, 0, s>>>(d, st, wb, we);
+        const int wb = L.pk_lw[1][l], wf = L.pk_lw[1][l + 1] - wb;
+        const int g0 = L.lp_lg[1][l], ng = L.lp_lg[1][l + 1] - g0;
+        if (wf + ng <= 0) continue;
+        const int blocks = ((wf + ng) * 32 + 255) / 256;
+        if (d.precision) k_sweep_packed<JVP, false, float><<<blocks, 256, 0, s>>>(d, st, wb, wf, g0, ng);
+        else k_sweep_packed<JVP, false, double><<<blocks, 256, 0, s>>>(d, st, wb, wf, g0, ng);
         (*launches)++;
     }
 }
@@ -1332,7 +1350,8 @@ cudaError_t enqueue_sweeps(const Dev &d, const Launch &L, int cur, int n_levels,
     case 4: enqueue_sweeps_g<JVP, 4>(d, cur, n_levels, lvl_beg, lvl_act_end, s, launches, fwd, bwd); break;
     case 8: enqueue_sweeps_g<JVP, 8>(d, cur, n_levels, lvl_beg, lvl_act_end, s, launches, fwd, bwd); break;
     case 32:
-        if (!d.pk_pt[0] || !L.pk_lw[0]) return cudaErrorInvalidValue;
+        if (!d.pk_pt[0] || !L.pk_lw[0] || !L.lp_lg[0] || !(d.precision ? (void *)d.jcf : (void *)d.jc))
+            return cudaErrorInvalidValue;
         enqueue_sweeps_packed<JVP>(d, L, cur, n_levels, s, launches, fwd, bwd);
         break;
     default: return cudaErrorInvalidValue;
