@@ -413,7 +413,7 @@ static lskum_status verify_layout(lskum_ctx *c, const lskum_cloud *cl, const Hos
         // interior groups: sizes, and every lane's list inside its group's slots
         const std::vector<int32_t> &lg = c->lp_lg[dir], &lk = hp.lp_k[dir], &ll = hp.lp_len[dir];
         const std::vector<int32_t> &go = hp.lp_goff[dir], &lnb = hp.lp_nbr[dir];
-        if ((int32_t)lg.size() != c->n_levels + 1 || lg[0] != 0 || (size_t)lg.back() * 32 != lk.size() ||
+        if ((int32_t)lg.size() != c->n_levels + 1 || lg[0] != 0 || (size_t)lg.back() * kPointsPerWarp != lk.size() ||
             ll.size() != lk.size() || go.size() != (size_t)lg.back() + 1 || go[0] != 0 ||
             (size_t)go.back() != lnb.size() || hp.lp_mb[dir].size() != lnb.size() ||
             hp.lp_w1[dir].size() != lnb.size() || hp.lp_w2[dir].size() != lnb.size())
@@ -444,18 +444,19 @@ static lskum_status verify_layout(lskum_ctx *c, const lskum_cloud *cl, const Hos
                 if (go[g + 1] < go[g] || (go[g + 1] - go[g]) % 32 != 0)
                     return fail(c, LSKUM_ERR_ARG, "layout: interior group %lld", (long long)g);
                 const int32_t width = (go[g + 1] - go[g]) / 32;
-                for (int32_t t = 0; t < 32; t++) {
-                    const int32_t k = lk[32 * g + t];
+                constexpr int L = kLanesPerPoint;
+                for (int32_t t = 0; t < kPointsPerWarp; t++) {
+                    const int32_t k = lk[(int64_t)kPointsPerWarp * g + t];
                     if (k < 0) continue;
                     if (k >= n || c->flag[c->perm[k]] != LSKUM_INTERIOR)
                         return fail(c, LSKUM_ERR_ARG, "layout: interior group %lld", (long long)g);
                     const int32_t pos = pos_of[k], len = loff[k + 1] - loff[k];
                     if (pos < c->lvl_beg[l] || pos >= c->lvl_act_end[l] || seen_pos[pos]++)
                         return fail(c, LSKUM_ERR_ARG, "layout: interior point %d", k);
-                    if (ll[32 * g + t] != len || len > width)
+                    if (ll[(int64_t)kPointsPerWarp * g + t] != len || (len + L - 1) / L > width)
                         return fail(c, LSKUM_ERR_ARG, "layout: interior list of point %d", k);
                     for (int32_t j = 0; j < len; j++) {
-                        const int64_t e = go[g] + 32 * (int64_t)j + t;
+                        const int64_t e = go[g] + 32 * (int64_t)(j / L) + L * t + j % L;
                         if (lnb[e] != lnbr[loff[k] + j] || lnb[e] < 0 || lnb[e] >= n)
                             return fail(c, LSKUM_ERR_ARG, "layout: interior list of point %d", k);
                     }
@@ -860,9 +861,10 @@ static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &
     //   point with an empty list takes one slot with membership 0), a point
     //   never straddling two warps;
     // - interior points, which gather their neighbours' stored axis products:
-    //   one lane per point, in groups of 32 in sweep order (decreasing list
-    //   length), each group's lists in ELL layout (slot j of lane t at
-    //   lp_goff[g] + 32 j + t).
+    //   kLanesPerPoint lanes per point, in groups of kPointsPerWarp points in
+    //   sweep order (decreasing list length), each group's lists in ELL
+    //   layout (slot j of point p at lp_goff[g] + 32 (j / L) + L p + j % L,
+    //   L = kLanesPerPoint).
     c->pk_ok = true;
     for (int32_t k = 0; k < n; k++)
         if (hp.lo_off[k + 1] - hp.lo_off[k] > 32 || hp.up_off[k + 1] - hp.up_off[k] > 32) c->pk_ok = false;
@@ -938,15 +940,16 @@ static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &
             }
             nw += (int32_t)members.size();
             lw.push_back(nw);
-            // interior points: groups of 32 lanes, ELL lists
-            for (size_t g0 = 0; g0 < inner.size(); g0 += 32) {
-                int32_t width = 0;
-                for (size_t t = 0; t < 32; t++) {
+            // interior points: groups of kPointsPerWarp points, ELL lists
+            constexpr int L = kLanesPerPoint;
+            for (size_t g0 = 0; g0 < inner.size(); g0 += kPointsPerWarp) {
+                int32_t width = 0;  // rows of 32 slots
+                for (size_t t = 0; t < (size_t)kPointsPerWarp; t++) {
                     const int32_t k = g0 + t < inner.size() ? inner[g0 + t] : -1;
                     const int32_t len = k >= 0 ? loff[k + 1] - loff[k] : 0;
                     hp.lp_k[dir].push_back(k);
                     hp.lp_len[dir].push_back(len);
-                    width = std::max(width, len);
+                    width = std::max(width, (len + L - 1) / L);
                 }
                 const int32_t base = hp.lp_goff[dir].back();
                 hp.lp_goff[dir].push_back(base + 32 * width);
@@ -954,10 +957,10 @@ static lskum_status prepare_host(lskum_ctx *c, const lskum_cloud *cl, HostPrep &
                 hp.lp_mb[dir].resize((size_t)base + 32 * width, 0);
                 hp.lp_w1[dir].resize((size_t)base + 32 * width, 0.0);
                 hp.lp_w2[dir].resize((size_t)base + 32 * width, 0.0);
-                for (size_t t = 0; t < 32 && g0 + t < inner.size(); t++) {
+                for (size_t t = 0; t < (size_t)kPointsPerWarp && g0 + t < inner.size(); t++) {
                     const int32_t k = inner[g0 + t];
                     for (int32_t j = 0; j < loff[k + 1] - loff[k]; j++) {
-                        const size_t e = (size_t)base + 32 * (size_t)j + t;
+                        const size_t e = (size_t)base + 32 * (size_t)(j / L) + L * t + j % L;
                         hp.lp_nbr[dir][e] = lnbr[loff[k] + j];
                         hp.lp_mb[dir][e] = lmb[loff[k] + j];
                         hp.lp_w1[dir][e] = lw1[loff[k] + j];

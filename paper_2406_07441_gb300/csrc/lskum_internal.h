@@ -72,6 +72,12 @@ enum PrimField {
     P_NFIELDS
 };
 constexpr int kPrimStride = 24;
+
+// Packed sweep form: lanes per interior point (each takes every kLanesPerPoint-th
+// slot of the point's list and forms one of its four axis products), and so
+// interior points per warp.
+constexpr int kLanesPerPoint = 4;
+constexpr int kPointsPerWarp = 32 / kLanesPerPoint;
 static_assert(P_NFIELDS <= kPrimStride, "prim record too small");
 
 struct StateSet {
@@ -129,9 +135,11 @@ struct Dev {
     const uint8_t *pk_steps[2];  // per warp: steps of its segmented sum, ceil(log2(longest list))
     const double *pk_w1[2], *pk_w2[2];
     const float *pk_w1f[2], *pk_w2f[2];
-    // and for the interior points: one lane per point in groups of 32 (by
-    // decreasing list length): lane t of group g is point lp_k[32 g + t] (-1:
-    // none), whose lp_len[32 g + t] slots are at lp_goff[g] + 32 j + t
+    // and for the interior points: kLanesPerPoint lanes per point, in groups
+    // of kPointsPerWarp points (by decreasing list length): point p of group g
+    // is lp_k[kPointsPerWarp g + p] (-1: none), with lp_len[...] slots, slot j
+    // at lp_goff[g] + 32 (j / kLanesPerPoint) + kLanesPerPoint p + j % kLanesPerPoint
+    // (lane kLanesPerPoint p + s takes the slots j = s (mod kLanesPerPoint))
     const int32_t *lp_k[2], *lp_len[2], *lp_goff[2], *lp_nbr[2];
     const uint8_t *lp_mb[2];
     const double *lp_w1[2], *lp_w2[2];

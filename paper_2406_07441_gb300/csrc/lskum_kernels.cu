@@ -928,50 +928,39 @@ __device__ __forceinline__ void store4(float *p, const float v[4])
     *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
 
-// The four axis products (x+, x-, y+, y-) of point k's new increment w: the
-// values an interior point whose list holds k would form for those
-// sub-stencils (the same functions, arguments and precision), stored once
-// for every later level to gather.
+// Axis product cb (0: x+, 1: x-, 2: y+, 3: y-) of point k's new increment w:
+// the value an interior point whose list holds k would form for that
+// sub-stencil (the same functions, arguments and precision), stored once for
+// every later level to gather.
 template <int JVP, typename T>
-__device__ __forceinline__ void store_axis_products(const Dev &d, const StateSet &st, const MathTables &Tb,
-                                                    const SweepBufs<T> &sb, const T w[4], int k)
+__device__ __forceinline__ void store_axis_product(const Dev &d, const StateSet &st, const MathTables &Tb,
+                                                   const SweepBufs<T> &sb, const T w[4], int k, int cb)
 {
-    T *out = sb.jc + 16 * (size_t)k;
+    const bool pos = !(cb & 1);
+    T J[4];
     if (JVP == 0) {
         const PrimT<T> P = load_prim(sb.prim, k);
         const T *rec = sb.prim + (size_t)k * kPrimStride;
         const JvpBase<T> jb = jvp_base(P, w);
-#pragma unroll
-        for (int cb = 0; cb < 4; cb++) {
-            const bool pos = !(cb & 1);
-            T J[4];
-            if (cb < 2)
-                jvp_axis<0, T>(P, jb, pos, rec[pos ? P_APX : P_AMX], rec[P_EKX], rec[P_BX], rec[P_BSX], rec[P_UE1], J);
-            else
-                jvp_axis<1, T>(P, jb, pos, rec[pos ? P_APY : P_AMY], rec[P_EKY], rec[P_BY], rec[P_BSY], rec[P_VE1], J);
-            store4(out + 4 * cb, J);
-        }
+        if (cb < 2)
+            jvp_axis<0, T>(P, jb, pos, rec[pos ? P_APX : P_AMX], rec[P_EKX], rec[P_BX], rec[P_BSX], rec[P_UE1], J);
+        else
+            jvp_axis<1, T>(P, jb, pos, rec[pos ? P_APY : P_AMY], rec[P_EKY], rec[P_BY], rec[P_BSY], rec[P_VE1], J);
     } else {  // increment form, in FP64
         const int ld = d.ld;
-        double Ui[4], Up[4];
+        double Ui[4], Up[4], G1[4], G0[4];
 #pragma unroll
         for (int c = 0; c < 4; c++) {
             Ui[c] = st.U[c * ld + k];
             Up[c] = Ui[c] + (double)w[c];
         }
-#pragma unroll 1
-        for (int cb = 0; cb < 4; cb++) {
-            const bool pos = !(cb & 1);
-            const double ddx = cb < 2 ? 1.0 : 0.0, ddy = cb < 2 ? 0.0 : 1.0;
-            double G1[4], G0[4];
-            T J[4];
-            flux_cons(Tb, Up, ddx, ddy, pos, G1);
-            flux_cons(Tb, Ui, ddx, ddy, pos, G0);
+        const double ddx = cb < 2 ? 1.0 : 0.0, ddy = cb < 2 ? 0.0 : 1.0;
+        flux_cons(Tb, Up, ddx, ddy, pos, G1);
+        flux_cons(Tb, Ui, ddx, ddy, pos, G0);
 #pragma unroll
-            for (int c = 0; c < 4; c++) J[c] = (T)(G1[c] - G0[c]);
-            store4(out + 4 * cb, J);
-        }
+        for (int c = 0; c < 4; c++) J[c] = (T)(G1[c] - G0[c]);
     }
+    store4(sb.jc + 16 * (size_t)k + 4 * cb, J);
 }
 
 // Packed form of a level.  A neighbour's Jacobian product along an axis
@@ -979,15 +968,17 @@ __device__ __forceinline__ void store_axis_products(const Dev &d, const StateSet
 // point forms the four axis products of its new increment once, and
 // interior points gather them: 8 FMAs per slot instead of ~70 FP64
 // instructions, in the order the per-slot form adds them.
-// - Warps [0, wf): the points in a (t, n) frame (products per slot in their
+// - wf warps for the points in a (t, n) frame (products per slot in their
 //   own frame), their slots packed whole into warps (at create, by best
 //   fit; a point with an empty list takes one idle slot), one lane per slot;
 //   a segmented suffix sum over the lanes of each point (fixed tree order,
 //   no atomics) leaves the point's sum in its first lane, which finishes
-//   the point.  Packed warps [wb, wb + wf) are the level's.
-// - Warps [wf, wf + ng): the interior points, one lane per point, in groups
-//   of 32 of similar list length (groups [g0, g0 + ng) are the level's),
-//   each lane summing its list in order.
+//   the point, and the point's lanes share its four axis products.  Packed
+//   warps [wb, wb + wf) are the level's; they are spread evenly over the
+//   grid (every S-th warp), so that their long chains do not share SMs.
+// - ng warps for the interior points, kLanesPerPoint lanes per point,
+//   kPointsPerWarp points of similar list length per warp (groups
+//   [g0, g0 + ng) are the level's), in the other warp positions in order.
 template <int JVP, bool FWD, typename T>
 __global__ void __launch_bounds__(256) k_sweep_packed(Dev d, StateSet st, int wb, int wf, int g0, int ng)
 {
@@ -1001,9 +992,11 @@ __global__ void __launch_bounds__(256) k_sweep_packed(Dev d, StateSet st, int wb
     const T *__restrict__ dW = FWD ? sb.dUs : sb.dU;  // earlier levels' increments
     const T *__restrict__ jn = sb.jc;                 // earlier levels' axis products
     T acc[4] = {T(0), T(0), T(0), T(0)};
-    T w[4];
-    if (gw < wf) {
-        const size_t e = (size_t)(wb + gw) * 32 + lane;
+    T w[4] = {T(0), T(0), T(0), T(0)};
+    const int S = max(1, (wf + ng) / max(wf, 1)), q = gw / S;  // framed warp q at position q S
+    if (wf > 0 && gw % S == 0 && q < wf) {
+        const int fw = wb + q;
+        const size_t e = (size_t)fw * 32 + lane;
         const int pos = d.pk_pt[dir][e];  // sweep position of the slot's point, -1: padding
         const int k = pos >= 0 ? (FWD ? d.sw_fwd : d.sw_bwd)[pos] : 0;
         const bool live = pos >= 0 && !frozen(d, k);
@@ -1020,7 +1013,7 @@ __global__ void __launch_bounds__(256) k_sweep_packed(Dev d, StateSet st, int wb
         }
         // segmented suffix sum: lane l adds lane l + o when both hold the same
         // point; the warp's longest list bounds the steps (warp-uniform)
-        const int steps = d.pk_steps[dir][wb + gw];
+        const int steps = d.pk_steps[dir][fw];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             if (o >= (1 << steps)) break;
@@ -1033,21 +1026,31 @@ __global__ void __launch_bounds__(256) k_sweep_packed(Dev d, StateSet st, int wb
                 for (int c = 0; c < 4; c++) acc[c] += v[c];
             }
         }
-        const int prev = __shfl_up_sync(kFull, pos, 1);
-        if (live && (lane == 0 || prev != pos)) {
-            sweep_point<FWD, T>(d, st, sb, k, wall, e1x, e1y, e2x, e2y, acc, w);
-            store_axis_products<JVP, T>(d, st, Tb, sb, w, k);
-        }
+        // the point's lanes (consecutive; padding lanes form their own group):
+        // the first finishes the point, then lane r of the point's seg lanes
+        // forms the products r, r + seg, ... of the new increment
+        const unsigned m = __match_any_sync(kFull, pos);
+        const int head = __ffs(m) - 1, seg = __popc(m), r = lane - head;
+        if (live && r == 0) sweep_point<FWD, T>(d, st, sb, k, wall, e1x, e1y, e2x, e2y, acc, w);
+#pragma unroll
+        for (int c = 0; c < 4; c++) w[c] = __shfl_sync(kFull, w[c], head);
+        if (live)
+            for (int cb = r; cb < 4; cb += seg) store_axis_product<JVP, T>(d, st, Tb, sb, w, k, cb);
         return;
     }
-    const int g = g0 + gw - wf;
-    const int k = d.lp_k[dir][32 * g + lane];
-    if (k < 0 || frozen(d, k)) return;
-    const int len = d.lp_len[dir][32 * g + lane];
+    // interior points: kLanesPerPoint lanes per point, lane s taking the
+    // point's slots j = s (mod kLanesPerPoint) in order; a butterfly over the
+    // point's lanes gives every one of them the same sum (each addition has
+    // the same two operands in either order)
+    const int g = g0 + gw - min(wf, q + 1);  // the framed positions up to gw left out
+    const int p = lane / kLanesPerPoint, s = lane % kLanesPerPoint;
+    const int k = d.lp_k[dir][kPointsPerWarp * g + p];
+    const bool live = k >= 0 && !frozen(d, k);
+    const int len = live ? d.lp_len[dir][kPointsPerWarp * g + p] : 0;
     const size_t base = (size_t)d.lp_goff[dir][g] + lane;
-#pragma unroll 4
-    for (int j = 0; j < len; j++) {
-        const size_t e = base + 32 * (size_t)j;
+#pragma unroll 2
+    for (int j = s; j < len; j += kLanesPerPoint) {
+        const size_t e = base + 32 * (size_t)(j / kLanesPerPoint);
         const int i = d.lp_nbr[dir][e], mb = d.lp_mb[dir][e];
         T J[4];
         if (mb & 3) {
@@ -1063,8 +1066,19 @@ __global__ void __launch_bounds__(256) k_sweep_packed(Dev d, StateSet st, int wb
             for (int c = 0; c < 4; c++) acc[c] = fma(w2, J[c], acc[c]);
         }
     }
-    sweep_point<FWD, T>(d, st, sb, k, false, 1.0, 0.0, 0.0, 1.0, acc, w);
-    store_axis_products<JVP, T>(d, st, Tb, sb, w, k);
+#pragma unroll
+    for (int o = 1; o < kLanesPerPoint; o <<= 1) {
+#pragma unroll
+        for (int c = 0; c < 4; c++) acc[c] += __shfl_xor_sync(kFull, acc[c], o);
+    }
+    // the point's first lane finishes it; each of its lanes then forms one of
+    // the four axis products of the new increment
+#pragma unroll
+    for (int c = 0; c < 4; c++) w[c] = T(0);
+    if (live && s == 0) sweep_point<FWD, T>(d, st, sb, k, false, 1.0, 0.0, 0.0, 1.0, acc, w);
+#pragma unroll
+    for (int c = 0; c < 4; c++) w[c] = __shfl_sync(kFull, w[c], lane - s);
+    if (live) store_axis_product<JVP, T>(d, st, Tb, sb, w, k, s);
 }
 
 // ---------------------------------------------------------------------------
