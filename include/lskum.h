@@ -330,9 +330,13 @@ lskum_status lskum_time_phases(lskum_ctx *ctx, int32_t reps, double *ms);
  * results do not depend on it beyond the order of floating-point sums): for
  * every threads-per-point count {1,2,4,8} of the q-derivative and residual
  * kernels and lanes-per-point count {2,4,8} of the sweep kernels, plus the
- * packed sweep form (sweep_lanes = 32: one lane per list slot, whole points
- * packed into warps; available when no point has more than 32 lower or
- * upper neighbours), re-capture
+ * packed sweep form (sweep_lanes = 32: each point forms the axis Jacobian
+ * products of its new increment once and interior points gather their
+ * neighbours' products, four lanes per interior point; wall points, and
+ * outer points under the kinetic far field, form their products per slot in
+ * their own frame, one lane per list slot with whole points packed into
+ * warps; available when no point has more than 32 lower or upper
+ * neighbours), re-capture
  * the iteration graphs, run one warm-up iteration and time `trial_iters`
  * iterations between CUDA events on the context's stream; keep the fastest
  * shape.  The state, the per-case counters, stop flags and histories are
