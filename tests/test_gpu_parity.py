@@ -373,9 +373,11 @@ def test_four_component_residual_history():
 
 @pytest.mark.parametrize("jvp", [0, 1])
 def test_packed_sweeps_match_oracle(jvp):
-    """The packed sweep form (sweep_lanes = 32: one lane per list slot, whole
-    points packed into warps, segmented sums): one iteration's increments and
-    a 30-iteration history against the oracle, FP64 and mixed precision."""
+    """The packed sweep form (sweep_lanes = 32: each point's axis Jacobian
+    products formed once and gathered by interior points, four lanes per
+    interior point; wall points one lane per slot in packed warps with
+    segmented sums): one iteration's increments and a 30-iteration history
+    against the oracle, FP64 and mixed precision."""
     lk = _lskum()
     c = cached_cloud("jit64x32", CLOUDS["jit64x32"])
     o = O.Oracle(c)
