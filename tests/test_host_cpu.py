@@ -108,7 +108,8 @@ def test_host_layout_invariants_hold(lk, ordering):
     equals the oracle's Alg. 5."""
     import oracle as O
     clouds = [cg.naca0012_block(40, 16), cg.naca0012_jittered(64, 32, seed=12),
-              cg.cartesian_box(7, 7, seed=2, wall_bottom=True), cg.naca0012_jittered(200, 80, seed=5)]
+              cg.cartesian_box(7, 7, seed=2, wall_bottom=True), cg.naca0012_jittered(200, 80, seed=5),
+              cg.cartesian_box(9, 8, seed=3)]  # no wall: the packed sweeps' levels without framed points
     for c in clouds:
         nc, nl = lk.validate([c], [(0.5, 1.0)], ordering=ordering)
         assert nc == O.Oracle(c).ncolours
