@@ -4,7 +4,9 @@
 //               step and scalar LU-SGS diagonal (Eq. 26, 33-34), density-norm partials
 //   k_norm_*    per-case residual norms, histories and stopping tests
 //   k_sweep     one colour level of the forward or backward LU-SGS sweep (Eq. 27) with
-//               exact (forward-mode AD) or increment (Eq. 28) Jacobian-vector products
+//               exact (forward-mode AD) or increment (Eq. 28) Jacobian-vector products;
+//               k_sweep_packed: the same level with each point's axis products formed
+//               once and gathered by its neighbours
 //   k_update    U += dU, wall projection, q-variables and the per-point primal
 //               quantities the next iteration's sweeps need
 //
@@ -15,9 +17,10 @@
 // neighbour slot; the inverse of Eq. 14 uses beta^(-5/2) instead of a log;
 // the sweeps' Jacobian products reuse erf/exp of each point's own state,
 // computed once per iteration by k_update, so an exact product has no
-// transcendental call at all; exp and A = (1 + s erf S)/2 are the kernels' own
+// transcendental call at all, and a neighbour's product along an axis is
+// formed once and gathered; exp and A = (1 + s erf S)/2 are the kernels' own
 // (lskum_fastmath.cuh), which share exp(-S^2) and keep index work off the
-// FP64 pipe.
+// FP64 pipe, as are signs and multiplications by 2 and 1/2 (integer steps).
 #include "lskum_internal.h"
 
 #include <cstdint>
