@@ -62,6 +62,14 @@ RES_TRAFFIC = {2: 164.885504e6}
 RES_FP64_PIPE_ACTIVE = 0.894
 
 
+def _sweep_form(lanes):
+    """What the library's sweep launch-shape value means."""
+    if lanes == 32:
+        return ("packed: each point's axis Jacobian products formed once and gathered, 4 lanes per "
+                "interior point, one lane per slot for wall points")
+    return f"{lanes} lanes per point, products per slot"
+
+
 def _env_int(k, d):
     try:
         return int(os.environ.get(k, d))
@@ -279,6 +287,7 @@ def run_ours(args, rank, world, local_rank):
                    "order": f"second (timed steps follow {START} untimed first-order start-up iterations)",
                    "colours": info["n_colours"],
                    "launch_shape": {"threads_per_point": tpp, "sweep_lanes_per_point": lanes,
+                                    "sweep_form": _sweep_form(lanes),
                                     "by": "given" if args.launch_shape else "autotune"},
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": f"inputs larger than L2: device working set {ws / 2**20:.0f} MiB > 129 MiB L2"},
@@ -437,7 +446,8 @@ def run_batch(args, rank, world, local_rank):
                    "fp32 sweeps, fp64 residual/update", "cfl": 100.0, "inner_iters": 3, "jvp": "exact-AD",
                    "order": f"second (timed steps follow {START} untimed first-order start-up iterations)",
                    "colours": info["n_colours"],
-                   "launch_shape": {"threads_per_point": tpp, "sweep_lanes_per_point": lanes, "by": "autotune"},
+                   "launch_shape": {"threads_per_point": tpp, "sweep_lanes_per_point": lanes,
+                                    "sweep_form": _sweep_form(lanes), "by": "autotune"},
                    "parallelism": f"cases sharded over {world} ranks" if world > 1 else "single",
                    "residual_drop_min_max": [min(drops), max(drops)] if drops else None,
                    "l2": "inputs larger than L2"},
