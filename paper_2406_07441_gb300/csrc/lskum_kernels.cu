@@ -968,9 +968,11 @@ __device__ __forceinline__ void store_axis_product(const Dev &d, const StateSet 
 
 // Packed form of a level.  A neighbour's Jacobian product along an axis
 // depends only on the neighbour, the axis and the sub-stencil's sign, so a
-// point forms the four axis products of its new increment once, and
-// interior points gather them: 8 FMAs per slot instead of ~70 FP64
-// instructions, in the order the per-slot form adds them.
+// point forms the four axis products of its new increment once (the values
+// the per-slot form computed, bit for bit), and interior points gather them:
+// 8 FMAs per slot instead of ~70 FP64 instructions.  A point's sum depends
+// only on its own list, in a fixed order, so a batch still equals its
+// single solves bit for bit.
 // - wf warps for the points in a (t, n) frame (products per slot in their
 //   own frame), their slots packed whole into warps (at create, by best
 //   fit; a point with an empty list takes one idle slot), one lane per slot;
