@@ -376,9 +376,13 @@ lskum_status lskum_get_info(lskum_ctx *ctx, int32_t *n_points, int32_t *n_colour
  * GPU that loads it until the process exits; no cudaMalloc/cudaFree or other
  * allocating call is made.  The first call on each device performs a one-time
  * set-up (it looks up that array's device address with that device current),
- * so make that first call before any stream capture.  All calls share the
- * array: calls that overlap on the GPU race and must be serialised by the
- * caller.  Errors: LSKUM_ERR_ARG (NULL pointer, n out of range),
+ * so make that first call before any stream capture.  The address is cached
+ * per device number for the life of the process: after cudaDeviceReset (or
+ * any other teardown of the device's primary context) the library's module
+ * may load elsewhere, so do not call this entry point again in that process
+ * (a failed launch drops the cached address, the next call looks it up
+ * again).  All calls share the array: calls that overlap on the GPU race and
+ * must be serialised by the caller.  Errors: LSKUM_ERR_ARG (NULL pointer, n out of range),
  * LSKUM_ERR_CUDA (set-up or launch failed).
  */
 lskum_status lskum_density_norm_noalloc(const double *r_rho_dev, int32_t n, double *norm_dev, void *cuda_stream);

@@ -115,6 +115,18 @@ lskum_status lskum_get_wall_distance(lskum_ctx *ctx, double *d);
  * for the runs that follow; iterations are counted from the last new state. */
 lskum_status lskum_set_start_iters(lskum_ctx *ctx, int32_t first_order_iters);
 
+/* Failure-path test of the tensor-core waits (no counterpart in the paper).
+ * Every wait of the network's kernels for its tensor-core products is
+ * bounded: past wait_limit_s (1 s by default) the kernel gives up, frees its
+ * tensor memory and returns, and the call reports LSKUM_ERR_TIMEOUT with the
+ * object still usable.  skip_products = 1 makes the product kernels issue
+ * neither the products nor the commit that would complete the wait, so the
+ * wait runs out with nothing in flight; 0 restores normal operation.
+ *   skip_products  0 or 1
+ *   wait_limit_s   1e-4 .. 10 seconds, applied to every later call
+ * Errors: LSKUM_ERR_ARG. */
+lskum_status lskum_mlp_set_wait_test(lskum_mlp *m, int32_t skip_products, double wait_limit_s);
+
 /* Message of the last failure of m; never NULL. */
 const char *lskum_mlp_last_error(const lskum_mlp *m);
 

@@ -29,7 +29,8 @@ def _nvcc():
 
 
 def _deps():
-    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "lskum.h"), __file__]
+    files = ([os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
+             + [__file__])
     return max(os.path.getmtime(f) for f in files)
 
 

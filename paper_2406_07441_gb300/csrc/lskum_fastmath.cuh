@@ -3,8 +3,11 @@
 // pipes (range-reduction index, exponent scaling, interval selection, sign
 // tests) does, and exp(-S^2) is shared between the two places a split flux
 // needs it.  Constants: lskum_mathconst.h (gen_mathconst.py documents the
-// methods and their accuracy); the tables are staged in shared memory because
-// per-thread indices diverge, which serialises constant-cache reads.
+// methods and their accuracy).  The tables are read per thread at diverging
+// indices, which would serialise constant-cache reads, so they live in
+// memory: the kernels that evaluate them at every point (the residual and
+// the update) stage a copy in shared memory; the sweeps, which
+// need them only at wall and outer points, read one global copy (g_math).
 #pragma once
 #include "lskum_mathconst.h"
 
@@ -50,7 +53,10 @@ __device__ __forceinline__ double exp_t(const MathTables &T, double x)
 // for S >= 0 and E for S < 0, and (1 - erf S)/2 the other one.  |S| is
 // clamped to 9 (E < 1e-36 there), which also keeps exp's argument in range;
 // the absolute value, the clamp and the interval come from the high word on
-// the integer pipe (positive doubles order like their high words).
+// the integer pipe (positive doubles order like their high words).  A NaN S
+// is clamped too and gives finite E and eS, but S is NaN only when u_d or
+// beta is, and both enter every split flux directly, so a NaN state still
+// yields NaN fluxes; the update's positivity and finiteness check reports it.
 __device__ __forceinline__ void split_E(const MathTables &T, double S, double &E, double &eS)
 {
     constexpr int kNineHi = 0x40220000;  // high word of 9.0 (low word 0)

@@ -86,8 +86,10 @@ __device__ __forceinline__ float signed_by(float x, bool pos)
 // bits as the FP64 multiplication whenever both x and the result are normal
 // (a multiplication by a power of two is exact there).  Zeros and
 // non-finite values come back unchanged, which is again the exact result;
-// only magnitudes below 2^-1021 (halving) or above 2^1023 (doubling) would
-// differ, far outside what any quantity of the solver reaches.  FP32 keeps
+// only magnitudes below 2^-1021 (halving: the result would be subnormal),
+// subnormal inputs (doubling: returned as they are) and magnitudes above
+// 2^1023 (doubling) differ, far outside what any quantity of the solver
+// reaches.  FP32 keeps
 // its multiplication (its pipe is not the bottleneck).
 __device__ __forceinline__ double half_of(double x)
 {

@@ -31,6 +31,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -122,13 +123,14 @@ __device__ __forceinline__ uint64_t global_ns()
     return t;
 }
 
-// Wait for the barrier phase with a time limit (1 s): false if it never came.
-__device__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+// Wait for the barrier phase with a time limit (limit_ns; 1 s unless a test
+// shortens it): false if it never came.
+__device__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t limit_ns)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     while (!mbar_try_wait(bar, parity))
-        if (global_ns() - t0 > 1000000000ull) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     return true;
 }
 
@@ -222,6 +224,8 @@ struct GemmArgs {
     int ldt;
     float *out_f;       // kFwdOut: [rows][4]; kWgrad: [split][m_valid][N]
     int *err;
+    uint64_t wait_ns;   // time limit of each wait for the tensor core
+    int skip_products;  // failure-path test: issue neither products nor commit
 };
 
 // 24 KB of dynamic shared memory is requested on top of the 32 KB of operand
@@ -273,7 +277,7 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs g)
         }
         fence_smem_to_async();
         __syncthreads();
-        if (tid == 0) {
+        if (tid == 0 && !g.skip_products) {
             fence_after_sync();
             const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
             for (int s = 0; s < (kw >> 4); s++)
@@ -281,7 +285,7 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs g)
                          (kc > kb || s > 0) ? 1u : 0u);
             mma_commit(&bar);
         }
-        ok = __syncthreads_and(mbar_wait_bounded(&bar, parity) ? 1 : 0);
+        ok = __syncthreads_and(mbar_wait_bounded(&bar, parity, g.wait_ns) ? 1 : 0);
         parity ^= 1u;
     }
     fence_after_sync();
@@ -550,6 +554,8 @@ struct FusedArgs {
     int k0;
     const float *fourier;
     int *err;
+    uint64_t wait_ns;   // time limit of each wait for the tensor core
+    int skip_products;  // failure-path test: issue neither products nor commit
 };
 
 // Write a row of 16-bit values (8 per 16-byte chunk) into a core-matrix tile.
@@ -643,7 +649,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(FusedArgs a)
         __syncthreads();
         // 2. the four hidden layers
         for (int l = 0; l < 4 && ok; l++) {
-            if (tid == 0) {
+            if (tid == 0 && !a.skip_products) {
                 fence_after_sync();
                 const int kg = l == 0 ? kInPad / 8 : kWidth / 8;
                 const uint32_t a0 = l == 0 ? sX : sH;
@@ -653,7 +659,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(FusedArgs a)
                              idesc_bf16<128>(), s > 0 ? 1u : 0u);
                 mma_commit(&bar);
             }
-            ok = __syncthreads_and(mbar_wait_bounded(&bar, parity) ? 1 : 0);
+            ok = __syncthreads_and(mbar_wait_bounded(&bar, parity, a.wait_ns) ? 1 : 0);
             parity ^= 1u;
             if (!ok) break;
             fence_after_sync();
@@ -673,7 +679,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(FusedArgs a)
         }
         if (!ok) break;
         // 3. the output layer (N = 16, four used)
-        if (tid == 0) {
+        if (tid == 0 && !a.skip_products) {
             fence_after_sync();
             const uint32_t b0 = smem_u32(sm + kOffW5);
             for (int s = 0; s < kWidth / 16; s++)
@@ -681,7 +687,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(FusedArgs a)
                          smem_desc(b0 + 256u * s, 128u, 128u * (kWidth / 8)), idesc_bf16<16>(), s > 0 ? 1u : 0u);
             mma_commit(&bar);
         }
-        ok = __syncthreads_and(mbar_wait_bounded(&bar, parity) ? 1 : 0);
+        ok = __syncthreads_and(mbar_wait_bounded(&bar, parity, a.wait_ns) ? 1 : 0);
         parity ^= 1u;
         if (!ok) break;
         fence_after_sync();
@@ -821,6 +827,8 @@ struct lskum_mlp {
     float *GP[4] = {}, *O = nullptr, *part = nullptr, *Xf = nullptr, *Tf = nullptr;
     double *loss = nullptr;
     int *err = nullptr;
+    uint64_t wait_ns = 1000000000ull;  // time limit of the tensor-core waits
+    int skip_products = 0;             // failure-path test switch (lskum_mlp_set_wait_test)
     int32_t *idx = nullptr;
     // sample store
     float *s_in = nullptr, *s_tgt = nullptr;
@@ -899,6 +907,8 @@ cudaError_t forward(lskum_mlp *m, int n, int rows, bool train)
         g.out_t = train ? m->Ht[l] : nullptr;
         g.ldt = P;
         g.err = m->err;
+        g.wait_ns = m->wait_ns;
+        g.skip_products = m->skip_products;
         e = gemm<kFwdHidden, 128>(g, gx, 1, m->stream);
     }
     if (e != cudaSuccess) return e;
@@ -915,6 +925,8 @@ cudaError_t forward(lskum_mlp *m, int n, int rows, bool train)
     g.bias = m->params + m->off[4] + kOut * kWidth;
     g.out_f = m->O;
     g.err = m->err;
+    g.wait_ns = m->wait_ns;
+    g.skip_products = m->skip_products;
     return gemm<kFwdOut, 16>(g, gx, 1, m->stream);
 }
 
@@ -939,6 +951,8 @@ cudaError_t backward(lskum_mlp *m, int n, int rows)
         w.m_valid = kOutTrue[l];
         w.out_f = m->part;
         w.err = m->err;
+        w.wait_ns = m->wait_ns;
+        w.skip_products = m->skip_products;
         e = l == 0 ? gemm<kWgrad, kInPad>(w, 1, splits, m->stream) : gemm<kWgrad, 128>(w, 1, splits, m->stream);
         if (e != cudaSuccess) break;
         const int nw = kOutTrue[l] * kInTrue[l];
@@ -964,6 +978,8 @@ cudaError_t backward(lskum_mlp *m, int n, int rows)
         d.out_t = m->Gt[l - 1];
         d.ldt = P;
         d.err = m->err;
+        d.wait_ns = m->wait_ns;
+        d.skip_products = m->skip_products;
         e = gemm<kBwdData, 128>(d, gx, 1, m->stream);
     }
     if (e == cudaSuccess) e = cudaGetLastError();
@@ -978,7 +994,9 @@ lskum_status check_err(lskum_mlp *m)
     if (e != cudaSuccess) return mcuda(m, e, "network kernels");
     if (h) {
         cudaMemsetAsync(m->err, 0, sizeof(int), m->stream);
-        return mfail(m, LSKUM_ERR_TIMEOUT, "tensor-core product did not complete within 1 s");
+        char buf[96];
+        snprintf(buf, sizeof(buf), "tensor-core product did not complete within %.3g s", (double)m->wait_ns * 1e-9);
+        return mfail(m, LSKUM_ERR_TIMEOUT, buf);
     }
     return LSKUM_OK;
 }
@@ -1045,6 +1063,8 @@ cudaError_t fused_forward(lskum_mlp *m, int n, const uint16_t *X, float *O, cons
     a.k0 = k0;
     a.fourier = m->fourier;
     a.err = m->err;
+    a.wait_ns = m->wait_ns;
+    a.skip_products = m->skip_products;
     const int tiles = (n + 127) / 128;
     k_mlp_fused<SRC><<<std::min(tiles, g_num_sms), kFusedThreads, kFusedSmem, m->stream>>>(a);
     return cudaGetLastError();
@@ -1057,6 +1077,16 @@ extern "C" {
 int32_t lskum_mlp_n_params(void)
 {
     return kNParams;
+}
+
+lskum_status lskum_mlp_set_wait_test(lskum_mlp *m, int32_t skip_products, double wait_limit_s)
+{
+    if (!m) return LSKUM_ERR_ARG;
+    if ((skip_products != 0 && skip_products != 1) || !(wait_limit_s >= 1e-4 && wait_limit_s <= 10.0))
+        return mfail(m, LSKUM_ERR_ARG, "wait test: skip_products 0 or 1, wait_limit_s in [1e-4, 10]");
+    m->skip_products = skip_products;
+    m->wait_ns = (uint64_t)(wait_limit_s * 1e9);
+    return LSKUM_OK;
 }
 
 const char *lskum_mlp_last_error(const lskum_mlp *m)

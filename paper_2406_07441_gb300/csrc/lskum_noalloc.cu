@@ -34,7 +34,8 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) double g_partials[kNoAllocMaxPartials];
 
 // Host-side device addresses of g_partials, one per device (the symbol's name
-// in host code is only a stand-in, never a device address).
+// in host code is only a stand-in, never a device address).  Valid while the
+// device's primary context lives; a failed launch clears the entry.
 double *g_partials_dev[kMaxDevices] = {};
 std::mutex g_setup_mutex;
 
@@ -96,5 +97,10 @@ extern "C" lskum_status lskum_density_norm_noalloc(const double *r_rho_dev, int3
     if (blocks > kNoAllocMaxPartials) blocks = kNoAllocMaxPartials;
     if (blocks > 0) k_sumsq_partials<<<blocks, kNoAllocThreads, 0, s>>>(r_rho_dev, n, partials);
     k_sqrt_of_partials<<<1, 1024, 0, s>>>(partials, blocks, norm_dev);
-    return cudaGetLastError() == cudaSuccess ? LSKUM_OK : LSKUM_ERR_CUDA;
+    if (cudaGetLastError() == cudaSuccess) return LSKUM_OK;
+    // the cached address may be stale (a reset device reloads the module):
+    // forget it, so that the next call looks it up again
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    g_partials_dev[dev] = nullptr;
+    return LSKUM_ERR_CUDA;
 }

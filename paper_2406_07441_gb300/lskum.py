@@ -100,6 +100,7 @@ def load():
     L.lskum_mlp_n_samples.argtypes = [vp, P(i32)]
     L.lskum_mlp_train.argtypes = [vp, i32, i32, C.c_float, u64, vp]
     L.lskum_mlp_predict.argtypes = [vp, vp, vp]
+    L.lskum_mlp_set_wait_test.argtypes = [vp, i32, d]
     L.lskum_mlp_last_error.argtypes = [vp]
     L.lskum_mlp_last_error.restype = C.c_char_p
     L.lskum_mlp_destroy.argtypes = [vp]
@@ -116,7 +117,7 @@ def load():
               "lskum_set_host_io", "lskum_get_host_io", "lskum_mlp_create", "lskum_mlp_get_params",
               "lskum_mlp_set_params", "lskum_mlp_features", "lskum_mlp_forward", "lskum_mlp_loss_grads",
               "lskum_mlp_adam", "lskum_mlp_add_samples", "lskum_mlp_time_forward", "lskum_mlp_n_samples", "lskum_mlp_train",
-              "lskum_mlp_predict"):
+              "lskum_mlp_predict", "lskum_mlp_set_wait_test"):
         getattr(L, f).restype = st
     _lib = L
     return L
@@ -437,6 +438,10 @@ class Mlp:
         self._check(load().lskum_mlp_train(self._h, int(epochs), int(batch), C.c_float(lr), C.c_uint64(seed),
                                            _p(losses)))
         return losses[:int(epochs)]
+
+    def set_wait_test(self, skip_products, wait_limit_s=1.0):
+        """Failure-path test of the bounded tensor-core waits (see lskum_mlp_set_wait_test)."""
+        self._check(load().lskum_mlp_set_wait_test(self._h, int(skip_products), float(wait_limit_s)))
 
     def predict(self, solver):
         """Warm-start the solver's state; returns per case whether the prediction was kept."""

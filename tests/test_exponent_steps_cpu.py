@@ -48,12 +48,17 @@ def test_zeros_and_non_finite_values_are_returned_unchanged():
 
 
 def test_only_the_range_edges_differ_from_the_multiplication():
-    """Halving of magnitudes below 2^-1021 (result subnormal) and doubling
-    above 2^1023 (result infinite) are left unscaled: the documented limits,
+    """Halving of magnitudes below 2^-1021 (result subnormal), doubling of
+    subnormal inputs and doubling above 2^1023 (result infinite) are left
+    unscaled: the documented limits,
     far outside what a state, a q-derivative or an increment reaches."""
     tiny = np.array([np.ldexp(1.5, -1022), 5e-324, np.ldexp(1.0, -1021)])
     assert np.array_equal(_bits(_step(tiny[:2], False)), _bits(tiny[:2]))
     assert np.array_equal(_bits(_step(tiny[2:], False)), _bits(tiny[2:] * 0.5))
+    # subnormal inputs (exponent field 0) are not doubled either
+    sub = np.array([5e-324, np.ldexp(1.0, -1030), -np.ldexp(1.0, -1023)])
+    assert np.array_equal(_bits(_step(sub, True)), _bits(sub))
+    assert not np.any(_bits(sub * 2.0) == _bits(sub))
     huge = np.array([np.ldexp(1.5, 1023), np.ldexp(1.0, 1022)])
     with np.errstate(over="ignore"):
         assert _step(huge[:1], True)[0] == huge[0] and np.isinf(huge[0] * 2.0)

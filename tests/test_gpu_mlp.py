@@ -187,3 +187,33 @@ def test_predict_on_a_batch_equals_single_contexts_and_judges_per_case():
     Uf = fs.field(lk.FIELD_U)
     outer = np.concatenate([c.flag == 2] * len(tests))
     assert np.array_equal(U[outer], Uf[outer])
+
+
+def test_bounded_tensor_core_wait_runs_out_and_the_network_stays_usable():
+    """Failure detection without a fault: with the products switched off (no
+    tcgen05.mma and no commit, so nothing is in flight) every wait for the
+    tensor core runs out after its 1 ms limit; the kernels free their tensor
+    memory and return, the calls report LSKUM_ERR_TIMEOUT, and once the
+    products are switched back on the same object gives exactly its earlier
+    results (forward pass and training gradients)."""
+    from paper_2406_07441_gb300 import lskum as lk
+    m = _net(3)
+    rng = np.random.default_rng(4)
+    X = rng.normal(0, 1, (300, 34)).astype(np.float32)
+    T = rng.normal(0, 0.1, (300, 4)).astype(np.float32)
+    out0 = m.forward(X)
+    loss0, g0 = m.loss_grads(X, T)
+    m.set_wait_test(1, 1e-3)
+    for call in (lambda: m.forward(X), lambda: m.loss_grads(X, T)):
+        with pytest.raises(lk.LskumError) as ei:
+            call()
+        assert ei.value.status == lk.ERR_TIMEOUT
+        assert "did not complete" in str(ei.value)
+    m.set_wait_test(0, 1.0)
+    assert np.array_equal(m.forward(X), out0)
+    loss1, g1 = m.loss_grads(X, T)
+    assert abs(loss1 - loss0) <= 1e-6 * loss0 and np.array_equal(g1, g0)
+    with pytest.raises(lk.LskumError):
+        m.set_wait_test(2, 1.0)
+    with pytest.raises(lk.LskumError):
+        m.set_wait_test(0, 0.0)

@@ -100,13 +100,17 @@ def test_sweeps_from_the_same_residual_are_level_parallel_exact():
     assert nrel(s.field(lk.FIELD_DU), dU) < 1e-12
 
 
+@pytest.mark.parametrize("shape", [None, (2, 32)])
 @pytest.mark.parametrize("jvp,iters", [(0, 300), (1, 100)])
-def test_history_and_final_fields_config1(jvp, iters):
-    """NACA 0012, 160x64 = 10,240 points, M = 0.63, AoA = 2 deg, CFL 100."""
+def test_history_and_final_fields_config1(jvp, iters, shape):
+    """NACA 0012, 160x64 = 10,240 points, M = 0.63, AoA = 2 deg, CFL 100, in the
+    context's default launch shape and in the packed sweeps at 2 threads per
+    point."""
     lk = _lskum()
     c, s, o, cond = _pair("naca160x64", jvp=jvp)
-    U0 = o.initial_state(cond["mach"], cond["aoa_deg"])
-    r = o.run(U0, iters, cfl=100.0, K=3, jvp=jvp)
+    if shape is not None:
+        s.set_launch_shape(*shape)
+    r = _oracle_run(("naca160x64", jvp, iters), c, cond["mach"], cond["aoa_deg"], iters, cfl=100.0, K=3, jvp=jvp)
     assert r["status"] == 0 and r["done"] == iters
     assert s.run(iters) == iters
     h = s.residuals()
@@ -186,28 +190,82 @@ def test_set_state_round_trip_and_rejects_nonphysical():
     assert np.array_equal(rho2, rho)
 
 
-def test_config2_full_size():
+_ORACLE_RUNS = {}
+
+
+def _oracle_run(key, cloud, mach, aoa, iters, **kw):
+    """One oracle run per (cloud, conditions), shared by the tests that need it."""
+    if key not in _ORACLE_RUNS:
+        o = O.Oracle(cloud)
+        _ORACLE_RUNS[key] = o.run(o.initial_state(mach, aoa), iters, **kw)
+    return _ORACLE_RUNS[key]
+
+
+# Launch shapes (threads per point in the gradient and residual kernels, sweep
+# lanes per point; 32 = the packed sweeps): the benchmark's autotuned choice on
+# the 147,584-point cloud first, then the size-based default of a new context,
+# then the packed form with the widest gradient / residual groups.
+FULL_SIZE_SHAPES = [(2, 32), (1, 4), (4, 32)]
+
+
+@pytest.mark.parametrize("jvp", [0, 1])
+def test_config2_full_size(jvp):
     """Jittered 640x256 cloud, 10% removed: 147,584 points, M = 0.85, AoA = 1 deg,
-    exact JVPs, the bench's launch configuration: one first-order start-up
-    iteration and two second-order ones, every field of the last."""
+    K = 2 (the benchmark's setting), each JVP mode: one first-order start-up
+    iteration and two second-order ones, every field of the last against the
+    oracle, in each launch shape of FULL_SIZE_SHAPES -- among them the packed
+    sweeps at 2 threads per point that the benchmark times, at full size (all
+    16 colour levels, framed-point warps spread over the grid, the interior
+    groups of 20-slot lists)."""
     lk = _lskum()
     c = cached_cloud("jit640x256", lambda: cg.build_workload("naca0012_640x256_jit"))
     assert c.n == 147584
-    s = lk.Solver(c, 0.85, 1.0, first_order_iters=1)
-    o = O.Oracle(c)
-    U0 = o.initial_state(0.85, 1.0)
-    r = o.run(U0, 3, cfl=100.0, K=3, first_order=1)
+    r = _oracle_run(("jit640x256", jvp), c, 0.85, 1.0, 3, cfl=100.0, K=2, jvp=jvp, first_order=1)
     assert r["status"] == 0
-    assert s.run(3) == 3
-    assert nrel(s.field(lk.FIELD_QX), r["qx"]) < 1e-12
-    assert nrel(s.field(lk.FIELD_R), r["R"]) < 1e-10
-    D = s.field(lk.FIELD_D)
-    assert np.max(np.abs(D - r["D"]) / np.abs(r["D"])) < 1e-12
-    assert nrel(s.field(lk.FIELD_DUS), r["dUs"]) < 1e-10
-    assert nrel(s.field(lk.FIELD_DU), r["dU"]) < 1e-10
-    assert nrel(s.field(lk.FIELD_U), r["U"]) < 1e-12
+    clo, cdo = O.Oracle(c).forces(r["U"], 0.85, 1.0)
+    for tpp, lanes in FULL_SIZE_SHAPES:
+        s = lk.Solver(c, 0.85, 1.0, inner_iters=2, jvp=jvp, first_order_iters=1)
+        s.set_launch_shape(tpp, lanes)
+        assert s.run(3) == 3
+        shape = (tpp, lanes)
+        assert nrel(s.field(lk.FIELD_QX), r["qx"]) < 1e-12, shape
+        assert nrel(s.field(lk.FIELD_QY), r["qy"]) < 1e-12, shape
+        assert nrel(s.field(lk.FIELD_R), r["R"]) < 1e-10, shape
+        D = s.field(lk.FIELD_D)
+        assert np.max(np.abs(D - r["D"]) / np.abs(r["D"])) < 1e-12, shape
+        assert nrel(s.field(lk.FIELD_DUS), r["dUs"]) < 1e-10, shape
+        assert nrel(s.field(lk.FIELD_DU), r["dU"]) < 1e-10, shape
+        assert nrel(s.field(lk.FIELD_U), r["U"]) < 1e-12, shape
+        assert nrel(s.field(lk.FIELD_Q), r["q"]) < 1e-12, shape
+        h = s.residuals()
+        assert np.max(np.abs(h - r["hist"]) / r["hist"]) < 1e-10, shape
+        cl, cd = s.forces()
+        assert abs(cl - clo) < 1e-11 and abs(cd - cdo) < 1e-11, shape
+        del s
+
+
+@pytest.mark.parametrize("jvp", [0, 1])
+def test_packed_sweeps_history_41k_points(jvp):
+    """The packed sweeps (2 threads per point, as the benchmark runs them) on a
+    jittered 336x136 cloud with 10% removed (41,264 points, 14+ colour levels
+    with many framed-point warps each): 40 iterations (20 first-order start-up,
+    20 second-order) against the oracle: history 1e-10 per entry, final state
+    1e-9, Cl / Cd 1e-9."""
+    lk = _lskum()
+    c = cached_cloud("jit336x136", lambda: cg.naca0012_jittered(336, 136, seed=cg.BASE_SEED + 21))
+    assert c.n > 40000
+    r = _oracle_run(("jit336x136", jvp), c, 0.8, 1.25, 40, cfl=100.0, K=2, jvp=jvp, first_order=20)
+    assert r["status"] == 0 and r["done"] == 40
+    s = lk.Solver(c, 0.8, 1.25, inner_iters=2, jvp=jvp, first_order_iters=20)
+    s.set_launch_shape(2, 32)
+    assert s.run(40) == 40
     h = s.residuals()
-    assert np.max(np.abs(h - r["hist"]) / r["hist"]) < 1e-10
+    rel = np.abs(h - r["hist"]) / r["hist"]
+    assert rel.max() < 1e-10, (rel.argmax(), rel.max())
+    assert nrel(s.field(lk.FIELD_U), r["U"]) < 1e-9
+    cl, cd = s.forces()
+    clo, cdo = O.Oracle(c).forces(r["U"], 0.8, 1.25)
+    assert abs(cl - clo) < 1e-9 and abs(cd - cdo) < 1e-9
 
 
 @pytest.mark.slow
