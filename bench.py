@@ -206,6 +206,7 @@ def run_ours(args, rank, world, local_rank):
         s.set_launch_shape(tpp, lanes)
     else:
         tpp, lanes, _ = s.autotune(5)
+    info = s.info()  # launches per iteration in the chosen launch shape
     assert s.run(args.warmup) == args.warmup
     stream = torch.cuda.ExternalStream(s.stream())
     e0 = torch.cuda.Event(enable_timing=True)
@@ -379,6 +380,7 @@ def run_batch(args, rank, world, local_rank):
     nslots = int(sum(np.count_nonzero(_memberships(c)) for c in clouds))
     assert s.run(START) == START
     tpp, lanes, _ = s.autotune(5)
+    info = s.info()  # launches per iteration in the chosen launch shape
     assert s.run(args.warmup) == args.warmup
     it0 = [s.case_info(k)["iters"] for k in range(len(cases))]
     stream = torch.cuda.ExternalStream(s.stream())

@@ -263,13 +263,13 @@ def _csr(rows):
     return off.astype(np.int32), idx.astype(np.int32)
 
 
-def _stencils_ok_all(x, y, flag, nx, ny, rows, tol=1e-6, kinetic_outer=False):
-    """Vectorised well-posedness of every point's stencil (same tests as the
-    per-point functions above): boolean per point."""
+def _stencils_ok_all(x, y, flag, nx, ny, off, idx, tol=1e-6, kinetic_outer=False):
+    """Vectorised well-posedness of every point's stencil (CSR off / idx; same
+    tests as the per-point functions above): boolean per point."""
     n = x.shape[0]
-    deg = np.fromiter((len(r) for r in rows), dtype=np.int64, count=n)
+    deg = np.diff(off).astype(np.int64)
     owner = np.repeat(np.arange(n), deg)
-    nb = np.fromiter((q for r in rows for q in r), dtype=np.int64, count=int(deg.sum()))
+    nb = np.asarray(idx, dtype=np.int64)
     dx = x[nb] - x[owner]
     dy = y[nb] - y[owner]
     wall = flag == WALL
@@ -304,13 +304,15 @@ def _stencils_ok_all(x, y, flag, nx, ny, rows, tol=1e-6, kinetic_outer=False):
     return ok
 
 
-def _fix_stencils(x, y, flag, nx, ny, rows, cand_fn, body=None, kinetic_outer=False):
-    """Augment stencils (nearest-first candidates) until every sub-stencil is well posed."""
+def _fix_stencils(x, y, flag, nx, ny, off, idx, cand_fn, body=None, kinetic_outer=False):
+    """Augment stencils (nearest-first candidates) until every sub-stencil is
+    well posed.  CSR in (off, idx), CSR out, and the number of points augmented."""
     bad = 0
-    ok_all = _stencils_ok_all(x, y, flag, nx, ny, rows, kinetic_outer=kinetic_outer)
+    ok_all = _stencils_ok_all(x, y, flag, nx, ny, off, idx, kinetic_outer=kinetic_outer)
+    new_rows = {}
     for p in np.flatnonzero(~ok_all):
         p = int(p)
-        r = rows[p]
+        r = [int(q) for q in idx[off[p]:off[p + 1]]]
         dx = x[r] - x[p]
         dy = y[r] - y[p]
         kind = _kind(flag, p, kinetic_outer)
@@ -344,8 +346,27 @@ def _fix_stencils(x, y, flag, nx, ny, rows, cand_fn, body=None, kinetic_outer=Fa
                 break
         if not ok:
             raise RuntimeError(f"could not build a well-posed stencil at point {p}")
-        rows[p] = r
-    return rows, bad
+        new_rows[p] = r
+    if not new_rows:
+        return np.asarray(off, np.int32), np.asarray(idx, np.int32), bad
+    # splice the augmented rows into the CSR arrays
+    n = x.shape[0]
+    deg = np.diff(off).astype(np.int64)
+    deg_new = deg.copy()
+    changed = np.zeros(n, dtype=bool)
+    for p, r in new_rows.items():
+        deg_new[p] = len(r)
+        changed[p] = True
+    off_new = np.zeros(n + 1, dtype=np.int64)
+    off_new[1:] = np.cumsum(deg_new)
+    idx_new = np.empty(int(off_new[-1]), dtype=np.int64)
+    owner = np.repeat(np.arange(n), deg)
+    keep = ~changed[owner]
+    pos = np.arange(owner.shape[0]) - np.asarray(off, np.int64)[owner]
+    idx_new[off_new[owner[keep]] + pos[keep]] = np.asarray(idx, np.int64)[keep]
+    for p, r in new_rows.items():
+        idx_new[off_new[p]:off_new[p + 1]] = r
+    return off_new.astype(np.int32), idx_new.astype(np.int32), bad
 
 
 def _outer_normals(x, y):
@@ -392,18 +413,69 @@ def naca0012_block(n_i: int = 160, n_j: int = 64, kinetic_outer: bool = False) -
 
     widx = np.full(n, -1)
     widx[:n_i] = np.arange(n_i)
-    rows, bad = _fix_stencils(x, y, flag, nx, ny, rows, cand, body=(x[:n_i], y[:n_i], widx),
-                              kinetic_outer=kinetic_outer)
     off, idx = _csr(rows)
+    off, idx, bad = _fix_stencils(x, y, flag, nx, ny, off, idx, cand, body=(x[:n_i], y[:n_i], widx),
+                                  kinetic_outer=kinetic_outer)
     return Cloud(x, y, flag, nx, ny, off, idx,
                  dict(kind="block", n_i=n_i, n_j=n_j, augmented=bad, kinetic_outer=kinetic_outer))
+
+
+def _metric_candidates(n_i, n_j, keep, hxi, heta, exi, eeta, x, y, reach=3, chunk_rows=128):
+    """Candidate neighbours of every kept node among the nodes within +-reach
+    index steps (periodic in i, clipped in j), ordered by the distance in the
+    node's index-normalised metric: |(d xi, d eta)| where r_q - r_p =
+    h_xi d xi e_xi + h_eta d eta e_eta with the node's own spacings and
+    grid directions.
+    Returns (metric distance, candidate) arrays [n, (2 reach + 1)^2 - 1],
+    missing nodes last (distance inf, index -1)."""
+    gid = np.full(n_i * n_j, -1, dtype=np.int64)
+    gid[keep] = np.arange(int(keep.sum()))
+    gid = gid.reshape(n_j, n_i)
+    offs = [(dj, di) for dj in range(-reach, reach + 1) for di in range(-reach, reach + 1) if (di, dj) != (0, 0)]
+    odj = np.array([o[0] for o in offs])
+    odi = np.array([o[1] for o in offs])
+    kq = len(offs)
+    n = int(keep.sum())
+    dist = np.empty((n, kq))
+    nb = np.empty((n, kq), dtype=np.int64)
+    jj_all, ii_all = np.divmod(np.flatnonzero(keep), n_i)
+    for r0 in range(0, n, chunk_rows * n_i):
+        sl = slice(r0, min(n, r0 + chunk_rows * n_i))
+        jj, ii = jj_all[sl], ii_all[sl]
+        J = jj[:, None] + odj[None, :]
+        I = (ii[:, None] + odi[None, :]) % n_i
+        inside = (J >= 0) & (J < n_j)
+        q = np.where(inside, gid[np.clip(J, 0, n_j - 1), I], -1)
+        p = np.arange(sl.start, sl.stop)
+        dx = x[np.maximum(q, 0)] - x[p][:, None]
+        dy = y[np.maximum(q, 0)] - y[p][:, None]
+        # index offsets: the inverse of the local map (d xi, d eta) -> h_xi d xi
+        # e_xi + h_eta d eta e_eta applied to the offset (the grid lines are
+        # not orthogonal near the wall)
+        ax, ay = exi[0][jj, ii][:, None], exi[1][jj, ii][:, None]
+        bx, by = eeta[0][jj, ii][:, None], eeta[1][jj, ii][:, None]
+        cr = ax * by - ay * bx
+        a = (by * dx - bx * dy) / (cr * hxi[jj, ii][:, None])
+        b = (ax * dy - ay * dx) / (cr * heta[jj, ii][:, None])
+        md = np.where(q >= 0, np.hypot(a, b), np.inf)
+        order = np.argsort(md, axis=1, kind="stable")
+        dist[sl] = np.take_along_axis(md, order, axis=1)
+        nb[sl] = np.take_along_axis(q, order, axis=1)
+    return dist, nb
 
 
 def naca0012_jittered(n_i: int = 640, n_j: int = 256, jitter: float = 0.15,
                       remove_frac: float = 0.10, seed: int = BASE_SEED + 2,
                       radius_factor: float = 2.5, k_min: int = 8, k_max: int = 20,
-                      kinetic_outer: bool = False) -> Cloud:
-    """Jittered O-grid cloud with random interior removal and radius/kNN stencils."""
+                      kinetic_outer: bool = False, stencil: str = "euclid") -> Cloud:
+    """Jittered O-grid cloud with random interior removal and radius/kNN stencils.
+
+    stencil = "euclid": the points within radius_factor local spacings
+    (max(h_xi, h_eta)), nearest first (Euclidean), capped at k_max, at least
+    k_min.  stencil = "metric": the same rule in each node's index-normalised
+    metric (the offset in local index units along the grid directions), so that
+    on strongly stretched layers the stencil spans both index directions
+    instead of filling up with one side of the node's own column."""
     from scipy.spatial import cKDTree
 
     rng = np.random.default_rng(seed)
@@ -418,6 +490,8 @@ def naca0012_jittered(n_i: int = 640, n_j: int = 256, jitter: float = 0.15,
     x = Xj.ravel()
     y = Yj.ravel()
     h = np.maximum(hxi, heta).ravel()
+    if stencil not in ("euclid", "metric"):
+        raise ValueError(f"unknown stencil rule {stencil!r}")
     n0 = n_i * n_j
     flag = np.zeros(n0, dtype=np.uint8)
     flag[:n_i] = WALL
@@ -438,22 +512,34 @@ def naca0012_jittered(n_i: int = 640, n_j: int = 256, jitter: float = 0.15,
     widx[:n_i] = np.arange(n_i)
     wx, wy = x[:n_i].copy(), y[:n_i].copy()
 
-    tree = cKDTree(np.stack([x, y], axis=1))
-    kq = 48
-    dist, nb = tree.query(np.stack([x, y], axis=1), k=kq + 1)
-    dist, nb = dist[:, 1:], nb[:, 1:]
-    # reject neighbours seen through the aerofoil (only segments near the body can)
+    if stencil == "euclid":
+        tree = cKDTree(np.stack([x, y], axis=1))
+        kq = 48
+        dist, nb = tree.query(np.stack([x, y], axis=1), k=kq + 1, workers=-1)
+        dist, nb = dist[:, 1:], nb[:, 1:]
+        radius = radius_factor * h
+    else:
+        dist, nb = _metric_candidates(n_i, n_j, keep, hxi, heta, exi, eeta, x, y)
+        kq = nb.shape[1]
+        radius = np.full(n, radius_factor)
+    # reject neighbours seen through the aerofoil (only segments near the body
+    # can: a segment that meets the wall polygon is at least as long as its end
+    # point's distance to the polygon, which is at least the distance to the
+    # nearest wall vertex minus half the longest wall edge)
     P = np.repeat(np.arange(n), kq)
     Q = nb.ravel()
     near = ((np.minimum(x[P], x[Q]) <= 1.02) & (np.maximum(x[P], x[Q]) >= -0.02)
             & (np.minimum(y[P], y[Q]) <= 0.07) & (np.maximum(y[P], y[Q]) >= -0.07))
+    half_edge = 0.5 * float(np.max(np.hypot(np.roll(wx, -1) - wx, np.roll(wy, -1) - wy)))
+    dwall, _ = cKDTree(np.stack([wx, wy], axis=1)).query(np.stack([x, y], axis=1), workers=-1)
+    seg = dist.ravel() if stencil == "euclid" else np.hypot(x[Q] - x[P], y[Q] - y[P])
+    near &= (Q >= 0) & (seg >= dwall[P] - half_edge)
     cross = np.zeros(P.shape[0], dtype=bool)
     ii = np.flatnonzero(near)
     cross[ii] = _crosses_body_sectors(x[P[ii]], y[P[ii]], x[Q[ii]], y[Q[ii]], wx, wy, widx[P[ii]], widx[Q[ii]],
                                       col[P[ii]], col[Q[ii]])
     cross = cross.reshape(n, kq)
-    valid = ~cross
-    radius = radius_factor * h
+    valid = ~cross & (nb >= 0)
     # valid candidates first (stable: nearest first), then the count to keep
     order = np.argsort(~valid, axis=1, kind="stable")
     nbv = np.take_along_axis(nb, order, axis=1)
@@ -464,12 +550,24 @@ def naca0012_jittered(n_i: int = 640, n_j: int = 256, jitter: float = 0.15,
     keep = np.arange(kq)[None, :] < m[:, None]
     flat = nbv[keep]
     offs = np.concatenate([[0], np.cumsum(m)])
-    rows = [flat[offs[p]:offs[p + 1]].tolist() for p in range(n)]
-    rows, bad = _fix_stencils(x, y, flag, nx, ny, rows, lambda p: nbv[p][:nvalid[p]], kinetic_outer=kinetic_outer)
-    off, idx = _csr(rows)
+    if stencil == "euclid":
+        off, idx, bad = _fix_stencils(x, y, flag, nx, ny, offs, flat, lambda p: nbv[p][:nvalid[p]],
+                                      kinetic_outer=kinetic_outer)
+    else:
+        # augmentation: the metric candidates, then the Euclidean nearest
+        # points (beside the trailing edge the index block holds too few on
+        # one side), each checked against the body
+        tree = cKDTree(np.stack([x, y], axis=1))
+
+        def cand(p):
+            _, e = tree.query([x[p], y[p]], k=min(n, 65))
+            return np.concatenate([nbv[p][:nvalid[p]], np.asarray(e)[1:]])
+
+        off, idx, bad = _fix_stencils(x, y, flag, nx, ny, offs, flat, cand, body=(wx, wy, widx),
+                                      kinetic_outer=kinetic_outer)
     return Cloud(x, y, flag, nx, ny, off, idx,
                  dict(kind="jittered", n_i=n_i, n_j=n_j, jitter=jitter, remove_frac=remove_frac,
-                      seed=seed, removed=n_rm, augmented=bad, kinetic_outer=kinetic_outer))
+                      seed=seed, removed=n_rm, augmented=bad, kinetic_outer=kinetic_outer, stencil=stencil))
 
 
 def cartesian_box(n: int = 7, m: int = 7, jitter: float = 0.2, seed: int = BASE_SEED + 7,
@@ -504,8 +602,8 @@ def cartesian_box(n: int = 7, m: int = 7, jitter: float = 0.2, seed: int = BASE_
     d, nb = tree.query(np.stack([x, y], 1), k=min(N, 13))
     rows = [[int(q) for q in nb[p, 1:9]] for p in range(N)]
     cand = [nb[p, 1:] for p in range(N)]
-    rows, bad = _fix_stencils(x, y, flag, nx, ny, rows, lambda p: cand[p], kinetic_outer=kinetic_outer)
     off, idx = _csr(rows)
+    off, idx, bad = _fix_stencils(x, y, flag, nx, ny, off, idx, lambda p: cand[p], kinetic_outer=kinetic_outer)
     return Cloud(x, y, flag, nx, ny, off, idx,
                  dict(kind="box", n=n, m=m, seed=seed, augmented=bad, kinetic_outer=kinetic_outer))
 
@@ -515,8 +613,12 @@ WORKLOADS = {
     "naca0012_160x64": dict(builder="block", n_i=160, n_j=64, mach=0.63, aoa_deg=2.0, cfl=100.0, iters=300),
     "naca0012_640x256_jit": dict(builder="jittered", n_i=640, n_j=256, mach=0.85, aoa_deg=1.0, cfl=100.0,
                                  iters=2000, seed=BASE_SEED + 2),
+    # 2,048 layers clustered to 1.4e-4 chords at the wall against ~10x coarser
+    # tangential spacing: stencils in the index-normalised metric (the
+    # Euclidean rule fills a near-wall stencil with the node's own column and
+    # one side of it, which leaves its split sub-stencils ill conditioned)
     "naca0012_2560x2048_jit": dict(builder="jittered", n_i=2560, n_j=2048, mach=0.8, aoa_deg=1.25, cfl=100.0,
-                                   remove_frac=0.0, seed=BASE_SEED + 3),
+                                   remove_frac=0.0, seed=BASE_SEED + 3, stencil="metric"),
     # the supersonic case (Sec. 5.3: M 1.2, AoA 0) on the 147,584-point cloud,
     # with the outer stencils the kinetic far field needs
     "naca0012_640x256_jit_m1.2": dict(builder="jittered", n_i=640, n_j=256, mach=1.2, aoa_deg=0.0, cfl=100.0,
@@ -550,4 +652,4 @@ def build_workload(name: str) -> Cloud:
     if w["builder"] == "block":
         return naca0012_block(w["n_i"], w["n_j"], kinetic_outer=ko)
     return naca0012_jittered(w["n_i"], w["n_j"], remove_frac=w.get("remove_frac", 0.10), seed=w["seed"],
-                             kinetic_outer=ko)
+                             kinetic_outer=ko, stencil=w.get("stencil", "euclid"))

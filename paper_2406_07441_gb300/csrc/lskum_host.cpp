@@ -75,6 +75,8 @@ struct lskum_ctx {
     cudaStream_t stream = nullptr;      // internal, capture-capable
     cudaStream_t user_stream = nullptr;
     cudaEvent_t ev = nullptr;
+    cudaStream_t side = nullptr;                      // side branch of the captured iterations
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     double *dscratch = nullptr;         // 4 * ld doubles on the device: caller-order staging
     bool host_direct_ok = false;        // the device reads and writes pageable host memory
@@ -1019,6 +1021,10 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamCreate");
     e = cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventCreate");
+    e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(c, e, "side stream");
     Arena &A = c->arena;
     Dev &d = c->dev;
     d.n = n;
@@ -1109,6 +1115,41 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
     if (c->pk_ok) {
         if (mixed) d.jcf = A.alloc<float>(16 * (size_t)ld);
         else d.jc = A.alloc<double>(16 * (size_t)ld);
+    }
+    // the framed points' Jacobians of the packed form (exact products):
+    // per slot lane a weighted 4x4 matrix, per framed point its four axis
+    // Jacobians; framed points numbered in internal order
+    std::vector<int32_t> h_fidx, h_fpt;
+    for (int dir = 0; dir < 2; dir++) {
+        d.pk_jm[dir] = nullptr;
+        d.pk_jmf[dir] = nullptr;
+        d.pk_lanes[dir] = 0;
+    }
+    d.fj = nullptr;
+    d.fjf = nullptr;
+    d.fidx = d.fpt = nullptr;
+    d.nf = 0;
+    if (c->pk_ok && c->opts.jvp == LSKUM_JVP_EXACT) {
+        h_fidx.assign(ld, -1);
+        for (int32_t k = 0; k < n; k++) {
+            const uint8_t fl = c->flag[c->perm[k]];
+            if (fl == LSKUM_WALL || (fl == LSKUM_OUTER && c->opts.farfield == LSKUM_FARFIELD_KINETIC)) {
+                h_fidx[k] = (int32_t)h_fpt.size();
+                h_fpt.push_back(k);
+            }
+        }
+        d.nf = (int32_t)h_fpt.size();
+        for (int dir = 0; dir < 2; dir++) {
+            d.pk_lanes[dir] = (int32_t)hp.pk_pt[dir].size();
+            const size_t m = 16 * std::max<size_t>(hp.pk_pt[dir].size(), 1);
+            if (mixed) d.pk_jmf[dir] = A.alloc<float>(m);
+            else d.pk_jm[dir] = A.alloc<double>(m);
+        }
+        const size_t mf = 64 * std::max<size_t>(h_fpt.size(), 1);
+        if (mixed) d.fjf = A.alloc<float>(mf);
+        else d.fj = A.alloc<double>(mf);
+        d.fidx = A.alloc<int32_t>(ld);
+        d.fpt = A.alloc<int32_t>(std::max<size_t>(h_fpt.size(), 1));
     }
     c->launch.pk_lw[0] = c->pk_ok ? c->pk_lw[0].data() : nullptr;
     c->launch.pk_lw[1] = c->pk_ok ? c->pk_lw[1].data() : nullptr;
@@ -1265,6 +1306,10 @@ static lskum_status upload(lskum_ctx *c, HostPrep &hp)
             up((void *)d.lp_w2f[dir], lpf[dir][1].data(), ne * sizeof(float));
         }
     }
+    if (d.fidx) {
+        up((void *)d.fidx, h_fidx.data(), ld * sizeof(int32_t));
+        up((void *)d.fpt, h_fpt.data(), h_fpt.size() * sizeof(int32_t));
+    }
     if (e == cudaSuccess && d.jc) e = cudaMemset(d.jc, 0, 16 * (size_t)ld * sizeof(double));
     if (e == cudaSuccess && d.jcf) e = cudaMemset(d.jcf, 0, 16 * (size_t)ld * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(c->case_state, 0, c->n_cases * sizeof(int32_t));
@@ -1330,7 +1375,11 @@ static lskum_status build_graphs(lskum_ctx *c)
         cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamBeginCapture");
         int launches = 0;
-        cudaError_t le = launch_iteration(c->dev, c->launch, par, c->n_levels, c->lvl_beg.data(),
+        Launch L = c->launch;  // captured: the framed Jacobians on the side branch
+        L.side = c->side;
+        L.fork = c->ev_fork;
+        L.join = c->ev_join;
+        cudaError_t le = launch_iteration(c->dev, L, par, c->n_levels, c->lvl_beg.data(),
                                           c->lvl_act_end.data(), c->lvl_end.data(), c->stream, &launches);
         e = cudaStreamEndCapture(c->stream, &g);
         if (le != cudaSuccess) {
@@ -1354,6 +1403,9 @@ void lskum_destroy(lskum_ctx *c)
         if (g) cudaGraphExecDestroy(g);
     c->arena.release();
     if (c->ev) cudaEventDestroy(c->ev);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->side) cudaStreamDestroy(c->side);
     if (c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }

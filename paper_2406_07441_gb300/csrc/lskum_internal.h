@@ -150,6 +150,19 @@ struct Dev {
     // points (FP64, or FP32 for the mixed-precision sweeps; the other is null)
     double *jc;
     float *jcf;
+    // packed form, exact Jacobian products of the points in a (t, n) frame:
+    // the Jacobians of the split fluxes depend only on the state of the
+    // iteration, not on the increments, so they are formed for the whole
+    // level set before the forward sweep (k_framed_jac) and the sweeps'
+    // framed chains reduce to matrix-vector products.  pk_jm[dir]: per packed
+    // slot lane, M = w1 dG_e1/dU + w2 dG_e2/dU at the neighbour's state, 16
+    // values (row c, column j at 4 c + j); fj: per framed point f, its four
+    // axis Jacobians (x+, x-, y+, y-) at its own state, [nf][4][16]; fidx[k]
+    // = f or -1.  FP64, or FP32 for the mixed-precision sweeps.
+    double *pk_jm[2], *fj;
+    float *pk_jmf[2], *fjf;
+    const int32_t *fidx, *fpt;  // fpt[f] = internal index of framed point f
+    int32_t pk_lanes[2], nf;
     // per-case residual norm: stage 1 sums R_rho^2 over blocks of up to 256
     // points of one case (caller order), stage 2 adds each case's blocks
     double *blk;             // [n_blk][4] partial sums of the four components
@@ -180,6 +193,12 @@ struct Launch {
     int sweep_lanes;  // lanes per point of the sweep kernels (2, 4, 8), or 32: the packed form
     const int32_t *pk_lw[2];  // packed form: host arrays [n_levels + 1], first framed-point warp of each level
     const int32_t *lp_lg[2];  // packed form: host arrays [n_levels + 1], first interior group of each level
+    // optional side branch of a captured iteration: the framed points'
+    // Jacobians (k_framed_jac) run on `side` between the `fork` after k_begin
+    // and the `join` before the forward sweep, beside the q-derivatives and
+    // the residual; null: inline, before the forward sweep
+    cudaStream_t side;
+    cudaEvent_t fork, join;
 };
 
 cudaError_t launch_iteration(const Dev &d, const Launch &L, int cur, int n_levels, const int32_t *lvl_beg,

@@ -299,6 +299,35 @@ __device__ __forceinline__ void jvp_axis(const PrimT<T> &P, const JvpBase<T> &b,
     out[3] = fma(t1, A, fma(ude1, dA, t3));  // ude1 = u_d e1, from the record
 }
 
+// The same product with the axis chosen at run time (xdir: d = (1,0), else
+// (0,1)) without a branch: the axis-dependent operands are selected on the
+// integer pipe, so the lanes of a warp that form x- and y-products issue one
+// FP64 sequence together.  Equal to jvp_axis<0 or 1> except that a pressure
+// term of zero is added as +0 (an exactly zero product then has sign +).
+template <typename T>
+__device__ __forceinline__ void jvp_axis_sel(const PrimT<T> &P, const JvpBase<T> &b, bool xdir, bool pos, T A, T ek,
+                                             T B, T B2S, T ude1, T out[4])
+{
+    const T ud = xdir ? P.u : P.v;
+    const T dud = xdir ? b.du : b.dv;
+    const T dS = fma(dud, P.sb, ud * b.dsb);
+    const T dA = signed_by(ek * dS, pos);
+    const T sB = signed_by(B, pos);
+    const T sdB = signed_by(fma(B2S, dS, B * b.dsbi), !pos);
+    const T M1 = fma(ud, A, sB);
+    const T dM1 = fma(dud, A, fma(ud, dA, sdB));
+    const T rm = P.rho * M1;
+    const T drm = fma(b.drho, M1, P.rho * dM1);
+    const T pA = fma(b.dp, A, P.p * dA);
+    const T zero = T(0);
+    out[0] = drm;
+    out[1] = fma(drm, P.u, fma(rm, b.du, xdir ? pA : zero));
+    out[2] = fma(drm, P.v, fma(rm, b.dv, xdir ? zero : pA));
+    const T t1 = fma(dud, P.e1, ud * b.de1);
+    const T t3 = fma(b.de2, sB, P.e2 * sdB);
+    out[3] = fma(t1, A, fma(ude1, dA, t3));
+}
+
 // Unsplit Euler-flux Jacobian product A_d(U) dU in direction d = (dx, dy)
 // (the tangent of G_d = (rho u_d, rho u u_d + p dx, rho v u_d + p dy,
 // (E + p) u_d) along dU; the revised LU-SGS's S term).
@@ -933,61 +962,67 @@ __device__ __forceinline__ void store4(float *p, const float v[4])
     *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
 
-// Axis product cb (0: x+, 1: x-, 2: y+, 3: y-) of point k's new increment w:
-// the value an interior point whose list holds k would form for that
-// sub-stencil (the same functions, arguments and precision), stored once for
-// every later level to gather.
-template <int JVP, typename T>
-__device__ __forceinline__ void store_axis_product(const Dev &d, const StateSet &st, const MathTables &Tb,
-                                                   const SweepBufs<T> &sb, const T w[4], int k, int cb)
+// Axis product cb (0: x+, 1: x-, 2: y+, 3: y-) of point k's new increment w
+// in the increment form, G_d(U_k + w) - G_d(U_k) in FP64 (the value an
+// interior point whose list holds k would form for that sub-stencil),
+// stored once for every later level to gather.  (The exact products are
+// formed by jvp_axis_sel from the point's record, or from the framed
+// points' precomputed Jacobians.)
+template <typename T>
+__device__ __forceinline__ void store_increment_product(const Dev &d, const StateSet &st, const MathTables &Tb,
+                                                        const SweepBufs<T> &sb, const T w[4], int k, int cb)
 {
     const bool pos = !(cb & 1);
-    T J[4];
-    if (JVP == 0) {
-        const PrimT<T> P = load_prim(sb.prim, k);
-        const T *rec = sb.prim + (size_t)k * kPrimStride;
-        const JvpBase<T> jb = jvp_base(P, w);
-        if (cb < 2)
-            jvp_axis<0, T>(P, jb, pos, rec[pos ? P_APX : P_AMX], rec[P_EKX], rec[P_BX], rec[P_BSX], rec[P_UE1], J);
-        else
-            jvp_axis<1, T>(P, jb, pos, rec[pos ? P_APY : P_AMY], rec[P_EKY], rec[P_BY], rec[P_BSY], rec[P_VE1], J);
-    } else {  // increment form, in FP64
-        const int ld = d.ld;
-        double Ui[4], Up[4], G1[4], G0[4];
+    const int ld = d.ld;
+    double Ui[4], Up[4], G1[4], G0[4];
 #pragma unroll
-        for (int c = 0; c < 4; c++) {
-            Ui[c] = st.U[c * ld + k];
-            Up[c] = Ui[c] + (double)w[c];
-        }
-        const double ddx = cb < 2 ? 1.0 : 0.0, ddy = cb < 2 ? 0.0 : 1.0;
-        flux_cons(Tb, Up, ddx, ddy, pos, G1);
-        flux_cons(Tb, Ui, ddx, ddy, pos, G0);
-#pragma unroll
-        for (int c = 0; c < 4; c++) J[c] = (T)(G1[c] - G0[c]);
+    for (int c = 0; c < 4; c++) {
+        Ui[c] = st.U[c * ld + k];
+        Up[c] = Ui[c] + (double)w[c];
     }
+    const double ddx = cb < 2 ? 1.0 : 0.0, ddy = cb < 2 ? 0.0 : 1.0;
+    flux_cons(Tb, Up, ddx, ddy, pos, G1);
+    flux_cons(Tb, Ui, ddx, ddy, pos, G0);
+    T J[4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) J[c] = (T)(G1[c] - G0[c]);
     store4(sb.jc + 16 * (size_t)k + 4 * cb, J);
 }
 
+// Threads per block of the packed sweeps: a level is only a few thousand
+// warps, so small blocks spread them evenly over the SMs (whole blocks of
+// eight warps left half the SMs with one block and half with two).
+#ifndef LSKUM_SWEEP_BLOCK
+#define LSKUM_SWEEP_BLOCK 64
+#endif
+constexpr int kSweepBlock = LSKUM_SWEEP_BLOCK;
+static_assert(kSweepBlock % 32 == 0 && kSweepBlock <= 256, "sweep block");
+
 // Packed form of a level.  A neighbour's Jacobian product along an axis
 // depends only on the neighbour, the axis and the sub-stencil's sign, so a
-// point forms the four axis products of its new increment once (the values
-// the per-slot form computed, bit for bit), and interior points gather them:
-// 8 FMAs per slot instead of ~70 FP64 instructions.  A point's sum depends
-// only on its own list, in a fixed order, so a batch still equals its
-// single solves bit for bit.
-// - wf warps for the points in a (t, n) frame (products per slot in their
-//   own frame), their slots packed whole into warps (at create, by best
-//   fit; a point with an empty list takes one idle slot), one lane per slot;
-//   a segmented suffix sum over the lanes of each point (fixed tree order,
-//   no atomics) leaves the point's sum in its first lane, which finishes
-//   the point, and the point's lanes share its four axis products.  Packed
-//   warps [wb, wb + wf) are the level's; they are spread evenly over the
-//   grid (every S-th warp), so that their long chains do not share SMs.
+// point forms the four axis products of its new increment once, and
+// interior points gather them: 8 FMAs per slot instead of ~70 FP64
+// instructions.  A point's sum depends only on its own list, in a fixed
+// order, so a batch still equals its single solves bit for bit.
+// - wf warps for the points in a (t, n) frame, their slots packed whole into
+//   warps (at create, by best fit; a point with an empty list takes one idle
+//   slot), one lane per slot.  Exact products: the lane applies the slot's
+//   weighted Jacobian, formed for the whole iteration by k_framed_jac (16
+//   FMAs); increments: the split fluxes per slot in the point's frame.  A
+//   segmented suffix sum over the lanes of each point (fixed tree order, no
+//   atomics) leaves the point's sum in its first lane, which finishes the
+//   point; the point's lanes share its four axis products (exact: its
+//   precomputed axis Jacobians).  Packed warps [wb, wb + wf) are the
+//   level's; they are spread evenly over the grid (every S-th warp).
 // - ng warps for the interior points, kLanesPerPoint lanes per point,
 //   kPointsPerWarp points of similar list length per warp (groups
 //   [g0, g0 + ng) are the level's), in the other warp positions in order.
+//   A level is a chain of dependent loads (list, gathers, the point's own
+//   record) and a short FP64 sequence per lane, so the point's own loads
+//   are issued before the gathers, and the x- and y-products of a warp's
+//   lanes share one branch-free FP64 sequence (jvp_axis_sel).
 template <int JVP, bool FWD, typename T>
-__global__ void __launch_bounds__(256) k_sweep_packed(Dev d, StateSet st, int wb, int wf, int g0, int ng)
+__global__ void __launch_bounds__(kSweepBlock) k_sweep_packed(Dev d, StateSet st, int wb, int wf, int g0, int ng)
 {
     const MathTables &Tb = g_math;  // framed points only: no per-block copy
     if (halted(d.ctrl)) return;
@@ -1013,10 +1048,21 @@ __global__ void __launch_bounds__(256) k_sweep_packed(Dev d, StateSet st, int wb
         point_frame(d, k, framed, e1x, e1y, e2x, e2y);
         const int mb = d.pk_mb[dir][e];
         if (live && mb) {
-            const T w1 = sizeof(T) == 4 ? (T)d.pk_w1f[dir][e] : (T)d.pk_w1[dir][e];
-            const T w2 = sizeof(T) == 4 ? (T)d.pk_w2f[dir][e] : (T)d.pk_w2[dir][e];
-            sweep_slot<JVP, T>(d, st, Tb, dW, sb.prim, framed, e1x, e1y, e2x, e2y, d.pk_nbr[dir][e], mb, w1, w2,
-                               acc);
+            if (JVP == 0) {
+                // the slot's weighted Jacobian, formed before the sweeps: acc += M dW_i
+                const T *__restrict__ M = (sizeof(T) == 4 ? (const T *)d.pk_jmf[dir] : (const T *)d.pk_jm[dir]) + 16 * e;
+                T dl[4];
+                load4(dW + 4 * (size_t)d.pk_nbr[dir][e], dl);
+#pragma unroll
+                for (int c = 0; c < 4; c++)
+#pragma unroll
+                    for (int j = 0; j < 4; j++) acc[c] = fma(M[4 * c + j], dl[j], acc[c]);
+            } else {
+                const T w1 = sizeof(T) == 4 ? (T)d.pk_w1f[dir][e] : (T)d.pk_w1[dir][e];
+                const T w2 = sizeof(T) == 4 ? (T)d.pk_w2f[dir][e] : (T)d.pk_w2[dir][e];
+                sweep_slot<JVP, T>(d, st, Tb, dW, sb.prim, framed, e1x, e1y, e2x, e2y, d.pk_nbr[dir][e], mb, w1,
+                                   w2, acc);
+            }
         }
         // segmented suffix sum: lane l adds lane l + o when both hold the same
         // point; the warp's longest list bounds the steps (warp-uniform)
@@ -1041,8 +1087,25 @@ __global__ void __launch_bounds__(256) k_sweep_packed(Dev d, StateSet st, int wb
         if (live && r == 0) sweep_point<FWD, T>(d, st, sb, k, wall, e1x, e1y, e2x, e2y, acc, w);
 #pragma unroll
         for (int c = 0; c < 4; c++) w[c] = __shfl_sync(kFull, w[c], head);
-        if (live)
-            for (int cb = r; cb < 4; cb += seg) store_axis_product<JVP, T>(d, st, Tb, sb, w, k, cb);
+        if (live) {
+            if (JVP == 0) {
+                // the point's axis Jacobians, formed before the sweeps
+                const T *__restrict__ F =
+                    (sizeof(T) == 4 ? (const T *)d.fjf : (const T *)d.fj) + 64 * (size_t)d.fidx[k];
+                for (int cb = r; cb < 4; cb += seg) {
+                    T J[4];
+#pragma unroll
+                    for (int c = 0; c < 4; c++) {
+                        J[c] = F[16 * cb + 4 * c] * w[0];
+#pragma unroll
+                        for (int j = 1; j < 4; j++) J[c] = fma(F[16 * cb + 4 * c + j], w[j], J[c]);
+                    }
+                    store4(sb.jc + 16 * (size_t)k + 4 * cb, J);
+                }
+            } else {
+                for (int cb = r; cb < 4; cb += seg) store_increment_product<T>(d, st, Tb, sb, w, k, cb);
+            }
+        }
         return;
     }
     // interior points: kLanesPerPoint lanes per point, lane s taking the
@@ -1054,6 +1117,39 @@ __global__ void __launch_bounds__(256) k_sweep_packed(Dev d, StateSet st, int wb
     const int k = d.lp_k[dir][kPointsPerWarp * g + p];
     const bool live = k >= 0 && !frozen(d, k);
     const int len = live ? d.lp_len[dir][kPointsPerWarp * g + p] : 0;
+    const int kk = k >= 0 ? k : 0;  // index for the loads of a slot without a point
+    // loads that depend only on the point, issued before the gathers so that
+    // their latency overlaps theirs: this lane's entries of the point's
+    // primal record (its axis product s: 0 x+, 1 x-, 2 y+, 3 y-) and, in the
+    // point's first lane, the right-hand side (R forward, dU* backward) and 1/D
+    const bool xdir = s < 2, psg = !(s & 1);
+    PrimT<T> P{};
+    T rA = T(0), rEK = T(0), rB = T(0), rBS = T(0), rUE = T(0);
+    if (JVP == 0) {
+        P = load_prim(sb.prim, kk);
+        const T *rec = sb.prim + (size_t)kk * kPrimStride;
+        rA = rec[xdir ? (psg ? P_APX : P_AMX) : (psg ? P_APY : P_AMY)];
+        rEK = rec[xdir ? P_EKX : P_EKY];
+        rB = rec[xdir ? P_BX : P_BY];
+        rBS = rec[xdir ? P_BSX : P_BSY];
+        rUE = rec[xdir ? P_UE1 : P_VE1];
+    }
+    const bool plain = d.lusgs == 0;  // the revised LU-SGS adds its lagged term in sweep_point
+    double rhs[4] = {0.0, 0.0, 0.0, 0.0};
+    T iDk = T(0);
+    if (s == 0 && plain) {
+        iDk = (T)d.iD[kk];
+        if (FWD) {
+            const int ld = d.ld;
+#pragma unroll
+            for (int c = 0; c < 4; c++) rhs[c] = d.R[c * ld + kk];
+        } else {
+            T v[4];
+            load4(sb.dUs + 4 * (size_t)kk, v);
+#pragma unroll
+            for (int c = 0; c < 4; c++) rhs[c] = (double)v[c];
+        }
+    }
     const size_t base = (size_t)d.lp_goff[dir][g] + lane;
 #pragma unroll 2
     for (int j = s; j < len; j += kLanesPerPoint) {
@@ -1078,14 +1174,107 @@ __global__ void __launch_bounds__(256) k_sweep_packed(Dev d, StateSet st, int wb
 #pragma unroll
         for (int c = 0; c < 4; c++) acc[c] += __shfl_xor_sync(kFull, acc[c], o);
     }
-    // the point's first lane finishes it; each of its lanes then forms one of
-    // the four axis products of the new increment
+    // the point's first lane finishes it (forward dU* = -(R + acc) / D,
+    // backward dU = dU* - acc / D); each of its lanes then forms one of the
+    // four axis products of the new increment
 #pragma unroll
     for (int c = 0; c < 4; c++) w[c] = T(0);
-    if (live && s == 0) sweep_point<FWD, T>(d, st, sb, k, false, 1.0, 0.0, 0.0, 1.0, acc, w);
+    if (live && s == 0) {
+        if (plain) {
+#pragma unroll
+            for (int c = 0; c < 4; c++) w[c] = FWD ? -((T)rhs[c] + acc[c]) * iDk : fma(-acc[c], iDk, (T)rhs[c]);
+            store4((FWD ? sb.dUs : sb.dU) + 4 * (size_t)k, w);
+        } else {
+            sweep_point<FWD, T>(d, st, sb, k, false, 1.0, 0.0, 0.0, 1.0, acc, w);
+        }
+    }
 #pragma unroll
     for (int c = 0; c < 4; c++) w[c] = __shfl_sync(kFull, w[c], lane - s);
-    if (live) store_axis_product<JVP, T>(d, st, Tb, sb, w, k, s);
+    if (live) {
+        if (JVP == 0) {
+            const JvpBase<T> jb = jvp_base(P, w);
+            T J[4];
+            jvp_axis_sel<T>(P, jb, xdir, psg, rA, rEK, rB, rBS, rUE, J);
+            store4(sb.jc + 16 * (size_t)k + 4 * s, J);
+        } else {
+            store_increment_product<T>(d, st, Tb, sb, w, k, s);
+        }
+    }
+}
+
+// Jacobians of the framed points' products for the packed sweeps (exact
+// products).  The split-flux Jacobian A_d^+-(U_i) is the derivative of
+// G_d^+- at the state of this iteration and does not depend on the sweeps'
+// increments, so every matrix that the two sweeps apply at the points in a
+// (t, n) frame is formed here, all in parallel, before the forward sweep;
+// inside the levels the framed points' chains are then matrix-vector
+// products.  One thread per (slot lane, column) of pk_jm -- M = w1 A_e1 +
+// w2 A_e2 at the neighbour's state in the point's frame -- and per (framed
+// point, axis product, column) of fj -- A_x+-, A_y+- at the point's own
+// state.  Column j is the forward-mode tangent along the unit vector e_j,
+// evaluated in FP64 by the functions of the per-slot form (stored as T).
+template <typename T>
+__global__ void __launch_bounds__(256) k_framed_jac(Dev d, StateSet st)
+{
+    __shared__ MathTables Tb;
+    if (halted(d.ctrl)) return;
+    load_math_tables(Tb);
+    __syncthreads();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n0 = 4 * d.pk_lanes[0], n1 = 4 * d.pk_lanes[1], nfj = 16 * d.nf;
+    if (t >= n0 + n1 + nfj) return;
+    const int j = t & 3;  // n0 and n1 are multiples of 4
+    double dl[4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) dl[c] = c == j ? 1.0 : 0.0;  // the unit vector e_j
+    if (t < n0 + n1) {
+        const int dir = t < n0 ? 0 : 1;
+        const int e = (t - (dir ? n0 : 0)) >> 2;
+        T *M = (sizeof(T) == 4 ? (T *)d.pk_jmf[dir] : (T *)d.pk_jm[dir]) + 16 * (size_t)e;
+        const int pos = d.pk_pt[dir][e];
+        const int mb = d.pk_mb[dir][e];
+        double col[4] = {0.0, 0.0, 0.0, 0.0};
+        if (pos >= 0 && mb) {
+            const int k = (dir == 0 ? d.sw_fwd : d.sw_bwd)[pos];
+            double e1x, e1y, e2x, e2y;
+            point_frame(d, k, true, e1x, e1y, e2x, e2y);
+            const PrimU P = load_prim(st.prim, d.pk_nbr[dir][e]);
+            const JvpBase<double> jb = jvp_base(P, dl);
+#pragma unroll
+            for (int s = 0; s < 2; s++) {
+                const int m = s == 0 ? (mb & 3) : (mb >> 2);
+                if (!m) continue;
+                const bool pos_s = m & 1;
+                const double sg = pos_s ? 1.0 : -1.0;
+                const double ddx = s == 0 ? e1x : e2x, ddy = s == 0 ? e1y : e2y;
+                const double S = (P.u * ddx + P.v * ddy) * P.sb;
+                double A, eS, J[4];
+                split_A(Tb, S, pos_s, A, eS);
+                jvp_dir(P, jb, ddx, ddy, sg, S, A, eS, eS * kInv2SqrtPi * P.isb, J);
+                const double w = s == 0 ? d.pk_w1[dir][e] : d.pk_w2[dir][e];
+#pragma unroll
+                for (int c = 0; c < 4; c++) col[c] = fma(w, J[c], col[c]);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 4; c++) M[4 * c + j] = (T)col[c];
+        return;
+    }
+    const int u = t - n0 - n1;
+    const int f = u >> 4, cb = (u >> 2) & 3;
+    const int k = d.fpt[f];
+    const PrimU P = load_prim(st.prim, k);
+    const double *rec = st.prim + (size_t)k * kPrimStride;
+    const JvpBase<double> jb = jvp_base(P, dl);
+    const bool pos = !(cb & 1);
+    double J[4];
+    if (cb < 2)
+        jvp_axis<0, double>(P, jb, pos, rec[pos ? P_APX : P_AMX], rec[P_EKX], rec[P_BX], rec[P_BSX], rec[P_UE1], J);
+    else
+        jvp_axis<1, double>(P, jb, pos, rec[pos ? P_APY : P_AMY], rec[P_EKY], rec[P_BY], rec[P_BSY], rec[P_VE1], J);
+    T *F = (sizeof(T) == 4 ? (T *)d.fjf : (T *)d.fj) + 64 * (size_t)f + 16 * cb;
+#pragma unroll
+    for (int c = 0; c < 4; c++) F[4 * c + j] = (T)J[c];
 }
 
 // ---------------------------------------------------------------------------
@@ -1337,27 +1526,46 @@ void enqueue_sweeps_g(const Dev &d, int cur, int n_levels, const int32_t *lvl_be
     }
 }
 
+// The packed exact sweeps apply precomputed framed-point Jacobians.
+bool needs_framed_jac(const Dev &d, const Launch &L)
+{
+    return d.scheme == 0 && d.jvp == 0 && L.sweep_lanes == 32 && (d.pk_jm[0] || d.pk_jmf[0]) &&
+           4 * (d.pk_lanes[0] + d.pk_lanes[1]) + 16 * d.nf > 0;
+}
+
+void enqueue_framed_jac(const Dev &d, int cur, cudaStream_t s, int *launches)
+{
+    const int items = 4 * (d.pk_lanes[0] + d.pk_lanes[1]) + 16 * d.nf;
+    if (d.precision) k_framed_jac<float><<<(items + 255) / 256, 256, 0, s>>>(d, d.set[cur]);
+    else k_framed_jac<double><<<(items + 255) / 256, 256, 0, s>>>(d, d.set[cur]);
+    (*launches)++;
+}
+
 template <int JVP>
 void enqueue_sweeps_packed(const Dev &d, const Launch &L, int cur, int n_levels, cudaStream_t s, int *launches,
                            bool fwd, bool bwd)
 {
     const StateSet st = d.set[cur];
+    if (fwd && needs_framed_jac(d, L)) {
+        if (L.side) cudaStreamWaitEvent(s, L.join, 0);  // formed on the side branch
+        else enqueue_framed_jac(d, cur, s, launches);
+    }
     for (int l = 0; fwd && l < n_levels; l++) {
         const int wb = L.pk_lw[0][l], wf = L.pk_lw[0][l + 1] - wb;
         const int g0 = L.lp_lg[0][l], ng = L.lp_lg[0][l + 1] - g0;
         if (wf + ng <= 0) continue;
-        const int blocks = ((wf + ng) * 32 + 255) / 256;
-        if (d.precision) k_sweep_packed<JVP, true, float><<<blocks, 256, 0, s>>>(d, st, wb, wf, g0, ng);
-        else k_sweep_packed<JVP, true, double><<<blocks, 256, 0, s>>>(d, st, wb, wf, g0, ng);
+        const int blocks = ((wf + ng) * 32 + kSweepBlock - 1) / kSweepBlock;
+        if (d.precision) k_sweep_packed<JVP, true, float><<<blocks, kSweepBlock, 0, s>>>(d, st, wb, wf, g0, ng);
+        else k_sweep_packed<JVP, true, double><<<blocks, kSweepBlock, 0, s>>>(d, st, wb, wf, g0, ng);
         (*launches)++;
     }
     for (int l = n_levels - 1; bwd && l >= 0; l--) {
         const int wb = L.pk_lw[1][l], wf = L.pk_lw[1][l + 1] - wb;
         const int g0 = L.lp_lg[1][l], ng = L.lp_lg[1][l + 1] - g0;
         if (wf + ng <= 0) continue;
-        const int blocks = ((wf + ng) * 32 + 255) / 256;
-        if (d.precision) k_sweep_packed<JVP, false, float><<<blocks, 256, 0, s>>>(d, st, wb, wf, g0, ng);
-        else k_sweep_packed<JVP, false, double><<<blocks, 256, 0, s>>>(d, st, wb, wf, g0, ng);
+        const int blocks = ((wf + ng) * 32 + kSweepBlock - 1) / kSweepBlock;
+        if (d.precision) k_sweep_packed<JVP, false, float><<<blocks, kSweepBlock, 0, s>>>(d, st, wb, wf, g0, ng);
+        else k_sweep_packed<JVP, false, double><<<blocks, kSweepBlock, 0, s>>>(d, st, wb, wf, g0, ng);
         (*launches)++;
     }
 }
@@ -1373,6 +1581,7 @@ cudaError_t enqueue_sweeps(const Dev &d, const Launch &L, int cur, int n_levels,
     case 32:
         if (!d.pk_pt[0] || !L.pk_lw[0] || !L.lp_lg[0] || !(d.precision ? (void *)d.jcf : (void *)d.jc))
             return cudaErrorInvalidValue;
+        if (JVP == 0 && !(d.precision ? (void *)d.pk_jmf[0] : (void *)d.pk_jm[0])) return cudaErrorInvalidValue;
         enqueue_sweeps_packed<JVP>(d, L, cur, n_levels, s, launches, fwd, bwd);
         break;
     default: return cudaErrorInvalidValue;
@@ -1387,6 +1596,16 @@ cudaError_t enqueue_phase(const Dev &d, const Launch &L, int cur, int ph, int n_
     case 0:
         k_begin<<<1, 1, 0, s>>>(d.ctrl);
         (*launches)++;
+        if (L.side && needs_framed_jac(d, L)) {
+            // the framed points' Jacobians depend only on the state: a side
+            // branch beside the q-derivatives and the residual
+            cudaError_t e = cudaEventRecord(L.fork, s);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(L.side, L.fork, 0);
+            if (e != cudaSuccess) return e;
+            enqueue_framed_jac(d, cur, L.side, launches);
+            e = cudaEventRecord(L.join, L.side);
+            if (e != cudaSuccess) return e;
+        }
         return enqueue_grad_res(d, L, cur, s, launches, true, false);
     case 1: return enqueue_grad_res(d, L, cur, s, launches, false, true);
     case 2:
@@ -1433,7 +1652,9 @@ cudaError_t launch_phase(const Dev &d, const Launch &L, int cur, int phase, int 
                          const int32_t *lvl_act_end, const int32_t *lvl_end, cudaStream_t s)
 {
     int launches = 0;
-    return enqueue_phase(d, L, cur, phase, n_levels, lvl_beg, lvl_act_end, lvl_end, s, &launches);
+    Launch Li = L;  // one phase at a time: the framed Jacobians inline, in the forward sweep's phase
+    Li.side = nullptr;
+    return enqueue_phase(d, Li, cur, phase, n_levels, lvl_beg, lvl_act_end, lvl_end, s, &launches);
 }
 
 cudaError_t launch_init_state(const Dev &d, int cur, bool project, cudaStream_t s)
