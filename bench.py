@@ -1,19 +1,31 @@
 #!/usr/bin/env python
-"""Throughput of the implicit q-LSKUM hot path on GB300, in point-iterations/s.
+"""Throughput of the implicit q-LSKUM hot path on GB300, in point-iterations/s,
+and the wall time of whole solves to a 1e-8 residual drop.
 
-One step = one pseudo-time iteration (q-derivatives with 3 inner iterations,
-second-order split-flux residual, residual norm, forward and backward LU-SGS
-sweeps with exact-AD Jacobian products, state update) of the plain FP64 solver
-on the jittered NACA 0012 cloud of 640x256 nodes with 10% of the interior
-removed (147,584 points, 8-20 neighbours), M = 0.85, AoA = 1 deg, CFL 100.
-The solve starts with START first-order iterations (untimed set-up, before the
-warm-up); every timed step is a full second-order iteration.
+One step = one pseudo-time iteration (q-derivatives with K = 2 inner
+iterations, second-order split-flux residual, residual norm, forward and
+backward LU-SGS sweeps with exact-AD Jacobian products, state update) of the
+plain FP64 solver.  Default workload: the jittered NACA 0012 cloud of
+2560x2048 nodes (5,242,880 points, stencils in the index-normalised metric),
+M = 0.8, AoA = 1.25 deg, CFL 100.  The solve starts with START first-order
+iterations (untimed set-up, before the warm-up); every timed step is a full
+second-order iteration.
+
+At N = 1 the default run also times two whole solves to a 1e-8 drop of the
+density residual on the 147,584-point cloud (the largest whose two solves fit
+a few minutes; a 1e-8 solve of the 5.24M-point cloud takes ~1e5 iterations):
+plain FP64 from the free stream, and FP32 sweeps from the learned warm start
+judged by the residual (the network trained first on the solver's own
+batched solutions, training time reported apart) -- the `solve` block.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+                  [--workload W] [--solve on|off]
 
---workload naca0012_640x256_jit_m1.2 runs the paper's supersonic case (M 1.2,
-AoA 0, K = 2) on the same cloud with the kinetic far field, and also times a
-whole solve to a 1e-8 residual drop (--solve-iters caps it).
+--workload naca0012_640x256_jit runs the 147,584-point cloud (M 0.85, AoA 1);
+naca0012_640x256_jit_m1.2 the paper's supersonic case (M 1.2, AoA 0) on the
+same cloud with the kinetic far field (and a whole solve, --solve-iters caps
+it); naca0012_batch64 the 64-cloud batch; naca0012_warmstart the warm-start
+study on the 160x64 cloud.
 
 --impl reference times the FP64 CPU oracle on the host cores instead, on a
 bounded number of iterations of the same workload.  Under torchrun (N > 1)
@@ -33,12 +45,18 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "naca0012_640x256_jit"
-# the supersonic case with the kinetic far field (K = 2: with 3 inner
-# iterations the unlimited reconstruction fails in the coarse far field)
+WORKLOAD = "naca0012_2560x2048_jit"      # default: 5,242,880 points
+MID_WORKLOAD = "naca0012_640x256_jit"    # 147,584 points
+PROF_WORKLOAD = "naca0012_1280x1024_jit"  # 1,310,720 points, the default's construction (profiling)
 SUPER_WORKLOAD = "naca0012_640x256_jit_m1.2"
-CASES = {WORKLOAD: dict(mach=0.85, aoa=1.0, K=3, farfield=0),
+# K = 2 inner iterations everywhere: with 3 the unlimited reconstruction
+# diverges in the coarse far field in long runs from the free stream, so
+# the solves to a 1e-8 drop use 2 and the timed steps do the same
+CASES = {WORKLOAD: dict(mach=0.8, aoa=1.25, K=2, farfield=0),
+         MID_WORKLOAD: dict(mach=0.85, aoa=1.0, K=2, farfield=0),
+         PROF_WORKLOAD: dict(mach=0.8, aoa=1.25, K=2, farfield=0),
          SUPER_WORKLOAD: dict(mach=1.2, aoa=0.0, K=2, farfield=1)}
+SOLVE_WORKLOAD = MID_WORKLOAD
 METRIC = "point-iter/s; wall time to 1e-8 residual drop, plain FP64 vs FP32+warm start"
 UNIT = "point-iter/s"
 L2_BYTES = 129 * 2**20
@@ -46,20 +64,22 @@ L2_BYTES = 129 * 2**20
 # x 2070 MHz = 1.259 TFLOP/s (a DFMA-chain probe measured 1.196 at ~2.0 GHz).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # FP64 flops (DFMA = 2) the residual kernel executes per neighbour slot that
-# joins a split sub-stencil, counted by ncu on this workload
-# (2 x smsp__sass_thread_inst_executed_op_dfma_pred_on + dmul + dadd, one
-# launch: 1.0421e9, divided by the 2,926,611 such slots); see profiles/.
-RES_FLOPS_PER_SLOT = 356.07
+# joins a split sub-stencil, counted by ncu (2 x dfma + dmul + dadd thread
+# instructions of one launch / such slots; see profiles/): the 147,584-point
+# cloud's Euclidean stencils, and the metric stencils of the 1,310,720-point
+# cloud, which stand for the 5,242,880-point one (the same construction; the
+# count depends on the mix of slots joining one or two sub-stencils)
+RES_FLOPS_PER_SLOT = {MID_WORKLOAD: 356.07, SUPER_WORKLOAD: 356.07}
 START = 50  # first-order start-up iterations before warm-up and timing
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one residual
-# launch on this workload at 2 threads per point, from one ncu capture of the
-# current kernel (profiles/k_residual_naca0012_640x256_jit.md); reported only
-# when the bench runs that launch shape.
-RES_TRAFFIC = {2: 164.885504e6}
+# launch at 2 threads per point, from one ncu capture of the current kernel
+# (profiles/k_residual_*.md), per workload; reported only for that launch
+# shape and FP64
+RES_TRAFFIC = {MID_WORKLOAD: {2: 164.885504e6}}
 # sm__pipe_fp64_cycles_active of that launch (fraction of peak sustained): the
 # residual's binding unit; the counted-flop fraction is lower because
 # additions, multiplications and comparisons occupy the pipe like an FMA
-RES_FP64_PIPE_ACTIVE = 0.894
+RES_FP64_PIPE_ACTIVE = {MID_WORKLOAD: 0.894}
 
 
 def _sweep_form(lanes):
@@ -138,16 +158,42 @@ def _gpu_id(torch, dev):
         return str(dev)
 
 
-def cpu_baseline(cloud, iters, warm=0, mach=0.85, aoa=1.0, K=3, farfield=0):
-    """The FP64 oracle, as it stands, on one host core: `iters` iterations."""
+def cpu_baseline(cloud, iters, warm=0, mach=0.85, aoa=1.0, K=2, farfield=0, startup=1):
+    """The FP64 oracle, as it stands, on one host core: `iters` iterations
+    timed after `startup` first-order start-up and `warm` warm-up iterations
+    (startup = 0: the first `iters` iterations from the free stream, all
+    first-order -- the same arithmetic with the reconstruction's gradients
+    zero)."""
     import oracle as O
     o = O.Oracle(cloud, farfield=farfield, mach=mach, aoa_deg=aoa)
     U = o.initial_state(mach, aoa)
-    r0 = o.run(U, 1 + warm, cfl=100.0, K=K, first_order=1)
+    n0, hist0 = 0, 0.0
+    if startup + warm > 0:
+        r0 = o.run(U, startup + warm, cfl=100.0, K=K, first_order=startup)
+        U, n0, hist0 = r0["U"], startup + warm, r0["hist0"]
     t0 = time.perf_counter()
-    r = o.run(r0["U"], iters, cfl=100.0, K=K, n0=1 + warm, hist0=r0["hist0"])
+    r = o.run(U, iters, cfl=100.0, K=K, n0=n0, hist0=hist0, first_order=startup if startup else iters)
     dt = time.perf_counter() - t0
     return cloud.n * r["done"] / dt, dt, r["done"]
+
+
+def _cpu_sample(wl, steps, warm):
+    """(iterations, warm-up, start-up) of a bounded oracle sample: about 10-30 s
+    of one core per iteration on the 5.24M-point cloud, so one to three
+    iterations from the free stream there; up to 10 second-order ones on the
+    smaller clouds."""
+    if wl in (WORKLOAD, PROF_WORKLOAD):
+        return max(1, min(steps, 3 if wl == PROF_WORKLOAD else 2)), 0, 0
+    return max(1, min(steps, 10)), min(warm, 1), 1
+
+
+def _sample_text(done, warm, startup, n):
+    if startup == 0:
+        return (f"{done} FP64 oracle iteration(s) from the free stream on the full {n}-point cloud (first-order "
+                f"start-up: the arithmetic of a second-order iteration with the reconstruction's gradients zero), "
+                f"one thread")
+    return (f"{done} second-order FP64 oracle iterations on the full {n}-point cloud after {startup} first-order "
+            f"start-up and {warm} warm-up iterations, one thread")
 
 
 def run_reference(args, rank):
@@ -157,27 +203,49 @@ def run_reference(args, rank):
     wl = args.workload if args.workload in CASES else WORKLOAD
     case = CASES[wl]
     cloud = cg.build_workload(wl)
-    steps = max(1, min(args.steps, 10))
-    warm = min(args.warmup, 1)
+    steps, warm, startup = _cpu_sample(wl, args.steps, args.warmup)
     val, dt, done = cpu_baseline(cloud, steps, warm, mach=case["mach"], aoa=case["aoa"], K=case["K"],
-                                 farfield=case["farfield"])
-    sample = (f"{done} second-order FP64 oracle iterations on the full {cloud.n}-point cloud after "
-              f"1 first-order start-up and {warm} warm-up iterations")
+                                 farfield=case["farfield"], startup=startup)
+    sample = _sample_text(done, warm, startup, cloud.n)
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": done,
             "warmup": warm, "ms_per_step": dt * 1e3 / done, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wl, "points": cloud.n, "mach": case["mach"], "aoa_deg": case["aoa"], "cfl": 100.0,
-                       "inner_iters": case["K"], "jvp": "exact-AD", "order": "second (after start-up)"},
+                       "inner_iters": case["K"], "jvp": "exact-AD",
+                       "order": "first (start-up from the free stream)" if startup == 0 else "second (after start-up)"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _shared_cloud(wl, rank, world, dist):
+    """The workload's cloud; with several ranks rank 0 builds it once and the
+    others load it from a temporary file (a 5.24M-point build holds ~10 GB of
+    host memory)."""
+    import numpy as np
+
+    from paper_2406_07441_gb300 import cloudgen as cg
+    if world == 1 or dist is None:
+        return cg.build_workload(wl)
+    path = os.path.join(os.environ.get("TMPDIR", "/tmp"), f"lskum_cloud_{wl}_{os.getppid()}.npz")
+    if rank == 0:
+        c = cg.build_workload(wl)
+        np.savez(path + ".tmp.npz", x=c.x, y=c.y, flag=c.flag, nx=c.nx, ny=c.ny, off=c.nbr_off, idx=c.nbr_idx)
+        os.replace(path + ".tmp.npz", path)
+    dist.barrier()
+    if rank != 0:
+        z = np.load(path)
+        c = cg.Cloud(z["x"], z["y"], z["flag"], z["nx"], z["ny"], z["off"], z["idx"], {"workload": wl})
+    dist.barrier()
+    if rank == 0:
+        os.remove(path)
+    return c
 
 
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
 
-    from paper_2406_07441_gb300 import cloudgen as cg
     from paper_2406_07441_gb300 import lskum
 
     torch.cuda.set_device(local_rank)
@@ -188,14 +256,13 @@ def run_ours(args, rank, world, local_rank):
     wl = args.workload
     case = CASES[wl]
     mach, aoa, K, kinetic = case["mach"], case["aoa"], case["K"], case["farfield"] == 1
-    cloud = cg.build_workload(wl)
+    cloud = _shared_cloud(wl, rank, world, dist)
     n = cloud.n
     explicit = args.scheme == "explicit"
     cfl = 0.3 if explicit else 100.0
     kw = dict(cfl=cfl, inner_iters=K, jvp=lskum.JVP_EXACT, first_order_iters=START, precision=args.precision,
               scheme=lskum.SCHEME_EXPLICIT if explicit else lskum.SCHEME_LUSGS, farfield=case["farfield"])
     s = lskum.Solver(cloud, mach, aoa, **kw)
-    info = s.info()
     nslots = int(np.count_nonzero(_memberships(cloud, kinetic)))
     # first-order start-up, then warm-up iterations (untimed)
     assert s.run(START) == START
@@ -205,7 +272,7 @@ def run_ours(args, rank, world, local_rank):
         tpp, lanes = (int(t) for t in args.launch_shape.split(","))
         s.set_launch_shape(tpp, lanes)
     else:
-        tpp, lanes, _ = s.autotune(5)
+        tpp, lanes, _ = s.autotune(3 if n > 1_000_000 else 5)
     info = s.info()  # launches per iteration in the chosen launch shape
     assert s.run(args.warmup) == args.warmup
     stream = torch.cuda.ExternalStream(s.stream())
@@ -231,11 +298,12 @@ def run_ours(args, rank, world, local_rank):
     # live per-phase timing (CUDA events on the library stream) for the roofline
     phases = s.time_phases(5)
     res_ms = phases["residual"]
-    achieved = RES_FLOPS_PER_SLOT * nslots / (res_ms / 1e3) / 1e12
+    flops_slot = RES_FLOPS_PER_SLOT.get(wl)
+    achieved = flops_slot * nslots / (res_ms / 1e3) / 1e12 if flops_slot else None
 
     # end to end through the C-ABI with host buffers: state in (H2D), one
     # iteration, state out (D2H) every step
-    e2e_steps = min(args.steps, 20)
+    e2e_steps = min(args.steps, 20 if n < 1_000_000 else 10)
     U = s.field(lskum.FIELD_U)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -247,11 +315,13 @@ def run_ours(args, rank, world, local_rank):
     e2e_dt = time.perf_counter() - t0
     e2e = {"value": n * e2e_steps / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": int(U.nbytes),
            "d2h_bytes_per_step": int(U.nbytes) + 8}
+    del U
 
-    solve = None
+    whole = None
     if args.solve_iters > 0:
         # wall time of a whole solve from the free stream to the drop target
-        # (host clock around the C-ABI call; the launch shape of the timed steps)
+        # on this workload (host clock around the C-ABI call; the launch shape
+        # of the timed steps)
         s2 = lskum.Solver(cloud, mach, aoa, **kw)
         s2.set_launch_shape(tpp, lanes)
         torch.cuda.synchronize()
@@ -260,9 +330,14 @@ def run_ours(args, rank, world, local_rank):
         sec = time.perf_counter() - t0
         h = s2.residuals()
         cl, cd = s2.forces()
-        solve = {"target_drop": 1e-8, "iterations": int(it), "seconds": sec, "reached": bool(h[-1] / h[0] <= 1e-8),
+        whole = {"target_drop": 1e-8, "iterations": int(it), "seconds": sec, "reached": bool(h[-1] / h[0] <= 1e-8),
                  "final_drop": float(h[-1] / h[0]), "cl": cl, "cd": cd, "max_iters": args.solve_iters}
         s2.close()
+    s.close()
+
+    solve = None
+    if world == 1 and args.solve == "on":
+        solve = solve_block(args, torch)
 
     if rank != 0:
         if dist:
@@ -270,10 +345,13 @@ def run_ours(args, rank, world, local_rank):
         return
     cpu = None
     if world == 1:
-        cv, cdt, cdone = cpu_baseline(cloud, 10, mach=mach, aoa=aoa, K=K, farfield=case["farfield"])
+        steps, warm, startup = _cpu_sample(wl, 1 if wl == WORKLOAD else 10, 0)
+        cv, cdt, cdone = cpu_baseline(cloud, steps, warm, mach=mach, aoa=aoa, K=K, farfield=case["farfield"],
+                                      startup=startup)
         cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{cdone} FP64 oracle iterations on the full {n}-point cloud (single thread)"}
+               "sample": _sample_text(cdone, warm, startup, n)}
     ws = _working_set_bytes(cloud)
+    traffic = RES_TRAFFIC.get(wl, {}).get(tpp) if args.precision == 0 else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -293,25 +371,125 @@ def run_ours(args, rank, world, local_rank):
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": f"inputs larger than L2: device working set {ws / 2**20:.0f} MiB > 129 MiB L2"},
         "roofline": {"bound": "alu", "kernel": "k_residual", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                     "traffic": RES_TRAFFIC.get(tpp) if args.precision == 0 and wl == WORKLOAD else None,
-                     "traffic_unit": "bytes per launch (ncu)",
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
+                     "traffic": traffic, "traffic_unit": "bytes per launch (ncu)",
                      "algorithmic_bytes_per_launch": int(cloud.nnz) * 37 + n * 360,
                      "algorithmic_bytes_rule": "37 B per neighbour slot (index, membership, dx, dy, 2 weights) "
                                                "+ 360 B per point (q, grad q, frame, geometry, state, R, D)",
+                     "flops_per_active_slot": flops_slot, "active_slots": nslots,
                      "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz",
-                     "fp64_pipe_active_ncu": RES_FP64_PIPE_ACTIVE if args.precision == 0 and wl == WORKLOAD else None,
+                     "fp64_pipe_active_ncu": RES_FP64_PIPE_ACTIVE.get(wl) if args.precision == 0 else None,
                      "launch_ms": res_ms, "phase_ms": phases},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": info["launches_per_iter"] * args.steps,
         "clocks": clk.summary(),
     }
+    if whole is not None:
+        line["whole_solve"] = whole
     if solve is not None:
         line["solve"] = solve
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def train_network(n_solves, seed, K=2):
+    """The warm-start network trained on the solver's own solutions: batched
+    FP32-sweep solves of the 160x64 cloud at n_solves random (M, AoA)
+    (3,000 iterations each, 4,096 points sampled per solve), then Adam.
+    Returns (network, facts)."""
+    import numpy as np
+    import torch
+
+    from paper_2406_07441_gb300 import cloudgen as cg
+    from paper_2406_07441_gb300 import lskum
+    cloud = cg.build_workload("naca0012_160x64")
+    rng = np.random.default_rng(seed)
+    train = [(float(rng.uniform(0.3, 0.85)), float(rng.uniform(-4, 6))) for _ in range(n_solves)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    net = lskum.Mlp(seed=cg.BASE_SEED, max_batch=4096)
+    failed = 0
+    for g0 in range(0, len(train), 64):
+        conds = train[g0:g0 + 64]
+        b = lskum.Solver.batch([cloud] * len(conds), conds, first_order_iters=START, inner_iters=K, precision=1)
+        b.run(3000)
+        failed += sum(1 for k in range(len(conds)) if b.case_info(k)["status"] != 0)
+        net.add_samples(b, 4096, seed=g0)
+        del b
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    n_samp = net.n_samples()
+    epochs = max(10, min(200, int(100 * 262144 / max(n_samp, 1))))
+    t0 = time.perf_counter()
+    losses = net.train(epochs, 512, 1e-3, seed=1)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    return net, {"train_cloud": "naca0012_160x64", "train_solves": len(train), "train_iters": 3000,
+                 "train_failed": failed, "samples": n_samp, "epochs": epochs, "data_s": t_data, "train_s": t_train,
+                 "final_loss": float(losses[-1]), "conditions": "M ~ U[0.3, 0.85], AoA ~ U[-4, 6] deg"}
+
+
+def solve_block(args, torch):
+    """Wall time to a 1e-8 drop of the density residual on SOLVE_WORKLOAD:
+    plain FP64 from the free stream, then FP32 sweeps from the judged warm
+    start to the plain run's final absolute norm (1e-8 x its first norm).
+    Host clock around the C-ABI runs (set-up, autotuning and the network's
+    training outside; the prediction and its judging inside)."""
+    from paper_2406_07441_gb300 import cloudgen as cg
+    from paper_2406_07441_gb300 import lskum
+    case = CASES[SOLVE_WORKLOAD]
+    mach, aoa, K = case["mach"], case["aoa"], case["K"]
+    cloud = cg.build_workload(SOLVE_WORKLOAD)
+    drop, max_iters = 1e-8, args.solve_max
+    sp = lskum.Solver(cloud, mach, aoa, inner_iters=K, first_order_iters=START, precision=0)
+    tp_shape = sp.autotune(3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    it_p = sp.run(max_iters, target_drop=drop)
+    torch.cuda.synchronize()
+    sec_p = time.perf_counter() - t0
+    hp = sp.residuals()
+    clp, cdp = sp.forces()
+    target = hp[0] * drop
+    sp.close()
+    net, facts = train_network(args.train_solves, cg.BASE_SEED + 5, K=K)
+    sw = lskum.Solver(cloud, mach, aoa, inner_iters=K, first_order_iters=0, precision=1)
+    tw_shape = sw.autotune(3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    kept = bool(net.predict(sw)[0])
+    if not kept:
+        sw.set_start_iters(START)  # the free stream needs the first-order start-up
+    st_w, it_w, hw = _drop_run(sw, target, 20000, max_iters)
+    torch.cuda.synchronize()
+    sec_w = time.perf_counter() - t0
+    clw, cdw = sw.forces()
+    sw.close()
+    fwd_ms = net.time_forward(cloud.n, 5)
+    net.close()
+    ok_p = bool(hp[-1] <= target)
+    ok_w = bool(st_w == 0 and hw[-1] <= target)
+    return {
+        "cloud": SOLVE_WORKLOAD, "points": cloud.n, "mach": mach, "aoa_deg": aoa, "inner_iters": K, "cfl": 100.0,
+        "target_drop": drop, "max_iters": max_iters,
+        "plain": {"precision": "fp64", "start": f"free stream, {START} first-order start-up iterations",
+                  "iterations": int(it_p), "seconds": sec_p, "reached": ok_p, "final_drop": float(hp[-1] / hp[0]),
+                  "cl": clp, "cd": cdp, "launch_shape": list(tp_shape[:2])},
+        "warm": {"precision": "fp32 sweeps, fp64 residual/update",
+                 "start": "network prediction judged by the first residual (second order from iteration 1)"
+                 if kept else f"free stream (prediction rejected by the judge), {START} first-order iterations",
+                 "prediction_kept": kept, "iterations": int(it_w), "seconds": sec_w, "reached": ok_w,
+                 "first_norm_ratio": float(hw[0] / hp[0]), "final_norm_vs_plain_first": float(hw[-1] / hp[0]),
+                 "cl": clw, "cd": cdw, "launch_shape": list(tw_shape[:2]), "network_forward_ms": fwd_ms},
+        "time_ratio": sec_w / sec_p if ok_p and ok_w else None,
+        "iteration_ratio": it_w / it_p if ok_p and ok_w else None,
+        "dcl": abs(clw - clp), "dcd": abs(cdw - cdp),
+        "network": facts,
+        "reference": "the plain FP64 GPU path is the one checked against the FP64 oracle (parity tests: history "
+                     "1e-10 per entry, final fields 1e-9); dcl and dcd compare the warm arm with it",
+    }
 
 
 BATCH_WORKLOAD = "naca0012_batch64"
@@ -374,7 +552,7 @@ def run_batch(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     n = sum(c.n for c in clouds)
     conds = [(c["mach"], c["aoa_deg"]) for c in cases]
-    s = lskum.Solver.batch(clouds, conds, cfl=100.0, inner_iters=3, jvp=lskum.JVP_EXACT, first_order_iters=START,
+    s = lskum.Solver.batch(clouds, conds, cfl=100.0, inner_iters=2, jvp=lskum.JVP_EXACT, first_order_iters=START,
                            precision=args.precision)
     info = s.info()
     nslots = int(sum(np.count_nonzero(_memberships(c)) for c in clouds))
@@ -413,7 +591,7 @@ def run_batch(args, rank, world, local_rank):
 
     phases = s.time_phases(5)
     res_ms = phases["residual"]
-    achieved = RES_FLOPS_PER_SLOT * nslots / (res_ms / 1e3) / 1e12
+    achieved = RES_FLOPS_PER_SLOT[MID_WORKLOAD] * nslots / (res_ms / 1e3) / 1e12
 
     e2e_steps = min(args.steps, 10)
     U = s.field(lskum.FIELD_U)
@@ -434,7 +612,7 @@ def run_batch(args, rank, world, local_rank):
     cpu = None
     if world == 1:
         k0 = int(np.argmin([c.n for c in clouds]))
-        cv, cdt, cdone = cpu_baseline(clouds[k0], 10, mach=cases[k0]["mach"], aoa=cases[k0]["aoa_deg"])
+        cv, cdt, cdone = cpu_baseline(clouds[k0], 10, mach=cases[k0]["mach"], aoa=cases[k0]["aoa_deg"], K=2)
         cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{cdone} FP64 oracle iterations on the smallest case ({clouds[k0].n} points), one thread"}
     line = {
@@ -445,7 +623,7 @@ def run_batch(args, rank, world, local_rank):
         "config": {"workload": BATCH_WORKLOAD, "cases": len(cases_all), "cases_this_rank": len(cases),
                    "points": int(n_all), "failed_cases": int(failed_all),
                    "point_iterations_timed": int(work_all), "precision": "fp64" if args.precision == 0 else
-                   "fp32 sweeps, fp64 residual/update", "cfl": 100.0, "inner_iters": 3, "jvp": "exact-AD",
+                   "fp32 sweeps, fp64 residual/update", "cfl": 100.0, "inner_iters": 2, "jvp": "exact-AD",
                    "order": f"second (timed steps follow {START} untimed first-order start-up iterations)",
                    "colours": info["n_colours"],
                    "launch_shape": {"threads_per_point": tpp, "sweep_lanes_per_point": lanes,
@@ -455,6 +633,7 @@ def run_batch(args, rank, world, local_rank):
                    "l2": "inputs larger than L2"},
         "roofline": {"bound": "alu", "kernel": "k_residual", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "flops_per_active_slot": RES_FLOPS_PER_SLOT[MID_WORKLOAD],
                      "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz",
                      "launch_ms": res_ms, "phase_ms": phases},
         "cpu_baseline": cpu,
@@ -515,26 +694,12 @@ def run_warmstart(args, rank, world, local_rank):
     cloud = cg.build_workload(wl)
     K, drop, max_iters = 2, 1e-8, 60000
     rng = np.random.default_rng(cg.BASE_SEED + 5)
-    train = [(float(rng.uniform(0.3, 0.85)), float(rng.uniform(-4, 6))) for _ in range(args.train_solves)]
+    for _ in range(args.train_solves):  # the training draws come first from this generator
+        rng.uniform(0.3, 0.85), rng.uniform(-4, 6)
     test = [(float(rng.uniform(0.3, 0.85)), float(rng.uniform(-4, 6))) for _ in range(args.test_conditions)]
-    t0 = time.perf_counter()
-    net = lskum.Mlp(seed=cg.BASE_SEED, max_batch=4096)
-    failed_train = 0
-    for g0 in range(0, len(train), 64):
-        conds = train[g0:g0 + 64]
-        b = lskum.Solver.batch([cloud] * len(conds), conds, first_order_iters=START, inner_iters=K, precision=1)
-        b.run(3000)
-        failed_train += sum(1 for k in range(len(conds)) if b.case_info(k)["status"] != 0)
-        net.add_samples(b, 4096, seed=g0)
-        del b
-    torch.cuda.synchronize()
-    t_data = time.perf_counter() - t0
-    n_samp = net.n_samples()
-    epochs = max(10, min(200, int(100 * 262144 / max(n_samp, 1))))
-    t0 = time.perf_counter()
-    losses = net.train(epochs, 512, 1e-3, seed=1)
-    torch.cuda.synchronize()
-    t_train = time.perf_counter() - t0
+    net, facts = train_network(args.train_solves, cg.BASE_SEED + 5, K=K)
+    failed_train, n_samp, epochs = facts["train_failed"], facts["samples"], facts["epochs"]
+    t_data, t_train = facts["data_s"], facts["train_s"]
 
     rows = []
     for (m, a) in test:
@@ -576,7 +741,8 @@ def run_warmstart(args, rank, world, local_rank):
         "steps": max_iters, "warmup": 0, "dtype": "f64 (plain) / f64 + f32 sweeps + bf16 network (warm)",
         "data": "synthetic",
         "config": {"workload": WARM_WORKLOAD, "cloud": wl, "points": cloud.n, "inner_iters": K, "cfl": 100.0,
-                   "drop": drop, "train_solves": len(train), "train_iters": 3000, "train_failed": failed_train,
+                   "drop": drop, "train_solves": facts["train_solves"], "train_iters": 3000,
+                   "train_failed": failed_train,
                    "samples": n_samp, "epochs": epochs, "test_conditions": len(test),
                    "plain": f"FP64, {START} first-order start-up iterations, then second order, to 1e-8 x first norm",
                    "warm": "FP32 sweeps, prediction judged by the residual, second order from iteration 1, "
@@ -594,7 +760,7 @@ def run_warmstart(args, rank, world, local_rank):
             "warm_not_converged": int(sum(1 for r in rows if r["plain_ok"] and not r["warm_ok"])),
             "cl_diff_max": float(max([r["dcl"] for r in both], default=float("nan"))),
             "cd_diff_max": float(max([r["dcd"] for r in both], default=float("nan"))),
-            "data_s": t_data, "train_s": t_train, "final_loss": float(losses[-1]),
+            "data_s": t_data, "train_s": t_train, "final_loss": facts["final_loss"],
         },
         "cases": rows,
         "roofline": {"bound": "tensor", "kernel": "k_gemm (network forward, all layers)",
@@ -632,20 +798,25 @@ def _working_set_bytes(cloud):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", type=int, choices=[0, 1], default=None,
                     help="0: plain FP64 (default for the single cloud); 1: FP32 sweeps with FP64 residual "
                          "and update (default for the batch)")
-    ap.add_argument("--workload", choices=[WORKLOAD, SUPER_WORKLOAD, BATCH_WORKLOAD, WARM_WORKLOAD], default=WORKLOAD)
+    ap.add_argument("--workload", choices=[WORKLOAD, MID_WORKLOAD, PROF_WORKLOAD, SUPER_WORKLOAD, BATCH_WORKLOAD,
+                                           WARM_WORKLOAD], default=WORKLOAD)
+    ap.add_argument("--solve", choices=["on", "off"], default=None,
+                    help="time the two solves to a 1e-8 drop on the 147,584-point cloud (default: on for the "
+                         "default workload at N = 1)")
+    ap.add_argument("--solve-max", type=int, default=80000, help="iteration cap of each of those solves")
     ap.add_argument("--solve-iters", type=int, default=-1,
-                    help="single-cloud workloads: also time a whole solve to a 1e-8 drop, at most this many "
-                         "iterations (default: 0 for the transonic cloud, 30000 for the supersonic one)")
-    ap.add_argument("--train-solves", type=int, default=512, help="warm-start workload: training solves")
+                    help="single-cloud workloads: also time a whole solve of the workload itself to a 1e-8 drop, "
+                         "at most this many iterations (default: 30000 for the supersonic one, else 0)")
+    ap.add_argument("--train-solves", type=int, default=256, help="warm-start network: training solves")
     ap.add_argument("--test-conditions", type=int, default=16, help="warm-start workload: unseen conditions")
     ap.add_argument("--scheme", choices=["lusgs", "explicit"], default="lusgs",
-                    help="default workload: the implicit LU-SGS solver or the paper's explicit solver")
+                    help="single-cloud workloads: the implicit LU-SGS solver or the paper's explicit solver")
     ap.add_argument("--launch-shape", default="",
                     help="T,L: threads per point and sweep lanes per point instead of autotuning")
     args = ap.parse_args()
@@ -658,6 +829,9 @@ def main():
         args.precision = 1 if args.workload == BATCH_WORKLOAD else 0
     if args.solve_iters < 0:
         args.solve_iters = 30000 if args.workload == SUPER_WORKLOAD else 0
+    if args.solve is None:
+        args.solve = "on" if (args.workload == WORKLOAD and args.scheme == "lusgs" and args.precision == 0
+                              and not args.launch_shape) else "off"
     if args.impl == "reference":
         run_reference(args, rank)
     elif args.workload == BATCH_WORKLOAD:

@@ -304,11 +304,14 @@ def _stencils_ok_all(x, y, flag, nx, ny, off, idx, tol=1e-6, kinetic_outer=False
     return ok
 
 
-def _fix_stencils(x, y, flag, nx, ny, off, idx, cand_fn, body=None, kinetic_outer=False):
+def _fix_stencils(x, y, flag, nx, ny, off, idx, cand_fn, body=None, kinetic_outer=False, tol=1e-6):
     """Augment stencils (nearest-first candidates) until every sub-stencil is
-    well posed.  CSR in (off, idx), CSR out, and the number of points augmented."""
+    well posed: at least 2 points and a normalised determinant det / (sdd spp)
+    of its 2x2 least-squares system above tol (1 - the squared correlation of
+    the offsets along and across its direction; near 0 for nearly collinear
+    points).  CSR in (off, idx), CSR out, and the number of points augmented."""
     bad = 0
-    ok_all = _stencils_ok_all(x, y, flag, nx, ny, off, idx, kinetic_outer=kinetic_outer)
+    ok_all = _stencils_ok_all(x, y, flag, nx, ny, off, idx, tol=tol, kinetic_outer=kinetic_outer)
     new_rows = {}
     for p in np.flatnonzero(~ok_all):
         p = int(p)
@@ -317,10 +320,10 @@ def _fix_stencils(x, y, flag, nx, ny, off, idx, cand_fn, body=None, kinetic_oute
         dy = y[r] - y[p]
         kind = _kind(flag, p, kinetic_outer)
         if kind < 0:
-            ok = _full_ok(dx, dy)
+            ok = _full_ok(dx, dy, tol)
         else:
             e1, e2 = _frame(x, y, flag, nx, ny, p, kinetic_outer)
-            ok = _full_ok(dx, dy) and _substencils_ok(dx, dy, kind, e1, e2)
+            ok = _full_ok(dx, dy, tol) and _substencils_ok(dx, dy, kind, e1, e2, tol)
         if ok:
             continue
         bad += 1
@@ -338,10 +341,10 @@ def _fix_stencils(x, y, flag, nx, ny, off, idx, cand_fn, body=None, kinetic_oute
             dx = x[r] - x[p]
             dy = y[r] - y[p]
             if kind < 0:
-                ok = _full_ok(dx, dy)
+                ok = _full_ok(dx, dy, tol)
             else:
                 e1, e2 = _frame(x, y, flag, nx, ny, p, kinetic_outer)
-                ok = _full_ok(dx, dy) and _substencils_ok(dx, dy, kind, e1, e2)
+                ok = _full_ok(dx, dy, tol) and _substencils_ok(dx, dy, kind, e1, e2, tol)
             if ok:
                 break
         if not ok:
@@ -420,62 +423,60 @@ def naca0012_block(n_i: int = 160, n_j: int = 64, kinetic_outer: bool = False) -
                  dict(kind="block", n_i=n_i, n_j=n_j, augmented=bad, kinetic_outer=kinetic_outer))
 
 
-def _metric_candidates(n_i, n_j, keep, hxi, heta, exi, eeta, x, y, reach=3, chunk_rows=128):
-    """Candidate neighbours of every kept node among the nodes within +-reach
-    index steps (periodic in i, clipped in j), ordered by the distance in the
-    node's index-normalised metric: |(d xi, d eta)| where r_q - r_p =
-    h_xi d xi e_xi + h_eta d eta e_eta with the node's own spacings and
-    grid directions.
-    Returns (metric distance, candidate) arrays [n, (2 reach + 1)^2 - 1],
-    missing nodes last (distance inf, index -1)."""
-    gid = np.full(n_i * n_j, -1, dtype=np.int64)
-    gid[keep] = np.arange(int(keep.sum()))
-    gid = gid.reshape(n_j, n_i)
-    offs = [(dj, di) for dj in range(-reach, reach + 1) for di in range(-reach, reach + 1) if (di, dj) != (0, 0)]
-    odj = np.array([o[0] for o in offs])
-    odi = np.array([o[1] for o in offs])
-    kq = len(offs)
-    n = int(keep.sum())
-    dist = np.empty((n, kq))
-    nb = np.empty((n, kq), dtype=np.int64)
-    jj_all, ii_all = np.divmod(np.flatnonzero(keep), n_i)
-    for r0 in range(0, n, chunk_rows * n_i):
-        sl = slice(r0, min(n, r0 + chunk_rows * n_i))
-        jj, ii = jj_all[sl], ii_all[sl]
-        J = jj[:, None] + odj[None, :]
-        I = (ii[:, None] + odi[None, :]) % n_i
-        inside = (J >= 0) & (J < n_j)
-        q = np.where(inside, gid[np.clip(J, 0, n_j - 1), I], -1)
-        p = np.arange(sl.start, sl.stop)
-        dx = x[np.maximum(q, 0)] - x[p][:, None]
-        dy = y[np.maximum(q, 0)] - y[p][:, None]
-        # index offsets: the inverse of the local map (d xi, d eta) -> h_xi d xi
-        # e_xi + h_eta d eta e_eta applied to the offset (the grid lines are
-        # not orthogonal near the wall)
-        ax, ay = exi[0][jj, ii][:, None], exi[1][jj, ii][:, None]
-        bx, by = eeta[0][jj, ii][:, None], eeta[1][jj, ii][:, None]
-        cr = ax * by - ay * bx
-        a = (by * dx - bx * dy) / (cr * hxi[jj, ii][:, None])
-        b = (ax * dy - ay * dx) / (cr * heta[jj, ii][:, None])
-        md = np.where(q >= 0, np.hypot(a, b), np.inf)
-        order = np.argsort(md, axis=1, kind="stable")
-        dist[sl] = np.take_along_axis(md, order, axis=1)
-        nb[sl] = np.take_along_axis(q, order, axis=1)
-    return dist, nb
+def _cone_selection(x, y, flag, nx, ny, nbv, valid, m, kinetic_outer, c_min=2, cos_max=0.5):
+    """Per point, the candidates (columns of nbv, nearest first) to keep: the
+    first m[p] valid ones, plus, for each direction of a split sub-stencil the
+    point needs, the nearest valid candidates within +-60 degrees of that
+    direction until c_min of the kept ones lie in that cone.  Interior points
+    need +-x and +-y; wall points +-t and the fluid side +n; outer points
+    under the kinetic far field +-t and the inside -n; frozen outer points
+    none.  Returns a boolean [n, k] selection."""
+    n, kq = nbv.shape
+    sel = np.arange(kq)[None, :] < m[:, None]
+    wall = flag == WALL
+    framed = wall | ((flag == OUTER) & bool(kinetic_outer))
+    frozen = (flag == OUTER) & (not kinetic_outer)
+    e1x = np.where(framed, ny, 1.0)
+    e1y = np.where(framed, -nx, 0.0)
+    e2x = np.where(framed, nx, 0.0)
+    e2y = np.where(framed, ny, 1.0)
+    q = np.maximum(nbv, 0)
+    dx = x[q] - x[:, None]
+    dy = y[q] - y[:, None]
+    r = np.hypot(dx, dy)
+    a = dx * e1x[:, None] + dy * e1y[:, None]
+    b = dx * e2x[:, None] + dy * e2y[:, None]
+    dirs = [(-a, ~frozen), (a, ~frozen), (-b, ~frozen & ~wall), (b, ~frozen & ~(framed & ~wall))]
+    add = np.zeros_like(sel)
+    for comp, need_pts in dirs:
+        cone = valid & (comp >= cos_max * r) & need_pts[:, None]
+        have = np.count_nonzero(cone & sel, axis=1)
+        short = np.flatnonzero(have < c_min)
+        if short.size == 0:
+            continue
+        extra = cone[short] & ~sel[short]
+        rank = np.cumsum(extra, axis=1)
+        take = extra & (rank <= (c_min - have[short])[:, None])
+        add[short] |= take
+    return sel | add
 
 
 def naca0012_jittered(n_i: int = 640, n_j: int = 256, jitter: float = 0.15,
                       remove_frac: float = 0.10, seed: int = BASE_SEED + 2,
                       radius_factor: float = 2.5, k_min: int = 8, k_max: int = 20,
-                      kinetic_outer: bool = False, stencil: str = "euclid") -> Cloud:
+                      kinetic_outer: bool = False, stencil: str = "euclid", cond_tol: float = 1e-6) -> Cloud:
     """Jittered O-grid cloud with random interior removal and radius/kNN stencils.
 
     stencil = "euclid": the points within radius_factor local spacings
     (max(h_xi, h_eta)), nearest first (Euclidean), capped at k_max, at least
-    k_min.  stencil = "metric": the same rule in each node's index-normalised
-    metric (the offset in local index units along the grid directions), so that
-    on strongly stretched layers the stencil spans both index directions
-    instead of filling up with one side of the node's own column."""
+    k_min.  stencil = "cone": the same, then for each direction of a split
+    sub-stencil the point needs, the nearest further points within +-60
+    degrees of that direction until two of its neighbours lie there: on
+    strongly stretched layers the nearest points are the node's own column,
+    and one of its split sub-stencils would otherwise hold only points a
+    jitter away along its direction.  cond_tol: the conditioning every split
+    sub-stencil must reach (see _fix_stencils; 1e-6 only excludes exactly
+    collinear sets)."""
     from scipy.spatial import cKDTree
 
     rng = np.random.default_rng(seed)
@@ -490,7 +491,7 @@ def naca0012_jittered(n_i: int = 640, n_j: int = 256, jitter: float = 0.15,
     x = Xj.ravel()
     y = Yj.ravel()
     h = np.maximum(hxi, heta).ravel()
-    if stencil not in ("euclid", "metric"):
+    if stencil not in ("euclid", "cone"):
         raise ValueError(f"unknown stencil rule {stencil!r}")
     n0 = n_i * n_j
     flag = np.zeros(n0, dtype=np.uint8)
@@ -512,16 +513,11 @@ def naca0012_jittered(n_i: int = 640, n_j: int = 256, jitter: float = 0.15,
     widx[:n_i] = np.arange(n_i)
     wx, wy = x[:n_i].copy(), y[:n_i].copy()
 
-    if stencil == "euclid":
-        tree = cKDTree(np.stack([x, y], axis=1))
-        kq = 48
-        dist, nb = tree.query(np.stack([x, y], axis=1), k=kq + 1, workers=-1)
-        dist, nb = dist[:, 1:], nb[:, 1:]
-        radius = radius_factor * h
-    else:
-        dist, nb = _metric_candidates(n_i, n_j, keep, hxi, heta, exi, eeta, x, y)
-        kq = nb.shape[1]
-        radius = np.full(n, radius_factor)
+    tree = cKDTree(np.stack([x, y], axis=1))
+    kq = 48 if stencil == "euclid" else 64
+    dist, nb = tree.query(np.stack([x, y], axis=1), k=kq + 1, workers=-1)
+    dist, nb = dist[:, 1:], nb[:, 1:]
+    radius = radius_factor * h
     # reject neighbours seen through the aerofoil (only segments near the body
     # can: a segment that meets the wall polygon is at least as long as its end
     # point's distance to the polygon, which is at least the distance to the
@@ -532,14 +528,13 @@ def naca0012_jittered(n_i: int = 640, n_j: int = 256, jitter: float = 0.15,
             & (np.minimum(y[P], y[Q]) <= 0.07) & (np.maximum(y[P], y[Q]) >= -0.07))
     half_edge = 0.5 * float(np.max(np.hypot(np.roll(wx, -1) - wx, np.roll(wy, -1) - wy)))
     dwall, _ = cKDTree(np.stack([wx, wy], axis=1)).query(np.stack([x, y], axis=1), workers=-1)
-    seg = dist.ravel() if stencil == "euclid" else np.hypot(x[Q] - x[P], y[Q] - y[P])
-    near &= (Q >= 0) & (seg >= dwall[P] - half_edge)
+    near &= dist.ravel() >= dwall[P] - half_edge
     cross = np.zeros(P.shape[0], dtype=bool)
     ii = np.flatnonzero(near)
     cross[ii] = _crosses_body_sectors(x[P[ii]], y[P[ii]], x[Q[ii]], y[Q[ii]], wx, wy, widx[P[ii]], widx[Q[ii]],
                                       col[P[ii]], col[Q[ii]])
     cross = cross.reshape(n, kq)
-    valid = ~cross & (nb >= 0)
+    valid = ~cross
     # valid candidates first (stable: nearest first), then the count to keep
     order = np.argsort(~valid, axis=1, kind="stable")
     nbv = np.take_along_axis(nb, order, axis=1)
@@ -547,26 +542,17 @@ def naca0012_jittered(n_i: int = 640, n_j: int = 256, jitter: float = 0.15,
     nvalid = valid.sum(axis=1)
     inrad = (dv <= radius[:, None]) & (np.arange(kq)[None, :] < nvalid[:, None])
     m = np.minimum(np.minimum(np.maximum(inrad.sum(axis=1), k_min), k_max), nvalid)
-    keep = np.arange(kq)[None, :] < m[:, None]
-    flat = nbv[keep]
-    offs = np.concatenate([[0], np.cumsum(m)])
     if stencil == "euclid":
-        off, idx, bad = _fix_stencils(x, y, flag, nx, ny, offs, flat, lambda p: nbv[p][:nvalid[p]],
-                                      kinetic_outer=kinetic_outer)
+        keep = np.arange(kq)[None, :] < m[:, None]
     else:
-        # augmentation: the metric candidates, then the Euclidean nearest
-        # points (beside the trailing edge the index block holds too few on
-        # one side), each checked against the body
-        tree = cKDTree(np.stack([x, y], axis=1))
-
-        def cand(p):
-            _, e = tree.query([x[p], y[p]], k=min(n, 65))
-            return np.concatenate([nbv[p][:nvalid[p]], np.asarray(e)[1:]])
-
-        off, idx, bad = _fix_stencils(x, y, flag, nx, ny, offs, flat, cand, body=(wx, wy, widx),
-                                      kinetic_outer=kinetic_outer)
+        validv = np.arange(kq)[None, :] < nvalid[:, None]  # the valid candidates come first
+        keep = _cone_selection(x, y, flag, nx, ny, nbv, validv, m, kinetic_outer)
+    flat = nbv[keep]
+    offs = np.concatenate([[0], np.cumsum(keep.sum(axis=1))])
+    off, idx, bad = _fix_stencils(x, y, flag, nx, ny, offs, flat, lambda p: nbv[p][:nvalid[p]],
+                                  kinetic_outer=kinetic_outer, tol=cond_tol)
     return Cloud(x, y, flag, nx, ny, off, idx,
-                 dict(kind="jittered", n_i=n_i, n_j=n_j, jitter=jitter, remove_frac=remove_frac,
+                 dict(kind="jittered", cond_tol=cond_tol, n_i=n_i, n_j=n_j, jitter=jitter, remove_frac=remove_frac,
                       seed=seed, removed=n_rm, augmented=bad, kinetic_outer=kinetic_outer, stencil=stencil))
 
 
@@ -608,17 +594,30 @@ def cartesian_box(n: int = 7, m: int = 7, jitter: float = 0.2, seed: int = BASE_
                  dict(kind="box", n=n, m=m, seed=seed, augmented=bad, kinetic_outer=kinetic_outer))
 
 
+# Conditioning every split sub-stencil of the strongly stretched clouds must
+# reach (normalised determinant of its 2x2 least-squares system): 1e-6, the
+# default, only excludes exactly collinear sets, which leaves nearly collinear
+# near-wall sub-stencils of the 1280x1024 and 2560x2048 clouds, whose second-
+# order iterations then fail within tens of iterations.
+STRETCHED_COND_TOL = 0.2
+
 # Workloads of the benchmark and the parity tests (sizes and flow conditions).
 WORKLOADS = {
     "naca0012_160x64": dict(builder="block", n_i=160, n_j=64, mach=0.63, aoa_deg=2.0, cfl=100.0, iters=300),
     "naca0012_640x256_jit": dict(builder="jittered", n_i=640, n_j=256, mach=0.85, aoa_deg=1.0, cfl=100.0,
                                  iters=2000, seed=BASE_SEED + 2),
     # 2,048 layers clustered to 1.4e-4 chords at the wall against ~10x coarser
-    # tangential spacing: stencils in the index-normalised metric (the
-    # Euclidean rule fills a near-wall stencil with the node's own column and
-    # one side of it, which leaves its split sub-stencils ill conditioned)
+    # tangential spacing: the Euclidean rule fills a near-wall stencil with
+    # the node's own column and one side of it, so the stencils are completed
+    # to two neighbours within 60 degrees of every split direction and each
+    # split sub-stencil is augmented until its least-squares system is well
+    # conditioned (normalised determinant >= STRETCHED_COND_TOL)
     "naca0012_2560x2048_jit": dict(builder="jittered", n_i=2560, n_j=2048, mach=0.8, aoa_deg=1.25, cfl=100.0,
-                                   remove_frac=0.0, seed=BASE_SEED + 3, stencil="metric"),
+                                   remove_frac=0.0, seed=BASE_SEED + 3, stencil="cone", cond_tol="stretched"),
+    # a quarter-size cloud of the same construction and stencil rule as the
+    # 2560x2048 one (profiling stand-in: its device working set is ~2 GB)
+    "naca0012_1280x1024_jit": dict(builder="jittered", n_i=1280, n_j=1024, mach=0.8, aoa_deg=1.25, cfl=100.0,
+                                   remove_frac=0.0, seed=BASE_SEED + 3, stencil="cone", cond_tol="stretched"),
     # the supersonic case (Sec. 5.3: M 1.2, AoA 0) on the 147,584-point cloud,
     # with the outer stencils the kinetic far field needs
     "naca0012_640x256_jit_m1.2": dict(builder="jittered", n_i=640, n_j=256, mach=1.2, aoa_deg=0.0, cfl=100.0,
@@ -651,5 +650,7 @@ def build_workload(name: str) -> Cloud:
     ko = w.get("kinetic_outer", False)
     if w["builder"] == "block":
         return naca0012_block(w["n_i"], w["n_j"], kinetic_outer=ko)
+    tol = w.get("cond_tol", 1e-6)
     return naca0012_jittered(w["n_i"], w["n_j"], remove_frac=w.get("remove_frac", 0.10), seed=w["seed"],
-                             kinetic_outer=ko, stencil=w.get("stencil", "euclid"))
+                             kinetic_outer=ko, stencil=w.get("stencil", "euclid"),
+                             cond_tol=STRETCHED_COND_TOL if tol == "stretched" else tol)
