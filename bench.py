@@ -22,6 +22,8 @@ batched solutions, training time reported apart) -- the `solve` block.
                   [--workload W] [--solve on|off]
 
 --workload naca0012_640x256_jit runs the 147,584-point cloud (M 0.85, AoA 1);
+naca0012_160x64 the 10,240-point O-grid (M 0.63, AoA 2); naca0012_1280x1024_jit
+the quarter-size stand-in of the default cloud (profiling);
 naca0012_640x256_jit_m1.2 the paper's supersonic case (M 1.2, AoA 0) on the
 same cloud with the kinetic far field (and a whole solve, --solve-iters caps
 it); naca0012_batch64 the 64-cloud batch; naca0012_warmstart the warm-start
@@ -49,13 +51,15 @@ WORKLOAD = "naca0012_2560x2048_jit"      # default: 5,242,880 points
 MID_WORKLOAD = "naca0012_640x256_jit"    # 147,584 points
 PROF_WORKLOAD = "naca0012_1280x1024_jit"  # 1,310,720 points, the default's construction (profiling)
 SUPER_WORKLOAD = "naca0012_640x256_jit_m1.2"
+SMALL_WORKLOAD = "naca0012_160x64"        # 10,240 points, 3x3 index-block stencils
 # K = 2 inner iterations everywhere: with 3 the unlimited reconstruction
 # diverges in the coarse far field in long runs from the free stream, so
 # the solves to a 1e-8 drop use 2 and the timed steps do the same
 CASES = {WORKLOAD: dict(mach=0.8, aoa=1.25, K=2, farfield=0),
          MID_WORKLOAD: dict(mach=0.85, aoa=1.0, K=2, farfield=0),
          PROF_WORKLOAD: dict(mach=0.8, aoa=1.25, K=2, farfield=0),
-         SUPER_WORKLOAD: dict(mach=1.2, aoa=0.0, K=2, farfield=1)}
+         SUPER_WORKLOAD: dict(mach=1.2, aoa=0.0, K=2, farfield=1),
+         SMALL_WORKLOAD: dict(mach=0.63, aoa=2.0, K=2, farfield=0)}
 SOLVE_WORKLOAD = MID_WORKLOAD
 METRIC = "point-iter/s; wall time to 1e-8 residual drop, plain FP64 vs FP32+warm start"
 UNIT = "point-iter/s"
@@ -69,17 +73,20 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # cloud's Euclidean stencils, and the metric stencils of the 1,310,720-point
 # cloud, which stand for the 5,242,880-point one (the same construction; the
 # count depends on the mix of slots joining one or two sub-stencils)
-RES_FLOPS_PER_SLOT = {MID_WORKLOAD: 356.07, SUPER_WORKLOAD: 356.07}
+# 1,310,720-point launch at 1 thread per point: 2 x 3,501,632,248 dfma +
+# 1,797,345,032 dmul + 477,404,332 dadd over 26,159,870 active slots
+RES_FLOPS_PER_SLOT = {MID_WORKLOAD: 356.07, SUPER_WORKLOAD: 356.07, PROF_WORKLOAD: 354.665, WORKLOAD: 354.665}
 START = 50  # first-order start-up iterations before warm-up and timing
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one residual
 # launch at 2 threads per point, from one ncu capture of the current kernel
 # (profiles/k_residual_*.md), per workload; reported only for that launch
 # shape and FP64
-RES_TRAFFIC = {MID_WORKLOAD: {2: 164.885504e6}}
+RES_TRAFFIC = {MID_WORKLOAD: {2: 164.885504e6}, PROF_WORKLOAD: {1: 3.41828352e9},
+               WORKLOAD: {1: 13.812823e9}}  # one-pass capture of the full-size launch
 # sm__pipe_fp64_cycles_active of that launch (fraction of peak sustained): the
 # residual's binding unit; the counted-flop fraction is lower because
 # additions, multiplications and comparisons occupy the pipe like an FMA
-RES_FP64_PIPE_ACTIVE = {MID_WORKLOAD: 0.894}
+RES_FP64_PIPE_ACTIVE = {MID_WORKLOAD: 0.894, PROF_WORKLOAD: 0.8987, WORKLOAD: 0.8987}
 
 
 def _sweep_form(lanes):
@@ -804,8 +811,8 @@ def main():
     ap.add_argument("--precision", type=int, choices=[0, 1], default=None,
                     help="0: plain FP64 (default for the single cloud); 1: FP32 sweeps with FP64 residual "
                          "and update (default for the batch)")
-    ap.add_argument("--workload", choices=[WORKLOAD, MID_WORKLOAD, PROF_WORKLOAD, SUPER_WORKLOAD, BATCH_WORKLOAD,
-                                           WARM_WORKLOAD], default=WORKLOAD)
+    ap.add_argument("--workload", choices=[WORKLOAD, MID_WORKLOAD, PROF_WORKLOAD, SMALL_WORKLOAD, SUPER_WORKLOAD,
+                                           BATCH_WORKLOAD, WARM_WORKLOAD], default=WORKLOAD)
     ap.add_argument("--solve", choices=["on", "off"], default=None,
                     help="time the two solves to a 1e-8 drop on the 147,584-point cloud (default: on for the "
                          "default workload at N = 1)")
