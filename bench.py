@@ -165,7 +165,7 @@ def _gpu_id(torch, dev):
         return str(dev)
 
 
-def cpu_baseline(cloud, iters, warm=0, mach=0.85, aoa=1.0, K=2, farfield=0, startup=1):
+def cpu_baseline(cloud, iters, warm=0, mach=0.85, aoa=1.0, K=2, farfield=0, startup=1, jvp=0):
     """The FP64 oracle, as it stands, on one host core: `iters` iterations
     timed after `startup` first-order start-up and `warm` warm-up iterations
     (startup = 0: the first `iters` iterations from the free stream, all
@@ -176,10 +176,10 @@ def cpu_baseline(cloud, iters, warm=0, mach=0.85, aoa=1.0, K=2, farfield=0, star
     U = o.initial_state(mach, aoa)
     n0, hist0 = 0, 0.0
     if startup + warm > 0:
-        r0 = o.run(U, startup + warm, cfl=100.0, K=K, first_order=startup)
+        r0 = o.run(U, startup + warm, cfl=100.0, K=K, first_order=startup, jvp=jvp)
         U, n0, hist0 = r0["U"], startup + warm, r0["hist0"]
     t0 = time.perf_counter()
-    r = o.run(U, iters, cfl=100.0, K=K, n0=n0, hist0=hist0, first_order=startup if startup else iters)
+    r = o.run(U, iters, cfl=100.0, K=K, n0=n0, hist0=hist0, first_order=startup if startup else iters, jvp=jvp)
     dt = time.perf_counter() - t0
     return cloud.n * r["done"] / dt, dt, r["done"]
 
@@ -267,7 +267,8 @@ def run_ours(args, rank, world, local_rank):
     n = cloud.n
     explicit = args.scheme == "explicit"
     cfl = 0.3 if explicit else 100.0
-    kw = dict(cfl=cfl, inner_iters=K, jvp=lskum.JVP_EXACT, first_order_iters=START, precision=args.precision,
+    jvp = lskum.JVP_INCREMENT if args.jvp == "increment" else lskum.JVP_EXACT
+    kw = dict(cfl=cfl, inner_iters=K, jvp=jvp, first_order_iters=START, precision=args.precision,
               scheme=lskum.SCHEME_EXPLICIT if explicit else lskum.SCHEME_LUSGS, farfield=case["farfield"])
     s = lskum.Solver(cloud, mach, aoa, **kw)
     nslots = int(np.count_nonzero(_memberships(cloud, kinetic)))
@@ -354,7 +355,7 @@ def run_ours(args, rank, world, local_rank):
     if world == 1:
         steps, warm, startup = _cpu_sample(wl, 1 if wl == WORKLOAD else 10, 0)
         cv, cdt, cdone = cpu_baseline(cloud, steps, warm, mach=mach, aoa=aoa, K=K, farfield=case["farfield"],
-                                      startup=startup)
+                                      startup=startup, jvp=jvp)
         cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": _sample_text(cdone, warm, startup, n)}
     ws = _working_set_bytes(cloud)
@@ -369,7 +370,7 @@ def run_ours(args, rank, world, local_rank):
                    "far_field": "kinetic (outer points updated, free-stream ghosts)" if kinetic
                    else "free stream held at the outer points",
                    "scheme": "explicit (forward Euler, no sweeps)" if explicit else "implicit LU-SGS",
-                   "jvp": "exact-AD",
+                   "jvp": "increment (split-flux differences)" if args.jvp == "increment" else "exact-AD",
                    "order": f"second (timed steps follow {START} untimed first-order start-up iterations)",
                    "colours": info["n_colours"],
                    "launch_shape": {"threads_per_point": tpp, "sweep_lanes_per_point": lanes,
@@ -401,6 +402,9 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+FWD_POINTS = 131072  # points of the timed forward pass of the network (one launch)
+
+
 def train_network(n_solves, seed, K=2):
     """The warm-start network trained on the solver's own solutions: batched
     FP32-sweep solves of the 160x64 cloud at n_solves random (M, AoA)
@@ -416,7 +420,7 @@ def train_network(n_solves, seed, K=2):
     train = [(float(rng.uniform(0.3, 0.85)), float(rng.uniform(-4, 6))) for _ in range(n_solves)]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    net = lskum.Mlp(seed=cg.BASE_SEED, max_batch=4096)
+    net = lskum.Mlp(seed=cg.BASE_SEED, max_batch=FWD_POINTS)  # buffers for one forward tile set
     failed = 0
     for g0 in range(0, len(train), 64):
         conds = train[g0:g0 + 64]
@@ -474,7 +478,8 @@ def solve_block(args, torch):
     sec_w = time.perf_counter() - t0
     clw, cdw = sw.forces()
     sw.close()
-    fwd_ms = net.time_forward(cloud.n, 5)
+    net.time_forward(FWD_POINTS, 3)
+    fwd_ms = net.time_forward(FWD_POINTS, 20)
     net.close()
     ok_p = bool(hp[-1] <= target)
     ok_w = bool(st_w == 0 and hw[-1] <= target)
@@ -489,7 +494,8 @@ def solve_block(args, torch):
                  if kept else f"free stream (prediction rejected by the judge), {START} first-order iterations",
                  "prediction_kept": kept, "iterations": int(it_w), "seconds": sec_w, "reached": ok_w,
                  "first_norm_ratio": float(hw[0] / hp[0]), "final_norm_vs_plain_first": float(hw[-1] / hp[0]),
-                 "cl": clw, "cd": cdw, "launch_shape": list(tw_shape[:2]), "network_forward_ms": fwd_ms},
+                 "cl": clw, "cd": cdw, "launch_shape": list(tw_shape[:2]),
+                 "network_forward_ms_per_131072_points": fwd_ms},
         "time_ratio": sec_w / sec_p if ok_p and ok_w else None,
         "iteration_ratio": it_w / it_p if ok_p and ok_w else None,
         "dcl": abs(clw - clp), "dcd": abs(cdw - cdp),
@@ -612,6 +618,34 @@ def run_batch(args, rank, world, local_rank):
     e2e_dt = time.perf_counter() - t0
     e2e = {"value": world * work / args.steps * e2e_steps / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": int(U.nbytes),
            "d2h_bytes_per_step": int(U.nbytes) + 8}
+    rates = None
+    if args.solve_iters > 0:
+        # per-case convergence: run on, then extrapolate each running case's
+        # iterations to a 1e-8 drop from its rate over the last half
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.run(args.solve_iters)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        per = []
+        for k in range(len(cases)):
+            inf = s.case_info(k)
+            h = s.case_residuals(k)
+            if inf["status"] != 0 or len(h) < 200:
+                per.append({"case": k, "status": inf["status"], "iters": inf["iters"]})
+                continue
+            m = len(h) // 2
+            r = (h[-1] / h[m]) ** (1.0 / (len(h) - 1 - m))
+            drop = h[-1] / h[0]
+            est = len(h) + (np.log(1e-8 / drop) / np.log(r) if r < 1.0 and drop > 1e-8 else 0.0)
+            per.append({"case": k, "points": clouds[k].n, "iters": len(h), "drop": float(drop), "rate": float(r),
+                        "iters_to_1e-8_est": float(est) if r < 1.0 else None})
+        ok = [q for q in per if q.get("iters_to_1e-8_est")]
+        rates = {"extra_iters": args.solve_iters, "seconds": sec, "cases": per,
+                 "est_iters_to_1e-8_median": float(np.median([q["iters_to_1e-8_est"] for q in ok])) if ok else None,
+                 "est_iters_to_1e-8_max": float(max(q["iters_to_1e-8_est"] for q in ok)) if ok else None,
+                 "estimate": "iterations so far + log(1e-8 / drop) / log(rate), rate per iteration over the last "
+                             "half of the history"}
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -648,6 +682,8 @@ def run_batch(args, rank, world, local_rank):
         "gpu_launches": info["launches_per_iter"] * args.steps,
         "clocks": clk.summary(),
     }
+    if rates is not None:
+        line["per_case_convergence"] = rates
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -737,10 +773,10 @@ def run_warmstart(args, rank, world, local_rank):
     both = [r for r in rows if r["plain_ok"] and r["warm_ok"]]
     ratio = np.array([r["warm_s"] / r["plain_s"] for r in both]) if both else np.array([np.inf])
     it_ratio = np.array([r["warm_iters"] / r["plain_iters"] for r in both]) if both else np.array([np.inf])
-    net.time_forward(cloud.n, 3)
-    fwd_ms = net.time_forward(cloud.n, 20)
-    mlp_flops = 2.0 * (34 * 128 + 3 * 128 * 128 + 128 * 4) * cloud.n
-    bf16_peak = 1944.1  # measured bf16 dense (cuBLAS burst) on this GPU type
+    net.time_forward(FWD_POINTS, 3)
+    fwd_ms = net.time_forward(FWD_POINTS, 20)
+    mlp_flops = 2.0 * (34 * 128 + 3 * 128 * 128 + 128 * 4) * FWD_POINTS
+    bf16_peak, peak_src = _bf16_peak()
     line = {
         "metric": "wall time to a 1e-8 residual drop, FP32 sweeps + learned warm start vs plain FP64 from the "
                   "free stream (ratio, median over unseen conditions)",
@@ -770,12 +806,23 @@ def run_warmstart(args, rank, world, local_rank):
             "data_s": t_data, "train_s": t_train, "final_loss": facts["final_loss"],
         },
         "cases": rows,
-        "roofline": {"bound": "tensor", "kernel": "k_gemm (network forward, all layers)",
+        "roofline": {"bound": "tensor", "kernel": "k_mlp_fused (network forward, all five layers)",
                      "achieved": mlp_flops / (fwd_ms / 1e3) / 1e12, "peak": bf16_peak, "unit": "TFLOP/s",
                      "frac": mlp_flops / (fwd_ms / 1e3) / 1e12 / bf16_peak, "traffic": None,
-                     "forward_ms": fwd_ms, "flops": mlp_flops, "peak_source": "measured bf16 dense (cuBLAS burst)"},
+                     "forward_ms": fwd_ms, "points": FWD_POINTS, "flops": mlp_flops, "peak_source": peak_src},
     }
     print(json.dumps(line), flush=True)
+
+
+def _bf16_peak():
+    """Dense bf16 peak (TFLOP/s) for a kernel timed alone: the burst figure of
+    MEASURED_PEAKS.json when present, else the profiling fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            v = float(json.load(f)["bf16_tflops"])
+        return v, "measured: MEASURED_PEAKS.json bf16_tflops (cuBLAS burst)"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback: 1.9 PFLOP/s bf16 burst"
 
 
 def _memberships(cloud, kinetic=False):
@@ -820,8 +867,12 @@ def main():
     ap.add_argument("--solve-iters", type=int, default=-1,
                     help="single-cloud workloads: also time a whole solve of the workload itself to a 1e-8 drop, "
                          "at most this many iterations (default: 30000 for the supersonic one, else 0)")
-    ap.add_argument("--train-solves", type=int, default=256, help="warm-start network: training solves")
+    ap.add_argument("--train-solves", type=int, default=None,
+                    help="warm-start network: training solves (default 256 for the solve block, 512 for the "
+                         "warm-start study)")
     ap.add_argument("--test-conditions", type=int, default=16, help="warm-start workload: unseen conditions")
+    ap.add_argument("--jvp", choices=["exact", "increment"], default="exact",
+                    help="single-cloud workloads: exact (forward-mode AD) or increment Jacobian-vector products")
     ap.add_argument("--scheme", choices=["lusgs", "explicit"], default="lusgs",
                     help="single-cloud workloads: the implicit LU-SGS solver or the paper's explicit solver")
     ap.add_argument("--launch-shape", default="",
@@ -836,9 +887,11 @@ def main():
         args.precision = 1 if args.workload == BATCH_WORKLOAD else 0
     if args.solve_iters < 0:
         args.solve_iters = 30000 if args.workload == SUPER_WORKLOAD else 0
+    if args.train_solves is None:
+        args.train_solves = 512 if args.workload == WARM_WORKLOAD else 256
     if args.solve is None:
         args.solve = "on" if (args.workload == WORKLOAD and args.scheme == "lusgs" and args.precision == 0
-                              and not args.launch_shape) else "off"
+                              and args.jvp == "exact" and not args.launch_shape) else "off"
     if args.impl == "reference":
         run_reference(args, rank)
     elif args.workload == BATCH_WORKLOAD:
