@@ -57,3 +57,41 @@ def test_batch_sharding_and_combining_over_gloo_ranks(world):
     assert ms == 10.0 + 2.5 * (world - 1)                    # slowest rank
     assert work == total and ncase == ncases                 # summed work
     assert max(loads) <= 1.1 * min(loads)                    # balanced
+
+
+def _rank_cloud(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    import numpy as np
+
+    import bench
+    os.environ["TMPDIR"] = os.environ.get("LSKUM_TEST_TMP", "/tmp")
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        c = bench._shared_cloud("naca0012_160x64", rank, world, dist)
+        h = [float(np.sum(c.x)), float(np.sum(c.y)), int(np.sum(c.nbr_idx)), int(c.nbr_off[-1]), int(c.n)]
+        allh = [None] * world
+        dist.all_gather_object(allh, h)
+        if rank == 0:
+            q.put(allh)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_ranks_share_one_cloud_built_on_rank_0(tmp_path):
+    """With several ranks, rank 0 builds the workload's cloud once and the
+    others load it from a temporary file: every rank holds the same arrays
+    (and the file is gone afterwards)."""
+    world = 2
+    os.environ["LSKUM_TEST_TMP"] = str(tmp_path)
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_rank_cloud, args=(r, world, port, q)) for r in range(world)]
+    for p in ps:
+        p.start()
+    allh = q.get(timeout=120)
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert allh[0] == allh[1] and allh[0][4] == 10240
+    assert not list(tmp_path.iterdir())
