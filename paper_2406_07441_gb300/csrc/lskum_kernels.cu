@@ -1151,7 +1151,7 @@ __global__ void __launch_bounds__(kSweepBlock) k_sweep_packed(Dev d, StateSet st
         }
     }
     const size_t base = (size_t)d.lp_goff[dir][g] + lane;
-#pragma unroll 2
+#pragma unroll 4
     for (int j = s; j < len; j += kLanesPerPoint) {
         const size_t e = base + 32 * (size_t)(j / kLanesPerPoint);
         const int i = d.lp_nbr[dir][e], mb = d.lp_mb[dir][e];

@@ -30,10 +30,11 @@ def _consts():
     eshift = int(re.search(r"kErfcxShift = (\d+);", s).group(1))
     key0 = int(re.search(r"kErfcxKey0 = (0x[0-9a-f]+);", s).group(1), 16)
     n = int(re.search(r"kExpN = (\d+);", s).group(1))
+    edeg = int(re.search(r"kExpDeg = (\d+);", s).group(1))
     shift = int(re.search(r"kExpShift = (\d+);", s).group(1))
     return dict(inv=scalar("kExpInvLn2N"), hi=scalar("kExpLn2NHi"), lo=scalar("kExpLn2NLo"), n=n, shift=shift,
                 tab=array("kExpTable"), sc=array("kErfcxScale"), off=array("kErfcxOffset"), ecx=ecx, deg=deg,
-                eshift=eshift, key0=key0)
+                eshift=eshift, key0=key0, deg_exp=edeg)
 
 
 C = _consts()
@@ -67,8 +68,8 @@ def exp_t(x):
     kd = t - big
     r = fma(kd, -C["hi"], x)
     r = fma(kd, -C["lo"], r)
-    h = fma(r, 1.0 / 24.0, 1.0 / 6.0)
-    h = fma(r, h, 0.5)
+    assert C["deg_exp"] == 3
+    h = fma(r, 1.0 / 6.0, 0.5)
     p = fma(mul(r, r), h, r)
     e = C["tab"][k & (C["n"] - 1)]
     res = fma(e, p, e)
