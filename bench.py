@@ -70,23 +70,22 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # FP64 flops (DFMA = 2) the residual kernel executes per neighbour slot that
 # joins a split sub-stencil, counted by ncu (2 x dfma + dmul + dadd thread
 # instructions of one launch / such slots; see profiles/): the 147,584-point
-# cloud's Euclidean stencils, and the metric stencils of the 1,310,720-point
-# cloud, which stand for the 5,242,880-point one (the same construction; the
+# cloud's Euclidean stencils (2,926,611 slots at 2 threads per point), and
+# the cone-completed stencils of the 1,310,720-point cloud (26,159,870 slots
+# at 1 thread per point: 2 x 3,240,043,812 + 1,797,370,444 + 477,404,332),
+# which stand for the 5,242,880-point cloud of the same construction (the
 # count depends on the mix of slots joining one or two sub-stencils)
-# 1,310,720-point launch at 1 thread per point: 2 x 3,501,632,248 dfma +
-# 1,797,345,032 dmul + 477,404,332 dadd over 26,159,870 active slots
-RES_FLOPS_PER_SLOT = {MID_WORKLOAD: 356.07, SUPER_WORKLOAD: 356.07, PROF_WORKLOAD: 354.665, WORKLOAD: 354.665}
+RES_FLOPS_PER_SLOT = {MID_WORKLOAD: 336.07, SUPER_WORKLOAD: 336.07, PROF_WORKLOAD: 334.668, WORKLOAD: 334.668}
 START = 50  # first-order start-up iterations before warm-up and timing
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one residual
-# launch at 2 threads per point, from one ncu capture of the current kernel
-# (profiles/k_residual_*.md), per workload; reported only for that launch
-# shape and FP64
-RES_TRAFFIC = {MID_WORKLOAD: {2: 164.885504e6}, PROF_WORKLOAD: {1: 3.41828352e9},
-               WORKLOAD: {1: 13.812823e9}}  # one-pass capture of the full-size launch
+# launch, from one ncu capture of the current kernel (profiles/), per
+# workload and threads per point; reported only for that launch shape and FP64
+RES_TRAFFIC = {MID_WORKLOAD: {2: 164.582144e6}, PROF_WORKLOAD: {1: 3.388122624e9},
+               WORKLOAD: {1: 13.973204224e9}}  # the last from a one-pass capture of the full-size launch
 # sm__pipe_fp64_cycles_active of that launch (fraction of peak sustained): the
 # residual's binding unit; the counted-flop fraction is lower because
 # additions, multiplications and comparisons occupy the pipe like an FMA
-RES_FP64_PIPE_ACTIVE = {MID_WORKLOAD: 0.894, PROF_WORKLOAD: 0.8987, WORKLOAD: 0.8987}
+RES_FP64_PIPE_ACTIVE = {MID_WORKLOAD: 0.8891, PROF_WORKLOAD: 0.9008, WORKLOAD: 0.9008}
 
 
 def _sweep_form(lanes):

@@ -17,11 +17,13 @@ e = -5 .. 3 (132 in all, the last one [9, 9.5) holding only the clamp value
 9): the interval of x is the high word of x shifted right by 16 (its
 exponent and top four significand bits) minus that of 2^-5, plus one,
 floored at 0 -- two integer instructions.  On each interval the Chebyshev
-interpolant of degree 9 at Chebyshev points of the first kind, rewritten as
+interpolant of degree 8 at Chebyshev points of the first kind, rewritten as
 a polynomial in t = (x - c)/h (c, h the interval's centre and half width)
-and evaluated by Horner's rule; the interpolants are within 4e-17 relative
+and evaluated by Horner's rule; the interpolants are within 6e-17 relative
 of erfcx in exact arithmetic (checked at 200 points per interval with
-mpmath), so the evaluation's rounding dominates.  The kernels use it as
+mpmath; the worst, 5.9e-17, on [8, 8.5], where E < 1e-28), so the
+evaluation's rounding dominates (degree 9 reached 4e-17 at one FMA more per
+split flux).  The kernels use it as
   A = (1 + s erf S)/2 = 1 - E (s S >= 0)  or  E (s S < 0),
   E = exp(-S^2) erfcx(|S|) / 2,
 which shares exp(-S^2) with the B term of the split flux and is accurate in
@@ -55,7 +57,7 @@ def _intervals():
 
 
 INTERVALS = _intervals()
-DEGREE = 9
+DEGREE = 8
 EXP_N = 4096
 EXP_DEG = 3
 
@@ -151,7 +153,7 @@ def main():
             p = mp.mpf(0)
             for m in reversed(mono):
                 p = p * t + m
-            assert abs(p / erfcx(x) - 1) < 4e-17, (a, b, x)
+            assert abs(p / erfcx(x) - 1) < 6e-17, (a, b, x)
         coef_rows.append([hexd(m / 2) for m in mono])  # E = exp(-S^2) * (erfcx/2)
         sc.append(hexd(1 / h))
         off.append(hexd(-c / h))
