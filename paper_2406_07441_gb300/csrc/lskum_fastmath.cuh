@@ -1,14 +1,15 @@
 // FP64 elementary functions of the split fluxes, shaped for GB300's scarce
 // FP64 issue rate (1/64 of FP32): everything that can run on the integer
 // pipes (range-reduction index, exponent scaling, interval selection, sign
-// tests) does, and exp(-S^2) is shared between the two places a split flux
-// needs it.  Constants: lskum_mathconst.h (gen_mathconst.py documents the
+// tests, the multiplications: mul_i) does, and exp(-S^2) is shared between
+// the two places a split flux needs it.  Constants: lskum_mathconst.h (gen_mathconst.py documents the
 // methods and their accuracy).  The tables are read per thread at diverging
 // indices, which would serialise constant-cache reads, so they live in
 // memory: the kernels that evaluate them at every point (the residual and
 // the update) stage a copy in shared memory; the sweeps, which
 // need them only at wall and outer points, read one global copy (g_math).
 #pragma once
+#include "lskum_intmul.cuh"
 #include "lskum_mathconst.h"
 
 namespace lskum {
@@ -43,7 +44,7 @@ __device__ __forceinline__ double exp_t(const MathTables &T, double x)
     r = fma(kd, -kExpLn2NLo, r);                            // |r| <= ln2/(2N)
     static_assert(kExpDeg == 3, "exp_t evaluates a cubic");
     const double h = fma(r, 1.0 / 6.0, 0.5);
-    const double p = fma(r * r, h, r);                      // e^r - 1
+    const double p = fma(mul_i(r, r), h, r);                // e^r - 1
     const double e = T.exp2j[k & (kExpN - 1)];
     const double res = fma(e, p, e);                        // 2^(j/N) e^r
     return __hiloint2double(__double2hiint(res) + ((k >> kExpShift) << 20), __double2loint(res));
@@ -69,8 +70,8 @@ __device__ __forceinline__ void split_E(const MathTables &T, double S, double &E
     double p = c[kErfcxDeg];
 #pragma unroll
     for (int j = kErfcxDeg - 1; j >= 0; j--) p = fma(p, t, c[j]);
-    eS = exp_t(T, -a * a);
-    E = eS * p;
+    eS = exp_t(T, -mul_i(a, a));
+    E = mul_i(eS, p);
 }
 
 // A = (1 + sg erf S)/2 (sg = +1 if pos, else -1) and eS = exp(-S^2).

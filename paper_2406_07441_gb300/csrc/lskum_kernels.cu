@@ -21,6 +21,11 @@
 // formed once and gathered; exp and A = (1 + s erf S)/2 are the kernels' own
 // (lskum_fastmath.cuh), which share exp(-S^2) and keep index work off the
 // FP64 pipe, as are signs and multiplications by 2 and 1/2 (integer steps).
+// In the residual, the update and the elementary functions every other FP64
+// multiplication runs on the integer pipes too (mul_i, lskum_intmul.cuh:
+// correctly rounded, the same bits), leaving the FP64 pipe the fused
+// multiply-adds and additions; the sweeps, bound by the latency of their
+// dependent chains rather than by FP64 issue, keep the FP64 multiply.
 #include "lskum_internal.h"
 
 #include <cstdint>
@@ -121,19 +126,19 @@ __device__ __forceinline__ Prim q_to_prim(const MathTables &T, const double q[4]
     Prim P;
     const double beta = signed_by(half_of(q[3]), false);  // -q4/2, the sign by XOR
     P.isb = rsqrt(beta);
-    const double ib = P.isb * P.isb;   // 1/beta
-    const double r = ib * ib * P.isb;  // beta^(-5/2)
+    const double ib = mul_i(P.isb, P.isb);          // 1/beta
+    const double r = mul_i(mul_i(ib, ib), P.isb);  // beta^(-5/2)
     const double i2b = half_of(ib);    // 1/(2 beta)
-    P.sb = beta * P.isb;
-    P.u = q[1] * i2b;
-    P.v = q[2] * i2b;
-    const double q2 = P.u * P.u + P.v * P.v;
-    P.rho = exp_t(T, fma(beta, q2, q[0])) * r;
-    P.p = P.rho * i2b;
-    const double k = half_of(P.rho * q2);
+    P.sb = mul_i(beta, P.isb);
+    P.u = mul_i(q[1], i2b);
+    P.v = mul_i(q[2], i2b);
+    const double q2 = fma(P.u, P.u, mul_i(P.v, P.v));
+    P.rho = mul_i(exp_t(T, fma(beta, q2, q[0])), r);
+    P.p = mul_i(P.rho, i2b);
+    const double k = half_of(mul_i(P.rho, q2));
     P.e1 = fma(3.5, P.p, k);
     P.e2 = fma(3.0, P.p, k);
-    P.bk = kInv2SqrtPi * P.isb;
+    P.bk = mul_i(kInv2SqrtPi, P.isb);
     return P;
 }
 
@@ -144,27 +149,27 @@ template <int DIR>
 __device__ __forceinline__ void split_flux(const MathTables &T, const Prim &P, double dx, double dy, bool pos,
                                           double G[4])
 {
-    const double ud = DIR == 0 ? P.u : (DIR == 1 ? P.v : P.u * dx + P.v * dy);
-    const double S = ud * P.sb;
+    const double ud = DIR == 0 ? P.u : (DIR == 1 ? P.v : fma(P.u, dx, mul_i(P.v, dy)));
+    const double S = mul_i(ud, P.sb);
     double A, eS;
     split_A(T, S, pos, A, eS);
-    const double B = eS * P.bk;
+    const double B = mul_i(eS, P.bk);
     const double sB = signed_by(B, pos);
     const double M1 = fma(ud, A, sB);
-    const double rm = P.rho * M1;
-    const double pA = P.p * A;
+    const double rm = mul_i(P.rho, M1);
+    const double pA = mul_i(P.p, A);
     G[0] = rm;
     if (DIR == 0) {
         G[1] = fma(rm, P.u, pA);
-        G[2] = rm * P.v;
+        G[2] = mul_i(rm, P.v);
     } else if (DIR == 1) {
-        G[1] = rm * P.u;
+        G[1] = mul_i(rm, P.u);
         G[2] = fma(rm, P.v, pA);
     } else {
-        G[1] = fma(rm, P.u, pA * dx);
-        G[2] = fma(rm, P.v, pA * dy);
+        G[1] = fma(rm, P.u, mul_i(pA, dx));
+        G[2] = fma(rm, P.v, mul_i(pA, dy));
     }
-    G[3] = fma(ud * P.e1, A, P.e2 * sB);
+    G[3] = fma(mul_i(ud, P.e1), A, mul_i(P.e2, sB));
 }
 
 // Primal quantities of a conserved state for the Jacobian products (FP64,
@@ -180,17 +185,18 @@ __device__ __forceinline__ PrimU prim_from_cons(const double U[4])
     PrimU P;
     P.rho = U[0];
     P.irho = 1.0 / U[0];
-    P.u = U[1] * P.irho;
-    P.v = U[2] * P.irho;
-    P.q2 = P.u * P.u + P.v * P.v;
-    P.p = kGm1 * (U[3] - 0.5 * P.rho * P.q2);
+    P.u = mul_i(U[1], P.irho);
+    P.v = mul_i(U[2], P.irho);
+    P.q2 = fma(P.u, P.u, mul_i(P.v, P.v));
+    const double hr = half_of(P.rho);
+    P.p = mul_i(kGm1, fma(-hr, P.q2, U[3]));
+    const double k = mul_i(hr, P.q2);  // rho |u|^2 / 2
     P.i2p = 0.5 / P.p;
-    P.beta = P.rho * P.i2p;
+    P.beta = mul_i(P.rho, P.i2p);
     P.sb = sqrt(P.beta);
     P.isb = 1.0 / P.sb;
-    const double k = 0.5 * P.rho * P.q2;
-    P.e1 = 3.5 * P.p + k;
-    P.e2 = 3.0 * P.p + k;
+    P.e1 = fma(3.5, P.p, k);
+    P.e2 = fma(3.0, P.p, k);
     return P;
 }
 
@@ -479,7 +485,13 @@ __device__ __forceinline__ double zero_like(double x)
 }
 
 template <int TPP, bool COMP>
-__global__ void __launch_bounds__(128) k_residual(Dev d, StateSet st, const double *__restrict__ g)
+// Blocks of the residual kept resident per SM: 4 x 128 threads caps it at
+// 128 registers without spills (5 spills and runs slower; with no cap the
+// integer multiplies take it to 139 registers and 3 blocks).
+#ifndef LSKUM_RES_MIN_BLOCKS
+#define LSKUM_RES_MIN_BLOCKS 4
+#endif
+__global__ void __launch_bounds__(128, LSKUM_RES_MIN_BLOCKS) k_residual(Dev d, StateSet st, const double *__restrict__ g)
 {
     __shared__ MathTables T;
     if (halted(d.ctrl)) return;
@@ -1344,10 +1356,10 @@ __global__ void __launch_bounds__(256) k_update(Dev d, int cur, bool inc, bool p
 #pragma unroll
     for (int c = 0; c < 4; c++) dst.U[c * ld + k] = U[c];
     // q1 = ln rho + 2.5 ln beta - beta |u|^2 with one logarithm: ln(rho beta^2 sqrt(beta))
-    dst.q[0 * ld + k] = log(P.rho * (P.beta * P.beta) * P.sb) - P.beta * P.q2;
-    dst.q[1 * ld + k] = 2.0 * P.beta * P.u;
-    dst.q[2 * ld + k] = 2.0 * P.beta * P.v;
-    dst.q[3 * ld + k] = -2.0 * P.beta;
+    dst.q[0 * ld + k] = fma(-P.beta, P.q2, log(mul_i(mul_i(P.rho, mul_i(P.beta, P.beta)), P.sb)));
+    dst.q[1 * ld + k] = mul_i(twice(P.beta), P.u);
+    dst.q[2 * ld + k] = mul_i(twice(P.beta), P.v);
+    dst.q[3 * ld + k] = signed_by(twice(P.beta), false);
     double *pr = dst.prim + (size_t)k * kPrimStride;
     pr[P_RHO] = P.rho;
     pr[P_IRHO] = P.irho;
@@ -1361,23 +1373,24 @@ __global__ void __launch_bounds__(256) k_update(Dev d, int cur, bool inc, bool p
     pr[P_Q2] = P.q2;
     pr[P_E1] = P.e1;
     pr[P_E2] = P.e2;
-    const double sx = P.u * P.sb, sy = P.v * P.sb;
+    const double sx = mul_i(P.u, P.sb), sy = mul_i(P.v, P.sb);
     double Ex, ex, Ey, ey;
     split_E(T, sx, Ex, ex);
     split_E(T, sy, Ey, ey);
-    const double bx = ex * kInv2SqrtPi * P.isb, by = ey * kInv2SqrtPi * P.isb;
-    pr[P_BSX] = 2.0 * bx * sx;
+    const double bk = mul_i(kInv2SqrtPi, P.isb);
+    const double bx = mul_i(ex, bk), by = mul_i(ey, bk);
+    pr[P_BSX] = mul_i(twice(bx), sx);
     pr[P_APX] = sx >= 0.0 ? 1.0 - Ex : Ex;
     pr[P_AMX] = sx >= 0.0 ? Ex : 1.0 - Ex;
-    pr[P_EKX] = ex * kInvSqrtPi;
+    pr[P_EKX] = mul_i(ex, kInvSqrtPi);
     pr[P_BX] = bx;
-    pr[P_BSY] = 2.0 * by * sy;
+    pr[P_BSY] = mul_i(twice(by), sy);
     pr[P_APY] = sy >= 0.0 ? 1.0 - Ey : Ey;
     pr[P_AMY] = sy >= 0.0 ? Ey : 1.0 - Ey;
-    pr[P_EKY] = ey * kInvSqrtPi;
+    pr[P_EKY] = mul_i(ey, kInvSqrtPi);
     pr[P_BY] = by;
-    pr[P_UE1] = P.u * P.e1;
-    pr[P_VE1] = P.v * P.e1;
+    pr[P_UE1] = mul_i(P.u, P.e1);
+    pr[P_VE1] = mul_i(P.v, P.e1);
     if (dst.primf) {  // mixed precision: the sweeps' FP32 copy of the record
         float *pf = dst.primf + (size_t)k * kPrimStride;
 #pragma unroll
