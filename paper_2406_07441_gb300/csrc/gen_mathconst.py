@@ -18,12 +18,18 @@ e = -5 .. 3 (132 in all, the last one [9, 9.5) holding only the clamp value
 exponent and top four significand bits) minus that of 2^-5, plus one,
 floored at 0 -- two integer instructions.  On each interval the Chebyshev
 interpolant of degree 8 at Chebyshev points of the first kind, rewritten as
-a polynomial in t = (x - c)/h (c, h the interval's centre and half width)
-and evaluated by Horner's rule; the interpolants are within 6e-17 relative
-of erfcx in exact arithmetic (checked at 200 points per interval with
-mpmath; the worst, 5.9e-17, on [8, 8.5], where E < 1e-28), so the
-evaluation's rounding dominates (degree 9 reached 4e-17 at one FMA more per
-split flux).  The kernels use it as
+a polynomial in t = (x - c)/h (c, h the interval's centre and half width;
+on the binade intervals t is 2u - 1 with u the significand bits below the
+top four); the interpolants are within 6e-17 relative of erfcx in exact
+arithmetic (checked at 200 points per interval with mpmath; the worst,
+5.9e-17, on [8, 8.5], where E < 1e-28).  The kernels evaluate them by
+Horner's rule in 64-bit fixed point on the integer pipes
+(lskum_fixmath.cuh): coefficients of erfcx/2 in units of 2^-(62+s), the
+scale s per interval the largest that keeps every Horner partial sum below
+1.5 in magnitude on [-1, 1]; the generator runs those integer steps exactly
+at the same 200 points and checks them against the exact-arithmetic
+polynomial (within 2e-17 relative before the final rounding).  The kernels
+use it as
   A = (1 + s erf S)/2 = 1 - E (s S >= 0)  or  E (s S < 0),
   E = exp(-S^2) erfcx(|S|) / 2,
 which shares exp(-S^2) with the B term of the split flux and is accurate in
@@ -142,26 +148,45 @@ def main():
     lines.append("{")
     lines.append("    return max(0, (ha >> kErfcxShift) - kErfcxKey0 + 1);")
     lines.append("}")
-    lines.append("// then scale 1/h and offset -c/h of t = (x - c)/h per interval")
-    coef_rows, sc, off = [], [], []
+    coef_rows, shifts = [], []
     for a, b in INTERVALS:
         mono, c, h = cheb_monomial(erfcx, a, b, DEGREE)
-        # the interpolant in exact arithmetic, at 200 points of the interval
+        half = [m / 2 for m in mono]  # E = exp(-S^2) * (erfcx/2)
+        # the scale: every Horner partial sum below 1.5 x 2^-s on [-1, 1]
+        bound = mp.mpf(0)
+        for k in range(401):
+            t = mp.mpf(-1) + mp.mpf(2) * k / 400
+            p = mp.mpf(0)
+            for m in reversed(half):
+                p = p * t + m
+                bound = max(bound, abs(p))
+        sft = int(mp.floor(mp.log(mp.mpf(1.5) / bound, 2)))
+        assert 0 <= sft <= 8, sft
+        fx = [int(mp.nint(m * mp.mpf(2) ** (62 + sft))) for m in half]
+        assert all(abs(v) < 2 ** 63 for v in fx)
         for k in range(200):
             x = mp.mpf(a) + (mp.mpf(b) - a) * k / 199
             t = (x - c) / h
             p = mp.mpf(0)
             for m in reversed(mono):
                 p = p * t + m
+            # the interpolant in exact arithmetic
             assert abs(p / erfcx(x) - 1) < 6e-17, (a, b, x)
-        coef_rows.append([hexd(m / 2) for m in mono])  # E = exp(-S^2) * (erfcx/2)
-        sc.append(hexd(1 / h))
-        off.append(hexd(-c / h))
+            # the kernels' integer steps, exactly (t in 2^-63 units, floor of
+            # the high word of each 128-bit product, shifted left by one)
+            tq = int(mp.floor(t * 2 ** 63))
+            q = fx[DEGREE]
+            for j in range(DEGREE - 1, -1, -1):
+                q = ((q * tq) >> 64) * 2 + fx[j]
+                assert abs(q) < 2 ** 63
+            assert abs(mp.mpf(q) / mp.mpf(2) ** (62 + sft) / (p / 2) - 1) < 2e-17, (a, b, x)
+        coef_rows.append([str(v) + "ll" if v >= -(2 ** 63) + 1 else None for v in fx])
+        shifts.append(str(sft))
     # global (not constant) memory: blocks copy the tables with coalesced loads
-    lines.append(f"__device__ double kErfcxScale[{nI}] = {{" + ", ".join(sc) + "};")
-    lines.append(f"__device__ double kErfcxOffset[{nI}] = {{" + ", ".join(off) + "};")
     lines.append(f"// erfcx/2 on each interval as a polynomial in t, coefficients of t^0 .. t^{DEGREE}")
-    lines.append(f"__device__ double kErfcxHalf[{nI}][{DEGREE + 1}] = {{")
+    lines.append(f"// in units of 2^-(62 + kErfcxFxShift[interval])")
+    lines.append(f"__device__ int kErfcxFxShift[{nI}] = {{" + ", ".join(shifts) + "};")
+    lines.append(f"__device__ long long kErfcxFx[{nI}][{DEGREE + 1}] = {{")
     for row in coef_rows:
         lines.append("    {" + ", ".join(row) + "},")
     lines.append("};")

@@ -1,23 +1,25 @@
 // FP64 elementary functions of the split fluxes, shaped for GB300's scarce
 // FP64 issue rate (1/64 of FP32): everything that can run on the integer
 // pipes (range-reduction index, exponent scaling, interval selection, sign
-// tests, the multiplications: mul_i) does, and exp(-S^2) is shared between
-// the two places a split flux needs it.  Constants: lskum_mathconst.h (gen_mathconst.py documents the
-// methods and their accuracy).  The tables are read per thread at diverging
+// tests, the multiplications: mul_i, the erfcx polynomial in fixed point:
+// lskum_fixmath.cuh) does, and exp(-S^2) is shared between the two places a
+// split flux needs it.  Constants: lskum_mathconst.h (gen_mathconst.py
+// documents the methods and their accuracy).  The tables are read per thread at diverging
 // indices, which would serialise constant-cache reads, so they live in
 // memory: the kernels that evaluate them at every point (the residual and
 // the update) stage a copy in shared memory; the sweeps, which
 // need them only at wall and outer points, read one global copy (g_math).
 #pragma once
+#include "lskum_fixmath.cuh"
 #include "lskum_intmul.cuh"
 #include "lskum_mathconst.h"
 
 namespace lskum {
 
 struct MathTables {
-    double exp2j[kExpN];                        // 2^(j/N)
-    double ecx[kErfcxIntervals][kErfcxDeg + 1]; // erfcx/2 per interval, Horner coefficients
-    double sc[kErfcxIntervals], off[kErfcxIntervals];  // t = x * sc + off
+    double exp2j[kExpN];                           // 2^(j/N)
+    long long ecx[kErfcxIntervals][kErfcxDeg + 1]; // erfcx/2 per interval, fixed-point Horner coefficients
+    int esh[kErfcxIntervals];                      // their scales: units of 2^-(62 + esh)
 };
 
 // Copy the tables into shared memory (all threads of the block; then sync).
@@ -25,11 +27,8 @@ __device__ __forceinline__ void load_math_tables(MathTables &T)
 {
     for (int i = threadIdx.x; i < kExpN; i += blockDim.x) T.exp2j[i] = kExpTable[i];
     for (int i = threadIdx.x; i < kErfcxIntervals * (kErfcxDeg + 1); i += blockDim.x)
-        T.ecx[i / (kErfcxDeg + 1)][i % (kErfcxDeg + 1)] = kErfcxHalf[i / (kErfcxDeg + 1)][i % (kErfcxDeg + 1)];
-    if (threadIdx.x < kErfcxIntervals) {
-        T.sc[threadIdx.x] = kErfcxScale[threadIdx.x];
-        T.off[threadIdx.x] = kErfcxOffset[threadIdx.x];
-    }
+        T.ecx[i / (kErfcxDeg + 1)][i % (kErfcxDeg + 1)] = kErfcxFx[i / (kErfcxDeg + 1)][i % (kErfcxDeg + 1)];
+    for (int i = threadIdx.x; i < kErfcxIntervals; i += blockDim.x) T.esh[i] = kErfcxFxShift[i];
 }
 
 // exp(x) for |x| <= 700 (Tang's table-driven method, N = 4096 table entries,
@@ -63,13 +62,10 @@ __device__ __forceinline__ void split_E(const MathTables &T, double S, double &E
     constexpr int kNineHi = 0x40220000;  // high word of 9.0 (low word 0)
     const int hs = __double2hiint(S) & 0x7fffffff;
     const bool clamp = hs >= kNineHi;
-    const double a = clamp ? 9.0 : __hiloint2double(hs, __double2loint(S));
-    const int iv = erfcx_interval(clamp ? kNineHi : hs);
-    const double t = fma(a, T.sc[iv], T.off[iv]);
-    const double *c = T.ecx[iv];
-    double p = c[kErfcxDeg];
-#pragma unroll
-    for (int j = kErfcxDeg - 1; j >= 0; j--) p = fma(p, t, c[j]);
+    const int ha = clamp ? kNineHi : hs, la = clamp ? 0 : __double2loint(S);
+    const double a = __hiloint2double(ha, la);
+    const int iv = erfcx_interval(ha);
+    const double p = erfcx_half_fx<kErfcxDeg>((uint32_t)ha, (uint32_t)la, iv, (const int64_t *)T.ecx[iv], T.esh[iv]);
     eS = exp_t(T, -mul_i(a, a));
     E = mul_i(eS, p);
 }

@@ -143,13 +143,16 @@ __device__ __forceinline__ Prim q_to_prim(const MathTables &T, const double q[4]
 }
 
 // Kinetic split flux G_d^sg (half-range moments of the Maxwellian; sg = +1
-// if pos, else -1, applied by negation) in unit direction d: DIR 0 is (1,0),
-// DIR 1 is (0,1), DIR 2 is (dx, dy).
-template <int DIR>
-__device__ __forceinline__ void split_flux(const MathTables &T, const Prim &P, double dx, double dy, bool pos,
-                                          double G[4])
+// if pos, else -1, applied by negation) in unit direction d: (dx, dy) in a
+// (t, n) frame (framed), else the x axis (xdir) or the y axis, where the
+// axis components are selected on the integer pipe instead of multiplied by
+// 0 and 1.  One body for every frame and axis keeps the residual's loop
+// small enough for the instruction cache.
+__device__ __forceinline__ void split_flux(const MathTables &T, const Prim &P, bool framed, bool xdir, double dx,
+                                          double dy, bool pos, double G[4])
 {
-    const double ud = DIR == 0 ? P.u : (DIR == 1 ? P.v : fma(P.u, dx, mul_i(P.v, dy)));
+    const double ua = xdir ? P.u : P.v, uo = xdir ? P.v : P.u;  // along and across the axis
+    const double ud = framed ? fma(P.u, dx, mul_i(P.v, dy)) : ua;
     const double S = mul_i(ud, P.sb);
     double A, eS;
     split_A(T, S, pos, A, eS);
@@ -159,15 +162,13 @@ __device__ __forceinline__ void split_flux(const MathTables &T, const Prim &P, d
     const double rm = mul_i(P.rho, M1);
     const double pA = mul_i(P.p, A);
     G[0] = rm;
-    if (DIR == 0) {
-        G[1] = fma(rm, P.u, pA);
-        G[2] = mul_i(rm, P.v);
-    } else if (DIR == 1) {
-        G[1] = mul_i(rm, P.u);
-        G[2] = fma(rm, P.v, pA);
-    } else {
+    if (framed) {
         G[1] = fma(rm, P.u, mul_i(pA, dx));
         G[2] = fma(rm, P.v, mul_i(pA, dy));
+    } else {
+        const double ga = fma(rm, ua, pA), go = mul_i(rm, uo);
+        G[1] = xdir ? ga : go;
+        G[2] = xdir ? go : ga;
     }
     G[3] = fma(mul_i(ud, P.e1), A, mul_i(P.e2, sB));
 }
@@ -463,16 +464,14 @@ __global__ void __launch_bounds__(256) k_grad(Dev d, const double *__restrict__ 
 // ---------------------------------------------------------------------------
 // flux residual, time step, diagonal, norm partials
 // ---------------------------------------------------------------------------
-// R += w1 dG1 + w2 dG2 (a slot's two split sub-stencils; a weight and its
-// difference are 0 where the slot is in one only) with Kahan's compensated
-// summation (W. Kahan, "Further remarks on reducing truncation errors", CACM
-// 8(1), 1965): c carries the negated rounding error of the running sum into
-// the next term; the products are folded into that correction by two FMAs,
-// so one compensated addition serves both sub-stencils.  The final sum is
-// R - c.
-__device__ __forceinline__ void comp_add2(double &R, double &c, double w1, double dG1, double w2, double dG2)
+// R += y with Kahan's compensated summation (W. Kahan, "Further remarks on
+// reducing truncation errors", CACM 8(1), 1965): c carries the negated
+// rounding error of the running sum into the next term.  The caller forms y
+// as the slot's term less c, the weighted flux differences of its two split
+// sub-stencils folded in by FMAs, so one compensated addition serves both.
+// The final sum is R - c.
+__device__ __forceinline__ void comp_add(double &R, double &c, double y)
 {
-    const double y = fma(w1, dG1, fma(w2, dG2, -c));  // the slot's term less the carried error
     const double t = R + y;
     c = (t - R) - y;  // what the addition lost (negated)
     R = t;
@@ -541,47 +540,29 @@ __global__ void __launch_bounds__(128, LSKUM_RES_MIN_BLOCKS) k_residual(Dev d, S
             }
             const Prim Pi = q_to_prim(T, qi);
             const Prim P0 = q_to_prim(T, q0t);
-            double w1 = 0.0, dG1[4] = {0.0, 0.0, 0.0, 0.0};  // (COMP) the first sub-stencil's term
-            if (mb & 3) {
-                const bool pos = mb & 1;
-                const double w = d.w1[e];
+            // the slot's sub-stencils (x then y, or t then n): one loop body
+            double y[4];  // (COMP) the slot's term less the carried error
+#pragma unroll
+            for (int c = 0; c < 4; c++) y[c] = -Rc[c];
+#pragma unroll 1
+            for (int sb = 0; sb < 2; sb++) {
+                const int m = sb == 0 ? (mb & 3) : (mb >> 2);
+                if (!m) continue;
+                const bool pos = m & 1, xdir = sb == 0;
+                const double w = xdir ? d.w1[e] : d.w2[e];
+                const double dx = xdir ? e1x : e2x, dy = xdir ? e1y : e2y;
                 double Gi[4], G0[4];
-                if (framed) {
-                    split_flux<2>(T, Pi, e1x, e1y, pos, Gi);
-                    split_flux<2>(T, P0, e1x, e1y, pos, G0);
-                } else {
-                    split_flux<0>(T, Pi, 1.0, 0.0, pos, Gi);
-                    split_flux<0>(T, P0, 1.0, 0.0, pos, G0);
-                }
+                split_flux(T, Pi, framed, xdir, dx, dy, pos, Gi);
+                split_flux(T, P0, framed, xdir, dx, dy, pos, G0);
 #pragma unroll
                 for (int c = 0; c < 4; c++) {
-                    if (COMP) dG1[c] = Gi[c] - G0[c];
+                    if (COMP) y[c] = fma(w, Gi[c] - G0[c], y[c]);
                     else R[c] = fma(w, Gi[c] - G0[c], R[c]);
                 }
-                w1 = w;
-            }
-            double w2 = 0.0, dG2[4] = {0.0, 0.0, 0.0, 0.0};
-            if (mb & 12) {
-                const bool pos = mb & 4;
-                const double w = d.w2[e];
-                double Gi[4], G0[4];
-                if (framed) {
-                    split_flux<2>(T, Pi, e2x, e2y, pos, Gi);
-                    split_flux<2>(T, P0, e2x, e2y, pos, G0);
-                } else {
-                    split_flux<1>(T, Pi, 0.0, 1.0, pos, Gi);
-                    split_flux<1>(T, P0, 0.0, 1.0, pos, G0);
-                }
-#pragma unroll
-                for (int c = 0; c < 4; c++) {
-                    if (COMP) dG2[c] = Gi[c] - G0[c];
-                    else R[c] = fma(w, Gi[c] - G0[c], R[c]);
-                }
-                w2 = w;
             }
             if (COMP) {
 #pragma unroll
-                for (int c = 0; c < 4; c++) comp_add2(R[c], Rc[c], w1, dG1[c], w2, dG2[c]);
+                for (int c = 0; c < 4; c++) comp_add(R[c], Rc[c], y[c]);
             }
         }
     }

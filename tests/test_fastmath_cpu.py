@@ -1,6 +1,7 @@
 """The kernels' own FP64 exp and A = (1 + s erf S)/2, emulated on the CPU
-operation by operation (fused multiply-adds rounded once) with the constants
-of the generated header, against mpmath at 60 digits."""
+operation by operation (fused multiply-adds rounded once, the erfcx
+polynomial's fixed-point integer steps exactly) with the constants of the
+generated header, against mpmath at 60 digits."""
 import os
 import re
 import struct
@@ -26,14 +27,17 @@ def _consts():
 
     deg = int(re.search(r"kErfcxDeg = (\d+);", s).group(1))
     nI = int(re.search(r"kErfcxIntervals = (\d+);", s).group(1))
-    ecx = np.array(array("kErfcxHalf")).reshape(nI, deg + 1)
+    body = re.search(r"kErfcxFx\[[^=]*\] = \{(.*?)\n\};", s, re.S).group(1)
+    ecx = [[int(v) for v in re.findall(r"-?\d+(?=ll)", row)] for row in body.strip().split("\n")]
+    assert len(ecx) == nI and all(len(r) == deg + 1 for r in ecx)
+    esh = [int(v) for v in re.search(r"kErfcxFxShift\[[^=]*\] = \{(.*?)\};", s).group(1).split(",")]
     eshift = int(re.search(r"kErfcxShift = (\d+);", s).group(1))
     key0 = int(re.search(r"kErfcxKey0 = (0x[0-9a-f]+);", s).group(1), 16)
     n = int(re.search(r"kExpN = (\d+);", s).group(1))
     edeg = int(re.search(r"kExpDeg = (\d+);", s).group(1))
     shift = int(re.search(r"kExpShift = (\d+);", s).group(1))
     return dict(inv=scalar("kExpInvLn2N"), hi=scalar("kExpLn2NHi"), lo=scalar("kExpLn2NLo"), n=n, shift=shift,
-                tab=array("kExpTable"), sc=array("kErfcxScale"), off=array("kErfcxOffset"), ecx=ecx, deg=deg,
+                tab=array("kExpTable"), ecx=ecx, esh=esh, deg=deg,
                 eshift=eshift, key0=key0, deg_exp=edeg)
 
 
@@ -76,16 +80,38 @@ def exp_t(x):
     return from_words(hi_word(res) + ((k >> C["shift"]) << 20), lo_word(res))
 
 
+def fx_to_double(v, f):
+    """v 2^-f (0 < v < 2^63) rounded to nearest even, as the kernels do it."""
+    assert 0 < v < 2 ** 63
+    lz = 64 - v.bit_length()
+    w = v << (lz - 1)
+    M = (w + 0x1FF + ((w >> 10) & 1)) >> 10
+    return float(M) * 2.0 ** (10 - (lz - 1) - f)
+
+
+def erfcx_half_fx(a):
+    """erfcx(a)/2 by the kernels' integer steps (a >= 0 after the clamp)."""
+    bits = struct.unpack(">Q", struct.pack(">d", a))[0]
+    ha, la = bits >> 32, bits & 0xFFFFFFFF
+    iv = max(0, (ha >> C["eshift"]) - C["key0"] + 1)
+    assert 0 <= iv < len(C["ecx"])
+    ex = ha >> 20
+    M = (((ha & 0xFFFFF) | (0x100000 if ex else 0)) << 32) | la
+    sh = 16 if iv > 0 else ex - 1006
+    v = (M << sh) % 2 ** 64 if sh >= 0 else (M >> -sh if sh > -64 else 0)
+    t = v ^ (1 << 63)
+    t = t - 2 ** 64 if t >= 2 ** 63 else t  # t 2^63, signed
+    c = C["ecx"][iv]
+    p = c[C["deg"]]
+    for j in range(C["deg"] - 1, -1, -1):
+        p = ((p * t) >> 64) * 2 + c[j]  # floor of the high word, as the signed 128-bit product gives it
+        assert -(2 ** 63) <= p < 2 ** 63
+    return fx_to_double(p, 62 + C["esh"][iv])
+
+
 def split_E(S):
     a = min(abs(S), 9.0)
-    ha = hi_word(a)
-    iv = max(0, (ha >> C["eshift"]) - C["key0"] + 1)
-    assert 0 <= iv < len(C["sc"])
-    t = fma(a, C["sc"][iv], C["off"][iv])
-    c = C["ecx"][iv]
-    p = float(c[C["deg"]])
-    for j in range(C["deg"] - 1, -1, -1):
-        p = fma(p, t, float(c[j]))
+    p = erfcx_half_fx(a)
     eS = exp_t(-mul(a, a))
     return mul(eS, p), eS
 
