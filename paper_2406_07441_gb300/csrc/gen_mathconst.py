@@ -4,12 +4,15 @@ Run from the repository root:  python paper_2406_07441_gb300/csrc/gen_mathconst.
 (needs mpmath; the generated header is committed, so building does not).
 
 exp (table-driven, after P. T. P. Tang, "Table-driven implementation of the
-exponential function in IEEE floating-point arithmetic", ACM TOMS 15(2), 1989):
-  x = (N m + j) ln2/N + r, |r| <= ln2/(2N), N = 4096,
-  exp(x) = 2^m * 2^(j/N) * e^r, 2^(j/N) tabulated (correctly rounded),
-  e^r - 1 by its Taylor polynomial of degree 3 (truncation < 2.2e-18 relative
-  on |r| <= ln2/8192; each doubling of the table halves |r|, and N = 4096
-  instead of 512 buys one FP64 instruction per exp, six per residual slot).
+exponential function in IEEE floating-point arithmetic", ACM TOMS 15(2), 1989),
+evaluated in 64-bit fixed point on the integer pipes (lskum_fixmath.cuh):
+  x N/ln2 = k + f exactly to 2^-64 (the 53-bit significand times N/ln2 in
+  units of 2^-50, a 116-bit integer product), k = N m + j, 0 <= f < 1,
+  exp(x) = 2^m * 2^(j/N) * e^r with r = f ln2/N in [0, ln2/N), N = 4096,
+  2^(j/N) tabulated in units of 2^-63 (rounded to nearest), e^r - 1 by its
+  Taylor polynomial of degree 4 (truncation < 1.3e-21 on [0, ln2/N)).  The
+  constant N/ln2 carries 63 bits, so the reduction is within |x| 2^-63 of
+  exact: below 1e-17 relative for the |x| <= 81 the split fluxes need.
 
 erfcx(x) = exp(x^2) erfc(x) for 0 <= x <= 9: the intervals are [0, 2^-5)
 and, above it, sixteen per binade, [2^e (1 + m/16), 2^e (1 + (m+1)/16)) for
@@ -65,7 +68,7 @@ def _intervals():
 INTERVALS = _intervals()
 DEGREE = 8
 EXP_N = 4096
-EXP_DEG = 3
+EXP_DEG = 4
 
 
 def erfcx(x):
@@ -110,28 +113,26 @@ def main():
         "",
         f"constexpr int kExpN = {EXP_N};  // table size N (a power of two)",
         f"constexpr int kExpShift = {EXP_N.bit_length() - 1};  // log2 N",
-        f"constexpr double kExpInvLn2N = {hexd(EXP_N / mp.log(2))};  // N / ln 2",
-        f"constexpr int kExpDeg = {EXP_DEG};  // degree of the polynomial for e^r - 1",
     ]
-    ln2_n = mp.log(2) / EXP_N
-    # high part: ln2/N with the low 24 significand bits cleared, so that k * hi
-    # is exact for the |k| < 2^23 that finite results need (29 + 23 < 53 bits)
-    bits = int.from_bytes(struct.pack(">d", float(ln2_n)), "big") & ~((1 << 24) - 1)
-    fhi = struct.unpack(">d", bits.to_bytes(8, "big"))[0]
-    flo = float(ln2_n - mp.mpf(fhi))
+    # N/ln2 in units of 2^-50 (63 bits) and ln2/N in units of 2^-76 (64 bits)
+    cfx = int(mp.nint(EXP_N / mp.log(2) * mp.mpf(2) ** 50))
+    lfx = int(mp.nint(mp.log(2) / EXP_N * mp.mpf(2) ** 76))
+    assert 2 ** 62 <= cfx < 2 ** 63 and 2 ** 63 <= lfx < 2 ** 64
     lines += [
-        f"constexpr double kExpLn2NHi = {fhi.hex()};  // ln2/N, 29 significant bits",
-        f"constexpr double kExpLn2NLo = {flo.hex()};  // ln2/N - kExpLn2NHi",
-        f"// 2^(j/N), j = 0..N-1, correctly rounded",
-        f"__device__ double kExpTable[{EXP_N}] = {{",
+        f"constexpr int kExpDeg = {EXP_DEG};  // degree of the polynomial for e^r - 1",
+        f"constexpr unsigned long long kExpFxC = {cfx}ull;  // N/ln2 in units of 2^-50",
+        f"constexpr unsigned long long kExpFxL = {lfx}ull;  // ln2/N in units of 2^-76",
+        f"// 2^(j/N), j = 0..N-1, in units of 2^-63 (rounded to nearest)",
+        f"__device__ unsigned long long kExpTableFx[{EXP_N}] = {{",
     ]
     for j in range(0, EXP_N, 4):
-        lines.append("    " + ", ".join(hexd(mp.power(2, mp.mpf(k) / EXP_N)) for k in range(j, j + 4)) + ",")
+        lines.append("    " + ", ".join(str(int(mp.nint(mp.power(2, mp.mpf(k) / EXP_N) * mp.mpf(2) ** 63))) + "ull"
+                                        for k in range(j, j + 4)) + ",")
     lines.append("};")
-    # the polynomial's truncation on |r| <= ln2/(2N)
-    rmax = mp.log(2) / (2 * EXP_N)
-    trunc = abs(mp.exp(rmax) - (1 + rmax + rmax ** 2 / 2 + rmax ** 3 / 6)) / mp.exp(rmax)
-    assert EXP_DEG == 3 and trunc < 2.2e-18, trunc
+    # the polynomial's truncation on 0 <= r < ln2/N
+    rmax = mp.log(2) / EXP_N
+    trunc = abs(mp.exp(rmax) - (1 + rmax + rmax ** 2 / 2 + rmax ** 3 / 6 + rmax ** 4 / 24)) / mp.exp(rmax)
+    assert EXP_DEG == 4 and trunc < 1.3e-21, trunc
     nI = len(INTERVALS)
     key0 = (int.from_bytes(struct.pack(">d", 2.0 ** LOW_EXP), "big") >> 32) >> (20 - MBITS)
     # the index function reproduces the table's intervals

@@ -17,7 +17,7 @@
 namespace lskum {
 
 struct MathTables {
-    double exp2j[kExpN];                           // 2^(j/N)
+    unsigned long long exp2j[kExpN];               // 2^(j/N) in units of 2^-63
     long long ecx[kErfcxIntervals][kErfcxDeg + 1]; // erfcx/2 per interval, fixed-point Horner coefficients
     int esh[kErfcxIntervals];                      // their scales: units of 2^-(62 + esh)
 };
@@ -25,28 +25,17 @@ struct MathTables {
 // Copy the tables into shared memory (all threads of the block; then sync).
 __device__ __forceinline__ void load_math_tables(MathTables &T)
 {
-    for (int i = threadIdx.x; i < kExpN; i += blockDim.x) T.exp2j[i] = kExpTable[i];
+    for (int i = threadIdx.x; i < kExpN; i += blockDim.x) T.exp2j[i] = kExpTableFx[i];
     for (int i = threadIdx.x; i < kErfcxIntervals * (kErfcxDeg + 1); i += blockDim.x)
         T.ecx[i / (kErfcxDeg + 1)][i % (kErfcxDeg + 1)] = kErfcxFx[i / (kErfcxDeg + 1)][i % (kErfcxDeg + 1)];
     for (int i = threadIdx.x; i < kErfcxIntervals; i += blockDim.x) T.esh[i] = kErfcxFxShift[i];
 }
 
-// exp(x) for |x| <= 700 (Tang's table-driven method, N = 4096 table entries,
-// e^r - 1 of degree 3): 8 FP64 instructions.
+// exp(x) in fixed point on the integer pipes (lskum_fixmath.cuh): within
+// 0.51 ulp for |x| <= 100, 1 ulp up to 708, the library's exp beyond.
 __device__ __forceinline__ double exp_t(const MathTables &T, double x)
 {
-    const double big = 0x1.8p52;                            // rounds x*N/ln2 into the low word
-    const double t = fma(x, kExpInvLn2N, big);
-    const int k = __double2loint(t);                        // round(x * N / ln2)
-    const double kd = t - big;
-    double r = fma(kd, -kExpLn2NHi, x);
-    r = fma(kd, -kExpLn2NLo, r);                            // |r| <= ln2/(2N)
-    static_assert(kExpDeg == 3, "exp_t evaluates a cubic");
-    const double h = fma(r, 1.0 / 6.0, 0.5);
-    const double p = fma(mul_i(r, r), h, r);                // e^r - 1
-    const double e = T.exp2j[k & (kExpN - 1)];
-    const double res = fma(e, p, e);                        // 2^(j/N) e^r
-    return __hiloint2double(__double2hiint(res) + ((k >> kExpShift) << 20), __double2loint(res));
+    return exp_fx<kExpShift>((const uint64_t *)T.exp2j, kExpFxC, kExpFxL, x);
 }
 
 // E = exp(-S^2) erfcx(|S|)/2 and eS = exp(-S^2); then (1 + erf S)/2 is 1 - E

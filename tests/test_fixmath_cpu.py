@@ -1,9 +1,9 @@
-"""erfcx on the integer pipes (csrc/lskum_fixmath.cuh): the header compiled for
-the host with the generated coefficient tables gives bit for bit what an
-exact emulation of its integer steps gives, and both are within the
-interpolant's own error (6e-17) plus one rounding of erfcx(x)/2 by mpmath,
-over the whole clamped range [0, 9], interval edges and tiny arguments
-included."""
+"""exp and erfcx on the integer pipes (csrc/lskum_fixmath.cuh): the header
+compiled for the host with the generated tables gives bit for bit what exact
+emulations of its integer steps give; erfcx is within the interpolant's own
+error (6e-17) plus one rounding of erfcx(x)/2 by mpmath over the whole
+clamped range [0, 9], interval edges and tiny arguments included (exp's
+accuracy: test_fastmath_cpu)."""
 import ctypes
 import os
 import shutil
@@ -27,6 +27,12 @@ using std::max;
 #define __forceinline__ inline
 #include "lskum_mathconst.h"
 #include "lskum_fixmath.cuh"
+extern "C" void exp_many(const double *x, double *r, long n)
+{
+    for (long k = 0; k < n; k++)
+        r[k] = lskum::exp_fx<lskum::kExpShift>((const uint64_t *)lskum::kExpTableFx, lskum::kExpFxC, lskum::kExpFxL,
+                                              x[k]);
+}
 extern "C" void erfcx_half_many(const double *x, double *r, long n)
 {
     for (long k = 0; k < n; k++) {
@@ -42,7 +48,7 @@ extern "C" void erfcx_half_many(const double *x, double *r, long n)
 
 
 @pytest.fixture(scope="module")
-def host_erfcx():
+def host_fns():
     gxx = shutil.which("g++")
     if gxx is None:
         pytest.skip("no host C++ compiler")
@@ -54,13 +60,16 @@ def host_erfcx():
     lib = ctypes.CDLL(so)
     dp = ctypes.POINTER(ctypes.c_double)
     lib.erfcx_half_many.argtypes = [dp, dp, ctypes.c_long]
+    lib.exp_many.argtypes = [dp, dp, ctypes.c_long]
 
-    def f(x):
-        x = np.ascontiguousarray(x, dtype=np.float64)
-        r = np.empty_like(x)
-        lib.erfcx_half_many(x.ctypes.data_as(dp), r.ctypes.data_as(dp), x.size)
-        return r
-    yield f
+    def call(fn):
+        def f(x):
+            x = np.ascontiguousarray(x, dtype=np.float64)
+            r = np.empty_like(x)
+            fn(x.ctypes.data_as(dp), r.ctypes.data_as(dp), x.size)
+            return r
+        return f
+    yield call(lib.erfcx_half_many), call(lib.exp_many)
     shutil.rmtree(d, ignore_errors=True)
 
 
@@ -76,18 +85,24 @@ def _args():
                            [x for x in edges if x <= 9.0], tiny, [9.0]])
 
 
-def test_host_build_equals_the_exact_emulation(host_erfcx):
-    from test_fastmath_cpu import erfcx_half_fx
+def test_host_build_equals_the_exact_emulation(host_fns):
+    from test_fastmath_cpu import erfcx_half_fx, exp_t
     x = _args()
-    got = host_erfcx(x)
+    got = host_fns[0](x)
     ref = np.array([erfcx_half_fx(float(v)) for v in x])
+    assert np.array_equal(got.view(np.uint64), ref.view(np.uint64))
+    rng = np.random.default_rng(22)
+    y = np.concatenate([rng.uniform(-707.9, 707.9, 4000), -rng.uniform(0, 81, 4000), rng.normal(0, 1e-6, 500),
+                        [0.0, -0.0, 5e-324, -5e-324, 1e-300, 707.99, -707.99, 1.0, -1.0]])
+    got = host_fns[1](y)
+    ref = np.array([exp_t(float(v)) for v in y])
     assert np.array_equal(got.view(np.uint64), ref.view(np.uint64))
 
 
-def test_within_the_interpolant_error_and_one_rounding(host_erfcx):
+def test_within_the_interpolant_error_and_one_rounding(host_fns):
     mp.mp.dps = 40
     x = _args()
-    got = host_erfcx(x)
+    got = host_fns[0](x)
     worst = 0.0
     for v, g in zip(x, got):
         ref = mp.exp(mp.mpf(float(v)) ** 2) * mp.erfc(mp.mpf(float(v))) / 2
