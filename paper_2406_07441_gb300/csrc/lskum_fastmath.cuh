@@ -1,14 +1,14 @@
 // FP64 elementary functions of the split fluxes, shaped for GB300's scarce
 // FP64 issue rate (1/64 of FP32): everything that can run on the integer
 // pipes (range-reduction index, exponent scaling, interval selection, sign
-// tests, the multiplications: mul_i, the erfcx polynomial in fixed point:
-// lskum_fixmath.cuh) does, and exp(-S^2) is shared between the two places a
-// split flux needs it.  Constants: lskum_mathconst.h (gen_mathconst.py
-// documents the methods and their accuracy).  The tables are read per thread at diverging
+// tests, exp and the erfcx polynomial in fixed point: lskum_fixmath.cuh)
+// does, and exp(-S^2) is shared between the two places a split flux needs
+// it.  Constants: lskum_mathconst.h (gen_mathconst.py documents the methods
+// and their accuracy).  The tables are read per thread at diverging
 // indices, which would serialise constant-cache reads, so they live in
 // memory: the kernels that evaluate them at every point (the residual and
-// the update) stage a copy in shared memory; the sweeps, which
-// need them only at wall and outer points, read one global copy (g_math).
+// the update) stage a copy in shared memory; the sweeps, which need them
+// only at wall and outer points, read one global copy (g_math).
 #pragma once
 #include "lskum_fixmath.cuh"
 #include "lskum_intmul.cuh"
@@ -55,8 +55,10 @@ __device__ __forceinline__ void split_E(const MathTables &T, double S, double &E
     const double a = __hiloint2double(ha, la);
     const int iv = erfcx_interval(ha);
     const double p = erfcx_half_fx<kErfcxDeg>((uint32_t)ha, (uint32_t)la, iv, (const int64_t *)T.ecx[iv], T.esh[iv]);
-    eS = exp_t(T, -mul_i(a, a));
-    E = mul_i(eS, p);
+    // the two multiplications stay on the FP64 unit (short latency on the
+    // path to A; measured faster than the integer multiply here)
+    eS = exp_t(T, -(a * a));
+    E = eS * p;
 }
 
 // A = (1 + sg erf S)/2 (sg = +1 if pos, else -1) and eS = exp(-S^2).
