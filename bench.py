@@ -67,25 +67,42 @@ L2_BYTES = 129 * 2**20
 # FP64 peak derived from unit counts and clock: 152 SMs x 2 DFMA/clk/SM x 2 flop
 # x 2070 MHz = 1.259 TFLOP/s (a DFMA-chain probe measured 1.196 at ~2.0 GHz).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
-# FP64 flops (DFMA = 2) the residual kernel executes per neighbour slot that
-# joins a split sub-stencil, counted by ncu (2 x dfma + dmul + dadd thread
-# instructions of one launch / such slots; see profiles/): the 147,584-point
-# cloud's Euclidean stencils (2,926,611 slots at 2 threads per point), and
-# the cone-completed stencils of the 1,310,720-point cloud (26,159,870 slots
-# at 1 thread per point: 2 x 3,240,043,812 + 1,797,370,444 + 477,404,332),
-# which stand for the 5,242,880-point cloud of the same construction (the
-# count depends on the mix of slots joining one or two sub-stencils)
+# The residual's algorithmic arithmetic per neighbour slot that joins a split
+# sub-stencil, in FP64 flops (DFMA = 2): what the method's formulas cost when
+# every operation runs on the FP64 unit, counted by ncu (2 x dfma + dmul +
+# dadd thread instructions of one launch / such slots) on the all-FP64 form
+# of this kernel (the same exp, erfcx and reconstruction formulas): the
+# 147,584-point cloud's Euclidean stencils (2,926,611 slots at 2 threads per
+# point), and the cone-completed stencils of the 1,310,720-point cloud
+# (26,159,870 slots at 1 thread per point: 2 x 3,240,043,812 + 1,797,370,444
+# + 477,404,332), which stand for the 5,242,880-point cloud of the same
+# construction (the count depends on the mix of slots joining one or two
+# sub-stencils)
 RES_FLOPS_PER_SLOT = {MID_WORKLOAD: 336.07, SUPER_WORKLOAD: 336.07, PROF_WORKLOAD: 334.668, WORKLOAD: 334.668}
+# The current kernel runs exp and erfcx in fixed point and the split fluxes'
+# multiplications as correctly rounded integer multiplies on the integer
+# pipes, beside the FP64 unit; the FP64 flops it still executes on the FP64
+# unit per slot (ncu, the same counting; profiles/)
+RES_FP64_UNIT_FLOPS_PER_SLOT = {MID_WORKLOAD: 155.07, SUPER_WORKLOAD: 155.07, PROF_WORKLOAD: 154.67,
+                                WORKLOAD: 154.67}
 START = 50  # first-order start-up iterations before warm-up and timing
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one residual
 # launch, from one ncu capture of the current kernel (profiles/), per
 # workload and threads per point; reported only for that launch shape and FP64
-RES_TRAFFIC = {MID_WORKLOAD: {2: 164.582144e6}, PROF_WORKLOAD: {1: 3.388122624e9},
-               WORKLOAD: {1: 13.973204224e9}}  # the last from a one-pass capture of the full-size launch
-# sm__pipe_fp64_cycles_active of that launch (fraction of peak sustained): the
-# residual's binding unit; the counted-flop fraction is lower because
-# additions, multiplications and comparisons occupy the pipe like an FMA
-RES_FP64_PIPE_ACTIVE = {MID_WORKLOAD: 0.8891, PROF_WORKLOAD: 0.9008, WORKLOAD: 0.9008}
+RES_TRAFFIC = {MID_WORKLOAD: {2: 164.318208e6}, PROF_WORKLOAD: {1: 3.3923008e9},
+               WORKLOAD: {1: 14.592e9}}  # the last from a one-pass capture of the full-size launch
+# Unit utilisation of that launch (fraction of peak sustained, ncu): the FP64
+# pipe is the binding unit; the integer pipes (ALU, FMA-heavy: IMAD) carry
+# the fixed-point functions and the integer multiplies
+RES_UNITS_NCU = {MID_WORKLOAD: {"fp64_pipe": 0.7927, "alu_pipe": 0.3778, "fmaheavy_pipe": 0.3309, "issue": 0.3952},
+                 PROF_WORKLOAD: {"fp64_pipe": 0.8122, "alu_pipe": 0.3936, "fmaheavy_pipe": 0.3420,
+                                 "issue": 0.4065}}
+RES_UNITS_NCU[SUPER_WORKLOAD] = RES_UNITS_NCU[MID_WORKLOAD]
+RES_UNITS_NCU[WORKLOAD] = RES_UNITS_NCU[PROF_WORKLOAD]
+ROOFLINE_NOTE = ("achieved counts the method's FP64 arithmetic as the all-FP64 form executes it "
+                 "(flops_per_active_slot); frac can exceed 1 because exp and erfcx run in 64-bit fixed point "
+                 "and the split fluxes' multiplications as correctly rounded integer multiplies on the integer "
+                 "pipes, beside the FP64 unit; fp64_unit gives the FP64 unit's own share and utilisation")
 
 
 def _sweep_form(lanes):
@@ -307,6 +324,8 @@ def run_ours(args, rank, world, local_rank):
     res_ms = phases["residual"]
     flops_slot = RES_FLOPS_PER_SLOT.get(wl)
     achieved = flops_slot * nslots / (res_ms / 1e3) / 1e12 if flops_slot else None
+    unit_slot = RES_FP64_UNIT_FLOPS_PER_SLOT.get(wl)
+    unit_tf = unit_slot * nslots / (res_ms / 1e3) / 1e12 if unit_slot else None
 
     # end to end through the C-ABI with host buffers: state in (H2D), one
     # iteration, state out (D2H) every step
@@ -384,8 +403,11 @@ def run_ours(args, rank, world, local_rank):
                      "algorithmic_bytes_rule": "37 B per neighbour slot (index, membership, dx, dy, 2 weights) "
                                                "+ 360 B per point (q, grad q, frame, geometry, state, R, D)",
                      "flops_per_active_slot": flops_slot, "active_slots": nslots,
-                     "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz",
-                     "fp64_pipe_active_ncu": RES_FP64_PIPE_ACTIVE.get(wl) if args.precision == 0 else None,
+                     "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz (the FP64 unit)",
+                     "note": ROOFLINE_NOTE,
+                     "fp64_unit": {"flops_per_active_slot": unit_slot, "achieved": unit_tf,
+                                   "frac": unit_tf / FP64_PEAK_TFLOPS if unit_tf else None},
+                     "units_active_ncu": RES_UNITS_NCU.get(wl) if args.precision == 0 else None,
                      "launch_ms": res_ms, "phase_ms": phases},
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -674,7 +696,8 @@ def run_batch(args, rank, world, local_rank):
         "roofline": {"bound": "alu", "kernel": "k_residual", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
                      "flops_per_active_slot": RES_FLOPS_PER_SLOT[MID_WORKLOAD],
-                     "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz",
+                     "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz (the FP64 unit)",
+                     "note": ROOFLINE_NOTE,
                      "launch_ms": res_ms, "phase_ms": phases},
         "cpu_baseline": cpu,
         "e2e": e2e,
