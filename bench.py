@@ -89,14 +89,14 @@ START = 50  # first-order start-up iterations before warm-up and timing
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one residual
 # launch, from one ncu capture of the current kernel (profiles/), per
 # workload and threads per point; reported only for that launch shape and FP64
-RES_TRAFFIC = {MID_WORKLOAD: {2: 164.318208e6}, PROF_WORKLOAD: {1: 3.3923008e9},
+RES_TRAFFIC = {MID_WORKLOAD: {2: 164.222208e6}, PROF_WORKLOAD: {1: 3.380188928e9},
                WORKLOAD: {1: 14.592e9}}  # the last from a one-pass capture of the full-size launch
 # Unit utilisation of that launch (fraction of peak sustained, ncu): the FP64
 # pipe is the binding unit; the integer pipes (ALU, FMA-heavy: IMAD) carry
 # the fixed-point functions and the integer multiplies
-RES_UNITS_NCU = {MID_WORKLOAD: {"fp64_pipe": 0.7927, "alu_pipe": 0.3778, "fmaheavy_pipe": 0.3309, "issue": 0.3952},
-                 PROF_WORKLOAD: {"fp64_pipe": 0.8122, "alu_pipe": 0.3936, "fmaheavy_pipe": 0.3420,
-                                 "issue": 0.4065}}
+RES_UNITS_NCU = {MID_WORKLOAD: {"fp64_pipe": 0.7945, "alu_pipe": 0.3787, "fmaheavy_pipe": 0.3317, "issue": 0.3952},
+                 PROF_WORKLOAD: {"fp64_pipe": 0.8132, "alu_pipe": 0.3941, "fmaheavy_pipe": 0.3424,
+                                 "issue": 0.4070}}
 RES_UNITS_NCU[SUPER_WORKLOAD] = RES_UNITS_NCU[MID_WORKLOAD]
 RES_UNITS_NCU[WORKLOAD] = RES_UNITS_NCU[PROF_WORKLOAD]
 ROOFLINE_NOTE = ("achieved counts the method's FP64 arithmetic as the all-FP64 form executes it "
