@@ -387,6 +387,25 @@ lskum_status lskum_get_info(lskum_ctx *ctx, int32_t *n_points, int32_t *n_colour
  */
 lskum_status lskum_density_norm_noalloc(const double *r_rho_dev, int32_t n, double *norm_dev, void *cuda_stream);
 
+/*
+ * Self-test of the kernels' integer-pipe FP64 arithmetic (no counterpart in
+ * the paper: GB300-specific implementation of the method's operations).  On
+ * the current device, for k < n, out[k] =
+ *   op 0: a[k] * b[k] by the integer multiply the residual and the update
+ *         use (correctly rounded, the FP64 multiply's bits);
+ *   op 1: exp(a[k]) by the fixed-point exp behind exp(-S^2) in the split
+ *         fluxes (Eq. 11-13) and rho in the inverse of Eq. 14 (Tang's
+ *         table-driven method);
+ *   op 2: erfcx(min(|a[k]|, 9))/2 by the fixed-point Horner evaluation
+ *         behind A = (1 +- erf S)/2 of Eq. 11-13;
+ *   op 3: a[k] * b[k] by the FP64 unit.
+ * a, b, out: host arrays of n doubles (b may be NULL for ops 1 and 2); the
+ * call allocates, copies and synchronises (a test and diagnostics service,
+ * not for a hot path).  Errors: LSKUM_ERR_ARG (op not 0-3, n < 0, NULL
+ * array), LSKUM_ERR_CUDA.
+ */
+lskum_status lskum_selftest_fpint(int32_t op, const double *a, const double *b, double *out, int32_t n);
+
 /* Message of the last failure of ctx (or of the last failed create when ctx
  * is NULL); never NULL; valid until the next call on the same context. */
 const char *lskum_last_error(const lskum_ctx *ctx);

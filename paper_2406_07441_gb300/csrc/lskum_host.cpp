@@ -2302,6 +2302,26 @@ lskum_status lskum_get_wall_distance(lskum_ctx *c, double *d)
     return LSKUM_OK;
 }
 
+lskum_status lskum_selftest_fpint(int32_t op, const double *a, const double *b, double *out, int32_t n)
+{
+    if (op < 0 || op > 3 || n < 0 || (n > 0 && (!a || !out || ((op == 0 || op == 3) && !b))))
+        return LSKUM_ERR_ARG;
+    if (n == 0) return LSKUM_OK;
+    double *da = nullptr, *db = nullptr, *dout = nullptr;
+    const size_t bytes = (size_t)n * sizeof(double);
+    cudaError_t e = cudaMalloc(&da, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&db, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&dout, bytes);
+    if (e == cudaSuccess) e = cudaMemcpy(da, a, bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = b ? cudaMemcpy(db, b, bytes, cudaMemcpyHostToDevice) : cudaMemset(db, 0, bytes);
+    if (e == cudaSuccess) e = launch_selftest_fpint(op, da, db, dout, n, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, bytes, cudaMemcpyDeviceToHost);
+    cudaFree(da);
+    cudaFree(db);
+    cudaFree(dout);
+    return e == cudaSuccess ? LSKUM_OK : LSKUM_ERR_CUDA;
+}
+
 lskum_status lskum_set_launch_shape(lskum_ctx *c, int32_t tpp, int32_t sweep_lanes)
 {
     if (!c) return LSKUM_ERR_ARG;

@@ -213,6 +213,8 @@ cudaError_t launch_phase(const Dev &d, const Launch &L, int cur, int phase, int 
 cudaError_t launch_init_state(const Dev &d, int cur, bool project, cudaStream_t s);
 // Fill the global copy of the function tables the sweeps read (idempotent).
 cudaError_t launch_init_math(cudaStream_t s);
+// The integer-pipe FP64 arithmetic on n device values (lskum_selftest_fpint).
+cudaError_t launch_selftest_fpint(int op, const double *a, const double *b, double *out, int n, cudaStream_t s);
 cudaError_t launch_reset_ctrl(Ctrl *c, cudaStream_t s);
 // Prepare the control block for a run, on the device: flags cleared, drop
 // target set, it_start = it, stopped cases running again (failed ones stay).

@@ -1708,6 +1708,42 @@ cudaError_t launch_from_caller(const double *in, int ld, int n, const int32_t *i
     return cudaGetLastError();
 }
 
+// The integer-pipe FP64 arithmetic on the device, for the self-test entry
+// (op 0: a * b by mul_i; 1: exp(a) in fixed point; 2: erfcx(|a|)/2 in fixed
+// point after the kernels' clamp of |a| to 9; 3: a * b on the FP64 unit).
+__global__ void __launch_bounds__(256) k_selftest_fpint(int op, const double *a, const double *b, double *out, int n)
+{
+    __shared__ MathTables T;
+    load_math_tables(T);
+    __syncthreads();
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        double r;
+        if (op == 0) {
+            r = mul_i(a[k], b[k]);
+        } else if (op == 1) {
+            r = exp_t(T, a[k]);
+        } else if (op == 2) {
+            constexpr int kNineHi = 0x40220000;
+            const int hs = __double2hiint(a[k]) & 0x7fffffff;
+            const bool clamp = hs >= kNineHi;
+            const int ha = clamp ? kNineHi : hs, la = clamp ? 0 : __double2loint(a[k]);
+            const int iv = erfcx_interval(ha);
+            r = erfcx_half_fx<kErfcxDeg>((uint32_t)ha, (uint32_t)la, iv, (const int64_t *)T.ecx[iv], T.esh[iv]);
+        } else {
+            r = a[k] * b[k];
+        }
+        out[k] = r;
+    }
+}
+
+cudaError_t launch_selftest_fpint(int op, const double *a, const double *b, double *out, int n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const int blocks = (n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024;
+    k_selftest_fpint<<<blocks, 256, 0, s>>>(op, a, b, out, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_init_math(cudaStream_t s)
 {
     k_init_math<<<1, 256, 0, s>>>();

@@ -72,6 +72,7 @@ def load():
     L.lskum_time_phases.argtypes = [vp, i32, vp]
     L.lskum_autotune.argtypes = [vp, i32, P(i32), P(i32), P(d)]
     L.lskum_density_norm_noalloc.argtypes = [vp, i32, vp, vp]
+    L.lskum_selftest_fpint.argtypes = [i32, vp, vp, vp, i32]
     L.lskum_batch_create.argtypes = [P(lskum_cloud), P(lskum_opts), i32, vp, P(vp)]
     L.lskum_get_case_residuals.argtypes = [vp, i32, vp, i32, P(i32)]
     L.lskum_get_case_residuals4.argtypes = [vp, i32, vp, i32, P(i32)]
@@ -111,7 +112,8 @@ def load():
     L.lskum_destroy.restype = None
     for f in ("lskum_create", "lskum_set_state", "lskum_set_conserved", "lskum_run", "lskum_enqueue", "lskum_wait",
               "lskum_get_state", "lskum_get_field", "lskum_get_residuals", "lskum_get_forces", "lskum_get_order",
-              "lskum_get_info", "lskum_time_phases", "lskum_density_norm_noalloc", "lskum_batch_create",
+              "lskum_get_info", "lskum_time_phases", "lskum_density_norm_noalloc", "lskum_selftest_fpint",
+              "lskum_batch_create",
               "lskum_get_case_residuals", "lskum_get_case_residuals4", "lskum_get_case_forces", "lskum_get_case_info", "lskum_autotune",
               "lskum_get_wall_distance", "lskum_validate", "lskum_set_start_iters", "lskum_get_field_dev", "lskum_set_conserved_dev", "lskum_set_launch_shape",
               "lskum_set_host_io", "lskum_get_host_io", "lskum_mlp_create", "lskum_mlp_get_params",
@@ -137,6 +139,23 @@ def _cloud_struct(cloud, keep):
             np.ascontiguousarray(cloud.nbr_off, np.int32), np.ascontiguousarray(cloud.nbr_idx, np.int32)]
     keep.extend(a for a in arrs if a is not None)
     return lskum_cloud(int(len(cloud.x)), *[None if a is None else a.ctypes.data for a in arrs])
+
+
+FPINT_MUL, FPINT_EXP, FPINT_ERFCX_HALF, FPINT_MUL_FP64 = 0, 1, 2, 3
+
+
+def selftest_fpint(op, a, b=None):
+    """The kernels' integer-pipe FP64 arithmetic evaluated on the device
+    (include/lskum.h, lskum_selftest_fpint): op FPINT_MUL a*b (integer
+    multiply), FPINT_EXP exp(a), FPINT_ERFCX_HALF erfcx(min(|a|, 9))/2,
+    FPINT_MUL_FP64 a*b on the FP64 unit."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    bb = None if b is None else np.ascontiguousarray(b, dtype=np.float64)
+    out = np.empty_like(a)
+    s = load().lskum_selftest_fpint(int(op), _p(a), None if bb is None else _p(bb), _p(out), int(a.size))
+    if s != 0:
+        raise LskumError(s, f"lskum_selftest_fpint: status {s}")
+    return out
 
 
 def validate(clouds, conditions, **kw):

@@ -47,11 +47,12 @@ extern "C" void erfcx_half_many(const double *x, double *r, long n)
 """
 
 
-@pytest.fixture(scope="module")
-def host_fns():
+def build_host_fns():
+    """The header compiled for the host: (erfcx_half, exp) over float64
+    arrays, and the temporary directory to remove; None without g++."""
     gxx = shutil.which("g++")
     if gxx is None:
-        pytest.skip("no host C++ compiler")
+        return None
     d = tempfile.mkdtemp()
     src, so = os.path.join(d, "h.cpp"), os.path.join(d, "libh.so")
     with open(src, "w") as f:
@@ -69,11 +70,19 @@ def host_fns():
             fn(x.ctypes.data_as(dp), r.ctypes.data_as(dp), x.size)
             return r
         return f
-    yield call(lib.erfcx_half_many), call(lib.exp_many)
-    shutil.rmtree(d, ignore_errors=True)
+    return call(lib.erfcx_half_many), call(lib.exp_many), d
 
 
-def _args():
+@pytest.fixture(scope="module")
+def host_fns():
+    fns = build_host_fns()
+    if fns is None:
+        pytest.skip("no host C++ compiler")
+    yield fns[:2]
+    shutil.rmtree(fns[2], ignore_errors=True)
+
+
+def erfcx_args():
     rng = np.random.default_rng(21)
     edges = []
     for e in range(-5, 4):  # the binade intervals' edges and their neighbours
@@ -87,7 +96,7 @@ def _args():
 
 def test_host_build_equals_the_exact_emulation(host_fns):
     from test_fastmath_cpu import erfcx_half_fx, exp_t
-    x = _args()
+    x = erfcx_args()
     got = host_fns[0](x)
     ref = np.array([erfcx_half_fx(float(v)) for v in x])
     assert np.array_equal(got.view(np.uint64), ref.view(np.uint64))
@@ -101,7 +110,7 @@ def test_host_build_equals_the_exact_emulation(host_fns):
 
 def test_within_the_interpolant_error_and_one_rounding(host_fns):
     mp.mp.dps = 40
-    x = _args()
+    x = erfcx_args()
     got = host_fns[0](x)
     worst = 0.0
     for v, g in zip(x, got):

@@ -203,9 +203,10 @@ def _oracle_run(key, cloud, mach, aoa, iters, **kw):
 
 # Launch shapes (threads per point in the gradient and residual kernels, sweep
 # lanes per point; 32 = the packed sweeps): the benchmark's autotuned choice on
-# the 147,584-point cloud first, then the size-based default of a new context,
-# then the packed form with the widest gradient / residual groups.
-FULL_SIZE_SHAPES = [(2, 32), (1, 4), (4, 32)]
+# the 147,584- and 5,242,880-point clouds first (one thread per point, packed
+# sweeps), the packed form at 2 and 4 threads per point (the autotuner's choice
+# on other clouds and kernels), then the size-based default of a new context.
+FULL_SIZE_SHAPES = [(1, 32), (2, 32), (4, 32), (1, 4)]
 
 
 @pytest.mark.parametrize("jvp", [0, 1])
@@ -214,7 +215,7 @@ def test_config2_full_size(jvp):
     K = 2 (the benchmark's setting), each JVP mode: one first-order start-up
     iteration and two second-order ones, every field of the last against the
     oracle, in each launch shape of FULL_SIZE_SHAPES -- among them the packed
-    sweeps at 2 threads per point that the benchmark times, at full size (all
+    sweeps at 1 thread per point that the benchmark times, at full size (all
     16 colour levels, framed-point warps spread over the grid, the interior
     groups of 20-slot lists)."""
     lk = _lskum()
@@ -244,20 +245,21 @@ def test_config2_full_size(jvp):
         del s
 
 
+@pytest.mark.parametrize("tpp", [1, 2])
 @pytest.mark.parametrize("jvp", [0, 1])
-def test_packed_sweeps_history_41k_points(jvp):
-    """The packed sweeps (2 threads per point, as the benchmark runs them) on a
-    jittered 336x136 cloud with 10% removed (41,264 points, 14+ colour levels
-    with many framed-point warps each): 40 iterations (20 first-order start-up,
-    20 second-order) against the oracle: history 1e-10 per entry, final state
-    1e-9, Cl / Cd 1e-9."""
+def test_packed_sweeps_history_41k_points(jvp, tpp):
+    """The packed sweeps (1 or 2 threads per point in the gradient and
+    residual kernels, the benchmark's shapes) on a jittered 336x136 cloud with
+    10% removed (41,264 points, 14+ colour levels with many framed-point warps
+    each): 40 iterations (20 first-order start-up, 20 second-order) against
+    the oracle: history 1e-10 per entry, final state 1e-9, Cl / Cd 1e-9."""
     lk = _lskum()
     c = cached_cloud("jit336x136", lambda: cg.naca0012_jittered(336, 136, seed=cg.BASE_SEED + 21))
     assert c.n > 40000
     r = _oracle_run(("jit336x136", jvp), c, 0.8, 1.25, 40, cfl=100.0, K=2, jvp=jvp, first_order=20)
     assert r["status"] == 0 and r["done"] == 40
     s = lk.Solver(c, 0.8, 1.25, inner_iters=2, jvp=jvp, first_order_iters=20)
-    s.set_launch_shape(2, 32)
+    s.set_launch_shape(tpp, 32)
     assert s.run(40) == 40
     h = s.residuals()
     rel = np.abs(h - r["hist"]) / r["hist"]
