@@ -83,20 +83,20 @@ RES_FLOPS_PER_SLOT = {MID_WORKLOAD: 336.07, SUPER_WORKLOAD: 336.07, PROF_WORKLOA
 # multiplications as correctly rounded integer multiplies on the integer
 # pipes, beside the FP64 unit; the FP64 flops it still executes on the FP64
 # unit per slot (ncu, the same counting; profiles/)
-RES_FP64_UNIT_FLOPS_PER_SLOT = {MID_WORKLOAD: 155.07, SUPER_WORKLOAD: 155.07, PROF_WORKLOAD: 154.67,
+RES_FP64_UNIT_FLOPS_PER_SLOT = {MID_WORKLOAD: 154.72, SUPER_WORKLOAD: 154.72, PROF_WORKLOAD: 154.67,
                                 WORKLOAD: 154.67}
 START = 50  # first-order start-up iterations before warm-up and timing
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one residual
 # launch, from one ncu capture of the current kernel (profiles/), per
 # workload and threads per point; reported only for that launch shape and FP64
-RES_TRAFFIC = {MID_WORKLOAD: {2: 164.222208e6}, PROF_WORKLOAD: {1: 3.380188928e9},
-               WORKLOAD: {1: 14.592e9}}  # the last from a one-pass capture of the full-size launch
+RES_TRAFFIC = {MID_WORKLOAD: {1: 163.482624e6}, PROF_WORKLOAD: {1: 3.407065856e9},
+               WORKLOAD: {1: 14.650e9}}  # the last from a one-pass capture of the full-size launch
 # Unit utilisation of that launch (fraction of peak sustained, ncu): the FP64
 # pipe is the binding unit; the integer pipes (ALU, FMA-heavy: IMAD) carry
 # the fixed-point functions and the integer multiplies
-RES_UNITS_NCU = {MID_WORKLOAD: {"fp64_pipe": 0.7945, "alu_pipe": 0.3787, "fmaheavy_pipe": 0.3317, "issue": 0.3952},
-                 PROF_WORKLOAD: {"fp64_pipe": 0.8132, "alu_pipe": 0.3941, "fmaheavy_pipe": 0.3424,
-                                 "issue": 0.4070}}
+RES_UNITS_NCU = {MID_WORKLOAD: {"fp64_pipe": 0.8058, "alu_pipe": 0.3980, "fmaheavy_pipe": 0.3469, "issue": 0.4153},
+                 PROF_WORKLOAD: {"fp64_pipe": 0.8342, "alu_pipe": 0.4119, "fmaheavy_pipe": 0.3591,
+                                 "issue": 0.4282}}
 RES_UNITS_NCU[SUPER_WORKLOAD] = RES_UNITS_NCU[MID_WORKLOAD]
 RES_UNITS_NCU[WORKLOAD] = RES_UNITS_NCU[PROF_WORKLOAD]
 ROOFLINE_NOTE = ("achieved counts the method's FP64 arithmetic as the all-FP64 form executes it "
