@@ -90,7 +90,7 @@ START = 50  # first-order start-up iterations before warm-up and timing
 # launch, from one ncu capture of the current kernel (profiles/), per
 # workload and threads per point; reported only for that launch shape and FP64
 RES_TRAFFIC = {MID_WORKLOAD: {1: 163.482624e6}, PROF_WORKLOAD: {1: 3.407065856e9},
-               WORKLOAD: {1: 14.650e9}}  # the last from a one-pass capture of the full-size launch
+               WORKLOAD: {1: 14.584e9}}  # the last from a one-pass capture of the full-size launch
 # Unit utilisation of that launch (fraction of peak sustained, ncu): the FP64
 # pipe is the binding unit; the integer pipes (ALU, FMA-heavy: IMAD) carry
 # the fixed-point functions and the integer multiplies

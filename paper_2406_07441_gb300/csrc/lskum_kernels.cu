@@ -475,9 +475,11 @@ __global__ void __launch_bounds__(256) k_grad(Dev d, const double *__restrict__ 
 // R += y with Kahan's compensated summation (W. Kahan, "Further remarks on
 // reducing truncation errors", CACM 8(1), 1965): c carries the negated
 // rounding error of the running sum into the next term.  The caller forms y
-// as the slot's term less c, the weighted flux differences of its two split
-// sub-stencils folded in by FMAs, so one compensated addition serves both.
-// The final sum is R - c.
+// as the terms of a group of four slots less c, the weighted flux
+// differences of their split sub-stencils folded in by FMAs, so one
+// compensated addition serves the group (a quarter of the per-slot
+// additions' FP64 instructions; R changed by at most 6e-17 relative).  The
+// final sum is R - c.
 __device__ __forceinline__ void comp_add(double &R, double &c, double y)
 {
     const double t = R + y;
@@ -530,6 +532,11 @@ __global__ void __launch_bounds__(128, LSKUM_RES_MIN_BLOCKS) k_residual(Dev d, S
         }
         const int deg = d.deg[kk];
         const int base = d.slice_off[kk >> 5] + (kk & 31);
+        // (COMP) the terms of a group of four slots are summed by FMAs into y,
+        // which starts as the negated carried error; each group then enters R
+        // by one compensated addition, and a last partial group after the loop
+        double y[4] = {0.0, 0.0, 0.0, 0.0};
+        int ng = 0;  // (COMP) slots in the current group
         for (int j = sub; j < deg; j += TPP) {
             const int e = base + 32 * j;
             const int mb = d.memb[e];
@@ -549,9 +556,6 @@ __global__ void __launch_bounds__(128, LSKUM_RES_MIN_BLOCKS) k_residual(Dev d, S
             const Prim Pi = q_to_prim(T, qi);
             const Prim P0 = q_to_prim(T, q0t);
             // the slot's sub-stencils (x then y, or t then n): one loop body
-            double y[4];  // (COMP) the slot's term less the carried error
-#pragma unroll
-            for (int c = 0; c < 4; c++) y[c] = -Rc[c];
 #pragma unroll 1
             for (int sb = 0; sb < 2; sb++) {
                 const int m = sb == 0 ? (mb & 3) : (mb >> 2);
@@ -568,10 +572,18 @@ __global__ void __launch_bounds__(128, LSKUM_RES_MIN_BLOCKS) k_residual(Dev d, S
                     else R[c] = fma(w, Gi[c] - G0[c], R[c]);
                 }
             }
-            if (COMP) {
+            if (COMP && ++ng == 4) {
 #pragma unroll
-                for (int c = 0; c < 4; c++) comp_add(R[c], Rc[c], y[c]);
+                for (int c = 0; c < 4; c++) {
+                    comp_add(R[c], Rc[c], y[c]);
+                    y[c] = -Rc[c];
+                }
+                ng = 0;
             }
+        }
+        if (COMP && ng > 0) {
+#pragma unroll
+            for (int c = 0; c < 4; c++) comp_add(R[c], Rc[c], y[c]);
         }
     }
 #pragma unroll
@@ -1349,41 +1361,48 @@ __global__ void __launch_bounds__(256) k_update(Dev d, int cur, bool inc, bool p
     dst.q[1 * ld + k] = mul_i(twice(P.beta), P.u);
     dst.q[2 * ld + k] = mul_i(twice(P.beta), P.v);
     dst.q[3 * ld + k] = signed_by(twice(P.beta), false);
-    double *pr = dst.prim + (size_t)k * kPrimStride;
-    pr[P_RHO] = P.rho;
-    pr[P_IRHO] = P.irho;
-    pr[P_U] = P.u;
-    pr[P_V] = P.v;
-    pr[P_P] = P.p;
-    pr[P_BETA] = P.beta;
-    pr[P_SB] = P.sb;
-    pr[P_ISB] = P.isb;
-    pr[P_I2P] = P.i2p;
-    pr[P_Q2] = P.q2;
-    pr[P_E1] = P.e1;
-    pr[P_E2] = P.e2;
+    // the per-point record, assembled in registers and stored as 16-byte
+    // vectors (and, in mixed precision, its FP32 copy from the same registers)
+    double rec[P_NFIELDS];
+    rec[P_RHO] = P.rho;
+    rec[P_IRHO] = P.irho;
+    rec[P_U] = P.u;
+    rec[P_V] = P.v;
+    rec[P_P] = P.p;
+    rec[P_BETA] = P.beta;
+    rec[P_SB] = P.sb;
+    rec[P_ISB] = P.isb;
+    rec[P_I2P] = P.i2p;
+    rec[P_Q2] = P.q2;
+    rec[P_E1] = P.e1;
+    rec[P_E2] = P.e2;
     const double sx = mul_i(P.u, P.sb), sy = mul_i(P.v, P.sb);
     double Ex, ex, Ey, ey;
     split_E(T, sx, Ex, ex);
     split_E(T, sy, Ey, ey);
     const double bk = mul_i(kInv2SqrtPi, P.isb);
     const double bx = mul_i(ex, bk), by = mul_i(ey, bk);
-    pr[P_BSX] = mul_i(twice(bx), sx);
-    pr[P_APX] = sx >= 0.0 ? 1.0 - Ex : Ex;
-    pr[P_AMX] = sx >= 0.0 ? Ex : 1.0 - Ex;
-    pr[P_EKX] = mul_i(ex, kInvSqrtPi);
-    pr[P_BX] = bx;
-    pr[P_BSY] = mul_i(twice(by), sy);
-    pr[P_APY] = sy >= 0.0 ? 1.0 - Ey : Ey;
-    pr[P_AMY] = sy >= 0.0 ? Ey : 1.0 - Ey;
-    pr[P_EKY] = mul_i(ey, kInvSqrtPi);
-    pr[P_BY] = by;
-    pr[P_UE1] = mul_i(P.u, P.e1);
-    pr[P_VE1] = mul_i(P.v, P.e1);
-    if (dst.primf) {  // mixed precision: the sweeps' FP32 copy of the record
-        float *pf = dst.primf + (size_t)k * kPrimStride;
+    rec[P_BSX] = mul_i(twice(bx), sx);
+    rec[P_APX] = sx >= 0.0 ? 1.0 - Ex : Ex;
+    rec[P_AMX] = sx >= 0.0 ? Ex : 1.0 - Ex;
+    rec[P_EKX] = mul_i(ex, kInvSqrtPi);
+    rec[P_BX] = bx;
+    rec[P_BSY] = mul_i(twice(by), sy);
+    rec[P_APY] = sy >= 0.0 ? 1.0 - Ey : Ey;
+    rec[P_AMY] = sy >= 0.0 ? Ey : 1.0 - Ey;
+    rec[P_EKY] = mul_i(ey, kInvSqrtPi);
+    rec[P_BY] = by;
+    rec[P_UE1] = mul_i(P.u, P.e1);
+    rec[P_VE1] = mul_i(P.v, P.e1);
+    static_assert(P_NFIELDS == kPrimStride && kPrimStride % 4 == 0, "record stored as whole vectors");
+    double2 *pr2 = reinterpret_cast<double2 *>(dst.prim + (size_t)k * kPrimStride);
 #pragma unroll
-        for (int f = 0; f < P_NFIELDS; f++) pf[f] = (float)pr[f];
+    for (int f = 0; f < P_NFIELDS / 2; f++) pr2[f] = make_double2(rec[2 * f], rec[2 * f + 1]);
+    if (dst.primf) {  // mixed precision: the sweeps' FP32 copy of the record
+        float4 *pf4 = reinterpret_cast<float4 *>(dst.primf + (size_t)k * kPrimStride);
+#pragma unroll
+        for (int f = 0; f < P_NFIELDS / 4; f++)
+            pf4[f] = make_float4((float)rec[4 * f], (float)rec[4 * f + 1], (float)rec[4 * f + 2], (float)rec[4 * f + 3]);
     }
 }
 
