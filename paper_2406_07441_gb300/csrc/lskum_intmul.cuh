@@ -7,8 +7,10 @@
 // or two cycles, stand idle in an FP64-bound kernel.  mul_i moves a
 // multiplication onto those pipes: the 106-bit product of the two 53-bit
 // significands from four 32x32->64-bit integer multiply-adds, then
-// normalisation, rounding and packing in about thirty integer instructions.
-// That is cheaper than the FP64 unit's 64 cycles and runs beside it.
+// normalisation, rounding and packing: about fifty integer instructions in
+// all (ncu), some thirty of them on the ALU pipe, which issues one every two
+// cycles per sub-partition -- as fast as the FP64 unit's 64 cycles, and it
+// runs beside it.
 //
 // Method: the textbook binary multiplication of IEEE 754-2008 sec. 4.3 and
 // 5.4.1 (exact significand product, one normalising shift, round to nearest
