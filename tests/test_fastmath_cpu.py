@@ -2,6 +2,7 @@
 step (the fixed-point integer steps of exp and of the erfcx polynomial
 exactly, multiplications rounded once) with the constants of the generated
 header, against mpmath at 60 digits."""
+import functools
 import os
 import re
 import struct
@@ -44,15 +45,20 @@ def _consts():
     return dict(cfx=cfx, lfx=lfx, n=n, shift=shift, tab=tab, ecx=ecx, esh=esh, deg=deg, eshift=eshift, key0=key0)
 
 C = _consts()
-mp.mp.prec = 300
+# exact products and sums of doubles (rounded once by float()) need ~2 x 53
+# bits plus the exponent spread; 300 bits, set locally so that no other test
+# module's precision leaks in
+PREC = 300
 
 
 def fma(a, b, c):
-    return float(mp.mpf(a) * mp.mpf(b) + mp.mpf(c))
+    with mp.workprec(PREC):
+        return float(mp.mpf(a) * mp.mpf(b) + mp.mpf(c))
 
 
 def mul(a, b):
-    return float(mp.mpf(a) * mp.mpf(b))
+    with mp.workprec(PREC):
+        return float(mp.mpf(a) * mp.mpf(b))
 
 
 def hi_word(x):
@@ -139,6 +145,16 @@ def ulp(x):
     return np.spacing(abs(x))
 
 
+def _at_prec(test):
+    """Run a test's mpmath references at PREC bits."""
+    @functools.wraps(test)
+    def run(*a, **k):
+        with mp.workprec(PREC):
+            return test(*a, **k)
+    return run
+
+
+@_at_prec
 def test_exp_within_one_ulp():
     rng = np.random.default_rng(3)
     xs = np.concatenate([np.linspace(-700, 700, 401), rng.uniform(-5, 5, 600), rng.uniform(-1e-3, 1e-3, 50),
@@ -155,6 +171,7 @@ def test_exp_within_one_ulp():
     assert worst_small <= 0.52 and worst <= 1.0, (worst_small, worst)
 
 
+@_at_prec
 def test_split_A_absolute_and_tail_accuracy():
     rng = np.random.default_rng(4)
     Ss = np.concatenate([np.linspace(-9.5, 9.5, 381), rng.normal(0, 1.0, 400), [0.0, -0.0, 0.75, 1.75, 3.25, 5.5]])
