@@ -103,7 +103,7 @@ def hexd(v):
     return float(v).hex()
 
 
-def main():
+def main(out=OUT):
     lines = [
         "// Generated by gen_mathconst.py (mpmath, 60 digits); do not edit.",
         "// Constants of the kernels' own FP64 exp and erfcx; see gen_mathconst.py for the methods.",
@@ -192,9 +192,9 @@ def main():
         lines.append("    {" + ", ".join(row) + "},")
     lines.append("};")
     lines += ["", "}  // namespace lskum", ""]
-    with open(OUT, "w") as f:
+    with open(out, "w") as f:
         f.write("\n".join(lines))
-    print(OUT)
+    print(out)
 
 
 if __name__ == "__main__":
